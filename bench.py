@@ -1,0 +1,356 @@
+"""Benchmark of the sketched Tucker core update on GB300 (one JSON line).
+
+A step is one sketched core update (leverage scores -> product-distribution
+sampling -> dedupe -> gather and weights -> Kronecker Gram / right-hand side ->
+ridge solve) on the 3-way dense workload 512 x 512 x 512 FP32, Tucker rank
+(8,8,8) (core dimension d = 512), sigma = 0.05, lambda = 1e-2, m = 50,000
+sampled rows.  The exact core update (TTM chain + factor eigendecompositions)
+on the same inputs is timed beside it, and the ridge-loss ratio of the two
+cores is reported.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|tf32|fp32|fp64]
+    python bench.py --impl reference ...   # the CPU oracle, timed on host cores
+
+Timing: CUDA events on the library's stream around each call, L2 flushed
+(256 MiB write) before every timed step; W untimed warm-up steps; barrier +
+synchronize around the timed region; max over ranks.  Multi-GPU runs are
+independent replicas (the update has no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "core-update ms, sketched vs exact, 1 GB300 at <=1.01x ridge loss; Kron rows/s"
+WORKLOAD = "dense3_512_r8_f32"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# FP64 CUDA-core peak: 1.25 TFLOP/s (the GB300 nominal FP64 rate).
+FP64_PEAK_TFLOPS = 1.25
+# tcgen05 dense peak relative to BF16: TF32 runs at half the BF16 rate.
+TC_RATIO = {"bf16": 1.0, "tf32": 0.5}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--prec", default="auto")
+    p.add_argument("--reg", default="exact")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+def cpu_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads", 0) for i in threadpool_info()), default=0)
+        if n:
+            return n
+    except Exception:
+        pass
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(v):
+            return int(os.environ[v])
+    return len(os.sched_getaffinity(0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{self.gpu}.csv")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_step(X, F, w, reg):
+    from oracle import core_update as CU, sampling as S
+    regc = S.REG_EXACT if reg == "exact" else S.REG_AUGMENTED
+    return CU.sketched_core(X, F, w.lam, w.m, w.seed_sample, 0, regc)
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    w = synth.WORKLOADS[args.workload]
+    P = synth.tucker_problem(w)
+    X, F = P["X"], P["factors"]
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_step(X, F, w, args.reg)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(X, F, w, args.reg)
+        times.append((time.perf_counter() - t0) * 1e3)
+    ms = statistics.mean(times)
+    cores = cpu_cores()
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, "fp64", args.reg),
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full sketched core updates of the workload "
+                                       f"(numpy FP64 oracle)"},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(w, prec, reg):
+    return {"workload": w.name, "dims": list(w.dims), "ranks": list(w.ranks), "d": w.d,
+            "m": w.m, "lambda": w.lam, "sigma": w.sigma, "x_dtype": w.dtype, "gram_prec": prec,
+            "reg": reg, "seed": w.seed_sample,
+            "l2": "flushed before every timed step (256 MiB write); X is 512 MiB"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2107_10654_gb300 import tucker as T
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    w = synth.WORKLOADS[args.workload]
+    prec = args.prec
+    if prec == "auto":
+        prec = os.environ.get("TUCKER_BENCH_PREC", "bf16")
+    P = synth.tucker_problem(w)
+    X_h, F_h = P["X"], P["factors"]
+    X_pin = torch.from_numpy(X_h).pin_memory()
+    F_pin = [torch.from_numpy(a).pin_memory() for a in F_h]
+    X = X_pin.to(dev)
+    F = [a.to(dev) for a in F_pin]
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    h = T.Handle()
+    stream = h.stream
+
+    def sketched(core_out=None, stats=True):
+        return T.tucker_core_update_sketched(h, X, F, w.lam, w.m, w.seed_sample, 0, args.reg, prec,
+                                             core_out=core_out, stats=stats)
+
+    def exact(core_out=None):
+        return T.tucker_core_update_exact(h, X, F, w.lam, "fp64", core_out=core_out)
+
+    # correctness of this configuration before timing: loss ratio vs exact
+    g_sk, st0 = sketched()
+    g_ex = exact()
+    loss_sk = T.tucker_ridge_loss(h, X, F, w.lam, g_sk)
+    loss_ex = T.tucker_ridge_loss(h, X, F, w.lam, g_ex)
+    loss_ratio = loss_sk / loss_ex
+
+    for _ in range(args.warmup):
+        sketched(core_out=g_sk)
+        exact(core_out=g_ex)
+    torch.cuda.synchronize()
+
+    def timed(fn, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        out = []
+        for i in range(k):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            out.append(fn())
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], out
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        sk_ms, sk_out = timed(lambda: sketched(core_out=g_sk), args.steps)
+        ex_ms, _ = timed(lambda: exact(core_out=g_ex), args.steps)
+        # end to end through the public API: host (pinned) inputs in, core out to host
+        core_host = torch.empty(w.d, dtype=torch.float64).pin_memory()
+        Xe = torch.empty_like(X)
+        Fe = [torch.empty_like(a) for a in F]
+        e2e_ms = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                Xe.copy_(X_pin, non_blocking=True)
+                for a, b in zip(Fe, F_pin):
+                    a.copy_(b, non_blocking=True)
+            g = T.tucker_core_update_sketched(h, Xe, Fe, w.lam, w.m, w.seed_sample, 0, args.reg,
+                                              prec)
+            with torch.cuda.stream(stream):
+                core_host.copy_(g, non_blocking=True)
+            stream.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    ms = statistics.mean(sk_ms)
+    ms_ex = statistics.mean(ex_ms)
+    ms_e2e = statistics.mean(e2e_ms)
+    stats = [s for _, s in sk_out]
+    stage = {k: statistics.mean(s[k] for s in stats)
+             for k in ("ms_leverage", "ms_sample", "ms_dedupe", "ms_gather", "ms_gram", "ms_solve")}
+    n_real = stats[-1]["n_real"]
+    launches = int(sum(s["launches"] for s in stats))
+    kron_rows_s = n_real / (stage["ms_gram"] * 1e-3)
+
+    if world > 1:
+        t = torch.tensor([ms, ms_ex, ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_ex, ms_e2e = [float(v) for v in t.tolist()]
+
+    pk, src = peaks()
+    d = w.d
+    dominant = max(stage, key=stage.get)
+    if dominant == "ms_gram":
+        flops = n_real * d * (d + 1) + 2 * n_real * d
+        if prec in ("bf16", "tf32"):
+            peak = pk["bf16_tflops"] * TC_RATIO[prec]
+            bound, unit, note = "tensor", "TFLOP/s", f"{prec} tcgen05 ({src} bf16 x {TC_RATIO[prec]})"
+        elif prec == "fp32":
+            peak = 152 * 128 * 2 * 2.07e9 / 1e12
+            bound, unit, note = "alu", "TFLOP/s", "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+        else:
+            peak = FP64_PEAK_TFLOPS
+            bound, unit, note = "alu", "TFLOP/s", "FP64 nominal 1.25 TFLOP/s"
+        achieved = flops / (stage["ms_gram"] * 1e-3) / 1e12
+        kernel = "k_syrk (Kronecker Gram)"
+        traffic = None
+    elif dominant == "ms_solve":
+        flops = d ** 3 / 3 + 4 * d * d
+        achieved = flops / (stage["ms_solve"] * 1e-3) / 1e12
+        peak, bound, unit, note = FP64_PEAK_TFLOPS, "alu", "TFLOP/s", "FP64 nominal 1.25 TFLOP/s"
+        kernel = "FP64 Cholesky + triangular solves"
+        traffic = None
+    else:
+        dominant_ms = stage[dominant]
+        byts = 8 * w.m * 3
+        achieved = byts / (dominant_ms * 1e-3) / 1e9
+        peak, bound, unit, note = pk["hbm_gbs"], "hbm", "GB/s", f"{src} copy bandwidth"
+        kernel = dominant
+        traffic = None
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": traffic, "kernel": kernel, "peak_source": note,
+            "stage_ms": stage[dominant]}
+    # exact path: one streaming read of X by the first n-mode product
+    exact_gbs = (X.numel() * X.element_size()) / (ms_ex * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        budget, times = 12.0, []
+        t_start = time.perf_counter()
+        while not times or (time.perf_counter() - t_start) < budget and len(times) < 5:
+            t0 = time.perf_counter()
+            oracle_step(X_h, F_h, w, args.reg)
+            times.append((time.perf_counter() - t0) * 1e3)
+        cpu = {"value": statistics.mean(times), "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{len(times)} full sketched core updates of the same workload "
+                         f"(numpy FP64 oracle, m = {w.m})"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+                "config": workload_config(w, prec, args.reg),
+                "exact_ms": ms_ex, "speedup_vs_exact": ms_ex / ms, "loss_ratio": loss_ratio,
+                "kron_rows_per_s": kron_rows_s * world, "n_unique": stats[-1]["n_unique"],
+                "refine_iters": stats[-1]["refine_iters"], "stage_ms": stage,
+                "exact_hbm_gbs": exact_gbs,
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": ms_e2e, "unit": "ms",
+                        "h2d_bytes_per_step": int(X.numel() * X.element_size() +
+                                                  sum(a.numel() * a.element_size() for a in F)),
+                        "d2h_bytes_per_step": int(w.d * 8)},
+                "clocks": clk.summary(), "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

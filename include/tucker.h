@@ -1,0 +1,283 @@
+/*
+ * tucker.h - C ABI of the GB300 sketched Tucker core-update library (libtucker.so).
+ *
+ * The library implements the core-tensor step of regularised Tucker ALS from
+ * "Fast Low-Rank Tensor Decomposition by Ridge Leverage Score Sampling"
+ * (Fahrbach, Ghadiri, Fu): the ridge regression
+ *
+ *     argmin_g || K g - vec(X) ||_2^2 + lambda ||g||_2^2,
+ *     K = A^(1) (x) A^(2) (x) ... (x) A^(N)                    (Alg. 2, core line)
+ *
+ * solved either exactly (the plain method) or on a row sketch of K drawn from
+ * the product of the factor leverage-score distributions (Alg. 3 -> Alg. 1).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Layout: tensors are row-major with the LAST index fastest; the linear
+ *    index of (i_1..i_N) is ((i_1*I_2 + i_2)*I_3 + i_3)...  A factor A^(n) is
+ *    an I_n x R_n row-major matrix.  vec(G) of the core uses the same row-major
+ *    order over (r_1..r_N), which is the column order of K.  (The paper writes
+ *    vec as column stacking; only row-major vec makes K = A^(1) (x) ... (x)
+ *    A^(N) consistent, so row-major is used throughout.)
+ *  - Pointers: every array argument is a DEVICE pointer owned by the caller
+ *    unless the parameter name ends in _host.  The library never frees caller
+ *    memory.  Device arrays must be aligned to their element size.
+ *  - Streams: every call enqueues work on the handle's stream.  Calls that
+ *    return host values (counts, ranks, losses, statistics) synchronise that
+ *    stream before returning; the others are asynchronous unless the handle
+ *    is in synchronous-status mode (the default, see tucker_set_sync).
+ *  - Errors: functions return a tucker_status; they never abort, trap or
+ *    print.  tucker_last_error() gives a one-line message for the last failure
+ *    on a handle.  Errors found on the device (non-SPD pivot, draw limit, hash
+ *    probe limit) are reported by the call that launched the work when the
+ *    handle is in synchronous-status mode, else by tucker_sync().
+ *  - Determinism: the same inputs, seed and sweep give bit-identical sampled
+ *    keys, counts and probabilities, equal to the CPU oracle's given the same
+ *    leverage scores.
+ *  - Thread safety: a handle is used by one host thread at a time.
+ */
+#ifndef TUCKER_H
+#define TUCKER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TUCKER_MAX_ORDER 8
+#define TUCKER_MAX_RANK 64      /* per-mode rank limit R_n */
+
+typedef enum {
+  TUCKER_OK = 0,
+  TUCKER_EINVAL = 1,      /* invalid argument: shape, rank, dtype, null pointer, lambda */
+  TUCKER_ENOMEM = 2,      /* device allocation of the handle's workspace failed */
+  TUCKER_ECUDA = 3,       /* a CUDA runtime call failed (message in tucker_last_error) */
+  TUCKER_ENOTSPD = 4,     /* Cholesky met a non-positive pivot: G + lambda*reg is not SPD */
+  TUCKER_ERANK = 5,       /* a factor has zero total leverage (e.g. an all-zero factor) */
+  TUCKER_EDRAWLIMIT = 6,  /* missing-entry sampling used max_draws before m accepted */
+  TUCKER_EHASHFULL = 7,   /* observed-entry hash table exceeded its probe limit */
+  TUCKER_ECAPACITY = 8,   /* a caller-provided output array is too small */
+  TUCKER_ENOTSUP = 9,     /* combination not supported by this build (e.g. no sm_103a GPU) */
+  TUCKER_EINTERNAL = 10   /* a device-side consistency check failed */
+} tucker_status;
+
+typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
+
+/* Arithmetic of the sketched Gram G = sum_u w_u k_u k_u^T (and of the exact
+ * missing-entry Gram).  The right-hand side h, the Cholesky factorisation of
+ * G + lambda*I and the iterative-refinement residual are FP64 in every mode.
+ * With a reduced-precision Gram the Cholesky factor of the rounded Gram is a
+ * preconditioner: g <- g + M~^-1 (h - M g) with M g evaluated in FP64 on the
+ * implicit rows, until ||correction|| < 1e-13 ||g|| (at most 8 iterations). */
+typedef enum {
+  TUCKER_PREC_FP64 = 0,   /* FP64 CUDA-core Gram; no refinement needed */
+  TUCKER_PREC_FP32 = 1,   /* FP32 CUDA-core Gram, FP64 refinement */
+  TUCKER_PREC_TF32 = 2,   /* tcgen05 TF32 tensor-core Gram, FP32 accumulate, FP64 refinement */
+  TUCKER_PREC_BF16 = 3    /* tcgen05 BF16 tensor-core Gram, FP32 accumulate, FP64 refinement */
+} tucker_prec;
+
+/* How the lambda*I term enters the sketched problem. */
+typedef enum {
+  /* sketch only the rows of K and add lambda*I exactly: solve (G + lambda I) g = h */
+  TUCKER_REG_EXACT = 0,
+  /* Alg. 1 with d'_eff = 0: sample from the augmented distribution D(l(K), 0)
+   * of Sec. 3 over the rows of [K; sqrt(lambda) I]; a coin picks a row of K
+   * (mass l(K), normalised to d) or one of the d regulariser rows (mass 1
+   * each); the sampled regulariser rows give lambda*diag(D) in place of
+   * lambda*I */
+  TUCKER_REG_AUGMENTED = 1
+} tucker_reg;
+
+/* The data tensor X of the problem statement (Sec. 2): either dense or a list
+ * of observed entries (Sec. 4.2, missing data).  Exactly one of `dense` and
+ * (`keys`,`vals`) is non-NULL. */
+typedef struct {
+  int order;                        /* N, 1 <= N <= TUCKER_MAX_ORDER */
+  int64_t dims[TUCKER_MAX_ORDER];   /* I_1..I_N; prod(I_n) < 2^62 */
+  tucker_dtype dtype;               /* element type of dense / vals (and of the factors) */
+  const void* dense;                /* device, prod(I_n) elements row-major, or NULL */
+  int64_t nnz;                      /* number of observed entries (COO) */
+  const uint64_t* keys;             /* device [nnz]: row-major linear indices, strictly increasing */
+  const void* vals;                 /* device [nnz]: entry values, dtype */
+} tucker_tensor;
+
+/* A deduplicated row sample of K (or of [K; sqrt(lambda) I]).  Caller-owned
+ * device arrays of length `capacity`; n_unique and n_draws are written by
+ * tucker_sample_rows and read by tucker_core_update_sketched when the sample
+ * is passed back in (a frozen sketch, used for finite differences and the
+ * adjoint). */
+typedef struct {
+  int64_t capacity;     /* length of keys / counts / prob */
+  int64_t n_unique;     /* number of distinct sampled rows, sorted ascending by key */
+  int64_t n_draws;      /* T: draws used (= m when dense; more when entries are missing) */
+  uint64_t* keys;       /* row key: linear row index of K, or prod(I)+j for regulariser row j */
+  uint32_t* counts;     /* multiplicity c_u of each distinct row among the accepted draws */
+  double* prob;         /* sampling probability p_u of the row (weights are c_u/(T p_u)) */
+} tucker_samples;
+
+/* Per-call statistics (host struct, optional). Times are CUDA-event
+ * milliseconds per stage on the handle's stream. */
+typedef struct {
+  double ms_leverage, ms_sample, ms_dedupe, ms_gather, ms_gram, ms_solve, ms_total;
+  int64_t n_unique;     /* distinct rows in the sketch */
+  int64_t n_draws;      /* T */
+  int64_t n_real;       /* distinct rows of K (the rest are regulariser rows) */
+  int refine_iters;     /* refinement iterations used (tensor-core precisions) */
+  double refine_rel;    /* last ||correction|| / ||g|| of the refinement */
+  uint64_t solve_id;    /* identifies the cached Cholesky factor for the adjoint */
+  int64_t launches;     /* CUDA kernels this call launched */
+} tucker_stats;
+
+typedef struct tucker_handle tucker_handle;
+
+/* Create a handle bound to the current CUDA device and `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  The handle owns its
+ * device workspace (grown on demand), the observed-entry hash table and the
+ * cached Cholesky factor of the last sketched solve.
+ * Errors: EINVAL (h NULL), ENOTSUP (no sm_103 device), ECUDA. */
+tucker_status tucker_create(tucker_handle** h, void* cuda_stream);
+
+/* Release the handle and all device memory it owns (synchronises its stream). */
+tucker_status tucker_destroy(tucker_handle* h);
+
+/* One-line description of the last error on h (never NULL; "" if none). */
+const char* tucker_last_error(const tucker_handle* h);
+
+/* 1 (default): calls that launch device work synchronise and return
+ * device-detected errors.  0: calls return after enqueueing; device errors
+ * are returned by the next tucker_sync(). */
+tucker_status tucker_set_sync(tucker_handle* h, int synchronous);
+
+/* Wait for the handle's stream and return any pending device-side error. */
+tucker_status tucker_sync(tucker_handle* h);
+
+/* Statistical leverage scores of each factor (Alg. 3 line 1; Eq.
+ * ridge_leverage_score_def with lambda = 0):
+ *     l_i(A^(n)) = a_i (A^(n)T A^(n))^+ a_i^T,
+ * the pseudo-inverse through a Jacobi eigendecomposition of the R_n x R_n Gram
+ * in FP64, eigenvalues <= max(I_n,R_n) * 2^-52 * lambda_max treated as zero.
+ *   N, I[N], R[N]   host arrays: order, dims, ranks (R_n <= TUCKER_MAX_RANK)
+ *   dtype           element type of the factors
+ *   A[N]            host array of device pointers to the I_n x R_n factors
+ *   lev_out[N]      host array of device pointers, FP64 [I_n] each
+ *   cdf_out[N]      nullable; device uint64 [I_n] each: the inclusive prefix
+ *                   sums C of q_i = floor(clamp(l_i,0,1) * 2^32) used by the sampler
+ *   rank_out_host   nullable host int[N]: numerical rank of each factor
+ * Synchronises when rank_out_host is given.  Errors: EINVAL, ERANK. */
+tucker_status tucker_leverage_scores(tucker_handle* h, int N, const int64_t* I, const int* R,
+                                     tucker_dtype dtype, const void* const* A,
+                                     double* const* lev_out, uint64_t* const* cdf_out,
+                                     int* rank_out_host);
+
+/* Draw m rows of K from the product distribution of the factor leverage
+ * scores (Lemma 4.1 at lambda = 0; Alg. 3 line 3; Alg. 1 sampling loop) and
+ * deduplicate them.  Draw t uses Philox4x64-10 with key (seed, sweep) and
+ * counter (t, s, 0, 0); mode n takes word n%4 of stream s = n/4 as a 64-bit
+ * uniform u and picks i_n = min{i : C_i > floor(u Q_n / 2^64)}.  With
+ * TUCKER_REG_AUGMENTED the top bit of word 0 of stream 2 chooses a
+ * regulariser row j = floor(u' d / 2^64) (u' = word 1 of stream 2), key
+ * prod(I)+j.  With `observed` (COO), a draw whose key is not observed is
+ * rejected; draws continue in counter order until m are accepted (regulariser
+ * rows are always accepted).
+ *   lev[N]          device FP64 [I_n] leverage scores (e.g. from tucker_leverage_scores)
+ *   m               accepted draws, 1 <= m < 2^31
+ *   observed        NULL (dense) or a COO tucker_tensor whose keys define Omega
+ *   max_draws       limit on T in missing mode (0 = 64*m)
+ *   out             caller arrays of capacity >= m; n_unique/n_draws written
+ * Synchronises.  Errors: EINVAL, ERANK (sum of q is 0), EDRAWLIMIT, EHASHFULL,
+ * ECAPACITY. */
+tucker_status tucker_sample_rows(tucker_handle* h, int N, const int64_t* I, const int* R,
+                                 const double* const* lev, int64_t m, uint64_t seed,
+                                 uint32_t sweep, tucker_reg reg, const tucker_tensor* observed,
+                                 int64_t max_draws, tucker_samples* out);
+
+/* FastCoreTensorUpdate (Alg. 3 -> Alg. 1): sketched core update.
+ * Builds rows k_u = A^(1)[i_1] (x) ... (x) A^(N)[i_N] of the sampled rows on
+ * the fly (K is never formed), accumulates G = sum_u w_u k_u k_u^T and
+ * h = sum_u w_u x_u k_u with w_u = c_u / (T p_u) (Appendix B, proof of Thm 4.2:
+ * normal equations as outer products), and solves (G + lambda R) g = h by an
+ * FP64 Cholesky factorisation, R = I or the sampled regulariser diagonal.
+ *   X               dense or COO tensor (dtype F32 or F64; factors share it)
+ *   R[N]            host ranks; d = prod(R_n) <= 8192
+ *   A[N]            host array of device factor pointers
+ *   lambda          >= 0 (> 0 required for TUCKER_REG_AUGMENTED)
+ *   m               sample count; 0 = the paper's s of Alg. 1 line 3 with
+ *                   beta' = 1/2 at (eps, delta)
+ *   seed, sweep     Philox key (the sweep index keeps resumed runs identical)
+ *   fixed           NULL, or a sample from tucker_sample_rows to reuse (frozen sketch)
+ *   core_out        device FP64 [d]: vec(G) row-major
+ *   stats_host      nullable; filled (and the stream synchronised) when given
+ * Errors: EINVAL, ERANK, ENOTSPD, EDRAWLIMIT, EHASHFULL, ENOMEM, ECUDA. */
+tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                          const void* const* A, double lambda, int64_t m,
+                                          double eps, double delta, uint64_t seed, uint32_t sweep,
+                                          tucker_reg reg, tucker_prec prec,
+                                          const tucker_samples* fixed, double* core_out,
+                                          tucker_stats* stats_host);
+
+/* Exact core update, the plain method (Alg. 2, core line).
+ * Dense X: K^T K + lambda I = (x V_n)(x S_n^2 + lambda)(x V_n)^T (proof of
+ * Lemma 4.1), so g = (x V_n)[(x V_n)^T (X x_1 A^(1)T ... x_N A^(N)T)] /
+ * (x S_n^2 + lambda): one streaming pass over X for the n-mode product chain,
+ * Jacobi eigendecompositions of the R_n x R_n Grams, and small mode products.
+ * COO X: the Gram of all observed rows sum_{i in Omega} k_i k_i^T (with
+ * `prec`) and sum x_i k_i, then the FP64 Cholesky solve (+ refinement for
+ * tensor-core precisions).
+ *   core_out        device FP64 [d]
+ * Errors: EINVAL, ENOTSPD, ENOMEM, ECUDA. */
+tucker_status tucker_core_update_exact(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                       const void* const* A, double lambda, tucker_prec prec,
+                                       double* core_out);
+
+/* One pass of the repeat loop of Alg. 2: factor updates n = 1..N (each row a
+ * ridge regression with design G_(n) ((x)_{k!=n} A^(k))^T), then the core
+ * update (sketched when `sketched`, else exact).  Dense X only.
+ *   A_inout[N]      device factors (dtype of X), updated in place
+ *   core_inout      device FP64 [d], updated in place
+ *   loss_out_host   nullable: L = ||X - X-hat||^2 + lambda(||G||^2 + sum ||A^(n)||^2) (Sec. 2)
+ *   rmse_out_host   nullable: sqrt(||X - X-hat||^2 / prod(I_n))
+ * Errors: EINVAL, ENOTSPD, ENOMEM, ECUDA. */
+tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const int* R,
+                               void* const* A_inout, double* core_inout, double lambda,
+                               int sketched, int64_t m, uint64_t seed, uint32_t sweep,
+                               tucker_reg reg, tucker_prec prec, double* loss_out_host,
+                               double* rmse_out_host);
+
+/* Ridge loss of a core for the current factors (the objective of Alg. 2's
+ * core line): ||K g - vec(X)||^2 + lambda ||g||^2 over all entries (dense) or
+ * the observed entries (COO), evaluated entry by entry in FP64.
+ *   g               device FP64 [d]
+ *   loss_out_host   host double
+ * Synchronises.  Errors: EINVAL, ECUDA. */
+tucker_status tucker_ridge_loss(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                const void* const* A, double lambda, const double* g,
+                                double* loss_out_host);
+
+/* Adjoint (reverse-mode derivative) of the sketched solve g = M^-1 h with
+ * M = sum_u w_u k_u k_u^T + lambda R and h = sum_u w_u x_u k_u, the sample
+ * (keys, counts, p) held fixed.  For a cotangent gbar:
+ *     v = M^-1 gbar                  (reuses the cached Cholesky factor when
+ *                                     solve_id names the last sketched solve,
+ *                                     else refactorises M)
+ *     dx_u = w_u (k_u . v)
+ *     dA^(n)[i_n, r_n] += sum_{r : r_n} w_u (x_u v - (k_u.g) v - (k_u.v) g)[r]
+ *                                      * prod_{m != n} A^(m)[i_m, r_m]
+ *   X               the tensor of the forward call (x_u are gathered from it)
+ *   samples         the frozen sample of the forward call
+ *   g               device FP64 [d] forward result; gbar device FP64 [d]
+ *   dA_out[N]       device FP64 I_n x R_n each (overwritten)
+ *   dx_out          device FP64 [samples->n_unique] (0 for regulariser rows)
+ * Errors: EINVAL, ENOTSPD, ECUDA. */
+tucker_status tucker_core_solve_adjoint(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                        const void* const* A, double lambda, tucker_reg reg,
+                                        tucker_prec prec, const tucker_samples* samples,
+                                        uint64_t solve_id, const double* g, const double* gbar,
+                                        double* const* dA_out, double* dx_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TUCKER_H */

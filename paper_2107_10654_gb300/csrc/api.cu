@@ -1,0 +1,832 @@
+// C ABI entry points of libtucker (declared in include/tucker.h).
+//
+// Each entry point validates its arguments on the host, sizes one workspace
+// arena, and enqueues the kernel pipeline on the handle's stream:
+//   sketched core update (Alg. 3 -> Alg. 1):
+//     leverage (+ fixed-point CDF) -> sample keys -> sort + run-length dedupe
+//     -> gather x and weights -> Gram G and right-hand side h -> + lambda R
+//     -> FP64 Cholesky solve (-> FP64 refinement for tensor-core Grams)
+//   exact core update (Alg. 2 core line; Lemma 4.1 proof): TTM chain,
+//     factor eigendecompositions, diagonal scaling; or the Gram of all
+//     observed rows for missing data
+//   ALS sweep (Alg. 2), ridge loss, adjoint of the frozen-sketch solve.
+#include <math.h>
+#include <stdarg.h>
+
+#include <algorithm>
+#include <new>
+
+#include "common.cuh"
+
+namespace tk {
+
+// ------------------------------------------------ launchers from other files
+tucker_status hash_ensure(tucker_handle* h, const tucker_tensor* X, int* probes_out);
+tucker_status sample_keys(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
+                          int64_t m, uint64_t seed, uint32_t sweep, int reg,
+                          const tucker_tensor* observed, int64_t max_draws,
+                          uint64_t* keys_out, int64_t* d_T, int64_t* T_host, Arena& ar);
+tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
+                            int reg, const uint64_t* keys_u, const uint32_t* counts,
+                            const int* d_nu, const int64_t* d_T, const tucker_tensor* X,
+                            int64_t cap, uint32_t* const* idx, double* w, double* x, double* p,
+                            float* sw32, int* d_nreal, double* D, const double* p_in);
+tucker_status launch_cdf_from_lev(tucker_handle* h, int N, const int64_t* I,
+                                  const double* const* lev, uint64_t* const* cdf);
+int gram_simt_splits(tucker_handle* h, int d, int64_t cap);
+size_t gram_simt_partial_bytes(int d, int nsplit, int is64);
+tucker_status launch_gram_simt(tucker_handle* h, const RowSet& s, int use64, int nsplit,
+                               void* partial, double* G);
+int axpy_splits(tucker_handle* h, int d, int64_t cap);
+tucker_status launch_kron_axpy(tucker_handle* h, const RowSet& s, const double* a,
+                               const double* b, double coef, int nsplit, double* partial,
+                               const double* base, const double* diag, const double* y,
+                               double* out);
+tucker_status launch_kron_dot(tucker_handle* h, const RowSet& s, const double* g1,
+                              const double* g2, double* z1, double* z2);
+tucker_status cholesky(tucker_handle* h, double* M, int d);
+tucker_status chol_solve(tucker_handle* h, const double* L, int d, const double* rhs, double* g);
+tucker_status launch_regdiag(tucker_handle* h, double* out, int d, double lambda, const double* D);
+tucker_status launch_refine_update(tucker_handle* h, double* g, const double* r, int d,
+                                   double* out2);
+tucker_status launch_add_diag(tucker_handle* h, double* M, int d, const double* diag);
+tucker_status ttm_chain_all(tucker_handle* h, const FactorSet& F, const void* X, double* buf0,
+                            double* buf1, double* y);
+tucker_status ttm_chain_except(tucker_handle* h, const FactorSet& F, const void* X, int n,
+                               double* buf0, double* buf1, double* out);
+tucker_status kron_eig_core(tucker_handle* h, const FactorSet& F, double* const* V,
+                            double* const* s, const double* y, double lambda, double* g);
+tucker_status residual_sq(tucker_handle* h, const FactorSet& F, const tucker_tensor* X,
+                          const double* g, double* buf0, double* buf1, double* partial,
+                          int npartial, double* out);
+tucker_status sumsq(tucker_handle* h, const void* v, int is64, int64_t n, double* partial,
+                    int npartial, double* out);
+tucker_status factor_solve(tucker_handle* h, const FactorSet& F, int n, double* const* gram,
+                           const double* core, const double* B, double lambda, void* A_out);
+tucker_status launch_adjoint_rows(tucker_handle* h, const FactorSet& F, uint32_t* const* idx,
+                                  const double* w, const double* x, const double* zg,
+                                  const double* zv, const double* g, const double* v,
+                                  const int* n_rows, int64_t cap, double* const* dA, double* dx);
+tucker_status launch_decode_rows(tucker_handle* h, const FactorSet& F, const uint64_t* keys,
+                                 int64_t n, uint32_t* const* idx, const void* vals, double* x);
+int gram_tc_supported(int prec, int d);
+size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int64_t cap);
+tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_t cap, char* ws,
+                             size_t ws_bytes, double* G);
+
+// ----------------------------------------------------------------- plumbing
+
+tucker_status fail(tucker_handle* h, tucker_status s, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+  }
+  return s;
+}
+
+tucker_status ws_reserve(tucker_handle* h, size_t bytes) {
+  if (bytes <= h->ws_cap) return TUCKER_OK;
+  TK_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->ws) cudaFree(h->ws);
+  h->ws = nullptr;
+  h->ws_cap = 0;
+  size_t want = bytes + bytes / 4 + (1 << 20);
+  void* p = nullptr;
+  if (cudaMalloc(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, TUCKER_ENOMEM, "workspace of %zu bytes", bytes);
+    }
+    want = bytes;
+  }
+  h->ws = static_cast<char*>(p);
+  h->ws_cap = want;
+  return TUCKER_OK;
+}
+
+static const char* dev_msg(int code) {
+  switch (code) {
+    case DEV_NOTSPD: return "Cholesky met a non-positive pivot (matrix not SPD)";
+    case DEV_RANK: return "a factor has zero total leverage";
+    case DEV_DRAWLIMIT: return "draw limit reached before m accepted";
+    case DEV_HASHFULL: return "observed-entry hash table probe limit exceeded";
+    default: return "device-side consistency check failed";
+  }
+}
+
+tucker_status device_status(tucker_handle* h) {
+  TK_CUDA(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                             h->stream));
+  TK_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int code = *h->h_status;
+  if (!code) return TUCKER_OK;
+  TK_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+  TK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return fail(h, (tucker_status)code, "%s", dev_msg(code));
+}
+
+tucker_status finish(tucker_handle* h) {
+  if (!h->sync_mode) return TUCKER_OK;
+  return device_status(h);
+}
+
+static tucker_status make_factors(tucker_handle* h, int N, const int64_t* I, const int* R,
+                                  tucker_dtype dt, const void* const* A, FactorSet* F) {
+  if (N < 1 || N > TUCKER_MAX_ORDER) return fail(h, TUCKER_EINVAL, "order %d out of range", N);
+  if (!I || !R) return fail(h, TUCKER_EINVAL, "null dims or ranks");
+  if (dt != TUCKER_F32 && dt != TUCKER_F64) return fail(h, TUCKER_EINVAL, "bad dtype");
+  memset(F, 0, sizeof(*F));
+  F->N = N;
+  F->is64 = dt == TUCKER_F64;
+  int64_t d = 1;
+  double tot = 1.0;
+  uint64_t total = 1;
+  for (int n = 0; n < N; ++n) {
+    if (I[n] < 1 || I[n] > (int64_t(1) << 31)) return fail(h, TUCKER_EINVAL, "I_%d out of range", n);
+    if (R[n] < 1 || R[n] > TUCKER_MAX_RANK) return fail(h, TUCKER_EINVAL, "R_%d out of range", n);
+    F->I[n] = I[n];
+    F->R[n] = R[n];
+    F->A[n] = A ? A[n] : nullptr;
+    if (A && !A[n]) return fail(h, TUCKER_EINVAL, "factor %d is NULL", n);
+    d *= R[n];
+    tot *= double(I[n]);
+    total *= (uint64_t)I[n];
+  }
+  if (d > 8192) return fail(h, TUCKER_EINVAL, "prod(R_n) = %lld exceeds 8192", (long long)d);
+  if (tot >= 4.0e18) return fail(h, TUCKER_EINVAL, "prod(I_n) too large");
+  F->d = (int)d;
+  F->total = total;
+  return TUCKER_OK;
+}
+
+static tucker_status check_tensor(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                  const void* const* A, FactorSet* F) {
+  if (!X) return fail(h, TUCKER_EINVAL, "X is NULL");
+  TK_TRY(make_factors(h, X->order, X->dims, R, X->dtype, A, F));
+  const bool dense = X->dense != nullptr;
+  const bool coo = X->keys != nullptr && X->vals != nullptr;
+  if (dense == coo) return fail(h, TUCKER_EINVAL, "X must be dense or COO (exactly one)");
+  if (coo && X->nnz < 1) return fail(h, TUCKER_EINVAL, "COO tensor with nnz < 1");
+  if (coo && (uint64_t)X->nnz > F->total) return fail(h, TUCKER_EINVAL, "nnz > prod(I)");
+  return TUCKER_OK;
+}
+
+static int bits_for(uint64_t v) {   // bits needed to hold values < v
+  int b = 1;
+  while (b < 64 && (v - 1) >> b) ++b;
+  return b;
+}
+
+static void ev_record(tucker_handle* h, bool on, int i) {
+  if (on) cudaEventRecord(h->ev[i], h->stream);
+}
+
+static double ev_ms(tucker_handle* h, int a, int b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev[a], h->ev[b]);
+  return ms;
+}
+
+// --------------------------------------------------------- sketch pipeline
+
+struct SketchBufs {
+  double* lev[TUCKER_MAX_ORDER];
+  uint64_t* cdf[TUCKER_MAX_ORDER];
+  int* rank;
+  uint64_t* keys_raw;
+  int64_t* d_T;
+  char* sort_scratch;
+  size_t sort_bytes;
+  uint64_t* keys_u;
+  uint32_t* counts;
+  int* nu;
+  int* nreal;
+  uint32_t* idx[TUCKER_MAX_ORDER];
+  double *w, *x, *p, *z;
+  float* sw32;
+  double *D, *regdiag, *h, *g, *r, *axpy_part;
+  char* gram_ws;
+  size_t gram_bytes;
+  int axpy_split;
+  int simt_split;
+};
+
+static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_t m,
+                         int prec, int fixed, SketchBufs* b) {
+  for (int n = 0; n < F.N; ++n) {
+    b->lev[n] = ar.get<double>(F.I[n]);
+    b->cdf[n] = ar.get<uint64_t>(F.I[n]);
+  }
+  b->rank = ar.get<int>(F.N);
+  b->keys_raw = fixed ? nullptr : ar.get<uint64_t>(m);
+  b->d_T = ar.get<int64_t>(1);
+  b->sort_bytes = fixed ? 0 : sort_dedupe_scratch(m);
+  b->sort_scratch = fixed ? nullptr : ar.get<char>(b->sort_bytes);
+  b->keys_u = fixed ? nullptr : ar.get<uint64_t>(m);
+  b->counts = fixed ? nullptr : ar.get<uint32_t>(m);
+  b->nu = ar.get<int>(1);
+  b->nreal = ar.get<int>(1);
+  for (int n = 0; n < F.N; ++n) b->idx[n] = ar.get<uint32_t>(m);
+  b->w = ar.get<double>(m);
+  b->x = ar.get<double>(m);
+  b->p = ar.get<double>(m);
+  b->z = ar.get<double>(m);
+  b->sw32 = ar.get<float>(m);
+  b->D = ar.get<double>(F.d);
+  b->regdiag = ar.get<double>(F.d);
+  b->h = ar.get<double>(F.d);
+  b->g = ar.get<double>(F.d);
+  b->r = ar.get<double>(F.d);
+  b->axpy_split = axpy_splits(h, F.d, m);
+  b->axpy_part = ar.get<double>((size_t)b->axpy_split * F.d);
+  b->simt_split = gram_simt_splits(h, F.d, m);
+  if (prec == TUCKER_PREC_TF32 || prec == TUCKER_PREC_BF16)
+    b->gram_bytes = gram_tc_workspace(h, prec, F.d, m);
+  else
+    b->gram_bytes = gram_simt_partial_bytes(F.d, b->simt_split, prec == TUCKER_PREC_FP64);
+  b->gram_ws = ar.get<char>(b->gram_bytes);
+}
+
+static tucker_status chol_reserve(tucker_handle* h, int d) {
+  CholCache& c = h->chol;
+  const size_t need = (size_t)d * d;
+  if (c.cap < need) {
+    TK_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (c.L) cudaFree(c.L);
+    c.L = nullptr;
+    c.cap = 0;
+    void* p = nullptr;
+    if (cudaMalloc(&p, (need + d) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, TUCKER_ENOMEM, "Cholesky buffer for d = %d", d);
+    }
+    c.L = static_cast<double*>(p);
+    c.regdiag = c.L + need;
+    c.cap = need;
+  }
+  c.d = d;
+  c.id = 0;
+  return TUCKER_OK;
+}
+
+// G (into L buffer) from the sample, by precision.
+static tucker_status build_gram(tucker_handle* h, const FactorSet& F, const RowSet& rs, int prec,
+                                int64_t cap, SketchBufs& b, double* G) {
+  if (prec == TUCKER_PREC_FP64 || prec == TUCKER_PREC_FP32)
+    return launch_gram_simt(h, rs, prec == TUCKER_PREC_FP64, b.simt_split, b.gram_ws, G);
+  if (!gram_tc_supported(prec, F.d))
+    return fail(h, TUCKER_ENOTSUP, "tensor-core Gram does not support d = %d", F.d);
+  return launch_gram_tc(h, rs, prec, cap, b.gram_ws, b.gram_bytes, G);
+}
+
+// Solve (G + diag(regdiag)) g = h with L cached; refinement for tensor-core G.
+static tucker_status solve_refine(tucker_handle* h, const FactorSet& F, const RowSet& rs,
+                                  int prec, SketchBufs& b, int* iters, double* rel) {
+  const int d = F.d;
+  double* L = h->chol.L;
+  TK_TRY(launch_add_diag(h, L, d, b.regdiag));
+  TK_TRY(cholesky(h, L, d));
+  TK_TRY(chol_solve(h, L, d, b.h, b.g));
+  *iters = 0;
+  *rel = 0.0;
+  if (prec == TUCKER_PREC_FP64) return TUCKER_OK;
+  // g <- g + M~^-1 (h - (sum w k k^T + R) g), residual in FP64 on the implicit rows
+  const int max_iters = 8;
+  for (int it = 0; it < max_iters; ++it) {
+    TK_TRY(launch_kron_dot(h, rs, b.g, nullptr, b.z, nullptr));
+    TK_TRY(launch_kron_axpy(h, rs, b.w, b.z, -1.0, b.axpy_split, b.axpy_part, b.h, b.regdiag,
+                            b.g, b.r));
+    TK_TRY(chol_solve(h, L, d, b.r, b.r));
+    // g += correction; ||correction|| / ||g|| decides convergence
+    double hv[2] = {0, 0};
+    TK_TRY(launch_refine_update(h, b.g, b.r, d, b.z));
+    TK_CUDA(h, cudaMemcpyAsync(hv, b.z, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    TK_CUDA(h, cudaStreamSynchronize(h->stream));
+    *iters = it + 1;
+    *rel = hv[1] > 0 ? sqrt(hv[0] / hv[1]) : 0.0;
+    if (*rel < 1e-13) break;
+  }
+  return TUCKER_OK;
+}
+
+}  // namespace tk
+
+using namespace tk;
+
+// ========================================================== C entry points
+
+extern "C" {
+
+tucker_status tucker_create(tucker_handle** out, void* cuda_stream) {
+  if (!out) return TUCKER_EINVAL;
+  *out = nullptr;
+  tucker_handle* h = new (std::nothrow) tucker_handle();
+  if (!h) return TUCKER_ENOMEM;
+  h->err[0] = 0;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return TUCKER_ECUDA;
+  }
+  if (prop.major * 10 + prop.minor != 103) {
+    delete h;
+    return TUCKER_ENOTSUP;
+  }
+  h->num_sms = prop.multiProcessorCount;
+  if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&h->h_status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return TUCKER_ECUDA;
+  }
+  for (int i = 0; i < 16; ++i) cudaEventCreate(&h->ev[i]);
+  *out = h;
+  return TUCKER_OK;
+}
+
+tucker_status tucker_destroy(tucker_handle* h) {
+  if (!h) return TUCKER_EINVAL;
+  cudaStreamSynchronize(h->stream);
+  if (h->ws) cudaFree(h->ws);
+  if (h->hash.slot_key) cudaFree(h->hash.slot_key);
+  if (h->chol.L) cudaFree(h->chol.L);
+  if (h->d_status) cudaFree(h->d_status);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  for (int i = 0; i < 16; ++i) cudaEventDestroy(h->ev[i]);
+  delete h;
+  return TUCKER_OK;
+}
+
+const char* tucker_last_error(const tucker_handle* h) { return h ? h->err : "null handle"; }
+
+tucker_status tucker_set_sync(tucker_handle* h, int synchronous) {
+  if (!h) return TUCKER_EINVAL;
+  h->sync_mode = synchronous != 0;
+  return TUCKER_OK;
+}
+
+tucker_status tucker_sync(tucker_handle* h) {
+  if (!h) return TUCKER_EINVAL;
+  return device_status(h);
+}
+
+tucker_status tucker_leverage_scores(tucker_handle* h, int N, const int64_t* I, const int* R,
+                                     tucker_dtype dtype, const void* const* A,
+                                     double* const* lev_out, uint64_t* const* cdf_out,
+                                     int* rank_out_host) {
+  if (!h) return TUCKER_EINVAL;
+  if (!A || !lev_out) return fail(h, TUCKER_EINVAL, "null factor or output array");
+  FactorSet F;
+  TK_TRY(make_factors(h, N, I, R, dtype, A, &F));
+  for (int n = 0; n < N; ++n)
+    if (!lev_out[n]) return fail(h, TUCKER_EINVAL, "lev_out[%d] is NULL", n);
+  Arena sz(nullptr);
+  uint64_t* cdf_ws[TUCKER_MAX_ORDER];
+  for (int n = 0; n < N; ++n) cdf_ws[n] = sz.get<uint64_t>(F.I[n]);
+  int* rk = sz.get<int>(N);
+  TK_TRY(ws_reserve(h, sz.off));
+  Arena ar(h->ws);
+  for (int n = 0; n < N; ++n) {
+    uint64_t* c = ar.get<uint64_t>(F.I[n]);
+    cdf_ws[n] = (cdf_out && cdf_out[n]) ? cdf_out[n] : c;
+  }
+  rk = ar.get<int>(N);
+  TK_TRY(launch_leverage(h, F, lev_out, cdf_ws, rk, nullptr, nullptr, nullptr));
+  if (rank_out_host) {
+    TK_CUDA(h, cudaMemcpyAsync(rank_out_host, rk, sizeof(int) * N, cudaMemcpyDeviceToHost, h->stream));
+    return device_status(h);
+  }
+  return finish(h);
+}
+
+tucker_status tucker_sample_rows(tucker_handle* h, int N, const int64_t* I, const int* R,
+                                 const double* const* lev, int64_t m, uint64_t seed,
+                                 uint32_t sweep, tucker_reg reg, const tucker_tensor* observed,
+                                 int64_t max_draws, tucker_samples* out) {
+  if (!h) return TUCKER_EINVAL;
+  if (!lev || !out || !out->keys || !out->counts || !out->prob)
+    return fail(h, TUCKER_EINVAL, "null scores or output arrays");
+  if (m < 1 || m >= (int64_t(1) << 31)) return fail(h, TUCKER_EINVAL, "m out of range");
+  if (out->capacity < m) return fail(h, TUCKER_ECAPACITY, "capacity %lld < m %lld",
+                                     (long long)out->capacity, (long long)m);
+  if (reg != TUCKER_REG_EXACT && reg != TUCKER_REG_AUGMENTED)
+    return fail(h, TUCKER_EINVAL, "bad reg mode");
+  FactorSet F;
+  TK_TRY(make_factors(h, N, I, R, TUCKER_F64, nullptr, &F));
+  if (observed) {
+    if (!observed->keys || !observed->vals || observed->dense || observed->order != N)
+      return fail(h, TUCKER_EINVAL, "observed must be a COO tensor of the same order");
+    for (int n = 0; n < N; ++n)
+      if (observed->dims[n] != I[n]) return fail(h, TUCKER_EINVAL, "observed dims differ");
+  }
+  for (int n = 0; n < N; ++n) if (!lev[n]) return fail(h, TUCKER_EINVAL, "lev[%d] NULL", n);
+  auto carve = [&](Arena& ar, uint64_t** cdf, uint64_t** raw, int64_t** dT, char** ss, int** nu,
+                   int** nreal, uint32_t** idx, double** w, double** x, double** D) {
+    for (int n = 0; n < N; ++n) cdf[n] = ar.get<uint64_t>(F.I[n]);
+    *raw = ar.get<uint64_t>(m);
+    *dT = ar.get<int64_t>(1);
+    *ss = ar.get<char>(sort_dedupe_scratch(m));
+    *nu = ar.get<int>(1);
+    *nreal = ar.get<int>(1);
+    for (int n = 0; n < N; ++n) idx[n] = ar.get<uint32_t>(m);
+    *w = ar.get<double>(m);
+    *x = ar.get<double>(m);
+    *D = ar.get<double>(F.d);
+  };
+  uint64_t* cdf[TUCKER_MAX_ORDER];
+  uint64_t* raw;
+  int64_t* dT;
+  char* ss;
+  int *nu, *nreal;
+  uint32_t* idx[TUCKER_MAX_ORDER];
+  double *w, *x, *D;
+  Arena sz(nullptr);
+  carve(sz, cdf, &raw, &dT, &ss, &nu, &nreal, idx, &w, &x, &D);
+  // the missing-mode sampler carves its round buffers after these
+  size_t extra = observed ? (size_t)((1 << 26) * 9 + (8 << 20)) : 0;
+  TK_TRY(ws_reserve(h, sz.off + extra));
+  Arena ar(h->ws);
+  carve(ar, cdf, &raw, &dT, &ss, &nu, &nreal, idx, &w, &x, &D);
+  TK_TRY(launch_cdf_from_lev(h, N, I, lev, cdf));
+  TK_TRY(device_status(h));
+  int64_t T = 0;
+  TK_TRY(sample_keys(h, F, cdf, m, seed, sweep, reg, observed, max_draws, raw, dT, &T, ar));
+  const uint64_t key_range = F.total + (reg == TUCKER_REG_AUGMENTED ? (uint64_t)F.d : 0);
+  TK_TRY(sort_dedupe(h, raw, m, bits_for(key_range), out->keys, out->counts, nu, ss,
+                     sort_dedupe_scratch(m)));
+  tucker_tensor none;
+  memset(&none, 0, sizeof(none));
+  none.order = N;
+  none.dtype = TUCKER_F64;
+  TK_TRY(launch_gather(h, F, cdf, reg, out->keys, out->counts, nu, dT, &none, m, idx, w, x,
+                       out->prob, nullptr, nreal, D, nullptr));
+  int nuh = 0;
+  TK_CUDA(h, cudaMemcpyAsync(&nuh, nu, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  TK_TRY(device_status(h));
+  out->n_unique = nuh;
+  out->n_draws = T;
+  return TUCKER_OK;
+}
+
+static int64_t paper_s(int d, double eps, double delta) {
+  double s = 4.0 * d / 0.5 * fmax(420.0 * log(4.0 * d / delta), 1.0 / (delta * eps));
+  return (int64_t)ceil(s);
+}
+
+tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                          const void* const* A, double lambda, int64_t m,
+                                          double eps, double delta, uint64_t seed, uint32_t sweep,
+                                          tucker_reg reg, tucker_prec prec,
+                                          const tucker_samples* fixed, double* core_out,
+                                          tucker_stats* stats) {
+  if (!h) return TUCKER_EINVAL;
+  FactorSet F;
+  TK_TRY(check_tensor(h, X, R, A, &F));
+  if (!A) return fail(h, TUCKER_EINVAL, "factors NULL");
+  if (!core_out) return fail(h, TUCKER_EINVAL, "core_out NULL");
+  if (!(lambda >= 0.0) || (reg == TUCKER_REG_AUGMENTED && !(lambda > 0.0)))
+    return fail(h, TUCKER_EINVAL, "lambda must be >= 0 (> 0 in augmented mode)");
+  if (reg != TUCKER_REG_EXACT && reg != TUCKER_REG_AUGMENTED) return fail(h, TUCKER_EINVAL, "reg");
+  if (prec < TUCKER_PREC_FP64 || prec > TUCKER_PREC_BF16) return fail(h, TUCKER_EINVAL, "prec");
+  int64_t cap;
+  if (fixed) {
+    if (!fixed->keys || !fixed->counts || !fixed->prob || fixed->n_unique < 1 ||
+        fixed->n_unique > fixed->capacity || fixed->n_draws < 1)
+      return fail(h, TUCKER_EINVAL, "fixed sample is incomplete");
+    cap = fixed->n_unique;
+  } else {
+    if (m == 0) {
+      if (!(eps > 0 && eps < 1 && delta > 0 && delta < 1))
+        return fail(h, TUCKER_EINVAL, "eps, delta must be in (0,1) when m = 0");
+      m = paper_s(F.d, eps, delta);
+    }
+    if (m < 1 || m >= (int64_t(1) << 31)) return fail(h, TUCKER_EINVAL, "m out of range");
+    cap = m;
+  }
+  if (reg == TUCKER_REG_AUGMENTED && F.total + (uint64_t)F.d < F.total)
+    return fail(h, TUCKER_EINVAL, "key range overflow");
+  const bool timing = stats != nullptr;
+  const int64_t launches0 = h->launches;
+  SketchBufs b;
+  memset(&b, 0, sizeof(b));
+  Arena sz(nullptr);
+  carve_sketch(sz, h, F, cap, prec, fixed != nullptr, &b);
+  size_t extra = (!fixed && !X->dense) ? (size_t)((1 << 26) * 9 + (8 << 20)) : 0;
+  TK_TRY(ws_reserve(h, sz.off + extra));
+  TK_TRY(chol_reserve(h, F.d));
+  Arena ar(h->ws);
+  carve_sketch(ar, h, F, cap, prec, fixed != nullptr, &b);
+  ev_record(h, timing, 0);
+  int64_t T = 0;
+  const uint64_t* keys_u;
+  const uint32_t* counts;
+  const double* p_in = nullptr;
+  if (!fixed) {
+    TK_TRY(launch_leverage(h, F, b.lev, b.cdf, b.rank, nullptr, nullptr, nullptr));
+    ev_record(h, timing, 1);
+    TK_TRY(sample_keys(h, F, b.cdf, m, seed, sweep, reg, X->dense ? nullptr : X, 0, b.keys_raw,
+                       b.d_T, &T, ar));
+    ev_record(h, timing, 2);
+    const uint64_t key_range = F.total + (reg == TUCKER_REG_AUGMENTED ? (uint64_t)F.d : 0);
+    TK_TRY(sort_dedupe(h, b.keys_raw, m, bits_for(key_range), b.keys_u, b.counts, b.nu,
+                       b.sort_scratch, b.sort_bytes));
+    keys_u = b.keys_u;
+    counts = b.counts;
+  } else {
+    ev_record(h, timing, 1);
+    ev_record(h, timing, 2);
+    int nuh = (int)fixed->n_unique;
+    T = fixed->n_draws;
+    TK_CUDA(h, cudaMemcpyAsync(b.nu, &nuh, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    TK_CUDA(h, cudaMemcpyAsync(b.d_T, &fixed->n_draws, sizeof(int64_t), cudaMemcpyHostToDevice,
+                               h->stream));
+    keys_u = fixed->keys;
+    counts = fixed->counts;
+    p_in = fixed->prob;
+    if (!X->dense) { int pr; TK_TRY(hash_ensure(h, X, &pr)); }
+    TK_CUDA(h, cudaStreamSynchronize(h->stream));   // host values above are stack-held
+  }
+  ev_record(h, timing, 3);
+  TK_TRY(launch_gather(h, F, b.cdf, reg, keys_u, counts, b.nu, b.d_T, X, cap, b.idx, b.w, b.x,
+                       b.p, b.sw32, b.nreal, b.D, p_in));
+  ev_record(h, timing, 4);
+  RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
+  double* G = h->chol.L;
+  TK_TRY(build_gram(h, F, rs, prec, cap, b, G));
+  TK_TRY(launch_kron_axpy(h, rs, b.w, b.x, 1.0, b.axpy_split, b.axpy_part, nullptr, nullptr,
+                          nullptr, b.h));
+  TK_TRY(launch_regdiag(h, b.regdiag, F.d, lambda, reg == TUCKER_REG_AUGMENTED ? b.D : nullptr));
+  TK_CUDA(h, cudaMemcpyAsync(h->chol.regdiag, b.regdiag, sizeof(double) * F.d,
+                             cudaMemcpyDeviceToDevice, h->stream));
+  ev_record(h, timing, 5);
+  int iters = 0;
+  double rel = 0.0;
+  TK_TRY(solve_refine(h, F, rs, prec, b, &iters, &rel));
+  TK_CUDA(h, cudaMemcpyAsync(core_out, b.g, sizeof(double) * F.d, cudaMemcpyDeviceToDevice,
+                             h->stream));
+  ev_record(h, timing, 6);
+  h->chol.id = h->next_solve_id++;
+  if (timing) {
+    tucker_status st = device_status(h);
+    memset(stats, 0, sizeof(*stats));
+    stats->ms_leverage = ev_ms(h, 0, 1);
+    stats->ms_sample = ev_ms(h, 1, 2);
+    stats->ms_dedupe = ev_ms(h, 2, 3);
+    stats->ms_gather = ev_ms(h, 3, 4);
+    stats->ms_gram = ev_ms(h, 4, 5);
+    stats->ms_solve = ev_ms(h, 5, 6);
+    stats->ms_total = ev_ms(h, 0, 6);
+    int nuh = 0, nrh = 0;
+    cudaMemcpy(&nuh, b.nu, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&nrh, b.nreal, sizeof(int), cudaMemcpyDeviceToHost);
+    stats->n_unique = nuh;
+    stats->n_real = nrh;
+    stats->n_draws = T;
+    stats->refine_iters = iters;
+    stats->refine_rel = rel;
+    stats->solve_id = h->chol.id;
+    stats->launches = h->launches - launches0;
+    if (st != TUCKER_OK) h->chol.id = 0;
+    return st;
+  }
+  tucker_status st = finish(h);
+  if (st != TUCKER_OK) h->chol.id = 0;
+  return st;
+}
+
+tucker_status tucker_core_update_exact(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                       const void* const* A, double lambda, tucker_prec prec,
+                                       double* core_out) {
+  if (!h) return TUCKER_EINVAL;
+  FactorSet F;
+  TK_TRY(check_tensor(h, X, R, A, &F));
+  if (!A || !core_out) return fail(h, TUCKER_EINVAL, "null factors or core_out");
+  if (!(lambda >= 0.0)) return fail(h, TUCKER_EINVAL, "lambda must be >= 0");
+  if (X->dense) {
+    const int N = F.N;
+    const int64_t inter = (int64_t)(F.total / (uint64_t)F.I[N - 1]) * F.R[N - 1];
+    auto carve = [&](Arena& ar, double** lev, uint64_t** cdf, double** V, double** s, int** rk,
+                     double** b0, double** b1, double** y) {
+      for (int n = 0; n < N; ++n) {
+        lev[n] = ar.get<double>(F.I[n]);
+        cdf[n] = ar.get<uint64_t>(F.I[n]);
+        V[n] = ar.get<double>(F.R[n] * F.R[n]);
+        s[n] = ar.get<double>(F.R[n]);
+      }
+      *rk = ar.get<int>(N);
+      *b0 = ar.get<double>(inter);
+      *b1 = ar.get<double>(inter);
+      *y = ar.get<double>(F.d);
+    };
+    double *lev[TUCKER_MAX_ORDER], *V[TUCKER_MAX_ORDER], *s[TUCKER_MAX_ORDER];
+    uint64_t* cdf[TUCKER_MAX_ORDER];
+    int* rk;
+    double *b0, *b1, *y;
+    Arena sz(nullptr);
+    carve(sz, lev, cdf, V, s, &rk, &b0, &b1, &y);
+    TK_TRY(ws_reserve(h, sz.off));
+    Arena ar(h->ws);
+    carve(ar, lev, cdf, V, s, &rk, &b0, &b1, &y);
+    TK_TRY(launch_leverage(h, F, lev, cdf, rk, V, s, nullptr));
+    TK_TRY(ttm_chain_all(h, F, X->dense, b0, b1, y));
+    TK_TRY(kron_eig_core(h, F, V, s, y, lambda, core_out));
+    return finish(h);
+  }
+  // missing entries: Gram of all observed rows, FP64 Cholesky (+ refinement)
+  const int64_t nnz = X->nnz;
+  if (nnz >= (int64_t(1) << 31)) return fail(h, TUCKER_EINVAL, "nnz must be < 2^31");
+  SketchBufs b;
+  memset(&b, 0, sizeof(b));
+  Arena sz(nullptr);
+  carve_sketch(sz, h, F, nnz, prec, 1, &b);
+  TK_TRY(ws_reserve(h, sz.off));
+  TK_TRY(chol_reserve(h, F.d));
+  Arena ar(h->ws);
+  carve_sketch(ar, h, F, nnz, prec, 1, &b);
+  int nn = (int)nnz;
+  TK_CUDA(h, cudaMemcpyAsync(b.nreal, &nn, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  TK_TRY(launch_decode_rows(h, F, X->keys, nnz, b.idx, X->vals, b.x));
+  TK_CUDA(h, cudaStreamSynchronize(h->stream));
+  RowSet rs = make_rowset(F, b.idx, nullptr, b.nreal);
+  // unit weights: w = 1 for every observed row
+  TK_TRY(launch_regdiag(h, b.w, (int)std::min<int64_t>(nnz, 1 << 30), 1.0, nullptr));
+  rs.w = b.w;
+  double* G = h->chol.L;
+  TK_TRY(build_gram(h, F, rs, prec, nnz, b, G));
+  TK_TRY(launch_kron_axpy(h, rs, b.w, b.x, 1.0, b.axpy_split, b.axpy_part, nullptr, nullptr,
+                          nullptr, b.h));
+  TK_TRY(launch_regdiag(h, b.regdiag, F.d, lambda, nullptr));
+  int iters;
+  double rel;
+  TK_TRY(solve_refine(h, F, rs, prec, b, &iters, &rel));
+  TK_CUDA(h, cudaMemcpyAsync(core_out, b.g, sizeof(double) * F.d, cudaMemcpyDeviceToDevice,
+                             h->stream));
+  return finish(h);
+}
+
+tucker_status tucker_ridge_loss(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                const void* const* A, double lambda, const double* g,
+                                double* loss_out_host) {
+  if (!h) return TUCKER_EINVAL;
+  FactorSet F;
+  TK_TRY(check_tensor(h, X, R, A, &F));
+  if (!A || !g || !loss_out_host) return fail(h, TUCKER_EINVAL, "null argument");
+  const int N = F.N;
+  const int64_t rows = (int64_t)(F.total / (uint64_t)F.I[N - 1]) * F.R[N - 1];
+  const int np = h->num_sms * 8;
+  Arena sz(nullptr);
+  sz.get<double>(rows); sz.get<double>(rows); sz.get<double>(np); sz.get<double>(4);
+  TK_TRY(ws_reserve(h, sz.off));
+  Arena ar(h->ws);
+  double* b0 = ar.get<double>(rows);
+  double* b1 = ar.get<double>(rows);
+  double* part = ar.get<double>(np);
+  double* res = ar.get<double>(4);
+  TK_TRY(residual_sq(h, F, X, g, b0, b1, part, np, res));
+  TK_TRY(sumsq(h, g, 1, F.d, part, np, res + 1));
+  double hv[2];
+  TK_CUDA(h, cudaMemcpyAsync(hv, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  TK_TRY(device_status(h));
+  *loss_out_host = hv[0] + lambda * hv[1];
+  return TUCKER_OK;
+}
+
+tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const int* R,
+                               void* const* A_inout, double* core_inout, double lambda,
+                               int sketched, int64_t m, uint64_t seed, uint32_t sweep,
+                               tucker_reg reg, tucker_prec prec, double* loss_out_host,
+                               double* rmse_out_host) {
+  if (!h) return TUCKER_EINVAL;
+  FactorSet F;
+  TK_TRY(check_tensor(h, X, R, (const void* const*)A_inout, &F));
+  if (!X->dense) return fail(h, TUCKER_EINVAL, "ALS sweep needs a dense X");
+  if (!A_inout || !core_inout) return fail(h, TUCKER_EINVAL, "null factors or core");
+  if (!(lambda >= 0.0)) return fail(h, TUCKER_EINVAL, "lambda must be >= 0");
+  if (F.N < 2) return fail(h, TUCKER_EINVAL, "ALS needs order >= 2");
+  const int N = F.N;
+  // largest intermediate of the mode-n product chains
+  int64_t inter = 0;
+  for (int n = 0; n < N; ++n) {
+    int first = (n != N - 1) ? N - 1 : N - 2;
+    int64_t e = (int64_t)(F.total / (uint64_t)F.I[first]) * F.R[first];
+    if (e > inter) inter = e;
+  }
+  const int np = h->num_sms * 8;
+  auto carve = [&](Arena& ar, double** lev, uint64_t** cdf, double** gram, int** rk, double** b0,
+                   double** b1, double** B, double** part, double** res) {
+    for (int n = 0; n < N; ++n) {
+      lev[n] = ar.get<double>(F.I[n]);
+      cdf[n] = ar.get<uint64_t>(F.I[n]);
+      gram[n] = ar.get<double>(F.R[n] * F.R[n]);
+    }
+    *rk = ar.get<int>(N);
+    *b0 = ar.get<double>(inter);
+    *b1 = ar.get<double>(inter);
+    *B = ar.get<double>(inter);
+    *part = ar.get<double>(np);
+    *res = ar.get<double>(2 + N);
+  };
+  double *lev[TUCKER_MAX_ORDER], *gram[TUCKER_MAX_ORDER];
+  uint64_t* cdf[TUCKER_MAX_ORDER];
+  int* rk;
+  double *b0, *b1, *B, *part, *res;
+  Arena sz(nullptr);
+  carve(sz, lev, cdf, gram, &rk, &b0, &b1, &B, &part, &res);
+  TK_TRY(ws_reserve(h, sz.off));
+  Arena ar(h->ws);
+  carve(ar, lev, cdf, gram, &rk, &b0, &b1, &B, &part, &res);
+  for (int n = 0; n < N; ++n) {
+    TK_TRY(launch_leverage(h, F, lev, cdf, rk, nullptr, nullptr, gram));
+    TK_TRY(ttm_chain_except(h, F, X->dense, n, b0, b1, B));
+    TK_TRY(factor_solve(h, F, n, gram, core_inout, B, lambda, A_inout[n]));
+  }
+  TK_TRY(device_status(h));
+  tucker_status st;
+  if (sketched)
+    st = tucker_core_update_sketched(h, X, R, (const void* const*)A_inout, lambda, m, 0.1, 0.1,
+                                     seed, sweep, reg, prec, nullptr, core_inout, nullptr);
+  else
+    st = tucker_core_update_exact(h, X, R, (const void* const*)A_inout, lambda, prec, core_inout);
+  if (st != TUCKER_OK) return st;
+  if (loss_out_host || rmse_out_host) {
+    // workspace may have been regrown by the core update: carve again
+    Arena sz2(nullptr);
+    carve(sz2, lev, cdf, gram, &rk, &b0, &b1, &B, &part, &res);
+    TK_TRY(ws_reserve(h, sz2.off));
+    Arena ar2(h->ws);
+    carve(ar2, lev, cdf, gram, &rk, &b0, &b1, &B, &part, &res);
+    TK_TRY(residual_sq(h, F, X, core_inout, b0, b1, part, np, res));
+    TK_TRY(sumsq(h, core_inout, 1, F.d, part, np, res + 1));
+    for (int n = 0; n < N; ++n)
+      TK_TRY(sumsq(h, A_inout[n], F.is64, F.I[n] * F.R[n], part, np, res + 2 + n));
+    double hv[2 + TUCKER_MAX_ORDER];
+    TK_CUDA(h, cudaMemcpyAsync(hv, res, (2 + N) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    TK_TRY(device_status(h));
+    double reg_sum = hv[1];
+    for (int n = 0; n < N; ++n) reg_sum += hv[2 + n];
+    if (loss_out_host) *loss_out_host = hv[0] + lambda * reg_sum;
+    if (rmse_out_host) *rmse_out_host = sqrt(hv[0] / (double)F.total);
+  }
+  return TUCKER_OK;
+}
+
+tucker_status tucker_core_solve_adjoint(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                        const void* const* A, double lambda, tucker_reg reg,
+                                        tucker_prec prec, const tucker_samples* samples,
+                                        uint64_t solve_id, const double* g, const double* gbar,
+                                        double* const* dA_out, double* dx_out) {
+  if (!h) return TUCKER_EINVAL;
+  FactorSet F;
+  TK_TRY(check_tensor(h, X, R, A, &F));
+  if (!A || !samples || !g || !gbar || !dA_out || !dx_out)
+    return fail(h, TUCKER_EINVAL, "null argument");
+  if (!samples->keys || !samples->counts || !samples->prob || samples->n_unique < 1 ||
+      samples->n_draws < 1)
+    return fail(h, TUCKER_EINVAL, "incomplete sample");
+  for (int n = 0; n < F.N; ++n) if (!dA_out[n]) return fail(h, TUCKER_EINVAL, "dA_out NULL");
+  const int64_t cap = samples->n_unique;
+  SketchBufs b;
+  memset(&b, 0, sizeof(b));
+  Arena sz(nullptr);
+  carve_sketch(sz, h, F, cap, prec, 1, &b);
+  double* v = sz.get<double>(F.d);
+  double* zv = sz.get<double>(cap);
+  TK_TRY(ws_reserve(h, sz.off));
+  const bool reuse = solve_id != 0 && solve_id == h->chol.id && h->chol.d == F.d;
+  if (!reuse) TK_TRY(chol_reserve(h, F.d));
+  Arena ar(h->ws);
+  carve_sketch(ar, h, F, cap, prec, 1, &b);
+  v = ar.get<double>(F.d);
+  zv = ar.get<double>(cap);
+  int nuh = (int)cap;
+  int64_t T = samples->n_draws;
+  TK_CUDA(h, cudaMemcpyAsync(b.nu, &nuh, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  TK_CUDA(h, cudaMemcpyAsync(b.d_T, &T, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+  if (!X->dense) { int pr; TK_TRY(hash_ensure(h, X, &pr)); }
+  TK_TRY(launch_gather(h, F, b.cdf, reg, samples->keys, samples->counts, b.nu, b.d_T, X, cap,
+                       b.idx, b.w, b.x, b.p, b.sw32, b.nreal, b.D, samples->prob));
+  TK_CUDA(h, cudaStreamSynchronize(h->stream));
+  RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
+  if (!reuse) {
+    TK_TRY(build_gram(h, F, rs, prec, cap, b, h->chol.L));
+    TK_TRY(launch_regdiag(h, h->chol.regdiag, F.d, lambda,
+                          reg == TUCKER_REG_AUGMENTED ? b.D : nullptr));
+    TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
+    TK_TRY(cholesky(h, h->chol.L, F.d));
+    h->chol.id = h->next_solve_id++;
+  }
+  TK_TRY(chol_solve(h, h->chol.L, F.d, gbar, v));
+  TK_TRY(launch_kron_dot(h, rs, g, v, b.z, zv));
+  TK_CUDA(h, cudaMemsetAsync(dx_out, 0, sizeof(double) * cap, h->stream));
+  TK_TRY(launch_adjoint_rows(h, F, b.idx, b.w, b.x, b.z, zv, g, v, b.nreal, cap, dA_out, dx_out));
+  return finish(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,432 @@
+// Exact core update for dense X (the plain method), n-mode product chains and
+// the FP64 residual used for losses.
+//
+// Exact core (Alg. 2 core line, solved through the eigendecomposition of the
+// proof of Lemma 4.1): with A^(n)T A^(n) = V_n diag(s_n) V_n^T,
+//     y = K^T vec X = vec(X x_1 A^(1)T ... x_N A^(N)T)       (n-mode products, Sec. 2)
+//     z = y x_n V_n^T;  z /= (s_1 (x) ... (x) s_N + lambda);  g = z x_n V_n.
+// The first product streams X once (HBM-bound: one warp per row of the last
+// mode, lanes over the row, R_N accumulators, A^(N) in shared memory); the
+// rest act on tensors with at most prod(I)/I_N * R_N entries.
+#include "common.cuh"
+
+namespace tk {
+
+// out[p][r] = sum_i X[p][i] A[i][r]   (X: P x I row-major; out FP64 P x R)
+template <class T, int RC>
+__global__ void __launch_bounds__(256) k_ttm_last(const T* X, int64_t P, int I, const T* A, int R,
+                                                  double* out) {
+  extern __shared__ unsigned char smraw[];
+  T* As = reinterpret_cast<T*>(smraw);               // I x R
+  for (int e = threadIdx.x; e < I * R; e += blockDim.x) As[e] = A[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = warp; p < P; p += nwarps) {
+    const T* row = X + p * I;
+    for (int r0 = 0; r0 < R; r0 += RC) {
+      T acc[RC];
+#pragma unroll
+      for (int j = 0; j < RC; ++j) acc[j] = T(0);
+      for (int i = lane; i < I; i += 32) {
+        const T x = row[i];
+        const T* a = As + i * R + r0;
+#pragma unroll
+        for (int j = 0; j < RC; ++j)
+          if (r0 + j < R) acc[j] = fma(x, a[j], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < RC; ++j) {
+        T v = warp_sum(acc[j]);
+        if (lane == 0 && r0 + j < R) out[p * R + r0 + j] = (double)v;
+      }
+    }
+  }
+}
+
+// out[p][r][q] = sum_i X[p][i][q] A[i][r]   (big X, middle mode; coalesced over q)
+template <class T, int RC>
+__global__ void __launch_bounds__(256) k_ttm_mid(const T* X, int64_t pre, int I, int64_t post,
+                                                 const T* A, int R, double* out) {
+  extern __shared__ unsigned char smraw[];
+  T* As = reinterpret_cast<T*>(smraw);
+  for (int e = threadIdx.x; e < I * R; e += blockDim.x) As[e] = A[e];
+  __syncthreads();
+  const int64_t total = pre * post;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = t / post, q = t % post;
+    for (int r0 = 0; r0 < R; r0 += RC) {
+      T acc[RC];
+#pragma unroll
+      for (int j = 0; j < RC; ++j) acc[j] = T(0);
+      for (int i = 0; i < I; ++i) {
+        const T x = X[(p * I + i) * post + q];
+#pragma unroll
+        for (int j = 0; j < RC; ++j)
+          if (r0 + j < R) acc[j] = fma(x, As[i * R + r0 + j], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < RC; ++j)
+        if (r0 + j < R) out[(p * R + r0 + j) * post + q] = (double)acc[j];
+    }
+  }
+}
+
+// contract: out[p][r][q] = sum_{i<I} in[p][i][q] A[i][r]   (out middle dim R)
+// expand:   out[p][i][q] = sum_{r<R} in[p][r][q] A[i][r]   (out middle dim I)
+__global__ void k_ttm_small(const double* in, int64_t pre, int64_t post, const void* A, int is64,
+                            int I, int R, int contract, double* out) {
+  const int K = contract ? I : R, M = contract ? R : I;
+  const int64_t total = pre * M * post;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t % post;
+    const int mo = (int)((t / post) % M);
+    const int64_t p = t / (post * M);
+    double acc = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const double a = contract ? load_as_double(A, (int64_t)k * R + mo, is64)
+                                : load_as_double(A, (int64_t)mo * R + k, is64);
+      acc = fma(in[(p * K + k) * post + q], a, acc);
+    }
+    out[t] = acc;
+  }
+}
+
+// g = (x V_n) [ ((x V_n)^T y) / (x s_n + lambda) ]   -- one CTA, d <= 8192
+struct EigArgs {
+  int N;
+  int R[TUCKER_MAX_ORDER];
+  const double* V[TUCKER_MAX_ORDER];   // R x R, V[a][k]
+  const double* s[TUCKER_MAX_ORDER];   // R eigenvalues
+  const double* y;
+  double lambda;
+  double* g;
+  int d;
+};
+
+__global__ void __launch_bounds__(1024) k_kron_eig_core(EigArgs a) {
+  extern __shared__ double buf[];
+  double* z0 = buf;
+  double* z1 = buf + a.d;
+  for (int i = threadIdx.x; i < a.d; i += blockDim.x) z0[i] = a.y[i];
+  __syncthreads();
+  // forward: z <- z x_n V_n^T  (z[p][k][q] = sum_a z[p][a][q] V[a][k])
+  for (int pass = 0; pass < 2; ++pass) {
+    int pre = 1;
+    for (int n = 0; n < a.N; ++n) {
+      const int R = a.R[n];
+      const int post = a.d / (pre * R);
+      for (int t = threadIdx.x; t < a.d; t += blockDim.x) {
+        const int q = t % post, k = (t / post) % R, p = t / (post * R);
+        double acc = 0.0;
+        for (int j = 0; j < R; ++j) {
+          const double v = pass == 0 ? a.V[n][j * R + k] : a.V[n][k * R + j];
+          acc = fma(z0[(p * R + j) * post + q], v, acc);
+        }
+        z1[t] = acc;
+      }
+      __syncthreads();
+      double* tmp = z0; z0 = z1; z1 = tmp;
+      pre *= R;
+    }
+    if (pass == 0) {
+      for (int t = threadIdx.x; t < a.d; t += blockDim.x) {
+        double ev = 1.0;
+        int rem = t;
+        for (int n = a.N - 1; n >= 0; --n) { ev *= a.s[n][rem % a.R[n]]; rem /= a.R[n]; }
+        z0[t] /= (ev + a.lambda);
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < a.d; i += blockDim.x) a.g[i] = z0[i];
+}
+
+// Residual sum of squares  sum_p sum_i (X[p][i] - T[p] . A^(N)[i])^2  in FP64,
+// T = G x_1 A^(1) ... x_{N-1} A^(N-1) (P x R rows).  Block partials.
+__global__ void __launch_bounds__(256) k_residual_dense(const void* X, int is64, int64_t P, int I,
+                                                        const double* T, const void* A, int R,
+                                                        double* partial) {
+  extern __shared__ double As[];             // I x R
+  __shared__ double red[8];
+  for (int e = threadIdx.x; e < I * R; e += blockDim.x) As[e] = load_as_double(A, e, is64);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double acc = 0.0;
+  for (int64_t p = warp; p < P; p += nwarps) {
+    const double* t = T + p * R;
+    for (int i = lane; i < I; i += 32) {
+      double xh = 0.0;
+      for (int r = 0; r < R; ++r) xh = fma(t[r], As[i * R + r], xh);
+      const double e = load_as_double(X, p * I + i, is64) - xh;
+      acc = fma(e, e, acc);
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_residual_coo(const uint64_t* keys, const void* vals,
+                                                      int is64, int64_t nnz, int I,
+                                                      const double* T, const void* A, int R,
+                                                      double* partial) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[e];
+    const int64_t p = (int64_t)(k / (uint64_t)I);
+    const int i = (int)(k % (uint64_t)I);
+    double xh = 0.0;
+    for (int r = 0; r < R; ++r) xh = fma(T[p * R + r], load_as_double(A, (int64_t)i * R + r, is64), xh);
+    const double d = load_as_double(vals, e, is64) - xh;
+    acc = fma(d, d, acc);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_sum_partials(const double* partial, int n, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *out = t;
+  }
+}
+
+// sum of squares of a device FP64/FP32 array (block partials + final sum)
+__global__ void k_sumsq(const void* v, int is64, int64_t n, double* partial) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = load_as_double(v, i, is64);
+    s = fma(x, x, s);
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// ------------------------------------------------------------------- host side
+
+static int grid_for(tucker_handle* h, int64_t work, int per = 256) {
+  int64_t g = (work + per - 1) / per;
+  int64_t cap = (int64_t)h->num_sms * 32;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// Contract the last mode of the dense X: out = X_(as P x I_N) A^(N)  (FP64 out)
+tucker_status ttm_last(tucker_handle* h, const void* X, int is64, int64_t P, int I, const void* A,
+                       int R, double* out) {
+  const size_t smem = (size_t)I * R * (is64 ? 8 : 4);
+  const int grid = grid_for(h, P * 32);
+  if (is64) {
+    auto k = R <= 8 ? k_ttm_last<double, 8> : k_ttm_last<double, 16>;
+    TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TK_COUNT(h);
+    k<<<grid, 256, smem, h->stream>>>((const double*)X, P, I, (const double*)A, R, out);
+  } else {
+    auto k = R <= 8 ? k_ttm_last<float, 8> : k_ttm_last<float, 16>;
+    TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TK_COUNT(h);
+    k<<<grid, 256, smem, h->stream>>>((const float*)X, P, I, (const float*)A, R, out);
+  }
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+tucker_status ttm_mid(tucker_handle* h, const void* X, int is64, int64_t pre, int I, int64_t post,
+                      const void* A, int R, double* out) {
+  const size_t smem = (size_t)I * R * (is64 ? 8 : 4);
+  const int grid = grid_for(h, pre * post);
+  if (is64) {
+    auto k = R <= 8 ? k_ttm_mid<double, 8> : k_ttm_mid<double, 16>;
+    TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TK_COUNT(h);
+    k<<<grid, 256, smem, h->stream>>>((const double*)X, pre, I, post, (const double*)A, R, out);
+  } else {
+    auto k = R <= 8 ? k_ttm_mid<float, 8> : k_ttm_mid<float, 16>;
+    TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TK_COUNT(h);
+    k<<<grid, 256, smem, h->stream>>>((const float*)X, pre, I, post, (const float*)A, R, out);
+  }
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+tucker_status ttm_small(tucker_handle* h, const double* in, int64_t pre, int64_t post,
+                        const void* A, int is64, int I, int R, int contract, double* out) {
+  const int64_t total = pre * (contract ? R : I) * post;
+  TK_COUNT(h);
+  k_ttm_small<<<grid_for(h, total), 256, 0, h->stream>>>(in, pre, post, A, is64, I, R, contract, out);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+// y = X x_1 A^(1)T ... x_N A^(N)T  (all modes), FP64 d-vector.  buf: two
+// scratch arrays of prod(I)/I_N * R_N doubles.
+tucker_status ttm_chain_all(tucker_handle* h, const FactorSet& F, const void* X, double* buf0,
+                            double* buf1, double* y) {
+  const int N = F.N;
+  int64_t P = (int64_t)(F.total / (uint64_t)F.I[N - 1]);
+  double* cur = (N == 1) ? y : buf0;
+  TK_TRY(ttm_last(h, X, F.is64, P, (int)F.I[N - 1], F.A[N - 1], F.R[N - 1], cur));
+  int64_t post = F.R[N - 1];
+  for (int n = N - 2; n >= 0; --n) {
+    int64_t pre = P / F.I[n];
+    double* nxt = (n == 0) ? y : (cur == buf0 ? buf1 : buf0);
+    TK_TRY(ttm_small(h, cur, pre, post, F.A[n], F.is64, (int)F.I[n], F.R[n], 1, nxt));
+    cur = nxt;
+    P = pre;
+    post *= F.R[n];
+  }
+  return TUCKER_OK;
+}
+
+// B = X x_{k != n} A^(k)T, laid out (prod_{k<n} R_k, I_n, prod_{k>n} R_k) in `out`.
+tucker_status ttm_chain_except(tucker_handle* h, const FactorSet& F, const void* X, int n,
+                               double* buf0, double* buf1, double* out) {
+  const int N = F.N;
+  // shape tracked as dims[] with the current extent of each mode
+  int64_t ext[TUCKER_MAX_ORDER];
+  for (int k = 0; k < N; ++k) ext[k] = F.I[k];
+  auto prod = [&](int a, int b) { int64_t p = 1; for (int k = a; k < b; ++k) p *= ext[k]; return p; };
+  const double* cur = nullptr;
+  double* bufs[2] = {buf0, buf1};
+  int which = 0;
+  int remaining = 0;
+  for (int k = 0; k < N; ++k) if (k != n) ++remaining;
+  if (remaining == 0) return fail(h, TUCKER_EINVAL, "order-1 ALS is not supported");
+  // first contraction straight from X
+  int first = (n != N - 1) ? N - 1 : N - 2;
+  double* dst = (--remaining == 0) ? out : bufs[which];
+  if (first == N - 1) {
+    TK_TRY(ttm_last(h, X, F.is64, prod(0, N - 1), (int)F.I[N - 1], F.A[N - 1], F.R[N - 1], dst));
+  } else {
+    TK_TRY(ttm_mid(h, X, F.is64, prod(0, first), (int)F.I[first], prod(first + 1, N), F.A[first],
+                   F.R[first], dst));
+  }
+  ext[first] = F.R[first];
+  cur = dst;
+  which ^= 1;
+  for (int k = first - 1; k >= 0; --k) {
+    if (k == n) continue;
+    dst = (--remaining == 0) ? out : bufs[which];
+    TK_TRY(ttm_small(h, cur, prod(0, k), prod(k + 1, N), F.A[k], F.is64, (int)F.I[k], F.R[k], 1, dst));
+    ext[k] = F.R[k];
+    cur = dst;
+    which ^= 1;
+  }
+  return TUCKER_OK;
+}
+
+tucker_status kron_eig_core(tucker_handle* h, const FactorSet& F, double* const* V,
+                            double* const* s, const double* y, double lambda, double* g) {
+  EigArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = F.N;
+  for (int n = 0; n < F.N; ++n) { a.R[n] = F.R[n]; a.V[n] = V[n]; a.s[n] = s[n]; }
+  a.y = y; a.lambda = lambda; a.g = g; a.d = F.d;
+  const size_t smem = (size_t)2 * F.d * sizeof(double);
+  TK_CUDA(h, cudaFuncSetAttribute(k_kron_eig_core, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  TK_COUNT(h);
+  k_kron_eig_core<<<1, 1024, smem, h->stream>>>(a);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+// T = G x_1 A^(1) ... x_{N-1} A^(N-1)  (P x R_N rows, P = prod_{n<N} I_n)
+tucker_status model_rows(tucker_handle* h, const FactorSet& F, const double* g, double* buf0,
+                         double* buf1, double** T_out) {
+  const int N = F.N;
+  const double* cur = g;
+  int64_t pre = 1;
+  int64_t post = 1;
+  for (int k = 1; k < N; ++k) post *= F.R[k];
+  double* bufs[2] = {buf0, buf1};
+  int which = 0;
+  for (int n = 0; n < N - 1; ++n) {
+    double* dst = bufs[which];
+    TK_TRY(ttm_small(h, cur, pre, post, F.A[n], F.is64, (int)F.I[n], F.R[n], 0, dst));
+    cur = dst;
+    which ^= 1;
+    pre *= F.I[n];
+    post /= F.R[n + 1];
+  }
+  *T_out = const_cast<double*>(cur);
+  return TUCKER_OK;
+}
+
+// ||X - X-hat(g)||^2 (dense or COO) in FP64 into *out (device).
+tucker_status residual_sq(tucker_handle* h, const FactorSet& F, const tucker_tensor* X,
+                          const double* g, double* buf0, double* buf1, double* partial,
+                          int npartial, double* out) {
+  double* T = nullptr;
+  TK_TRY(model_rows(h, F, g, buf0, buf1, &T));
+  const int N = F.N;
+  const int I = (int)F.I[N - 1], R = F.R[N - 1];
+  const int64_t P = (int64_t)(F.total / (uint64_t)I);
+  int grid = npartial;
+  if (X->dense) {
+    const size_t smem = (size_t)I * R * 8;
+    TK_CUDA(h, cudaFuncSetAttribute(k_residual_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+    TK_COUNT(h);
+    k_residual_dense<<<grid, 256, smem, h->stream>>>(X->dense, F.is64, P, I, T, F.A[N - 1], R,
+                                                    partial);
+  } else {
+    TK_COUNT(h);
+    k_residual_coo<<<grid, 256, 0, h->stream>>>(X->keys, X->vals, F.is64, X->nnz, I, T,
+                                               F.A[N - 1], R, partial);
+  }
+  TK_LAUNCH(h);
+  TK_COUNT(h);
+  k_sum_partials<<<1, 1024, 0, h->stream>>>(partial, grid, out);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+tucker_status sumsq(tucker_handle* h, const void* v, int is64, int64_t n, double* partial,
+                    int npartial, double* out) {
+  TK_COUNT(h);
+  k_sumsq<<<npartial, 256, 0, h->stream>>>(v, is64, n, partial);
+  TK_LAUNCH(h);
+  TK_COUNT(h);
+  k_sum_partials<<<1, 1024, 0, h->stream>>>(partial, npartial, out);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+}  // namespace tk
