@@ -276,6 +276,41 @@ tucker_status tucker_core_solve_adjoint(tucker_handle* h, const tucker_tensor* X
                                         uint64_t solve_id, const double* g, const double* gbar,
                                         double* const* dA_out, double* dx_out);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free sampling.  The paper has no counterpart to this entry
+ * point; it exists for callers that are not allowed to allocate device memory
+ * while they run (code working inside a memory pool it does not own, a
+ * process that has reserved or capped all GPU memory up front, a real-time
+ * loop where a cudaMalloc could block or fail).  Such callers cannot use a
+ * tucker_handle, whose workspace grows on demand.
+ *
+ * tucker_sample_rows_noalloc computes exactly what tucker_sample_rows
+ * computes for a dense tensor (same keys, counts, probabilities, n_unique and
+ * n_draws) with the same kernels, but all of its scratch lives in one
+ * statically sized device array inside libtucker: TUCKER_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) that every GPU which loads the library keeps until the process
+ * exits.  The caller still provides the inputs (scores) and the outputs (out).
+ *   cuda_stream     cudaStream_t to run on (NULL = legacy default stream);
+ *                   the current device must be an sm_103 GPU
+ *   N, I, R, lev, m, seed, sweep, reg, out: as for tucker_sample_rows; dense
+ *                   mode only (no observed-entry mask, which needs a hash table)
+ *   err_host        nullable host buffer of err_len bytes for a one-line message
+ * Limits: m is bounded by the scratch size - about 2.5e5 draws for order 3;
+ * larger m returns TUCKER_ECAPACITY with the bytes needed in err_host.
+ * The first call on each device looks up the device address of the array
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the one array, so calls whose
+ * work overlaps on the GPU (two streams, two host threads) race and corrupt
+ * each other: serialise them.  Each call clears what must start at zero.
+ * Synchronises the stream.  Calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Errors: EINVAL, ECAPACITY, ERANK, ENOTSUP, ECUDA. */
+#define TUCKER_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+tucker_status tucker_sample_rows_noalloc(void* cuda_stream, int N, const int64_t* I, const int* R,
+                                         const double* const* lev, int64_t m, uint64_t seed,
+                                         uint32_t sweep, tucker_reg reg, tucker_samples* out,
+                                         char* err_host, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

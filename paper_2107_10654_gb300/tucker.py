@@ -18,7 +18,8 @@ from . import _lib as L
 
 __all__ = ["TuckerError", "Handle", "Samples", "CooTensor", "tucker_leverage_scores",
            "tucker_sample_rows", "tucker_core_update_sketched", "tucker_core_update_exact",
-           "tucker_als_sweep", "tucker_ridge_loss", "tucker_core_solve_adjoint"]
+           "tucker_als_sweep", "tucker_ridge_loss", "tucker_core_solve_adjoint",
+           "tucker_sample_rows_noalloc"]
 
 PREC = {"fp64": L.PREC_FP64, "fp32": L.PREC_FP32, "tf32": L.PREC_TF32, "bf16": L.PREC_BF16}
 REG = {"exact": L.REG_EXACT, "augmented": L.REG_AUGMENTED}
@@ -248,3 +249,26 @@ def tucker_core_solve_adjoint(h: Handle, X, A: Sequence[torch.Tensor], lam: floa
         REG[reg], PREC[prec], C.byref(samples._c()), int(solve_id), g.data_ptr(), gbar.data_ptr(),
         L.ptr_array([t.data_ptr() for t in dA]), dx.data_ptr()))
     return dA, dx
+
+
+def tucker_sample_rows_noalloc(dims: Sequence[int], ranks: Sequence[int],
+                               lev: Sequence[torch.Tensor], m: int, seed: int, sweep: int = 0,
+                               reg: str = "exact", out: Optional[Samples] = None,
+                               stream: Optional[torch.cuda.Stream] = None) -> Samples:
+    """tucker_sample_rows without a handle and without device allocation by the
+    library: its scratch is a fixed array inside libtucker (dense tensors only).
+    `out` must be preallocated by callers that cannot allocate."""
+    lib = L.load()
+    N = len(dims)
+    I = (C.c_int64 * L.MAX_ORDER)(*[int(v) for v in dims])
+    out = out if out is not None else Samples.empty(m, lev[0].device)
+    cs = out._c()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    err = C.create_string_buffer(256)
+    st = lib.tucker_sample_rows_noalloc(C.c_void_p(s.cuda_stream), N, I, _ranks(ranks),
+                                        L.ptr_array([t.data_ptr() for t in lev]), int(m), int(seed),
+                                        int(sweep), REG[reg], C.byref(cs), err, 256)
+    if st != L.OK:
+        raise TuckerError(st, err.value.decode(errors="replace"))
+    out.n_unique, out.n_draws = int(cs.n_unique), int(cs.n_draws)
+    return out
