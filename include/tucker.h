@@ -255,6 +255,19 @@ tucker_status tucker_ridge_loss(tucker_handle* h, const tucker_tensor* X, const 
                                 const void* const* A, double lambda, const double* g,
                                 double* loss_out_host);
 
+/* Normal equations of a given sample (Appendix B, proof of Thm 4.2: the
+ * sketched A^T A and A^T b as sums of outer products over the sampled rows):
+ *     G = sum_u w_u k_u k_u^T,   h = sum_u w_u x_u k_u,   w_u = c_u / (T p_u),
+ * over the rows of K in the sample (regulariser rows are skipped), with the
+ * Gram arithmetic of `prec` (no refinement) and h in FP64.
+ *   samples         a sample from tucker_sample_rows (keys, counts, prob, T)
+ *   G_out           device FP64 d x d, row-major, both triangles written
+ *   h_out           nullable device FP64 [d]
+ * Errors: EINVAL, ENOTSUP, ECUDA. */
+tucker_status tucker_sketched_gram(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                   const void* const* A, tucker_prec prec,
+                                   const tucker_samples* samples, double* G_out, double* h_out);
+
 /* Adjoint (reverse-mode derivative) of the sketched solve g = M^-1 h with
  * M = sum_u w_u k_u k_u^T + lambda R and h = sum_u w_u x_u k_u, the sample
  * (keys, counts, p) held fixed.  For a cotangent gbar:

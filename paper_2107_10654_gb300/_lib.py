@@ -69,6 +69,8 @@ SIGNATURES = {
     "tucker_core_solve_adjoint": (C.c_int, [_P, C.POINTER(TuckerTensor), _IP, _PP, C.c_double,
                                             C.c_int, C.c_int, C.POINTER(TuckerSamples),
                                             C.c_uint64, _P, _P, _PP, _P]),
+    "tucker_sketched_gram": (C.c_int, [_P, C.POINTER(TuckerTensor), _IP, _PP, C.c_int,
+                                       C.POINTER(TuckerSamples), _P, _P]),
     "tucker_sample_rows_noalloc": (C.c_int, [_P, C.c_int, _I64P, _IP, _PP, C.c_int64, C.c_uint64,
                                              C.c_uint32, C.c_int, C.POINTER(TuckerSamples),
                                              C.c_char_p, C.c_size_t]),

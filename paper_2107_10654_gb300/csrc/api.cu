@@ -70,7 +70,7 @@ tucker_status launch_adjoint_rows(tucker_handle* h, const FactorSet& F, uint32_t
 tucker_status launch_decode_rows(tucker_handle* h, const FactorSet& F, const uint64_t* keys,
                                  int64_t n, uint32_t* const* idx, const void* vals, double* x);
 int gram_tc_supported(int prec, int d);
-size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int64_t cap);
+size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int sumR, int64_t cap);
 tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_t cap, char* ws,
                              size_t ws_bytes, double* G);
 
@@ -243,8 +243,10 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
   b->axpy_split = axpy_splits(h, F.d, m);
   b->axpy_part = ar.get<double>((size_t)b->axpy_split * F.d);
   b->simt_split = gram_simt_splits(h, F.d, m);
+  int sumR = 0;
+  for (int n = 0; n < F.N; ++n) sumR += F.R[n];
   if (prec == TUCKER_PREC_TF32 || prec == TUCKER_PREC_BF16)
-    b->gram_bytes = gram_tc_workspace(h, prec, F.d, m);
+    b->gram_bytes = gram_tc_workspace(h, prec, F.d, sumR, m);
   else
     b->gram_bytes = gram_simt_partial_bytes(F.d, b->simt_split, prec == TUCKER_PREC_FP64);
   b->gram_ws = ar.get<char>(b->gram_bytes);
@@ -775,6 +777,41 @@ tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const i
     if (rmse_out_host) *rmse_out_host = sqrt(hv[0] / (double)F.total);
   }
   return TUCKER_OK;
+}
+
+tucker_status tucker_sketched_gram(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                   const void* const* A, tucker_prec prec,
+                                   const tucker_samples* samples, double* G_out, double* h_out) {
+  if (!h) return TUCKER_EINVAL;
+  FactorSet F;
+  TK_TRY(check_tensor(h, X, R, A, &F));
+  if (!A || !samples || !G_out) return fail(h, TUCKER_EINVAL, "null argument");
+  if (!samples->keys || !samples->counts || !samples->prob || samples->n_unique < 1 ||
+      samples->n_draws < 1)
+    return fail(h, TUCKER_EINVAL, "incomplete sample");
+  if (prec < TUCKER_PREC_FP64 || prec > TUCKER_PREC_BF16) return fail(h, TUCKER_EINVAL, "prec");
+  const int64_t cap = samples->n_unique;
+  SketchBufs b;
+  memset(&b, 0, sizeof(b));
+  Arena sz(nullptr);
+  carve_sketch(sz, h, F, cap, prec, 1, &b);
+  TK_TRY(ws_reserve(h, sz.off));
+  Arena ar(h->ws);
+  carve_sketch(ar, h, F, cap, prec, 1, &b);
+  int nuh = (int)cap;
+  int64_t T = samples->n_draws;
+  TK_CUDA(h, cudaMemcpyAsync(b.nu, &nuh, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  TK_CUDA(h, cudaMemcpyAsync(b.d_T, &T, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+  if (!X->dense) { int pr; TK_TRY(hash_ensure(h, X, &pr)); }
+  TK_TRY(launch_gather(h, F, b.cdf, TUCKER_REG_EXACT, samples->keys, samples->counts, b.nu,
+                       b.d_T, X, cap, b.idx, b.w, b.x, b.p, b.sw32, b.nreal, b.D, samples->prob));
+  TK_CUDA(h, cudaStreamSynchronize(h->stream));
+  RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
+  TK_TRY(build_gram(h, F, rs, prec, cap, b, G_out));
+  if (h_out)
+    TK_TRY(launch_kron_axpy(h, rs, b.w, b.x, 1.0, b.axpy_split, b.axpy_part, nullptr, nullptr,
+                            nullptr, h_out));
+  return finish(h);
 }
 
 tucker_status tucker_core_solve_adjoint(tucker_handle* h, const tucker_tensor* X, const int* R,

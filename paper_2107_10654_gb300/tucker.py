@@ -19,7 +19,7 @@ from . import _lib as L
 __all__ = ["TuckerError", "Handle", "Samples", "CooTensor", "tucker_leverage_scores",
            "tucker_sample_rows", "tucker_core_update_sketched", "tucker_core_update_exact",
            "tucker_als_sweep", "tucker_ridge_loss", "tucker_core_solve_adjoint",
-           "tucker_sample_rows_noalloc"]
+           "tucker_sample_rows_noalloc", "tucker_sketched_gram"]
 
 PREC = {"fp64": L.PREC_FP64, "fp32": L.PREC_FP32, "tf32": L.PREC_TF32, "bf16": L.PREC_BF16}
 REG = {"exact": L.REG_EXACT, "augmented": L.REG_AUGMENTED}
@@ -235,6 +235,21 @@ def tucker_ridge_loss(h: Handle, X, A: Sequence[torch.Tensor], lam: float, g: to
     _check(h.h, lib.tucker_ridge_loss(h.h, C.byref(_tensor(X)), _ranks([a.shape[1] for a in A]),
                                       _factors(A), float(lam), g.data_ptr(), C.byref(out)))
     return out.value
+
+
+def tucker_sketched_gram(h: Handle, X, A: Sequence[torch.Tensor], prec: str, samples: Samples,
+                         with_rhs: bool = True):
+    """(G d x d FP64, h FP64 or None) of a frozen sample: sum_u w_u k_u k_u^T, sum_u w_u x_u k_u."""
+    lib = L.load()
+    d = 1
+    for a in A:
+        d *= a.shape[1]
+    G = torch.empty((d, d), dtype=torch.float64, device=A[0].device)
+    hv = torch.empty(d, dtype=torch.float64, device=A[0].device) if with_rhs else None
+    _check(h.h, lib.tucker_sketched_gram(h.h, C.byref(_tensor(X)), _ranks([a.shape[1] for a in A]),
+                                         _factors(A), PREC[prec], C.byref(samples._c()),
+                                         G.data_ptr(), hv.data_ptr() if hv is not None else None))
+    return G, hv
 
 
 def tucker_core_solve_adjoint(h: Handle, X, A: Sequence[torch.Tensor], lam: float, reg: str,

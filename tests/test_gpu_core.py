@@ -47,6 +47,9 @@ CASES = [
     ("dense3_512_r8_f32", (96, 80, 72), None, 6000, "fp32"),
     ("dense3_512_r8_f32", (96, 80, 72), None, 6000, "fp64"),
     ("dense4_128_r8_f32", (40, 36, 48, 44), (4, 4, 4, 4), 8000, "fp32"),
+    ("dense3_512_r8_f32", (96, 80, 72), None, 6000, "bf16"),
+    ("dense3_512_r8_f32", (96, 80, 72), None, 6000, "tf32"),
+    ("dense4_128_r8_f32", (40, 36, 48, 44), (4, 4, 4, 4), 8000, "bf16"),
 ]
 
 
