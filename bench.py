@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--prec", default="auto")
     p.add_argument("--reg", default="exact")
+    p.add_argument("--solver", default="fp64", choices=["fp64", "mixed"],
+                   help="ridge solver of the timed update (the other one is timed beside it)")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     return p.parse_args()
 
@@ -165,8 +167,8 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(w, prec, reg):
-    return {"workload": w.name, "dims": list(w.dims), "ranks": list(w.ranks), "d": w.d,
+def workload_config(w, prec, reg, solver="fp64"):
+    return {"workload": w.name, "solver": solver, "dims": list(w.dims), "ranks": list(w.ranks), "d": w.d,
             "m": w.m, "lambda": w.lam, "sigma": w.sigma, "x_dtype": w.dtype, "gram_prec": prec,
             "reg": reg, "seed": w.seed_sample,
             "l2": "flushed before every timed step (256 MiB write); X is 512 MiB"}
@@ -205,7 +207,7 @@ def main():
     F = [a.to(dev) for a in F_pin]
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
-    h = T.Handle()
+    h = T.Handle(solver=args.solver)
     stream = h.stream
 
     def sketched(core_out=None, stats=True):
@@ -267,6 +269,24 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+
+    # the other ridge solver on the same sample, timed the same way (not the headline)
+    other = "mixed" if args.solver == "fp64" else "fp64"
+    h2 = T.Handle(stream=stream, solver=other)
+    g_alt = torch.empty_like(g_sk)
+
+    def sketched_alt():
+        return T.tucker_core_update_sketched(h2, X, F, w.lam, w.m, w.seed_sample, 0, args.reg,
+                                             prec, core_out=g_alt, stats=True)
+    for _ in range(args.warmup):
+        sketched_alt()
+    alt_ms, alt_out = timed(sketched_alt, args.steps)
+    alt_loss = T.tucker_ridge_loss(h2, X, F, w.lam, g_alt) / loss_ex
+    alt = {"solver": other, "ms": statistics.mean(alt_ms), "loss_ratio": alt_loss,
+           "ms_solve": statistics.mean(s["ms_solve"] for _, s in alt_out),
+           "refine_iters": alt_out[-1][1]["refine_iters"],
+           "rel_diff_vs_timed": float(torch.linalg.norm(g_alt - g_sk) / torch.linalg.norm(g_sk))}
+    h2.close()
 
     ms = statistics.mean(sk_ms)
     ms_ex = statistics.mean(ex_ms)
@@ -335,11 +355,11 @@ def main():
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
-                "config": workload_config(w, prec, args.reg),
+                "config": workload_config(w, prec, args.reg, args.solver),
                 "exact_ms": ms_ex, "speedup_vs_exact": ms_ex / ms, "loss_ratio": loss_ratio,
                 "kron_rows_per_s": kron_rows_s * world, "n_unique": stats[-1]["n_unique"],
                 "refine_iters": stats[-1]["refine_iters"], "stage_ms": stage,
-                "exact_hbm_gbs": exact_gbs,
+                "exact_hbm_gbs": exact_gbs, "solver": args.solver, "other_solver": alt,
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": ms_e2e, "unit": "ms",
                         "h2d_bytes_per_step": int(X.numel() * X.element_size() +

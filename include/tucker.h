@@ -70,13 +70,36 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
  * G + lambda*I and the iterative-refinement residual are FP64 in every mode.
  * With a reduced-precision Gram the Cholesky factor of the rounded Gram is a
  * preconditioner: g <- g + M~^-1 (h - M g) with M g evaluated in FP64 on the
- * implicit rows, until ||correction|| < 1e-13 ||g|| (at most 8 iterations). */
+ * implicit rows, until ||correction|| < 1e-9 ||g|| (at most 8 iterations); the
+ * remaining error is about the contraction factor times that, ~1e-12 or less. */
 typedef enum {
   TUCKER_PREC_FP64 = 0,   /* FP64 CUDA-core Gram; no refinement needed */
   TUCKER_PREC_FP32 = 1,   /* FP32 CUDA-core Gram, FP64 refinement */
   TUCKER_PREC_TF32 = 2,   /* tcgen05 TF32 tensor-core Gram, FP32 accumulate, FP64 refinement */
   TUCKER_PREC_BF16 = 3    /* tcgen05 BF16 tensor-core Gram, FP32 accumulate, FP64 refinement */
 } tucker_prec;
+
+/* How (G + lambda R) g = h is solved (Eq. problem_def; Appendix B, proof of
+ * Thm 4.2).  Both return the FP64 solution to the tolerances stated for
+ * tucker_prec; they differ in what the O(d^3) factorisation runs in.
+ *   FP64_CHOLESKY  the factorisation is FP64 (default).  With an FP64 Gram
+ *                  the solve is direct; with a reduced-precision Gram the
+ *                  FP64 factor preconditions the refinement described above.
+ *   MIXED          the factorisation and triangular solves are FP32 and only
+ *                  precondition an FP64 iterative refinement,
+ *                  g <- g + L32^-T L32^-1 (h - M g), with the residual h - M g
+ *                  in FP64 (the explicit FP64 M for TUCKER_PREC_FP64; the
+ *                  implicit FP64 rows otherwise).  It stops when
+ *                  ||correction|| < tol ||g|| (tol = 1e-14 for an FP64 Gram,
+ *                  1e-9 otherwise) or when the correction stops shrinking, at
+ *                  most 12 iterations.  It converges when kappa(M) * 2^-24 is
+ *                  well below 1; lambda > 0 keeps kappa(M) <= (||G|| +
+ *                  lambda)/lambda.  A matrix that FP32 cannot factor (a
+ *                  pivot <= 0 after rounding) returns TUCKER_ENOTSPD. */
+typedef enum {
+  TUCKER_SOLVER_FP64_CHOLESKY = 0,
+  TUCKER_SOLVER_MIXED = 1
+} tucker_solver;
 
 /* How the lambda*I term enters the sketched problem. */
 typedef enum {
@@ -149,6 +172,11 @@ const char* tucker_last_error(const tucker_handle* h);
  * device-detected errors.  0: calls return after enqueueing; device errors
  * are returned by the next tucker_sync(). */
 tucker_status tucker_set_sync(tucker_handle* h, int synchronous);
+
+/* Select the ridge solver of later core updates and adjoints on h
+ * (TUCKER_SOLVER_FP64_CHOLESKY by default).  Invalidates the cached factor.
+ * Errors: EINVAL (h NULL or an unknown solver). */
+tucker_status tucker_set_solver(tucker_handle* h, tucker_solver solver);
 
 /* Wait for the handle's stream and return any pending device-side error. */
 tucker_status tucker_sync(tucker_handle* h);

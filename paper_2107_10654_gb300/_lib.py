@@ -16,6 +16,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTSPD", "ERANK", "EDRAWLIM
 F32, F64 = 0, 1
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16 = 0, 1, 2, 3
 REG_EXACT, REG_AUGMENTED = 0, 1
+SOLVER_FP64_CHOLESKY, SOLVER_MIXED = 0, 1
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtucker.so")
 
@@ -51,6 +52,7 @@ SIGNATURES = {
     "tucker_destroy": (C.c_int, [_P]),
     "tucker_last_error": (C.c_char_p, [_P]),
     "tucker_set_sync": (C.c_int, [_P, C.c_int]),
+    "tucker_set_solver": (C.c_int, [_P, C.c_int]),
     "tucker_sync": (C.c_int, [_P]),
     "tucker_leverage_scores": (C.c_int, [_P, C.c_int, _I64P, _IP, C.c_int, _PP, _PP, _PP, _IP]),
     "tucker_sample_rows": (C.c_int, [_P, C.c_int, _I64P, _IP, _PP, C.c_int64, C.c_uint64,

@@ -45,7 +45,17 @@ tucker_status launch_kron_axpy(tucker_handle* h, const RowSet& s, const double* 
 tucker_status launch_kron_dot(tucker_handle* h, const RowSet& s, const double* g1,
                               const double* g2, double* z1, double* z2);
 tucker_status cholesky(tucker_handle* h, double* M, int d);
-tucker_status chol_solve(tucker_handle* h, const double* L, int d, const double* rhs, double* g);
+tucker_status cholesky32(tucker_handle* h, float* M, int d);
+tucker_status chol_prepare(tucker_handle* h, const double* L, int d, double* LT, double* Linv);
+tucker_status chol_prepare32(tucker_handle* h, const float* L, int d, float* LT, float* Linv);
+tucker_status chol_solve2(tucker_handle* h, const double* L, const double* LT, const double* Linv,
+                          int d, const double* rhs, double* g, double* tmp);
+tucker_status chol_solve32(tucker_handle* h, const float* L, const float* LT, const float* Linv,
+                           int d, const double* rhs, double* g, double* tmp);
+tucker_status launch_to_f32(tucker_handle* h, const double* in, size_t n, float* out);
+tucker_status launch_gemv_resid(tucker_handle* h, const double* M, int d, const double* g,
+                                const double* hv, double* r);
+size_t chol_inv_doubles(int d);
 tucker_status launch_regdiag(tucker_handle* h, double* out, int d, double lambda, const double* D);
 tucker_status launch_refine_update(tucker_handle* h, double* g, const double* r, int d,
                                    double* out2);
@@ -67,12 +77,55 @@ tucker_status launch_adjoint_rows(tucker_handle* h, const FactorSet& F, uint32_t
                                   const double* w, const double* x, const double* zg,
                                   const double* zv, const double* g, const double* v,
                                   const int* n_rows, int64_t cap, double* const* dA, double* dx);
+size_t walk_scratch_doubles(int64_t I1, int d, int R1);
+bool walk_fits(int N, const int* R, int64_t I1);
+tucker_status walk_segments(tucker_handle* h, const RowSet& s, int64_t I1, int64_t cap,
+                            double* scratch);
+tucker_status walk_dot(tucker_handle* h, const RowSet& s, int64_t I1, double* scratch,
+                       const double* g1, const double* g2, double* z1, double* z2);
+tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, double* scratch,
+                        const double* ca, const double* cb, double coef, const double* base,
+                        const double* diag, const double* y, double* out);
 tucker_status launch_decode_rows(tucker_handle* h, const FactorSet& F, const uint64_t* keys,
                                  int64_t n, uint32_t* const* idx, const void* vals, double* x);
 int gram_tc_supported(int prec, int d);
 size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int sumR, int64_t cap);
 tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_t cap, char* ws,
                              size_t ws_bytes, double* G);
+
+tucker_status launch_to_f64(tucker_handle* h, const FactorSet& F, double* const* out);
+size_t leverage_aux_bytes(int64_t maxI);
+static int64_t max_dim(const FactorSet& F) { int64_t m = 1; for (int n = 0; n < F.N; ++n) if (F.I[n] > m) m = F.I[n]; return m; }
+
+// The row set with FP64 factors (converted once per call when they are FP32).
+static tucker_status rowset64(tucker_handle* h, const FactorSet& F, const RowSet& rs,
+                              double* const* A64, RowSet* out) {
+  *out = rs;
+  if (F.is64) return TUCKER_OK;
+  TK_TRY(launch_to_f64(h, F, A64));
+  for (int n = 0; n < F.N; ++n) out->A[n] = A64[n];
+  out->is64 = 1;
+  return TUCKER_OK;
+}
+
+// ---------------------------------------------- FP64 products with sampled rows
+// Level walk along the sorted sample when its vectors fit in shared memory,
+// else the per-element kernels (same results up to summation order).
+static tucker_status rows_dot(tucker_handle* h, const FactorSet& F, const RowSet& rs,
+                              double* walk, const double* g1, const double* g2, double* z1,
+                              double* z2) {
+  if (walk_fits(F.N, F.R, F.I[0])) return walk_dot(h, rs, F.I[0], walk, g1, g2, z1, z2);
+  return launch_kron_dot(h, rs, g1, g2, z1, z2);
+}
+
+static tucker_status rows_axpy(tucker_handle* h, const FactorSet& F, const RowSet& rs,
+                               double* walk, int nsplit, double* part, const double* ca,
+                               const double* cb, double coef, const double* base,
+                               const double* diag, const double* y, double* out) {
+  if (walk_fits(F.N, F.R, F.I[0]))
+    return walk_axpy(h, rs, F.I[0], walk, ca, cb, coef, base, diag, y, out);
+  return launch_kron_axpy(h, rs, ca, cb, coef, nsplit, part, base, diag, y, out);
+}
 
 // ----------------------------------------------------------------- plumbing
 
@@ -207,7 +260,8 @@ struct SketchBufs {
   uint32_t* idx[TUCKER_MAX_ORDER];
   double *w, *x, *p, *z;
   float* sw32;
-  double *D, *regdiag, *h, *g, *r, *axpy_part;
+  double *D, *h, *g, *r, *axpy_part, *walk;
+  double* A64[TUCKER_MAX_ORDER];      // FP64 copies of FP32 factors (walk kernels)
   char* gram_ws;
   size_t gram_bytes;
   int axpy_split;
@@ -220,7 +274,7 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
     b->lev[n] = ar.get<double>(F.I[n]);
     b->cdf[n] = ar.get<uint64_t>(F.I[n]);
   }
-  b->rank = ar.get<int>(F.N);
+  b->rank = reinterpret_cast<int*>(ar.get<char>(leverage_aux_bytes(max_dim(F))));
   b->keys_raw = fixed ? nullptr : ar.get<uint64_t>(m);
   b->d_T = ar.get<int64_t>(1);
   b->sort_bytes = fixed ? 0 : sort_dedupe_scratch(m);
@@ -236,12 +290,14 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
   b->z = ar.get<double>(m);
   b->sw32 = ar.get<float>(m);
   b->D = ar.get<double>(F.d);
-  b->regdiag = ar.get<double>(F.d);
   b->h = ar.get<double>(F.d);
   b->g = ar.get<double>(F.d);
   b->r = ar.get<double>(F.d);
   b->axpy_split = axpy_splits(h, F.d, m);
   b->axpy_part = ar.get<double>((size_t)b->axpy_split * F.d);
+  b->walk = ar.get<double>(walk_scratch_doubles(F.I[0], F.d, F.R[0]));
+  for (int n = 0; n < F.N; ++n)
+    b->A64[n] = F.is64 ? nullptr : ar.get<double>((size_t)F.I[n] * F.R[n]);
   b->simt_split = gram_simt_splits(h, F.d, m);
   int sumR = 0;
   for (int n = 0; n < F.N; ++n) sumR += F.R[n];
@@ -255,23 +311,55 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
 static tucker_status chol_reserve(tucker_handle* h, int d) {
   CholCache& c = h->chol;
   const size_t need = (size_t)d * d;
+  const size_t inv = chol_inv_doubles(d);
   if (c.cap < need) {
     TK_CUDA(h, cudaStreamSynchronize(h->stream));
     if (c.L) cudaFree(c.L);
     c.L = nullptr;
     c.cap = 0;
     void* p = nullptr;
-    if (cudaMalloc(&p, (need + d) * sizeof(double)) != cudaSuccess) {
+    // FP64: L, LT, regdiag, tmp, Linv; FP32: L32, LT32, Linv32
+    const size_t total = (2 * need + 2 * (size_t)d + inv + 64) * sizeof(double) +
+                         (2 * need + inv + 64) * sizeof(float);
+    if (cudaMalloc(&p, total) != cudaSuccess) {
       cudaGetLastError();
       return fail(h, TUCKER_ENOMEM, "Cholesky buffer for d = %d", d);
     }
     c.L = static_cast<double*>(p);
-    c.regdiag = c.L + need;
     c.cap = need;
   }
+  c.LT = c.L + need;
+  c.regdiag = c.LT + need;
+  c.tmp = c.regdiag + d;
+  c.Linv = c.tmp + d;
+  c.L32 = reinterpret_cast<float*>(c.Linv + inv + 64);
+  c.LT32 = c.L32 + need;
+  c.Linv32 = c.LT32 + need;
   c.d = d;
   c.id = 0;
   return TUCKER_OK;
+}
+
+// Factor M (= G + diag(regdiag), full and symmetric in the FP64 buffer L)
+// with the handle's solver.  FP64: L L^T = M in place.  Mixed: the FP32 copy
+// is factored and L keeps M for the FP64 residual.
+static tucker_status factorize(tucker_handle* h, double* L, int d) {
+  CholCache& c = h->chol;
+  c.mixed = h->solver == TUCKER_SOLVER_MIXED;
+  if (c.mixed) {
+    TK_TRY(launch_to_f32(h, L, (size_t)d * d, c.L32));
+    TK_TRY(cholesky32(h, c.L32, d));
+    return chol_prepare32(h, c.L32, d, c.LT32, c.Linv32);
+  }
+  TK_TRY(cholesky(h, L, d));
+  return chol_prepare(h, L, d, c.LT, c.Linv);
+}
+
+// g = (L L^T)^-1 rhs with the cached factor (g may alias rhs).
+static tucker_status chol_solve(tucker_handle* h, int d, const double* rhs, double* g) {
+  const CholCache& c = h->chol;
+  if (c.mixed) return chol_solve32(h, c.L32, c.LT32, c.Linv32, d, rhs, g, c.tmp);
+  return chol_solve2(h, c.L, c.LT, c.Linv, d, rhs, g, c.tmp);
 }
 
 // G (into L buffer) from the sample, by precision.
@@ -284,34 +372,51 @@ static tucker_status build_gram(tucker_handle* h, const FactorSet& F, const RowS
   return launch_gram_tc(h, rs, prec, cap, b.gram_ws, b.gram_bytes, G);
 }
 
-// Solve (G + diag(regdiag)) g = h with L cached; refinement for tensor-core G.
-static tucker_status solve_refine(tucker_handle* h, const FactorSet& F, const RowSet& rs,
-                                  int prec, SketchBufs& b, int* iters, double* rel) {
+// g = M^-1 rhs with the cached factor of M~ (the Gram as built + diag(regdiag)),
+// refined in FP64 whenever the factor is not an FP64 factor of M itself:
+//   g <- g + M~^-1 (rhs - M g),  M g = sum_u w_u k_u (k_u . g) + regdiag * g
+// on the implicit FP64 rows, or the explicit FP64 M when the Gram was FP64
+// (mixed solver).  Stops at ||correction|| < tol ||g|| or when the correction
+// stops shrinking.
+static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const RowSet& rs,
+                                   int prec, SketchBufs& b, const double* rhs, double* g,
+                                   int* iters, double* rel) {
   const int d = F.d;
-  double* L = h->chol.L;
-  TK_TRY(launch_add_diag(h, L, d, b.regdiag));
-  TK_TRY(cholesky(h, L, d));
-  TK_TRY(chol_solve(h, L, d, b.h, b.g));
+  TK_TRY(chol_solve(h, d, rhs, g));
   *iters = 0;
   *rel = 0.0;
-  if (prec == TUCKER_PREC_FP64) return TUCKER_OK;
-  // g <- g + M~^-1 (h - (sum w k k^T + R) g), residual in FP64 on the implicit rows
-  const int max_iters = 8;
+  const bool explicit_m = prec == TUCKER_PREC_FP64;
+  if (explicit_m && !h->chol.mixed) return TUCKER_OK;
+  const double tol = explicit_m ? 1e-14 : 1e-9;
+  const int max_iters = h->chol.mixed ? 12 : 8;
+  double prev = INFINITY;
   for (int it = 0; it < max_iters; ++it) {
-    TK_TRY(launch_kron_dot(h, rs, b.g, nullptr, b.z, nullptr));
-    TK_TRY(launch_kron_axpy(h, rs, b.w, b.z, -1.0, b.axpy_split, b.axpy_part, b.h, b.regdiag,
-                            b.g, b.r));
-    TK_TRY(chol_solve(h, L, d, b.r, b.r));
-    // g += correction; ||correction|| / ||g|| decides convergence
+    if (explicit_m) {
+      TK_TRY(launch_gemv_resid(h, h->chol.L, d, g, rhs, b.r));
+    } else {
+      TK_TRY(rows_dot(h, F, rs, b.walk, g, nullptr, b.z, nullptr));
+      TK_TRY(rows_axpy(h, F, rs, b.walk, b.axpy_split, b.axpy_part, b.w, b.z, -1.0, rhs,
+                       h->chol.regdiag, g, b.r));
+    }
+    TK_TRY(chol_solve(h, d, b.r, b.r));
     double hv[2] = {0, 0};
-    TK_TRY(launch_refine_update(h, b.g, b.r, d, b.z));
+    TK_TRY(launch_refine_update(h, g, b.r, d, b.z));
     TK_CUDA(h, cudaMemcpyAsync(hv, b.z, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     TK_CUDA(h, cudaStreamSynchronize(h->stream));
     *iters = it + 1;
     *rel = hv[1] > 0 ? sqrt(hv[0] / hv[1]) : 0.0;
-    if (*rel < 1e-13) break;
+    if (*rel < tol || *rel > 0.5 * prev) break;
+    prev = *rel;
   }
   return TUCKER_OK;
+}
+
+// Factor G + diag(regdiag) (G in the FP64 buffer L) and solve for b.h.
+static tucker_status solve_refine(tucker_handle* h, const FactorSet& F, const RowSet& rs,
+                                  int prec, SketchBufs& b, int* iters, double* rel) {
+  TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
+  TK_TRY(factorize(h, h->chol.L, F.d));
+  return solve_refined(h, F, rs, prec, b, b.h, b.g, iters, rel);
 }
 
 }  // namespace tk
@@ -374,6 +479,15 @@ tucker_status tucker_set_sync(tucker_handle* h, int synchronous) {
   return TUCKER_OK;
 }
 
+tucker_status tucker_set_solver(tucker_handle* h, tucker_solver solver) {
+  if (!h) return TUCKER_EINVAL;
+  if (solver != TUCKER_SOLVER_FP64_CHOLESKY && solver != TUCKER_SOLVER_MIXED)
+    return fail(h, TUCKER_EINVAL, "unknown solver %d", (int)solver);
+  h->solver = solver;
+  h->chol.id = 0;
+  return TUCKER_OK;
+}
+
 tucker_status tucker_sync(tucker_handle* h) {
   if (!h) return TUCKER_EINVAL;
   return device_status(h);
@@ -392,14 +506,14 @@ tucker_status tucker_leverage_scores(tucker_handle* h, int N, const int64_t* I, 
   Arena sz(nullptr);
   uint64_t* cdf_ws[TUCKER_MAX_ORDER];
   for (int n = 0; n < N; ++n) cdf_ws[n] = sz.get<uint64_t>(F.I[n]);
-  int* rk = sz.get<int>(N);
+  int* rk = reinterpret_cast<int*>(sz.get<char>(leverage_aux_bytes(max_dim(F))));
   TK_TRY(ws_reserve(h, sz.off));
   Arena ar(h->ws);
   for (int n = 0; n < N; ++n) {
     uint64_t* c = ar.get<uint64_t>(F.I[n]);
     cdf_ws[n] = (cdf_out && cdf_out[n]) ? cdf_out[n] : c;
   }
-  rk = ar.get<int>(N);
+  rk = reinterpret_cast<int*>(ar.get<char>(leverage_aux_bytes(max_dim(F))));
   TK_TRY(launch_leverage(h, F, lev_out, cdf_ws, rk, nullptr, nullptr, nullptr));
   if (rank_out_host) {
     TK_CUDA(h, cudaMemcpyAsync(rank_out_host, rk, sizeof(int) * N, cudaMemcpyDeviceToHost, h->stream));
@@ -560,17 +674,19 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
                        b.p, b.sw32, b.nreal, b.D, p_in));
   ev_record(h, timing, 4);
   RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
+  RowSet rs64;
+  TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
   double* G = h->chol.L;
+  TK_TRY(walk_segments(h, rs, F.I[0], cap, b.walk));
   TK_TRY(build_gram(h, F, rs, prec, cap, b, G));
-  TK_TRY(launch_kron_axpy(h, rs, b.w, b.x, 1.0, b.axpy_split, b.axpy_part, nullptr, nullptr,
-                          nullptr, b.h));
-  TK_TRY(launch_regdiag(h, b.regdiag, F.d, lambda, reg == TUCKER_REG_AUGMENTED ? b.D : nullptr));
-  TK_CUDA(h, cudaMemcpyAsync(h->chol.regdiag, b.regdiag, sizeof(double) * F.d,
-                             cudaMemcpyDeviceToDevice, h->stream));
+  TK_TRY(rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x, 1.0, nullptr, nullptr,
+                   nullptr, b.h));
+  TK_TRY(launch_regdiag(h, h->chol.regdiag, F.d, lambda,
+                        reg == TUCKER_REG_AUGMENTED ? b.D : nullptr));
   ev_record(h, timing, 5);
   int iters = 0;
   double rel = 0.0;
-  TK_TRY(solve_refine(h, F, rs, prec, b, &iters, &rel));
+  TK_TRY(solve_refine(h, F, rs64, prec, b, &iters, &rel));
   TK_CUDA(h, cudaMemcpyAsync(core_out, b.g, sizeof(double) * F.d, cudaMemcpyDeviceToDevice,
                              h->stream));
   ev_record(h, timing, 6);
@@ -622,7 +738,7 @@ tucker_status tucker_core_update_exact(tucker_handle* h, const tucker_tensor* X,
         V[n] = ar.get<double>(F.R[n] * F.R[n]);
         s[n] = ar.get<double>(F.R[n]);
       }
-      *rk = ar.get<int>(N);
+      *rk = reinterpret_cast<int*>(ar.get<char>(leverage_aux_bytes(max_dim(F))));
       *b0 = ar.get<double>(inter);
       *b1 = ar.get<double>(inter);
       *y = ar.get<double>(F.d);
@@ -660,14 +776,17 @@ tucker_status tucker_core_update_exact(tucker_handle* h, const tucker_tensor* X,
   // unit weights: w = 1 for every observed row
   TK_TRY(launch_regdiag(h, b.w, (int)std::min<int64_t>(nnz, 1 << 30), 1.0, nullptr));
   rs.w = b.w;
+  RowSet rs64;
+  TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
   double* G = h->chol.L;
+  TK_TRY(walk_segments(h, rs, F.I[0], nnz, b.walk));
   TK_TRY(build_gram(h, F, rs, prec, nnz, b, G));
-  TK_TRY(launch_kron_axpy(h, rs, b.w, b.x, 1.0, b.axpy_split, b.axpy_part, nullptr, nullptr,
-                          nullptr, b.h));
-  TK_TRY(launch_regdiag(h, b.regdiag, F.d, lambda, nullptr));
+  TK_TRY(rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x, 1.0, nullptr, nullptr,
+                   nullptr, b.h));
+  TK_TRY(launch_regdiag(h, h->chol.regdiag, F.d, lambda, nullptr));
   int iters;
   double rel;
-  TK_TRY(solve_refine(h, F, rs, prec, b, &iters, &rel));
+  TK_TRY(solve_refine(h, F, rs64, prec, b, &iters, &rel));
   TK_CUDA(h, cudaMemcpyAsync(core_out, b.g, sizeof(double) * F.d, cudaMemcpyDeviceToDevice,
                              h->stream));
   return finish(h);
@@ -728,7 +847,7 @@ tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const i
       cdf[n] = ar.get<uint64_t>(F.I[n]);
       gram[n] = ar.get<double>(F.R[n] * F.R[n]);
     }
-    *rk = ar.get<int>(N);
+    *rk = reinterpret_cast<int*>(ar.get<char>(leverage_aux_bytes(max_dim(F))));
     *b0 = ar.get<double>(inter);
     *b1 = ar.get<double>(inter);
     *B = ar.get<double>(inter);
@@ -807,10 +926,13 @@ tucker_status tucker_sketched_gram(tucker_handle* h, const tucker_tensor* X, con
                        b.d_T, X, cap, b.idx, b.w, b.x, b.p, b.sw32, b.nreal, b.D, samples->prob));
   TK_CUDA(h, cudaStreamSynchronize(h->stream));
   RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
+  RowSet rs64;
+  TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
+  TK_TRY(walk_segments(h, rs, F.I[0], cap, b.walk));
   TK_TRY(build_gram(h, F, rs, prec, cap, b, G_out));
   if (h_out)
-    TK_TRY(launch_kron_axpy(h, rs, b.w, b.x, 1.0, b.axpy_split, b.axpy_part, nullptr, nullptr,
-                            nullptr, h_out));
+    TK_TRY(rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x, 1.0, nullptr, nullptr,
+                     nullptr, h_out));
   return finish(h);
 }
 
@@ -851,16 +973,21 @@ tucker_status tucker_core_solve_adjoint(tucker_handle* h, const tucker_tensor* X
                        b.idx, b.w, b.x, b.p, b.sw32, b.nreal, b.D, samples->prob));
   TK_CUDA(h, cudaStreamSynchronize(h->stream));
   RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
+  RowSet rs64;
+  TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
+  TK_TRY(walk_segments(h, rs, F.I[0], cap, b.walk));
   if (!reuse) {
     TK_TRY(build_gram(h, F, rs, prec, cap, b, h->chol.L));
     TK_TRY(launch_regdiag(h, h->chol.regdiag, F.d, lambda,
                           reg == TUCKER_REG_AUGMENTED ? b.D : nullptr));
     TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
-    TK_TRY(cholesky(h, h->chol.L, F.d));
+    TK_TRY(factorize(h, h->chol.L, F.d));
     h->chol.id = h->next_solve_id++;
   }
-  TK_TRY(chol_solve(h, h->chol.L, F.d, gbar, v));
-  TK_TRY(launch_kron_dot(h, rs, g, v, b.z, zv));
+  int iters;
+  double rel;
+  TK_TRY(solve_refined(h, F, rs64, prec, b, gbar, v, &iters, &rel));
+  TK_TRY(rows_dot(h, F, rs64, b.walk, g, v, b.z, zv));
   TK_CUDA(h, cudaMemsetAsync(dx_out, 0, sizeof(double) * cap, h->stream));
   TK_TRY(launch_adjoint_rows(h, F, b.idx, b.w, b.x, b.z, zv, g, v, b.nreal, cap, dA_out, dx_out));
   return finish(h);

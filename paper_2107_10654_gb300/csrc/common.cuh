@@ -34,6 +34,13 @@ struct HashTable {
 struct CholCache {
   double* L = nullptr;    // d x d lower factor (row-major), FP64
   double* regdiag = nullptr;  // d: lambda * (1 or D_j)
+  double* Linv = nullptr;     // inverses of the 64 x 64 diagonal blocks of L
+  double* LT = nullptr;       // L transposed (upper triangle), d x d
+  double* tmp = nullptr;      // d doubles of solve scratch
+  float* L32 = nullptr;       // FP32 factor of the mixed solver (d x d)
+  float* LT32 = nullptr;      // its transpose
+  float* Linv32 = nullptr;    // its inverted 64 x 64 diagonal blocks
+  int mixed = 0;          // the cached factor is the FP32 one (L then holds M itself)
   int d = 0;
   size_t cap = 0;         // elements of L allocated
   uint64_t id = 0;        // solve id of the cached factor (0 = none)
@@ -54,6 +61,7 @@ struct tucker_handle {
   tk::CholCache chol;
   uint64_t next_solve_id = 1;
   int64_t launches = 0;         // kernels launched by this handle (all calls)
+  int solver = 0;               // tucker_solver: FP64 Cholesky (0) or mixed (1)
   cudaEvent_t ev[16];
   char err[512];
 };

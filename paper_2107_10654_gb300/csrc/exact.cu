@@ -12,36 +12,159 @@
 
 namespace tk {
 
+// Sum v[0..RP) over the 32 lanes so that lane l ends with the total of entry
+// r(l) = bits (4, 3, ..) of l: halving exchanges (RP/2 + RP/4 + ... + 1
+// shuffles) then plain butterflies over the remaining lane bits.  Lanes with
+// (l & (32/RP - 1)) == 0 hold distinct r = l / (32/RP).
+template <class T, int RP>
+__device__ __forceinline__ T transpose_reduce(T (&v)[RP], int lane) {
+  int width = RP;
+#pragma unroll
+  for (int o = 16; o >= 32 / RP; o >>= 1) {
+    const bool upper = lane & o;
+    const int h = width >> 1;
+#pragma unroll
+    for (int j = 0; j < RP / 2; ++j) {
+      if (j < h) {
+        const T send = upper ? v[j] : v[j + h];
+        const T recv = __shfl_xor_sync(0xffffffffu, send, o);
+        v[j] = (upper ? v[j + h] : v[j]) + recv;
+      }
+    }
+    width = h;
+  }
+  T x = v[0];
+#pragma unroll
+  for (int o = (32 / RP) >> 1; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
 // out[p][r] = sum_i X[p][i] A[i][r]   (X: P x I row-major; out FP64 P x R)
-template <class T, int RC>
+// One warp per row; A^T in shared memory ([r][i], conflict-free); 16-byte
+// loads of X when the row length allows; R <= RP accumulators per lane.
+template <class T, int RP>
 __global__ void __launch_bounds__(256) k_ttm_last(const T* X, int64_t P, int I, const T* A, int R,
                                                   double* out) {
   extern __shared__ unsigned char smraw[];
-  T* As = reinterpret_cast<T*>(smraw);               // I x R
-  for (int e = threadIdx.x; e < I * R; e += blockDim.x) As[e] = A[e];
+  T* At = reinterpret_cast<T*>(smraw);               // RP x I (zero rows beyond R)
+  for (int e = threadIdx.x; e < RP * I; e += blockDim.x) {
+    const int r = e / I, i = e % I;
+    At[e] = r < R ? A[(int64_t)i * R + r] : T(0);
+  }
   __syncthreads();
+  constexpr int VEC = 16 / sizeof(T);
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool vec = (I % VEC) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
   for (int64_t p = warp; p < P; p += nwarps) {
     const T* row = X + p * I;
-    for (int r0 = 0; r0 < R; r0 += RC) {
-      T acc[RC];
+    T acc[RP];
 #pragma unroll
-      for (int j = 0; j < RC; ++j) acc[j] = T(0);
+    for (int j = 0; j < RP; ++j) acc[j] = T(0);
+    if (vec) {
+      for (int i0 = lane * VEC; i0 < I; i0 += 32 * VEC) {
+        T xv[VEC];
+        *reinterpret_cast<uint4*>(xv) = __ldg(reinterpret_cast<const uint4*>(row + i0));
+#pragma unroll
+        for (int j = 0; j < RP; ++j) {
+          T av[VEC];
+          *reinterpret_cast<uint4*>(av) = *reinterpret_cast<const uint4*>(At + j * I + i0);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) acc[j] = fma(xv[q], av[q], acc[j]);
+        }
+      }
+    } else {
       for (int i = lane; i < I; i += 32) {
         const T x = row[i];
-        const T* a = As + i * R + r0;
 #pragma unroll
-        for (int j = 0; j < RC; ++j)
-          if (r0 + j < R) acc[j] = fma(x, a[j], acc[j]);
-      }
-#pragma unroll
-      for (int j = 0; j < RC; ++j) {
-        T v = warp_sum(acc[j]);
-        if (lane == 0 && r0 + j < R) out[p * R + r0 + j] = (double)v;
+        for (int j = 0; j < RP; ++j) acc[j] = fma(x, At[j * I + i], acc[j]);
       }
     }
+    const T tot = transpose_reduce<T, RP>(acc, lane);
+    constexpr int G = 32 / RP;
+    if ((lane % G) == 0) {
+      const int r = lane / G;
+      if (r < R) out[p * R + r] = (double)tot;
+    }
+  }
+}
+
+// Fused contraction of the last two modes of one slab per CTA:
+//   out[p][a][b] = sum_{i,j} X[p][i][j] A1[i][a] A2[j][b]
+// (A1 = A^(N-1), I1 x R1; A2 = A^(N), I2 x R2).  Each warp reduces rows j of
+// the slab against A2 (as in k_ttm_last), then adds A1[i][a] * t[b] into
+// per-warp FP64 accumulators; warps are combined in a fixed order.
+template <class T, int RP>
+__global__ void __launch_bounds__(256) k_ttm_last2(const T* X, int64_t pre, int I1, int I2,
+                                                   const T* A1, int R1, const T* A2, int R2,
+                                                   double* out) {
+  extern __shared__ unsigned char smraw[];
+  T* At = reinterpret_cast<T*>(smraw);                         // RP x I2
+  T* A1s = reinterpret_cast<T*>(smraw + (((size_t)RP * I2 * sizeof(T) + 15) & ~size_t(15)));
+  double* Yw = reinterpret_cast<double*>(smraw + (((size_t)RP * I2 * sizeof(T) + 15) & ~size_t(15)) +
+                                         (((size_t)I1 * R1 * sizeof(T) + 15) & ~size_t(15)));
+  for (int e = threadIdx.x; e < RP * I2; e += blockDim.x) {
+    const int r = e / I2, j = e % I2;
+    At[e] = r < R2 ? A2[(int64_t)j * R2 + r] : T(0);
+  }
+  for (int e = threadIdx.x; e < I1 * R1; e += blockDim.x) A1s[e] = A1[e];
+  constexpr int VEC = 16 / sizeof(T);
+  constexpr int G = 32 / RP;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int RR = R1 * R2;
+  const bool vec = (I2 % VEC) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  __syncthreads();
+  for (int64_t p = blockIdx.x; p < pre; p += gridDim.x) {
+    T y[8];                                                    // outputs lane, lane+32, ...
+#pragma unroll
+    for (int q = 0; q < 8; ++q) y[q] = T(0);
+    const T* slab = X + p * (int64_t)I1 * I2;
+    for (int i = w; i < I1; i += 8) {
+      const T* row = slab + (int64_t)i * I2;
+      T acc[RP];
+#pragma unroll
+      for (int j = 0; j < RP; ++j) acc[j] = T(0);
+      if (vec) {
+        for (int j0 = lane * VEC; j0 < I2; j0 += 32 * VEC) {
+          T xv[VEC];
+          *reinterpret_cast<uint4*>(xv) = __ldg(reinterpret_cast<const uint4*>(row + j0));
+#pragma unroll
+          for (int j = 0; j < RP; ++j) {
+            T av[VEC];
+            *reinterpret_cast<uint4*>(av) = *reinterpret_cast<const uint4*>(At + j * I2 + j0);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) acc[j] = fma(xv[q], av[q], acc[j]);
+          }
+        }
+      } else {
+        for (int j0 = lane; j0 < I2; j0 += 32) {
+          const T x = row[j0];
+#pragma unroll
+          for (int j = 0; j < RP; ++j) acc[j] = fma(x, At[j * I2 + j0], acc[j]);
+        }
+      }
+      const T t = transpose_reduce<T, RP>(acc, lane);         // t[b] at lane b*G
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = lane + 32 * q;
+        const int b = e % R2;
+        const T tb = __shfl_sync(0xffffffffu, t, (b % RP) * G);
+        if (e < RR) y[q] = fma(A1s[i * R1 + e / R2], tb, y[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = lane + 32 * q;
+      if (e < RR) Yw[w * RR + e] = (double)y[q];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+      double v = 0.0;
+      for (int ww = 0; ww < 8; ++ww) v += Yw[ww * RR + e];
+      out[p * RR + e] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -92,6 +215,30 @@ __global__ void k_ttm_small(const double* in, int64_t pre, int64_t post, const v
       acc = fma(in[(p * K + k) * post + q], a, acc);
     }
     out[t] = acc;
+  }
+}
+
+// Same as k_ttm_small, one warp per output (lanes over the contracted index)
+// for long contractions; fixed butterfly order.
+__global__ void k_ttm_small_warp(const double* in, int64_t pre, int64_t post, const void* A,
+                                 int is64, int I, int R, int contract, double* out) {
+  const int K = contract ? I : R, M = contract ? R : I;
+  const int64_t total = pre * M * post;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = warp; t < total; t += nwarps) {
+    const int64_t q = t % post;
+    const int mo = (int)((t / post) % M);
+    const int64_t p = t / (post * M);
+    double acc = 0.0;
+    for (int k = lane; k < K; k += 32) {
+      const double a = contract ? load_as_double(A, (int64_t)k * R + mo, is64)
+                                : load_as_double(A, (int64_t)mo * R + k, is64);
+      acc = fma(in[(p * K + k) * post + q], a, acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) out[t] = acc;
   }
 }
 
@@ -247,23 +394,32 @@ static int grid_for(tucker_handle* h, int64_t work, int per = 256) {
 }
 
 // Contract the last mode of the dense X: out = X_(as P x I_N) A^(N)  (FP64 out)
-tucker_status ttm_last(tucker_handle* h, const void* X, int is64, int64_t P, int I, const void* A,
-                       int R, double* out) {
-  const size_t smem = (size_t)I * R * (is64 ? 8 : 4);
-  const int grid = grid_for(h, P * 32);
-  if (is64) {
-    auto k = R <= 8 ? k_ttm_last<double, 8> : k_ttm_last<double, 16>;
-    TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    TK_COUNT(h);
-    k<<<grid, 256, smem, h->stream>>>((const double*)X, P, I, (const double*)A, R, out);
-  } else {
-    auto k = R <= 8 ? k_ttm_last<float, 8> : k_ttm_last<float, 16>;
-    TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    TK_COUNT(h);
-    k<<<grid, 256, smem, h->stream>>>((const float*)X, P, I, (const float*)A, R, out);
-  }
+template <class T>
+static tucker_status ttm_last_t(tucker_handle* h, const T* X, int64_t P, int I, const T* A, int R,
+                                double* out) {
+  const int RP = R <= 4 ? 4 : R <= 8 ? 8 : R <= 16 ? 16 : 32;
+  const size_t smem = (size_t)RP * I * sizeof(T);
+  if (smem > 200 * 1024) return fail(h, TUCKER_ENOTSUP, "I_N * R_N too large for the TTM kernel");
+  auto k = RP == 4 ? k_ttm_last<T, 4> : RP == 8 ? k_ttm_last<T, 8>
+         : RP == 16 ? k_ttm_last<T, 16> : k_ttm_last<T, 32>;
+  TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  TK_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
+  int64_t grid = (int64_t)h->num_sms * (per_sm > 0 ? per_sm : 1);
+  const int64_t need = (P + 7) / 8;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  TK_COUNT(h);
+  k<<<(int)grid, 256, smem, h->stream>>>(X, P, I, A, R, out);
   TK_LAUNCH(h);
   return TUCKER_OK;
+}
+
+tucker_status ttm_last(tucker_handle* h, const void* X, int is64, int64_t P, int I, const void* A,
+                       int R, double* out) {
+  if (R > 32) return fail(h, TUCKER_ENOTSUP, "R_N > 32 in the TTM kernel");
+  if (is64) return ttm_last_t<double>(h, (const double*)X, P, I, (const double*)A, R, out);
+  return ttm_last_t<float>(h, (const float*)X, P, I, (const float*)A, R, out);
 }
 
 tucker_status ttm_mid(tucker_handle* h, const void* X, int is64, int64_t pre, int I, int64_t post,
@@ -288,10 +444,46 @@ tucker_status ttm_mid(tucker_handle* h, const void* X, int is64, int64_t pre, in
 tucker_status ttm_small(tucker_handle* h, const double* in, int64_t pre, int64_t post,
                         const void* A, int is64, int I, int R, int contract, double* out) {
   const int64_t total = pre * (contract ? R : I) * post;
+  const int K = contract ? I : R;
   TK_COUNT(h);
-  k_ttm_small<<<grid_for(h, total), 256, 0, h->stream>>>(in, pre, post, A, is64, I, R, contract, out);
+  if (K >= 64 && total < (int64_t)h->num_sms * 2048)
+    k_ttm_small_warp<<<grid_for(h, total * 32), 256, 0, h->stream>>>(in, pre, post, A, is64, I, R,
+                                                                    contract, out);
+  else
+    k_ttm_small<<<grid_for(h, total), 256, 0, h->stream>>>(in, pre, post, A, is64, I, R, contract, out);
   TK_LAUNCH(h);
   return TUCKER_OK;
+}
+
+template <class T>
+static tucker_status ttm_last2_t(tucker_handle* h, const T* X, int64_t pre, int I1, int I2,
+                                 const T* A1, int R1, const T* A2, int R2, double* out) {
+  const int RP = R2 <= 4 ? 4 : R2 <= 8 ? 8 : R2 <= 16 ? 16 : 32;
+  const size_t smem = (((size_t)RP * I2 * sizeof(T) + 15) & ~size_t(15)) +
+                      (((size_t)I1 * R1 * sizeof(T) + 15) & ~size_t(15)) + (size_t)8 * R1 * R2 * 8;
+  auto k = RP == 4 ? k_ttm_last2<T, 4> : RP == 8 ? k_ttm_last2<T, 8>
+         : RP == 16 ? k_ttm_last2<T, 16> : k_ttm_last2<T, 32>;
+  TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  TK_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
+  int64_t grid = (int64_t)h->num_sms * (per_sm > 0 ? per_sm : 1);
+  if (grid > pre) grid = pre;
+  TK_COUNT(h);
+  k<<<(int)grid, 256, smem, h->stream>>>(X, pre, I1, I2, A1, R1, A2, R2, out);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+// Can the last two modes be contracted in one streaming pass?
+static bool fused_last2_ok(tucker_handle* h, const FactorSet& F) {
+  const int N = F.N;
+  if (N < 3) return false;
+  const int64_t I1 = F.I[N - 2], I2 = F.I[N - 1];
+  const int R1 = F.R[N - 2], R2 = F.R[N - 1];
+  const int64_t pre = (int64_t)(F.total / (uint64_t)(I1 * I2));
+  const int RP = R2 <= 4 ? 4 : R2 <= 8 ? 8 : R2 <= 16 ? 16 : 32;
+  const size_t smem = (size_t)RP * I2 * (F.is64 ? 8 : 4) + (size_t)I1 * R1 * 8 + 8 * R1 * R2 * 8 + 16;
+  return R2 <= 32 && R1 * R2 <= 256 && R1 <= I1 && pre >= h->num_sms && smem <= 160 * 1024;
 }
 
 // y = X x_1 A^(1)T ... x_N A^(N)T  (all modes), FP64 d-vector.  buf: two
@@ -299,6 +491,28 @@ tucker_status ttm_small(tucker_handle* h, const double* in, int64_t pre, int64_t
 tucker_status ttm_chain_all(tucker_handle* h, const FactorSet& F, const void* X, double* buf0,
                             double* buf1, double* y) {
   const int N = F.N;
+  if (fused_last2_ok(h, F)) {
+    const int I1 = (int)F.I[N - 2], I2 = (int)F.I[N - 1];
+    const int64_t pre = (int64_t)(F.total / (uint64_t)((int64_t)I1 * I2));
+    double* cur = (N == 2) ? y : buf0;
+    if (F.is64)
+      TK_TRY(ttm_last2_t<double>(h, (const double*)X, pre, I1, I2, (const double*)F.A[N - 2],
+                                 F.R[N - 2], (const double*)F.A[N - 1], F.R[N - 1], cur));
+    else
+      TK_TRY(ttm_last2_t<float>(h, (const float*)X, pre, I1, I2, (const float*)F.A[N - 2],
+                                F.R[N - 2], (const float*)F.A[N - 1], F.R[N - 1], cur));
+    int64_t P = pre;
+    int64_t post = (int64_t)F.R[N - 2] * F.R[N - 1];
+    for (int n = N - 3; n >= 0; --n) {
+      const int64_t pr = P / F.I[n];
+      double* nxt = (n == 0) ? y : (cur == buf0 ? buf1 : buf0);
+      TK_TRY(ttm_small(h, cur, pr, post, F.A[n], F.is64, (int)F.I[n], F.R[n], 1, nxt));
+      cur = nxt;
+      P = pr;
+      post *= F.R[n];
+    }
+    return TUCKER_OK;
+  }
   int64_t P = (int64_t)(F.total / (uint64_t)F.I[N - 1]);
   double* cur = (N == 1) ? y : buf0;
   TK_TRY(ttm_last(h, X, F.is64, P, (int)F.I[N - 1], F.A[N - 1], F.R[N - 1], cur));

@@ -156,4 +156,39 @@ tucker_status launch_decode_rows(tucker_handle* h, const FactorSet& F, const uin
   return TUCKER_OK;
 }
 
+// FP64 copies of FP32 factors (the FP64 products with the sampled rows then
+// load doubles instead of converting every entry on the FP64 pipe).
+struct ToF64Args {
+  int N;
+  int64_t len[TUCKER_MAX_ORDER];
+  const float* src[TUCKER_MAX_ORDER];
+  double* dst[TUCKER_MAX_ORDER];
+};
+
+__global__ void k_to_f64(ToF64Args a) {
+  const int n = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.len[n];
+       i += (int64_t)gridDim.x * blockDim.x)
+    a.dst[n][i] = (double)a.src[n][i];
+}
+
+tucker_status launch_to_f64(tucker_handle* h, const FactorSet& F, double* const* out) {
+  ToF64Args a;
+  memset(&a, 0, sizeof(a));
+  a.N = F.N;
+  int64_t mx = 1;
+  for (int n = 0; n < F.N; ++n) {
+    a.len[n] = F.I[n] * F.R[n];
+    a.src[n] = static_cast<const float*>(F.A[n]);
+    a.dst[n] = out[n];
+    if (a.len[n] > mx) mx = a.len[n];
+  }
+  int gx = ceil_div(mx, 256);
+  if (gx > 64) gx = 64;
+  TK_COUNT(h);
+  k_to_f64<<<dim3(gx, F.N), 256, 0, h->stream>>>(a);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
 }  // namespace tk

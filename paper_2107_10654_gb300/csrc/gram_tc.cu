@@ -216,6 +216,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
   float* tab = reinterpret_cast<float*>(opB + TC_STAGES * TC_N * TC_ROWB);   // TSTAGES x sumR x CS
   const int tab_elems = a.sumR * CS;
   float* Ptab = tab + TC_TSTAGES * tab_elems;                 // (N/RN + 2 + M/RN + 2) x CS
+  const int nPB = TC_N / a.RN + 2, nPA = TC_M / a.RN + 2;
+  // decode tables (fixed per tile): T entry offsets of each P row, and for
+  // each operand row its P row and its column of a_N (0xffff: beyond d)
+  int* Poff = reinterpret_cast<int*>(Ptab + (nPB + nPA) * CS);           // (nPB+nPA) x (N-1)
+  uint32_t* rowinfo = reinterpret_cast<uint32_t*>(Poff + (nPB + nPA) * TUCKER_MAX_ORDER);  // 384
   __shared__ uint64_t bar_tfull[TC_TSTAGES], bar_tempty[TC_TSTAGES];
   __shared__ uint64_t bar_ofull[TC_STAGES], bar_oempty[TC_STAGES], bar_done;
   __shared__ uint32_t tmem_slot;
@@ -241,6 +246,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
   const bool a_in_b = row0 >= col0 && row0 + TC_M <= col0 + TC_N;
   const int rho0B = col0 / a.RN, rho0A = row0 / a.RN;
 
+  for (int pr = threadIdx.x; pr < nPB + nPA; pr += blockDim.x) {
+    int rr = pr < nPB ? rho0B + pr : rho0A + (pr - nPB);
+    for (int n = a.N - 2; n >= 0; --n) {
+      Poff[pr * TUCKER_MAX_ORDER + n] = (a.off[n] + rr % a.R[n]) * CS;
+      rr /= a.R[n];
+    }
+  }
+  for (int r = threadIdx.x; r < TC_N + TC_M; r += blockDim.x) {
+    const bool isB = r < TC_N;
+    const int grow = isB ? col0 + r : row0 + (r - TC_N);
+    uint32_t info = 0xffffffffu;
+    if (grow < a.d) {
+      const int rho = grow / a.RN, t = grow - rho * a.RN;
+      const int prow = isB ? rho - rho0B : nPB + (rho - rho0A);
+      info = ((uint32_t)prow << 16) | (uint32_t)t;
+    }
+    rowinfo[r] = info;
+  }
   if (threadIdx.x == 0) {
     for (int i = 0; i < TC_TSTAGES; ++i) { mbar_init(&bar_tfull[i], 1); mbar_init(&bar_tempty[i], TC_BUILD_WARPS * 32); }
     for (int i = 0; i < TC_STAGES; ++i) { mbar_init(&bar_ofull[i], TC_BUILD_WARPS * 32); mbar_init(&bar_oempty[i], 1); }
@@ -294,7 +317,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
   } else {
     // ---------------- builders (warps 0..7)
     const int bt = threadIdx.x;                       // 0..255
-    const int nPB = TC_N / a.RN + 2, nPA = TC_M / a.RN + 2;
     for (int it = 0; it < nchunks; ++it) {
       const int ts = it % TC_TSTAGES, os = it % TC_STAGES;
       const bool ok1 = mbar_wait(&bar_tfull[ts], (it / TC_TSTAGES) & 1, a.status, &abort_flag);
@@ -302,15 +324,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
       if (ok1) {
         // P[rho][s] = prod over modes 1..N-1 of the factor entries of rho
         for (int e = bt; e < (nPB + nPA) * CS; e += TC_BUILD_WARPS * 32) {
-          const int pr = e / CS, s = e % CS;
-          const int rho = pr < nPB ? rho0B + pr : rho0A + (pr - nPB);
+          const int pr = e / CS, s = e % CS;          // CS is a power of two
+          const int* po = Poff + pr * TUCKER_MAX_ORDER;
           float v = 1.f;
-          int rr = rho;
-          for (int n = a.N - 2; n >= 0; --n) {
-            const int rn = rr % a.R[n];
-            rr /= a.R[n];
-            v *= T[(a.off[n] + rn) * CS + s];
-          }
+          for (int n = 0; n < a.N - 1; ++n) v *= T[po[n] + s];
           Ptab[pr * CS + s] = v;
         }
       }
@@ -326,11 +343,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
         const bool isB = uidx < TC_N * 8;
         const int ul = isB ? uidx : uidx - TC_N * 8;
         const int r = ul >> 3, c = ul & 7;
-        const int grow = (isB ? col0 : row0) + r;
+        const uint32_t info = rowinfo[isB ? r : TC_N + r];
         uint4 out = make_uint4(0, 0, 0, 0);
-        if (grow < a.d) {
-          const int rho = grow / a.RN, t = grow - rho * a.RN;
-          const float* P = Ptab + (isB ? (rho - rho0B) : nPB + (rho - rho0A)) * CS;
+        if (info != 0xffffffffu) {
+          const int t = (int)(info & 0xffffu);
+          const float* P = Ptab + (int)(info >> 16) * CS;
           const int s0 = c * Tr::PER16;
           if (PREC == TUCKER_PREC_BF16) {
             const float4 p0 = *reinterpret_cast<const float4*>(P + s0);
@@ -457,7 +474,8 @@ static size_t tc_smem_bytes(int sumR, int RN, int CS) {
   const size_t ops = (size_t)TC_STAGES * (TC_M + TC_N) * TC_ROWB;
   const size_t tab = (size_t)TC_TSTAGES * sumR * CS * 4;
   const size_t P = (size_t)(TC_N / RN + 2 + TC_M / RN + 2) * CS * 4;
-  return ops + tab + P + 1024;
+  const size_t dec = (size_t)(TC_N / RN + 2 + TC_M / RN + 2) * TUCKER_MAX_ORDER * 4 + (TC_M + TC_N) * 4;
+  return ops + tab + P + dec + 1024;
 }
 
 size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int sumR, int64_t cap) {

@@ -22,11 +22,58 @@ struct LevArgs {
   double* gram[TUCKER_MAX_ORDER];    // nullable: R x R Gram before diagonalisation
   int* rank;                          // device int[N]
   int* status;
+  double* gpart[TUCKER_MAX_ORDER];    // [nchunk][R(R+1)/2] partial Grams
+  int nchunk;
 };
 
-constexpr int LEV_THREADS = 256;
+// Partial Gram of rows [chunk * rows_per, ...) of every mode (grid: chunk x mode).
+// Row tile staged in shared memory as FP64; thread -> (pair, row phase), then
+// a fixed-order reduction over the phases.
+constexpr int GP_ROWS = 256;
+__global__ void __launch_bounds__(256) k_gram_partial(LevArgs a) {
+  extern __shared__ double st[];                      // GP_ROWS x R, then 256 partials
+  const int n = blockIdx.y, ch = blockIdx.x;
+  const int R = a.F.R[n];
+  const int64_t I = a.F.I[n];
+  const int64_t i0 = (int64_t)ch * GP_ROWS;
+  const int npairs = R * (R + 1) / 2;
+  double* red = st + GP_ROWS * R;
+  const int rows = (int)(i0 < I ? ((I - i0) < GP_ROWS ? (I - i0) : GP_ROWS) : 0);
+  for (int e = threadIdx.x; e < rows * R; e += blockDim.x)
+    st[e] = load_as_double(a.F.A[n], i0 * R + e, a.F.is64);
+  __syncthreads();
+  const int phases = npairs >= 256 ? 1 : 256 / npairs;
+  for (int base = 0; base < npairs; base += 256 / phases) {
+    const int pidx = base + threadIdx.x / phases, ph = threadIdx.x % phases;
+    double v = 0.0;
+    if (pidx < npairs && threadIdx.x / phases < 256 / phases) {
+      int r = 0, rem = pidx;
+      while (rem >= R - r) { rem -= R - r; ++r; }
+      const int c = r + rem;
+      for (int i = ph; i < rows; i += phases) v = fma(st[i * R + r], st[i * R + c], v);
+    }
+    red[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < 256 / phases) {
+      const int pi = base + threadIdx.x;
+      if (pi < npairs) {
+        double sum = 0.0;
+        for (int q = 0; q < phases; ++q) sum += red[threadIdx.x * phases + q];
+        a.gpart[n][(size_t)ch * npairs + pi] = sum;
+      }
+    }
+    __syncthreads();
+  }
+}
 
-__global__ void __launch_bounds__(LEV_THREADS) k_leverage(LevArgs a) {
+constexpr int LEV_THREADS = 256;
+constexpr int LEV_STAGE = 4096;               // doubles of staged factor rows
+constexpr int LEV_PAIRS_PER_THREAD = (64 * 65 / 2 + LEV_THREADS - 1) / LEV_THREADS;
+
+// Per mode: Gram (all warps), Jacobi eigendecomposition (warp 0, warp-
+// synchronous), and W = V diag(ev^-1/2) with the columns of eigenvalues
+// <= tol zeroed, so that l_i = || a_i W ||^2 = a_i G^+ a_i^T.
+__global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a, double* const* Wout) {
   extern __shared__ double sm[];
   const int n = blockIdx.x;
   const int R = a.F.R[n];
@@ -40,141 +87,142 @@ __global__ void __launch_bounds__(LEV_THREADS) k_leverage(LevArgs a) {
   double* sn = cs + Rp / 2;                   // Rp/2 sin
   int* pp = reinterpret_cast<int*>(sn + Rp / 2);
   int* qq = pp + Rp / 2;
-  double* red = reinterpret_cast<double*>(qq + Rp / 2 + 2);  // 64 doubles
-  __shared__ int64_t scan_tmp[32];
-  __shared__ int s_done;
-
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
 
-  // 1. Gram (upper triangle, mirrored), padded entries zero.
   for (int e = tid; e < Rp * Rp; e += blockDim.x) {
     G[e] = 0.0;
     V[e] = (e / Rp == e % Rp) ? 1.0 : 0.0;
   }
   __syncthreads();
+  // Gram = sum of the per-chunk partial Grams (fixed order)
+  (void)A; (void)is64; (void)nw; (void)wid;
   const int npairs = R * (R + 1) / 2;
-  for (int pidx = wid; pidx < npairs; pidx += nw) {
-    // decode pidx -> (r, c) with r <= c
+  for (int pidx = tid; pidx < npairs; pidx += blockDim.x) {
     int r = 0, rem = pidx;
     while (rem >= R - r) { rem -= R - r; ++r; }
-    int c = r + rem;
-    double s = 0.0;
-    for (int64_t i = lane; i < I; i += 32)
-      s += load_as_double(A, i * R + r, is64) * load_as_double(A, i * R + c, is64);
-    s = warp_sum(s);
-    if (lane == 0) { G[r * Rp + c] = s; G[c * Rp + r] = s; }
+    const int c = r + rem;
+    double v = 0.0;
+    for (int ch = 0; ch < a.nchunk; ++ch) v += a.gpart[n][(size_t)ch * npairs + pidx];
+    G[r * Rp + c] = v;
+    G[c * Rp + r] = v;
   }
+  (void)I;
   __syncthreads();
   if (a.gram[n])
     for (int e = tid; e < R * R; e += blockDim.x) a.gram[n][e] = G[(e / R) * Rp + e % R];
-
-  // 2. Jacobi sweeps.
-  const int half = Rp / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    // convergence test: off-diagonal mass vs diagonal mass
-    double off = 0.0, dia = 0.0;
-    for (int e = tid; e < Rp * Rp; e += blockDim.x) {
-      double v = G[e] * G[e];
-      if (e / Rp == e % Rp) dia += v; else off += v;
-    }
-    off = warp_sum(off);
-    dia = warp_sum(dia);
-    if (lane == 0) { red[wid] = off; red[32 + wid] = dia; }
-    __syncthreads();
-    if (tid == 0) {
-      double o = 0.0, g = 0.0;
-      for (int w = 0; w < nw; ++w) { o += red[w]; g += red[32 + w]; }
-      s_done = (o <= 1e-30 * g) || Rp <= 1;
-    }
-    __syncthreads();
-    if (s_done) break;
-    for (int step = 0; step < Rp - 1; ++step) {
-      if (tid < half) {
-        // circle method: slot 0 fixed, slots 1..Rp-1 rotate by `step`
-        int k = tid;
-        int s0 = k, s1 = Rp - 1 - k;
-        int p = s0 == 0 ? 0 : ((s0 - 1 + step) % (Rp - 1)) + 1;
-        int q = ((s1 - 1 + step) % (Rp - 1)) + 1;
-        if (p > q) { int t = p; p = q; q = t; }
-        double apq = G[p * Rp + q], app = G[p * Rp + p], aqq = G[q * Rp + q];
-        double c = 1.0, s = 0.0;
-        if (apq != 0.0 && fabs(apq) > 1e-300) {
-          double theta = (aqq - app) / (2.0 * apq);
-          double t;
-          if (fabs(theta) > 1e150) t = 0.5 / theta;
-          else t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
-          s = t * c;
+  if (wid == 0) {
+    const int half = Rp / 2;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+      double off = 0.0, dia = 0.0;
+      for (int e = lane; e < Rp * Rp; e += 32) {
+        const double v = G[e] * G[e];
+        if (e / Rp == e % Rp) dia += v; else off += v;
+      }
+      off = warp_sum(off);
+      dia = warp_sum(dia);
+      if (off <= 1e-28 * dia || Rp <= 1) break;
+      for (int step = 0; step < Rp - 1; ++step) {
+        for (int k = lane; k < half; k += 32) {
+          // circle method: slot 0 fixed, slots 1..Rp-1 rotate by `step`
+          const int s1 = Rp - 1 - k;
+          int p = k == 0 ? 0 : ((k - 1 + step) % (Rp - 1)) + 1;
+          int q = ((s1 - 1 + step) % (Rp - 1)) + 1;
+          if (p > q) { const int t = p; p = q; q = t; }
+          const double apq = G[p * Rp + q], app = G[p * Rp + p], aqq = G[q * Rp + q];
+          double c = 1.0, s = 0.0;
+          if (fabs(apq) > 1e-16 * fabs(app + aqq) && fabs(apq) > 1e-300) {
+            // tangent of the rotation angle in FP32 (an approximate annihilation
+            // is enough for Jacobi); (c, s) formed in FP64 so that the
+            // rotation is orthogonal to FP64 rounding
+            const float theta = (float)((aqq - app) / (2.0 * apq));
+            float tf;
+            if (fabsf(theta) > 1e18f) tf = 0.5f / theta;
+            else tf = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+            const double t = (double)tf;
+            const double q2 = fma(t, t, 1.0);
+            double y = (double)rsqrtf((float)q2);          // Newton-Raphson for 1/sqrt(q2)
+            y = y * fma(-0.5 * q2, y * y, 1.5);
+            y = y * fma(-0.5 * q2, y * y, 1.5);
+            c = y;
+            s = t * y;
+          }
+          cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
         }
-        cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
+        __syncwarp();
+        for (int e = lane; e < half * Rp; e += 32) {      // rows p, q
+          const int k = e / Rp, j = e % Rp;
+          const int p = pp[k], q = qq[k];
+          const double c = cs[k], s = sn[k];
+          const double gp = G[p * Rp + j], gq = G[q * Rp + j];
+          G[p * Rp + j] = c * gp - s * gq;
+          G[q * Rp + j] = s * gp + c * gq;
+        }
+        __syncwarp();
+        for (int e = lane; e < half * Rp; e += 32) {      // columns p, q (and V)
+          const int k = e / Rp, i = e % Rp;
+          const int p = pp[k], q = qq[k];
+          const double c = cs[k], s = sn[k];
+          const double gp = G[i * Rp + p], gq = G[i * Rp + q];
+          G[i * Rp + p] = c * gp - s * gq;
+          G[i * Rp + q] = s * gp + c * gq;
+          const double vp = V[i * Rp + p], vq = V[i * Rp + q];
+          V[i * Rp + p] = c * vp - s * vq;
+          V[i * Rp + q] = s * vp + c * vq;
+        }
+        __syncwarp();
       }
-      __syncthreads();
-      for (int e = tid; e < half * Rp; e += blockDim.x) {      // rows p, q
-        int k = e / Rp, j = e % Rp;
-        int p = pp[k], q = qq[k];
-        double c = cs[k], s = sn[k];
-        double gp = G[p * Rp + j], gq = G[q * Rp + j];
-        G[p * Rp + j] = c * gp - s * gq;
-        G[q * Rp + j] = s * gp + c * gq;
-      }
-      __syncthreads();
-      for (int e = tid; e < half * Rp; e += blockDim.x) {      // columns p, q (and V)
-        int k = e / Rp, i = e % Rp;
-        int p = pp[k], q = qq[k];
-        double c = cs[k], s = sn[k];
-        double gp = G[i * Rp + p], gq = G[i * Rp + q];
-        G[i * Rp + p] = c * gp - s * gq;
-        G[i * Rp + q] = s * gp + c * gq;
-        double vp = V[i * Rp + p], vq = V[i * Rp + q];
-        V[i * Rp + p] = c * vp - s * vq;
-        V[i * Rp + q] = s * vp + c * vq;
-      }
-      __syncthreads();
     }
-  }
-
-  // 3. eigenvalues, tolerance, rank
-  if (tid == 0) {
+    // eigenvalues, tolerance, rank, W
     double emax = 0.0;
     for (int k = 0; k < R; ++k) emax = fmax(emax, G[k * Rp + k]);
-    double tol = double(I > R ? I : R) * 2.220446049250313e-16 * emax;
+    const double tol = double(I > R ? I : R) * 2.220446049250313e-16 * emax;
     int rk = 0;
     for (int k = 0; k < R; ++k) rk += G[k * Rp + k] > tol;
-    red[0] = tol;
-    a.rank[n] = rk;
-  }
-  __syncthreads();
-  const double tol = red[0];
-  if (a.evecs[n])
-    for (int e = tid; e < R * R; e += blockDim.x) a.evecs[n][e] = V[(e / R) * Rp + e % R];
-  if (a.evals[n])
-    for (int k = tid; k < R; k += blockDim.x) a.evals[n][k] = G[k * Rp + k];
-
-  // 4. scores, fixed point, inclusive prefix sum in chunks of blockDim
-  uint64_t carry = 0;
-  for (int64_t base = 0; base < I; base += blockDim.x) {
-    int64_t i = base + tid;
-    uint64_t q = 0;
-    if (i < I) {
-      double l = 0.0;
-      for (int k = 0; k < R; ++k) {
-        double ev = G[k * Rp + k];
-        if (!(ev > tol)) continue;
-        double pr = 0.0;
-        for (int r = 0; r < R; ++r) pr += load_as_double(A, i * R + r, is64) * V[r * Rp + k];
-        l += pr * pr / ev;
-      }
-      a.lev[n][i] = l;
-      double v = fmin(fmax(l, 0.0), 1.0) * 4294967296.0;
-      q = (uint64_t)__double2ull_rz(v);
+    if (lane == 0) a.rank[n] = rk;
+    for (int e = lane; e < R * R; e += 32) {
+      const int r = e / R, k = e % R;
+      const double ev = G[k * Rp + k];
+      Wout[n][e] = ev > tol ? V[r * Rp + k] / sqrt(ev) : 0.0;
+      if (a.evecs[n]) a.evecs[n][e] = V[r * Rp + k];
     }
-    int64_t tot;
-    int64_t ex = block_exclusive_scan((int64_t)q, scan_tmp, &tot);
-    if (i < I) a.cdf[n][i] = carry + (uint64_t)ex + q;
-    carry += (uint64_t)tot;
+    if (a.evals[n])
+      for (int k = lane; k < R; k += 32) a.evals[n][k] = G[k * Rp + k];
   }
-  if (tid == 0 && carry == 0) set_status(a.status, DEV_RANK);
 }
+
+// l_i = || a_i W ||^2 for every row of every mode (grid y = mode).
+struct LevRowArgs {
+  int N;
+  int64_t I[TUCKER_MAX_ORDER];
+  int R[TUCKER_MAX_ORDER];
+  const void* A[TUCKER_MAX_ORDER];
+  int is64;
+  const double* W[TUCKER_MAX_ORDER];
+  double* lev[TUCKER_MAX_ORDER];
+};
+
+__global__ void __launch_bounds__(256) k_leverage_rows(LevRowArgs a) {
+  extern __shared__ double Ws[];
+  const int n = blockIdx.y;
+  const int R = a.R[n];
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Ws[e] = a.W[n][e];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.I[n];
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double row[TUCKER_MAX_RANK];
+    for (int r = 0; r < R; ++r) row[r] = load_as_double(a.A[n], i * R + r, a.is64);
+    double l = 0.0;
+    for (int k = 0; k < R; ++k) {
+      double p = 0.0;
+      for (int r = 0; r < R; ++r) p = fma(row[r], Ws[r * R + k], p);
+      l = fma(p, p, l);
+    }
+    a.lev[n][i] = l;
+  }
+}
+
+tucker_status launch_cdf_from_lev(tucker_handle* h, int N, const int64_t* I,
+                                  const double* const* lev, uint64_t* const* cdf);
 
 // q_i = floor(clamp(l_i,0,1) 2^32) and inclusive prefix sums from given scores
 // (the sampler's integer CDF), one CTA per mode.
@@ -225,26 +273,70 @@ tucker_status launch_leverage(tucker_handle* h, const FactorSet& F, double* cons
   LevArgs a;
   memset(&a, 0, sizeof(a));
   a.F = F;
-  int maxRp = 0;
+  int maxRp = 0, maxR = 0;
+  int64_t maxI = 1;
   for (int n = 0; n < F.N; ++n) {
     a.lev[n] = lev[n];
     a.cdf[n] = cdf[n];
     a.evecs[n] = evecs ? evecs[n] : nullptr;
     a.evals[n] = evals ? evals[n] : nullptr;
     a.gram[n] = gram_out ? gram_out[n] : nullptr;
-    int Rp = F.R[n] + (F.R[n] & 1);
+    const int Rp = F.R[n] + (F.R[n] & 1);
     if (Rp > maxRp) maxRp = Rp;
+    if (F.R[n] > maxR) maxR = F.R[n];
+    if (F.I[n] > maxI) maxI = F.I[n];
   }
   a.rank = d_rank;
   a.status = h->d_status;
-  size_t smem = size_t(2 * maxRp * maxRp + maxRp) * sizeof(double) +
-                size_t(maxRp + 2) * sizeof(int) + 64 * sizeof(double) + 64;
-  TK_CUDA(h, cudaFuncSetAttribute(k_leverage, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  // W matrices live in the rank buffer's neighbourhood: use the handle's
+  // small device scratch after the rank ints (d_rank is carved with room).
+  double* Wbuf = reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(d_rank + 2 * TUCKER_MAX_ORDER + 64) & ~uintptr_t(255));
+  double* W[TUCKER_MAX_ORDER];
+  LevRowArgs ra;
+  memset(&ra, 0, sizeof(ra));
+  ra.N = F.N;
+  ra.is64 = F.is64;
+  for (int n = 0; n < F.N; ++n) {
+    W[n] = Wbuf + (size_t)n * TUCKER_MAX_RANK * TUCKER_MAX_RANK;
+    ra.I[n] = F.I[n]; ra.R[n] = F.R[n]; ra.A[n] = F.A[n]; ra.W[n] = W[n]; ra.lev[n] = lev[n];
+  }
+  double** Wdev = reinterpret_cast<double**>(Wbuf + (size_t)TUCKER_MAX_ORDER * TUCKER_MAX_RANK * TUCKER_MAX_RANK);
+  TK_CUDA(h, cudaMemcpyAsync(Wdev, W, sizeof(W), cudaMemcpyHostToDevice, h->stream));
+  // partial Grams behind the W matrices
+  double* gp = reinterpret_cast<double*>(Wdev + TUCKER_MAX_ORDER);
+  a.nchunk = (int)((maxI + GP_ROWS - 1) / GP_ROWS);
+  for (int n = 0; n < F.N; ++n) {
+    a.gpart[n] = gp;
+    gp += (size_t)a.nchunk * (F.R[n] * (F.R[n] + 1) / 2);
+  }
+  const size_t gsm = (size_t)(GP_ROWS * maxR + 256) * sizeof(double);
+  TK_CUDA(h, cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)gsm));
+  TK_COUNT(h);
+  k_gram_partial<<<dim3(a.nchunk, F.N), 256, gsm, h->stream>>>(a);
+  TK_LAUNCH(h);
+  const size_t smem = size_t(2 * maxRp * maxRp + maxRp) * sizeof(double) +
+                      size_t(maxRp + 2) * sizeof(int) + 64;
+  TK_CUDA(h, cudaFuncSetAttribute(k_leverage_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
   TK_COUNT(h);
-  k_leverage<<<F.N, LEV_THREADS, smem, h->stream>>>(a);
+  k_leverage_eig<<<F.N, LEV_THREADS, smem, h->stream>>>(a, Wdev);
   TK_LAUNCH(h);
-  return TUCKER_OK;
+  int gx = (int)((maxI + 255) / 256);
+  if (gx > 64) gx = 64;
+  TK_COUNT(h);
+  k_leverage_rows<<<dim3(gx, F.N), 256, (size_t)maxR * maxR * sizeof(double), h->stream>>>(ra);
+  TK_LAUNCH(h);
+  return launch_cdf_from_lev(h, F.N, F.I, lev, cdf);
+}
+
+// Device bytes the leverage launcher needs behind its rank pointer.
+size_t leverage_aux_bytes(int64_t maxI) {
+  const size_t nchunk = (size_t)((maxI + GP_ROWS - 1) / GP_ROWS);
+  return (2 * TUCKER_MAX_ORDER + 64) * sizeof(int) + 256 +
+         (size_t)TUCKER_MAX_ORDER * TUCKER_MAX_RANK * TUCKER_MAX_RANK * sizeof(double) +
+         TUCKER_MAX_ORDER * sizeof(double*) + 64 +
+         nchunk * TUCKER_MAX_ORDER * (TUCKER_MAX_RANK * (TUCKER_MAX_RANK + 1) / 2) * sizeof(double);
 }
 
 }  // namespace tk

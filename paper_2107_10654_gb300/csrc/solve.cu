@@ -1,29 +1,38 @@
 // Ridge solve of the (sketched or exact) normal equations (Eq. problem_def;
 // Appendix B, proof of Thm 4.2): M = G + diag(regdiag), M = L L^T by a blocked
-// right-looking FP64 Cholesky, then L y = h and L^T g = y.
+// right-looking Cholesky, then L y = h and L^T g = y.
 //
-// Cholesky step for panel k (width CB):
-//   k_potrf_diag     factor the CB x CB diagonal block in shared memory; a
-//                    non-positive or NaN pivot records TUCKER_ENOTSPD and all
-//                    later kernels return immediately (no trap, no hang);
-//   k_trsm_panel     rows below: A[i, k:k+CB] <- A[i, k:k+CB] L_kk^-T;
-//   k_syrk_trailing  A[i, j] -= A[i, k:k+CB] . A[j, k:k+CB] on the lower trailing
-//                    triangle, 64x64 tiles, FP64 FMA.
+// The factorisation and the triangular solves are templated on the element
+// type: FP64 (the FP64 Cholesky solver) or FP32 (the mixed solver, where the
+// FP32 factor only preconditions an FP64 iterative refinement; see api.cu).
+//
+// Cholesky: one persistent cooperative launch (one CTA per SM, grid-wide
+// barriers between phases).  Step k (panel width CB):
+//   phase 1: every CTA factors the CB x CB diagonal block in shared memory
+//            (the same arithmetic in every CTA, so all agree on a failed
+//            pivot and leave together); CTA 0 stores L_kk; each warp solves
+//            one panel row  L_ik = A_ik L_kk^-T;
+//   phase 2: lower trailing tiles A_ij -= L_ik L_jk^T (CT x CT), distributed
+//            over the CTAs.
+// A non-positive or NaN pivot records TUCKER_ENOTSPD (no trap, no hang).
 // L overwrites the lower triangle of M (row-major, d x d).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace tk {
 
 constexpr int CB = 32;      // panel width
-constexpr int CT = 64;      // trailing tile
+constexpr int CT = 32;      // trailing tile (small: one step spreads over many SMs)
+constexpr int SB = 64;      // block of the triangular solves
 
 __global__ void k_add_diag(double* M, int d, const double* diag) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x)
     M[(size_t)i * d + i] += diag[i];
-}
-
-__global__ void k_fill(double* v, int n, double val) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = val;
 }
 
 // regdiag[j] = lambda (exact) or lambda * D[j] (augmented)
@@ -32,194 +41,364 @@ __global__ void k_regdiag(double* out, int d, double lambda, const double* D) {
     out[i] = D ? lambda * D[i] : lambda;
 }
 
-__global__ void __launch_bounds__(256) k_potrf_diag(double* M, int d, int k, int* status) {
-  __shared__ double a[CB][CB + 1];
+__global__ void k_to_f32(const double* in, size_t n, float* out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// 1/sqrt(p) for p > 0.  FP64: an FP32 seed refined by two Newton-Raphson
+// steps for f(y) = 1/y^2 - p, y <- y (3 - p y^2) / 2 (each step doubles the
+// correct bits: 23 -> 46 -> full FP64), on an exactly power-of-two-scaled p.
+// Cheaper on the FP64 pipe than a square root and a divide.
+__device__ __forceinline__ double rsqrt_piv(double p) {
+  int e;
+  double m = frexp(p, &e);                   // p = m 2^e exactly, m in [0.5, 1)
+  if (e & 1) { m *= 2.0; e -= 1; }           // e even, m in [0.5, 2)
+  double y = (double)rsqrtf((float)m);
+  y = y * fma(-0.5 * m, y * y, 1.5);
+  y = y * fma(-0.5 * m, y * y, 1.5);
+  return ldexp(y, -e / 2);
+}
+__device__ __forceinline__ float rsqrt_piv(float p) { return rsqrtf(p); }
+
+template <class T> __device__ __forceinline__ T tmax();
+template <> __device__ __forceinline__ double tmax<double>() { return 1.7976931348623157e308; }
+template <> __device__ __forceinline__ float tmax<float>() { return 3.402823466e38f; }
+
+// Factor the nb x nb diagonal block at (k, k) in shared memory (all threads).
+// One thread forms each pivot's l_jj = p / sqrt(p) and 1/l_jj; the trailing
+// entries (i, c), j < c <= i, are packed densely over the threads.  Returns
+// false on a non-positive or NaN pivot; every CTA computes the same.
+template <class T>
+__device__ bool factor_diag_block(const T* M, int d, int k, int nb, T (*a)[CB + 1]) {
   __shared__ int bad;
-  if (*status) return;
-  const int nb = min(CB, d - k);
+  __shared__ T rp;
   for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
-    int i = e / CB, j = e % CB;
-    a[i][j] = (i < nb && j < nb) ? M[(size_t)(k + i) * d + k + j] : 0.0;
+    const int i = e / CB, j = e % CB;
+    a[i][j] = (i < nb && j < nb) ? M[(size_t)(k + i) * d + k + j] : T(0);
   }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
     if (threadIdx.x == 0) {
-      double p = a[j][j];
-      if (!(p > 0.0)) { bad = 1; set_status(status, DEV_NOTSPD); }
-      a[j][j] = sqrt(fmax(p, 0.0));
+      const T p = a[j][j];
+      if (!(p > T(0)) || !(p <= tmax<T>())) {
+        bad = 1;
+      } else {
+        const T y = rsqrt_piv(p);
+        a[j][j] = p * y;
+        rp = y;
+      }
     }
     __syncthreads();
-    if (bad) return;
-    const double djj = a[j][j];
-    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][j] /= djj;
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-      int i = e / nb, c = e % nb;
-      if (c > j && i >= c) a[i][c] -= a[i][j] * a[c][j];
+    if (bad) return false;
+    const T r = rp;
+    const int m = nb - j - 1;                       // trailing size
+    for (int e = threadIdx.x; e < m * (m + 1) / 2; e += blockDim.x) {
+      // row-major packing of the lower triangle of the trailing block
+      int ii = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+      while (ii * (ii + 1) / 2 > e) --ii;
+      const int cc = e - ii * (ii + 1) / 2;
+      const int i = j + 1 + ii, c = j + 1 + cc;     // j < c <= i
+      a[i][c] = fma(-(a[i][j] * r), a[c][j] * r, a[i][c]);
     }
     __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][j] *= r;
+    __syncthreads();
   }
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    int i = e / nb, j = e % nb;
-    if (j <= i) M[(size_t)(k + i) * d + k + j] = a[i][j];
-  }
+  return true;
 }
 
-__global__ void __launch_bounds__(128) k_trsm_panel(double* M, int d, int k, const int* status) {
-  __shared__ double L[CB][CB + 1];
-  if (*status) return;
-  const int nb = min(CB, d - k);
-  for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
-    int i = e / CB, j = e % CB;
-    L[i][j] = (i < nb && j < nb && j <= i) ? M[(size_t)(k + i) * d + k + j] : 0.0;
-  }
-  __syncthreads();
-  const int row = k + nb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= d) return;
-  double x[CB];
-  double* mrow = M + (size_t)row * d + k;
-#pragma unroll
-  for (int c = 0; c < CB; ++c) x[c] = c < nb ? mrow[c] : 0.0;
-#pragma unroll
-  for (int c = 0; c < CB; ++c) {
-    if (c >= nb) break;
-    double v = x[c];
-#pragma unroll
-    for (int cc = 0; cc < CB; ++cc)
-      if (cc < c) v -= x[cc] * L[c][cc];
-    x[c] = v / L[c][c];
-  }
-#pragma unroll
-  for (int c = 0; c < CB; ++c) if (c < nb) mrow[c] = x[c];
-}
-
-__global__ void __launch_bounds__(256) k_syrk_trailing(double* M, int d, int k, const int* status) {
-  __shared__ double Pa[CT][CB + 1];
-  __shared__ double Pb[CT][CB + 1];
-  if (*status) return;
-  const int s = k + CB;                       // trailing start
-  const int Tt = (d - s + CT - 1) / CT;
-  int ti = 0, rem = blockIdx.x;               // lower-triangle tile (ti >= tj)
-  while (rem > ti) { rem -= ti + 1; ++ti; }
-  const int tj = rem;
-  if (ti >= Tt) return;
-  const int r0 = s + ti * CT, c0 = s + tj * CT;
-  for (int e = threadIdx.x; e < CT * CB; e += blockDim.x) {
-    int i = e / CB, c = e % CB;
-    Pa[i][c] = (r0 + i < d) ? M[(size_t)(r0 + i) * d + k + c] : 0.0;
-    Pb[i][c] = (c0 + i < d) ? M[(size_t)(c0 + i) * d + k + c] : 0.0;
-  }
-  __syncthreads();
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4] = {};
-#pragma unroll 8
-  for (int c = 0; c < CB; ++c) {
-    double a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) { a[i] = Pa[ty * 4 + i][c]; b[i] = Pb[tx * 4 + i][c]; }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = r0 + ty * 4 + i;
-    if (r >= d) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = c0 + tx * 4 + j;
-      if (c < d && c <= r) M[(size_t)r * d + c] -= acc[i][j];
-    }
-  }
-}
-
-tucker_status cholesky(tucker_handle* h, double* M, int d) {
+template <class T>
+__global__ void __launch_bounds__(256) k_chol_coop(T* M, int d, int* status) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ T Lkk[CB][CB + 1];
+  __shared__ T rinv[CB];
+  __shared__ T Pa[CT][CB + 1];
+  __shared__ T Pb[CT][CB + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int k = 0; k < d; k += CB) {
-    TK_COUNT(h);
-    k_potrf_diag<<<1, 256, 0, h->stream>>>(M, d, k, h->d_status);
-    const int rows = d - k - CB;
-    if (rows > 0) {
-      TK_COUNT(h);
-      k_trsm_panel<<<ceil_div(rows, 128), 128, 0, h->stream>>>(M, d, k, h->d_status);
-      const int Tt = ceil_div(rows, CT);
-      TK_COUNT(h);
-      k_syrk_trailing<<<Tt * (Tt + 1) / 2, 256, 0, h->stream>>>(M, d, k, h->d_status);
+    const int nb = min(CB, d - k);
+    if (!factor_diag_block<T>(M, d, k, nb, Lkk)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, DEV_NOTSPD);
+      return;                                   // every CTA takes this branch at the same k
     }
+    if (threadIdx.x < CB)
+      rinv[threadIdx.x] = threadIdx.x < nb ? T(1) / Lkk[threadIdx.x][threadIdx.x] : T(0);
+    if (blockIdx.x == 0)
+      for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int i = e / nb, j = e % nb;
+        if (j <= i) M[(size_t)(k + i) * d + k + j] = Lkk[i][j];
+      }
+    __syncthreads();
+    // panel rows below the diagonal block: one warp per row, lane c owns column c
+    for (int row = k + nb + blockIdx.x * nwarps + warp; row < d; row += gridDim.x * nwarps) {
+      T* mrow = M + (size_t)row * d + k;
+      T x = lane < nb ? mrow[lane] : T(0);
+      T acc = T(0);                             // sum_{cc < lane} x_cc L[lane][cc]
+      for (int c = 0; c < nb; ++c) {
+        const T xc = __shfl_sync(0xffffffffu, (x - acc) * rinv[lane], c);
+        if (lane == c) x = xc;
+        if (lane > c) acc = fma(xc, Lkk[lane][c], acc);
+      }
+      if (lane < nb) mrow[lane] = x;
+    }
+    grid.sync();
+    const int s = k + nb;
+    if (s < d) {
+      const int Tt = (d - s + CT - 1) / CT;
+      const int ntiles = Tt * (Tt + 1) / 2;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int ti = 0, rem = tile;
+        while (rem > ti) { rem -= ti + 1; ++ti; }
+        const int tj = rem;
+        const int r0 = s + ti * CT, c0 = s + tj * CT;
+        __syncthreads();
+        for (int e = threadIdx.x; e < CT * CB; e += blockDim.x) {
+          const int i = e / CB, c = e % CB;
+          Pa[i][c] = (r0 + i < d && c < nb) ? M[(size_t)(r0 + i) * d + k + c] : T(0);
+          Pb[i][c] = (c0 + i < d && c < nb) ? M[(size_t)(c0 + i) * d + k + c] : T(0);
+        }
+        __syncthreads();
+        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 2 x 2 outputs each
+        T acc[2][2] = {};
+#pragma unroll 8
+        for (int c = 0; c < CB; ++c) {
+          const T a0 = Pa[ty * 2][c], a1 = Pa[ty * 2 + 1][c];
+          const T b0 = Pb[tx * 2][c], b1 = Pb[tx * 2 + 1][c];
+          acc[0][0] = fma(a0, b0, acc[0][0]);
+          acc[0][1] = fma(a0, b1, acc[0][1]);
+          acc[1][0] = fma(a1, b0, acc[1][0]);
+          acc[1][1] = fma(a1, b1, acc[1][1]);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int r = r0 + ty * 2 + i;
+          if (r >= d) continue;
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const int c = c0 + tx * 2 + j;
+            if (c < d && c <= r) M[(size_t)r * d + c] -= acc[i][j];
+          }
+        }
+      }
+    }
+    grid.sync();
   }
+}
+
+static int coop_grid(tucker_handle* h, const void* kernel, int threads, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return h->num_sms;                         // one CTA per SM
+}
+
+template <class T>
+tucker_status cholesky_t(tucker_handle* h, T* M, int d) {
+  const void* kern = (const void*)k_chol_coop<T>;
+  const int grid = coop_grid(h, kern, 256, 0);
+  if (grid < 1) return fail(h, TUCKER_ECUDA, "cooperative Cholesky cannot be resident");
+  void* args[] = {&M, &d, &h->d_status};
+  TK_COUNT(h);
+  TK_CUDA(h, cudaLaunchCooperativeKernel(kern, grid, 256, args, 0, h->stream));
+  return TUCKER_OK;
+}
+
+tucker_status cholesky(tucker_handle* h, double* M, int d) { return cholesky_t<double>(h, M, d); }
+tucker_status cholesky32(tucker_handle* h, float* M, int d) { return cholesky_t<float>(h, M, d); }
+
+// ------------------------------------------------------------ triangular solves
+// Inverses of the SB x SB diagonal blocks of L (one CTA per block, thread j
+// forward-substitutes column j of the identity); then each solve is one
+// persistent launch: per block, every CTA forms y_k = Linv_kk b_k in shared
+// memory and removes it from its share of the remaining rows (warp per row),
+// with one grid-wide barrier per block.  Forward L y = b, then backward
+// L^T g = y reading the transposed factor row-wise.
+
+template <class T>
+__global__ void __launch_bounds__(SB) k_inv_diag_blocks(const T* L, int d, T* Linv) {
+  __shared__ T a[SB][SB + 1];
+  __shared__ T rp[SB];
+  const int k = blockIdx.x * SB, nb = min(SB, d - k);
+  for (int e = threadIdx.x; e < SB * SB; e += blockDim.x) {
+    const int i = e / SB, j = e % SB;
+    a[i][j] = (i < nb && j < nb && j <= i) ? L[(size_t)(k + i) * d + k + j] : (i == j ? T(1) : T(0));
+  }
+  __syncthreads();
+  rp[threadIdx.x] = T(1) / a[threadIdx.x][threadIdx.x];
+  __syncthreads();
+  const int j = threadIdx.x;                      // column j of the inverse
+  T x[SB];
+#pragma unroll
+  for (int i = 0; i < SB; ++i) {
+    T v = (i == j) ? T(1) : T(0);
+#pragma unroll
+    for (int c = 0; c < i; ++c) v = fma(-a[i][c], x[c], v);
+    x[i] = (i < j) ? T(0) : v * rp[i];
+  }
+  T* out = Linv + (size_t)blockIdx.x * SB * SB;
+#pragma unroll
+  for (int i = 0; i < SB; ++i) out[i * SB + j] = x[i];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_trsv_coop(const T* L, const T* LT, const T* Linv, int d,
+                                                   double* b, double* y, const int* status) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ T yk[SB];
+  __shared__ T bk[SB];
+  __shared__ T Ls[SB][SB + 1];
+  if (*status) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int nblk = (d + SB - 1) / SB;
+  // forward: L y = b   (b is consumed as workspace)
+  for (int kb = 0; kb < nblk; ++kb) {
+    const int k = kb * SB, nb = min(SB, d - k);
+    const T* Li = Linv + (size_t)kb * SB * SB;
+    for (int e = threadIdx.x; e < SB * SB; e += blockDim.x) Ls[e / SB][e % SB] = Li[e];
+    if (threadIdx.x < SB) bk[threadIdx.x] = threadIdx.x < nb ? (T)b[k + threadIdx.x] : T(0);
+    __syncthreads();
+    if (threadIdx.x < SB) {                             // yk = Linv_kk bk
+      const int i = threadIdx.x;
+      T v = T(0);
+      for (int j = 0; j <= i; ++j) v = fma(Ls[i][j], bk[j], v);
+      yk[i] = v;
+      if (blockIdx.x == 0 && i < nb) y[k + i] = (double)v;
+    }
+    __syncthreads();
+    for (int row = k + nb + blockIdx.x * nwarps + warp; row < d; row += gridDim.x * nwarps) {
+      const T* lr = L + (size_t)row * d + k;
+      T v = T(0);
+      for (int j = lane; j < nb; j += 32) v = fma(lr[j], yk[j], v);
+      v = warp_sum(v);
+      if (lane == 0) b[row] -= (double)v;
+    }
+    grid.sync();
+  }
+  // backward: L^T g = y   (g written into b)
+  for (int kb = nblk - 1; kb >= 0; --kb) {
+    const int k = kb * SB, nb = min(SB, d - k);
+    const T* Li = Linv + (size_t)kb * SB * SB;
+    for (int e = threadIdx.x; e < SB * SB; e += blockDim.x) Ls[e / SB][e % SB] = Li[e];
+    if (threadIdx.x < SB) bk[threadIdx.x] = threadIdx.x < nb ? (T)y[k + threadIdx.x] : T(0);
+    __syncthreads();
+    if (threadIdx.x < SB) {                             // (L_kk^T)^-1 = (L_kk^-1)^T
+      const int i = threadIdx.x;
+      T v = T(0);
+      for (int j = i; j < SB; ++j) v = fma(Ls[j][i], bk[j], v);
+      yk[i] = v;
+      if (blockIdx.x == 0 && i < nb) b[k + i] = (double)v;
+    }
+    __syncthreads();
+    for (int col = blockIdx.x * nwarps + warp; col < k; col += gridDim.x * nwarps) {
+      const T* lc = LT + (size_t)col * d + k;          // row col of L^T = column col of L
+      T v = T(0);
+      for (int j = lane; j < nb; j += 32) v = fma(lc[j], yk[j], v);
+      v = warp_sum(v);
+      if (lane == 0) y[col] -= (double)v;
+    }
+    grid.sync();
+  }
+}
+
+// LT[c][r] = L[r][c] for c <= r (the transposed factor, for coalesced
+// backward substitution).
+template <class T>
+__global__ void k_transpose_lower(const T* L, int d, T* LT) {
+  __shared__ T t[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  if (bx > by + 31) return;                       // tile entirely above the diagonal of L
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = by + i, c = bx + threadIdx.x;
+    t[i][threadIdx.x] = (r < d && c < d && c <= r) ? L[(size_t)r * d + c] : T(0);
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = bx + i, r = by + threadIdx.x;
+    if (r < d && c < d && c <= r) LT[(size_t)c * d + r] = t[threadIdx.x][i];
+  }
+}
+
+size_t chol_inv_doubles(int d) { return (size_t)((d + SB - 1) / SB) * SB * SB; }
+
+// Transposed copy and inverted diagonal blocks of a computed factor.
+template <class T>
+tucker_status chol_prepare_t(tucker_handle* h, const T* L, int d, T* LT, T* Linv) {
+  dim3 grid((d + 31) / 32, (d + 31) / 32);
+  TK_COUNT(h);
+  k_transpose_lower<T><<<grid, dim3(32, 8), 0, h->stream>>>(L, d, LT);
+  TK_LAUNCH(h);
+  TK_COUNT(h);
+  k_inv_diag_blocks<T><<<(d + SB - 1) / SB, SB, 0, h->stream>>>(L, d, Linv);
   TK_LAUNCH(h);
   return TUCKER_OK;
 }
 
-// ------------------------------------------------------------ triangular solves
-// Blocked: per block of CB unknowns, one CTA solves the diagonal block and then
-// a multi-CTA GEMV removes it from the remaining right-hand side.
-
-__global__ void k_trsv_block(const double* L, int d, int k, double* b, int upper,
-                             const int* status) {
-  // solve the CB diagonal block in place (single warp, sequential over CB)
-  __shared__ double x[CB];
-  if (*status) return;
-  const int nb = min(CB, d - k);
-  if (threadIdx.x < nb) x[threadIdx.x] = b[k + threadIdx.x];
-  __syncwarp();
-  if (threadIdx.x == 0) {
-    if (!upper) {
-      for (int i = 0; i < nb; ++i) {
-        double v = x[i];
-        for (int j = 0; j < i; ++j) v -= L[(size_t)(k + i) * d + k + j] * x[j];
-        x[i] = v / L[(size_t)(k + i) * d + k + i];
-      }
-    } else {                                  // L^T: row i of L^T is column i of L
-      for (int i = nb - 1; i >= 0; --i) {
-        double v = x[i];
-        for (int j = i + 1; j < nb; ++j) v -= L[(size_t)(k + j) * d + k + i] * x[j];
-        x[i] = v / L[(size_t)(k + i) * d + k + i];
-      }
-    }
-  }
-  __syncwarp();
-  if (threadIdx.x < nb) b[k + threadIdx.x] = x[threadIdx.x];
+tucker_status chol_prepare(tucker_handle* h, const double* L, int d, double* LT, double* Linv) {
+  return chol_prepare_t<double>(h, L, d, LT, Linv);
+}
+tucker_status chol_prepare32(tucker_handle* h, const float* L, int d, float* LT, float* Linv) {
+  return chol_prepare_t<float>(h, L, d, LT, Linv);
 }
 
-// Lower: b[i] -= sum_{j in block} L[i][j] x[j] for i >= k + CB.
-// Upper (L^T): b[i] -= sum_{j in block} L[j][i] x[j] for i < k.
-__global__ void k_trsv_update(const double* L, int d, int k, double* b, int upper,
-                              const int* status) {
-  if (*status) return;
-  const int nb = min(CB, d - k);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (!upper) {
-    const int row = k + nb + i;
-    if (row >= d) return;
-    double v = 0.0;
-    for (int j = 0; j < nb; ++j) v += L[(size_t)row * d + k + j] * b[k + j];
-    b[row] -= v;
-  } else {
-    if (i >= k) return;
-    double v = 0.0;
-    for (int j = 0; j < nb; ++j) v += L[(size_t)(k + j) * d + i] * b[k + j];
-    b[i] -= v;
-  }
-}
-
-// g = (L L^T)^-1 rhs  (g may alias rhs)
-tucker_status chol_solve(tucker_handle* h, const double* L, int d, const double* rhs, double* g) {
+// g = (L L^T)^-1 rhs; tmp: d doubles of scratch.  g may alias rhs.
+template <class T>
+tucker_status chol_solve_t(tucker_handle* h, const T* L, const T* LT, const T* Linv, int d,
+                           const double* rhs, double* g, double* tmp) {
   if (g != rhs)
     TK_CUDA(h, cudaMemcpyAsync(g, rhs, sizeof(double) * d, cudaMemcpyDeviceToDevice, h->stream));
-  for (int k = 0; k < d; k += CB) {
-    TK_COUNT(h);
-    k_trsv_block<<<1, 32, 0, h->stream>>>(L, d, k, g, 0, h->d_status);
-    const int rows = d - k - CB;
-    if (rows > 0) { TK_COUNT(h); k_trsv_update<<<ceil_div(rows, 128), 128, 0, h->stream>>>(L, d, k, g, 0, h->d_status); }
+  const void* kern = (const void*)k_trsv_coop<T>;
+  const int grid = coop_grid(h, kern, 256, 0);
+  if (grid < 1) return fail(h, TUCKER_ECUDA, "cooperative solve cannot be resident");
+  void* args[] = {(void*)&L, (void*)&LT, (void*)&Linv, &d, &g, &tmp, &h->d_status};
+  TK_COUNT(h);
+  TK_CUDA(h, cudaLaunchCooperativeKernel(kern, grid, 256, args, 0, h->stream));
+  return TUCKER_OK;
+}
+
+tucker_status chol_solve2(tucker_handle* h, const double* L, const double* LT, const double* Linv,
+                          int d, const double* rhs, double* g, double* tmp) {
+  return chol_solve_t<double>(h, L, LT, Linv, d, rhs, g, tmp);
+}
+tucker_status chol_solve32(tucker_handle* h, const float* L, const float* LT, const float* Linv,
+                           int d, const double* rhs, double* g, double* tmp) {
+  return chol_solve_t<float>(h, L, LT, Linv, d, rhs, g, tmp);
+}
+
+tucker_status launch_to_f32(tucker_handle* h, const double* in, size_t n, float* out) {
+  int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)h->num_sms * 16);
+  if (grid < 1) grid = 1;
+  TK_COUNT(h);
+  k_to_f32<<<grid, 256, 0, h->stream>>>(in, n, out);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+// r = h - M g with the explicit symmetric FP64 matrix M (warp per row).
+__global__ void k_gemv_resid(const double* M, int d, const double* g, const double* hv, double* r) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int row = warp; row < d; row += nwarps) {
+    const double* mr = M + (size_t)row * d;
+    double v = 0.0;
+    for (int j = lane; j < d; j += 32) v = fma(mr[j], g[j], v);
+    v = warp_sum(v);
+    if (lane == 0) r[row] = hv[row] - v;
   }
-  const int last = ((d - 1) / CB) * CB;
-  for (int k = last; k >= 0; k -= CB) {
-    TK_COUNT(h);
-    k_trsv_block<<<1, 32, 0, h->stream>>>(L, d, k, g, 1, h->d_status);
-    if (k > 0) { TK_COUNT(h); k_trsv_update<<<ceil_div(k, 128), 128, 0, h->stream>>>(L, d, k, g, 1, h->d_status); }
-  }
+}
+
+tucker_status launch_gemv_resid(tucker_handle* h, const double* M, int d, const double* g,
+                                const double* hv, double* r) {
+  int grid = (d + 7) / 8;
+  if (grid > h->num_sms * 8) grid = h->num_sms * 8;
+  TK_COUNT(h);
+  k_gemv_resid<<<grid, 256, 0, h->stream>>>(M, d, g, hv, r);
   TK_LAUNCH(h);
   return TUCKER_OK;
 }

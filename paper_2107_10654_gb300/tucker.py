@@ -19,10 +19,11 @@ from . import _lib as L
 __all__ = ["TuckerError", "Handle", "Samples", "CooTensor", "tucker_leverage_scores",
            "tucker_sample_rows", "tucker_core_update_sketched", "tucker_core_update_exact",
            "tucker_als_sweep", "tucker_ridge_loss", "tucker_core_solve_adjoint",
-           "tucker_sample_rows_noalloc", "tucker_sketched_gram"]
+           "tucker_sample_rows_noalloc", "tucker_sketched_gram", "tucker_set_solver"]
 
 PREC = {"fp64": L.PREC_FP64, "fp32": L.PREC_FP32, "tf32": L.PREC_TF32, "bf16": L.PREC_BF16}
 REG = {"exact": L.REG_EXACT, "augmented": L.REG_AUGMENTED}
+SOLVER = {"fp64": L.SOLVER_FP64_CHOLESKY, "mixed": L.SOLVER_MIXED}
 
 
 class TuckerError(RuntimeError):
@@ -68,7 +69,8 @@ def _check(h, st: int):
 class Handle:
     """Owns a tucker_handle bound to a CUDA stream (default: torch's current stream)."""
 
-    def __init__(self, stream: Optional[torch.cuda.Stream] = None, synchronous: bool = True):
+    def __init__(self, stream: Optional[torch.cuda.Stream] = None, synchronous: bool = True,
+                 solver: str = "fp64"):
         lib = L.load()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         hp = C.c_void_p()
@@ -77,6 +79,12 @@ class Handle:
             raise TuckerError(st, "tucker_create failed (needs an sm_103 GPU)")
         self.h = hp
         _check(self.h, lib.tucker_set_sync(self.h, int(synchronous)))
+        self.set_solver(solver)
+
+    def set_solver(self, solver: str):
+        """Ridge solver of later updates: "fp64" (FP64 Cholesky) or "mixed"
+        (FP32 Cholesky preconditioning an FP64 iterative refinement)."""
+        _check(self.h, L.load().tucker_set_solver(self.h, SOLVER[solver]))
 
     def close(self):
         if getattr(self, "h", None):
@@ -287,3 +295,8 @@ def tucker_sample_rows_noalloc(dims: Sequence[int], ranks: Sequence[int],
         raise TuckerError(st, err.value.decode(errors="replace"))
     out.n_unique, out.n_draws = int(cs.n_unique), int(cs.n_draws)
     return out
+
+
+def tucker_set_solver(h: Handle, solver: str) -> None:
+    """tucker_set_solver: "fp64" (FP64 Cholesky, the default) or "mixed"."""
+    h.set_solver(solver)
