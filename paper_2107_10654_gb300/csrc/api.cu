@@ -77,13 +77,12 @@ tucker_status launch_adjoint_rows(tucker_handle* h, const FactorSet& F, uint32_t
                                   const double* w, const double* x, const double* zg,
                                   const double* zv, const double* g, const double* v,
                                   const int* n_rows, int64_t cap, double* const* dA, double* dx);
-size_t walk_scratch_doubles(int64_t I1, int d, int R1);
+size_t walk_scratch_doubles(int64_t I1, int d, int R1, int64_t cap, int sms);
 bool walk_fits(int N, const int* R, int64_t I1);
-tucker_status walk_segments(tucker_handle* h, const RowSet& s, int64_t I1, int64_t cap,
-                            double* scratch);
-tucker_status walk_dot(tucker_handle* h, const RowSet& s, int64_t I1, double* scratch,
+tucker_status walk_segments(tucker_handle* h, const RowSet& s, int64_t I1, const WalkBuf& wb);
+tucker_status walk_dot(tucker_handle* h, const RowSet& s, int64_t I1, const WalkBuf& wb,
                        const double* g1, const double* g2, double* z1, double* z2);
-tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, double* scratch,
+tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, const WalkBuf& wb,
                         const double* ca, const double* cb, double coef, const double* base,
                         const double* diag, const double* y, double* out);
 tucker_status launch_decode_rows(tucker_handle* h, const FactorSet& F, const uint64_t* keys,
@@ -112,14 +111,14 @@ static tucker_status rowset64(tucker_handle* h, const FactorSet& F, const RowSet
 // Level walk along the sorted sample when its vectors fit in shared memory,
 // else the per-element kernels (same results up to summation order).
 static tucker_status rows_dot(tucker_handle* h, const FactorSet& F, const RowSet& rs,
-                              double* walk, const double* g1, const double* g2, double* z1,
+                              const WalkBuf& walk, const double* g1, const double* g2, double* z1,
                               double* z2) {
   if (walk_fits(F.N, F.R, F.I[0])) return walk_dot(h, rs, F.I[0], walk, g1, g2, z1, z2);
   return launch_kron_dot(h, rs, g1, g2, z1, z2);
 }
 
 static tucker_status rows_axpy(tucker_handle* h, const FactorSet& F, const RowSet& rs,
-                               double* walk, int nsplit, double* part, const double* ca,
+                               const WalkBuf& walk, int nsplit, double* part, const double* ca,
                                const double* cb, double coef, const double* base,
                                const double* diag, const double* y, double* out) {
   if (walk_fits(F.N, F.R, F.I[0]))
@@ -260,7 +259,8 @@ struct SketchBufs {
   uint32_t* idx[TUCKER_MAX_ORDER];
   double *w, *x, *p, *z;
   float* sw32;
-  double *D, *h, *g, *r, *axpy_part, *walk;
+  double *D, *h, *g, *r, *axpy_part;
+  WalkBuf walk;
   double* A64[TUCKER_MAX_ORDER];      // FP64 copies of FP32 factors (walk kernels)
   char* gram_ws;
   size_t gram_bytes;
@@ -295,7 +295,8 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
   b->r = ar.get<double>(F.d);
   b->axpy_split = axpy_splits(h, F.d, m);
   b->axpy_part = ar.get<double>((size_t)b->axpy_split * F.d);
-  b->walk = ar.get<double>(walk_scratch_doubles(F.I[0], F.d, F.R[0]));
+  b->walk.p = ar.get<double>(walk_scratch_doubles(F.I[0], F.d, F.R[0], m, h->num_sms));
+  b->walk.cap = m;
   for (int n = 0; n < F.N; ++n)
     b->A64[n] = F.is64 ? nullptr : ar.get<double>((size_t)F.I[n] * F.R[n]);
   b->simt_split = gram_simt_splits(h, F.d, m);
@@ -341,24 +342,44 @@ static tucker_status chol_reserve(tucker_handle* h, int d) {
 }
 
 // Factor M (= G + diag(regdiag), full and symmetric in the FP64 buffer L)
-// with the handle's solver.  FP64: L L^T = M in place.  Mixed: the FP32 copy
+// with the handle's solver.  FP64: L L^T = M in place; the solves run in FP64
+// when the Gram is FP64 (no refinement follows), else in FP32 on the rounded
+// factor (they only precondition the FP64 refinement).  Mixed: the FP32 copy
 // is factored and L keeps M for the FP64 residual.
-static tucker_status factorize(tucker_handle* h, double* L, int d) {
+static tucker_status factorize(tucker_handle* h, double* L, int d, int prec) {
   CholCache& c = h->chol;
   c.mixed = h->solver == TUCKER_SOLVER_MIXED;
+  c.prep64 = c.prep32 = 0;
   if (c.mixed) {
     TK_TRY(launch_to_f32(h, L, (size_t)d * d, c.L32));
     TK_TRY(cholesky32(h, c.L32, d));
-    return chol_prepare32(h, c.L32, d, c.LT32, c.Linv32);
+    TK_TRY(chol_prepare32(h, c.L32, d, c.LT32, c.Linv32));
+    c.prep32 = 1;
+    return TUCKER_OK;
   }
   TK_TRY(cholesky(h, L, d));
-  return chol_prepare(h, L, d, c.LT, c.Linv);
+  if (prec == TUCKER_PREC_FP64) {
+    TK_TRY(chol_prepare(h, L, d, c.LT, c.Linv));
+    c.prep64 = 1;
+  } else {
+    TK_TRY(launch_to_f32(h, L, (size_t)d * d, c.L32));
+    TK_TRY(chol_prepare32(h, c.L32, d, c.LT32, c.Linv32));
+    c.prep32 = 1;
+  }
+  return TUCKER_OK;
 }
 
-// g = (L L^T)^-1 rhs with the cached factor (g may alias rhs).
-static tucker_status chol_solve(tucker_handle* h, int d, const double* rhs, double* g) {
-  const CholCache& c = h->chol;
-  if (c.mixed) return chol_solve32(h, c.L32, c.LT32, c.Linv32, d, rhs, g, c.tmp);
+// g = (L L^T)^-1 rhs with the cached factor (g may alias rhs).  FP32 solves
+// when the factor is FP32, or when the Gram precision calls for refinement and
+// the rounded copy exists; FP64 otherwise.
+static tucker_status chol_solve(tucker_handle* h, int d, const double* rhs, double* g, int prec) {
+  CholCache& c = h->chol;
+  if (c.mixed || (c.prep32 && prec != TUCKER_PREC_FP64))
+    return chol_solve32(h, c.L32, c.LT32, c.Linv32, d, rhs, g, c.tmp);
+  if (!c.prep64) {
+    TK_TRY(chol_prepare(h, c.L, d, c.LT, c.Linv));
+    c.prep64 = 1;
+  }
   return chol_solve2(h, c.L, c.LT, c.Linv, d, rhs, g, c.tmp);
 }
 
@@ -382,7 +403,7 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
                                    int prec, SketchBufs& b, const double* rhs, double* g,
                                    int* iters, double* rel) {
   const int d = F.d;
-  TK_TRY(chol_solve(h, d, rhs, g));
+  TK_TRY(chol_solve(h, d, rhs, g, prec));
   *iters = 0;
   *rel = 0.0;
   const bool explicit_m = prec == TUCKER_PREC_FP64;
@@ -398,7 +419,7 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
       TK_TRY(rows_axpy(h, F, rs, b.walk, b.axpy_split, b.axpy_part, b.w, b.z, -1.0, rhs,
                        h->chol.regdiag, g, b.r));
     }
-    TK_TRY(chol_solve(h, d, b.r, b.r));
+    TK_TRY(chol_solve(h, d, b.r, b.r, prec));
     double hv[2] = {0, 0};
     TK_TRY(launch_refine_update(h, g, b.r, d, b.z));
     TK_CUDA(h, cudaMemcpyAsync(hv, b.z, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -415,7 +436,7 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
 static tucker_status solve_refine(tucker_handle* h, const FactorSet& F, const RowSet& rs,
                                   int prec, SketchBufs& b, int* iters, double* rel) {
   TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
-  TK_TRY(factorize(h, h->chol.L, F.d));
+  TK_TRY(factorize(h, h->chol.L, F.d, prec));
   return solve_refined(h, F, rs, prec, b, b.h, b.g, iters, rel);
 }
 
@@ -677,7 +698,7 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   RowSet rs64;
   TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
   double* G = h->chol.L;
-  TK_TRY(walk_segments(h, rs, F.I[0], cap, b.walk));
+  TK_TRY(walk_segments(h, rs, F.I[0], b.walk));
   TK_TRY(build_gram(h, F, rs, prec, cap, b, G));
   TK_TRY(rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x, 1.0, nullptr, nullptr,
                    nullptr, b.h));
@@ -779,7 +800,7 @@ tucker_status tucker_core_update_exact(tucker_handle* h, const tucker_tensor* X,
   RowSet rs64;
   TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
   double* G = h->chol.L;
-  TK_TRY(walk_segments(h, rs, F.I[0], nnz, b.walk));
+  TK_TRY(walk_segments(h, rs, F.I[0], b.walk));
   TK_TRY(build_gram(h, F, rs, prec, nnz, b, G));
   TK_TRY(rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x, 1.0, nullptr, nullptr,
                    nullptr, b.h));
@@ -928,7 +949,7 @@ tucker_status tucker_sketched_gram(tucker_handle* h, const tucker_tensor* X, con
   RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
   RowSet rs64;
   TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
-  TK_TRY(walk_segments(h, rs, F.I[0], cap, b.walk));
+  TK_TRY(walk_segments(h, rs, F.I[0], b.walk));
   TK_TRY(build_gram(h, F, rs, prec, cap, b, G_out));
   if (h_out)
     TK_TRY(rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x, 1.0, nullptr, nullptr,
@@ -975,13 +996,13 @@ tucker_status tucker_core_solve_adjoint(tucker_handle* h, const tucker_tensor* X
   RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
   RowSet rs64;
   TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
-  TK_TRY(walk_segments(h, rs, F.I[0], cap, b.walk));
+  TK_TRY(walk_segments(h, rs, F.I[0], b.walk));
   if (!reuse) {
     TK_TRY(build_gram(h, F, rs, prec, cap, b, h->chol.L));
     TK_TRY(launch_regdiag(h, h->chol.regdiag, F.d, lambda,
                           reg == TUCKER_REG_AUGMENTED ? b.D : nullptr));
     TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
-    TK_TRY(factorize(h, h->chol.L, F.d));
+    TK_TRY(factorize(h, h->chol.L, F.d, prec));
     h->chol.id = h->next_solve_id++;
   }
   int iters;

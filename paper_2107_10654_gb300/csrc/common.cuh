@@ -41,6 +41,8 @@ struct CholCache {
   float* LT32 = nullptr;      // its transpose
   float* Linv32 = nullptr;    // its inverted 64 x 64 diagonal blocks
   int mixed = 0;          // the cached factor is the FP32 one (L then holds M itself)
+  int prep64 = 0;         // LT / Linv of the FP64 factor are ready
+  int prep32 = 0;         // L32 / LT32 / Linv32 are ready (the FP32 factor, or the FP64 one rounded)
   int d = 0;
   size_t cap = 0;         // elements of L allocated
   uint64_t id = 0;        // solve id of the cached factor (0 = none)
@@ -238,6 +240,12 @@ struct FactorSet {
   int is64;
   int d;
   uint64_t total;   // prod I_n
+};
+
+// Scratch of the level walks (walk.cu): the buffer and the sample capacity it was sized for.
+struct WalkBuf {
+  double* p = nullptr;
+  int64_t cap = 0;
 };
 
 struct RowSet {                       // the deduplicated sample as device arrays

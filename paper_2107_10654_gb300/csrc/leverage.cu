@@ -134,15 +134,15 @@ __global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a, double*
             // tangent of the rotation angle in FP32 (an approximate annihilation
             // is enough for Jacobi); (c, s) formed in FP64 so that the
             // rotation is orthogonal to FP64 rounding
-            const float theta = (float)((aqq - app) / (2.0 * apq));
+            const double num = aqq - app, den = 2.0 * apq;
+            const bool in32 = fabs(den) > 1e-30 && fabs(den) < 1e30 && fabs(num) < 1e30;
+            const float theta = in32 ? (float)num / (float)den : (float)(num / den);
             float tf;
             if (fabsf(theta) > 1e18f) tf = 0.5f / theta;
             else tf = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
             const double t = (double)tf;
             const double q2 = fma(t, t, 1.0);
-            double y = (double)rsqrtf((float)q2);          // Newton-Raphson for 1/sqrt(q2)
-            y = y * fma(-0.5 * q2, y * y, 1.5);
-            y = y * fma(-0.5 * q2, y * y, 1.5);
+            const double y = rsqrt(q2);
             c = y;
             s = t * y;
           }

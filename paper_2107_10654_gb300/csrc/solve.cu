@@ -27,8 +27,8 @@ namespace cg = cooperative_groups;
 namespace tk {
 
 constexpr int CB = 32;      // panel width
-constexpr int CT = 32;      // trailing tile (small: one step spreads over many SMs)
 constexpr int SB = 64;      // block of the triangular solves
+constexpr int CHOL_THREADS = 128;   // one warp per SM sub-partition: enough for the FP64 pipe
 
 __global__ void k_add_diag(double* M, int d, const double* diag) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x)
@@ -46,81 +46,172 @@ __global__ void k_to_f32(const double* in, size_t n, float* out) {
     out[i] = (float)in[i];
 }
 
-// 1/sqrt(p) for p > 0.  FP64: an FP32 seed refined by two Newton-Raphson
-// steps for f(y) = 1/y^2 - p, y <- y (3 - p y^2) / 2 (each step doubles the
-// correct bits: 23 -> 46 -> full FP64), on an exactly power-of-two-scaled p.
-// Cheaper on the FP64 pipe than a square root and a divide.
-__device__ __forceinline__ double rsqrt_piv(double p) {
-  int e;
-  double m = frexp(p, &e);                   // p = m 2^e exactly, m in [0.5, 1)
-  if (e & 1) { m *= 2.0; e -= 1; }           // e even, m in [0.5, 2)
-  double y = (double)rsqrtf((float)m);
-  y = y * fma(-0.5 * m, y * y, 1.5);
-  y = y * fma(-0.5 * m, y * y, 1.5);
-  return ldexp(y, -e / 2);
-}
+// 1/sqrt(p) of a pivot p > 0 (CUDA's rsqrt of the element type).
+__device__ __forceinline__ double rsqrt_piv(double p) { return rsqrt(p); }
 __device__ __forceinline__ float rsqrt_piv(float p) { return rsqrtf(p); }
 
 template <class T> __device__ __forceinline__ T tmax();
 template <> __device__ __forceinline__ double tmax<double>() { return 1.7976931348623157e308; }
 template <> __device__ __forceinline__ float tmax<float>() { return 3.402823466e38f; }
 
-// Factor the nb x nb diagonal block at (k, k) in shared memory (all threads).
-// One thread forms each pivot's l_jj = p / sqrt(p) and 1/l_jj; the trailing
-// entries (i, c), j < c <= i, are packed densely over the threads.  Returns
-// false on a non-positive or NaN pivot; every CTA computes the same.
 template <class T>
-__device__ bool factor_diag_block(const T* M, int d, int k, int nb, T (*a)[CB + 1]) {
+__device__ __forceinline__ bool pivot_ok(T p) { return p > T(0) && p <= tmax<T>(); }
+
+// Factor the nb x nb diagonal block at (k, k) in shared memory (all threads
+// of the CTA).  Right-looking, one barrier per pivot: in phase j the scaled
+// column l_ij = a_ij y_j (y_j = p_j^-1/2) is written to the unused upper
+// triangle a[j][i] while the trailing entries are updated from the unscaled
+// column, a_ic -= (a_ij r_j) a_cj with r_j = y_j^2.  Thread 0 updates the next
+// diagonal entry first and computes its y, so the square-root chain overlaps
+// the rest of the update.  Returns false (in every thread) on a pivot that is
+// not positive and finite; every CTA computes the same.
+template <class T>
+__device__ bool factor_diag_block(const T* M, int d, int k, int nb, T (*a)[CB + 1],
+                                  const uint16_t* tri) {
+  __shared__ T ys[CB + 1], rs[CB + 1];
   __shared__ int bad;
-  __shared__ T rp;
-  for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < CB * CB; e += blockDim.x) {
     const int i = e / CB, j = e % CB;
-    a[i][j] = (i < nb && j < nb) ? M[(size_t)(k + i) * d + k + j] : T(0);
+    a[i][j] = (i < nb && j <= i) ? M[(size_t)(k + i) * d + k + j] : T(0);
   }
-  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  if (tid == 0) {
+    const T p = a[0][0];
+    bad = !pivot_ok(p);
+    if (!bad) { ys[0] = rsqrt_piv(p); rs[0] = ys[0] * ys[0]; }
+  }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    if (threadIdx.x == 0) {
-      const T p = a[j][j];
-      if (!(p > T(0)) || !(p <= tmax<T>())) {
-        bad = 1;
-      } else {
-        const T y = rsqrt_piv(p);
-        a[j][j] = p * y;
-        rp = y;
+    if (bad) return false;                          // read after a barrier: uniform
+    const T y = ys[j], r = rs[j];
+    const int m = nb - 1 - j;                       // trailing size
+    if (tid == 0) {
+      a[j][j] = a[j][j] * y;                        // l_jj = p_j / sqrt(p_j)
+      if (m > 0) {
+        const T l = a[j + 1][j];
+        const T v = fma(-(l * r), l, a[j + 1][j + 1]);
+        a[j + 1][j + 1] = v;
+        if (!pivot_ok(v)) {
+          bad = 1;
+        } else {
+          const T yn = rsqrt_piv(v);
+          ys[j + 1] = yn;
+          rs[j + 1] = yn * yn;
+        }
+      }
+    } else {
+      // scaled column into the upper triangle: thread t < m writes l_{j+1+t, j}
+      for (int t = tid - 1; t < m; t += blockDim.x - 1) a[j][j + 1 + t] = a[j + 1 + t][j] * y;
+      // trailing entries except (j+1, j+1): packed index e -> (ii, cc), cc <= ii < m
+      const int cnt = m * (m + 1) / 2;
+      for (int e = tid; e < cnt; e += blockDim.x - 1) {
+        const uint32_t ic = tri[e];
+        const int i = j + 1 + (int)(ic >> 8), c = j + 1 + (int)(ic & 0xffu);
+        a[i][c] = fma(-(a[i][j] * r), a[c][j], a[i][c]);
       }
     }
     __syncthreads();
-    if (bad) return false;
-    const T r = rp;
-    const int m = nb - j - 1;                       // trailing size
-    for (int e = threadIdx.x; e < m * (m + 1) / 2; e += blockDim.x) {
-      // row-major packing of the lower triangle of the trailing block
-      int ii = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
-      while (ii * (ii + 1) / 2 > e) --ii;
-      const int cc = e - ii * (ii + 1) / 2;
-      const int i = j + 1 + ii, c = j + 1 + cc;     // j < c <= i
-      a[i][c] = fma(-(a[i][j] * r), a[c][j] * r, a[i][c]);
-    }
-    __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][j] *= r;
-    __syncthreads();
   }
+  // move the scaled columns from the upper to the lower triangle
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    if (j < i) a[i][j] = a[j][i];
+  }
+  __syncthreads();
   return true;
 }
 
+// A_ij -= L_ik L_jk^T over the lower TS x TS tiles of the trailing matrix
+// (rows and columns >= s), tiles distributed over the CTAs.  The panel rows of
+// a CTA's next tile are loaded into registers while the current tile is
+// multiplied.  Thread (ty, tx) owns rows ty + 16 i and columns tx + 8 j.
+template <class T, int TS>
+__device__ void trailing_update(T* M, int d, int k, int nb, int s, T (*Pa)[CB + 1],
+                                T (*Pb)[CB + 1]) {
+  constexpr int PER = TS * CB / CHOL_THREADS;   // panel elements per thread and operand
+  constexpr int OR = TS / 16, OC = TS / 8;      // outputs per thread
+  const int Tt = (d - s + TS - 1) / TS;
+  const int ntiles = Tt * (Tt + 1) / 2;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  auto origin = [&](int tile, int* r0, int* c0) {
+    // lower tiles in row-major packed order: tile = ti (ti + 1) / 2 + tj
+    int ti = (int)((sqrtf(8.0f * tile + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+    while (ti * (ti + 1) / 2 > tile) --ti;
+    *r0 = s + ti * TS;
+    *c0 = s + (tile - ti * (ti + 1) / 2) * TS;
+  };
+  T ra[PER], rb[PER];
+  auto fetch = [&](int tile) {
+    int r0, c0;
+    origin(tile, &r0, &c0);
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * CHOL_THREADS, i = e / CB, c = e % CB;
+      ra[q] = (r0 + i < d && c < nb) ? M[(size_t)(r0 + i) * d + k + c] : T(0);
+      rb[q] = (c0 + i < d && c < nb) ? M[(size_t)(c0 + i) * d + k + c] : T(0);
+    }
+  };
+  if ((int)blockIdx.x < ntiles) fetch(blockIdx.x);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int r0, c0;
+    origin(tile, &r0, &c0);
+    __syncthreads();                            // the previous tile's reads are done
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * CHOL_THREADS;
+      Pa[e / CB][e % CB] = ra[q];
+      Pb[e / CB][e % CB] = rb[q];
+    }
+    __syncthreads();
+    if (tile + (int)gridDim.x < ntiles) fetch(tile + gridDim.x);
+    T acc[OR][OC];
+#pragma unroll
+    for (int i = 0; i < OR; ++i)
+#pragma unroll
+      for (int j = 0; j < OC; ++j) acc[i][j] = T(0);
+#pragma unroll 4
+    for (int c = 0; c < CB; ++c) {
+      T av[OR], bv[OC];
+#pragma unroll
+      for (int i = 0; i < OR; ++i) av[i] = Pa[ty + 16 * i][c];
+#pragma unroll
+      for (int j = 0; j < OC; ++j) bv[j] = Pb[tx + 8 * j][c];
+#pragma unroll
+      for (int i = 0; i < OR; ++i)
+#pragma unroll
+        for (int j = 0; j < OC; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < OR; ++i) {
+      const int r = r0 + ty + 16 * i;
+      if (r >= d) continue;
+#pragma unroll
+      for (int j = 0; j < OC; ++j) {
+        const int c = c0 + tx + 8 * j;
+        if (c < d && c <= r) M[(size_t)r * d + c] -= acc[i][j];
+      }
+    }
+  }
+}
+
 template <class T>
-__global__ void __launch_bounds__(256) k_chol_coop(T* M, int d, int* status) {
+__global__ void __launch_bounds__(CHOL_THREADS) k_chol_coop(T* M, int d, int* status) {
   cg::grid_group grid = cg::this_grid();
   __shared__ T Lkk[CB][CB + 1];
   __shared__ T rinv[CB];
-  __shared__ T Pa[CT][CB + 1];
-  __shared__ T Pb[CT][CB + 1];
+  __shared__ T Pa[32][CB + 1];
+  __shared__ T Pb[32][CB + 1];
+  __shared__ uint16_t tri[CB * (CB - 1) / 2 + CB];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // packed trailing-triangle table: entry e = ii (ii + 1) / 2 + cc
+  for (int ii = threadIdx.x; ii < CB; ii += blockDim.x)
+    for (int cc = 0; cc <= ii; ++cc) tri[ii * (ii + 1) / 2 + cc] = (uint16_t)((ii << 8) | cc);
+  __syncthreads();
   for (int k = 0; k < d; k += CB) {
     const int nb = min(CB, d - k);
-    if (!factor_diag_block<T>(M, d, k, nb, Lkk)) {
+    if (!factor_diag_block<T>(M, d, k, nb, Lkk, tri)) {
       if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, DEV_NOTSPD);
       return;                                   // every CTA takes this branch at the same k
     }
@@ -147,42 +238,12 @@ __global__ void __launch_bounds__(256) k_chol_coop(T* M, int d, int* status) {
     grid.sync();
     const int s = k + nb;
     if (s < d) {
-      const int Tt = (d - s + CT - 1) / CT;
-      const int ntiles = Tt * (Tt + 1) / 2;
-      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        int ti = 0, rem = tile;
-        while (rem > ti) { rem -= ti + 1; ++ti; }
-        const int tj = rem;
-        const int r0 = s + ti * CT, c0 = s + tj * CT;
-        __syncthreads();
-        for (int e = threadIdx.x; e < CT * CB; e += blockDim.x) {
-          const int i = e / CB, c = e % CB;
-          Pa[i][c] = (r0 + i < d && c < nb) ? M[(size_t)(r0 + i) * d + k + c] : T(0);
-          Pb[i][c] = (c0 + i < d && c < nb) ? M[(size_t)(c0 + i) * d + k + c] : T(0);
-        }
-        __syncthreads();
-        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 2 x 2 outputs each
-        T acc[2][2] = {};
-#pragma unroll 8
-        for (int c = 0; c < CB; ++c) {
-          const T a0 = Pa[ty * 2][c], a1 = Pa[ty * 2 + 1][c];
-          const T b0 = Pb[tx * 2][c], b1 = Pb[tx * 2 + 1][c];
-          acc[0][0] = fma(a0, b0, acc[0][0]);
-          acc[0][1] = fma(a0, b1, acc[0][1]);
-          acc[1][0] = fma(a1, b0, acc[1][0]);
-          acc[1][1] = fma(a1, b1, acc[1][1]);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const int r = r0 + ty * 2 + i;
-          if (r >= d) continue;
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            const int c = c0 + tx * 2 + j;
-            if (c < d && c <= r) M[(size_t)r * d + c] -= acc[i][j];
-          }
-        }
-      }
+      // 32 x 32 tiles while there are at least two per CTA, then 16 x 16
+      const int t32 = (d - s + 31) / 32;
+      if (t32 * (t32 + 1) / 2 >= 2 * (int)gridDim.x)
+        trailing_update<T, 32>(M, d, k, nb, s, Pa, Pb);
+      else
+        trailing_update<T, 16>(M, d, k, nb, s, Pa, Pb);
     }
     grid.sync();
   }
@@ -201,11 +262,11 @@ static int coop_grid(tucker_handle* h, const void* kernel, int threads, size_t s
 template <class T>
 tucker_status cholesky_t(tucker_handle* h, T* M, int d) {
   const void* kern = (const void*)k_chol_coop<T>;
-  const int grid = coop_grid(h, kern, 256, 0);
+  const int grid = coop_grid(h, kern, CHOL_THREADS, 0);
   if (grid < 1) return fail(h, TUCKER_ECUDA, "cooperative Cholesky cannot be resident");
   void* args[] = {&M, &d, &h->d_status};
   TK_COUNT(h);
-  TK_CUDA(h, cudaLaunchCooperativeKernel(kern, grid, 256, args, 0, h->stream));
+  TK_CUDA(h, cudaLaunchCooperativeKernel(kern, grid, CHOL_THREADS, args, 0, h->stream));
   return TUCKER_OK;
 }
 
@@ -263,12 +324,16 @@ __global__ void __launch_bounds__(256) k_trsv_coop(const T* L, const T* LT, cons
     for (int e = threadIdx.x; e < SB * SB; e += blockDim.x) Ls[e / SB][e % SB] = Li[e];
     if (threadIdx.x < SB) bk[threadIdx.x] = threadIdx.x < nb ? (T)b[k + threadIdx.x] : T(0);
     __syncthreads();
-    if (threadIdx.x < SB) {                             // yk = Linv_kk bk
-      const int i = threadIdx.x;
+    {                                                   // yk = Linv_kk bk: 4 threads per row
+      const int i = threadIdx.x >> 2, part = threadIdx.x & 3;
       T v = T(0);
-      for (int j = 0; j <= i; ++j) v = fma(Ls[i][j], bk[j], v);
-      yk[i] = v;
-      if (blockIdx.x == 0 && i < nb) y[k + i] = (double)v;
+      for (int j = part; j <= i; j += 4) v = fma(Ls[i][j], bk[j], v);
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      if (part == 0) {
+        yk[i] = v;
+        if (blockIdx.x == 0 && i < nb) y[k + i] = (double)v;
+      }
     }
     __syncthreads();
     for (int row = k + nb + blockIdx.x * nwarps + warp; row < d; row += gridDim.x * nwarps) {
@@ -287,12 +352,16 @@ __global__ void __launch_bounds__(256) k_trsv_coop(const T* L, const T* LT, cons
     for (int e = threadIdx.x; e < SB * SB; e += blockDim.x) Ls[e / SB][e % SB] = Li[e];
     if (threadIdx.x < SB) bk[threadIdx.x] = threadIdx.x < nb ? (T)y[k + threadIdx.x] : T(0);
     __syncthreads();
-    if (threadIdx.x < SB) {                             // (L_kk^T)^-1 = (L_kk^-1)^T
-      const int i = threadIdx.x;
+    {                                                   // (L_kk^T)^-1 = (L_kk^-1)^T
+      const int i = threadIdx.x >> 2, part = threadIdx.x & 3;
       T v = T(0);
-      for (int j = i; j < SB; ++j) v = fma(Ls[j][i], bk[j], v);
-      yk[i] = v;
-      if (blockIdx.x == 0 && i < nb) b[k + i] = (double)v;
+      for (int j = i + part; j < SB; j += 4) v = fma(Ls[j][i], bk[j], v);
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      if (part == 0) {
+        yk[i] = v;
+        if (blockIdx.x == 0 && i < nb) b[k + i] = (double)v;
+      }
     }
     __syncthreads();
     for (int col = blockIdx.x * nwarps + warp; col < k; col += gridDim.x * nwarps) {

@@ -5,50 +5,72 @@
 // The sampled keys are sorted, so rows that share the leading indices
 // (i_1, ..., i_n) are contiguous.  With k_u = a_1 (x) a_2 (x) ... (x) a_N
 // (a_n = A^(n)[i_n(u)]) and g viewed as an R_1 x ... x R_N tensor:
-//   dot:  V_1 = g x_1 a_1 (once per i_1 segment), V_n = V_{n-1} x_n a_n, z_u = V_N;
+//   dot:  V_1 = g x_1 a_1 (a table over i_1), V_n = V_{n-1} x_n a_n, z_u = V_N;
 //         moving to the next row only the levels whose index changed are
 //         recomputed (V_n has prod_{k>n} R_k entries);
 //   axpy: W_N = c_u for one row; when the index at level n changes the level
-//         accumulators are folded upwards, W_{n-1} += a_n (x) W_n, and each
-//         i_1 segment yields W_1 = sum_u c_u a_2 (x) ... (x) a_N; finally
-//         out = sum_{i_1} A^(1)[i_1] (x) W_1[i_1].
-// One CTA per i_1 value; its 8 warps walk contiguous parts of the segment
-// and are combined in a fixed order, so the results are deterministic.
+//         accumulators are folded upwards, W_{n-1} += a_n (x) W_n, so every
+//         run of rows with one i_1 yields W_1 = sum_u c_u a_2 (x) ... (x) a_N;
+//         finally out = sum_{i_1} A^(1)[i_1] (x) W_1[i_1].
+// Work is split into pieces: at most CH consecutive rows of one i_1 segment,
+// one warp per piece, so every SM is busy whatever the number of leading
+// indices.  A warp loads the indices (and coefficients) of 32 rows at once,
+// one per lane, and broadcasts them row by row with shuffles.  Piece partial
+// sums are combined in a fixed order, so the results are deterministic.
 // The arithmetic is exact reassociation of sum_r k_u[r] g[r] and
 // sum_u c_u k_u[r] in FP64.
 #include "common.cuh"
 
 namespace tk {
 
-constexpr int WK_WARPS = 8;
+constexpr int WK_WARPS = 8;                 // warps (pieces) per CTA
+constexpr int WK_MIN_ROWS = 32;             // rows per piece, at least (one per lane)
+constexpr int64_t WK_PIECE_TARGET = 16384;  // pieces are widened beyond this count
+constexpr int WK_WARP_SMEM = 12 * 1024;     // axpy: bytes of shared memory per warp, at most
+constexpr int WK_DOT_SMEM = 24 * 1024;      // dot: bytes of shared memory per warp, at most
+
+// dot: V_1 of the piece (nvec vectors) and 32 lanes' factor rows
+static size_t dot_warp_bytes(int L1, int fstore, int nvec) {
+  return ((size_t)nvec * L1 + (size_t)32 * fstore) * 8;
+}
 
 struct WalkArgs {
   int N;
   int R[TUCKER_MAX_ORDER];
   int lsz[TUCKER_MAX_ORDER + 1];     // lsz[n] = prod_{k >= n} R_k (level-n vector size), lsz[N] = 1
-  int lofs[TUCKER_MAX_ORDER + 1];    // offset of level n (n >= 1) in a warp's level storage
-  int lstore;                         // doubles of level storage per warp (one vector)
-  const void* A[TUCKER_MAX_ORDER];
-  int is64;
+  int lofs[TUCKER_MAX_ORDER + 1];    // axpy: offset of level n >= 1 in a warp's accumulators
+  int lstore;                         // axpy: doubles of accumulators per warp
+  int fofs[TUCKER_MAX_ORDER];        // dot: first column of mode n >= 2 in a lane's factor rows
+  int fstore;                         // dot: factor entries per lane (sum of R_n, n >= 2)
+  const double* A[TUCKER_MAX_ORDER];  // FP64 factors
   int d;
-  const uint32_t* idx[TUCKER_MAX_ORDER];
-  const int* seg_begin;               // [I_1]
-  const int* seg_end;                 // [I_1]
   int I1;
+  int CH;
+  const uint32_t* idx[TUCKER_MAX_ORDER];
+  const int* seg_begin;               // [I1]
+  const int* seg_end;                 // [I1]
+  const int64_t* pcnt;                // [I1] pieces of each segment
+  const int64_t* pstart;              // [I1] first piece of each segment
+  const int64_t* npieces;             // [1]
+  const int* p_i1;                    // [maxP]
+  const int* p_u0;
+  const int* p_u1;
   // dot
   const double* g1;
   const double* g2;                   // nullable
   double* z1;
   double* z2;
+  double* V1;                         // [nvec][I1][lsz1]
   // axpy: c_u = coef * ca[u] * (cb ? cb[u] : 1)
   const double* ca;
   const double* cb;
   double coef;
-  double* W1;                          // [I_1][lsz[1]]
+  double* Wp;                          // [maxP][lsz1] piece partials
+  double* W1;                          // [I1][lsz1]
 };
 
 __device__ __forceinline__ double fac(const WalkArgs& a, int n, uint32_t i, int r) {
-  return load_as_double(a.A[n], (int64_t)i * a.R[n] + r, a.is64);
+  return __ldg(a.A[n] + (size_t)i * a.R[n] + r);
 }
 
 // Segment table: seg_begin[i1] / seg_end[i1] of the real rows (sorted keys).
@@ -61,125 +83,168 @@ __global__ void k_segments(const uint32_t* idx0, const int* n_rows, int* seg_beg
   }
 }
 
-__global__ void __launch_bounds__(WK_WARPS * 32) k_walk_dot(WalkArgs a) {
-  extern __shared__ double sm[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nvec = a.g2 ? 2 : 1;
-  double* V1 = sm;                                          // nvec x lsz[1]
-  double* wst = sm + nvec * a.lsz[1] + warp * nvec * a.lstore;  // per-warp levels 2..N-1
-  for (int i1 = blockIdx.x; i1 < a.I1; i1 += gridDim.x) {
-    const int s0 = a.seg_begin[i1], s1 = a.seg_end[i1];
-    if (s1 <= s0) continue;
-    __syncthreads();
-    // V_1 = g x_1 a_1
-    for (int e = threadIdx.x; e < a.lsz[1]; e += blockDim.x) {
-      double v1 = 0.0, v2 = 0.0;
-      for (int r = 0; r < a.R[0]; ++r) {
-        const double f = fac(a, 0, (uint32_t)i1, r);
-        v1 = fma(f, a.g1[(size_t)r * a.lsz[1] + e], v1);
-        if (a.g2) v2 = fma(f, a.g2[(size_t)r * a.lsz[1] + e], v2);
-      }
-      V1[e] = v1;
-      if (a.g2) V1[a.lsz[1] + e] = v2;
-    }
-    __syncthreads();
-    const int len = s1 - s0;
-    const int per = (len + WK_WARPS - 1) / WK_WARPS;
-    const int u0 = s0 + warp * per, u1 = min(s1, u0 + per);
-    uint32_t prev[TUCKER_MAX_ORDER];
-    for (int n = 0; n < a.N; ++n) prev[n] = 0xffffffffu;
-    for (int u = u0; u < u1; ++u) {
-      uint32_t cur[TUCKER_MAX_ORDER];
-      int lvl = a.N;                                        // first changed level (1-based for n >= 1)
-      for (int n = 0; n < a.N; ++n) cur[n] = a.idx[n][u];
-      for (int n = a.N - 1; n >= 1; --n)
-        if (cur[n] != prev[n]) lvl = n;
-      if (prev[0] == 0xffffffffu) lvl = 1;
-      // recompute V_{n+1} for n = lvl .. N-2 (levels stored per warp); level N handled last
-      for (int n = lvl; n <= a.N - 2; ++n) {
-        const int sz = a.lsz[n + 1];
-        const double* src = (n == 1) ? V1 : wst + a.lofs[n];
-        double* dst = wst + a.lofs[n + 1];
-        for (int v = 0; v < nvec; ++v) {
-          const double* s = src + (n == 1 ? v * a.lsz[1] : v * a.lstore);
-          double* dd = dst + v * a.lstore;
-          for (int j = lane; j < sz; j += 32) {
-            double acc = 0.0;
-            for (int r = 0; r < a.R[n]; ++r) acc = fma(fac(a, n, cur[n], r), s[(size_t)r * sz + j], acc);
-            dd[j] = acc;
-          }
-        }
-        __syncwarp();
-      }
-      // z = V_{N-1} . a_N   (V_{N-1} has R_N entries; for N == 1, V_1 is the scalar)
-      double z1 = 0.0, z2 = 0.0;
-      if (a.N == 1) {
-        z1 = V1[0];
-        if (a.g2) z2 = V1[1];
-      } else {
-        const double* src = (a.N == 2) ? V1 : wst + a.lofs[a.N - 1];
-        const int RN = a.R[a.N - 1];
-        for (int r = lane; r < RN; r += 32) {
-          const double f = fac(a, a.N - 1, cur[a.N - 1], r);
-          z1 = fma(f, src[r], z1);
-          if (a.g2) z2 = fma(f, src[(a.N == 2 ? a.lsz[1] : a.lstore) + r], z2);
-        }
-        z1 = warp_sum(z1);
-        if (a.g2) z2 = warp_sum(z2);
-      }
-      if (lane == 0) { a.z1[u] = z1; if (a.z2) a.z2[u] = z2; }
-      for (int n = 0; n < a.N; ++n) prev[n] = cur[n];
-      __syncwarp();
+__global__ void k_piece_count(const int* seg_begin, const int* seg_end, int I1, int CH,
+                              int64_t* pcnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I1; i += gridDim.x * blockDim.x) {
+    const int len = seg_end[i] - seg_begin[i];
+    pcnt[i] = len > 0 ? (len + CH - 1) / CH : 0;
+  }
+}
+
+__global__ void k_piece_fill(const int* seg_begin, const int* seg_end, int I1, int CH,
+                             const int64_t* pcnt, const int64_t* pstart, int* p_i1, int* p_u0,
+                             int* p_u1) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I1; i += gridDim.x * blockDim.x) {
+    const int b = seg_begin[i], e = seg_end[i];
+    for (int64_t q = 0; q < pcnt[i]; ++q) {
+      const int64_t p = pstart[i] + q;
+      const int u0 = b + (int)q * CH;
+      p_i1[p] = i;
+      p_u0[p] = u0;
+      p_u1[p] = min(e, u0 + CH);
     }
   }
 }
 
+// V_1[v][i1][j] = sum_{r_1} A^(1)[i1][r_1] g_v[r_1 * lsz1 + j] for the segments with rows.
+__global__ void k_walk_v1(WalkArgs a) {
+  const int L1 = a.lsz[1];
+  const int nvec = a.g2 ? 2 : 1;
+  const int64_t total = (int64_t)a.I1 * L1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i1 = (int)(t / L1), j = (int)(t % L1);
+    if (a.pcnt[i1] == 0) continue;
+    for (int v = 0; v < nvec; ++v) {
+      const double* g = v ? a.g2 : a.g1;
+      double acc = 0.0;
+      for (int r = 0; r < a.R[0]; ++r) acc = fma(fac(a, 0, (uint32_t)i1, r), g[(size_t)r * L1 + j], acc);
+      a.V1[((size_t)v * a.I1 + i1) * L1 + j] = acc;
+    }
+  }
+}
+
+// z = sum over the trailing modes L..N-1 of (x)_{l >= L} a_l[r_l] * V[r_L, ..., r_{N-1}]
+// for this lane's row; F holds the lane's factor rows, entry (mode l, column r)
+// at F[(fofs[l] + r) * 32 + lane].  Nested loops with runtime ranks; the
+// innermost level is one FMA per element of V.
+template <int N, int L>
+struct FlatDot {
+  static __device__ __forceinline__ void run(const WalkArgs& a, const double* V1, const double* V2,
+                                             bool two, const double* F, int lane, double* z1,
+                                             double* z2) {
+    double s1 = 0.0, s2 = 0.0;
+    const int step = a.lsz[L + 1];
+    for (int r = 0; r < a.R[L]; ++r) {
+      double t1, t2;
+      FlatDot<N, L + 1>::run(a, V1 + r * step, V2 + r * step, two, F, lane, &t1, &t2);
+      const double f = F[(a.fofs[L] + r) * 32 + lane];
+      s1 = fma(f, t1, s1);
+      if (two) s2 = fma(f, t2, s2);
+    }
+    *z1 = s1;
+    *z2 = s2;
+  }
+};
+template <int N>
+struct FlatDot<N, N> {
+  static __device__ __forceinline__ void run(const WalkArgs&, const double* V1, const double* V2,
+                                             bool, const double*, int, double* z1, double* z2) {
+    *z1 = V1[0];
+    *z2 = V2[0];
+  }
+};
+
+// z_u = k_u . g for the rows of one piece per warp, one row per lane: V_1 of
+// the piece's i_1 (shared by its rows) is copied to shared memory, each lane
+// stages its own factor rows of modes 2..N, and contracts them against V_1.
+template <int N>
+__global__ void __launch_bounds__(WK_WARPS * 32) k_walk_dot(WalkArgs a) {
+  extern __shared__ double sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * WK_WARPS + warp;
+  if (p >= *a.npieces) return;                              // warp-uniform; no CTA barriers below
+  const bool two = a.g2 != nullptr;
+  const int nvec = two ? 2 : 1;
+  const int L1 = a.lsz[1];
+  double* V = sm + (size_t)warp * (nvec * L1 + 32 * a.fstore);
+  double* F = V + nvec * L1;
+  const int i1 = a.p_i1[p], u0 = a.p_u0[p], u1 = a.p_u1[p];
+  for (int v = 0; v < nvec; ++v) {
+    const double* src = a.V1 + ((size_t)v * a.I1 + i1) * L1;
+    for (int j = lane; j < L1; j += 32) V[v * L1 + j] = src[j];
+  }
+  const double* V2 = V + (two ? L1 : 0);
+  for (int base = u0; base < u1; base += 32) {
+    const int u = base + lane;
+    const bool act = u < u1;
+    __syncwarp();
+    for (int n = 1; n < N; ++n) {
+      const uint32_t i = act ? __ldg(a.idx[n] + u) : 0u;
+      for (int r = 0; r < a.R[n]; ++r) F[(a.fofs[n] + r) * 32 + lane] = act ? fac(a, n, i, r) : 0.0;
+    }
+    __syncwarp();
+    double z1, z2;
+    FlatDot<N, 1>::run(a, V, V2, two, F, lane, &z1, &z2);
+    if (act) {
+      a.z1[u] = z1;
+      if (a.z2) a.z2[u] = z2;
+    }
+  }
+}
+
+template <int N>
 __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy(WalkArgs a) {
   extern __shared__ double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // per warp: accumulators W_1 .. W_{N-1} (level n has lsz[n] entries) at lofs[n]
-  double* wst = sm + warp * a.lstore;
-  double* Wsum = sm + WK_WARPS * a.lstore;                  // lsz[1]: combined W_1
-  for (int i1 = blockIdx.x; i1 < a.I1; i1 += gridDim.x) {
-    const int s0 = a.seg_begin[i1], s1 = a.seg_end[i1];
-    if (s1 <= s0) continue;
-    for (int e = lane; e < a.lstore; e += 32) wst[e] = 0.0;
-    __syncwarp();
-    const int len = s1 - s0;
-    const int per = (len + WK_WARPS - 1) / WK_WARPS;
-    const int u0 = s0 + warp * per, u1 = min(s1, u0 + per);
-    uint32_t prev[TUCKER_MAX_ORDER];
-    double cprev = 0.0;
-    bool have = false;
-    for (int u = u0; u <= u1; ++u) {
+  const int64_t p = (int64_t)blockIdx.x * WK_WARPS + warp;
+  if (p >= *a.npieces) return;                              // warp-uniform
+  double* wst = sm + (size_t)warp * a.lstore;               // W_1 .. W_{N-1} at lofs[n]
+  const int u0 = a.p_u0[p], u1 = a.p_u1[p];
+  for (int e = lane; e < a.lstore; e += 32) wst[e] = 0.0;
+  __syncwarp();
+  uint32_t prev[TUCKER_MAX_ORDER];
+  double cprev = 0.0;
+  bool have = false;
+  // batches of 32 rows; after the last row one more step (j == cnt of the
+  // final batch, or an empty batch at base == u1) flushes every level
+  for (int base = u0; base <= u1; base += 32) {
+    const int cnt = min(32, u1 - base);
+    uint32_t mine[TUCKER_MAX_ORDER];
+    double cm = 0.0;
+    for (int n = 1; n < N; ++n) mine[n] = lane < cnt ? __ldg(a.idx[n] + base + lane) : 0u;
+    if (lane < cnt) cm = a.coef * a.ca[base + lane] * (a.cb ? a.cb[base + lane] : 1.0);
+    for (int j = 0; j <= cnt; ++j) {
+      const bool last = (j == cnt);
+      if (last && cnt == 32) break;                          // rows continue in the next batch
       uint32_t cur[TUCKER_MAX_ORDER];
       int lvl = 1;                                           // levels >= lvl are flushed
-      const bool last = (u == u1);
+      double c = 0.0;
       if (!last) {
-        for (int n = 0; n < a.N; ++n) cur[n] = a.idx[n][u];
-        lvl = a.N;
-        for (int n = a.N - 1; n >= 1; --n)
+        for (int n = 1; n < N; ++n) cur[n] = __shfl_sync(0xffffffffu, mine[n], j);
+        c = __shfl_sync(0xffffffffu, cm, j);
+        lvl = N;
+        for (int n = N - 1; n >= 1; --n)
           if (!have || cur[n] != prev[n]) lvl = n;
       }
       if (have) {
         // fold the previous row: W_{N-1} += c * a_N ; then W_{n-1} += a_n (x) W_n for n > lvl
-        if (a.N >= 2) {
-          double* WN1 = wst + a.lofs[a.N - 1];
-          const int RN = a.R[a.N - 1];
-          for (int r = lane; r < RN; r += 32) WN1[r] = fma(cprev, fac(a, a.N - 1, prev[a.N - 1], r), WN1[r]);
+        if (N >= 2) {
+          double* WN1 = wst + a.lofs[N - 1];
+          const int RN = a.R[N - 1];
+          for (int r = lane; r < RN; r += 32) WN1[r] = fma(cprev, fac(a, N - 1, prev[N - 1], r), WN1[r]);
           __syncwarp();
-          for (int n = a.N - 1; n > lvl; --n) {
-            // W_{n-1}[r * lsz[n] + j] += a_{n-1}[r] * W_n[j]; W_n = 0
+          for (int n = N - 1; n > lvl; --n) {
             const int sz = a.lsz[n];
             double* lo = wst + a.lofs[n];
             double* up = wst + a.lofs[n - 1];
             const int Rm = a.R[n - 1];
             for (int e = lane; e < Rm * sz; e += 32) {
-              const int r = e / sz, j = e % sz;
-              up[e] = fma(fac(a, n - 1, prev[n - 1], r), lo[j], up[e]);
+              const int r = e / sz, jj = e - r * sz;
+              up[e] = fma(fac(a, n - 1, prev[n - 1], r), lo[jj], up[e]);
             }
             __syncwarp();
-            for (int j = lane; j < sz; j += 32) lo[j] = 0.0;
+            for (int jj = lane; jj < sz; jj += 32) lo[jj] = 0.0;
             __syncwarp();
           }
         } else {
@@ -188,18 +253,28 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy(WalkArgs a) {
         }
       }
       if (last) break;
-      cprev = a.coef * a.ca[u] * (a.cb ? a.cb[u] : 1.0);
-      for (int n = 0; n < a.N; ++n) prev[n] = cur[n];
+      cprev = c;
+      for (int n = 1; n < N; ++n) prev[n] = cur[n];
       have = true;
     }
-    // combine the warps' W_1 in a fixed order
-    __syncthreads();
-    for (int e = threadIdx.x; e < a.lsz[1]; e += blockDim.x) {
-      double v = 0.0;
-      for (int w = 0; w < WK_WARPS; ++w) v += sm[w * a.lstore + a.lofs[1] + e];
-      a.W1[(size_t)i1 * a.lsz[1] + e] = v;
-    }
-    __syncthreads();
+    if (cnt < 32) break;
+  }
+  const int L1 = a.lsz[1];
+  double* out = a.Wp + (size_t)p * L1;
+  for (int e = lane; e < L1; e += 32) out[e] = wst[a.lofs[1] + e];
+}
+
+// W1[i1][j] = sum of the piece partials of segment i1 (fixed order); 0 if empty.
+__global__ void k_walk_reduce(WalkArgs a) {
+  const int L1 = a.lsz[1];
+  const int64_t total = (int64_t)a.I1 * L1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i1 = (int)(t / L1), j = (int)(t % L1);
+    const int64_t p0 = a.pstart[i1], np = a.pcnt[i1];
+    double s = 0.0;
+    for (int64_t q = 0; q < np; ++q) s += a.Wp[(size_t)(p0 + q) * L1 + j];
+    a.W1[t] = s;
   }
 }
 
@@ -228,107 +303,231 @@ __global__ void k_walk_expand(WalkArgs a, const double* base, const double* diag
 
 // ------------------------------------------------------------------ host side
 
-struct WalkPlan {
-  WalkArgs a;
-  size_t smem_dot, smem_axpy;
+struct WalkGeom {
+  int64_t I1;
+  int L1;
+  int CH;
+  int64_t maxP;
 };
 
-static WalkPlan walk_plan(const RowSet& s, int64_t I1, int* seg_begin, int* seg_end, double* W1) {
-  WalkPlan p;
-  memset(&p, 0, sizeof(p));
-  WalkArgs& a = p.a;
-  a.N = s.N;
-  a.is64 = s.is64;
-  a.d = s.d;
-  a.I1 = (int)I1;
-  for (int n = 0; n < s.N; ++n) { a.R[n] = s.R[n]; a.A[n] = s.A[n]; a.idx[n] = s.idx[n]; }
-  a.lsz[s.N] = 1;
-  for (int n = s.N - 1; n >= 0; --n) a.lsz[n] = a.lsz[n + 1] * s.R[n];
+static WalkGeom walk_geom(int64_t I1, int d, int R1, int64_t cap, int sms) {
+  WalkGeom g;
+  g.I1 = I1;
+  g.L1 = d / R1;
+  const int64_t c = cap > 0 ? cap : 1;
+  // about 32 pieces (warps) per SM, and no more than WK_PIECE_TARGET pieces
+  int64_t want = (int64_t)sms * 32;
+  if (want > WK_PIECE_TARGET) want = WK_PIECE_TARGET;
+  if (want < 1) want = 1;
+  const int64_t ch = (c + want - 1) / want;
+  g.CH = (int)(ch < WK_MIN_ROWS ? WK_MIN_ROWS : ch);
+  g.maxP = (c + g.CH - 1) / g.CH + (I1 < c ? I1 : c);
+  return g;
+}
+
+// Scratch layout (doubles): seg_begin/seg_end (I1 ints each) | pcnt, pstart (I1 int64
+// each) + npieces | p_i1, p_u0, p_u1 (maxP ints each) | W1 (I1 x L1) | V1 (2 x I1 x L1)
+// or Wp (maxP x L1), whichever is larger (dot and axpy do not overlap).
+struct WalkPtrs {
+  int* seg_begin;
+  int* seg_end;
+  int64_t* pcnt;
+  int64_t* pstart;
+  int64_t* npieces;
+  int* p_i1;
+  int* p_u0;
+  int* p_u1;
+  double* W1;
+  double* V1;
+  double* Wp;
+};
+
+static size_t walk_carve(const WalkGeom& g, double* base, WalkPtrs* w) {
+  size_t off = 0;
+  auto take = [&](size_t doubles) {
+    double* p = base ? base + off : nullptr;
+    off += (doubles + 1) & ~size_t(1);                 // 16-byte aligned pieces
+    return p;
+  };
+  double* sb = take((size_t)g.I1);                     // 2 * I1 ints
+  double* pc = take((size_t)2 * g.I1 + 1);
+  double* pi = take(((size_t)3 * g.maxP + 1) / 2);
+  w->W1 = take((size_t)g.I1 * g.L1);
+  const size_t v1 = (size_t)2 * g.I1 * g.L1, wp = (size_t)g.maxP * g.L1;
+  double* big = take(v1 > wp ? v1 : wp);
+  w->seg_begin = reinterpret_cast<int*>(sb);
+  w->seg_end = w->seg_begin ? w->seg_begin + g.I1 : nullptr;
+  w->pcnt = reinterpret_cast<int64_t*>(pc);
+  w->pstart = w->pcnt ? w->pcnt + g.I1 : nullptr;
+  w->npieces = w->pstart ? w->pstart + g.I1 : nullptr;
+  w->p_i1 = reinterpret_cast<int*>(pi);
+  w->p_u0 = w->p_i1 ? w->p_i1 + g.maxP : nullptr;
+  w->p_u1 = w->p_u0 ? w->p_u0 + g.maxP : nullptr;
+  w->V1 = big;
+  w->Wp = big;
+  return off + 64;
+}
+
+static void level_sizes(int N, const int* R, int* lsz, int* lofs, int* lstore, int* fofs,
+                        int* fstore) {
+  lsz[N] = 1;
+  for (int n = N - 1; n >= 0; --n) lsz[n] = lsz[n + 1] * R[n];
   int off = 0;
-  for (int n = 1; n <= s.N; ++n) { a.lofs[n] = off; off += a.lsz[n]; }
-  a.lstore = (off + 1) & ~1;
-  a.seg_begin = seg_begin;
-  a.seg_end = seg_end;
-  a.W1 = W1;
-  p.smem_dot = (size_t)(2 * a.lsz[1] + WK_WARPS * 2 * a.lstore) * sizeof(double);
-  p.smem_axpy = (size_t)(WK_WARPS * a.lstore + a.lsz[1]) * sizeof(double);
-  return p;
+  for (int n = 1; n <= N; ++n) { lofs[n] = off; off += lsz[n]; }
+  *lstore = (off + 1) & ~1;
+  off = 0;
+  for (int n = 1; n < N; ++n) { fofs[n] = off; off += R[n]; }
+  *fstore = off;
 }
 
 // Whether the level vectors of the walk fit in shared memory for these ranks.
 bool walk_fits(int N, const int* R, int64_t I1) {
-  int lsz[TUCKER_MAX_ORDER + 1];
-  lsz[N] = 1;
-  for (int n = N - 1; n >= 0; --n) lsz[n] = lsz[n + 1] * R[n];
-  int store = 0;
-  for (int n = 1; n <= N; ++n) store += lsz[n];
-  store = (store + 1) & ~1;
-  const size_t dot = (size_t)(2 * lsz[1] + WK_WARPS * 2 * store) * 8;
-  const size_t axpy = (size_t)(WK_WARPS * store + lsz[1]) * 8;
-  return dot <= 200 * 1024 && axpy <= 200 * 1024 && (double)I1 * lsz[1] <= double(1 << 27);
+  int lsz[TUCKER_MAX_ORDER + 1], lofs[TUCKER_MAX_ORDER + 1], fofs[TUCKER_MAX_ORDER];
+  int lstore, fstore;
+  level_sizes(N, R, lsz, lofs, &lstore, fofs, &fstore);
+  return (size_t)lstore * 8 <= (size_t)WK_WARP_SMEM &&
+         dot_warp_bytes(lsz[1], fstore, 2) <= (size_t)WK_DOT_SMEM &&
+         (double)I1 * lsz[1] <= double(1 << 26);
 }
 
-size_t walk_scratch_doubles(int64_t I1, int d, int R1) {
-  const double n = (double)I1 * (d / R1);
-  if (n > double(1 << 27)) return (size_t)2 * I1 + 64;      // level walk not used
-  return (size_t)2 * I1 + (size_t)I1 * (d / R1) + 64;
+size_t walk_scratch_doubles(int64_t I1, int d, int R1, int64_t cap, int sms) {
+  if ((double)I1 * (d / R1) > double(1 << 26)) return 64;    // level walk not used
+  WalkPtrs w;
+  return walk_carve(walk_geom(I1, d, R1, cap, sms), nullptr, &w);
 }
 
-// Build the segment table for a sample (once per sample set).
-tucker_status walk_segments(tucker_handle* h, const RowSet& s, int64_t I1, int64_t cap,
-                            double* scratch) {
-  int* seg_begin = reinterpret_cast<int*>(scratch);
-  int* seg_end = seg_begin + I1;
-  TK_CUDA(h, cudaMemsetAsync(seg_begin, 0, sizeof(int) * 2 * I1, h->stream));
-  int grid = ceil_div(cap, 256);
-  if (grid > h->num_sms * 8) grid = h->num_sms * 8;
-  if (grid < 1) grid = 1;
+static WalkArgs walk_args(const RowSet& s, const WalkGeom& g, const WalkPtrs& w) {
+  WalkArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = s.N;
+  a.d = s.d;
+  a.I1 = (int)g.I1;
+  a.CH = g.CH;
+  for (int n = 0; n < s.N; ++n) {
+    a.R[n] = s.R[n];
+    a.A[n] = static_cast<const double*>(s.A[n]);
+    a.idx[n] = s.idx[n];
+  }
+  level_sizes(s.N, s.R, a.lsz, a.lofs, &a.lstore, a.fofs, &a.fstore);
+  a.seg_begin = w.seg_begin;
+  a.seg_end = w.seg_end;
+  a.pcnt = w.pcnt;
+  a.pstart = w.pstart;
+  a.npieces = w.npieces;
+  a.p_i1 = w.p_i1;
+  a.p_u0 = w.p_u0;
+  a.p_u1 = w.p_u1;
+  a.V1 = w.V1;
+  a.Wp = w.Wp;
+  a.W1 = w.W1;
+  return a;
+}
+
+static int grid_for(tucker_handle* h, int64_t work, int threads) {
+  int64_t g = (work + threads - 1) / threads;
+  if (g > (int64_t)h->num_sms * 16) g = (int64_t)h->num_sms * 16;
+  return (int)(g < 1 ? 1 : g);
+}
+
+using WalkKernel = void (*)(WalkArgs);
+
+static WalkKernel walk_dot_kernel(int N) {
+  switch (N) {
+    case 1: return k_walk_dot<1>;
+    case 2: return k_walk_dot<2>;
+    case 3: return k_walk_dot<3>;
+    case 4: return k_walk_dot<4>;
+    case 5: return k_walk_dot<5>;
+    case 6: return k_walk_dot<6>;
+    case 7: return k_walk_dot<7>;
+    default: return k_walk_dot<8>;
+  }
+}
+
+static WalkKernel walk_axpy_kernel(int N) {
+  switch (N) {
+    case 1: return k_walk_axpy<1>;
+    case 2: return k_walk_axpy<2>;
+    case 3: return k_walk_axpy<3>;
+    case 4: return k_walk_axpy<4>;
+    case 5: return k_walk_axpy<5>;
+    case 6: return k_walk_axpy<6>;
+    case 7: return k_walk_axpy<7>;
+    default: return k_walk_axpy<8>;
+  }
+}
+
+// One warp per piece: ceil(maxP / WK_WARPS) CTAs; warps past the piece count exit.
+static tucker_status launch_by_order(tucker_handle* h, WalkKernel k, int64_t maxP, size_t smem,
+                                     const WalkArgs& a) {
+  TK_CUDA(h, cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
   TK_COUNT(h);
-  k_segments<<<grid, 256, 0, h->stream>>>(s.idx[0], s.n_rows, seg_begin, seg_end);
+  k<<<(int)((maxP + WK_WARPS - 1) / WK_WARPS), WK_WARPS * 32, smem, h->stream>>>(a);
   TK_LAUNCH(h);
   return TUCKER_OK;
 }
 
-static WalkPlan plan_from_scratch(const RowSet& s, int64_t I1, double* scratch) {
-  int* seg_begin = reinterpret_cast<int*>(scratch);
-  int* seg_end = seg_begin + I1;
-  double* W1 = scratch + I1 + 2;          // after 2*I1 ints (= I1 doubles), 16-byte aligned
-  return walk_plan(s, I1, seg_begin, seg_end, W1);
-}
-
-static int walk_grid(tucker_handle* h, int64_t I1) {
-  int64_t g = I1;
-  if (g > (int64_t)h->num_sms * 8) g = (int64_t)h->num_sms * 8;
-  return (int)(g < 1 ? 1 : g);
+// Build the segment and piece tables for a sample (once per sample set).
+tucker_status walk_segments(tucker_handle* h, const RowSet& s, int64_t I1, const WalkBuf& wb) {
+  if (!walk_fits(s.N, s.R, I1)) return TUCKER_OK;          // the per-element kernels are used
+  const WalkGeom g = walk_geom(I1, s.d, s.R[0], wb.cap, h->num_sms);
+  WalkPtrs w;
+  walk_carve(g, wb.p, &w);
+  TK_CUDA(h, cudaMemsetAsync(w.seg_begin, 0, sizeof(int) * 2 * I1, h->stream));
+  TK_COUNT(h);
+  k_segments<<<grid_for(h, wb.cap, 256), 256, 0, h->stream>>>(s.idx[0], s.n_rows, w.seg_begin,
+                                                              w.seg_end);
+  TK_LAUNCH(h);
+  TK_COUNT(h);
+  k_piece_count<<<grid_for(h, I1, 256), 256, 0, h->stream>>>(w.seg_begin, w.seg_end, (int)I1,
+                                                             g.CH, w.pcnt);
+  TK_LAUNCH(h);
+  launch_scan_i64(h, w.pcnt, w.pstart, I1, w.npieces);
+  TK_LAUNCH(h);
+  TK_COUNT(h);
+  k_piece_fill<<<grid_for(h, I1, 128), 128, 0, h->stream>>>(w.seg_begin, w.seg_end, (int)I1, g.CH,
+                                                            w.pcnt, w.pstart, w.p_i1, w.p_u0,
+                                                            w.p_u1);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
 }
 
 // z1[u] = k_u . g1, z2[u] = k_u . g2 (g2 nullable) for the real rows.
-tucker_status walk_dot(tucker_handle* h, const RowSet& s, int64_t I1, double* scratch,
+tucker_status walk_dot(tucker_handle* h, const RowSet& s, int64_t I1, const WalkBuf& wb,
                        const double* g1, const double* g2, double* z1, double* z2) {
-  WalkPlan p = plan_from_scratch(s, I1, scratch);
-  p.a.g1 = g1; p.a.g2 = g2; p.a.z1 = z1; p.a.z2 = z2;
-  TK_CUDA(h, cudaFuncSetAttribute(k_walk_dot, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)p.smem_dot));
+  if (!s.is64) return fail(h, TUCKER_EINTERNAL, "walk needs FP64 factors");
+  const WalkGeom g = walk_geom(I1, s.d, s.R[0], wb.cap, h->num_sms);
+  WalkPtrs w;
+  walk_carve(g, wb.p, &w);
+  WalkArgs a = walk_args(s, g, w);
+  a.g1 = g1; a.g2 = g2; a.z1 = z1; a.z2 = z2;
+  const int nvec = g2 ? 2 : 1;
+  const size_t smem = (size_t)WK_WARPS * dot_warp_bytes(a.lsz[1], a.fstore, nvec);
   TK_COUNT(h);
-  k_walk_dot<<<walk_grid(h, I1), WK_WARPS * 32, p.smem_dot, h->stream>>>(p.a);
+  k_walk_v1<<<grid_for(h, I1 * a.lsz[1], 256), 256, 0, h->stream>>>(a);
   TK_LAUNCH(h);
+  TK_TRY(launch_by_order(h, walk_dot_kernel(s.N), g.maxP, smem, a));
   return TUCKER_OK;
 }
 
 // out = base - diag .* y + coef * sum_u ca_u cb_u k_u  (real rows)
-tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, double* scratch,
+tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, const WalkBuf& wb,
                         const double* ca, const double* cb, double coef, const double* base,
                         const double* diag, const double* y, double* out) {
-  WalkPlan p = plan_from_scratch(s, I1, scratch);
-  p.a.ca = ca; p.a.cb = cb; p.a.coef = coef;
-  TK_CUDA(h, cudaMemsetAsync(p.a.W1, 0, sizeof(double) * (size_t)I1 * p.a.lsz[1], h->stream));
-  TK_CUDA(h, cudaFuncSetAttribute(k_walk_axpy, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)p.smem_axpy));
+  if (!s.is64) return fail(h, TUCKER_EINTERNAL, "walk needs FP64 factors");
+  const WalkGeom g = walk_geom(I1, s.d, s.R[0], wb.cap, h->num_sms);
+  WalkPtrs w;
+  walk_carve(g, wb.p, &w);
+  WalkArgs a = walk_args(s, g, w);
+  a.ca = ca; a.cb = cb; a.coef = coef;
+  const size_t smem = (size_t)WK_WARPS * a.lstore * 8;
+  TK_TRY(launch_by_order(h, walk_axpy_kernel(s.N), g.maxP, smem, a));
   TK_COUNT(h);
-  k_walk_axpy<<<walk_grid(h, I1), WK_WARPS * 32, p.smem_axpy, h->stream>>>(p.a);
+  k_walk_reduce<<<grid_for(h, I1 * a.lsz[1], 256), 256, 0, h->stream>>>(a);
   TK_LAUNCH(h);
   TK_COUNT(h);
-  k_walk_expand<<<ceil_div(s.d, 8), 256, 0, h->stream>>>(p.a, base, diag, y, out);
+  k_walk_expand<<<ceil_div(s.d, 8), 256, 0, h->stream>>>(a, base, diag, y, out);
   TK_LAUNCH(h);
   return TUCKER_OK;
 }
