@@ -4,23 +4,29 @@
 // a sum of outer products as in the proof of Thm 4.2).  The design matrix is
 // never stored: operand tiles of x are generated in shared memory.
 //
-// Pipeline per CTA (one 128 x 256 output tile of the upper triangle of G and
-// one contiguous range of 64-sample chunks):
-//   pack kernel  : per chunk, the factor rows of its samples are laid out
-//                  entry-major [e][s] (e over (n, r_n), s over 64 samples) in
-//                  FP32, with sqrt(w) folded into mode 1 -> one contiguous block;
+// Work unit: one 256 x 256 tile of the upper triangle of G (two 128 x 256
+// tcgen05 accumulators in TMEM, 512 columns) and one contiguous range of
+// sample chunks (64 samples for BF16, 32 for TF32).
+//   pack kernel  : per chunk, the factor rows of its samples laid out
+//                  entry-major [e][s] (e over (n, r_n)) in FP32, sqrt(w) folded
+//                  into mode 1; for BF16 the samples of each 8-sample group
+//                  are split into two 16-byte halves so that lanes reading
+//                  consecutive groups hit consecutive shared-memory banks;
 //   producer warp: 1-D bulk TMA (cp.async.bulk) of each chunk block into a
-//                  4-deep shared-memory ring (mbarrier transaction counts);
-//   builder warps: P[rho][s] = prod_{n<N} a_n[s][r_n] (rho = r / R_N) for the
-//                  tile's row ranges, then x[r][s] = P[rho(r)][s] * a_N[s][r mod R_N]
-//                  rounded to BF16 (or TF32) into K-major, 128-byte-swizzled
-//                  operand tiles (rows = d index, 128 bytes of samples per row);
-//   MMA thread   : tcgen05.mma.cta_group::1 (M = 128, N = 256) accumulating in
-//                  TMEM (FP32), tcgen05.commit frees the operand stage;
-//   epilogue     : tcgen05.ld of the accumulator, FP32 partial tile to global.
+//                  ring of table stages (mbarrier transaction counts);
+//   builder warps: the 512 operand rows (256 of B = the tile's columns, 256
+//                  of A = its rows; A is B on diagonal tiles) are cut into
+//                  groups of 8 rows and, inside a group, into runs of rows
+//                  that share (r_1, ..., r_{N-1}); a thread owns one (group,
+//                  8-sample octet), forms p = prod_{n<N} a_n over the octet once
+//                  per run and writes x = p * a_N[r_N] rounded once to BF16
+//                  (or TF32) into K-major, 128-byte-swizzled operand rows;
+//   MMA thread   : per chunk 2 x 4 tcgen05.mma (M = 128, N = 256, K = 16 or 8)
+//                  into the two TMEM accumulators; tcgen05.commit frees the
+//                  operand stage;
+//   epilogue     : tcgen05.ld of both accumulators, FP32 partial tile to global.
 // A reduction kernel sums the sample splits in a fixed order into the
-// symmetric FP64 G.  Tiles whose row range lies inside their column range
-// reuse the B operand rows as A (no second build).
+// symmetric FP64 G.
 // Every wait is bounded: on timeout the kernel records TUCKER_EINTERNAL,
 // waits (bounded) for its MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
@@ -31,25 +37,37 @@
 
 namespace tk {
 
-constexpr int TC_M = 128;          // rows of an output tile (TMEM lanes)
-constexpr int TC_N = 256;          // columns of an output tile (TMEM columns)
+constexpr int TC_M = 128;          // rows of one MMA (TMEM lanes)
+constexpr int TC_N = 256;          // columns of one MMA
+constexpr int TC_TILE = 256;       // output tile edge (two accumulators)
 constexpr int TC_ROWB = 128;       // bytes of K per operand row (one swizzle atom)
 constexpr int TC_STAGES = 2;       // operand stages
-constexpr int TC_TSTAGES = 4;      // sample-table stages
-constexpr int TC_BUILD_WARPS = 8;
+constexpr int TC_BUILD_WARPS = 16;
 constexpr int TC_THREADS = (TC_BUILD_WARPS + 2) * 32;   // + MMA warp + TMA warp
+constexpr int TC_GROUPS = 2 * TC_TILE / 8;               // 8-row groups of B then A
+constexpr int TC_TMEM_COLS = 512;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
 
 template <int PREC> struct TcTraits;
 template <> struct TcTraits<TUCKER_PREC_BF16> {
   static constexpr int CS = 64;        // samples per chunk (128 bytes of BF16)
-  static constexpr int PER16 = 8;      // samples per 16-byte unit
   static constexpr uint32_t FMT = 1;   // BF16 in the instruction descriptor
+  static constexpr int KSTEPS = 4;     // MMAs of K = 16 per chunk
 };
 template <> struct TcTraits<TUCKER_PREC_TF32> {
   static constexpr int CS = 32;
-  static constexpr int PER16 = 4;
   static constexpr uint32_t FMT = 2;   // TF32
+  static constexpr int KSTEPS = 4;     // MMAs of K = 8 per chunk
+};
+
+// One run of rows inside an 8-row group: rows row0 .. row0 + n - 1 of the
+// group have a_N columns t0 .. t0 + n - 1 and share the product of modes
+// 1..N-1, whose table rows start at po[0..N-2] (element offsets into a chunk
+// block).  zero: rows beyond d.
+struct TcRun {
+  uint8_t row0, n, t0, zero;
+  int po[TUCKER_MAX_ORDER - 1];
+  int pad;                         // 36 bytes: the 4 groups a warp reads fall in distinct banks
 };
 
 struct TcArgs {
@@ -58,13 +76,13 @@ struct TcArgs {
   int off[TUCKER_MAX_ORDER];          // entry offset of mode n in a chunk block
   int sumR;
   int d;
-  int RN;                              // R_N
-  int Ti, Tj;                          // tiles along rows (128) and columns (256)
+  int Tt;                              // tiles along each edge
   int ntiles;
   int nsplit;
+  int tstages;                         // chunk-table stages
   const float* pack;                   // [chunks][sumR][CS]
   const int* n_rows;
-  float* partial;                      // [nsplit][ntiles][128][256]
+  float* partial;                      // [nsplit][ntiles][256][256]
   int* status;
 };
 
@@ -164,7 +182,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // ------------------------------------------------------------------ pack
-// pack[q][e][s] = value e (mode n, column r) of sample q*CS + s; mode 1 scaled by sqrt(w).
+// pack[q][e][pos(s)] = value e (mode n, column r) of sample q*CS + s; mode 1
+// scaled by sqrt(w).  BF16: within each 64-sample chunk, sample s = 8c + j is
+// stored at 4c + j (j < 4) or 32 + 4c + (j - 4) (j >= 4).
 struct PackArgs {
   int N;
   int R[TUCKER_MAX_ORDER];
@@ -176,9 +196,15 @@ struct PackArgs {
   const double* w;
   const int* n_rows;
   int CS;
-  int64_t cap_chunks;
+  int perm;
   float* pack;
 };
+
+__device__ __forceinline__ int pack_pos(int s, int perm) {
+  if (!perm) return s;
+  const int c = s >> 3, j = s & 7;
+  return j < 4 ? 4 * c + j : 32 + 4 * c + (j - 4);
+}
 
 __global__ void k_tc_pack(PackArgs a) {
   const int nrows = *a.n_rows;
@@ -195,85 +221,99 @@ __global__ void k_tc_pack(PackArgs a) {
       int n = 0;
       while (n + 1 < a.N && e >= a.off[n + 1]) ++n;
       const int r = e - a.off[n];
-      v = (float)load_as_double(a.A[n], (int64_t)a.idx[n][u] * a.R[n] + r, a.is64);
-      if (n == 0) v = (float)(sqrt(a.w[u]) * load_as_double(a.A[n], (int64_t)a.idx[n][u] * a.R[n] + r, a.is64));
+      const double f = load_as_double(a.A[n], (int64_t)a.idx[n][u] * a.R[n] + r, a.is64);
+      v = (float)(n == 0 ? sqrt(a.w[u]) * f : f);
     }
-    a.pack[t] = v;
+    a.pack[t - s + pack_pos(s, a.perm)] = v;
   }
 }
 
 // --------------------------------------------------------------- the SYRK
+__device__ __forceinline__ void tile_of(int tile, int Tt, int* ti, int* tj) {
+  // upper tiles (ti <= tj), column-major packed: tile = tj (tj + 1) / 2 + ti
+  int j = (int)((sqrtf(8.0f * tile + 1.0f) - 1.0f) * 0.5f);
+  while ((j + 1) * (j + 2) / 2 <= tile) ++j;
+  while (j * (j + 1) / 2 > tile) --j;
+  *tj = j;
+  *ti = tile - j * (j + 1) / 2;
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
   using Tr = TcTraits<PREC>;
   constexpr int CS = Tr::CS;
   extern __shared__ __align__(1024) unsigned char smraw[];
-  // carve shared memory (1024-byte aligned operand stages first)
   const uint32_t base_u = smem_u32(smraw);
   unsigned char* sm = smraw + ((1024 - (base_u & 1023)) & 1023);
-  unsigned char* opA = sm;                                   // STAGES x 128 rows x 128 B
-  unsigned char* opB = opA + TC_STAGES * TC_M * TC_ROWB;      // STAGES x 256 rows x 128 B
-  float* tab = reinterpret_cast<float*>(opB + TC_STAGES * TC_N * TC_ROWB);   // TSTAGES x sumR x CS
+  unsigned char* opA = sm;                                          // STAGES x 256 rows x 128 B
+  unsigned char* opB = opA + TC_STAGES * TC_TILE * TC_ROWB;         // STAGES x 256 rows x 128 B
+  float* tab = reinterpret_cast<float*>(opB + TC_STAGES * TC_TILE * TC_ROWB);
   const int tab_elems = a.sumR * CS;
-  float* Ptab = tab + TC_TSTAGES * tab_elems;                 // (N/RN + 2 + M/RN + 2) x CS
-  const int nPB = TC_N / a.RN + 2, nPA = TC_M / a.RN + 2;
-  // decode tables (fixed per tile): T entry offsets of each P row, and for
-  // each operand row its P row and its column of a_N (0xffff: beyond d)
-  int* Poff = reinterpret_cast<int*>(Ptab + (nPB + nPA) * CS);           // (nPB+nPA) x (N-1)
-  uint32_t* rowinfo = reinterpret_cast<uint32_t*>(Poff + (nPB + nPA) * TUCKER_MAX_ORDER);  // 384
-  __shared__ uint64_t bar_tfull[TC_TSTAGES], bar_tempty[TC_TSTAGES];
+  TcRun* runs = reinterpret_cast<TcRun*>(tab + (size_t)a.tstages * tab_elems);   // [groups][8]
+  uint8_t* nruns = reinterpret_cast<uint8_t*>(runs + TC_GROUPS * 8);             // [groups]
+  __shared__ uint64_t bar_tfull[4], bar_tempty[4];
   __shared__ uint64_t bar_ofull[TC_STAGES], bar_oempty[TC_STAGES], bar_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // tile (ti, tj) of the upper triangle and the chunk range of this split
-  int rem = blockIdx.x % a.ntiles, tj = 0;
-  while (true) {
-    const int cnt = min(2 * tj + 2, a.Ti);
-    if (rem < cnt) break;
-    rem -= cnt;
-    ++tj;
-  }
-  const int ti = rem;
+  int ti, tj;
+  tile_of(blockIdx.x % a.ntiles, a.Tt, &ti, &tj);
   const int split = blockIdx.x / a.ntiles;
   const int nrows = *a.n_rows;
   const int nch = (nrows + CS - 1) / CS;
   const int cps = (nch + a.nsplit - 1) / a.nsplit;
   const int c0 = split * cps, c1 = min(nch, c0 + cps);
   const int nchunks = max(0, c1 - c0);
-  const int row0 = ti * TC_M, col0 = tj * TC_N;
-  const bool a_in_b = row0 >= col0 && row0 + TC_M <= col0 + TC_N;
-  const int rho0B = col0 / a.RN, rho0A = row0 / a.RN;
+  const int row0 = ti * TC_TILE, col0 = tj * TC_TILE;
+  const bool diag = ti == tj;                     // A rows are the B rows
+  const int ngroups = diag ? TC_GROUPS / 2 : TC_GROUPS;
+  const int RN = a.R[a.N - 1];
 
-  for (int pr = threadIdx.x; pr < nPB + nPA; pr += blockDim.x) {
-    int rr = pr < nPB ? rho0B + pr : rho0A + (pr - nPB);
-    for (int n = a.N - 2; n >= 0; --n) {
-      Poff[pr * TUCKER_MAX_ORDER + n] = (a.off[n] + rr % a.R[n]) * CS;
-      rr /= a.R[n];
+  // runs of each 8-row group (group g < 32: B rows col0 + 8g.., else A rows)
+  for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    const int gbase = g < TC_GROUPS / 2 ? col0 + 8 * g : row0 + 8 * (g - TC_GROUPS / 2);
+    int cnt = 0, i = 0;
+    while (i < 8) {
+      TcRun run;
+      const int grow = gbase + i;
+      run.row0 = (uint8_t)i;
+      if (grow >= a.d) {
+        run.n = (uint8_t)(8 - i); run.t0 = 0; run.zero = 1;
+        for (int n = 0; n < TUCKER_MAX_ORDER - 1; ++n) run.po[n] = 0;
+      } else {
+        const int rho = grow / RN, t = grow - rho * RN;
+        int n = min(8 - i, RN - t);
+        if (grow + n > a.d) n = a.d - grow;
+        run.n = (uint8_t)n; run.t0 = (uint8_t)t; run.zero = 0;
+        int rr = rho;
+        for (int m = a.N - 2; m >= 0; --m) {
+          run.po[m] = (a.off[m] + rr % a.R[m]) * CS;
+          rr /= a.R[m];
+        }
+        for (int m = a.N - 1; m < TUCKER_MAX_ORDER - 1; ++m) run.po[m] = 0;
+      }
+      runs[g * 8 + cnt++] = run;
+      i += run.n;
     }
-  }
-  for (int r = threadIdx.x; r < TC_N + TC_M; r += blockDim.x) {
-    const bool isB = r < TC_N;
-    const int grow = isB ? col0 + r : row0 + (r - TC_N);
-    uint32_t info = 0xffffffffu;
-    if (grow < a.d) {
-      const int rho = grow / a.RN, t = grow - rho * a.RN;
-      const int prow = isB ? rho - rho0B : nPB + (rho - rho0A);
-      info = ((uint32_t)prow << 16) | (uint32_t)t;
-    }
-    rowinfo[r] = info;
+    nruns[g] = (uint8_t)cnt;
   }
   if (threadIdx.x == 0) {
-    for (int i = 0; i < TC_TSTAGES; ++i) { mbar_init(&bar_tfull[i], 1); mbar_init(&bar_tempty[i], TC_BUILD_WARPS * 32); }
-    for (int i = 0; i < TC_STAGES; ++i) { mbar_init(&bar_ofull[i], TC_BUILD_WARPS * 32); mbar_init(&bar_oempty[i], 1); }
+    for (int i = 0; i < a.tstages; ++i) {
+      mbar_init(&bar_tfull[i], 1);
+      mbar_init(&bar_tempty[i], TC_BUILD_WARPS * 32);
+    }
+    for (int i = 0; i < TC_STAGES; ++i) {
+      mbar_init(&bar_ofull[i], TC_BUILD_WARPS * 32);
+      mbar_init(&bar_oempty[i], 1);
+    }
     mbar_init(&bar_done, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == TC_BUILD_WARPS) {     // TMEM allocation: 256 FP32 columns
+  if (warp == TC_BUILD_WARPS) {     // TMEM allocation: two 256-column FP32 accumulators
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(&tmem_slot)), "r"(TC_N) : "memory");
+                 ::"r"(smem_u32(&tmem_slot)), "r"(TC_TMEM_COLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
@@ -286,9 +326,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
     if (lane == 0) {
       const uint32_t bytes = (uint32_t)tab_elems * 4u;
       for (int it = 0; it < nchunks; ++it) {
-        const int ts = it % TC_TSTAGES;
-        if (it >= TC_TSTAGES &&
-            !mbar_wait(&bar_tempty[ts], ((it / TC_TSTAGES) - 1) & 1, a.status, &abort_flag))
+        const int ts = it % a.tstages;
+        if (it >= a.tstages &&
+            !mbar_wait(&bar_tempty[ts], ((it / a.tstages) - 1) & 1, a.status, &abort_flag))
           break;
         mbar_expect_tx(&bar_tfull[ts], bytes);
         bulk_g2s(tab + (size_t)ts * tab_elems, a.pack + (size_t)(c0 + it) * tab_elems, bytes,
@@ -303,95 +343,139 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
         const int os = it % TC_STAGES;
         if (!mbar_wait(&bar_ofull[os], (it / TC_STAGES) & 1, a.status, &abort_flag)) break;
         tc_fence_after();
-        const uint32_t bB = smem_u32(opB + (size_t)os * TC_N * TC_ROWB);
-        const uint32_t bA = a_in_b ? bB + (uint32_t)(row0 - col0) * TC_ROWB
-                                   : smem_u32(opA + (size_t)os * TC_M * TC_ROWB);
+        const uint32_t bB = smem_u32(opB + (size_t)os * TC_TILE * TC_ROWB);
+        const uint32_t bA = diag ? bB : smem_u32(opA + (size_t)os * TC_TILE * TC_ROWB);
 #pragma unroll
-        for (int k = 0; k < 4; ++k)     // 4 x 32 bytes of K per 128-byte row
-          mma<PREC>(tmem, sw128_desc(bA + 32 * k), sw128_desc(bB + 32 * k), id,
-                    (it > 0 || k > 0) ? 1u : 0u);
+        for (int mb = 0; mb < 2; ++mb) {
+          const uint32_t aA = bA + (uint32_t)(mb * TC_M * TC_ROWB);
+#pragma unroll
+          for (int k = 0; k < Tr::KSTEPS; ++k)     // 32 bytes of K per MMA
+            mma<PREC>(tmem + (uint32_t)(mb * TC_N), sw128_desc(aA + 32 * k),
+                      sw128_desc(bB + 32 * k), id, (it > 0 || k > 0) ? 1u : 0u);
+        }
         mma_commit(&bar_oempty[os]);
       }
       mma_commit(&bar_done);
     }
   } else {
-    // ---------------- builders (warps 0..7)
-    const int bt = threadIdx.x;                       // 0..255
+    // ---------------- builders (warps 0..15): item = (8-row group, 16-byte octet)
+    const int bt = threadIdx.x;
+    const int aNoff = a.off[a.N - 1] * CS;
     for (int it = 0; it < nchunks; ++it) {
-      const int ts = it % TC_TSTAGES, os = it % TC_STAGES;
-      const bool ok1 = mbar_wait(&bar_tfull[ts], (it / TC_TSTAGES) & 1, a.status, &abort_flag);
-      const float* T = tab + (size_t)ts * tab_elems;
-      if (ok1) {
-        // P[rho][s] = prod over modes 1..N-1 of the factor entries of rho
-        for (int e = bt; e < (nPB + nPA) * CS; e += TC_BUILD_WARPS * 32) {
-          const int pr = e / CS, s = e % CS;          // CS is a power of two
-          const int* po = Poff + pr * TUCKER_MAX_ORDER;
-          float v = 1.f;
-          for (int n = 0; n < a.N - 1; ++n) v *= T[po[n] + s];
-          Ptab[pr * CS + s] = v;
-        }
-      }
-      // the operand stage must be free (MMAs of chunk it - STAGES done)
+      const int ts = it % a.tstages, os = it % TC_STAGES;
+      const bool ok1 = mbar_wait(&bar_tfull[ts], (it / a.tstages) & 1, a.status, &abort_flag);
       const bool ok2 = it < TC_STAGES ||
                        mbar_wait(&bar_oempty[os], ((it / TC_STAGES) - 1) & 1, a.status, &abort_flag);
-      if (!builders_all(ok1 && ok2)) break;            // uniform; also publishes Ptab
-      const float* aN = T + a.off[a.N - 1] * CS;
-      unsigned char* sB = opB + (size_t)os * TC_N * TC_ROWB;
-      unsigned char* sA = opA + (size_t)os * TC_M * TC_ROWB;
-      const int units = (TC_N + (a_in_b ? 0 : TC_M)) * 8;
-      for (int uidx = bt; uidx < units; uidx += TC_BUILD_WARPS * 32) {
-        const bool isB = uidx < TC_N * 8;
-        const int ul = isB ? uidx : uidx - TC_N * 8;
-        const int r = ul >> 3, c = ul & 7;
-        const uint32_t info = rowinfo[isB ? r : TC_N + r];
-        uint4 out = make_uint4(0, 0, 0, 0);
-        if (info != 0xffffffffu) {
-          const int t = (int)(info & 0xffffu);
-          const float* P = Ptab + (int)(info >> 16) * CS;
-          const int s0 = c * Tr::PER16;
+      if (!builders_all(ok1 && ok2)) break;            // uniform
+      const float* T = tab + (size_t)ts * tab_elems;
+      unsigned char* sB = opB + (size_t)os * TC_TILE * TC_ROWB;
+      unsigned char* sA = opA + (size_t)os * TC_TILE * TC_ROWB;
+      for (int item = bt; item < ngroups * 8; item += TC_BUILD_WARPS * 32) {
+        const int g = item >> 3, c = item & 7;
+        unsigned char* op = g < TC_GROUPS / 2 ? sB + (size_t)(8 * g) * TC_ROWB
+                                              : sA + (size_t)(8 * (g - TC_GROUPS / 2)) * TC_ROWB;
+        const int nr = nruns[g];
+        for (int j = 0; j < nr; ++j) {
+          const TcRun& run = runs[g * 8 + j];
+          const int gr0 = 8 * (g & (TC_GROUPS / 2 - 1)) + run.row0;   // row inside the operand
           if (PREC == TUCKER_PREC_BF16) {
-            const float4 p0 = *reinterpret_cast<const float4*>(P + s0);
-            const float4 p1 = *reinterpret_cast<const float4*>(P + s0 + 4);
-            const float4 q0 = *reinterpret_cast<const float4*>(aN + t * CS + s0);
-            const float4 q1 = *reinterpret_cast<const float4*>(aN + t * CS + s0 + 4);
-            out.x = pack_bf16(p0.x * q0.x, p0.y * q0.y);
-            out.y = pack_bf16(p0.z * q0.z, p0.w * q0.w);
-            out.z = pack_bf16(p1.x * q1.x, p1.y * q1.y);
-            out.w = pack_bf16(p1.z * q1.z, p1.w * q1.w);
+            // octet c: samples 8c..8c+7 at 4c..4c+3 and 32+4c..32+4c+3
+            float4 p0 = make_float4(1.f, 1.f, 1.f, 1.f), p1 = p0;
+            for (int m = 0; m < a.N - 1; ++m) {
+              const float4 v0 = *reinterpret_cast<const float4*>(T + run.po[m] + 4 * c);
+              const float4 v1 = *reinterpret_cast<const float4*>(T + run.po[m] + 32 + 4 * c);
+              p0.x *= v0.x; p0.y *= v0.y; p0.z *= v0.z; p0.w *= v0.w;
+              p1.x *= v1.x; p1.y *= v1.y; p1.z *= v1.z; p1.w *= v1.w;
+            }
+            if (run.n == 8 && !run.zero) {           // whole group: rows gr0 .. gr0 + 7
+              const float* aN = T + aNoff + run.t0 * CS + 4 * c;
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const float4 q0 = *reinterpret_cast<const float4*>(aN + q * CS);
+                const float4 q1 = *reinterpret_cast<const float4*>(aN + q * CS + 32);
+                uint4 out;
+                out.x = pack_bf16(p0.x * q0.x, p0.y * q0.y);
+                out.y = pack_bf16(p0.z * q0.z, p0.w * q0.w);
+                out.z = pack_bf16(p1.x * q1.x, p1.y * q1.y);
+                out.w = pack_bf16(p1.z * q1.z, p1.w * q1.w);
+                *reinterpret_cast<uint4*>(op + q * TC_ROWB + ((c ^ q) << 4)) = out;
+              }
+              continue;
+            }
+            for (int q = 0; q < run.n; ++q) {
+              const int row = gr0 + q;
+              uint4 out = make_uint4(0, 0, 0, 0);
+              if (!run.zero) {
+                const float* aN = T + aNoff + (run.t0 + q) * CS;
+                const float4 q0 = *reinterpret_cast<const float4*>(aN + 4 * c);
+                const float4 q1 = *reinterpret_cast<const float4*>(aN + 32 + 4 * c);
+                out.x = pack_bf16(p0.x * q0.x, p0.y * q0.y);
+                out.y = pack_bf16(p0.z * q0.z, p0.w * q0.w);
+                out.z = pack_bf16(p1.x * q1.x, p1.y * q1.y);
+                out.w = pack_bf16(p1.z * q1.z, p1.w * q1.w);
+              }
+              *reinterpret_cast<uint4*>(op + (size_t)(row - 8 * (g & (TC_GROUPS / 2 - 1))) * TC_ROWB +
+                                        ((c ^ (row & 7)) << 4)) = out;
+            }
           } else {
-            const float4 p0 = *reinterpret_cast<const float4*>(P + s0);
-            const float4 q0 = *reinterpret_cast<const float4*>(aN + t * CS + s0);
-            out.x = to_tf32(p0.x * q0.x);
-            out.y = to_tf32(p0.y * q0.y);
-            out.z = to_tf32(p0.z * q0.z);
-            out.w = to_tf32(p0.w * q0.w);
+            float4 p0 = make_float4(1.f, 1.f, 1.f, 1.f);
+            for (int m = 0; m < a.N - 1; ++m) {
+              const float4 v0 = *reinterpret_cast<const float4*>(T + run.po[m] + 4 * c);
+              p0.x *= v0.x; p0.y *= v0.y; p0.z *= v0.z; p0.w *= v0.w;
+            }
+            if (run.n == 8 && !run.zero) {           // whole group: rows gr0 .. gr0 + 7
+              const float* aN = T + aNoff + run.t0 * CS + 4 * c;
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const float4 q0 = *reinterpret_cast<const float4*>(aN + q * CS);
+                uint4 out;
+                out.x = to_tf32(p0.x * q0.x);
+                out.y = to_tf32(p0.y * q0.y);
+                out.z = to_tf32(p0.z * q0.z);
+                out.w = to_tf32(p0.w * q0.w);
+                *reinterpret_cast<uint4*>(op + q * TC_ROWB + ((c ^ q) << 4)) = out;
+              }
+              continue;
+            }
+            for (int q = 0; q < run.n; ++q) {
+              const int row = gr0 + q;
+              uint4 out = make_uint4(0, 0, 0, 0);
+              if (!run.zero) {
+                const float4 q0 = *reinterpret_cast<const float4*>(T + aNoff + (run.t0 + q) * CS + 4 * c);
+                out.x = to_tf32(p0.x * q0.x);
+                out.y = to_tf32(p0.y * q0.y);
+                out.z = to_tf32(p0.z * q0.z);
+                out.w = to_tf32(p0.w * q0.w);
+              }
+              *reinterpret_cast<uint4*>(op + (size_t)(row - 8 * (g & (TC_GROUPS / 2 - 1))) * TC_ROWB +
+                                        ((c ^ (row & 7)) << 4)) = out;
+            }
           }
         }
-        unsigned char* dst = (isB ? sB : sA) + r * TC_ROWB + ((c ^ (r & 7)) << 4);
-        *reinterpret_cast<uint4*>(dst) = out;
       }
       fence_proxy_async();          // generic-proxy writes -> visible to the tensor core
       mbar_arrive(&bar_tempty[ts]);
       mbar_arrive(&bar_ofull[os]);
-      asm volatile("bar.sync 1, %0;" ::"r"(TC_BUILD_WARPS * 32) : "memory");   // Ptab reuse
     }
   }
 
-  // ---------------- epilogue: warps 0..7 (two per TMEM lane quadrant)
+  // ---------------- epilogue: warps 0..15, four per TMEM lane quadrant
   __syncthreads();
-  float* outp = a.partial + ((size_t)split * a.ntiles + (blockIdx.x % a.ntiles)) * (TC_M * TC_N);
+  float* outp = a.partial + ((size_t)split * a.ntiles + (blockIdx.x % a.ntiles)) * (TC_TILE * TC_TILE);
   if (warp < TC_BUILD_WARPS) {
     bool ok = true;
     if (nchunks > 0) ok = mbar_wait(&bar_done, 0, a.status, &abort_flag);
     ok = __all_sync(0xffffffffu, ok);
     tc_fence_after();
-    const int quad = warp & 3, half = warp >> 2;         // lanes 32*quad.., columns half*128..
-    const int row = quad * 32 + lane;
-    for (int cb = 0; cb < TC_N / 2; cb += 16) {
-      const int col = half * (TC_N / 2) + cb;
+    const int quad = warp & 3, cg = warp >> 2;            // lanes 32*quad.., TMEM columns cg*128..
+    const int mb = cg >> 1;                                // accumulator
+    const int row = mb * TC_M + quad * 32 + lane;          // row of the 256 x 256 tile
+    for (int cb = 0; cb < 128; cb += 16) {
+      const int tcol = cg * 128 + cb;                      // TMEM column
+      const int col = (cg & 1) * 128 + cb;                 // column of the tile
       uint32_t v[16];
       if (nchunks > 0 && ok) {
-        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col;
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)tcol;
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
                      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
@@ -403,7 +487,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = 0u;
       }
-      float4* dst = reinterpret_cast<float4*>(outp + (size_t)row * TC_N + col);
+      float4* dst = reinterpret_cast<float4*>(outp + (size_t)row * TC_TILE + col);
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
@@ -414,39 +498,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
   __syncthreads();
   if (warp == TC_BUILD_WARPS) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
                  : "memory");
   }
 }
 
 // G[r][c] = G[c][r] = sum over splits of the partial tiles (upper instances only)
-__global__ void k_tc_reduce(const float* partial, int nsplit, int ntiles, int Ti, int d, double* G) {
-  int rem = blockIdx.y, tj = 0;
-  while (true) {
-    const int cnt = min(2 * tj + 2, Ti);
-    if (rem < cnt) break;
-    rem -= cnt;
-    ++tj;
-  }
-  const int ti = rem;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < TC_M * TC_N; e += gridDim.x * blockDim.x) {
-    const int r = ti * TC_M + e / TC_N, c = tj * TC_N + e % TC_N;
+__global__ void k_tc_reduce(const float* partial, int nsplit, int ntiles, int Tt, int d, double* G) {
+  int ti, tj;
+  tile_of(blockIdx.y, Tt, &ti, &tj);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < TC_TILE * TC_TILE;
+       e += gridDim.x * blockDim.x) {
+    const int r = ti * TC_TILE + e / TC_TILE, c = tj * TC_TILE + e % TC_TILE;
     if (r >= d || c >= d || r > c) continue;
     double v = 0.0;
     for (int sp = 0; sp < nsplit; ++sp)
-      v += (double)partial[((size_t)sp * ntiles + blockIdx.y) * (TC_M * TC_N) + e];
+      v += (double)partial[((size_t)sp * ntiles + blockIdx.y) * (TC_TILE * TC_TILE) + e];
     G[(size_t)r * d + c] = v;
     G[(size_t)c * d + r] = v;
   }
 }
 
 // ------------------------------------------------------------------ host side
-static int tiles_of(int d, int* Ti, int* Tj) {
-  *Ti = (d + TC_M - 1) / TC_M;
-  *Tj = (d + TC_N - 1) / TC_N;
-  int n = 0;
-  for (int j = 0; j < *Tj; ++j) n += std::min(2 * j + 2, *Ti);
-  return n;
+static int tiles_of(int d, int* Tt) {
+  *Tt = (d + TC_TILE - 1) / TC_TILE;
+  return *Tt * (*Tt + 1) / 2;
 }
 
 static int chunk_samples(int prec) { return prec == TUCKER_PREC_BF16 ? 64 : 32; }
@@ -470,28 +546,27 @@ int gram_tc_supported(int prec, int d) {
   return (prec == TUCKER_PREC_BF16 || prec == TUCKER_PREC_TF32) && d >= 1 && d <= 8192;
 }
 
-static size_t tc_smem_bytes(int sumR, int RN, int CS) {
-  const size_t ops = (size_t)TC_STAGES * (TC_M + TC_N) * TC_ROWB;
-  const size_t tab = (size_t)TC_TSTAGES * sumR * CS * 4;
-  const size_t P = (size_t)(TC_N / RN + 2 + TC_M / RN + 2) * CS * 4;
-  const size_t dec = (size_t)(TC_N / RN + 2 + TC_M / RN + 2) * TUCKER_MAX_ORDER * 4 + (TC_M + TC_N) * 4;
-  return ops + tab + P + dec + 1024;
+static size_t tc_smem_bytes(int sumR, int CS, int tstages) {
+  const size_t ops = (size_t)TC_STAGES * 2 * TC_TILE * TC_ROWB;
+  const size_t tab = (size_t)tstages * sumR * CS * 4;
+  const size_t runs = (size_t)TC_GROUPS * 8 * sizeof(TcRun) + TC_GROUPS;
+  return ops + tab + runs + 1024;
 }
 
 size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int sumR, int64_t cap) {
-  int Ti, Tj;
-  const int ntiles = tiles_of(d, &Ti, &Tj);
+  int Tt;
+  const int ntiles = tiles_of(d, &Tt);
   const int CS = chunk_samples(prec);
   const int64_t nch = (cap + CS - 1) / CS;
   const int ns = pick_splits(ntiles, nch, h->num_sms);
   // pack (sum R_n entries per sample) + partial tiles
-  return (size_t)nch * CS * sumR * 4 + 4096 + (size_t)ns * ntiles * TC_M * TC_N * 4 + 4096;
+  return (size_t)nch * CS * sumR * 4 + 4096 + (size_t)ns * ntiles * TC_TILE * TC_TILE * 4 + 4096;
 }
 
 tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_t cap, char* ws,
                              size_t ws_bytes, double* G) {
-  int Ti, Tj;
-  const int ntiles = tiles_of(s.d, &Ti, &Tj);
+  int Tt;
+  const int ntiles = tiles_of(s.d, &Tt);
   const int CS = chunk_samples(prec);
   const int64_t nch = (cap + CS - 1) / CS;
   const int ns = pick_splits(ntiles, nch, h->num_sms);
@@ -511,27 +586,29 @@ tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_
   a.sumR = p.sumR = sumR;
   if ((size_t)sumR * CS * 4 % 16 != 0) return fail(h, TUCKER_EINTERNAL, "pack block not 16-byte sized");
   a.d = s.d;
-  a.RN = s.R[s.N - 1];
-  a.Ti = Ti; a.Tj = Tj; a.ntiles = ntiles; a.nsplit = ns;
+  a.Tt = Tt; a.ntiles = ntiles; a.nsplit = ns;
   a.n_rows = p.n_rows = s.n_rows;
   a.status = h->d_status;
   const size_t pack_bytes = (size_t)nch * sumR * CS * 4;
-  const size_t part_bytes = (size_t)ns * ntiles * TC_M * TC_N * 4;
+  const size_t part_bytes = (size_t)ns * ntiles * TC_TILE * TC_TILE * 4;
   if (pack_bytes + part_bytes + 512 > ws_bytes) return fail(h, TUCKER_EINTERNAL, "tc workspace too small");
   float* pack = reinterpret_cast<float*>(ws);
   float* partial = reinterpret_cast<float*>(ws + ((pack_bytes + 255) & ~size_t(255)));
   p.is64 = s.is64;
   p.w = s.w;
   p.CS = CS;
-  p.cap_chunks = nch;
+  p.perm = prec == TUCKER_PREC_BF16;
   p.pack = pack;
   a.pack = pack;
   a.partial = partial;
-  // >= 120 KB keeps one CTA per SM (the kernel allocates 256 TMEM columns)
-  const size_t smem = std::max<size_t>(tc_smem_bytes(sumR, a.RN, CS), 120 * 1024);
+  // as many chunk-table stages (2..4) as shared memory allows
+  int tst = 4;
+  while (tst > 2 && tc_smem_bytes(sumR, CS, tst) > 227 * 1024) --tst;
+  const size_t smem = tc_smem_bytes(sumR, CS, tst);
   if (smem > 227 * 1024)
     return fail(h, TUCKER_ENOTSUP, "tensor-core Gram needs %zu bytes of shared memory "
-                "(sum R_n = %d, R_N = %d)", smem, sumR, a.RN);
+                "(sum R_n = %d)", smem, sumR);
+  a.tstages = tst;
   int pg = (int)std::min<int64_t>((nch * sumR * CS + 255) / 256, (int64_t)h->num_sms * 16);
   if (pg < 1) pg = 1;
   TK_COUNT(h);
@@ -543,7 +620,7 @@ tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_
   kern<<<ntiles * ns, TC_THREADS, smem, h->stream>>>(a);
   TK_LAUNCH(h);
   TK_COUNT(h);
-  k_tc_reduce<<<dim3(32, ntiles), 256, 0, h->stream>>>(partial, ns, ntiles, Ti, s.d, G);
+  k_tc_reduce<<<dim3(64, ntiles), 256, 0, h->stream>>>(partial, ns, ntiles, Tt, s.d, G);
   TK_LAUNCH(h);
   return TUCKER_OK;
 }
