@@ -151,6 +151,8 @@ typedef struct {
   double refine_rel;    /* last ||correction|| / ||g|| of the refinement */
   uint64_t solve_id;    /* identifies the cached Cholesky factor for the adjoint */
   int64_t launches;     /* CUDA kernels this call launched */
+  double ms_factor;     /* the Cholesky factorisation kernel alone (inside ms_solve) */
+  double ms_gram_kernel;/* the Kronecker SYRK kernel alone (inside ms_gram) */
 } tucker_stats;
 
 typedef struct tucker_handle tucker_handle;

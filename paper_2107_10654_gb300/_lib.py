@@ -37,7 +37,8 @@ class TuckerStats(C.Structure):
                 ("ms_gather", C.c_double), ("ms_gram", C.c_double), ("ms_solve", C.c_double),
                 ("ms_total", C.c_double), ("n_unique", C.c_int64), ("n_draws", C.c_int64),
                 ("n_real", C.c_int64), ("refine_iters", C.c_int), ("refine_rel", C.c_double),
-                ("solve_id", C.c_uint64), ("launches", C.c_int64)]
+                ("solve_id", C.c_uint64), ("launches", C.c_int64), ("ms_factor", C.c_double),
+                ("ms_gram_kernel", C.c_double)]
 
 
 _P = C.c_void_p

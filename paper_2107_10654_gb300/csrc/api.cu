@@ -56,6 +56,11 @@ tucker_status launch_to_f32(tucker_handle* h, const double* in, size_t n, float*
 tucker_status launch_gemv_resid(tucker_handle* h, const double* M, int d, const double* g,
                                 const double* hv, double* r);
 size_t chol_inv_doubles(int d);
+int chol_inverse_fits(int d);
+tucker_status chol_inverse32(tucker_handle* h, const float* L, const float* Linv, int d, float* X,
+                             float* XC);
+tucker_status chol_solve_inv32(tucker_handle* h, const float* X, const float* XC, int d,
+                               const double* rhs, double* g, double* tmp);
 tucker_status launch_regdiag(tucker_handle* h, double* out, int d, double lambda, const double* D);
 tucker_status launch_refine_update(tucker_handle* h, double* g, const double* r, int d,
                                    double* out2);
@@ -313,21 +318,22 @@ static tucker_status chol_reserve(tucker_handle* h, int d) {
   CholCache& c = h->chol;
   const size_t need = (size_t)d * d;
   const size_t inv = chol_inv_doubles(d);
-  if (c.cap < need) {
+  const size_t xinv = chol_inverse_fits(d) ? 2 * need : 0;
+  // FP64: L, LT, regdiag, tmp, Linv; FP32: L32, LT32, Linv32 (+ X32, XC32 for small d)
+  const size_t bytes = (2 * need + 2 * (size_t)d + inv + 64) * sizeof(double) +
+                       (2 * need + inv + 64 + xinv) * sizeof(float);
+  if (c.cap < bytes) {
     TK_CUDA(h, cudaStreamSynchronize(h->stream));
     if (c.L) cudaFree(c.L);
     c.L = nullptr;
     c.cap = 0;
     void* p = nullptr;
-    // FP64: L, LT, regdiag, tmp, Linv; FP32: L32, LT32, Linv32
-    const size_t total = (2 * need + 2 * (size_t)d + inv + 64) * sizeof(double) +
-                         (2 * need + inv + 64) * sizeof(float);
-    if (cudaMalloc(&p, total) != cudaSuccess) {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
       cudaGetLastError();
       return fail(h, TUCKER_ENOMEM, "Cholesky buffer for d = %d", d);
     }
     c.L = static_cast<double*>(p);
-    c.cap = need;
+    c.cap = bytes;
   }
   c.LT = c.L + need;
   c.regdiag = c.LT + need;
@@ -336,6 +342,8 @@ static tucker_status chol_reserve(tucker_handle* h, int d) {
   c.L32 = reinterpret_cast<float*>(c.Linv + inv + 64);
   c.LT32 = c.L32 + need;
   c.Linv32 = c.LT32 + need;
+  c.X32 = xinv ? c.Linv32 + inv + 64 : nullptr;
+  c.XC32 = c.X32 ? c.X32 + need : nullptr;
   c.d = d;
   c.id = 0;
   return TUCKER_OK;
@@ -349,15 +357,23 @@ static tucker_status chol_reserve(tucker_handle* h, int d) {
 static tucker_status factorize(tucker_handle* h, double* L, int d, int prec) {
   CholCache& c = h->chol;
   c.mixed = h->solver == TUCKER_SOLVER_MIXED;
-  c.prep64 = c.prep32 = 0;
+  c.prep64 = c.prep32 = c.inv32 = 0;
   if (c.mixed) {
     TK_TRY(launch_to_f32(h, L, (size_t)d * d, c.L32));
+    ev_record(h, h->timing, 8);
     TK_TRY(cholesky32(h, c.L32, d));
+    ev_record(h, h->timing, 9);
     TK_TRY(chol_prepare32(h, c.L32, d, c.LT32, c.Linv32));
     c.prep32 = 1;
+    if (c.X32) {
+      TK_TRY(chol_inverse32(h, c.L32, c.Linv32, d, c.X32, c.XC32));
+      c.inv32 = 1;
+    }
     return TUCKER_OK;
   }
+  ev_record(h, h->timing, 8);
   TK_TRY(cholesky(h, L, d));
+  ev_record(h, h->timing, 9);
   if (prec == TUCKER_PREC_FP64) {
     TK_TRY(chol_prepare(h, L, d, c.LT, c.Linv));
     c.prep64 = 1;
@@ -365,6 +381,10 @@ static tucker_status factorize(tucker_handle* h, double* L, int d, int prec) {
     TK_TRY(launch_to_f32(h, L, (size_t)d * d, c.L32));
     TK_TRY(chol_prepare32(h, c.L32, d, c.LT32, c.Linv32));
     c.prep32 = 1;
+    if (c.X32) {
+      TK_TRY(chol_inverse32(h, c.L32, c.Linv32, d, c.X32, c.XC32));
+      c.inv32 = 1;
+    }
   }
   return TUCKER_OK;
 }
@@ -374,8 +394,10 @@ static tucker_status factorize(tucker_handle* h, double* L, int d, int prec) {
 // the rounded copy exists; FP64 otherwise.
 static tucker_status chol_solve(tucker_handle* h, int d, const double* rhs, double* g, int prec) {
   CholCache& c = h->chol;
-  if (c.mixed || (c.prep32 && prec != TUCKER_PREC_FP64))
+  if (c.mixed || (c.prep32 && prec != TUCKER_PREC_FP64)) {
+    if (c.inv32) return chol_solve_inv32(h, c.X32, c.XC32, d, rhs, g, c.tmp);
     return chol_solve32(h, c.L32, c.LT32, c.Linv32, d, rhs, g, c.tmp);
+  }
   if (!c.prep64) {
     TK_TRY(chol_prepare(h, c.L, d, c.LT, c.Linv));
     c.prep64 = 1;
@@ -651,6 +673,11 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
     return fail(h, TUCKER_EINVAL, "key range overflow");
   const bool timing = stats != nullptr;
   const int64_t launches0 = h->launches;
+  struct TimingFlag {
+    tucker_handle* h;
+    ~TimingFlag() { h->timing = 0; }
+  } timing_guard{h};
+  h->timing = timing;
   SketchBufs b;
   memset(&b, 0, sizeof(b));
   Arena sz(nullptr);
@@ -732,6 +759,8 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
     stats->refine_rel = rel;
     stats->solve_id = h->chol.id;
     stats->launches = h->launches - launches0;
+    stats->ms_factor = ev_ms(h, 8, 9);
+    stats->ms_gram_kernel = ev_ms(h, 10, 11);
     if (st != TUCKER_OK) h->chol.id = 0;
     return st;
   }

@@ -40,11 +40,14 @@ struct CholCache {
   float* L32 = nullptr;       // FP32 factor of the mixed solver (d x d)
   float* LT32 = nullptr;      // its transpose
   float* Linv32 = nullptr;    // its inverted 64 x 64 diagonal blocks
+  float* X32 = nullptr;       // explicit L32^-1, row-major (small d only)
+  float* XC32 = nullptr;      // the same, column-major
+  int inv32 = 0;          // X32 / XC32 are ready
   int mixed = 0;          // the cached factor is the FP32 one (L then holds M itself)
   int prep64 = 0;         // LT / Linv of the FP64 factor are ready
   int prep32 = 0;         // L32 / LT32 / Linv32 are ready (the FP32 factor, or the FP64 one rounded)
   int d = 0;
-  size_t cap = 0;         // elements of L allocated
+  size_t cap = 0;         // bytes allocated behind L
   uint64_t id = 0;        // solve id of the cached factor (0 = none)
 };
 
@@ -64,6 +67,7 @@ struct tucker_handle {
   uint64_t next_solve_id = 1;
   int64_t launches = 0;         // kernels launched by this handle (all calls)
   int solver = 0;               // tucker_solver: FP64 Cholesky (0) or mixed (1)
+  int timing = 0;               // record per-kernel events (ev[8..11]) during this call
   cudaEvent_t ev[16];
   char err[512];
 };

@@ -214,16 +214,19 @@ tucker_status launch_gram_simt(tucker_handle* h, const RowSet& s, int use64, int
   const int Tt = (s.d + ST - 1) / ST;
   const int tiles = Tt * (Tt + 1) / 2;
   dim3 grid(tiles, nsplit);
+  if (h->timing) cudaEventRecord(h->ev[10], h->stream);
   if (use64) {
     TK_COUNT(h);
     k_syrk_simt<double><<<grid, 256, 0, h->stream>>>(s, (double*)partial, nsplit);
     TK_LAUNCH(h);
+    if (h->timing) cudaEventRecord(h->ev[11], h->stream);
     TK_COUNT(h);
     k_tile_reduce<double><<<tiles, 256, 0, h->stream>>>((double*)partial, nsplit, tiles, s.d, G);
   } else {
     TK_COUNT(h);
     k_syrk_simt<float><<<grid, 256, 0, h->stream>>>(s, (float*)partial, nsplit);
     TK_LAUNCH(h);
+    if (h->timing) cudaEventRecord(h->ev[11], h->stream);
     TK_COUNT(h);
     k_tile_reduce<float><<<tiles, 256, 0, h->stream>>>((float*)partial, nsplit, tiles, s.d, G);
   }

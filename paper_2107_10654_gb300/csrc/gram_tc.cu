@@ -511,9 +511,20 @@ __global__ void k_tc_reduce(const float* partial, int nsplit, int ntiles, int Tt
        e += gridDim.x * blockDim.x) {
     const int r = ti * TC_TILE + e / TC_TILE, c = tj * TC_TILE + e % TC_TILE;
     if (r >= d || c >= d || r > c) continue;
-    double v = 0.0;
-    for (int sp = 0; sp < nsplit; ++sp)
-      v += (double)partial[((size_t)sp * ntiles + blockIdx.y) * (TC_TILE * TC_TILE) + e];
+    // FP32 partial sums of FP32 accumulators (their error is far below the
+    // operand rounding), four interleaved chains, combined in a fixed order
+    const float* src = partial + (size_t)blockIdx.y * (TC_TILE * TC_TILE) + e;
+    const size_t stride = (size_t)ntiles * (TC_TILE * TC_TILE);
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+    int sp = 0;
+    for (; sp + 4 <= nsplit; sp += 4) {
+      v0 += src[(size_t)sp * stride];
+      v1 += src[(size_t)(sp + 1) * stride];
+      v2 += src[(size_t)(sp + 2) * stride];
+      v3 += src[(size_t)(sp + 3) * stride];
+    }
+    for (; sp < nsplit; ++sp) v0 += src[(size_t)sp * stride];
+    const double v = ((double)v0 + (double)v1) + ((double)v2 + (double)v3);
     G[(size_t)r * d + c] = v;
     G[(size_t)c * d + r] = v;
   }
@@ -616,9 +627,11 @@ tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_
   TK_LAUNCH(h);
   auto kern = prec == TUCKER_PREC_BF16 ? k_syrk_tc<TUCKER_PREC_BF16> : k_syrk_tc<TUCKER_PREC_TF32>;
   TK_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (h->timing) cudaEventRecord(h->ev[10], h->stream);
   TK_COUNT(h);
   kern<<<ntiles * ns, TC_THREADS, smem, h->stream>>>(a);
   TK_LAUNCH(h);
+  if (h->timing) cudaEventRecord(h->ev[11], h->stream);
   TK_COUNT(h);
   k_tc_reduce<<<dim3(64, ntiles), 256, 0, h->stream>>>(partial, ns, ntiles, Tt, s.d, G);
   TK_LAUNCH(h);

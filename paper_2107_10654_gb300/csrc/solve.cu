@@ -439,6 +439,123 @@ tucker_status chol_solve32(tucker_handle* h, const float* L, const float* LT, co
   return chol_solve_t<float>(h, L, LT, Linv, d, rhs, g, tmp);
 }
 
+// ------------------------------------------------ explicit inverse (small FP32 factors)
+// For d <= INV_MAX_D the refinement applies M~^-1 = X^T X with X = L^-1 held
+// explicitly: two GEMVs per solve instead of 2 d / 64 dependent block steps.
+// X is built column by column: CTA c solves L x = e_j for its INV_COLS
+// columns by forward block substitution with the inverted 64 x 64 diagonal
+// blocks; the columns are independent, so no grid-wide barrier is needed.
+// X is stored row-major and column-major (XC[j][i] = X[i][j]) so that both
+// GEMVs read contiguous rows.
+constexpr int INV_COLS = 4;
+constexpr int INV_THREADS = 256;
+constexpr int INV_MAX_D = 1024;
+
+__global__ void __launch_bounds__(INV_THREADS) k_tri_inv_cols(const float* L, const float* Linv,
+                                                              int d, float* X, float* XC) {
+  extern __shared__ float bsm[];                  // right-hand sides, [INV_COLS][d]
+  __shared__ float Ls[SB][SB + 1];
+  __shared__ float yk[SB][INV_COLS];
+  const int j0 = blockIdx.x * INV_COLS;
+  const int ncol = min(INV_COLS, d - j0);
+  const int nblk = (d + SB - 1) / SB;
+  const int kb0 = j0 / SB;
+  for (int e = threadIdx.x; e < INV_COLS * d; e += blockDim.x) {
+    const int c = e / d, i = e % d;
+    bsm[e] = (c < ncol && i == j0 + c) ? 1.f : 0.f;
+  }
+  // rows above the first block with a nonzero right-hand side are zero
+  for (int e = threadIdx.x; e < kb0 * SB * INV_COLS; e += blockDim.x) {
+    const int i = e / INV_COLS, c = e % INV_COLS;
+    if (c < ncol) {
+      X[(size_t)i * d + j0 + c] = 0.f;
+      XC[(size_t)(j0 + c) * d + i] = 0.f;
+    }
+  }
+  __syncthreads();
+  for (int kb = kb0; kb < nblk; ++kb) {
+    const int k = kb * SB, nb = min(SB, d - k);
+    const float* Li = Linv + (size_t)kb * SB * SB;
+    for (int e = threadIdx.x; e < SB * SB; e += blockDim.x) Ls[e / SB][e % SB] = Li[e];
+    __syncthreads();
+    {                                             // yk = Linv_kk b_k: thread (row i, column c)
+      const int i = threadIdx.x >> 2, c = threadIdx.x & 3;
+      float v = 0.f;
+      if (i < nb && c < ncol) {
+        const float* bc = bsm + (size_t)c * d + k;
+        for (int jj = 0; jj <= i; ++jj) v = fmaf(Ls[i][jj], bc[jj], v);
+        X[(size_t)(k + i) * d + j0 + c] = v;
+        XC[(size_t)(j0 + c) * d + k + i] = v;
+      }
+      yk[i][c] = v;
+    }
+    __syncthreads();
+    // b_i -= L_ik y_k for the rows below the block, one thread per row
+    const int nb4 = (d & 3) == 0 ? nb / 4 : 0;    // 16-byte loads need 16-byte aligned rows
+    for (int i = k + nb + threadIdx.x; i < d; i += blockDim.x) {
+      const float4* lr = reinterpret_cast<const float4*>(L + (size_t)i * d + k);
+      float acc[INV_COLS] = {0.f, 0.f, 0.f, 0.f};
+      for (int q = 0; q < nb4; ++q) {
+        const float4 l4 = lr[q];
+#pragma unroll
+        for (int c = 0; c < INV_COLS; ++c)
+          acc[c] = fmaf(l4.x, yk[4 * q][c], fmaf(l4.y, yk[4 * q + 1][c],
+                   fmaf(l4.z, yk[4 * q + 2][c], fmaf(l4.w, yk[4 * q + 3][c], acc[c]))));
+      }
+      for (int jj = nb4 * 4; jj < nb; ++jj) {
+        const float l = L[(size_t)i * d + k + jj];
+#pragma unroll
+        for (int c = 0; c < INV_COLS; ++c) acc[c] = fmaf(l, yk[jj][c], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < INV_COLS; ++c) bsm[(size_t)c * d + i] -= acc[c];
+    }
+    __syncthreads();
+  }
+}
+
+// out_i = sum_j A[i][j] v_j over the lower (tri_lower) or upper part of a
+// row-major FP32 matrix, FP64 vectors; one warp per row.
+__global__ void k_gemv_tri(const float* A, int d, const double* v, double* out, int lower) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = warp; i < d; i += nwarps) {
+    const float* ar = A + (size_t)i * d;
+    const int j0 = lower ? 0 : i, j1 = lower ? i + 1 : d;
+    float acc = 0.f;
+    for (int j = j0 + lane; j < j1; j += 32) acc = fmaf(ar[j], (float)v[j], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) out[i] = (double)acc;
+  }
+}
+
+tucker_status chol_inverse32(tucker_handle* h, const float* L, const float* Linv, int d, float* X,
+                             float* XC) {
+  if (d > INV_MAX_D || !X || !XC) return fail(h, TUCKER_EINTERNAL, "explicit inverse not sized");
+  const size_t smem = (size_t)INV_COLS * d * sizeof(float);
+  TK_COUNT(h);
+  k_tri_inv_cols<<<(d + INV_COLS - 1) / INV_COLS, INV_THREADS, smem, h->stream>>>(L, Linv, d, X, XC);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+int chol_inverse_fits(int d) { return d <= INV_MAX_D; }
+
+// g = X^T (X rhs) with tmp holding X rhs (g may alias rhs).
+tucker_status chol_solve_inv32(tucker_handle* h, const float* X, const float* XC, int d,
+                               const double* rhs, double* g, double* tmp) {
+  int grid = (d + 7) / 8;
+  if (grid > h->num_sms * 8) grid = h->num_sms * 8;
+  TK_COUNT(h);
+  k_gemv_tri<<<grid, 256, 0, h->stream>>>(X, d, rhs, tmp, 1);
+  TK_LAUNCH(h);
+  TK_COUNT(h);
+  k_gemv_tri<<<grid, 256, 0, h->stream>>>(XC, d, tmp, g, 0);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
 tucker_status launch_to_f32(tucker_handle* h, const double* in, size_t n, float* out) {
   int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)h->num_sms * 16);
   if (grid < 1) grid = 1;
