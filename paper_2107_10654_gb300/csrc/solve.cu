@@ -61,9 +61,9 @@ __device__ __forceinline__ bool pivot_ok(T p) { return p > T(0) && p <= tmax<T>(
 // of the CTA).  Right-looking, one barrier per pivot: in phase j the scaled
 // column l_ij = a_ij y_j (y_j = p_j^-1/2) is written to the unused upper
 // triangle a[j][i] while the trailing entries are updated from the unscaled
-// column, a_ic -= (a_ij r_j) a_cj with r_j = y_j^2.  Thread 0 updates the next
-// diagonal entry first and computes its y, so the square-root chain overlaps
-// the rest of the update.  Returns false (in every thread) on a pivot that is
+// column, a_ic -= (a_ij r_j) a_cj with r_j = y_j^2.  Warp 0 updates the next
+// diagonal entry and computes its y while the other warps update the rest, so
+// the square-root chain overlaps the update (and no warp serialises both).  Returns false (in every thread) on a pivot that is
 // not positive and finite; every CTA computes the same.
 template <class T>
 __device__ bool factor_diag_block(const T* M, int d, int k, int nb, T (*a)[CB + 1],
@@ -86,26 +86,37 @@ __device__ bool factor_diag_block(const T* M, int d, int k, int nb, T (*a)[CB + 
     if (bad) return false;                          // read after a barrier: uniform
     const T y = ys[j], r = rs[j];
     const int m = nb - 1 - j;                       // trailing size
-    if (tid == 0) {
-      a[j][j] = a[j][j] * y;                        // l_jj = p_j / sqrt(p_j)
+    if (tid < 32) {
+      // warp 0: the pivot chain, computed redundantly by its lanes (no divergence
+      // with the update below), stored by lane 0
+      const T ajj = a[j][j];
+      T v = T(0), yn = T(0);
+      bool ok = true;
       if (m > 0) {
         const T l = a[j + 1][j];
-        const T v = fma(-(l * r), l, a[j + 1][j + 1]);
-        a[j + 1][j + 1] = v;
-        if (!pivot_ok(v)) {
-          bad = 1;
-        } else {
-          const T yn = rsqrt_piv(v);
-          ys[j + 1] = yn;
-          rs[j + 1] = yn * yn;
+        v = fma(-(l * r), l, a[j + 1][j + 1]);
+        ok = pivot_ok(v);
+        if (ok) yn = rsqrt_piv(v);
+      }
+      if (tid == 0) {
+        a[j][j] = ajj * y;                          // l_jj = p_j / sqrt(p_j)
+        if (m > 0) {
+          a[j + 1][j + 1] = v;
+          if (!ok) {
+            bad = 1;
+          } else {
+            ys[j + 1] = yn;
+            rs[j + 1] = yn * yn;
+          }
         }
       }
     } else {
-      // scaled column into the upper triangle: thread t < m writes l_{j+1+t, j}
-      for (int t = tid - 1; t < m; t += blockDim.x - 1) a[j][j + 1 + t] = a[j + 1 + t][j] * y;
+      const int t = tid - 32, nt = blockDim.x - 32;
+      // scaled column into the upper triangle: a[j][j + 1 + q] = l_{j+1+q, j}
+      for (int q = t; q < m; q += nt) a[j][j + 1 + q] = a[j + 1 + q][j] * y;
       // trailing entries except (j+1, j+1): packed index e -> (ii, cc), cc <= ii < m
       const int cnt = m * (m + 1) / 2;
-      for (int e = tid; e < cnt; e += blockDim.x - 1) {
+      for (int e = 1 + t; e < cnt; e += nt) {
         const uint32_t ic = tri[e];
         const int i = j + 1 + (int)(ic >> 8), c = j + 1 + (int)(ic & 0xffu);
         a[i][c] = fma(-(a[i][j] * r), a[c][j], a[i][c]);
