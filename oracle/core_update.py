@@ -50,6 +50,30 @@ def kron_rows(factors: Sequence[np.ndarray], idx: Sequence[np.ndarray]) -> np.nd
     return rows
 
 
+def sampled_rows_apply(factors: Sequence[np.ndarray], idx: Sequence[np.ndarray], g: np.ndarray,
+                       chunk: int = 2048) -> np.ndarray:
+    """z = K_S g for the sampled rows idx (z_u = k_u . g, the implicit design
+    matrix of Alg. 3 applied to a vector), built from explicit row chunks."""
+    n = len(idx[0])
+    z = np.empty(n)
+    g = np.asarray(g, dtype=np.float64)
+    for s in range(0, n, chunk):
+        z[s:s + chunk] = kron_rows(factors, [i[s:s + chunk] for i in idx]) @ g
+    return z
+
+
+def sampled_rows_apply_t(factors: Sequence[np.ndarray], idx: Sequence[np.ndarray],
+                         c: np.ndarray, chunk: int = 2048) -> np.ndarray:
+    """K_S^T c = sum_u c_u k_u over the sampled rows, from explicit row chunks."""
+    n = len(idx[0])
+    c = np.asarray(c, dtype=np.float64)
+    out = None
+    for s in range(0, n, chunk):
+        part = kron_rows(factors, [i[s:s + chunk] for i in idx]).T @ c[s:s + chunk]
+        out = part if out is None else out + part
+    return out
+
+
 def kron_gram_apply(factors: Sequence[np.ndarray], g: np.ndarray) -> np.ndarray:
     """(K^T K) vec(g) = vec(g x_n (A^(n)T A^(n)))  (mixed-product property)."""
     t = np.asarray(g, dtype=np.float64).reshape([A.shape[1] for A in factors])

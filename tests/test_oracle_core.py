@@ -212,3 +212,18 @@ def test_adjoint_matches_central_differences(reg):
         fd = (fp - fm) @ gbar / (2 * h)
         an = sum(np.sum(a * e) for a, e in zip(dA, dirs)) + dx @ dirx
         assert abs(fd - an) < 1e-7 * max(1.0, abs(an))
+
+
+def test_sampled_row_products_equal_explicit_rows():
+    """K_S g and K_S^T c against an explicit K indexed by the decoded keys."""
+    g = np.random.default_rng(7)
+    F = [g.standard_normal((5, 2)), g.standard_normal((4, 3)), g.standard_normal((3, 2))]
+    dims = (5, 4, 3)
+    keys = np.sort(g.choice(60, 25, replace=False)).astype(np.uint64)
+    idx = S.decode_keys(keys, dims)
+    K = CU.kron_matrix(F)[keys.astype(np.int64)]
+    v = g.standard_normal(12)
+    c = g.standard_normal(25)
+    assert np.allclose(CU.sampled_rows_apply(F, idx, v, chunk=7), K @ v, rtol=1e-13, atol=1e-13)
+    assert np.allclose(CU.sampled_rows_apply_t(F, idx, c, chunk=7), K.T @ c, rtol=1e-13, atol=1e-13)
+
