@@ -88,7 +88,7 @@ def cpu_cores():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -104,7 +104,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.f,
+                                          "-i", str(self.gpu), "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -142,6 +142,51 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def oracle_timing(w, Xh, F, reg, budget=12.0):
+    """Milliseconds of one oracle sketched core update on the host cores.
+
+    Small workloads run whole updates (up to 5 within the budget).  Large ones
+    (d > 1024 or observed entries) run the sampling in full, the normal
+    equations over a prefix of the sampled rows scaled linearly to all rows
+    (their cost is linear in the rows), and the full d x d Cholesky solve."""
+    import numpy as np
+    from oracle import core_update as CU, sampling as S
+    regc = S.REG_EXACT if reg == "exact" else S.REG_AUGMENTED
+    missing = isinstance(Xh, dict)
+    if not missing and w.d <= 1024:
+        times = []
+        t_start = time.perf_counter()
+        while not times or (time.perf_counter() - t_start) < budget and len(times) < 5:
+            t0 = time.perf_counter()
+            oracle_step(Xh, F, w, reg)
+            times.append((time.perf_counter() - t0) * 1e3)
+        return statistics.mean(times), (f"{len(times)} full sketched core updates of the same "
+                                        f"workload (numpy FP64 oracle, m = {w.m})")
+    dims = tuple(Xh["dims"]) if missing else tuple(Xh.shape)
+    t0 = time.perf_counter()
+    sk = CU.sketch(F, dims, w.m, w.seed_sample, 0, regc, Xh["keys"] if missing else None)
+    x = (CU.gather_observed(Xh["keys"], Xh["vals"], sk["keys"]) if missing
+         else CU.gather_dense(Xh, sk["keys"], dims))
+    t_sample = time.perf_counter() - t0
+    n = sk["keys"].size
+    n_sub = min(n, 4096)
+    while True:
+        t0 = time.perf_counter()
+        G, hv, D = CU.sketched_normal_equations(F, dims, sk["keys"][:n_sub], sk["w"][:n_sub],
+                                                x[:n_sub])
+        t_ne = time.perf_counter() - t0
+        if n_sub >= n or 2 * t_ne > budget / 2 or n_sub >= 1 << 16:
+            break
+        n_sub = min(n, 2 * n_sub)
+    t0 = time.perf_counter()
+    CU.cholesky_solve(CU.regularised_matrix(G, D, w.lam, regc), hv)
+    t_solve = time.perf_counter() - t0
+    total = t_sample + t_ne * n / n_sub + t_solve
+    return total * 1e3, (f"numpy FP64 oracle: leverage, sampling of all {w.m} rows (T = {sk['T']}) "
+                         f"and the d = {w.d} Cholesky solve in full; normal equations timed on "
+                         f"{n_sub} of the {n} sampled rows and scaled to all rows")
+
+
 def oracle_step(X, F, w, reg):
     from oracle import core_update as CU, sampling as S
     regc = S.REG_EXACT if reg == "exact" else S.REG_AUGMENTED
@@ -155,15 +200,26 @@ def run_reference(args):
         return
     import synth
     w = synth.WORKLOADS[args.workload]
-    P = synth.tucker_problem(w)
-    X, F = P["X"], P["factors"]
+    if w.observed < 1.0:
+        X = synth.observed_entries(w)
+        F = X["factors"]
+    else:
+        P = synth.tucker_problem(w)
+        X, F = P["X"], P["factors"]
+    small = w.observed >= 1.0 and w.d <= 1024
     for _ in range(max(0, min(args.warmup, 1))):
-        oracle_step(X, F, w, args.reg)
-    times = []
+        if small:
+            oracle_step(X, F, w, args.reg)
+    times, sample = [], ""
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle_step(X, F, w, args.reg)
-        times.append((time.perf_counter() - t0) * 1e3)
+        if small:
+            t0 = time.perf_counter()
+            oracle_step(X, F, w, args.reg)
+            times.append((time.perf_counter() - t0) * 1e3)
+            sample = f"{args.steps} full sketched core updates of the workload (numpy FP64 oracle)"
+        else:
+            ms_est, sample = oracle_timing(w, X, F, args.reg, budget=6.0)
+            times.append(ms_est)
     ms = statistics.mean(times)
     cores = cpu_cores()
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
@@ -171,8 +227,7 @@ def run_reference(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(w, "fp64", args.reg),
             "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} full sketched core updates of the workload "
-                                       f"(numpy FP64 oracle)"},
+                             "sample": sample},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -209,23 +264,41 @@ def main():
     prec = args.prec
     if prec == "auto":
         prec = os.environ.get("TUCKER_BENCH_PREC", "bf16")
-    P = synth.tucker_problem(w)
-    X_h, F_h = P["X"], P["factors"]
-    X_pin = torch.from_numpy(X_h).pin_memory()
+    missing = w.observed < 1.0
+    if missing:
+        O = synth.observed_entries(w)
+        F_h = O["factors"]
+        host_in = [torch.from_numpy(O["keys"].view(np.int64)).pin_memory(),
+                   torch.from_numpy(O["vals"]).pin_memory()]
+        X_h = O
+    else:
+        P = synth.tucker_problem(w)
+        X_h, F_h = P["X"], P["factors"]
+        host_in = [torch.from_numpy(X_h).pin_memory()]
     F_pin = [torch.from_numpy(a).pin_memory() for a in F_h]
-    X = X_pin.to(dev)
+    dev_in = [t.to(dev) for t in host_in]
     F = [a.to(dev) for a in F_pin]
+
+    def as_tensor(bufs):
+        return T.CooTensor(bufs[0], bufs[1], w.dims) if missing else bufs[0]
+
+    X = as_tensor(dev_in)
+    in_bytes = sum(t.numel() * t.element_size() for t in host_in)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
     h = T.Handle(solver=args.solver)
     stream = h.stream
+    # the exact update of an observed-entry tensor is the Gram of all observed
+    # rows (1e8 at 1024^3, seconds): timed once, on the tensor cores
+    exact_prec = "bf16" if missing else "fp64"
+    exact_steps = 1 if missing else args.steps
 
     def sketched(core_out=None, stats=True):
         return T.tucker_core_update_sketched(h, X, F, w.lam, w.m, w.seed_sample, 0, args.reg, prec,
                                              core_out=core_out, stats=stats)
 
     def exact(core_out=None):
-        return T.tucker_core_update_exact(h, X, F, w.lam, "fp64", core_out=core_out)
+        return T.tucker_core_update_exact(h, X, F, w.lam, exact_prec, core_out=core_out)
 
     # correctness of this configuration before timing: loss ratio vs exact
     g_sk, st0 = sketched()
@@ -236,7 +309,8 @@ def main():
 
     for _ in range(args.warmup):
         sketched(core_out=g_sk)
-        exact(core_out=g_ex)
+        if not missing:
+            exact(core_out=g_ex)
     torch.cuda.synchronize()
 
     def timed(fn, k):
@@ -256,10 +330,11 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         sk_ms, sk_out = timed(lambda: sketched(core_out=g_sk), args.steps)
-        ex_ms, _ = timed(lambda: exact(core_out=g_ex), args.steps)
-        # end to end through the public API: host (pinned) inputs in, core out to host
+        ex_ms, _ = timed(lambda: exact(core_out=g_ex), exact_steps)
+        # end to end through the public API: host (pinned) inputs in, core out to host; two
+        # alternating device buffers, so nothing (the observed-entry hash) carries over
         core_host = torch.empty(w.d, dtype=torch.float64).pin_memory()
-        Xe = torch.empty_like(X)
+        bufs = [[torch.empty_like(t) for t in dev_in] for _ in range(2)]
         Fe = [torch.empty_like(a) for a in F]
         e2e_ms = []
         for i in range(args.steps):
@@ -267,11 +342,12 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             with torch.cuda.stream(stream):
-                Xe.copy_(X_pin, non_blocking=True)
+                for a, b in zip(bufs[i % 2], host_in):
+                    a.copy_(b, non_blocking=True)
                 for a, b in zip(Fe, F_pin):
                     a.copy_(b, non_blocking=True)
-            g = T.tucker_core_update_sketched(h, Xe, Fe, w.lam, w.m, w.seed_sample, 0, args.reg,
-                                              prec)
+            g = T.tucker_core_update_sketched(h, as_tensor(bufs[i % 2]), Fe, w.lam, w.m,
+                                              w.seed_sample, 0, args.reg, prec)
             with torch.cuda.stream(stream):
                 core_host.copy_(g, non_blocking=True)
             stream.synchronize()
@@ -351,20 +427,14 @@ def main():
     # the dominant kernel of the timed update
     roof = factor_roofline() if kms["ms_factor"] >= kms["ms_gram_kernel"] else gram_roofline()
     roof_gram = gram_roofline()
-    # exact path: one streaming read of X by the first n-mode product
-    exact_gbs = (X.numel() * X.element_size()) / (ms_ex * 1e-3) / 1e9
+    # exact dense path: one streaming read of X by the first n-mode product
+    exact_gbs = None if missing else in_bytes / (ms_ex * 1e-3) / 1e9
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        budget, times = 12.0, []
-        t_start = time.perf_counter()
-        while not times or (time.perf_counter() - t_start) < budget and len(times) < 5:
-            t0 = time.perf_counter()
-            oracle_step(X_h, F_h, w, args.reg)
-            times.append((time.perf_counter() - t0) * 1e3)
-        cpu = {"value": statistics.mean(times), "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"{len(times)} full sketched core updates of the same workload "
-                         f"(numpy FP64 oracle, m = {w.m})"}
+        value, sample = oracle_timing(w, X_h, F_h, args.reg)
+        cpu = {"value": value, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+               "sample": sample}
 
     if rank == 0:
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -377,8 +447,8 @@ def main():
                 "exact_hbm_gbs": exact_gbs, "solver": args.solver, "other_solver": alt,
                 "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu,
                 "e2e": {"value": ms_e2e, "unit": "ms",
-                        "h2d_bytes_per_step": int(X.numel() * X.element_size() +
-                                                  sum(a.numel() * a.element_size() for a in F)),
+                        "h2d_bytes_per_step": int(in_bytes + sum(a.numel() * a.element_size()
+                                                             for a in F)),
                         "d2h_bytes_per_step": int(w.d * 8)},
                 "clocks": clk.summary(), "gpu_launches": launches}
         print(json.dumps(line), flush=True)
