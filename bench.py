@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--solver", default="fp64", choices=["fp64", "mixed"],
                    help="ridge solver of the timed update (the other one is timed beside it)")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    p.add_argument("--stage-roofline", action="store_true",
+                   help="time the sampler and the gather at 2^27 draws (their HBM/ALU rooflines); "
+                        "prints its own JSON line, not the headline")
     return p.parse_args()
 
 
@@ -239,10 +242,54 @@ def workload_config(w, prec, reg, solver="fp64"):
             "l2": "flushed before every timed step (256 MiB write); X is 512 MiB"}
 
 
+def run_stage_roofline(args):
+    """Sampler and gather at 2^27 draws from the 512^3 tensor, whose per-stage
+    times at the workload's m are launch-bound.  Rank-(2,2,2) factors keep the
+    Gram and the solve negligible; the stages are timed by the library's events."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2107_10654_gb300 import tucker as T
+    w = synth.WORKLOADS["dense3_512_r8_f32"]
+    P = synth.tucker_problem(w)
+    g = synth.rng(w.seed_data + 5)
+    F = [torch.from_numpy(g.standard_normal((i, 2)).astype(np.float32)).cuda() for i in w.dims]
+    X = torch.from_numpy(P["X"]).cuda()
+    m = 1 << 27
+    h = T.Handle()
+    T.tucker_core_update_sketched(h, X, F, w.lam, m, w.seed_sample, 0, "exact", "bf16")
+    sts = [T.tucker_core_update_sketched(h, X, F, w.lam, m, w.seed_sample, 0, "exact", "bf16",
+                                         stats=True)[1] for _ in range(3)]
+    pk, src = peaks()
+    ms_s = statistics.mean(s["ms_sample"] for s in sts)
+    ms_g = statistics.mean(s["ms_gather"] for s in sts)
+    n_u = sts[-1]["n_unique"]
+    # sampler: 8 B key written per draw (CDFs are read once into shared memory)
+    samp_gbs = 8.0 * m / (ms_s * 1e-3) / 1e9
+    # gather, per unique row: key 8 + count 4 + x 4 read, three u32 indices + w, x, p (FP64)
+    # + sqrt(w) (FP32) written = 56 B; the x read costs a 32 B sector (84 B with sectors)
+    gath_alg = 56.0 * n_u / (ms_g * 1e-3) / 1e9
+    gath_sec = 84.0 * n_u / (ms_g * 1e-3) / 1e9
+    line = {"mode": "stage_roofline", "draws": m, "n_unique": n_u, "workload": "512^3 X, rank (2,2,2)",
+            "sampler": {"ms": ms_s, "bytes_per_draw": 8, "achieved_gbs": samp_gbs,
+                        "frac_of_hbm": samp_gbs / pk["hbm_gbs"]},
+            "gather": {"ms": ms_g, "bytes_per_row": 56, "achieved_gbs": gath_alg,
+                       "frac_of_hbm": gath_alg / pk["hbm_gbs"], "with_32B_sector_gbs": gath_sec,
+                       "frac_with_sectors": gath_sec / pk["hbm_gbs"]},
+            "peak_hbm_gbs": pk["hbm_gbs"], "peak_source": src,
+            "stage_ms": {k: statistics.mean(s[k] for s in sts) for k in
+                         ("ms_leverage", "ms_sample", "ms_dedupe", "ms_gather", "ms_gram", "ms_solve")}}
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.stage_roofline:
+        run_stage_roofline(args)
         return
     import numpy as np
     import torch

@@ -30,7 +30,8 @@ tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t
                             int reg, const uint64_t* keys_u, const uint32_t* counts,
                             const int* d_nu, const int64_t* d_T, const tucker_tensor* X,
                             int64_t cap, uint32_t* const* idx, double* w, double* x, double* p,
-                            float* sw32, int* d_nreal, double* D, const double* p_in);
+                            float* sw32, int* d_nreal, double* D, const double* p_in,
+                            double* ptab);
 tucker_status launch_cdf_from_lev(tucker_handle* h, int N, const int64_t* I,
                                   const double* const* lev, uint64_t* const* cdf);
 int gram_simt_splits(tucker_handle* h, int d, int64_t cap);
@@ -265,6 +266,7 @@ struct SketchBufs {
   double *w, *x, *p, *z;
   float* sw32;
   double *D, *h, *g, *r, *axpy_part;
+  double* ptab;                       // per-mode q/Q and Q/q tables of the gather
   WalkBuf walk;
   double* A64[TUCKER_MAX_ORDER];      // FP64 copies of FP32 factors (walk kernels)
   char* gram_ws;
@@ -295,6 +297,11 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
   b->z = ar.get<double>(m);
   b->sw32 = ar.get<float>(m);
   b->D = ar.get<double>(F.d);
+  {
+    int64_t sumI = 0;
+    for (int n = 0; n < F.N; ++n) sumI += F.I[n];
+    b->ptab = ar.get<double>(2 * sumI);
+  }
   b->h = ar.get<double>(F.d);
   b->g = ar.get<double>(F.d);
   b->r = ar.get<double>(F.d);
@@ -625,7 +632,7 @@ tucker_status tucker_sample_rows(tucker_handle* h, int N, const int64_t* I, cons
   none.order = N;
   none.dtype = TUCKER_F64;
   TK_TRY(launch_gather(h, F, cdf, reg, out->keys, out->counts, nu, dT, &none, m, idx, w, x,
-                       out->prob, nullptr, nreal, D, nullptr));
+                       out->prob, nullptr, nreal, D, nullptr, nullptr));
   int nuh = 0;
   TK_CUDA(h, cudaMemcpyAsync(&nuh, nu, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   TK_TRY(device_status(h));
@@ -719,7 +726,7 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   }
   ev_record(h, timing, 3);
   TK_TRY(launch_gather(h, F, b.cdf, reg, keys_u, counts, b.nu, b.d_T, X, cap, b.idx, b.w, b.x,
-                       b.p, b.sw32, b.nreal, b.D, p_in));
+                       b.p, b.sw32, b.nreal, b.D, p_in, b.ptab));
   ev_record(h, timing, 4);
   RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
   RowSet rs64;
@@ -973,7 +980,8 @@ tucker_status tucker_sketched_gram(tucker_handle* h, const tucker_tensor* X, con
   TK_CUDA(h, cudaMemcpyAsync(b.d_T, &T, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
   if (!X->dense) { int pr; TK_TRY(hash_ensure(h, X, &pr)); }
   TK_TRY(launch_gather(h, F, b.cdf, TUCKER_REG_EXACT, samples->keys, samples->counts, b.nu,
-                       b.d_T, X, cap, b.idx, b.w, b.x, b.p, b.sw32, b.nreal, b.D, samples->prob));
+                       b.d_T, X, cap, b.idx, b.w, b.x, b.p, b.sw32, b.nreal, b.D, samples->prob,
+                       nullptr));
   TK_CUDA(h, cudaStreamSynchronize(h->stream));
   RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
   RowSet rs64;
@@ -1020,7 +1028,7 @@ tucker_status tucker_core_solve_adjoint(tucker_handle* h, const tucker_tensor* X
   TK_CUDA(h, cudaMemcpyAsync(b.d_T, &T, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
   if (!X->dense) { int pr; TK_TRY(hash_ensure(h, X, &pr)); }
   TK_TRY(launch_gather(h, F, b.cdf, reg, samples->keys, samples->counts, b.nu, b.d_T, X, cap,
-                       b.idx, b.w, b.x, b.p, b.sw32, b.nreal, b.D, samples->prob));
+                       b.idx, b.w, b.x, b.p, b.sw32, b.nreal, b.D, samples->prob, nullptr));
   TK_CUDA(h, cudaStreamSynchronize(h->stream));
   RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
   RowSet rs64;

@@ -11,8 +11,12 @@
 //       of Eq. problem_def), p_u = 0.5/d, and D_j = w_u;
 //   w_u = c_u / (T p_u)   (squared row scale 1/(Pr(j) s) of Alg. 1, summed
 //       over the c_u copies).
-// These are the same IEEE operations in the same order as the CPU oracle, so
-// p_u and w_u are bit-identical to it.
+// p_u uses the same IEEE operations in the same order as the CPU oracle, so it
+// is bit-identical to it.  When per-mode tables are supplied (ftab[i] = q_i/Q_n
+// and rtab[i] = 1/ftab[i], one division per factor row instead of several FP64
+// divisions per sampled row -- GB300's FP64 rate is 1/64 of FP32), p_u is the
+// product of table entries (still bit-identical) and w_u = c_u (1/T) prod_n rtab,
+// which differs from c_u / (T p_u) by a few units in the last place.
 #include "common.cuh"
 
 namespace tk {
@@ -44,32 +48,68 @@ struct GatherArgs {
   int* n_real;
   double* D;                          // [d], zeroed by the caller
   const double* p_in;                 // nullable: probabilities of a frozen sample
+  const double* ftab;                 // nullable: per-mode q_i / Q_n, modes concatenated
+  const double* rtab;                 // 1 / ftab
+  int64_t toff[TUCKER_MAX_ORDER];     // first entry of mode n in the tables
+  int small;                          // prod I_n < 2^32: 32-bit key decode
 };
+
+// ftab[off_n + i] = q_i / Q_n, rtab = 1 / ftab, for every factor row of every mode.
+__global__ void k_prob_tables(GatherArgs a) {
+  for (int n = 0; n < a.N; ++n) {
+    const uint64_t* C = a.cdf[n];
+    const double Q = (double)C[a.I[n] - 1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.I[n];
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const uint64_t q = C[i] - (i ? C[i - 1] : 0);
+      const double f = (double)q / Q;
+      const_cast<double*>(a.ftab)[a.toff[n] + i] = f;
+      const_cast<double*>(a.rtab)[a.toff[n] + i] = 1.0 / f;
+    }
+  }
+}
 
 __global__ void k_gather_weights(GatherArgs a) {
   const int nu = *a.n_unique;
   const double T = (double)*a.T;
+  const double invT = a.rtab ? 1.0 / T : 0.0;
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += gridDim.x * blockDim.x) {
     const uint64_t key = a.keys_u[u];
-    double p, x;
+    double p, x, rinv = 0.0;                     // rinv = 1 / p from the tables
     if (key < a.total) {
-      uint64_t rem = key;
       uint32_t ii[TUCKER_MAX_ORDER];
-      for (int n = a.N - 1; n >= 0; --n) {
-        ii[n] = (uint32_t)(rem % (uint64_t)a.I[n]);
-        rem /= (uint64_t)a.I[n];
+      if (a.small) {
+        uint32_t rem = (uint32_t)key;
+        for (int n = a.N - 1; n >= 0; --n) {
+          const uint32_t In = (uint32_t)a.I[n];
+          ii[n] = rem % In;
+          rem /= In;
+        }
+      } else {
+        uint64_t rem = key;
+        for (int n = a.N - 1; n >= 0; --n) {
+          ii[n] = (uint32_t)(rem % (uint64_t)a.I[n]);
+          rem /= (uint64_t)a.I[n];
+        }
       }
       p = 0.0;
       for (int n = 0; n < a.N; ++n) {
         a.idx[n][u] = ii[n];
         if (a.p_in) continue;
-        const uint64_t* C = a.cdf[n];
-        const uint64_t q = C[ii[n]] - (ii[n] ? C[ii[n] - 1] : 0);
-        const double f = (double)q / (double)C[a.I[n] - 1];
+        double f;
+        if (a.ftab) {
+          f = a.ftab[a.toff[n] + ii[n]];
+          const double r = a.rtab[a.toff[n] + ii[n]];
+          rinv = n ? rinv * r : r;
+        } else {
+          const uint64_t* C = a.cdf[n];
+          const uint64_t q = C[ii[n]] - (ii[n] ? C[ii[n] - 1] : 0);
+          f = (double)q / (double)C[a.I[n] - 1];
+        }
         p = n ? p * f : f;
       }
       if (a.p_in) p = a.p_in[u];
-      else if (a.reg == TUCKER_REG_AUGMENTED) p = 0.5 * p;
+      else if (a.reg == TUCKER_REG_AUGMENTED) { p = 0.5 * p; rinv = 2.0 * rinv; }
       if (a.dense) x = load_as_double(a.dense, (int64_t)key, a.is64);
       else if (a.slot_key)
         x = hash_value(a.slot_key, a.slot_idx, a.log2, a.max_probes, a.vals, a.is64, key);
@@ -83,11 +123,12 @@ __global__ void k_gather_weights(GatherArgs a) {
       a.idx[0][u] = j;
       if (u == 0 || a.keys_u[u - 1] < a.total) *a.n_real = u;
     }
-    const double w = (double)a.counts[u] / (T * p);
+    const bool fast = a.ftab && !a.p_in && key < a.total;
+    const double w = fast ? (double)a.counts[u] * (invT * rinv) : (double)a.counts[u] / (T * p);
     a.w[u] = w;
     a.x[u] = x;
     a.p[u] = p;
-    if (a.sw32) a.sw32[u] = (float)sqrt(w);
+    if (a.sw32) a.sw32[u] = sqrtf((float)w);
     if (key >= a.total) a.D[key - a.total] = w;
   }
 }
@@ -96,7 +137,8 @@ tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t
                             int reg, const uint64_t* keys_u, const uint32_t* counts,
                             const int* d_nu, const int64_t* d_T, const tucker_tensor* X,
                             int64_t cap, uint32_t* const* idx, double* w, double* x, double* p,
-                            float* sw32, int* d_nreal, double* D, const double* p_in) {
+                            float* sw32, int* d_nreal, double* D, const double* p_in,
+                            double* ptab) {
   GatherArgs a;
   memset(&a, 0, sizeof(a));
   a.N = F.N;
@@ -119,7 +161,19 @@ tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t
     a.vals = X->vals;
   }
   a.w = w; a.x = x; a.p = p; a.sw32 = sw32; a.n_real = d_nreal; a.D = D;
+  a.small = F.total <= 0xffffffffull;
   TK_CUDA(h, cudaMemsetAsync(D, 0, sizeof(double) * F.d, h->stream));
+  if (ptab && !p_in) {
+    int64_t sumI = 0;
+    for (int n = 0; n < F.N; ++n) { a.toff[n] = sumI; sumI += F.I[n]; }
+    a.ftab = ptab;
+    a.rtab = ptab + sumI;
+    int tg = ceil_div(F.I[0] > 1024 ? F.I[0] : 1024, 256);
+    if (tg > h->num_sms * 4) tg = h->num_sms * 4;
+    TK_COUNT(h);
+    k_prob_tables<<<tg, 256, 0, h->stream>>>(a);
+    TK_LAUNCH(h);
+  }
   int grid = ceil_div(cap, 256);
   if (grid > h->num_sms * 16) grid = h->num_sms * 16;
   if (grid < 1) grid = 1;

@@ -221,8 +221,8 @@ __global__ void k_tc_pack(PackArgs a) {
       int n = 0;
       while (n + 1 < a.N && e >= a.off[n + 1]) ++n;
       const int r = e - a.off[n];
-      const double f = load_as_double(a.A[n], (int64_t)a.idx[n][u] * a.R[n] + r, a.is64);
-      v = (float)(n == 0 ? sqrt(a.w[u]) * f : f);
+      const float f = (float)load_as_double(a.A[n], (int64_t)a.idx[n][u] * a.R[n] + r, a.is64);
+      v = n == 0 ? sqrtf((float)a.w[u]) * f : f;     // FP32 is exact enough: rounded to BF16/TF32 next
     }
     a.pack[t - s + pack_pos(s, a.perm)] = v;
   }

@@ -28,7 +28,8 @@ tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t
                             int reg, const uint64_t* keys_u, const uint32_t* counts,
                             const int* d_nu, const int64_t* d_T, const tucker_tensor* X,
                             int64_t cap, uint32_t* const* idx, double* w, double* x, double* p,
-                            float* sw32, int* d_nreal, double* D, const double* p_in);
+                            float* sw32, int* d_nreal, double* D, const double* p_in,
+                            double* ptab);
 
 // The shared scratch.  Host code must not pass this symbol to a kernel: in
 // host code it is only a stand-in, so its device address is looked up with
@@ -179,7 +180,7 @@ extern "C" tucker_status tucker_sample_rows_noalloc(void* cuda_stream, int N, co
     none.order = N;
     none.dtype = TUCKER_F64;
     st = launch_gather(&h, F, cdf, reg, out->keys, out->counts, nu, dT, &none, m, idx, w, x,
-                       out->prob, nullptr, nreal, D, nullptr);
+                       out->prob, nullptr, nreal, D, nullptr, nullptr);
   }
   int nuh = 0;
   if (st == TUCKER_OK) {

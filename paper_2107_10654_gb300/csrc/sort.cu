@@ -1,13 +1,14 @@
-// Dedupe of sampled rows: LSD radix sort of the 64-bit keys (4-bit digits,
+// Dedupe of sampled rows: LSD radix sort of the 64-bit keys (8-bit digits,
 // only as many passes as the key range needs) followed by a run-length encode
 // into (key_u, count_u).  Sampling is with replacement (Alg. 1 loop), so equal
 // rows merge into one row of weight c_u / (T p_u).
 //
-// Each sort pass: per-tile digit histogram -> exclusive scan over
-// (digit, tile) -> stable scatter.  A tile is 256 threads x 8 consecutive keys;
-// the rank of a key inside its tile is its digit's tile offset plus the number
-// of equal digits in earlier threads (block scan over digit-major counters)
-// plus the equal digits earlier in the same thread, which keeps the sort stable.
+// Each sort pass: per-tile digit histogram -> per-digit exclusive scan over
+// the tiles (one CTA per digit) -> stable scatter.  A tile is 4096 keys, 512
+// per warp in 16 rounds of 32; inside a round, lanes holding the same digit
+// find each other with match_any, so a key's rank is the digit's tile base,
+// plus the counts of earlier warps, plus the counts of earlier rounds of its
+// warp, plus the equal digits in lower lanes -- input order, hence stable.
 #include "common.cuh"
 
 namespace tk {
@@ -15,7 +16,6 @@ namespace tk {
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
-constexpr int RADIX = 16;
 
 // ---------------------------------------------------------- int64 scan (1 CTA)
 __global__ void __launch_bounds__(1024) k_scan_i64(const int64_t* in, int64_t* out, int64_t n,
@@ -47,63 +47,100 @@ void launch_scan_i64(tucker_handle* h, const int64_t* in, int64_t* out_excl, int
 }
 
 // ------------------------------------------------------------------ radix sort
-__global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const uint64_t* keys, int64_t n,
-                                                             int shift, int64_t* hist,
-                                                             int nblocks) {
-  __shared__ unsigned cnt[RADIX];
-  if (threadIdx.x < RADIX) cnt[threadIdx.x] = 0;
+constexpr int RX = 256;                         // 8-bit digits
+constexpr int RX_THREADS = 256;
+constexpr int RX_WARPS = RX_THREADS / 32;
+constexpr int RX_ROUNDS = 16;
+constexpr int RX_TILE = RX_THREADS * RX_ROUNDS;  // 4096 keys
+
+__global__ void __launch_bounds__(RX_THREADS) k_rx_hist(const uint64_t* keys, int64_t n, int shift,
+                                                        int* hist, int ntiles) {
+  __shared__ int cnt[RX];
+  cnt[threadIdx.x] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * SORT_TILE + threadIdx.x * SORT_ITEMS;
-#pragma unroll
-  for (int j = 0; j < SORT_ITEMS; ++j)
-    if (base + j < n) atomicAdd(&cnt[(keys[base + j] >> shift) & (RADIX - 1)], 1u);
+  const int64_t base = (int64_t)blockIdx.x * RX_TILE;
+#pragma unroll 4
+  for (int j = 0; j < RX_ROUNDS; ++j) {
+    const int64_t i = base + j * RX_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(int)((keys[i] >> shift) & (RX - 1))], 1);
+  }
   __syncthreads();
-  if (threadIdx.x < RADIX) hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint64_t* in, uint64_t* out,
-                                                                int64_t n, int shift,
-                                                                const int64_t* offs,
-                                                                int nblocks) {
-  __shared__ int64_t cnt[RADIX * SORT_THREADS];     // digit-major [digit][thread]
+// rowoff[d][t] = sum_{t' < t} hist[d][t'], tot[d] = sum_t hist[d][t]  (one CTA per digit)
+__global__ void __launch_bounds__(1024) k_rx_colscan(const int* hist, int ntiles, int* rowoff,
+                                                     int* tot) {
   __shared__ int64_t tmp[32];
-  __shared__ int64_t tile_start[RADIX];
-  const int t = threadIdx.x;
-  const int64_t base = (int64_t)blockIdx.x * SORT_TILE + t * SORT_ITEMS;
-  uint64_t k[SORT_ITEMS];
-  int dg[SORT_ITEMS];
+  const int* row = hist + (int64_t)blockIdx.x * ntiles;
+  int* orow = rowoff + (int64_t)blockIdx.x * ntiles;
+  int64_t carry = 0;
+  for (int b = 0; b < ntiles; b += 4 * (int)blockDim.x) {
+    const int i0 = b + 4 * threadIdx.x;
+    int v[4];
+    int64_t s = 0;
 #pragma unroll
-  for (int j = 0; j < SORT_ITEMS; ++j) {
-    k[j] = (base + j < n) ? in[base + j] : ~uint64_t(0);
-    dg[j] = (int)((k[j] >> shift) & (RADIX - 1));
+    for (int j = 0; j < 4; ++j) { v[j] = i0 + j < ntiles ? row[i0 + j] : 0; s += v[j]; }
+    int64_t all;
+    int64_t ex = carry + block_exclusive_scan(s, tmp, &all);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (i0 + j < ntiles) orow[i0 + j] = (int)ex;
+      ex += v[j];
+    }
+    carry += all;
   }
+  if (threadIdx.x == 0) tot[blockIdx.x] = (int)carry;
+}
+
+__global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const uint64_t* in, uint64_t* out,
+                                                           int64_t n, int shift, const int* rowoff,
+                                                           const int* tot, int ntiles) {
+  __shared__ int64_t tmp[32];
+  __shared__ int wcnt[RX_WARPS][RX];
+  __shared__ int wofs[RX_WARPS][RX];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * RX_TILE + (int64_t)w * (RX_ROUNDS * 32);
+  uint64_t k[RX_ROUNDS];
+  int dg[RX_ROUNDS];
 #pragma unroll
-  for (int d = 0; d < RADIX; ++d) {
-    int c = 0;
+  for (int r = 0; r < RX_ROUNDS; ++r) {
+    const int64_t i = base + r * 32 + lane;
+    k[r] = i < n ? in[i] : 0;
+    dg[r] = i < n ? (int)((k[r] >> shift) & (RX - 1)) : -1;
+  }
+  for (int d = lane; d < RX; d += 32) wcnt[w][d] = 0;
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int j = 0; j < SORT_ITEMS; ++j) c += (dg[j] == d);
-    cnt[d * SORT_THREADS + t] = c;
+  for (int r = 0; r < RX_ROUNDS; ++r) {              // per-warp digit counts
+    const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+    if (dg[r] >= 0 && (peers & lt) == 0) wcnt[w][dg[r]] += __popc(peers);
+    __syncwarp();
+  }
+  // digit bases: all tiles' totals of smaller digits, plus this tile's offset
+  int64_t all;
+  const int64_t dbase = block_exclusive_scan((int64_t)tot[threadIdx.x], tmp, &all) +
+                        rowoff[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  {
+    int64_t run = dbase;
+    for (int ww = 0; ww < RX_WARPS; ++ww) {
+      wofs[ww][threadIdx.x] = (int)run;
+      run += wcnt[ww][threadIdx.x];
+    }
   }
   __syncthreads();
-  // exclusive scan of the flat digit-major array; thread t owns 16 consecutive entries
-  int64_t loc[RADIX], s = 0;
 #pragma unroll
-  for (int j = 0; j < RADIX; ++j) { loc[j] = cnt[t * RADIX + j]; s += loc[j]; }
-  int64_t tot;
-  int64_t ex = block_exclusive_scan(s, tmp, &tot);
-#pragma unroll
-  for (int j = 0; j < RADIX; ++j) { cnt[t * RADIX + j] = ex; ex += loc[j]; }
-  __syncthreads();
-  if (t < RADIX) tile_start[t] = cnt[t * SORT_THREADS];
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < SORT_ITEMS; ++j) {
-    if (base + j >= n) break;
-    int before = 0;
-#pragma unroll
-    for (int jj = 0; jj < j; ++jj) before += (dg[jj] == dg[j]);
-    int64_t r = cnt[dg[j] * SORT_THREADS + t] + before - tile_start[dg[j]];
-    out[offs[(int64_t)dg[j] * nblocks + blockIdx.x] + r] = k[j];
+  for (int r = 0; r < RX_ROUNDS; ++r) {
+    const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+    int pos = 0;
+    if (dg[r] >= 0) pos = wofs[w][dg[r]] + __popc(peers & lt);
+    __syncwarp();
+    if (dg[r] >= 0) {
+      out[pos] = k[r];
+      if ((peers & lt) == 0) wofs[w][dg[r]] += __popc(peers);
+    }
+    __syncwarp();
   }
 }
 
@@ -155,8 +192,10 @@ __global__ void k_rle_counts(const int64_t* start, const int64_t* n_unique64, in
 }
 
 size_t sort_dedupe_scratch(int64_t n) {
-  int64_t nb = (n + SORT_TILE - 1) / SORT_TILE;
-  return size_t(n) * 8 * 2 + size_t(RADIX * nb) * 8 * 2 + size_t(nb) * 16 + size_t(n) * 8 + 4096;
+  const int64_t nb = (n + SORT_TILE - 1) / SORT_TILE;
+  const int64_t nt = (n + RX_TILE - 1) / RX_TILE;
+  return size_t(n) * 8 * 2 + size_t(RX * nt) * 4 * 2 + RX * 4 + 256 + size_t(nb) * 16 +
+         size_t(n) * 8 + 4096;
 }
 
 // Sort keys_in[0..n) (keys < 2^key_bits) and deduplicate into keys_u/counts_u;
@@ -167,28 +206,31 @@ tucker_status sort_dedupe(tucker_handle* h, const uint64_t* keys_in, int64_t n, 
   if (scratch_bytes < sort_dedupe_scratch(n))
     return fail(h, TUCKER_EINTERNAL, "sort scratch too small");
   const int nb = ceil_div(n, SORT_TILE);
+  const int nt = ceil_div(n, RX_TILE);
   Arena ar(scratch);
   uint64_t* b0 = ar.get<uint64_t>(n);
   uint64_t* b1 = ar.get<uint64_t>(n);
-  int64_t* hist = ar.get<int64_t>((size_t)RADIX * nb);
-  int64_t* offs = ar.get<int64_t>((size_t)RADIX * nb);
+  int* hist = ar.get<int>((size_t)RX * nt);
+  int* rowoff = ar.get<int>((size_t)RX * nt);
+  int* tot = ar.get<int>(RX);
   int64_t* bc = ar.get<int64_t>(nb);
   int64_t* bo = ar.get<int64_t>(nb + 1);
   int64_t* start = ar.get<int64_t>(n);
   int64_t* nu = bo + nb;
-  TK_CUDA(h, cudaMemcpyAsync(b0, keys_in, n * 8, cudaMemcpyDeviceToDevice, h->stream));
-  const uint64_t* cur = b0;
-  uint64_t* nxt = b1;
-  for (int shift = 0; shift < key_bits; shift += 4) {
+  const uint64_t* cur = keys_in;
+  uint64_t* nxt = b0;
+  for (int shift = 0; shift < key_bits; shift += 8) {
     TK_COUNT(h);
-    k_radix_hist<<<nb, SORT_THREADS, 0, h->stream>>>(cur, n, shift, hist, nb);
-    launch_scan_i64(h, hist, offs, (int64_t)RADIX * nb, nullptr);
-    TK_COUNT(h);
-    k_radix_scatter<<<nb, SORT_THREADS, 0, h->stream>>>(cur, nxt, n, shift, offs, nb);
+    k_rx_hist<<<nt, RX_THREADS, 0, h->stream>>>(cur, n, shift, hist, nt);
     TK_LAUNCH(h);
-    const uint64_t* t = cur;
+    TK_COUNT(h);
+    k_rx_colscan<<<RX, 1024, 0, h->stream>>>(hist, nt, rowoff, tot);
+    TK_LAUNCH(h);
+    TK_COUNT(h);
+    k_rx_scatter<<<nt, RX_THREADS, 0, h->stream>>>(cur, nxt, n, shift, rowoff, tot, nt);
+    TK_LAUNCH(h);
     cur = nxt;
-    nxt = const_cast<uint64_t*>(t);
+    nxt = nxt == b0 ? b1 : b0;
   }
   TK_COUNT(h);
   k_rle_heads<<<nb, SORT_THREADS, 0, h->stream>>>(cur, n, bc);
