@@ -67,13 +67,19 @@ __device__ __forceinline__ bool pivot_ok(T p) { return p > T(0) && p <= tmax<T>(
 // not positive and finite; every CTA computes the same.
 template <class T>
 __device__ bool factor_diag_block(const T* M, int d, int k, int nb, T (*a)[CB + 1],
-                                  const uint16_t* tri) {
+                                  const uint16_t* tri, T (*P)[CB + 1] = nullptr, int np = 0,
+                                  int prow0 = 0, int pstride = 1) {
   __shared__ T ys[CB + 1], rs[CB + 1];
   __shared__ int bad;
   const int tid = threadIdx.x;
   for (int e = tid; e < CB * CB; e += blockDim.x) {
     const int i = e / CB, j = e % CB;
     a[i][j] = (i < nb && j <= i) ? M[(size_t)(k + i) * d + k + j] : T(0);
+  }
+  // this CTA's panel rows prow0 + q * pstride (q < np), columns k .. k + nb
+  for (int e = tid; e < np * CB; e += blockDim.x) {
+    const int q = e / CB, j = e % CB;
+    P[q][j] = j < nb ? M[(size_t)(prow0 + q * pstride) * d + k + j] : T(0);
   }
   __syncthreads();
   if (tid == 0) {
@@ -121,8 +127,19 @@ __device__ bool factor_diag_block(const T* M, int d, int k, int nb, T (*a)[CB + 
         const int i = j + 1 + (int)(ic >> 8), c = j + 1 + (int)(ic & 0xffu);
         a[i][c] = fma(-(a[i][j] * r), a[c][j], a[i][c]);
       }
+      // the panel rows take the same rank-1 update (their column j stays unscaled)
+      if (m > 0)
+        for (int e = t; e < np * m; e += nt) {
+          const int q = e / m, c = j + 1 + (e - q * m);
+          P[q][c] = fma(-(P[q][j] * r), a[c][j], P[q][c]);
+        }
     }
     __syncthreads();
+  }
+  // panel rows: l_qj = p_qj y_j
+  for (int e = tid; e < np * nb; e += blockDim.x) {
+    const int q = e / nb, j = e % nb;
+    P[q][j] *= ys[j];
   }
   // move the scaled columns from the upper to the lower triangle
   for (int e = tid; e < nb * nb; e += blockDim.x) {
@@ -207,57 +224,59 @@ __device__ void trailing_update(T* M, int d, int k, int nb, int s, T (*Pa)[CB + 
   }
 }
 
+// Blocked right-looking Cholesky.  Step k: every CTA factors the diagonal
+// block redundantly and, in the same pivot loop, its share of the panel rows
+// below it (rows s + cta, s + cta + G, ...); CTA 0 stores L_kk, every CTA its
+// panel rows; grid barrier; the trailing tiles; grid barrier.
 template <class T>
 __global__ void __launch_bounds__(CHOL_THREADS) k_chol_coop(T* M, int d, int* status) {
   cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char chol_smem[];
+  T (*P)[CB + 1] = reinterpret_cast<T (*)[CB + 1]>(chol_smem);     // panel rows of this CTA
   __shared__ T Lkk[CB][CB + 1];
-  __shared__ T rinv[CB];
   __shared__ T Pa[32][CB + 1];
   __shared__ T Pb[32][CB + 1];
   __shared__ uint16_t tri[CB * (CB - 1) / 2 + CB];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int G = gridDim.x, cta = blockIdx.x;
   // packed trailing-triangle table: entry e = ii (ii + 1) / 2 + cc
   for (int ii = threadIdx.x; ii < CB; ii += blockDim.x)
     for (int cc = 0; cc <= ii; ++cc) tri[ii * (ii + 1) / 2 + cc] = (uint16_t)((ii << 8) | cc);
   __syncthreads();
   for (int k = 0; k < d; k += CB) {
     const int nb = min(CB, d - k);
-    if (!factor_diag_block<T>(M, d, k, nb, Lkk, tri)) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, DEV_NOTSPD);
+    const int s = k + nb;
+    const int np = s + cta < d ? (d - s - cta + G - 1) / G : 0;
+    if (!factor_diag_block<T>(M, d, k, nb, Lkk, tri, P, np, s + cta, G)) {
+      if (cta == 0 && threadIdx.x == 0) set_status(status, DEV_NOTSPD);
       return;                                   // every CTA takes this branch at the same k
     }
-    if (threadIdx.x < CB)
-      rinv[threadIdx.x] = threadIdx.x < nb ? T(1) / Lkk[threadIdx.x][threadIdx.x] : T(0);
-    if (blockIdx.x == 0)
+    if (cta == 0)
       for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
         const int i = e / nb, j = e % nb;
         if (j <= i) M[(size_t)(k + i) * d + k + j] = Lkk[i][j];
       }
-    __syncthreads();
-    // panel rows below the diagonal block: one warp per row, lane c owns column c
-    for (int row = k + nb + blockIdx.x * nwarps + warp; row < d; row += gridDim.x * nwarps) {
-      T* mrow = M + (size_t)row * d + k;
-      T x = lane < nb ? mrow[lane] : T(0);
-      T acc = T(0);                             // sum_{cc < lane} x_cc L[lane][cc]
-      for (int c = 0; c < nb; ++c) {
-        const T xc = __shfl_sync(0xffffffffu, (x - acc) * rinv[lane], c);
-        if (lane == c) x = xc;
-        if (lane > c) acc = fma(xc, Lkk[lane][c], acc);
-      }
-      if (lane < nb) mrow[lane] = x;
+    for (int e = threadIdx.x; e < np * nb; e += blockDim.x) {
+      const int q = e / nb, j = e % nb;
+      M[(size_t)(s + cta + q * G) * d + k + j] = P[q][j];
     }
     grid.sync();
-    const int s = k + nb;
     if (s < d) {
       // 32 x 32 tiles while there are at least two per CTA, then 16 x 16
       const int t32 = (d - s + 31) / 32;
-      if (t32 * (t32 + 1) / 2 >= 2 * (int)gridDim.x)
+      if (t32 * (t32 + 1) / 2 >= 2 * G)
         trailing_update<T, 32>(M, d, k, nb, s, Pa, Pb);
       else
         trailing_update<T, 16>(M, d, k, nb, s, Pa, Pb);
     }
     grid.sync();
   }
+}
+
+// dynamic shared memory of k_chol_coop: the largest panel share of a CTA
+template <class T>
+size_t chol_panel_smem(int d, int G) {
+  const int rows = d > CB ? (d - CB + G - 1) / G : 0;
+  return (size_t)(rows > 0 ? rows : 1) * (CB + 1) * sizeof(T);
 }
 
 static int coop_grid(tucker_handle* h, const void* kernel, int threads, size_t smem) {
@@ -273,11 +292,14 @@ static int coop_grid(tucker_handle* h, const void* kernel, int threads, size_t s
 template <class T>
 tucker_status cholesky_t(tucker_handle* h, T* M, int d) {
   const void* kern = (const void*)k_chol_coop<T>;
-  const int grid = coop_grid(h, kern, CHOL_THREADS, 0);
+  const size_t smem = chol_panel_smem<T>(d, h->num_sms);
+  if (smem > 160 * 1024) return fail(h, TUCKER_ENOTSUP, "Cholesky panel of d = %d too large", d);
+  TK_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = coop_grid(h, kern, CHOL_THREADS, smem);
   if (grid < 1) return fail(h, TUCKER_ECUDA, "cooperative Cholesky cannot be resident");
   void* args[] = {&M, &d, &h->d_status};
   TK_COUNT(h);
-  TK_CUDA(h, cudaLaunchCooperativeKernel(kern, grid, CHOL_THREADS, args, 0, h->stream));
+  TK_CUDA(h, cudaLaunchCooperativeKernel(kern, grid, CHOL_THREADS, args, smem, h->stream));
   return TUCKER_OK;
 }
 
