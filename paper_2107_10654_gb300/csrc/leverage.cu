@@ -110,6 +110,68 @@ __global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a, double*
   __syncthreads();
   if (a.gram[n])
     for (int e = tid; e < R * R; e += blockDim.x) a.gram[n][e] = G[(e / R) * Rp + e % R];
+  // Fast path when only the scores are wanted: G = L L^T and W = L^-T (so that
+  // || a_i W ||^2 = a_i G^-1 a_i^T), taken only if it certifies full rank under
+  // the pseudo-inverse tolerance: 1 / ||L^-1||_F^2 <= lambda_min, and
+  // lambda_max <= trace(G), so lambda_min > max(I, R) eps trace(G) implies that
+  // no eigenvalue is dropped.  Otherwise the Jacobi eigendecomposition below.
+  if (wid == 0 && !a.evecs[n] && !a.evals[n] && R <= 32) {
+    double tr = 0.0;
+    for (int i = lane; i < R; i += 32) tr += G[i * Rp + i];
+    tr = warp_sum(tr);
+    bool ok = true;
+    for (int j = 0; j < R && ok; ++j) {                  // lane i owns row i (i < R <= 32)
+      const double p = G[j * Rp + j];
+      ok = p > 0.0 && p <= 1.7976931348623157e308;
+      if (!ok) break;
+      const double y = rsqrt(p);
+      if (lane > j && lane < R) G[lane * Rp + j] *= y;
+      __syncwarp();
+      if (lane == j) G[j * Rp + j] = p * y;
+      if (lane > j && lane < R) {
+        const double lij = G[lane * Rp + j];
+        for (int c = j + 1; c <= lane; ++c) G[lane * Rp + c] = fma(-lij, G[c * Rp + j], G[lane * Rp + c]);
+      }
+      __syncwarp();
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (ok) {
+      // column c = lane of L^-1 by forward substitution (V holds L^-1)
+      double fro = 0.0;
+      if (lane < R) {
+        for (int i = 0; i < R; ++i) {
+          double v = (i == lane) ? 1.0 : 0.0;
+          for (int jj = lane; jj < i; ++jj) v = fma(-G[i * Rp + jj], V[jj * Rp + lane], v);
+          v = i < lane ? 0.0 : v / G[i * Rp + i];
+          V[i * Rp + lane] = v;
+          fro = fma(v, v, fro);
+        }
+      }
+      fro = warp_sum(fro);
+      const double tol = double(I > R ? I : R) * 2.220446049250313e-16 * tr;
+      ok = fro > 0.0 && 1.0 / fro > tol;
+      if (ok) {
+        for (int e = lane; e < R * R; e += 32) {
+          const int r = e / R, k = e % R;
+          Wout[n][e] = V[k * Rp + r];                  // W = L^-T
+        }
+        if (lane == 0) a.rank[n] = R;
+      }
+    }
+    if (ok) return;                                    // warp 0 only; the other warps are done
+    // restore G from the partial Grams and V = I for the eigendecomposition
+    for (int pidx = lane; pidx < npairs; pidx += 32) {
+      int r = 0, rem = pidx;
+      while (rem >= R - r) { rem -= R - r; ++r; }
+      const int c = r + rem;
+      double v = 0.0;
+      for (int ch = 0; ch < a.nchunk; ++ch) v += a.gpart[n][(size_t)ch * npairs + pidx];
+      G[r * Rp + c] = v;
+      G[c * Rp + r] = v;
+    }
+    for (int e = lane; e < Rp * Rp; e += 32) V[e] = (e / Rp == e % Rp) ? 1.0 : 0.0;
+    __syncwarp();
+  }
   if (wid == 0) {
     const int half = Rp / 2;
     for (int sweep = 0; sweep < 40; ++sweep) {
