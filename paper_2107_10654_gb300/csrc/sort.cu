@@ -9,6 +9,8 @@
 // find each other with match_any, so a key's rank is the digit's tile base,
 // plus the counts of earlier warps, plus the counts of earlier rounds of its
 // warp, plus the equal digits in lower lanes -- input order, hence stable.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace tk {
@@ -144,6 +146,127 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const uint64_t* in, u
   }
 }
 
+// ------------------------------------------------- small samples: one cluster
+// For n <= CL_MAX keys the whole sort + dedupe runs in one launch of a cluster
+// of CL_CTAS CTAs: each CTA keeps 8192 keys (32 warps x 8 rounds x 32 lanes)
+// in registers, per-CTA digit counts are exchanged through distributed shared
+// memory, and cluster barriers separate the passes (instead of three kernel
+// launches per pass).  The ranking is the same stable match_any scheme as above,
+// with the CTA's keys after those of lower-ranked CTAs.
+constexpr int CL_CTAS = 8;
+constexpr int CL_THREADS = 1024;
+constexpr int CL_WARPS = CL_THREADS / 32;
+constexpr int CL_ROUNDS = 8;
+constexpr int CL_CHUNK = CL_THREADS * CL_ROUNDS;            // 8192 keys per CTA
+constexpr int64_t CL_MAX = (int64_t)CL_CTAS * CL_CHUNK;     // 65536
+
+__global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
+    k_sort_dedupe_cluster(const uint64_t* keys_in, int n, int key_bits, uint64_t* b0,
+                          uint64_t* b1, uint64_t* keys_u, uint32_t* counts_u, int64_t* start,
+                          int* d_n_unique) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ int wofs[CL_WARPS][RX];          // per-warp digit counts, then offsets
+  __shared__ int ctot[RX];                    // this CTA's digit totals (read by the others)
+  __shared__ int64_t tmp[32];
+  __shared__ int64_t cta_heads[1];
+  const int c = (int)cluster.block_rank();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t wbase = (int64_t)c * CL_CHUNK + (int64_t)w * (CL_ROUNDS * 32);
+  uint64_t k[CL_ROUNDS];
+  const uint64_t* cur = keys_in;
+  uint64_t* nxt = b0;
+  for (int shift = 0; shift < key_bits; shift += 8) {
+    int dg[CL_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < CL_ROUNDS; ++r) {
+      const int64_t i = wbase + r * 32 + lane;
+      k[r] = i < n ? cur[i] : 0;
+      dg[r] = i < n ? (int)((k[r] >> shift) & (RX - 1)) : -1;
+    }
+    for (int d = lane; d < RX; d += 32) wofs[w][d] = 0;
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < CL_ROUNDS; ++r) {
+      const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+      if (dg[r] >= 0 && (peers & lt) == 0) wofs[w][dg[r]] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x < RX) {                   // per-warp exclusive offsets, CTA totals
+      int run = 0;
+      for (int ww = 0; ww < CL_WARPS; ++ww) {
+        const int v = wofs[ww][threadIdx.x];
+        wofs[ww][threadIdx.x] = run;
+        run += v;
+      }
+      ctot[threadIdx.x] = run;
+    }
+    cluster.sync();                           // every CTA's totals are final
+    int64_t all_d = 0, before = 0;
+    if (threadIdx.x < RX) {
+      for (int cc = 0; cc < CL_CTAS; ++cc) {
+        const int v = *cluster.map_shared_rank(&ctot[threadIdx.x], cc);
+        all_d += v;
+        if (cc < c) before += v;
+      }
+    }
+    int64_t total;
+    const int64_t dbase = block_exclusive_scan(threadIdx.x < RX ? all_d : 0, tmp, &total);
+    if (threadIdx.x < RX)
+      for (int ww = 0; ww < CL_WARPS; ++ww) wofs[ww][threadIdx.x] += (int)(dbase + before);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < CL_ROUNDS; ++r) {
+      const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+      int pos = 0;
+      if (dg[r] >= 0) pos = wofs[w][dg[r]] + __popc(peers & lt);
+      __syncwarp();
+      if (dg[r] >= 0) {
+        nxt[pos] = k[r];
+        if ((peers & lt) == 0) wofs[w][dg[r]] += __popc(peers);
+      }
+      __syncwarp();
+    }
+    __threadfence();
+    cluster.sync();                           // scattered keys visible; ctot free again
+    cur = nxt;
+    nxt = nxt == b0 ? b1 : b0;
+  }
+  // run-length encode: thread t owns keys [c * CHUNK + 8 t, +8) of the sorted array
+  const int64_t i0 = (int64_t)c * CL_CHUNK + (int64_t)threadIdx.x * CL_ROUNDS;
+  bool head[CL_ROUNDS];
+  int nh = 0;
+#pragma unroll
+  for (int r = 0; r < CL_ROUNDS; ++r) {
+    const int64_t i = i0 + r;
+    head[r] = i < n && (i == 0 || cur[i] != cur[i - 1]);
+    nh += head[r];
+  }
+  int64_t cnt;
+  int64_t u = block_exclusive_scan(nh, tmp, &cnt);
+  if (threadIdx.x == 0) cta_heads[0] = cnt;
+  cluster.sync();
+  int64_t ubase = 0, utot = 0;
+  for (int cc = 0; cc < CL_CTAS; ++cc) {
+    const int64_t v = *cluster.map_shared_rank(&cta_heads[0], cc);
+    if (cc < c) ubase += v;
+    utot += v;
+  }
+  u += ubase;
+#pragma unroll
+  for (int r = 0; r < CL_ROUNDS; ++r)
+    if (head[r]) { keys_u[u] = cur[i0 + r]; start[u] = i0 + r; ++u; }
+  __threadfence();
+  cluster.sync();                             // all starts written (and remote reads done)
+  for (int64_t q = (int64_t)c * CL_THREADS + threadIdx.x; q < utot; q += (int64_t)CL_CTAS * CL_THREADS) {
+    const int64_t e = q + 1 < utot ? start[q + 1] : n;
+    counts_u[q] = (uint32_t)(e - start[q]);
+  }
+  if (c == 0 && threadIdx.x == 0) *d_n_unique = (int)utot;
+}
+
 // ------------------------------------------------------------ run-length encode
 __global__ void __launch_bounds__(SORT_THREADS) k_rle_heads(const uint64_t* k, int64_t n,
                                                             int64_t* block_counts) {
@@ -207,6 +330,17 @@ tucker_status sort_dedupe(tucker_handle* h, const uint64_t* keys_in, int64_t n, 
     return fail(h, TUCKER_EINTERNAL, "sort scratch too small");
   const int nb = ceil_div(n, SORT_TILE);
   const int nt = ceil_div(n, RX_TILE);
+  if (n <= CL_MAX) {
+    Arena ca(scratch);
+    uint64_t* c0 = ca.get<uint64_t>(n);
+    uint64_t* c1 = ca.get<uint64_t>(n);
+    int64_t* cst = ca.get<int64_t>(n);
+    TK_COUNT(h);
+    k_sort_dedupe_cluster<<<CL_CTAS, CL_THREADS, 0, h->stream>>>(keys_in, (int)n, key_bits, c0, c1,
+                                                                keys_u, counts_u, cst, d_n_unique);
+    TK_LAUNCH(h);
+    return TUCKER_OK;
+  }
   Arena ar(scratch);
   uint64_t* b0 = ar.get<uint64_t>(n);
   uint64_t* b1 = ar.get<uint64_t>(n);
