@@ -70,8 +70,10 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
  * G + lambda*I and the iterative-refinement residual are FP64 in every mode.
  * With a reduced-precision Gram the Cholesky factor of the rounded Gram is a
  * preconditioner: g <- g + M~^-1 (h - M g) with M g evaluated in FP64 on the
- * implicit rows, until ||correction|| < 1e-9 ||g|| (at most 8 iterations); the
- * remaining error is about the contraction factor times that, ~1e-12 or less. */
+ * implicit rows.  With c_k = ||correction_k|| / ||g|| (c_0 = 1) and the
+ * contraction estimate rho = min(c_k / c_{k-1}, 1/2), the iteration stops once
+ * the estimated remaining relative error c_k rho / (1 - rho) is below 1e-8, or
+ * when the corrections stop shrinking, at most 8 iterations. */
 typedef enum {
   TUCKER_PREC_FP64 = 0,   /* FP64 CUDA-core Gram; no refinement needed */
   TUCKER_PREC_FP32 = 1,   /* FP32 CUDA-core Gram, FP64 refinement */
@@ -89,10 +91,9 @@ typedef enum {
  *                  precondition an FP64 iterative refinement,
  *                  g <- g + L32^-T L32^-1 (h - M g), with the residual h - M g
  *                  in FP64 (the explicit FP64 M for TUCKER_PREC_FP64; the
- *                  implicit FP64 rows otherwise).  It stops when
- *                  ||correction|| < tol ||g|| (tol = 1e-14 for an FP64 Gram,
- *                  1e-9 otherwise) or when the correction stops shrinking, at
- *                  most 12 iterations.  It converges when kappa(M) * 2^-24 is
+ *                  implicit FP64 rows otherwise).  It stops by the rule above
+ *                  with a target of 1e-13 for an FP64 Gram (1e-8 otherwise),
+ *                  at most 12 iterations.  It converges when kappa(M) * 2^-24 is
  *                  well below 1; lambda > 0 keeps kappa(M) <= (||G|| +
  *                  lambda)/lambda.  A matrix that FP32 cannot factor (a
  *                  pivot <= 0 after rounding) returns TUCKER_ENOTSPD. */

@@ -437,9 +437,12 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
   *rel = 0.0;
   const bool explicit_m = prec == TUCKER_PREC_FP64;
   if (explicit_m && !h->chol.mixed) return TUCKER_OK;
-  const double tol = explicit_m ? 1e-14 : 1e-9;
+  // stop when the remaining relative error, estimated from the last correction
+  // c_k and the contraction rho ~ c_k / c_{k-1}, is below target (c_0 = 1: the
+  // first solve), or when the corrections stop shrinking (rounding level)
+  const double target = explicit_m ? 1e-13 : 1e-8;
   const int max_iters = h->chol.mixed ? 12 : 8;
-  double prev = INFINITY;
+  double prev = 1.0;
   for (int it = 0; it < max_iters; ++it) {
     if (explicit_m) {
       TK_TRY(launch_gemv_resid(h, h->chol.L, d, g, rhs, b.r));
@@ -455,7 +458,9 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
     TK_CUDA(h, cudaStreamSynchronize(h->stream));
     *iters = it + 1;
     *rel = hv[1] > 0 ? sqrt(hv[0] / hv[1]) : 0.0;
-    if (*rel < tol || *rel > 0.5 * prev) break;
+    const double rho = fmin(*rel / prev, 0.5);
+    if (*rel == 0.0 || *rel * rho / (1.0 - rho) < target) break;
+    if (it > 0 && *rel > 0.5 * prev) break;
     prev = *rel;
   }
   return TUCKER_OK;
