@@ -22,6 +22,7 @@ namespace tk {
 
 // ------------------------------------------------ launchers from other files
 tucker_status hash_ensure(tucker_handle* h, const tucker_tensor* X, int* probes_out);
+size_t sample_keys_scratch(const FactorSet& F, bool observed);
 tucker_status sample_keys(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
                           int64_t m, uint64_t seed, uint32_t sweep, int reg,
                           const tucker_tensor* observed, int64_t max_draws,
@@ -621,7 +622,7 @@ tucker_status tucker_sample_rows(tucker_handle* h, int N, const int64_t* I, cons
   Arena sz(nullptr);
   carve(sz, cdf, &raw, &dT, &ss, &nu, &nreal, idx, &w, &x, &D);
   // the missing-mode sampler carves its round buffers after these
-  size_t extra = observed ? (size_t)((1 << 26) * 9 + (8 << 20)) : 0;
+  size_t extra = sample_keys_scratch(F, observed != nullptr);
   TK_TRY(ws_reserve(h, sz.off + extra));
   Arena ar(h->ws);
   carve(ar, cdf, &raw, &dT, &ss, &nu, &nreal, idx, &w, &x, &D);
@@ -694,7 +695,7 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   memset(&b, 0, sizeof(b));
   Arena sz(nullptr);
   carve_sketch(sz, h, F, cap, prec, fixed != nullptr, &b);
-  size_t extra = (!fixed && !X->dense) ? (size_t)((1 << 26) * 9 + (8 << 20)) : 0;
+  size_t extra = fixed ? 0 : sample_keys_scratch(F, !X->dense);
   TK_TRY(ws_reserve(h, sz.off + extra));
   TK_TRY(chol_reserve(h, F.d));
   Arena ar(h->ws);

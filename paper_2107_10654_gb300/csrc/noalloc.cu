@@ -20,6 +20,7 @@ namespace tk {
 
 tucker_status launch_cdf_from_lev(tucker_handle* h, int N, const int64_t* I,
                                   const double* const* lev, uint64_t* const* cdf);
+size_t sample_keys_scratch(const FactorSet& F, bool observed);
 tucker_status sample_keys(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
                           int64_t m, uint64_t seed, uint32_t sweep, int reg,
                           const tucker_tensor* observed, int64_t max_draws,
@@ -149,10 +150,11 @@ extern "C" tucker_status tucker_sample_rows_noalloc(void* cuda_stream, int N, co
   double *w, *x, *D;
   Arena sz(nullptr);
   carve(sz, &raw, &dT, &ss, &nu, &nreal, &w, &x, &D);
-  if (sz.off > h.ws_cap) {
+  if (sz.off + sample_keys_scratch(F, false) > h.ws_cap) {
     char msg[200];
     snprintf(msg, sizeof(msg), "m = %lld needs %zu scratch bytes; the fixed array holds %zu "
-             "(TUCKER_NOALLOC_SCRATCH_BYTES)", (long long)m, sz.off, h.ws_cap);
+             "(TUCKER_NOALLOC_SCRATCH_BYTES)", (long long)m, sz.off + sample_keys_scratch(F, false),
+             h.ws_cap);
     return noalloc_fail(err_host, err_len, TUCKER_ECAPACITY, msg);
   }
   Arena ar(h.ws);

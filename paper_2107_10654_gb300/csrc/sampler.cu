@@ -33,21 +33,48 @@ struct SampleArgs {
   int64_t* block_counts;       // [gridDim.x]
   int* status;
   int cdf_in_smem;
+  // cutpoint guide tables (Chen & Asau, 1974): for the 2^kbits buckets of the
+  // 64-bit uniform u, guide[b] = min{i : C[i] > floor(b Q / 2^kbits)}, the
+  // first candidate for every u of bucket b; a forward scan finishes the search
+  const uint32_t* guide;              // nullable; modes concatenated
+  int64_t gofs[TUCKER_MAX_ORDER];
+  int kbits[TUCKER_MAX_ORDER];
 };
+
+__global__ void k_guide(SampleArgs a, uint32_t* guide) {
+  for (int n = 0; n < a.N; ++n) {
+    const int64_t K = int64_t(1) << a.kbits[n];
+    const uint64_t* C = a.cdf[n];
+    const int In = (int)a.I[n];
+    const uint64_t Q = C[In - 1];
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < K;
+         b += (int64_t)gridDim.x * blockDim.x) {
+      const uint64_t lb = a.kbits[n] ? __umul64hi((uint64_t)b << (64 - a.kbits[n]), Q) : 0;
+      guide[a.gofs[n] + b] = (uint32_t)upper_bound_u64(C, In, lb);
+    }
+  }
+}
 
 constexpr int SAMPLE_THREADS = 256;
 constexpr int SAMPLE_ITEMS = 4;            // draws per thread (consecutive)
 
 __device__ __forceinline__ uint64_t draw_key(const SampleArgs& a, const uint64_t* const* C,
-                                             uint64_t t) {
+                                             const uint32_t* const* Gd, uint64_t t) {
   uint64_t key = 0;
   U64x4 w = philox4x64_10(t, 0, 0, 0, a.seed, a.sweep);
   for (int n = 0; n < a.N; ++n) {
     if (n == 4) w = philox4x64_10(t, 1, 0, 0, a.seed, a.sweep);
     const int In = (int)a.I[n];
     const uint64_t Q = C[n][In - 1];
-    uint64_t target = __umul64hi(w.v[n & 3], Q);
-    int i = upper_bound_u64(C[n], In, target);
+    const uint64_t u = w.v[n & 3];
+    const uint64_t target = __umul64hi(u, Q);
+    int i;
+    if (Gd) {                                   // min{i : C[i] > target} from the bucket's cutpoint
+      i = a.kbits[n] ? (int)Gd[n][u >> (64 - a.kbits[n])] : 0;
+      while (C[n][i] <= target) ++i;
+    } else {
+      i = upper_bound_u64(C[n], In, target);
+    }
     key = key * (uint64_t)In + (uint64_t)i;
   }
   if (a.reg == TUCKER_REG_AUGMENTED) {
@@ -61,12 +88,22 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(SampleArgs a) {
   extern __shared__ uint64_t scdf[];
   __shared__ int64_t scan_tmp[32];
   const uint64_t* C[TUCKER_MAX_ORDER];
+  const uint32_t* Gd[TUCKER_MAX_ORDER];
+  bool guided = false;
   if (a.cdf_in_smem) {
     int64_t off = 0;
     for (int n = 0; n < a.N; ++n) {
       for (int64_t i = threadIdx.x; i < a.I[n]; i += blockDim.x) scdf[off + i] = a.cdf[n][i];
       C[n] = scdf + off;
       off += a.I[n];
+    }
+    if (a.guide) {
+      uint32_t* sg = reinterpret_cast<uint32_t*>(scdf + off);
+      int64_t tot = 0;
+      for (int n = 0; n < a.N; ++n) tot += int64_t(1) << a.kbits[n];
+      for (int64_t i = threadIdx.x; i < tot; i += blockDim.x) sg[i] = a.guide[i];
+      for (int n = 0; n < a.N; ++n) Gd[n] = sg + a.gofs[n];
+      guided = true;
     }
     __syncthreads();
   } else {
@@ -79,7 +116,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(SampleArgs a) {
   for (int j = 0; j < SAMPLE_ITEMS; ++j) {
     int64_t e = base + j;
     if (e >= a.count) break;
-    uint64_t key = draw_key(a, C, (uint64_t)(a.t0 + e));
+    uint64_t key = draw_key(a, C, guided ? Gd : nullptr, (uint64_t)(a.t0 + e));
     a.keys_out[e] = key;
     if (a.slot_key) {
       bool ok = key >= a.total || hash_contains(a.slot_key, a.log2, a.max_probes, key, a.status);
@@ -205,6 +242,20 @@ tucker_status hash_ensure(tucker_handle* h, const tucker_tensor* X, int* probes_
   return TUCKER_OK;
 }
 
+static int guide_bits(int64_t I) {
+  int kb = 0;
+  while (kb < 12 && (int64_t(1) << kb) < I) ++kb;
+  return kb;
+}
+
+// Bytes sample_keys may take from the caller's arena beyond the caller's own
+// buffers: the guide tables and, with observed entries, the per-round buffers.
+size_t sample_keys_scratch(const FactorSet& F, bool observed) {
+  size_t g = 0;
+  for (int n = 0; n < F.N; ++n) g += (size_t(1) << guide_bits(F.I[n])) * 4;
+  return g + 512 + (observed ? (size_t)((1 << 26) * 9 + (8 << 20)) : 0);
+}
+
 static int cdf_smem_bytes(const SampleArgs& a) {
   int64_t tot = 0;
   for (int n = 0; n < a.N; ++n) tot += a.I[n];
@@ -231,6 +282,27 @@ tucker_status sample_keys(tucker_handle* h, const FactorSet& F, const uint64_t* 
   int smem = cdf_smem_bytes(a);
   a.cdf_in_smem = smem >= 0;
   if (smem < 0) smem = 0;
+  const int64_t expect_draws = observed ? 4 * m : m;
+  if (a.cdf_in_smem && expect_draws >= (int64_t(1) << 20)) {
+    // guide tables: 2^ceil(log2 I_n) buckets per mode (at most 2^12), if they fit too;
+    // only for large draw counts (their build is one more launch)
+    int64_t gtot = 0;
+    for (int n = 0; n < F.N; ++n) {
+      const int kb = guide_bits(F.I[n]);
+      a.kbits[n] = kb;
+      a.gofs[n] = gtot;
+      gtot += int64_t(1) << kb;
+    }
+    if (smem + gtot * 4 <= 200 * 1024) {
+      uint32_t* gbuf = ar.get<uint32_t>(gtot);
+      TK_COUNT(h);
+      k_guide<<<ceil_div(gtot, 256) < h->num_sms ? ceil_div(gtot, 256) : h->num_sms, 256, 0,
+                h->stream>>>(a, gbuf);
+      TK_LAUNCH(h);
+      a.guide = gbuf;
+      smem += (int)(gtot * 4);
+    }
+  }
   TK_CUDA(h, cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int per_block = SAMPLE_THREADS * SAMPLE_ITEMS;
   if (!observed) {
