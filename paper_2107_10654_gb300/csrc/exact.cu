@@ -120,6 +120,49 @@ __global__ void __launch_bounds__(256) k_ttm_last2(const T* X, int64_t pre, int 
 #pragma unroll
     for (int q = 0; q < 8; ++q) y[q] = T(0);
     const T* slab = X + p * (int64_t)I1 * I2;
+    // rows of up to 4 x 16 bytes per lane: the next row of this warp is loaded
+    // while the current one is contracted (two rows in flight per warp)
+    const int nc = vec && I2 % (32 * VEC) == 0 ? I2 / (32 * VEC) : 0;
+    if (nc >= 1 && nc <= 4) {
+      uint4 xa[4], xb[4];
+      auto load = [&](uint4* buf, int ri) {
+        const T* row = slab + (int64_t)ri * I2;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < nc) buf[c] = __ldg(reinterpret_cast<const uint4*>(row + (c * 32 + lane) * VEC));
+      };
+      if (w < I1) load(xa, w);
+      for (int i = w; i < I1; i += 8) {
+        if (i + 8 < I1) load(xb, i + 8);
+        T acc[RP];
+#pragma unroll
+        for (int j = 0; j < RP; ++j) acc[j] = T(0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c >= nc) break;
+          T xv[VEC];
+          *reinterpret_cast<uint4*>(xv) = xa[c];
+          const int j0 = (c * 32 + lane) * VEC;
+#pragma unroll
+          for (int j = 0; j < RP; ++j) {
+            T av[VEC];
+            *reinterpret_cast<uint4*>(av) = *reinterpret_cast<const uint4*>(At + j * I2 + j0);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) acc[j] = fma(xv[q], av[q], acc[j]);
+          }
+        }
+        const T t = transpose_reduce<T, RP>(acc, lane);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = lane + 32 * q;
+          const int b = e % R2;
+          const T tb = __shfl_sync(0xffffffffu, t, (b % RP) * G);
+          if (e < RR) y[q] = fma(A1s[i * R1 + e / R2], tb, y[q]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) xa[c] = xb[c];
+      }
+    } else
     for (int i = w; i < I1; i += 8) {
       const T* row = slab + (int64_t)i * I2;
       T acc[RP];
