@@ -151,9 +151,9 @@ __device__ bool factor_diag_block(const T* M, int d, int k, int nb, T (*a)[CB + 
 }
 
 // A_ij -= L_ik L_jk^T over the lower TS x TS tiles of the trailing matrix
-// (rows and columns >= s), tiles distributed over the CTAs.  The panel rows of
-// a CTA's next tile are loaded into registers while the current tile is
-// multiplied.  Thread (ty, tx) owns rows ty + 16 i and columns tx + 8 j.
+// (rows and columns >= s), tiles distributed over the CTAs.  The panel rows and
+// the entries of a CTA's next tile are loaded into registers while the current
+// tile is multiplied.  Thread (ty, tx) owns rows ty + 16 i and columns tx + 8 j.
 template <class T, int TS>
 __device__ void trailing_update(T* M, int d, int k, int nb, int s, T (*Pa)[CB + 1],
                                 T (*Pb)[CB + 1]) {
@@ -171,6 +171,7 @@ __device__ void trailing_update(T* M, int d, int k, int nb, int s, T (*Pa)[CB + 
     *c0 = s + (tile - ti * (ti + 1) / 2) * TS;
   };
   T ra[PER], rb[PER];
+  T cn[OR][OC];                                 // the next tile's entries of this thread
   auto fetch = [&](int tile) {
     int r0, c0;
     origin(tile, &r0, &c0);
@@ -179,6 +180,15 @@ __device__ void trailing_update(T* M, int d, int k, int nb, int s, T (*Pa)[CB + 
       const int e = threadIdx.x + q * CHOL_THREADS, i = e / CB, c = e % CB;
       ra[q] = (r0 + i < d && c < nb) ? M[(size_t)(r0 + i) * d + k + c] : T(0);
       rb[q] = (c0 + i < d && c < nb) ? M[(size_t)(c0 + i) * d + k + c] : T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < OR; ++i) {
+      const int r = r0 + ty + 16 * i;
+#pragma unroll
+      for (int j = 0; j < OC; ++j) {
+        const int c = c0 + tx + 8 * j;
+        cn[i][j] = (r < d && c < d && c <= r) ? M[(size_t)r * d + c] : T(0);
+      }
     }
   };
   if ((int)blockIdx.x < ntiles) fetch(blockIdx.x);
@@ -192,13 +202,13 @@ __device__ void trailing_update(T* M, int d, int k, int nb, int s, T (*Pa)[CB + 
       Pa[e / CB][e % CB] = ra[q];
       Pb[e / CB][e % CB] = rb[q];
     }
-    __syncthreads();
-    if (tile + (int)gridDim.x < ntiles) fetch(tile + gridDim.x);
     T acc[OR][OC];
 #pragma unroll
     for (int i = 0; i < OR; ++i)
 #pragma unroll
-      for (int j = 0; j < OC; ++j) acc[i][j] = T(0);
+      for (int j = 0; j < OC; ++j) acc[i][j] = cn[i][j];
+    __syncthreads();
+    if (tile + (int)gridDim.x < ntiles) fetch(tile + gridDim.x);
 #pragma unroll 4
     for (int c = 0; c < CB; ++c) {
       T av[OR], bv[OC];
@@ -209,7 +219,7 @@ __device__ void trailing_update(T* M, int d, int k, int nb, int s, T (*Pa)[CB + 
 #pragma unroll
       for (int i = 0; i < OR; ++i)
 #pragma unroll
-        for (int j = 0; j < OC; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < OC; ++j) acc[i][j] = fma(-av[i], bv[j], acc[i][j]);
     }
 #pragma unroll
     for (int i = 0; i < OR; ++i) {
@@ -218,7 +228,7 @@ __device__ void trailing_update(T* M, int d, int k, int nb, int s, T (*Pa)[CB + 
 #pragma unroll
       for (int j = 0; j < OC; ++j) {
         const int c = c0 + tx + 8 * j;
-        if (c < d && c <= r) M[(size_t)r * d + c] -= acc[i][j];
+        if (c < d && c <= r) M[(size_t)r * d + c] = acc[i][j];
       }
     }
   }
@@ -234,8 +244,9 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol_coop(T* M, int d, int* st
   extern __shared__ __align__(16) unsigned char chol_smem[];
   T (*P)[CB + 1] = reinterpret_cast<T (*)[CB + 1]>(chol_smem);     // panel rows of this CTA
   __shared__ T Lkk[CB][CB + 1];
-  __shared__ T Pa[32][CB + 1];
-  __shared__ T Pb[32][CB + 1];
+  constexpr int TSMAX = sizeof(T) == 4 ? 64 : 32;  // FP32 uses 64 x 64 tiles while they last
+  __shared__ T Pa[TSMAX][CB + 1];
+  __shared__ T Pb[TSMAX][CB + 1];
   __shared__ uint16_t tri[CB * (CB - 1) / 2 + CB];
   const int G = gridDim.x, cta = blockIdx.x;
   // packed trailing-triangle table: entry e = ii (ii + 1) / 2 + cc
@@ -261,9 +272,11 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol_coop(T* M, int d, int* st
     }
     grid.sync();
     if (s < d) {
-      // 32 x 32 tiles while there are at least two per CTA, then 16 x 16
-      const int t32 = (d - s + 31) / 32;
-      if (t32 * (t32 + 1) / 2 >= 2 * G)
+      // the largest tiles that still give every CTA at least two
+      const int t64 = (d - s + 63) / 64, t32 = (d - s + 31) / 32;
+      if (TSMAX == 64 && t64 * (t64 + 1) / 2 >= 2 * G)
+        trailing_update<T, TSMAX>(M, d, k, nb, s, Pa, Pb);
+      else if (t32 * (t32 + 1) / 2 >= 2 * G)
         trailing_update<T, 32>(M, d, k, nb, s, Pa, Pb);
       else
         trailing_update<T, 16>(M, d, k, nb, s, Pa, Pb);
