@@ -403,6 +403,30 @@ def main():
     if world > 1:
         dist.barrier()
 
+    # ALS sweeps (Alg. 2: factor updates, then the core update) and the adjoint of the
+    # frozen-sketch solve, timed the same way on copies of the state (not the headline)
+    extra = {}
+    if not missing:
+        Fa = [a.clone() for a in F]
+        ca = g_sk.clone()
+        for kind in ("sketched", "exact"):
+            sk = kind == "sketched"
+            T.tucker_als_sweep(h, X, Fa, ca, w.lam, sk, w.m, w.seed_sample, 0, args.reg, prec)
+            ms_s, _ = timed(lambda: T.tucker_als_sweep(h, X, Fa, ca, w.lam, sk, w.m, w.seed_sample,
+                                                       1, args.reg, prec), min(args.steps, 3))
+            extra[f"als_sweep_ms_{kind}"] = statistics.mean(ms_s)
+        smp = T.Samples.empty(w.m, dev)
+        lev = T.tucker_leverage_scores(h, F)[0]
+        smp = T.tucker_sample_rows(h, w.dims, w.ranks, lev, w.m, w.seed_sample, 0, args.reg, out=smp)
+        gf, stf = T.tucker_core_update_sketched(h, X, F, w.lam, 0, 0, 0, args.reg, prec, fixed=smp,
+                                                stats=True)
+        gbar = torch.ones(w.d, dtype=torch.float64, device=dev)
+        T.tucker_core_solve_adjoint(h, X, F, w.lam, args.reg, prec, smp, stf["solve_id"], gf, gbar)
+        ms_a, _ = timed(lambda: T.tucker_core_solve_adjoint(h, X, F, w.lam, args.reg, prec, smp,
+                                                            stf["solve_id"], gf, gbar),
+                        min(args.steps, 5))
+        extra["adjoint_ms"] = statistics.mean(ms_a)
+
     # the other ridge solver on the same sample, timed the same way (not the headline)
     other = "mixed" if args.solver == "fp64" else "fp64"
     h2 = T.Handle(stream=stream, solver=other)
@@ -491,7 +515,7 @@ def main():
                 "exact_ms": ms_ex, "speedup_vs_exact": ms_ex / ms, "loss_ratio": loss_ratio,
                 "kron_rows_per_s": kron_rows_s * world, "n_unique": stats[-1]["n_unique"],
                 "refine_iters": stats[-1]["refine_iters"], "stage_ms": stage,
-                "exact_hbm_gbs": exact_gbs, "solver": args.solver, "other_solver": alt,
+                "exact_hbm_gbs": exact_gbs, "solver": args.solver, "other_solver": alt, **extra,
                 "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu,
                 "e2e": {"value": ms_e2e, "unit": "ms",
                         "h2d_bytes_per_step": int(in_bytes + sum(a.numel() * a.element_size()
