@@ -53,10 +53,9 @@ def backward(factors: Sequence[np.ndarray], dims, keys_u, w, x, lam, reg_diag, g
     letters = "abcdefgh"[:len(R)]
     dA = []
     for n, A in enumerate(factors):
-        others = [rows[k] for k in range(len(R)) if k != n]
-        spec = ("u" + letters + "," + ",".join("u" + letters[k] for k in range(len(R)) if k != n)
-                + "->u" + letters[n])
-        contrib = np.einsum(spec, dK, *others)
+        rest = [k for k in range(len(R)) if k != n]
+        spec = ",".join(["u" + letters] + ["u" + letters[k] for k in rest]) + "->u" + letters[n]
+        contrib = np.einsum(spec, dK, *[rows[k] for k in rest])
         out = np.zeros(np.asarray(A).shape)
         np.add.at(out, idx[n], contrib)
         dA.append(out)

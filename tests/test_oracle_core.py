@@ -214,6 +214,32 @@ def test_adjoint_matches_central_differences(reg):
         assert abs(fd - an) < 1e-7 * max(1.0, abs(an))
 
 
+@pytest.mark.parametrize("dims,ranks", [((40,), (3,)), ((8, 9), (3, 2)),
+                                         ((5, 4, 3, 4), (2, 1, 2, 3))])
+def test_adjoint_other_orders_match_central_differences(dims, ranks):
+    """Orders 1, 2 and 4 (with a rank-1 mode): the contraction over the other
+    modes is empty, a single product, or three products."""
+    X, _, F = _problem(dims, ranks, 0.3, 15)
+    d, lam = int(np.prod(ranks)), 0.2
+    sk = CU.sketch(F, dims, 300, 4, 0, S.REG_EXACT)
+    keys, w = sk["keys"], sk["w"]
+    x = CU.gather_dense(X, keys, dims)
+    gbar = np.random.default_rng(7).standard_normal(d)
+    dA, dx = ADJ.backward(F, dims, keys, w, x, lam, np.ones(d), gbar)
+    h = 1e-6
+    g = np.random.default_rng(8)
+    for _ in range(6):
+        dirs = [g.standard_normal(A.shape) for A in F]
+        dirx = g.standard_normal(x.shape)
+        fp = ADJ.forward([A + h * e for A, e in zip(F, dirs)], dims, keys, w, x + h * dirx, lam,
+                         np.ones(d))
+        fm = ADJ.forward([A - h * e for A, e in zip(F, dirs)], dims, keys, w, x - h * dirx, lam,
+                         np.ones(d))
+        fd = (fp - fm) @ gbar / (2 * h)
+        an = sum(np.sum(a * e) for a, e in zip(dA, dirs)) + dx @ dirx
+        assert abs(fd - an) < 1e-7 * max(1.0, abs(an))
+
+
 def test_sampled_row_products_equal_explicit_rows():
     """K_S g and K_S^T c against an explicit K indexed by the decoded keys."""
     g = np.random.default_rng(7)
