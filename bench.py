@@ -35,6 +35,7 @@ WORKLOAD = "dense3_512_r8_f32"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # FP64 CUDA-core peak: 1.25 TFLOP/s (the GB300 nominal FP64 rate).
 FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e-3
 # tcgen05 dense peak relative to BF16: TF32 runs at half the BF16 rate.
 TC_RATIO = {"bf16": 1.0, "tf32": 0.5}
 
@@ -48,7 +49,7 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--prec", default="auto")
     p.add_argument("--reg", default="exact")
-    p.add_argument("--solver", default="fp64", choices=["fp64", "mixed"],
+    p.add_argument("--solver", default="mixed", choices=["fp64", "mixed"],
                    help="ridge solver of the timed update (the other one is timed beside it)")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     p.add_argument("--stage-roofline", action="store_true",
@@ -486,9 +487,15 @@ def main():
 
     def factor_roofline():
         flops = d ** 3 / 3
-        kernel = "k_chol_coop<double>" if args.solver == "fp64" else "k_chol_coop<float>"
-        peak = FP64_PEAK_TFLOPS if args.solver == "fp64" else 152 * 128 * 2 * 2.07
-        note = "FP64 nominal 1.25 TFLOP/s" if args.solver == "fp64" else "FP32 FMA nominal"
+        if args.solver == "fp64":
+            kernel, peak, note = "k_chol_coop<double>", FP64_PEAK_TFLOPS, "FP64 nominal 1.25 TFLOP/s"
+        else:
+            # FP32 FMA nominal of the whole GPU: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+            peak = FP32_PEAK_TFLOPS
+            if d <= 512:       # one thread-block cluster (8 or 16 SMs) holds the matrix
+                kernel, note = "k_chol32_cluster", "FP32 nominal of all 152 SMs (the kernel runs on one cluster)"
+            else:
+                kernel, note = "k_chol_coop<float>", "FP32 FMA nominal 80.5 TFLOP/s"
         achieved = flops / (kms["ms_factor"] * 1e-3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_tab.get((kernel, w.name)),

@@ -29,6 +29,7 @@ namespace tk {
 constexpr int CB = 32;      // panel width
 constexpr int SB = 64;      // block of the triangular solves
 constexpr int CHOL_THREADS = 128;   // one warp per SM sub-partition: enough for the FP64 pipe
+constexpr int CHOL_CL_MAX_D = 1024; // largest order factored by one cluster (if it fits)
 
 __global__ void k_add_diag(double* M, int d, const double* diag) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x)
@@ -317,7 +318,304 @@ tucker_status cholesky_t(tucker_handle* h, T* M, int d) {
 }
 
 tucker_status cholesky(tucker_handle* h, double* M, int d) { return cholesky_t<double>(h, M, d); }
-tucker_status cholesky32(tucker_handle* h, float* M, int d) { return cholesky_t<float>(h, M, d); }
+// ------------------------------------------------ FP32 Cholesky on one cluster
+// For small d the FP32 factor of the mixed solver is computed by a single
+// thread-block cluster (16 CTAs where the device allows that size, else 8)
+// with the whole matrix resident in the CTAs' shared memory: CTA c owns rows
+// c, c + C, c + 2C, ...  Data moves between CTAs only by stores into the
+// receivers' shared memory (a remote store does not wait for a round trip),
+// ordered by cluster barriers.  Step k (columns k0 .. k0 + 31):
+//   1. warp 0 factors the 32 x 32 diagonal block in registers (lane i holds
+//      row i; each pivot's scaled column goes through a shared-memory buffer
+//      and a release flag), and the other warps run the same pivots on this
+//      CTA's rows below the block as soon as each column is published, giving
+//      the panel rows L_ik = A_ik L_kk^-T;
+//   2. every CTA stores its panel rows into every CTA's panel buffer; cluster
+//      barrier;
+//   3. each CTA updates its own rows' trailing entries A_ic -= L_i . L_c
+//      (4 rows x 4 columns per thread, 8 threads per 32-column chunk), then
+//      stores its rows of the next diagonal block into every CTA; cluster
+//      barrier.
+// Every CTA factors the same block with the same instructions, so all agree
+// on a failed pivot and leave at the same step (no remote store follows).
+constexpr int CLB = 32;
+constexpr int CLPS = 36;                 // row stride of the panel and block buffers (floats)
+constexpr int CHOL_CL_THREADS = 256;
+constexpr size_t CHOL_CL_SMEM_MAX = 227 * 1024;
+
+struct ClGeom {
+  int nr;      // own rows per CTA (at most)
+  int ld;      // own-row stride in floats: 4 x odd, so 8 lanes' 16-byte row loads hit distinct banks
+  size_t smem;
+};
+
+__host__ __device__ inline ClGeom chol_cl_geom(int d, int C) {
+  ClGeom g;
+  g.nr = (d + C - 1) / C;
+  g.ld = 4 * (((d + 3) / 4) | 1);
+  g.smem = sizeof(float) * ((size_t)g.nr * g.ld + (size_t)d * CLPS + (size_t)CLB * CLPS +
+                            (size_t)CLB * CLB + CLB);
+  return g;
+}
+
+__device__ __forceinline__ void st_release_cta(int* p, int v) {
+  asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)),
+               "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_cta(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v)
+               : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(CHOL_CL_THREADS, 1) k_chol32_cluster(float* M, int d, int* status) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), me = (int)cl.block_rank();
+  const ClGeom G = chol_cl_geom(d, C);
+  extern __shared__ __align__(16) float cls[];
+  float* rows = cls;                                  // own row t = global row me + t C
+  float* Pb = rows + (size_t)G.nr * G.ld;             // panel row c at (c - s) * CLPS
+  float* Db = Pb + (size_t)d * CLPS;                  // diagonal block row i at i * CLPS
+  float* colL = Db + CLB * CLPS;                      // column j of L_kk at j * CLB
+  float* yv = colL + CLB * CLB;                       // the pivots' 1 / sqrt(p_j)
+  __shared__ int flag, bad_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int nown = d > me ? (d - me + C - 1) / C : 0;
+  for (int t = warp; t < nown; t += nw) {
+    const int i = me + t * C;
+    for (int c = lane; c <= i; c += 32) rows[(size_t)t * G.ld + c] = M[(size_t)i * d + c];
+  }
+  if (tid == 0) { flag = 0; bad_s = 0; }
+  __syncthreads();
+  // this CTA's rows of the diagonal block at k0, to every CTA's Db
+  auto push_diag = [&](int k0) {
+    const int nb = min(CLB, d - k0);
+    const int tf = k0 > me ? (k0 - me + C - 1) / C : 0;
+    const int tl = min(nown, (k0 + nb - me + C - 1) / C);
+    const int nd = max(0, tl - tf);
+    for (int e = tid; e < C * nd * (CLB / 4); e += blockDim.x) {
+      const int u = e & 7, rest = e >> 3, tt = tf + rest % nd, x = rest / nd;
+      const float4 v = *reinterpret_cast<const float4*>(rows + (size_t)tt * G.ld + k0 + 4 * u);
+      *reinterpret_cast<float4*>(cl.map_shared_rank(Db, x) + (me + tt * C - k0) * CLPS + 4 * u) = v;
+    }
+  };
+  push_diag(0);
+  cl.sync();
+  int step = 0;
+  for (int k0 = 0; k0 < d; k0 += CLB, ++step) {
+    const int nb = min(CLB, d - k0), s = k0 + nb;
+    const int t0 = s > me ? (s - me + C - 1) / C : 0;   // first own row below the block
+    const int np = max(0, nown - t0);
+    if (warp == 0) {
+      // the diagonal block (identity past nb)
+      float a[CLB];
+#pragma unroll
+      for (int j = 0; j < CLB; ++j)
+        a[j] = (lane < nb && j <= lane) ? Db[lane * CLPS + j] : (lane == j ? 1.f : 0.f);
+      bool bad = false;
+#pragma unroll
+      for (int j = 0; j < CLB; ++j) {
+        const float pv = __shfl_sync(0xffffffffu, a[j], j);
+        bad |= !(pv >= 1.17549435e-38f && pv <= 3.402823466e38f);   // normal and finite
+        float y;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(pv));
+        const float la = lane >= j ? a[j] * y : 0.f;                // l_ij, i = lane
+        a[j] = la;
+        colL[j * CLB + lane] = la;
+        if (lane == 0) yv[j] = y;
+        __syncwarp();
+        if (lane == 0) st_release_cta(&flag, step * CLB + j + 1);
+#pragma unroll
+        for (int u = (j + 1) / 4; u < CLB / 4; ++u) {
+          const float4 v = *reinterpret_cast<const float4*>(colL + j * CLB + 4 * u);
+          const float lc[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int w = 0; w < 4; ++w)
+            if (4 * u + w > j) a[4 * u + w] = fmaf(-la, lc[w], a[4 * u + w]);
+        }
+      }
+      if (lane == 0 && bad) bad_s = 1;
+      if (lane < nb && (k0 + lane) % C == me) {             // L_kk rows owned here
+        float* dr = rows + (size_t)((k0 + lane) / C) * G.ld + k0;
+#pragma unroll
+        for (int j = 0; j < CLB; ++j)
+          if (j <= lane) dr[j] = a[j];
+      }
+    } else {
+      // own rows below the block (lane = row), one pivot behind the published column
+      const int nchb = (np + 31) >> 5;
+      for (int ch = warp - 1; ch < nchb; ch += nw - 1) {
+        const int q = ch * 32 + lane;
+        const bool has = q < np;
+        float* prow = rows + (size_t)(t0 + (has ? q : 0)) * G.ld + k0;
+        float p[CLB];
+#pragma unroll
+        for (int u = 0; u < CLB / 4; ++u) {
+          const float4 v = has ? *reinterpret_cast<const float4*>(prow + 4 * u)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+          p[4 * u] = v.x; p[4 * u + 1] = v.y; p[4 * u + 2] = v.z; p[4 * u + 3] = v.w;
+        }
+#pragma unroll
+        for (int j = 0; j < CLB; ++j) {
+          // warp 0 never waits, so this wait ends; the limit only guards against a bug
+          for (int spins = 0; ld_acquire_cta(&flag) <= step * CLB + j; )
+            if (++spins > (1 << 24)) { set_status(status, DEV_INTERNAL); break; }
+          const float lp = p[j] * yv[j];
+          p[j] = lp;
+#pragma unroll
+          for (int u = (j + 1) / 4; u < CLB / 4; ++u) {
+            const float4 v = *reinterpret_cast<const float4*>(colL + j * CLB + 4 * u);
+            const float lc[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+              if (4 * u + w > j) p[4 * u + w] = fmaf(-lp, lc[w], p[4 * u + w]);
+          }
+        }
+        if (has) {
+#pragma unroll
+          for (int u = 0; u < CLB / 4; ++u)
+            *reinterpret_cast<float4*>(prow + 4 * u) =
+                make_float4(p[4 * u], p[4 * u + 1], p[4 * u + 2], p[4 * u + 3]);
+        }
+      }
+    }
+    __syncthreads();
+    if (bad_s) {                                      // the same in every CTA, at the same step
+      if (me == 0 && tid == 0) set_status(status, DEV_NOTSPD);
+      return;
+    }
+    if (s >= d) break;
+    // own panel rows into every CTA's panel buffer
+    for (int e = tid; e < C * np * (CLB / 4); e += blockDim.x) {
+      const int u = e & 7, rest = e >> 3, tt = t0 + rest % np, x = rest / np;
+      const float4 v = *reinterpret_cast<const float4*>(rows + (size_t)tt * G.ld + k0 + 4 * u);
+      *reinterpret_cast<float4*>(cl.map_shared_rank(Pb, x) + (size_t)(me + tt * C - s) * CLPS +
+                                 4 * u) = v;
+    }
+    cl.sync();                                        // every panel row has arrived
+    // trailing entries of the own rows i >= s, columns s <= c <= i: item = (4 own rows,
+    // 32 columns), 8 threads per item, thread columns c = cb + l8 + 8 v
+    const int npan = d - s;
+    const int nrg = (np + 3) / 4, nck = (npan + 31) / 32;
+    const int l8 = lane & 7;
+    for (int it = tid >> 3; it < nrg * nck; it += blockDim.x >> 3) {
+      const int rg = it / nck, ck = it - rg * nck;
+      const int tA = t0 + 4 * rg, nr4 = min(4, nown - tA);
+      const int ilast = me + (tA + nr4 - 1) * C;
+      const int cb = s + 32 * ck;
+      if (cb > ilast) continue;
+      float acc[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[r][v] = 0.f;
+#pragma unroll 2
+      for (int q4 = 0; q4 < CLB / 4; ++q4) {
+        float4 ar[4], b[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          ar[r] = r < nr4 ? *reinterpret_cast<const float4*>(rows + (size_t)(tA + r) * G.ld + k0 + 4 * q4)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          b[v] = *reinterpret_cast<const float4*>(Pb + (size_t)(cb - s + l8 + 8 * v) * CLPS + 4 * q4);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            acc[r][v] = fmaf(ar[r].x, b[v].x, fmaf(ar[r].y, b[v].y,
+                        fmaf(ar[r].z, b[v].z, fmaf(ar[r].w, b[v].w, acc[r][v]))));
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (r >= nr4) break;
+        const int i = me + (tA + r) * C;
+        float* dst = rows + (size_t)(tA + r) * G.ld;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int c = cb + l8 + 8 * v;
+          if (c <= i) dst[c] -= acc[r][v];
+        }
+      }
+    }
+    __syncthreads();
+    push_diag(s);
+    cl.sync();                                        // next block in place; panel reads done
+  }
+  for (int t = warp; t < nown; t += nw) {
+    const int i = me + t * C;
+    for (int c = lane; c <= i; c += 32) M[(size_t)i * d + c] = rows[(size_t)t * G.ld + c];
+  }
+}
+
+// CTAs per cluster for the one-cluster factor of order d (0: does not fit).
+static int chol_cluster_size(tucker_handle* h, int d) {
+  if (h->chol_cluster < 0) {
+    h->chol_cluster = 0;
+    const void* kern = (const void*)k_chol32_cluster;
+    for (int C : {16, 8}) {
+      if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                       cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      const size_t smem = chol_cl_geom(512, C).smem;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(C);
+      cfg.blockDim = dim3(CHOL_CL_THREADS);
+      cfg.dynamicSmemBytes = smem;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) {
+        h->chol_cluster = C;
+        break;
+      }
+      cudaGetLastError();
+    }
+  }
+  const int C = h->chol_cluster;
+  if (C == 0 || d > CHOL_CL_MAX_D || chol_cl_geom(d, C).smem > CHOL_CL_SMEM_MAX) return 0;
+  return C;
+}
+
+static tucker_status cholesky32_cluster(tucker_handle* h, float* M, int d, int C) {
+  const void* kern = (const void*)k_chol32_cluster;
+  const size_t smem = chol_cl_geom(d, C).smem;
+  TK_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(CHOL_CL_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = h->stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  TK_COUNT(h);
+  TK_CUDA(h, cudaLaunchKernelEx(&cfg, k_chol32_cluster, M, d, h->d_status));
+  return TUCKER_OK;
+}
+
+tucker_status cholesky32(tucker_handle* h, float* M, int d) {
+  const int C = chol_cluster_size(h, d);
+  if (C > 0) return cholesky32_cluster(h, M, d, C);
+  return cholesky_t<float>(h, M, d);
+}
 
 // ------------------------------------------------------------ triangular solves
 // Inverses of the SB x SB diagonal blocks of L (one CTA per block, thread j

@@ -234,6 +234,36 @@ def test_adjoint_matches_oracle_and_fd(handle, reg):
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
 
 
+@pytest.mark.parametrize("dims,ranks,dtype", [
+    ((300,), (7,), np.float64),                           # order 1: dA = w (al v - be g)
+    ((41, 37), (5, 3), np.float32),                       # order 2, R_1 > R_2
+    ((23, 19, 17, 15), (2, 3, 1, 4), np.float64),         # order 4, a rank-1 mode
+    ((9, 8, 7, 6, 5), (3, 2, 2, 3, 2), np.float64),       # order 5
+    ((33, 29, 31), (1, 6, 5), np.float32),                # R_1 = 1: T1 is all of dk
+])
+def test_adjoint_orders_and_ranks(handle, dims, ranks, dtype):
+    X, F = _ragged_problem(dims, ranks, dtype, 11)
+    d = int(np.prod(ranks))
+    levs = [CU.leverage_scores(np.asarray(A, dtype=np.float64))[0] for A in F]
+    smp = T.tucker_sample_rows(handle, dims, ranks, [dev(l) for l in levs], 2000, 8, 0)
+    Xd, Fd = dev(X), [dev(a) for a in F]
+    g, st = T.tucker_core_update_sketched(handle, Xd, Fd, 0.05, 0, 0, 0, "exact", "fp64",
+                                          fixed=smp, stats=True)
+    gbar = np.random.default_rng(4).standard_normal(d)
+    dA, dx = T.tucker_core_solve_adjoint(handle, Xd, Fd, 0.05, "exact", "fp64", smp,
+                                         st["solve_id"], g, dev(gbar))
+    keys = host_keys(smp.keys, smp.n_unique)
+    cnt = smp.counts[:smp.n_unique].cpu().numpy().astype(np.float64)
+    wts = S.sample_weights(cnt, smp.prob[:smp.n_unique].cpu().numpy(), smp.n_draws)
+    Fo = [np.asarray(a, dtype=np.float64) for a in F]
+    x = CU.gather_dense(np.asarray(X, dtype=np.float64), keys, dims)
+    rdA, rdx = ADJ.backward(Fo, dims, keys, wts, x, 0.05, np.ones(d), gbar)
+    for a, b in zip(dA, rdA):
+        assert a.shape == b.shape
+        assert rel_err(a.cpu().numpy(), b) <= 1e-9
+    assert rel_err(dx.cpu().numpy(), rdx) <= 1e-9
+
+
 def test_autograd_function(handle):
     from paper_2107_10654_gb300 import SketchedCoreSolve
     X, F = _ragged_problem((20, 18, 16), (2, 3, 2), np.float64, 6)
