@@ -325,11 +325,11 @@ tucker_status cholesky(tucker_handle* h, double* M, int d) { return cholesky_t<d
 // c, c + C, c + 2C, ...  Data moves between CTAs only by stores into the
 // receivers' shared memory (a remote store does not wait for a round trip),
 // ordered by cluster barriers.  Step k (columns k0 .. k0 + 31):
-//   1. warp 0 factors the 32 x 32 diagonal block in registers (lane i holds
-//      row i; each pivot's scaled column goes through a shared-memory buffer
-//      and a release flag), and the other warps run the same pivots on this
-//      CTA's rows below the block as soon as each column is published, giving
-//      the panel rows L_ik = A_ik L_kk^-T;
+//   1. warp 0 factors the 32 x 32 diagonal block in registers, four pivots per
+//      round (lane i holds row i; every lane factors the round's 4 x 4 block,
+//      then the round's columns go through shared memory with a release flag),
+//      and the other warps apply each published round to this CTA's rows below
+//      the block, giving the panel rows L_ik = A_ik L_kk^-T;
 //   2. every CTA stores its panel rows into every CTA's panel buffer; cluster
 //      barrier;
 //   3. each CTA updates its own rows' trailing entries A_ic -= L_i . L_c
@@ -354,8 +354,19 @@ __host__ __device__ inline ClGeom chol_cl_geom(int d, int C) {
   g.nr = (d + C - 1) / C;
   g.ld = 4 * (((d + 3) / 4) | 1);
   g.smem = sizeof(float) * ((size_t)g.nr * g.ld + (size_t)d * CLPS + (size_t)CLB * CLPS +
-                            (size_t)CLB * CLB + CLB);
+                            (size_t)CLB * CLB + (CLB / 4) * 12);
   return g;
+}
+
+// 1/sqrt(p) by the SFU's approximate reciprocal square root (flushes subnormals,
+// so pivots below the smallest normal float are rejected first).
+__device__ __forceinline__ float rsqrt_approx(float p) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(p));
+  return y;
+}
+__device__ __forceinline__ bool pivot_ok32(float p) {
+  return p >= 1.17549435e-38f && p <= 3.402823466e38f;
 }
 
 __device__ __forceinline__ void st_release_cta(int* p, int v) {
@@ -377,8 +388,8 @@ __global__ void __launch_bounds__(CHOL_CL_THREADS, 1) k_chol32_cluster(float* M,
   float* rows = cls;                                  // own row t = global row me + t C
   float* Pb = rows + (size_t)G.nr * G.ld;             // panel row c at (c - s) * CLPS
   float* Db = Pb + (size_t)d * CLPS;                  // diagonal block row i at i * CLPS
-  float* colL = Db + CLB * CLPS;                      // column j of L_kk at j * CLB
-  float* yv = colL + CLB * CLB;                       // the pivots' 1 / sqrt(p_j)
+  float4* colb = reinterpret_cast<float4*>(Db + CLB * CLPS);  // round r: the rows' 4 L entries
+  float* rbuf = reinterpret_cast<float*>(colb + (CLB / 4) * CLB);  // round r: its 4 x 4 block
   __shared__ int flag, bad_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int nown = d > me ? (d - me + C - 1) / C : 0;
@@ -408,31 +419,56 @@ __global__ void __launch_bounds__(CHOL_CL_THREADS, 1) k_chol32_cluster(float* M,
     const int t0 = s > me ? (s - me + C - 1) / C : 0;   // first own row below the block
     const int np = max(0, nown - t0);
     if (warp == 0) {
-      // the diagonal block (identity past nb)
+      // the diagonal block (identity past nb), four pivots per round: every lane
+      // factors the round's 4 x 4 block (broadcast by shuffles) and forward-
+      // substitutes its row, then the rank-4 update of the later columns
       float a[CLB];
 #pragma unroll
       for (int j = 0; j < CLB; ++j)
         a[j] = (lane < nb && j <= lane) ? Db[lane * CLPS + j] : (lane == j ? 1.f : 0.f);
       bool bad = false;
 #pragma unroll
-      for (int j = 0; j < CLB; ++j) {
-        const float pv = __shfl_sync(0xffffffffu, a[j], j);
-        bad |= !(pv >= 1.17549435e-38f && pv <= 3.402823466e38f);   // normal and finite
-        float y;
-        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(pv));
-        const float la = lane >= j ? a[j] * y : 0.f;                // l_ij, i = lane
-        a[j] = la;
-        colL[j * CLB + lane] = la;
-        if (lane == 0) yv[j] = y;
+      for (int r = 0; r < CLB / 4; ++r) {
+        const int jb = 4 * r;
+        const float d00 = __shfl_sync(~0u, a[jb], jb), d10 = __shfl_sync(~0u, a[jb], jb + 1),
+                    d11 = __shfl_sync(~0u, a[jb + 1], jb + 1), d20 = __shfl_sync(~0u, a[jb], jb + 2),
+                    d21 = __shfl_sync(~0u, a[jb + 1], jb + 2), d22 = __shfl_sync(~0u, a[jb + 2], jb + 2),
+                    d30 = __shfl_sync(~0u, a[jb], jb + 3), d31 = __shfl_sync(~0u, a[jb + 1], jb + 3),
+                    d32 = __shfl_sync(~0u, a[jb + 2], jb + 3), d33 = __shfl_sync(~0u, a[jb + 3], jb + 3);
+        bad |= !pivot_ok32(d00);
+        const float y0 = rsqrt_approx(d00);
+        const float l10 = d10 * y0, l20 = d20 * y0, l30 = d30 * y0;
+        const float e11 = fmaf(-l10, l10, d11);
+        bad |= !pivot_ok32(e11);
+        const float y1 = rsqrt_approx(e11);
+        const float l21 = fmaf(-l20, l10, d21) * y1, l31 = fmaf(-l30, l10, d31) * y1;
+        const float e22 = fmaf(-l21, l21, fmaf(-l20, l20, d22));
+        bad |= !pivot_ok32(e22);
+        const float y2 = rsqrt_approx(e22);
+        const float l32 = fmaf(-l31, l21, fmaf(-l30, l20, d32)) * y2;
+        const float e33 = fmaf(-l32, l32, fmaf(-l31, l31, fmaf(-l30, l30, d33)));
+        bad |= !pivot_ok32(e33);
+        const float y3 = rsqrt_approx(e33);
+        // row lane of L in columns jb .. jb + 3 (zero above the diagonal)
+        const float x0 = lane >= jb ? a[jb] * y0 : 0.f;
+        const float x1 = lane >= jb + 1 ? fmaf(-x0, l10, a[jb + 1]) * y1 : 0.f;
+        const float x2 = lane >= jb + 2 ? fmaf(-x1, l21, fmaf(-x0, l20, a[jb + 2])) * y2 : 0.f;
+        const float x3 =
+            lane >= jb + 3 ? fmaf(-x2, l32, fmaf(-x1, l31, fmaf(-x0, l30, a[jb + 3]))) * y3 : 0.f;
+        a[jb] = x0; a[jb + 1] = x1; a[jb + 2] = x2; a[jb + 3] = x3;
+        float4* cb = colb + r * CLB;
+        cb[lane] = make_float4(x0, x1, x2, x3);
+        if (lane == 0) {
+          float* rb = rbuf + r * 12;
+          rb[0] = y0; rb[1] = y1; rb[2] = y2; rb[3] = y3;
+          rb[4] = l10; rb[5] = l20; rb[6] = l21; rb[7] = l30; rb[8] = l31; rb[9] = l32;
+        }
         __syncwarp();
-        if (lane == 0) st_release_cta(&flag, step * CLB + j + 1);
+        if (lane == 0) st_release_cta(&flag, step * (CLB / 4) + r + 1);
 #pragma unroll
-        for (int u = (j + 1) / 4; u < CLB / 4; ++u) {
-          const float4 v = *reinterpret_cast<const float4*>(colL + j * CLB + 4 * u);
-          const float lc[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-          for (int w = 0; w < 4; ++w)
-            if (4 * u + w > j) a[4 * u + w] = fmaf(-la, lc[w], a[4 * u + w]);
+        for (int c = jb + 4; c < CLB; ++c) {
+          const float4 lc = cb[c];
+          a[c] = fmaf(-x3, lc.w, fmaf(-x2, lc.z, fmaf(-x1, lc.y, fmaf(-x0, lc.x, a[c]))));
         }
       }
       if (lane == 0 && bad) bad_s = 1;
@@ -443,7 +479,7 @@ __global__ void __launch_bounds__(CHOL_CL_THREADS, 1) k_chol32_cluster(float* M,
           if (j <= lane) dr[j] = a[j];
       }
     } else {
-      // own rows below the block (lane = row), one pivot behind the published column
+      // own rows below the block (lane = row), each round as soon as it is published
       const int nchb = (np + 31) >> 5;
       for (int ch = warp - 1; ch < nchb; ch += nw - 1) {
         const int q = ch * 32 + lane;
@@ -457,19 +493,25 @@ __global__ void __launch_bounds__(CHOL_CL_THREADS, 1) k_chol32_cluster(float* M,
           p[4 * u] = v.x; p[4 * u + 1] = v.y; p[4 * u + 2] = v.z; p[4 * u + 3] = v.w;
         }
 #pragma unroll
-        for (int j = 0; j < CLB; ++j) {
+        for (int r = 0; r < CLB / 4; ++r) {
+          const int jb = 4 * r;
           // warp 0 never waits, so this wait ends; the limit only guards against a bug
-          for (int spins = 0; ld_acquire_cta(&flag) <= step * CLB + j; )
+          for (int spins = 0; ld_acquire_cta(&flag) <= step * (CLB / 4) + r; )
             if (++spins > (1 << 24)) { set_status(status, DEV_INTERNAL); break; }
-          const float lp = p[j] * yv[j];
-          p[j] = lp;
+          const float* rb = rbuf + r * 12;
+          const float4 yy = *reinterpret_cast<const float4*>(rb);       // y0 .. y3
+          const float4 la = *reinterpret_cast<const float4*>(rb + 4);   // l10 l20 l21 l30
+          const float2 lb = *reinterpret_cast<const float2*>(rb + 8);   // l31 l32
+          const float x0 = p[jb] * yy.x;
+          const float x1 = fmaf(-x0, la.x, p[jb + 1]) * yy.y;
+          const float x2 = fmaf(-x1, la.z, fmaf(-x0, la.y, p[jb + 2])) * yy.z;
+          const float x3 = fmaf(-x2, lb.y, fmaf(-x1, lb.x, fmaf(-x0, la.w, p[jb + 3]))) * yy.w;
+          p[jb] = x0; p[jb + 1] = x1; p[jb + 2] = x2; p[jb + 3] = x3;
+          const float4* cb = colb + r * CLB;
 #pragma unroll
-          for (int u = (j + 1) / 4; u < CLB / 4; ++u) {
-            const float4 v = *reinterpret_cast<const float4*>(colL + j * CLB + 4 * u);
-            const float lc[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int w = 0; w < 4; ++w)
-              if (4 * u + w > j) p[4 * u + w] = fmaf(-lp, lc[w], p[4 * u + w]);
+          for (int c = jb + 4; c < CLB; ++c) {
+            const float4 lc = cb[c];
+            p[c] = fmaf(-x3, lc.w, fmaf(-x2, lc.z, fmaf(-x1, lc.y, fmaf(-x0, lc.x, p[c]))));
           }
         }
         if (has) {

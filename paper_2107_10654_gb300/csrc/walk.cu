@@ -264,6 +264,59 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy(WalkArgs a) {
   for (int e = lane; e < L1; e += 32) out[e] = wst[a.lofs[1] + e];
 }
 
+// The same piece partials with the W_1 entries spread over the lanes (orders
+// 2 .. 4 with lsz[1] <= 32 KE): lane l owns the entries e = l + 32 k and adds
+// c_u * prod_{n >= 2} A^(n)[i_n(u)][r_n(e)] for every row of the piece, so the
+// rows carry no dependence on one another and the factor loads of successive
+// rows overlap (the level fold above waits on each row's loads in turn).
+template <int N, int KE>
+__global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes(WalkArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * WK_WARPS + warp;
+  if (p >= *a.npieces) return;                              // warp-uniform
+  const int L1 = a.lsz[1];
+  const int u0 = a.p_u0[p], u1 = a.p_u1[p];
+  int col[KE][N - 1];                                       // r_n(e), n = 2 .. N
+  double acc[KE];
+#pragma unroll
+  for (int k = 0; k < KE; ++k) {
+    acc[k] = 0.0;
+    const int e = lane + 32 * k;
+#pragma unroll
+    for (int n = 1; n < N; ++n) col[k][n - 1] = e < L1 ? (e / a.lsz[n + 1]) % a.R[n] : 0;
+  }
+  for (int base = u0; base < u1; base += 32) {
+    const int cnt = min(32, u1 - base);
+    uint32_t mine[N];
+    double cm = 0.0;
+#pragma unroll
+    for (int n = 1; n < N; ++n) mine[n] = lane < cnt ? __ldg(a.idx[n] + base + lane) : 0u;
+    if (lane < cnt) cm = a.coef * a.ca[base + lane] * (a.cb ? a.cb[base + lane] : 1.0);
+    constexpr int UNROLL = KE >= 8 ? 1 : 4;                 // rows in flight, within the registers
+#pragma unroll UNROLL
+    for (int j = 0; j < cnt; ++j) {
+      const double c = __shfl_sync(0xffffffffu, cm, j);
+      const double* row[N];
+#pragma unroll
+      for (int n = 1; n < N; ++n)
+        row[n] = a.A[n] + (size_t)__shfl_sync(0xffffffffu, mine[n], j) * a.R[n];
+#pragma unroll
+      for (int k = 0; k < KE; ++k) {
+        double t = c;
+#pragma unroll
+        for (int n = N - 1; n >= 2; --n) t *= __ldg(row[n] + col[k][n - 1]);
+        acc[k] = fma(t, __ldg(row[1] + col[k][0]), acc[k]);
+      }
+    }
+  }
+  double* out = a.Wp + (size_t)p * L1;
+#pragma unroll
+  for (int k = 0; k < KE; ++k) {
+    const int e = lane + 32 * k;
+    if (e < L1) out[e] = acc[k];
+  }
+}
+
 // W1[i1][j] = sum of the piece partials of segment i1 (fixed order); 0 if empty.
 __global__ void k_walk_reduce(WalkArgs a) {
   const int L1 = a.lsz[1];
@@ -457,6 +510,26 @@ static WalkKernel walk_axpy_kernel(int N) {
   }
 }
 
+// The lane-parallel axpy for orders 2 .. 4 and lsz[1] <= 512 (else nullptr).
+template <int N>
+static WalkKernel axpy_lanes_by_width(int L1) {
+  if (L1 <= 32) return k_walk_axpy_lanes<N, 1>;
+  if (L1 <= 64) return k_walk_axpy_lanes<N, 2>;
+  if (L1 <= 128) return k_walk_axpy_lanes<N, 4>;
+  if (L1 <= 256) return k_walk_axpy_lanes<N, 8>;
+  if (L1 <= 512) return k_walk_axpy_lanes<N, 16>;
+  return nullptr;
+}
+
+static WalkKernel walk_axpy_lanes_kernel(int N, int L1) {
+  switch (N) {
+    case 2: return axpy_lanes_by_width<2>(L1);
+    case 3: return axpy_lanes_by_width<3>(L1);
+    case 4: return axpy_lanes_by_width<4>(L1);
+    default: return nullptr;
+  }
+}
+
 // One warp per piece: ceil(maxP / WK_WARPS) CTAs; warps past the piece count exit.
 static tucker_status launch_by_order(tucker_handle* h, WalkKernel k, int64_t maxP, size_t smem,
                                      const WalkArgs& a) {
@@ -521,8 +594,15 @@ tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, const Wal
   walk_carve(g, wb.p, &w);
   WalkArgs a = walk_args(s, g, w);
   a.ca = ca; a.cb = cb; a.coef = coef;
-  const size_t smem = (size_t)WK_WARPS * a.lstore * 8;
-  TK_TRY(launch_by_order(h, walk_axpy_kernel(s.N), g.maxP, smem, a));
+  WalkKernel lanes = walk_axpy_lanes_kernel(s.N, a.lsz[1]);
+  if (lanes) {
+    TK_COUNT(h);
+    lanes<<<(int)((g.maxP + WK_WARPS - 1) / WK_WARPS), WK_WARPS * 32, 0, h->stream>>>(a);
+    TK_LAUNCH(h);
+  } else {
+    const size_t smem = (size_t)WK_WARPS * a.lstore * 8;
+    TK_TRY(launch_by_order(h, walk_axpy_kernel(s.N), g.maxP, smem, a));
+  }
   TK_COUNT(h);
   k_walk_reduce<<<grid_for(h, I1 * a.lsz[1], 256), 256, 0, h->stream>>>(a);
   TK_LAUNCH(h);
