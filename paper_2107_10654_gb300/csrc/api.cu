@@ -47,7 +47,7 @@ tucker_status launch_kron_axpy(tucker_handle* h, const RowSet& s, const double* 
 tucker_status launch_kron_dot(tucker_handle* h, const RowSet& s, const double* g1,
                               const double* g2, double* z1, double* z2);
 tucker_status cholesky(tucker_handle* h, double* M, int d);
-tucker_status cholesky32(tucker_handle* h, float* M, int d);
+tucker_status cholesky32(tucker_handle* h, float* M, int d, float* X, float* XC, int* inv_done);
 tucker_status chol_prepare(tucker_handle* h, const double* L, int d, double* LT, double* Linv);
 tucker_status chol_prepare32(tucker_handle* h, const float* L, int d, float* LT, float* Linv);
 tucker_status chol_solve2(tucker_handle* h, const double* L, const double* LT, const double* Linv,
@@ -369,8 +369,13 @@ static tucker_status factorize(tucker_handle* h, double* L, int d, int prec) {
   if (c.mixed) {
     TK_TRY(launch_to_f32(h, L, (size_t)d * d, c.L32));
     ev_record(h, h->timing, 8);
-    TK_TRY(cholesky32(h, c.L32, d));
+    int inv_done = 0;
+    TK_TRY(cholesky32(h, c.L32, d, c.X32, c.XC32, &inv_done));
     ev_record(h, h->timing, 9);
+    if (inv_done) {                     // the factor's launch also formed X = L^-1
+      c.inv32 = 1;
+      return TUCKER_OK;
+    }
     TK_TRY(chol_prepare32(h, c.L32, d, c.LT32, c.Linv32));
     c.prep32 = 1;
     if (c.X32) {

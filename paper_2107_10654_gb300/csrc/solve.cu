@@ -336,25 +336,34 @@ tucker_status cholesky(tucker_handle* h, double* M, int d) { return cholesky_t<d
 //      (4 rows x 4 columns per thread, 8 threads per 32-column chunk), then
 //      stores its rows of the next diagonal block into every CTA; cluster
 //      barrier.
+// With X requested the kernel also forms X = L^-1 (the mixed solver applies
+// (L L^T)^-1 as X^T X): CTA c owns columns c, c + C, ... of B = I, and at step k
+// X_k = L_kk^-1 B_k (block row k, the same round-by-round substitution as the
+// panel rows, run by the same warps) and then B_i -= L_ik X_k for i below the
+// block, with the panel rows L_ik already in every CTA's panel buffer: the
+// inverse needs no data beyond what the factorisation moves.
 // Every CTA factors the same block with the same instructions, so all agree
 // on a failed pivot and leave at the same step (no remote store follows).
 constexpr int CLB = 32;
 constexpr int CLPS = 36;                 // row stride of the panel and block buffers (floats)
 constexpr int CHOL_CL_THREADS = 256;
-constexpr size_t CHOL_CL_SMEM_MAX = 227 * 1024;
+constexpr size_t CHOL_CL_SMEM_MAX = 227 * 1024;   // the opt-in limit per CTA
 
 struct ClGeom {
-  int nr;      // own rows per CTA (at most)
+  int nr;      // own rows (and own columns of X) per CTA, at most
   int ld;      // own-row stride in floats: 4 x odd, so 8 lanes' 16-byte row loads hit distinct banks
+  int xld;     // own-column stride of X in floats: odd, so 32 lanes' column reads hit distinct banks
   size_t smem;
 };
 
-__host__ __device__ inline ClGeom chol_cl_geom(int d, int C) {
+__host__ __device__ inline ClGeom chol_cl_geom(int d, int C, bool inv) {
   ClGeom g;
   g.nr = (d + C - 1) / C;
   g.ld = 4 * (((d + 3) / 4) | 1);
+  g.xld = d | 1;
   g.smem = sizeof(float) * ((size_t)g.nr * g.ld + (size_t)d * CLPS + (size_t)CLB * CLPS +
-                            (size_t)CLB * CLB + (CLB / 4) * 12);
+                            (size_t)CLB * CLB + (CLB / 4) * 12 +
+                            (inv ? (size_t)g.nr * CLB + (size_t)g.nr * g.xld : 0));
   return g;
 }
 
@@ -380,16 +389,20 @@ __device__ __forceinline__ int ld_acquire_cta(const int* p) {
   return v;
 }
 
-__global__ void __launch_bounds__(CHOL_CL_THREADS, 1) k_chol32_cluster(float* M, int d, int* status) {
+__global__ void __launch_bounds__(CHOL_CL_THREADS, 1) k_chol32_cluster(float* M, int d, int* status,
+                                                                     float* X, float* XC) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks(), me = (int)cl.block_rank();
-  const ClGeom G = chol_cl_geom(d, C);
+  const bool inv = X != nullptr;
+  const ClGeom G = chol_cl_geom(d, C, inv);
   extern __shared__ __align__(16) float cls[];
   float* rows = cls;                                  // own row t = global row me + t C
   float* Pb = rows + (size_t)G.nr * G.ld;             // panel row c at (c - s) * CLPS
   float* Db = Pb + (size_t)d * CLPS;                  // diagonal block row i at i * CLPS
   float4* colb = reinterpret_cast<float4*>(Db + CLB * CLPS);  // round r: the rows' 4 L entries
   float* rbuf = reinterpret_cast<float*>(colb + (CLB / 4) * CLB);  // round r: its 4 x 4 block
+  float* Xk = rbuf + (CLB / 4) * 12;                  // own column tc of X_k at tc * CLB
+  float* Xc = Xk + (size_t)G.nr * CLB;                // own column tc (global me + tc C) of B, then X
   __shared__ int flag, bad_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int nown = d > me ? (d - me + C - 1) / C : 0;
@@ -398,6 +411,11 @@ __global__ void __launch_bounds__(CHOL_CL_THREADS, 1) k_chol32_cluster(float* M,
     for (int c = lane; c <= i; c += 32) rows[(size_t)t * G.ld + c] = M[(size_t)i * d + c];
   }
   if (tid == 0) { flag = 0; bad_s = 0; }
+  if (inv)
+    for (int e = tid; e < nown * G.xld; e += blockDim.x) {
+      const int tc = e / G.xld, i = e - tc * G.xld;
+      Xc[e] = i == me + tc * C ? 1.f : 0.f;
+    }
   __syncthreads();
   // this CTA's rows of the diagonal block at k0, to every CTA's Db
   auto push_diag = [&](int k0) {
@@ -479,18 +497,28 @@ __global__ void __launch_bounds__(CHOL_CL_THREADS, 1) k_chol32_cluster(float* M,
           if (j <= lane) dr[j] = a[j];
       }
     } else {
-      // own rows below the block (lane = row), each round as soon as it is published
-      const int nchb = (np + 31) >> 5;
+      // own rows below the block and (with X) own columns j < s of B's block row k,
+      // one per lane, each round applied as soon as it is published
+      const int ncolk = inv && s > me ? (s - me + C - 1) / C : 0;
+      const int nitem = np + ncolk;
+      const int nchb = (nitem + 31) >> 5;
       for (int ch = warp - 1; ch < nchb; ch += nw - 1) {
         const int q = ch * 32 + lane;
         const bool has = q < np;
+        const bool hasx = !has && q < nitem;
+        const int tc = hasx ? q - np : 0;
         float* prow = rows + (size_t)(t0 + (has ? q : 0)) * G.ld + k0;
+        float* xcol = Xc + (size_t)tc * G.xld + k0;
         float p[CLB];
 #pragma unroll
         for (int u = 0; u < CLB / 4; ++u) {
           const float4 v = has ? *reinterpret_cast<const float4*>(prow + 4 * u)
                                : make_float4(0.f, 0.f, 0.f, 0.f);
           p[4 * u] = v.x; p[4 * u + 1] = v.y; p[4 * u + 2] = v.z; p[4 * u + 3] = v.w;
+        }
+        if (hasx) {
+#pragma unroll
+          for (int r = 0; r < CLB; ++r) p[r] = r < nb ? xcol[r] : 0.f;
         }
 #pragma unroll
         for (int r = 0; r < CLB / 4; ++r) {
@@ -518,6 +546,15 @@ __global__ void __launch_bounds__(CHOL_CL_THREADS, 1) k_chol32_cluster(float* M,
 #pragma unroll
           for (int u = 0; u < CLB / 4; ++u)
             *reinterpret_cast<float4*>(prow + 4 * u) =
+                make_float4(p[4 * u], p[4 * u + 1], p[4 * u + 2], p[4 * u + 3]);
+        }
+        if (hasx) {                                   // X_k column: into B and the staging copy
+#pragma unroll
+          for (int r = 0; r < CLB; ++r)
+            if (r < nb) xcol[r] = p[r];
+#pragma unroll
+          for (int u = 0; u < CLB / 4; ++u)
+            *reinterpret_cast<float4*>(Xk + tc * CLB + 4 * u) =
                 make_float4(p[4 * u], p[4 * u + 1], p[4 * u + 2], p[4 * u + 3]);
         }
       }
@@ -581,6 +618,46 @@ __global__ void __launch_bounds__(CHOL_CL_THREADS, 1) k_chol32_cluster(float* M,
         }
       }
     }
+    if (inv) {
+      // B_i -= L_ik X_k for the own columns j < s and the rows i >= s:
+      // item = (32 rows, 4 columns), thread rows i = s + 32 rc + l8 + 8 v
+      const int ncolk = s > me ? (s - me + C - 1) / C : 0;
+      const int nrc = (npan + 31) / 32, ncg = (ncolk + 3) / 4;
+      for (int it = tid >> 3; it < nrc * ncg; it += blockDim.x >> 3) {
+        const int rc = it / ncg, cg4 = it - rc * ncg;
+        float acc[4][4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[v][w] = 0.f;
+#pragma unroll 2
+        for (int q4 = 0; q4 < CLB / 4; ++q4) {
+          float4 b[4], xk[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            b[v] = *reinterpret_cast<const float4*>(Pb + (size_t)(32 * rc + l8 + 8 * v) * CLPS + 4 * q4);
+#pragma unroll
+          for (int w = 0; w < 4; ++w)
+            xk[w] = *reinterpret_cast<const float4*>(Xk + (4 * cg4 + w) * CLB + 4 * q4);
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+              acc[v][w] = fmaf(b[v].x, xk[w].x, fmaf(b[v].y, xk[w].y,
+                          fmaf(b[v].z, xk[w].z, fmaf(b[v].w, xk[w].w, acc[v][w]))));
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int tc = 4 * cg4 + w;
+          if (tc >= ncolk) break;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int i = s + 32 * rc + l8 + 8 * v;
+            if (i < d) Xc[(size_t)tc * G.xld + i] -= acc[v][w];
+          }
+        }
+      }
+    }
     __syncthreads();
     push_diag(s);
     cl.sync();                                        // next block in place; panel reads done
@@ -589,52 +666,70 @@ __global__ void __launch_bounds__(CHOL_CL_THREADS, 1) k_chol32_cluster(float* M,
     const int i = me + t * C;
     for (int c = lane; c <= i; c += 32) M[(size_t)i * d + c] = rows[(size_t)t * G.ld + c];
   }
+  if (inv)                                            // X row-major and column-major (XC = X^T)
+    for (int tc = warp; tc < nown; tc += nw) {
+      const int j = me + tc * C;
+      for (int i = lane; i < d; i += 32) {
+        const float v = Xc[(size_t)tc * G.xld + i];
+        XC[(size_t)j * d + i] = v;
+        X[(size_t)i * d + j] = v;
+      }
+    }
 }
 
-// CTAs per cluster for the one-cluster factor of order d (0: does not fit).
-static int chol_cluster_size(tucker_handle* h, int d) {
-  if (h->chol_cluster < 0) {
-    h->chol_cluster = 0;
-    const void* kern = (const void*)k_chol32_cluster;
-    for (int C : {16, 8}) {
-      if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                       cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
-      const size_t smem = chol_cl_geom(512, C).smem;
-      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
-      cudaLaunchConfig_t cfg = {};
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = C;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(C);
-      cfg.blockDim = dim3(CHOL_CL_THREADS);
-      cfg.dynamicSmemBytes = smem;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) {
-        h->chol_cluster = C;
-        break;
-      }
-      cudaGetLastError();
-    }
+// Whether a cluster of C CTAs with smem bytes of shared memory each can be
+// scheduled (the device's own answer; non-portable sizes need an opt-in).
+static bool cluster_fits(int C, size_t smem) {
+  const void* kern = (const void*)k_chol32_cluster;
+  if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                   cudaSuccess) {
+    cudaGetLastError();
+    return false;
   }
-  const int C = h->chol_cluster;
-  if (C == 0 || d > CHOL_CL_MAX_D || chol_cl_geom(d, C).smem > CHOL_CL_SMEM_MAX) return 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(CHOL_CL_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n >= 1;
+}
+
+// Cluster size for the one-cluster factor of order d, with or without the
+// inverse (0: neither 16 nor 8 CTAs can hold it).  Cached per (d, inverse).
+static int chol_cluster_size(tucker_handle* h, int d, bool inv) {
+  if (d > CHOL_CL_MAX_D) return 0;
+  const int key = 2 * d + (inv ? 1 : 0);
+  if (h->chol_cluster_key == key) return h->chol_cluster;
+  int C = 0;
+  for (int c : {16, 8}) {
+    const size_t smem = chol_cl_geom(d, c, inv).smem;
+    if (smem <= CHOL_CL_SMEM_MAX && cluster_fits(c, smem)) { C = c; break; }
+  }
+  h->chol_cluster_key = key;
+  h->chol_cluster = C;
   return C;
 }
 
-static tucker_status cholesky32_cluster(tucker_handle* h, float* M, int d, int C) {
+static tucker_status cholesky32_cluster(tucker_handle* h, float* M, int d, int C, float* X,
+                                        float* XC) {
   const void* kern = (const void*)k_chol32_cluster;
-  const size_t smem = chol_cl_geom(d, C).smem;
+  const size_t smem = chol_cl_geom(d, C, X != nullptr).smem;
   TK_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
@@ -649,13 +744,24 @@ static tucker_status cholesky32_cluster(tucker_handle* h, float* M, int d, int C
   cfg.attrs = at;
   cfg.numAttrs = 1;
   TK_COUNT(h);
-  TK_CUDA(h, cudaLaunchKernelEx(&cfg, k_chol32_cluster, M, d, h->d_status));
+  TK_CUDA(h, cudaLaunchKernelEx(&cfg, k_chol32_cluster, M, d, h->d_status, X, XC));
   return TUCKER_OK;
 }
 
-tucker_status cholesky32(tucker_handle* h, float* M, int d) {
-  const int C = chol_cluster_size(h, d);
-  if (C > 0) return cholesky32_cluster(h, M, d, C);
+// FP32 Cholesky; with X / XC given (d x d each) and d small enough, the
+// explicit inverse comes out of the same launch (*inv_done = 1).
+tucker_status cholesky32(tucker_handle* h, float* M, int d, float* X, float* XC, int* inv_done) {
+  *inv_done = 0;
+  if (X && XC) {
+    const int C = chol_cluster_size(h, d, true);
+    if (C > 0) {
+      TK_TRY(cholesky32_cluster(h, M, d, C, X, XC));
+      *inv_done = 1;
+      return TUCKER_OK;
+    }
+  }
+  const int C = chol_cluster_size(h, d, false);
+  if (C > 0) return cholesky32_cluster(h, M, d, C, nullptr, nullptr);
   return cholesky_t<float>(h, M, d);
 }
 
