@@ -81,6 +81,11 @@ class Handle:
         _check(self.h, lib.tucker_set_sync(self.h, int(synchronous)))
         self.set_solver(solver)
 
+    def set_sync(self, synchronous: bool):
+        """Synchronous calls wait for their kernels and report device errors at once;
+        asynchronous calls return after enqueueing (errors surface at sync())."""
+        _check(self.h, L.load().tucker_set_sync(self.h, int(synchronous)))
+
     def set_solver(self, solver: str):
         """Ridge solver of later updates: "fp64" (FP64 Cholesky) or "mixed"
         (FP32 Cholesky preconditioning an FP64 iterative refinement)."""
