@@ -251,6 +251,8 @@ static double ev_ms(tucker_handle* h, int a, int b) {
 
 // --------------------------------------------------------- sketch pipeline
 
+constexpr int kMaxRefine = 12;                 // refinement iterations, at most
+
 struct SketchBufs {
   double* lev[TUCKER_MAX_ORDER];
   uint64_t* cdf[TUCKER_MAX_ORDER];
@@ -267,6 +269,7 @@ struct SketchBufs {
   double *w, *x, *p, *z;
   float* sw32;
   double *D, *h, *g, *r, *axpy_part;
+  double* rstat;                      // refinement: ||c_k||^2, ||g_k||^2 per iteration
   double* ptab;                       // per-mode q/Q and Q/q tables of the gather
   WalkBuf walk;
   double* A64[TUCKER_MAX_ORDER];      // FP64 copies of FP32 factors (walk kernels)
@@ -306,6 +309,7 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
   b->h = ar.get<double>(F.d);
   b->g = ar.get<double>(F.d);
   b->r = ar.get<double>(F.d);
+  b->rstat = ar.get<double>(2 * kMaxRefine);
   b->axpy_split = axpy_splits(h, F.d, m);
   b->axpy_part = ar.get<double>((size_t)b->axpy_split * F.d);
   b->walk.p = ar.get<double>(walk_scratch_doubles(F.I[0], F.d, F.R[0], m, h->num_sms));
@@ -445,10 +449,14 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
   if (explicit_m && !h->chol.mixed) return TUCKER_OK;
   // stop when the remaining relative error, estimated from the last correction
   // c_k and the contraction rho ~ c_k / c_{k-1}, is below target (c_0 = 1: the
-  // first solve), or when the corrections stop shrinking (rounding level)
+  // first solve), or when the corrections stop shrinking (rounding level).  A
+  // tensor-core Gram (8- or 11-bit operands) always takes two corrections, so
+  // the first two are enqueued back to back and the host waits once for both.
   const double target = explicit_m ? 1e-13 : 1e-8;
   const int max_iters = h->chol.mixed ? 12 : 8;
+  const int batch = (prec == TUCKER_PREC_BF16 || prec == TUCKER_PREC_TF32) ? 2 : 1;
   double prev = 1.0;
+  int checked = 0;
   for (int it = 0; it < max_iters; ++it) {
     if (explicit_m) {
       TK_TRY(launch_gemv_resid(h, h->chol.L, d, g, rhs, b.r));
@@ -458,16 +466,25 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
                        h->chol.regdiag, g, b.r));
     }
     TK_TRY(chol_solve(h, d, b.r, b.r, prec));
-    double hv[2] = {0, 0};
-    TK_TRY(launch_refine_update(h, g, b.r, d, b.z));
-    TK_CUDA(h, cudaMemcpyAsync(hv, b.z, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    TK_TRY(launch_refine_update(h, g, b.r, d, b.rstat + 2 * it));
+    if (it + 1 < batch) continue;                     // the next correction is certain
+    double hv[2 * kMaxRefine];
+    const int n = it + 1 - checked;
+    TK_CUDA(h, cudaMemcpyAsync(hv, b.rstat + 2 * checked, 2 * n * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream));
     TK_CUDA(h, cudaStreamSynchronize(h->stream));
+    bool stop = false;
+    for (int k = 0; k < n; ++k) {
+      const double rk = hv[2 * k + 1] > 0 ? sqrt(hv[2 * k] / hv[2 * k + 1]) : 0.0;
+      const double rho = fmin(rk / prev, 0.5);
+      stop = stop || rk == 0.0 || rk * rho / (1.0 - rho) < target ||
+             (checked + k > 0 && rk > 0.5 * prev);
+      prev = rk;
+      *rel = rk;
+    }
+    checked = it + 1;
     *iters = it + 1;
-    *rel = hv[1] > 0 ? sqrt(hv[0] / hv[1]) : 0.0;
-    const double rho = fmin(*rel / prev, 0.5);
-    if (*rel == 0.0 || *rel * rho / (1.0 - rho) < target) break;
-    if (it > 0 && *rel > 0.5 * prev) break;
-    prev = *rel;
+    if (stop) break;
   }
   return TUCKER_OK;
 }
