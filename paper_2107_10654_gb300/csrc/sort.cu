@@ -148,123 +148,200 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const uint64_t* in, u
 
 // ------------------------------------------------- small samples: one cluster
 // For n <= CL_MAX keys the whole sort + dedupe runs in one launch of a cluster
-// of CL_CTAS CTAs: each CTA keeps 8192 keys (32 warps x 8 rounds x 32 lanes)
-// in registers, per-CTA digit counts are exchanged through distributed shared
-// memory, and cluster barriers separate the passes (instead of three kernel
-// launches per pass).  The ranking is the same stable match_any scheme as above,
-// with the CTA's keys after those of lower-ranked CTAs.
+// of CL_CTAS CTAs.  The keys stay in the CTAs' shared memory between passes
+// (CTA c holds sorted positions [c CL_CHUNK, (c + 1) CL_CHUNK)): a pass reads
+// its 8192 keys (32 warps x 8 rounds x 32 lanes) from its own shared memory,
+// ranks them with the same stable match_any scheme as above, and stores each
+// key straight into the shared memory of the CTA that owns its new position.
+// Digits are up to 10 bits (as many passes as the key range needs, all of
+// equal width), per-CTA digit totals are exchanged through distributed shared
+// memory, and cluster barriers separate the passes.
+// Lanes holding the same digit as this lane (invalid lanes carry digit -1):
+// the AND of one ballot per digit bit.  Every lane executes every ballot
+// (dbits is uniform), so the full mask is always valid.
+__device__ __forceinline__ unsigned digit_peers(int dg, int dbits) {
+  const unsigned inv = __ballot_sync(0xffffffffu, dg < 0);
+  unsigned m = ~inv;
+  for (int b = 0; b < dbits; ++b) {
+    const int bit = (dg >> b) & 1;
+    const unsigned bb = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? bb : ~bb;
+  }
+  return dg < 0 ? inv : m;
+}
+
 constexpr int CL_CTAS = 8;
 constexpr int CL_THREADS = 1024;
 constexpr int CL_WARPS = CL_THREADS / 32;
 constexpr int CL_ROUNDS = 8;
 constexpr int CL_CHUNK = CL_THREADS * CL_ROUNDS;            // 8192 keys per CTA
 constexpr int64_t CL_MAX = (int64_t)CL_CTAS * CL_CHUNK;     // 65536
+constexpr int CL_MAX_DBITS = 10;
+
+static int cl_digit_bits(int key_bits) {
+  const int passes = key_bits > 0 ? (key_bits + CL_MAX_DBITS - 1) / CL_MAX_DBITS : 1;
+  const int b = (key_bits + passes - 1) / passes;
+  return b > 0 ? b : 1;
+}
+
+// ints of the per-warp digit table, which afterwards holds the CTA's head positions
+static __host__ __device__ int cl_wofs_ints(int dbits) {
+  const int t = CL_WARPS << dbits;
+  return t > CL_CHUNK ? t : CL_CHUNK;
+}
+
+static size_t cl_smem_bytes(int dbits) {
+  const size_t rx = size_t(1) << dbits;
+  return (size_t)CL_CHUNK * 8 + (size_t)cl_wofs_ints(dbits) * 4 + rx * 4;
+}
 
 __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
-    k_sort_dedupe_cluster(const uint64_t* keys_in, int n, int key_bits, uint64_t* b0,
-                          uint64_t* b1, uint64_t* keys_u, uint32_t* counts_u, int64_t* start,
-                          int* d_n_unique) {
+    k_sort_dedupe_cluster(const uint64_t* keys_in, int n, int key_bits, int dbits,
+                          uint64_t* keys_u, uint32_t* counts_u, int* d_n_unique) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  __shared__ int wofs[CL_WARPS][RX];          // per-warp digit counts, then offsets
-  __shared__ int ctot[RX];                    // this CTA's digit totals (read by the others)
+  extern __shared__ __align__(16) unsigned char csm[];
+  const int RXB = 1 << dbits;
+  uint64_t* kbuf = reinterpret_cast<uint64_t*>(csm);           // this CTA's keys
+  int* wofs = reinterpret_cast<int*>(kbuf + CL_CHUNK);         // [CL_WARPS][RXB] counts, offsets
+  int* ctot = wofs + cl_wofs_ints(dbits);                      // [RXB] this CTA's digit totals
   __shared__ int64_t tmp[32];
-  __shared__ int64_t cta_heads[1];
+  __shared__ int cta_heads[2];                                // heads, first head position
   const int c = (int)cluster.block_rank();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  const int64_t wbase = (int64_t)c * CL_CHUNK + (int64_t)w * (CL_ROUNDS * 32);
+  const int lbase = w * (CL_ROUNDS * 32);
+  const int64_t cbase = (int64_t)c * CL_CHUNK;
   uint64_t k[CL_ROUNDS];
-  const uint64_t* cur = keys_in;
-  uint64_t* nxt = b0;
-  for (int shift = 0; shift < key_bits; shift += 8) {
+  bool valid[CL_ROUNDS];
+#pragma unroll
+  for (int r = 0; r < CL_ROUNDS; ++r) {
+    const int64_t i = cbase + lbase + r * 32 + lane;
+    valid[r] = i < n;
+    k[r] = valid[r] ? keys_in[i] : 0;
+  }
+  const uint64_t dmask = (uint64_t)RXB - 1;
+  for (int shift = 0; shift < key_bits; shift += dbits) {
+    if (shift > 0) {
+#pragma unroll
+      for (int r = 0; r < CL_ROUNDS; ++r) k[r] = kbuf[lbase + r * 32 + lane];
+    }
     int dg[CL_ROUNDS];
 #pragma unroll
-    for (int r = 0; r < CL_ROUNDS; ++r) {
-      const int64_t i = wbase + r * 32 + lane;
-      k[r] = i < n ? cur[i] : 0;
-      dg[r] = i < n ? (int)((k[r] >> shift) & (RX - 1)) : -1;
-    }
-    for (int d = lane; d < RX; d += 32) wofs[w][d] = 0;
-    __syncwarp();
+    for (int r = 0; r < CL_ROUNDS; ++r) dg[r] = valid[r] ? (int)((k[r] >> shift) & dmask) : -1;
+    for (int e = threadIdx.x; e < CL_WARPS * RXB; e += CL_THREADS) wofs[e] = 0;
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < CL_ROUNDS; ++r) {
-      const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
-      if (dg[r] >= 0 && (peers & lt) == 0) wofs[w][dg[r]] += __popc(peers);
+      const unsigned peers = digit_peers(dg[r], dbits);
+      if (dg[r] >= 0 && (peers & lt) == 0) wofs[w * RXB + dg[r]] += __popc(peers);
       __syncwarp();
     }
     __syncthreads();
-    if (threadIdx.x < RX) {                   // per-warp exclusive offsets, CTA totals
+    for (int t = threadIdx.x; t < RXB; t += CL_THREADS) {     // per-warp exclusive offsets
       int run = 0;
       for (int ww = 0; ww < CL_WARPS; ++ww) {
-        const int v = wofs[ww][threadIdx.x];
-        wofs[ww][threadIdx.x] = run;
+        const int v = wofs[ww * RXB + t];
+        wofs[ww * RXB + t] = run;
         run += v;
       }
-      ctot[threadIdx.x] = run;
+      ctot[t] = run;
     }
-    cluster.sync();                           // every CTA's totals are final
+    cluster.sync();                           // every CTA's totals final; every key loaded
     int64_t all_d = 0, before = 0;
-    if (threadIdx.x < RX) {
+    if (threadIdx.x < RXB) {
+      int v[CL_CTAS];
+#pragma unroll
+      for (int cc = 0; cc < CL_CTAS; ++cc) v[cc] = *cluster.map_shared_rank(&ctot[threadIdx.x], cc);
+#pragma unroll
       for (int cc = 0; cc < CL_CTAS; ++cc) {
-        const int v = *cluster.map_shared_rank(&ctot[threadIdx.x], cc);
-        all_d += v;
-        if (cc < c) before += v;
+        all_d += v[cc];
+        if (cc < c) before += v[cc];
       }
     }
     int64_t total;
-    const int64_t dbase = block_exclusive_scan(threadIdx.x < RX ? all_d : 0, tmp, &total);
-    if (threadIdx.x < RX)
-      for (int ww = 0; ww < CL_WARPS; ++ww) wofs[ww][threadIdx.x] += (int)(dbase + before);
+    const int64_t dbase = block_exclusive_scan(threadIdx.x < RXB ? all_d : 0, tmp, &total);
+    if (threadIdx.x < RXB)
+      for (int ww = 0; ww < CL_WARPS; ++ww) wofs[ww * RXB + threadIdx.x] += (int)(dbase + before);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < CL_ROUNDS; ++r) {
-      const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+      const unsigned peers = digit_peers(dg[r], dbits);
       int pos = 0;
-      if (dg[r] >= 0) pos = wofs[w][dg[r]] + __popc(peers & lt);
+      if (dg[r] >= 0) pos = wofs[w * RXB + dg[r]] + __popc(peers & lt);
       __syncwarp();
       if (dg[r] >= 0) {
-        nxt[pos] = k[r];
-        if ((peers & lt) == 0) wofs[w][dg[r]] += __popc(peers);
+        *cluster.map_shared_rank(kbuf + (pos & (CL_CHUNK - 1)), pos / CL_CHUNK) = k[r];
+        if ((peers & lt) == 0) wofs[w * RXB + dg[r]] += __popc(peers);
       }
       __syncwarp();
     }
-    __threadfence();
-    cluster.sync();                           // scattered keys visible; ctot free again
-    cur = nxt;
-    nxt = nxt == b0 ? b1 : b0;
+    cluster.sync();                           // every key in its new place; ctot reads done
   }
-  // run-length encode: thread t owns keys [c * CHUNK + 8 t, +8) of the sorted array
-  const int64_t i0 = (int64_t)c * CL_CHUNK + (int64_t)threadIdx.x * CL_ROUNDS;
+  if (key_bits <= 0) {                        // one possible key: the input order is sorted
+#pragma unroll
+    for (int r = 0; r < CL_ROUNDS; ++r) kbuf[lbase + r * 32 + lane] = k[r];
+    cluster.sync();
+  }
+  // run-length encode: thread t owns sorted positions [cbase + 8 t, +8)
+  const int l0 = threadIdx.x * CL_ROUNDS;
+  uint64_t prevk = 0;
+  if (l0 > 0) prevk = kbuf[l0 - 1];
+  else if (c > 0) prevk = *cluster.map_shared_rank(kbuf + (CL_CHUNK - 1), c - 1);
   bool head[CL_ROUNDS];
+  uint64_t kr[CL_ROUNDS];
   int nh = 0;
 #pragma unroll
   for (int r = 0; r < CL_ROUNDS; ++r) {
-    const int64_t i = i0 + r;
-    head[r] = i < n && (i == 0 || cur[i] != cur[i - 1]);
+    const int64_t i = cbase + l0 + r;
+    kr[r] = kbuf[l0 + r];
+    head[r] = i < n && (i == 0 || kr[r] != (r ? kr[r - 1] : prevk));
     nh += head[r];
   }
   int64_t cnt;
-  int64_t u = block_exclusive_scan(nh, tmp, &cnt);
-  if (threadIdx.x == 0) cta_heads[0] = cnt;
+  const int ul = (int)block_exclusive_scan(nh, tmp, &cnt);     // this thread's first local head
+  int* hpos = wofs;                                            // local head -> sorted position
+  {
+    int q = ul;
+#pragma unroll
+    for (int r = 0; r < CL_ROUNDS; ++r)
+      if (head[r]) hpos[q++] = (int)(cbase + l0 + r);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cta_heads[0] = (int)cnt;
+    cta_heads[1] = cnt > 0 ? hpos[0] : n;
+  }
   cluster.sync();
   int64_t ubase = 0, utot = 0;
-  for (int cc = 0; cc < CL_CTAS; ++cc) {
-    const int64_t v = *cluster.map_shared_rank(&cta_heads[0], cc);
-    if (cc < c) ubase += v;
-    utot += v;
-  }
-  u += ubase;
+  int next_first = n;                                          // first head after this CTA
+  {
+    int hv[CL_CTAS], fv[CL_CTAS];
 #pragma unroll
-  for (int r = 0; r < CL_ROUNDS; ++r)
-    if (head[r]) { keys_u[u] = cur[i0 + r]; start[u] = i0 + r; ++u; }
-  __threadfence();
-  cluster.sync();                             // all starts written (and remote reads done)
-  for (int64_t q = (int64_t)c * CL_THREADS + threadIdx.x; q < utot; q += (int64_t)CL_CTAS * CL_THREADS) {
-    const int64_t e = q + 1 < utot ? start[q + 1] : n;
-    counts_u[q] = (uint32_t)(e - start[q]);
+    for (int cc = 0; cc < CL_CTAS; ++cc) {
+      hv[cc] = *cluster.map_shared_rank(&cta_heads[0], cc);
+      fv[cc] = *cluster.map_shared_rank(&cta_heads[1], cc);
+    }
+#pragma unroll
+    for (int cc = CL_CTAS - 1; cc >= 0; --cc) {
+      if (cc < c) ubase += hv[cc];
+      utot += hv[cc];
+      if (cc > c && hv[cc] > 0) next_first = fv[cc];
+    }
+  }
+  {
+    int q = ul;
+#pragma unroll
+    for (int r = 0; r < CL_ROUNDS; ++r)
+      if (head[r]) {
+        const int e = q + 1 < (int)cnt ? hpos[q + 1] : next_first;
+        keys_u[ubase + q] = kr[r];
+        counts_u[ubase + q] = (uint32_t)(e - (int)(cbase + l0 + r));
+        ++q;
+      }
   }
   if (c == 0 && threadIdx.x == 0) *d_n_unique = (int)utot;
+  cluster.sync();                             // no CTA leaves while another reads its heads
 }
 
 // ------------------------------------------------------------ run-length encode
@@ -331,13 +408,13 @@ tucker_status sort_dedupe(tucker_handle* h, const uint64_t* keys_in, int64_t n, 
   const int nb = ceil_div(n, SORT_TILE);
   const int nt = ceil_div(n, RX_TILE);
   if (n <= CL_MAX) {
-    Arena ca(scratch);
-    uint64_t* c0 = ca.get<uint64_t>(n);
-    uint64_t* c1 = ca.get<uint64_t>(n);
-    int64_t* cst = ca.get<int64_t>(n);
+    const int dbits = cl_digit_bits(key_bits);
+    const size_t smem = cl_smem_bytes(dbits);
+    TK_CUDA(h, cudaFuncSetAttribute((const void*)k_sort_dedupe_cluster,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     TK_COUNT(h);
-    k_sort_dedupe_cluster<<<CL_CTAS, CL_THREADS, 0, h->stream>>>(keys_in, (int)n, key_bits, c0, c1,
-                                                                keys_u, counts_u, cst, d_n_unique);
+    k_sort_dedupe_cluster<<<CL_CTAS, CL_THREADS, smem, h->stream>>>(
+        keys_in, (int)n, key_bits, dbits, keys_u, counts_u, d_n_unique);
     TK_LAUNCH(h);
     return TUCKER_OK;
   }

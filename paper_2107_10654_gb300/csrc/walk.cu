@@ -278,6 +278,7 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes(WalkArgs a) {
   const int u0 = a.p_u0[p], u1 = a.p_u1[p];
   int col[KE][N - 1];                                       // r_n(e), n = 2 .. N
   double acc[KE];
+  const bool shared_last = N >= 3 && 32 % a.R[N - 1] == 0;
 #pragma unroll
   for (int k = 0; k < KE; ++k) {
     acc[k] = 0.0;
@@ -293,19 +294,40 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes(WalkArgs a) {
     for (int n = 1; n < N; ++n) mine[n] = lane < cnt ? __ldg(a.idx[n] + base + lane) : 0u;
     if (lane < cnt) cm = a.coef * a.ca[base + lane] * (a.cb ? a.cb[base + lane] : 1.0);
     constexpr int UNROLL = KE >= 8 ? 1 : 4;                 // rows in flight, within the registers
+    if (shared_last) {
+      // R_N divides 32: every entry of a lane has r_N = lane mod R_N, so c_u a_N
+      // is formed once per row
 #pragma unroll UNROLL
-    for (int j = 0; j < cnt; ++j) {
-      const double c = __shfl_sync(0xffffffffu, cm, j);
-      const double* row[N];
+      for (int j = 0; j < cnt; ++j) {
+        const double c = __shfl_sync(0xffffffffu, cm, j);
+        const double* row[N];
 #pragma unroll
-      for (int n = 1; n < N; ++n)
-        row[n] = a.A[n] + (size_t)__shfl_sync(0xffffffffu, mine[n], j) * a.R[n];
+        for (int n = 1; n < N; ++n)
+          row[n] = a.A[n] + (size_t)__shfl_sync(0xffffffffu, mine[n], j) * a.R[n];
+        const double cl = N >= 3 ? c * __ldg(row[N - 1] + col[0][N - 2]) : c;
 #pragma unroll
-      for (int k = 0; k < KE; ++k) {
-        double t = c;
+        for (int k = 0; k < KE; ++k) {
+          double t = cl;
 #pragma unroll
-        for (int n = N - 1; n >= 2; --n) t *= __ldg(row[n] + col[k][n - 1]);
-        acc[k] = fma(t, __ldg(row[1] + col[k][0]), acc[k]);
+          for (int n = N - 2; n >= 2; --n) t *= __ldg(row[n] + col[k][n - 1]);
+          acc[k] = fma(t, __ldg(row[1] + col[k][0]), acc[k]);
+        }
+      }
+    } else {
+#pragma unroll UNROLL
+      for (int j = 0; j < cnt; ++j) {
+        const double c = __shfl_sync(0xffffffffu, cm, j);
+        const double* row[N];
+#pragma unroll
+        for (int n = 1; n < N; ++n)
+          row[n] = a.A[n] + (size_t)__shfl_sync(0xffffffffu, mine[n], j) * a.R[n];
+#pragma unroll
+        for (int k = 0; k < KE; ++k) {
+          double t = c;
+#pragma unroll
+          for (int n = N - 1; n >= 2; --n) t *= __ldg(row[n] + col[k][n - 1]);
+          acc[k] = fma(t, __ldg(row[1] + col[k][0]), acc[k]);
+        }
       }
     }
   }
