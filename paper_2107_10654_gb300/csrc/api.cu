@@ -48,6 +48,7 @@ tucker_status launch_kron_dot(tucker_handle* h, const RowSet& s, const double* g
                               const double* g2, double* z1, double* z2);
 tucker_status cholesky(tucker_handle* h, double* M, int d);
 tucker_status cholesky32(tucker_handle* h, float* M, int d, float* X, float* XC, int* inv_done);
+bool chol32_on_cluster(tucker_handle* h, int d);
 tucker_status chol_prepare(tucker_handle* h, const double* L, int d, double* LT, double* Linv);
 tucker_status chol_prepare32(tucker_handle* h, const float* L, int d, float* LT, float* Linv);
 tucker_status chol_solve2(tucker_handle* h, const double* L, const double* LT, const double* Linv,
@@ -532,6 +533,13 @@ tucker_status tucker_create(tucker_handle** out, void* cuda_stream) {
     return TUCKER_ECUDA;
   }
   for (int i = 0; i < 16; ++i) cudaEventCreate(&h->ev[i]);
+  if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    tucker_destroy(h);
+    return TUCKER_ECUDA;
+  }
   *out = h;
   return TUCKER_OK;
 }
@@ -545,6 +553,12 @@ tucker_status tucker_destroy(tucker_handle* h) {
   if (h->d_status) cudaFree(h->d_status);
   if (h->h_status) cudaFreeHost(h->h_status);
   for (int i = 0; i < 16; ++i) cudaEventDestroy(h->ev[i]);
+  if (h->aux) {
+    cudaStreamSynchronize(h->aux);
+    cudaStreamDestroy(h->aux);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
   return TUCKER_OK;
 }
@@ -762,14 +776,34 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   double* G = h->chol.L;
   TK_TRY(walk_segments(h, rs, F.I[0], b.walk));
   TK_TRY(build_gram(h, F, rs, prec, cap, b, G));
-  TK_TRY(rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x, 1.0, nullptr, nullptr,
-                   nullptr, b.h));
+  // the right-hand side h = K_S^T W x; when the factorisation occupies one
+  // thread-block cluster (mixed solver, small d) it runs beside it on the
+  // second stream and is joined before the solve (a grid-wide factorisation
+  // needs every SM, so there it stays in order)
+  const bool beside = h->solver == TUCKER_SOLVER_MIXED && chol32_on_cluster(h, F.d);
+  if (beside) {
+    TK_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+    TK_CUDA(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    cudaStream_t main_stream = h->stream;
+    h->stream = h->aux;
+    const tucker_status st = rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x,
+                                       1.0, nullptr, nullptr, nullptr, b.h);
+    h->stream = main_stream;
+    TK_TRY(st);
+    TK_CUDA(h, cudaEventRecord(h->ev_join, h->aux));
+  } else {
+    TK_TRY(rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x, 1.0, nullptr,
+                     nullptr, nullptr, b.h));
+  }
   TK_TRY(launch_regdiag(h, h->chol.regdiag, F.d, lambda,
                         reg == TUCKER_REG_AUGMENTED ? b.D : nullptr));
   ev_record(h, timing, 5);
   int iters = 0;
   double rel = 0.0;
-  TK_TRY(solve_refine(h, F, rs64, prec, b, &iters, &rel));
+  TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
+  TK_TRY(factorize(h, h->chol.L, F.d, prec));
+  if (beside) TK_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+  TK_TRY(solve_refined(h, F, rs64, prec, b, b.h, b.g, &iters, &rel));
   TK_CUDA(h, cudaMemcpyAsync(core_out, b.g, sizeof(double) * F.d, cudaMemcpyDeviceToDevice,
                              h->stream));
   ev_record(h, timing, 6);

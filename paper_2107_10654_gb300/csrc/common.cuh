@@ -68,9 +68,11 @@ struct tucker_handle {
   int64_t launches = 0;         // kernels launched by this handle (all calls)
   int solver = 0;               // tucker_solver: FP64 Cholesky (0) or mixed (1)
   int timing = 0;               // record per-kernel events (ev[8..11]) during this call
-  int chol_cluster = 0;         // CTAs of the one-cluster FP32 Cholesky for chol_cluster_key
-  int chol_cluster_key = -1;    // 2 d + (explicit inverse) of that answer
+  int chol_cluster[2] = {0, 0}; // CTAs of the one-cluster FP32 Cholesky of order chol_cluster_key
+  int chol_cluster_key = -1;    // (without, with the explicit inverse; 0: does not fit)
   cudaEvent_t ev[16];
+  cudaStream_t aux = nullptr;   // second stream: work that runs beside the factorisation
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   char err[512];
 };
 

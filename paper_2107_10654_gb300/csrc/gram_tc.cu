@@ -503,30 +503,53 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
   }
 }
 
-// G[r][c] = G[c][r] = sum over splits of the partial tiles (upper instances only)
-__global__ void k_tc_reduce(const float* partial, int nsplit, int ntiles, int Tt, int d, double* G) {
+// G[r][c] = G[c][r] = sum over splits of the partial tiles (upper instances only).
+// Thread = four consecutive columns of a tile row (16-byte loads), eight
+// independent chains over the splits so that many loads are in flight (the
+// partial tiles were just written and are mostly still in L2); the chains are
+// combined in FP64 in a fixed order, so the result does not depend on timing.
+__global__ void __launch_bounds__(256) k_tc_reduce(const float* partial, int nsplit, int ntiles,
+                                                   int Tt, int d, double* G) {
   int ti, tj;
   tile_of(blockIdx.y, Tt, &ti, &tj);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < TC_TILE * TC_TILE;
-       e += gridDim.x * blockDim.x) {
-    const int r = ti * TC_TILE + e / TC_TILE, c = tj * TC_TILE + e % TC_TILE;
-    if (r >= d || c >= d || r > c) continue;
-    // FP32 partial sums of FP32 accumulators (their error is far below the
-    // operand rounding), four interleaved chains, combined in a fixed order
-    const float* src = partial + (size_t)blockIdx.y * (TC_TILE * TC_TILE) + e;
-    const size_t stride = (size_t)ntiles * (TC_TILE * TC_TILE);
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-    int sp = 0;
-    for (; sp + 4 <= nsplit; sp += 4) {
-      v0 += src[(size_t)sp * stride];
-      v1 += src[(size_t)(sp + 1) * stride];
-      v2 += src[(size_t)(sp + 2) * stride];
-      v3 += src[(size_t)(sp + 3) * stride];
+  constexpr int Q = TC_TILE / 4;                        // 16-byte groups per tile row
+  const size_t stride4 = (size_t)ntiles * (TC_TILE * TC_TILE) / 4;
+  for (int e4 = blockIdx.x * blockDim.x + threadIdx.x; e4 < TC_TILE * Q;
+       e4 += gridDim.x * blockDim.x) {
+    const int lr = e4 / Q, lc = 4 * (e4 % Q);
+    const int r = ti * TC_TILE + lr, c0 = tj * TC_TILE + lc;
+    if (r >= d || c0 >= d || c0 + 3 < r) continue;     // nothing of the upper triangle here
+    const float4* src = reinterpret_cast<const float4*>(partial) +
+                        ((size_t)blockIdx.y * (TC_TILE * TC_TILE) + (size_t)lr * TC_TILE + lc) / 4;
+    float4 acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int sp = 0; sp < nsplit; sp += 8) {             // chain j takes splits j, j + 8, ...
+      float4 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        v[j] = sp + j < nsplit ? src[(size_t)(sp + j) * stride4] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        acc[j].x += v[j].x; acc[j].y += v[j].y; acc[j].z += v[j].z; acc[j].w += v[j].w;
+      }
     }
-    for (; sp < nsplit; ++sp) v0 += src[(size_t)sp * stride];
-    const double v = ((double)v0 + (double)v1) + ((double)v2 + (double)v3);
-    G[(size_t)r * d + c] = v;
-    G[(size_t)c * d + r] = v;
+    double o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double t[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) t[j] = q == 0 ? acc[j].x : q == 1 ? acc[j].y : q == 2 ? acc[j].z : acc[j].w;
+      o[q] = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + q;
+      if (c < d && c >= r) {
+        G[(size_t)r * d + c] = o[q];
+        G[(size_t)c * d + r] = o[q];
+      }
+    }
   }
 }
 

@@ -711,19 +711,21 @@ static bool cluster_fits(int C, size_t smem) {
 }
 
 // Cluster size for the one-cluster factor of order d, with or without the
-// inverse (0: neither 16 nor 8 CTAs can hold it).  Cached per (d, inverse).
+// inverse (0: neither 16 nor 8 CTAs can hold it).  Both answers are cached per d.
 static int chol_cluster_size(tucker_handle* h, int d, bool inv) {
   if (d > CHOL_CL_MAX_D) return 0;
-  const int key = 2 * d + (inv ? 1 : 0);
-  if (h->chol_cluster_key == key) return h->chol_cluster;
-  int C = 0;
-  for (int c : {16, 8}) {
-    const size_t smem = chol_cl_geom(d, c, inv).smem;
-    if (smem <= CHOL_CL_SMEM_MAX && cluster_fits(c, smem)) { C = c; break; }
+  if (h->chol_cluster_key != d) {
+    for (int v = 0; v < 2; ++v) {
+      int C = 0;
+      for (int c : {16, 8}) {
+        const size_t smem = chol_cl_geom(d, c, v == 1).smem;
+        if (smem <= CHOL_CL_SMEM_MAX && cluster_fits(c, smem)) { C = c; break; }
+      }
+      h->chol_cluster[v] = C;
+    }
+    h->chol_cluster_key = d;
   }
-  h->chol_cluster_key = key;
-  h->chol_cluster = C;
-  return C;
+  return h->chol_cluster[inv ? 1 : 0];
 }
 
 static tucker_status cholesky32_cluster(tucker_handle* h, float* M, int d, int C, float* X,
@@ -746,6 +748,12 @@ static tucker_status cholesky32_cluster(tucker_handle* h, float* M, int d, int C
   TK_COUNT(h);
   TK_CUDA(h, cudaLaunchKernelEx(&cfg, k_chol32_cluster, M, d, h->d_status, X, XC));
   return TUCKER_OK;
+}
+
+// Whether the FP32 factor of order d runs on one thread-block cluster (so the
+// rest of the GPU is free for other work meanwhile).
+bool chol32_on_cluster(tucker_handle* h, int d) {
+  return chol_cluster_size(h, d, true) > 0 || chol_cluster_size(h, d, false) > 0;
 }
 
 // FP32 Cholesky; with X / XC given (d x d each) and d small enough, the
