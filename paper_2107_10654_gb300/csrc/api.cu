@@ -65,6 +65,8 @@ tucker_status chol_inverse32(tucker_handle* h, const float* L, const float* Linv
 tucker_status chol_solve_inv32(tucker_handle* h, const float* X, const float* XC, int d,
                                const double* rhs, double* g, double* tmp);
 tucker_status launch_regdiag(tucker_handle* h, double* out, int d, double lambda, const double* D);
+tucker_status chol_correct_inv32(tucker_handle* h, const float* X, const float* XC, int d,
+                                 double* r, double* g, double* stats, double* tmp, double* part);
 tucker_status launch_refine_update(tucker_handle* h, double* g, const double* r, int d,
                                    double* out2);
 tucker_status launch_add_diag(tucker_handle* h, double* M, int d, const double* diag);
@@ -327,13 +329,15 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
   b->gram_ws = ar.get<char>(b->gram_bytes);
 }
 
+constexpr size_t kPartDoubles = 512;            // per-CTA partial sums of one inverse application
+
 static tucker_status chol_reserve(tucker_handle* h, int d) {
   CholCache& c = h->chol;
   const size_t need = (size_t)d * d;
   const size_t inv = chol_inv_doubles(d);
   const size_t xinv = chol_inverse_fits(d) ? 2 * need : 0;
   // FP64: L, LT, regdiag, tmp, Linv; FP32: L32, LT32, Linv32 (+ X32, XC32 for small d)
-  const size_t bytes = (2 * need + 2 * (size_t)d + inv + 64) * sizeof(double) +
+  const size_t bytes = (2 * need + 2 * (size_t)d + inv + 64 + kPartDoubles) * sizeof(double) +
                        (2 * need + inv + 64 + xinv) * sizeof(float);
   if (c.cap < bytes) {
     TK_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -352,7 +356,8 @@ static tucker_status chol_reserve(tucker_handle* h, int d) {
   c.regdiag = c.LT + need;
   c.tmp = c.regdiag + d;
   c.Linv = c.tmp + d;
-  c.L32 = reinterpret_cast<float*>(c.Linv + inv + 64);
+  c.part = c.Linv + inv + 64;
+  c.L32 = reinterpret_cast<float*>(c.part + kPartDoubles);
   c.LT32 = c.L32 + need;
   c.Linv32 = c.LT32 + need;
   c.X32 = xinv ? c.Linv32 + inv + 64 : nullptr;
@@ -466,8 +471,13 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
       TK_TRY(rows_axpy(h, F, rs, b.walk, b.axpy_split, b.axpy_part, b.w, b.z, -1.0, rhs,
                        h->chol.regdiag, g, b.r));
     }
-    TK_TRY(chol_solve(h, d, b.r, b.r, prec));
-    TK_TRY(launch_refine_update(h, g, b.r, d, b.rstat + 2 * it));
+    CholCache& cc = h->chol;
+    if ((cc.mixed || (cc.prep32 && prec != TUCKER_PREC_FP64)) && cc.inv32) {
+      TK_TRY(chol_correct_inv32(h, cc.X32, cc.XC32, d, b.r, g, b.rstat + 2 * it, cc.tmp, cc.part));
+    } else {
+      TK_TRY(chol_solve(h, d, b.r, b.r, prec));
+      TK_TRY(launch_refine_update(h, g, b.r, d, b.rstat + 2 * it));
+    }
     if (it + 1 < batch) continue;                     // the next correction is certain
     double hv[2 * kMaxRefine];
     const int n = it + 1 - checked;

@@ -37,6 +37,7 @@ struct CholCache {
   double* Linv = nullptr;     // inverses of the 64 x 64 diagonal blocks of L
   double* LT = nullptr;       // L transposed (upper triangle), d x d
   double* tmp = nullptr;      // d doubles of solve scratch
+  double* part = nullptr;     // per-CTA partial norms of a refinement correction
   float* L32 = nullptr;       // FP32 factor of the mixed solver (d x d)
   float* LT32 = nullptr;      // its transpose
   float* Linv32 = nullptr;    // its inverted 64 x 64 diagonal blocks

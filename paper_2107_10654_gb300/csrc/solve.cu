@@ -1042,18 +1042,100 @@ tucker_status chol_inverse32(tucker_handle* h, const float* L, const float* Linv
 
 int chol_inverse_fits(int d) { return d <= INV_MAX_D; }
 
-// g = X^T (X rhs) with tmp holding X rhs (g may alias rhs).
+// out = X^T (X rhs) in one cooperative launch: each warp forms rows of
+// t = X rhs (the same per-row FP32 arithmetic as k_gemv_tri, rhs staged in
+// shared memory as FP32), a grid barrier, then rows of X^T t from the
+// column-major copy XC.  With upd given, also upd += out and
+// stats = (sum out_i^2, sum upd_i^2): partial sums per warp and per CTA,
+// combined by CTA 0 in a fixed order after a second barrier.  rhs may alias out.
+constexpr int IA_THREADS = 256;
+constexpr int IA_MAX_CTAS = 256;                 // CTAs of one application, at most
+
+__global__ void __launch_bounds__(IA_THREADS)
+    k_inv_apply(const float* X, const float* XC, int d, const double* rhs, double* out,
+                double* upd, double* stats, double* t, double* part) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ float ia_v[];                           // rhs, then t, as FP32
+  __shared__ double wpart[IA_THREADS / 32][2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (IA_THREADS / 32) + w, nwarps = gridDim.x * (IA_THREADS / 32);
+  for (int j = threadIdx.x; j < d; j += IA_THREADS) ia_v[j] = (float)rhs[j];
+  __syncthreads();
+  for (int i = gw; i < d; i += nwarps) {                    // t_i = sum_{j <= i} X_ij rhs_j
+    const float* xr = X + (size_t)i * d;
+    float acc = 0.f;
+#pragma unroll 4
+    for (int j = lane; j <= i; j += 32) acc = fmaf(xr[j], ia_v[j], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) t[i] = (double)acc;
+  }
+  grid.sync();                                              // t complete; every rhs read done
+  for (int j = threadIdx.x; j < d; j += IA_THREADS) ia_v[j] = (float)t[j];
+  __syncthreads();
+  double s_out = 0.0, s_upd = 0.0;
+  for (int j = gw; j < d; j += nwarps) {                    // out_j = sum_{i >= j} X_ij t_i
+    const float* xr = XC + (size_t)j * d;
+    float acc = 0.f;
+#pragma unroll 4
+    for (int i = j + lane; i < d; i += 32) acc = fmaf(xr[i], ia_v[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const double o = (double)acc;
+      if (out) out[j] = o;
+      if (upd) {
+        const double gn = upd[j] + o;
+        upd[j] = gn;
+        s_out = fma(o, o, s_out);
+        s_upd = fma(gn, gn, s_upd);
+      }
+    }
+  }
+  if (upd && stats) {
+    if (lane == 0) { wpart[w][0] = s_out; wpart[w][1] = s_upd; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int k = 0; k < IA_THREADS / 32; ++k) { a += wpart[k][0]; b += wpart[k][1]; }
+      part[2 * blockIdx.x] = a;
+      part[2 * blockIdx.x + 1] = b;
+    }
+    grid.sync();                                            // every CTA's partial written
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int k = 0; k < (int)gridDim.x; ++k) { a += part[2 * k]; b += part[2 * k + 1]; }
+      stats[0] = a;
+      stats[1] = b;
+    }
+  }
+}
+
+static tucker_status launch_inv_apply(tucker_handle* h, const float* X, const float* XC, int d,
+                                      const double* rhs, double* out, double* upd, double* stats,
+                                      double* t, double* part) {
+  const void* kern = (const void*)k_inv_apply;
+  const size_t smem = (size_t)d * sizeof(float);
+  int grid = (d + 7) / 8;                                   // one row per warp per phase
+  const int cap = coop_grid(h, kern, IA_THREADS, smem);
+  if (cap < 1) return fail(h, TUCKER_ECUDA, "cooperative inverse application cannot be resident");
+  if (grid > cap) grid = cap;
+  if (grid > IA_MAX_CTAS) grid = IA_MAX_CTAS;
+  void* args[] = {(void*)&X, (void*)&XC, &d, (void*)&rhs, &out, &upd, &stats, &t, &part};
+  TK_COUNT(h);
+  TK_CUDA(h, cudaLaunchCooperativeKernel(kern, grid, IA_THREADS, args, smem, h->stream));
+  return TUCKER_OK;
+}
+
+// g = X^T (X rhs) (g may alias rhs); tmp: d doubles of scratch.
 tucker_status chol_solve_inv32(tucker_handle* h, const float* X, const float* XC, int d,
                                const double* rhs, double* g, double* tmp) {
-  int grid = (d + 7) / 8;
-  if (grid > h->num_sms * 8) grid = h->num_sms * 8;
-  TK_COUNT(h);
-  k_gemv_tri<<<grid, 256, 0, h->stream>>>(X, d, rhs, tmp, 1);
-  TK_LAUNCH(h);
-  TK_COUNT(h);
-  k_gemv_tri<<<grid, 256, 0, h->stream>>>(XC, d, tmp, g, 0);
-  TK_LAUNCH(h);
-  return TUCKER_OK;
+  return launch_inv_apply(h, X, XC, d, rhs, g, nullptr, nullptr, tmp, nullptr);
+}
+
+// r = X^T (X r), then g += r and stats = (||r||^2, ||g||^2): one refinement
+// correction with the explicit inverse; tmp: d doubles, part: 2 IA_MAX_CTAS doubles.
+tucker_status chol_correct_inv32(tucker_handle* h, const float* X, const float* XC, int d,
+                                 double* r, double* g, double* stats, double* tmp, double* part) {
+  return launch_inv_apply(h, X, XC, d, r, r, g, stats, tmp, part);
 }
 
 tucker_status launch_to_f32(tucker_handle* h, const double* in, size_t n, float* out) {
