@@ -206,16 +206,19 @@ __device__ __forceinline__ int pack_pos(int s, int perm) {
   return j < 4 ? 4 * c + j : 32 + 4 * c + (j - 4);
 }
 
+// Thread = (chunk q, element e, sample slot s) with s fastest: a CTA covers
+// blockDim / CS whole (q, e) rows, so the index arithmetic is one 32-bit
+// division per output (the host keeps nch * sumR below 2^31).
 __global__ void k_tc_pack(PackArgs a) {
   const int nrows = *a.n_rows;
-  const int64_t nch = (nrows + a.CS - 1) / a.CS;
-  const int64_t total = nch * a.sumR * a.CS;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int s = (int)(t % a.CS);
-    const int e = (int)((t / a.CS) % a.sumR);
-    const int64_t q = t / ((int64_t)a.CS * a.sumR);
-    const int64_t u = q * a.CS + s;
+  const int nch = (nrows + a.CS - 1) / a.CS;
+  const int nrow_total = nch * a.sumR;                     // (chunk, element) rows
+  const int per_cta = blockDim.x / a.CS;
+  const int s = threadIdx.x % a.CS;
+  for (int row = blockIdx.x * per_cta + threadIdx.x / a.CS; row < nrow_total;
+       row += gridDim.x * per_cta) {
+    const int q = row / a.sumR, e = row - q * a.sumR;
+    const int64_t u = (int64_t)q * a.CS + s;
     float v = 0.f;
     if (u < nrows) {
       int n = 0;
@@ -224,7 +227,7 @@ __global__ void k_tc_pack(PackArgs a) {
       const float f = (float)load_as_double(a.A[n], (int64_t)a.idx[n][u] * a.R[n] + r, a.is64);
       v = n == 0 ? sqrtf((float)a.w[u]) * f : f;     // FP32 is exact enough: rounded to BF16/TF32 next
     }
-    a.pack[t - s + pack_pos(s, a.perm)] = v;
+    a.pack[(int64_t)row * a.CS + pack_pos(s, a.perm)] = v;
   }
 }
 
@@ -643,6 +646,8 @@ tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_
     return fail(h, TUCKER_ENOTSUP, "tensor-core Gram needs %zu bytes of shared memory "
                 "(sum R_n = %d)", smem, sumR);
   a.tstages = tst;
+  if (nch * sumR >= (int64_t)1 << 31)
+    return fail(h, TUCKER_ENOTSUP, "tensor-core Gram of %lld rows too large", (long long)cap);
   int pg = (int)std::min<int64_t>((nch * sumR * CS + 255) / 256, (int64_t)h->num_sms * 16);
   if (pg < 1) pg = 1;
   TK_COUNT(h);
