@@ -91,10 +91,12 @@ size_t walk_scratch_doubles(int64_t I1, int d, int R1, int64_t cap, int sms);
 bool walk_fits(int N, const int* R, int64_t I1);
 tucker_status walk_segments(tucker_handle* h, const RowSet& s, int64_t I1, const WalkBuf& wb);
 tucker_status walk_dot(tucker_handle* h, const RowSet& s, int64_t I1, const WalkBuf& wb,
-                       const double* g1, const double* g2, double* z1, double* z2);
+                       const double* g1, const double* g2, double* z1, double* z2,
+                       bool f32 = false);
 tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, const WalkBuf& wb,
                         const double* ca, const double* cb, double coef, const double* base,
-                        const double* diag, const double* y, double* out);
+                        const double* diag, const double* y, double* out, bool f32 = false);
+bool walk_f32_ok(const RowSet& s);
 tucker_status launch_decode_rows(tucker_handle* h, const FactorSet& F, const uint64_t* keys,
                                  int64_t n, uint32_t* const* idx, const void* vals, double* x);
 int gram_tc_supported(int prec, int d);
@@ -134,6 +136,11 @@ static tucker_status rows_axpy(tucker_handle* h, const FactorSet& F, const RowSe
   if (walk_fits(F.N, F.R, F.I[0]))
     return walk_axpy(h, rs, F.I[0], walk, ca, cb, coef, base, diag, y, out);
   return launch_kron_axpy(h, rs, ca, cb, coef, nsplit, part, base, diag, y, out);
+}
+
+// Whether a residual may be evaluated with the FP32 walks on the FP32 factors of rs32.
+static bool rows_f32_ok(const FactorSet& F, const RowSet* rs32) {
+  return rs32 && walk_fits(F.N, F.R, F.I[0]) && walk_f32_ok(*rs32);
 }
 
 // ----------------------------------------------------------------- plumbing
@@ -446,7 +453,7 @@ static tucker_status build_gram(tucker_handle* h, const FactorSet& F, const RowS
 // stops shrinking.
 static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const RowSet& rs,
                                    int prec, SketchBufs& b, const double* rhs, double* g,
-                                   int* iters, double* rel) {
+                                   int* iters, double* rel, const RowSet* rs32 = nullptr) {
   const int d = F.d;
   TK_TRY(chol_solve(h, d, rhs, g, prec));
   *iters = 0;
@@ -458,6 +465,9 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
   // first solve), or when the corrections stop shrinking (rounding level).  A
   // tensor-core Gram (8- or 11-bit operands) always takes two corrections, so
   // the first two are enqueued back to back and the host waits once for both.
+  // The first of them only has to be accurate to the Gram's rounding level, so
+  // with FP32 factors its residual is evaluated by the FP32 walks; every later
+  // residual, which sets the accuracy of the result, is FP64.
   const double target = explicit_m ? 1e-13 : 1e-8;
   const int max_iters = h->chol.mixed ? 12 : 8;
   const int batch = (prec == TUCKER_PREC_BF16 || prec == TUCKER_PREC_TF32) ? 2 : 1;
@@ -466,6 +476,10 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
   for (int it = 0; it < max_iters; ++it) {
     if (explicit_m) {
       TK_TRY(launch_gemv_resid(h, h->chol.L, d, g, rhs, b.r));
+    } else if (it == 0 && batch == 2 && rows_f32_ok(F, rs32)) {
+      TK_TRY(walk_dot(h, *rs32, F.I[0], b.walk, g, nullptr, b.z, nullptr, true));
+      TK_TRY(walk_axpy(h, *rs32, F.I[0], b.walk, b.w, b.z, -1.0, rhs, h->chol.regdiag, g, b.r,
+                       true));
     } else {
       TK_TRY(rows_dot(h, F, rs, b.walk, g, nullptr, b.z, nullptr));
       TK_TRY(rows_axpy(h, F, rs, b.walk, b.axpy_split, b.axpy_part, b.w, b.z, -1.0, rhs,
@@ -813,7 +827,7 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
   TK_TRY(factorize(h, h->chol.L, F.d, prec));
   if (beside) TK_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-  TK_TRY(solve_refined(h, F, rs64, prec, b, b.h, b.g, &iters, &rel));
+  TK_TRY(solve_refined(h, F, rs64, prec, b, b.h, b.g, &iters, &rel, &rs));
   TK_CUDA(h, cudaMemcpyAsync(core_out, b.g, sizeof(double) * F.d, cudaMemcpyDeviceToDevice,
                              h->stream));
   ev_record(h, timing, 6);

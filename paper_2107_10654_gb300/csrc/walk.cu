@@ -43,6 +43,7 @@ struct WalkArgs {
   int fofs[TUCKER_MAX_ORDER];        // dot: first column of mode n >= 2 in a lane's factor rows
   int fstore;                         // dot: factor entries per lane (sum of R_n, n >= 2)
   const double* A[TUCKER_MAX_ORDER];  // FP64 factors
+  const float* A32[TUCKER_MAX_ORDER]; // FP32 factors (the FP32 walks)
   int d;
   int I1;
   int CH;
@@ -72,6 +73,18 @@ struct WalkArgs {
 __device__ __forceinline__ double fac(const WalkArgs& a, int n, uint32_t i, int r) {
   return __ldg(a.A[n] + (size_t)i * a.R[n] + r);
 }
+
+// Factor entry in the walk's arithmetic type T (FP64 copies, or the FP32 originals).
+template <class T> __device__ __forceinline__ T fac_t(const WalkArgs& a, int n, uint32_t i, int r);
+template <> __device__ __forceinline__ double fac_t<double>(const WalkArgs& a, int n, uint32_t i, int r) {
+  return __ldg(a.A[n] + (size_t)i * a.R[n] + r);
+}
+template <> __device__ __forceinline__ float fac_t<float>(const WalkArgs& a, int n, uint32_t i, int r) {
+  return __ldg(a.A32[n] + (size_t)i * a.R[n] + r);
+}
+template <class T> __device__ __forceinline__ const T* fac_base(const WalkArgs& a, int n);
+template <> __device__ __forceinline__ const double* fac_base<double>(const WalkArgs& a, int n) { return a.A[n]; }
+template <> __device__ __forceinline__ const float* fac_base<float>(const WalkArgs& a, int n) { return a.A32[n]; }
 
 // Segment table: seg_begin[i1] / seg_end[i1] of the real rows (sorted keys).
 __global__ void k_segments(const uint32_t* idx0, const int* n_rows, int* seg_begin, int* seg_end) {
@@ -106,10 +119,13 @@ __global__ void k_piece_fill(const int* seg_begin, const int* seg_end, int I1, i
   }
 }
 
-// V_1[v][i1][j] = sum_{r_1} A^(1)[i1][r_1] g_v[r_1 * lsz1 + j] for the segments with rows.
+// V_1[v][i1][j] = sum_{r_1} A^(1)[i1][r_1] g_v[r_1 * lsz1 + j] for the segments with rows,
+// stored in the walk's arithmetic type T.
+template <class T>
 __global__ void k_walk_v1(WalkArgs a) {
   const int L1 = a.lsz[1];
   const int nvec = a.g2 ? 2 : 1;
+  T* V1 = reinterpret_cast<T*>(a.V1);
   const int64_t total = (int64_t)a.I1 * L1;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -117,9 +133,10 @@ __global__ void k_walk_v1(WalkArgs a) {
     if (a.pcnt[i1] == 0) continue;
     for (int v = 0; v < nvec; ++v) {
       const double* g = v ? a.g2 : a.g1;
-      double acc = 0.0;
-      for (int r = 0; r < a.R[0]; ++r) acc = fma(fac(a, 0, (uint32_t)i1, r), g[(size_t)r * L1 + j], acc);
-      a.V1[((size_t)v * a.I1 + i1) * L1 + j] = acc;
+      T acc = T(0);
+      for (int r = 0; r < a.R[0]; ++r)
+        acc = fma(fac_t<T>(a, 0, (uint32_t)i1, r), (T)g[(size_t)r * L1 + j], acc);
+      V1[((size_t)v * a.I1 + i1) * L1 + j] = acc;
     }
   }
 }
@@ -128,17 +145,16 @@ __global__ void k_walk_v1(WalkArgs a) {
 // for this lane's row; F holds the lane's factor rows, entry (mode l, column r)
 // at F[(fofs[l] + r) * 32 + lane].  Nested loops with runtime ranks; the
 // innermost level is one FMA per element of V.
-template <int N, int L>
+template <class T, int N, int L>
 struct FlatDot {
-  static __device__ __forceinline__ void run(const WalkArgs& a, const double* V1, const double* V2,
-                                             bool two, const double* F, int lane, double* z1,
-                                             double* z2) {
-    double s1 = 0.0, s2 = 0.0;
+  static __device__ __forceinline__ void run(const WalkArgs& a, const T* V1, const T* V2,
+                                             bool two, const T* F, int lane, T* z1, T* z2) {
+    T s1 = T(0), s2 = T(0);
     const int step = a.lsz[L + 1];
     for (int r = 0; r < a.R[L]; ++r) {
-      double t1, t2;
-      FlatDot<N, L + 1>::run(a, V1 + r * step, V2 + r * step, two, F, lane, &t1, &t2);
-      const double f = F[(a.fofs[L] + r) * 32 + lane];
+      T t1, t2;
+      FlatDot<T, N, L + 1>::run(a, V1 + r * step, V2 + r * step, two, F, lane, &t1, &t2);
+      const T f = F[(a.fofs[L] + r) * 32 + lane];
       s1 = fma(f, t1, s1);
       if (two) s2 = fma(f, t2, s2);
     }
@@ -146,10 +162,10 @@ struct FlatDot {
     *z2 = s2;
   }
 };
-template <int N>
-struct FlatDot<N, N> {
-  static __device__ __forceinline__ void run(const WalkArgs&, const double* V1, const double* V2,
-                                             bool, const double*, int, double* z1, double* z2) {
+template <class T, int N>
+struct FlatDot<T, N, N> {
+  static __device__ __forceinline__ void run(const WalkArgs&, const T* V1, const T* V2, bool,
+                                             const T*, int, T* z1, T* z2) {
     *z1 = V1[0];
     *z2 = V2[0];
   }
@@ -158,7 +174,7 @@ struct FlatDot<N, N> {
 // z_u = k_u . g for the rows of one piece per warp, one row per lane: V_1 of
 // the piece's i_1 (shared by its rows) is copied to shared memory, each lane
 // stages its own factor rows of modes 2..N, and contracts them against V_1.
-template <int N>
+template <class T, int N>
 __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_dot(WalkArgs a) {
   extern __shared__ double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -167,28 +183,29 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_dot(WalkArgs a) {
   const bool two = a.g2 != nullptr;
   const int nvec = two ? 2 : 1;
   const int L1 = a.lsz[1];
-  double* V = sm + (size_t)warp * (nvec * L1 + 32 * a.fstore);
-  double* F = V + nvec * L1;
+  T* V = reinterpret_cast<T*>(sm + (size_t)warp * (nvec * L1 + 32 * a.fstore));
+  T* F = V + nvec * L1;
   const int i1 = a.p_i1[p], u0 = a.p_u0[p], u1 = a.p_u1[p];
+  const T* V1 = reinterpret_cast<const T*>(a.V1);
   for (int v = 0; v < nvec; ++v) {
-    const double* src = a.V1 + ((size_t)v * a.I1 + i1) * L1;
+    const T* src = V1 + ((size_t)v * a.I1 + i1) * L1;
     for (int j = lane; j < L1; j += 32) V[v * L1 + j] = src[j];
   }
-  const double* V2 = V + (two ? L1 : 0);
+  const T* V2 = V + (two ? L1 : 0);
   for (int base = u0; base < u1; base += 32) {
     const int u = base + lane;
     const bool act = u < u1;
     __syncwarp();
     for (int n = 1; n < N; ++n) {
       const uint32_t i = act ? __ldg(a.idx[n] + u) : 0u;
-      for (int r = 0; r < a.R[n]; ++r) F[(a.fofs[n] + r) * 32 + lane] = act ? fac(a, n, i, r) : 0.0;
+      for (int r = 0; r < a.R[n]; ++r) F[(a.fofs[n] + r) * 32 + lane] = act ? fac_t<T>(a, n, i, r) : T(0);
     }
     __syncwarp();
-    double z1, z2;
-    FlatDot<N, 1>::run(a, V, V2, two, F, lane, &z1, &z2);
+    T z1, z2;
+    FlatDot<T, N, 1>::run(a, V, V2, two, F, lane, &z1, &z2);
     if (act) {
-      a.z1[u] = z1;
-      if (a.z2) a.z2[u] = z2;
+      a.z1[u] = (double)z1;
+      if (a.z2) a.z2[u] = (double)z2;
     }
   }
 }
@@ -269,7 +286,7 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy(WalkArgs a) {
 // c_u * prod_{n >= 2} A^(n)[i_n(u)][r_n(e)] for every row of the piece, so the
 // rows carry no dependence on one another and the factor loads of successive
 // rows overlap (the level fold above waits on each row's loads in turn).
-template <int N, int KE>
+template <class T, int N, int KE>
 __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes(WalkArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t p = (int64_t)blockIdx.x * WK_WARPS + warp;
@@ -277,11 +294,11 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes(WalkArgs a) {
   const int L1 = a.lsz[1];
   const int u0 = a.p_u0[p], u1 = a.p_u1[p];
   int col[KE][N - 1];                                       // r_n(e), n = 2 .. N
-  double acc[KE];
+  T acc[KE];
   const bool shared_last = N >= 3 && 32 % a.R[N - 1] == 0;
 #pragma unroll
   for (int k = 0; k < KE; ++k) {
-    acc[k] = 0.0;
+    acc[k] = T(0);
     const int e = lane + 32 * k;
 #pragma unroll
     for (int n = 1; n < N; ++n) col[k][n - 1] = e < L1 ? (e / a.lsz[n + 1]) % a.R[n] : 0;
@@ -289,25 +306,25 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes(WalkArgs a) {
   for (int base = u0; base < u1; base += 32) {
     const int cnt = min(32, u1 - base);
     uint32_t mine[N];
-    double cm = 0.0;
+    T cm = T(0);
 #pragma unroll
     for (int n = 1; n < N; ++n) mine[n] = lane < cnt ? __ldg(a.idx[n] + base + lane) : 0u;
-    if (lane < cnt) cm = a.coef * a.ca[base + lane] * (a.cb ? a.cb[base + lane] : 1.0);
+    if (lane < cnt) cm = (T)(a.coef * a.ca[base + lane] * (a.cb ? a.cb[base + lane] : 1.0));
     constexpr int UNROLL = KE >= 8 ? 1 : 4;                 // rows in flight, within the registers
     if (shared_last) {
       // R_N divides 32: every entry of a lane has r_N = lane mod R_N, so c_u a_N
       // is formed once per row
 #pragma unroll UNROLL
       for (int j = 0; j < cnt; ++j) {
-        const double c = __shfl_sync(0xffffffffu, cm, j);
-        const double* row[N];
+        const T c = __shfl_sync(0xffffffffu, cm, j);
+        const T* row[N];
 #pragma unroll
         for (int n = 1; n < N; ++n)
-          row[n] = a.A[n] + (size_t)__shfl_sync(0xffffffffu, mine[n], j) * a.R[n];
-        const double cl = N >= 3 ? c * __ldg(row[N - 1] + col[0][N - 2]) : c;
+          row[n] = fac_base<T>(a, n) + (size_t)__shfl_sync(0xffffffffu, mine[n], j) * a.R[n];
+        const T cl = N >= 3 ? c * __ldg(row[N - 1] + col[0][N - 2]) : c;
 #pragma unroll
         for (int k = 0; k < KE; ++k) {
-          double t = cl;
+          T t = cl;
 #pragma unroll
           for (int n = N - 2; n >= 2; --n) t *= __ldg(row[n] + col[k][n - 1]);
           acc[k] = fma(t, __ldg(row[1] + col[k][0]), acc[k]);
@@ -316,14 +333,14 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes(WalkArgs a) {
     } else {
 #pragma unroll UNROLL
       for (int j = 0; j < cnt; ++j) {
-        const double c = __shfl_sync(0xffffffffu, cm, j);
-        const double* row[N];
+        const T c = __shfl_sync(0xffffffffu, cm, j);
+        const T* row[N];
 #pragma unroll
         for (int n = 1; n < N; ++n)
-          row[n] = a.A[n] + (size_t)__shfl_sync(0xffffffffu, mine[n], j) * a.R[n];
+          row[n] = fac_base<T>(a, n) + (size_t)__shfl_sync(0xffffffffu, mine[n], j) * a.R[n];
 #pragma unroll
         for (int k = 0; k < KE; ++k) {
-          double t = c;
+          T t = c;
 #pragma unroll
           for (int n = N - 1; n >= 2; --n) t *= __ldg(row[n] + col[k][n - 1]);
           acc[k] = fma(t, __ldg(row[1] + col[k][0]), acc[k]);
@@ -335,7 +352,7 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes(WalkArgs a) {
 #pragma unroll
   for (int k = 0; k < KE; ++k) {
     const int e = lane + 32 * k;
-    if (e < L1) out[e] = acc[k];
+    if (e < L1) out[e] = (double)acc[k];
   }
 }
 
@@ -365,8 +382,11 @@ __global__ void k_walk_expand(WalkArgs a, const double* base, const double* diag
   for (int t = warp; t < a.d; t += nwarps) {
     const int r1 = t / lsz1, j = t % lsz1;
     double v = 0.0;
-    for (int i1 = lane; i1 < a.I1; i1 += 32)
-      v = fma(fac(a, 0, (uint32_t)i1, r1), a.W1[(size_t)i1 * lsz1 + j], v);
+    for (int i1 = lane; i1 < a.I1; i1 += 32) {
+      const double f = a.A32[0] ? (double)__ldg(a.A32[0] + (size_t)i1 * a.R[0] + r1)
+                                : fac(a, 0, (uint32_t)i1, r1);
+      v = fma(f, a.W1[(size_t)i1 * lsz1 + j], v);
+    }
     v = warp_sum(v);
     if (lane == 0) {
       double o = base ? base[t] : 0.0;
@@ -506,16 +526,17 @@ static int grid_for(tucker_handle* h, int64_t work, int threads) {
 
 using WalkKernel = void (*)(WalkArgs);
 
-static WalkKernel walk_dot_kernel(int N) {
+template <class T>
+static WalkKernel walk_dot_kernel_t(int N) {
   switch (N) {
-    case 1: return k_walk_dot<1>;
-    case 2: return k_walk_dot<2>;
-    case 3: return k_walk_dot<3>;
-    case 4: return k_walk_dot<4>;
-    case 5: return k_walk_dot<5>;
-    case 6: return k_walk_dot<6>;
-    case 7: return k_walk_dot<7>;
-    default: return k_walk_dot<8>;
+    case 1: return k_walk_dot<T, 1>;
+    case 2: return k_walk_dot<T, 2>;
+    case 3: return k_walk_dot<T, 3>;
+    case 4: return k_walk_dot<T, 4>;
+    case 5: return k_walk_dot<T, 5>;
+    case 6: return k_walk_dot<T, 6>;
+    case 7: return k_walk_dot<T, 7>;
+    default: return k_walk_dot<T, 8>;
   }
 }
 
@@ -533,21 +554,22 @@ static WalkKernel walk_axpy_kernel(int N) {
 }
 
 // The lane-parallel axpy for orders 2 .. 4 and lsz[1] <= 512 (else nullptr).
-template <int N>
+template <class T, int N>
 static WalkKernel axpy_lanes_by_width(int L1) {
-  if (L1 <= 32) return k_walk_axpy_lanes<N, 1>;
-  if (L1 <= 64) return k_walk_axpy_lanes<N, 2>;
-  if (L1 <= 128) return k_walk_axpy_lanes<N, 4>;
-  if (L1 <= 256) return k_walk_axpy_lanes<N, 8>;
-  if (L1 <= 512) return k_walk_axpy_lanes<N, 16>;
+  if (L1 <= 32) return k_walk_axpy_lanes<T, N, 1>;
+  if (L1 <= 64) return k_walk_axpy_lanes<T, N, 2>;
+  if (L1 <= 128) return k_walk_axpy_lanes<T, N, 4>;
+  if (L1 <= 256) return k_walk_axpy_lanes<T, N, 8>;
+  if (L1 <= 512) return k_walk_axpy_lanes<T, N, 16>;
   return nullptr;
 }
 
+template <class T>
 static WalkKernel walk_axpy_lanes_kernel(int N, int L1) {
   switch (N) {
-    case 2: return axpy_lanes_by_width<2>(L1);
-    case 3: return axpy_lanes_by_width<3>(L1);
-    case 4: return axpy_lanes_by_width<4>(L1);
+    case 2: return axpy_lanes_by_width<T, 2>(L1);
+    case 3: return axpy_lanes_by_width<T, 3>(L1);
+    case 4: return axpy_lanes_by_width<T, 4>(L1);
     default: return nullptr;
   }
 }
@@ -588,10 +610,17 @@ tucker_status walk_segments(tucker_handle* h, const RowSet& s, int64_t I1, const
   return TUCKER_OK;
 }
 
-// z1[u] = k_u . g1, z2[u] = k_u . g2 (g2 nullable) for the real rows.
+// Whether the FP32 walks apply to this sample: FP32 factors, orders 2-4, d / R_1 <= 512.
+bool walk_f32_ok(const RowSet& s) {
+  return !s.is64 && s.N >= 2 && s.N <= 4 && s.d / s.R[0] <= 512;
+}
+
+// z1[u] = k_u . g1, z2[u] = k_u . g2 (g2 nullable) for the real rows; with f32 the
+// products and sums are FP32 (the FP32 factors of s), else FP64 (s holds FP64 factors).
 tucker_status walk_dot(tucker_handle* h, const RowSet& s, int64_t I1, const WalkBuf& wb,
-                       const double* g1, const double* g2, double* z1, double* z2) {
-  if (!s.is64) return fail(h, TUCKER_EINTERNAL, "walk needs FP64 factors");
+                       const double* g1, const double* g2, double* z1, double* z2, bool f32) {
+  if (f32 ? !walk_f32_ok(s) : !s.is64)
+    return fail(h, TUCKER_EINTERNAL, "walk needs FP64 factors (FP32 ones for the FP32 walk)");
   const WalkGeom g = walk_geom(I1, s.d, s.R[0], wb.cap, h->num_sms);
   WalkPtrs w;
   walk_carve(g, wb.p, &w);
@@ -600,23 +629,34 @@ tucker_status walk_dot(tucker_handle* h, const RowSet& s, int64_t I1, const Walk
   const int nvec = g2 ? 2 : 1;
   const size_t smem = (size_t)WK_WARPS * dot_warp_bytes(a.lsz[1], a.fstore, nvec);
   TK_COUNT(h);
-  k_walk_v1<<<grid_for(h, I1 * a.lsz[1], 256), 256, 0, h->stream>>>(a);
-  TK_LAUNCH(h);
-  TK_TRY(launch_by_order(h, walk_dot_kernel(s.N), g.maxP, smem, a));
+  if (f32) {
+    for (int n = 0; n < s.N; ++n) a.A32[n] = static_cast<const float*>(s.A[n]);
+    k_walk_v1<float><<<grid_for(h, I1 * a.lsz[1], 256), 256, 0, h->stream>>>(a);
+    TK_LAUNCH(h);
+    TK_TRY(launch_by_order(h, walk_dot_kernel_t<float>(s.N), g.maxP, smem, a));
+  } else {
+    k_walk_v1<double><<<grid_for(h, I1 * a.lsz[1], 256), 256, 0, h->stream>>>(a);
+    TK_LAUNCH(h);
+    TK_TRY(launch_by_order(h, walk_dot_kernel_t<double>(s.N), g.maxP, smem, a));
+  }
   return TUCKER_OK;
 }
 
-// out = base - diag .* y + coef * sum_u ca_u cb_u k_u  (real rows)
+// out = base - diag .* y + coef * sum_u ca_u cb_u k_u  (real rows); f32 as for walk_dot
+// (the piece partials, their sums and the expansion stay FP64).
 tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, const WalkBuf& wb,
                         const double* ca, const double* cb, double coef, const double* base,
-                        const double* diag, const double* y, double* out) {
-  if (!s.is64) return fail(h, TUCKER_EINTERNAL, "walk needs FP64 factors");
+                        const double* diag, const double* y, double* out, bool f32) {
+  if (f32 ? !walk_f32_ok(s) : !s.is64)
+    return fail(h, TUCKER_EINTERNAL, "walk needs FP64 factors (FP32 ones for the FP32 walk)");
   const WalkGeom g = walk_geom(I1, s.d, s.R[0], wb.cap, h->num_sms);
   WalkPtrs w;
   walk_carve(g, wb.p, &w);
   WalkArgs a = walk_args(s, g, w);
   a.ca = ca; a.cb = cb; a.coef = coef;
-  WalkKernel lanes = walk_axpy_lanes_kernel(s.N, a.lsz[1]);
+  if (f32) for (int n = 0; n < s.N; ++n) a.A32[n] = static_cast<const float*>(s.A[n]);
+  WalkKernel lanes = f32 ? walk_axpy_lanes_kernel<float>(s.N, a.lsz[1])
+                         : walk_axpy_lanes_kernel<double>(s.N, a.lsz[1]);
   if (lanes) {
     TK_COUNT(h);
     lanes<<<(int)((g.maxP + WK_WARPS - 1) / WK_WARPS), WK_WARPS * 32, 0, h->stream>>>(a);
