@@ -59,7 +59,7 @@ typedef enum {
   TUCKER_EDRAWLIMIT = 6,  /* missing-entry sampling used max_draws before m accepted */
   TUCKER_EHASHFULL = 7,   /* observed-entry hash table exceeded its probe limit */
   TUCKER_ECAPACITY = 8,   /* a caller-provided output array is too small */
-  TUCKER_ENOTSUP = 9,     /* combination not supported by this build (e.g. no sm_103a GPU) */
+  TUCKER_ENOTSUP = 9,     /* combination not supported by the library (e.g. no sm_103a GPU) */
   TUCKER_EINTERNAL = 10   /* a device-side consistency check failed */
 } tucker_status;
 
