@@ -1055,17 +1055,29 @@ __global__ void __launch_bounds__(IA_THREADS)
     k_inv_apply(const float* X, const float* XC, int d, const double* rhs, double* out,
                 double* upd, double* stats, double* t, double* part) {
   cg::grid_group grid = cg::this_grid();
-  extern __shared__ float ia_v[];                           // rhs, then t, as FP32
+  extern __shared__ __align__(16) float ia_v[];             // rhs, then t, as FP32
   __shared__ double wpart[IA_THREADS / 32][2];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int gw = blockIdx.x * (IA_THREADS / 32) + w, nwarps = gridDim.x * (IA_THREADS / 32);
   for (int j = threadIdx.x; j < d; j += IA_THREADS) ia_v[j] = (float)rhs[j];
   __syncthreads();
+  const bool vec = (d & 3) == 0;                            // 16-byte rows: float4 loads
   for (int i = gw; i < d; i += nwarps) {                    // t_i = sum_{j <= i} X_ij rhs_j
     const float* xr = X + (size_t)i * d;
     float acc = 0.f;
+    if (vec) {                                              // X_ij = 0 above the diagonal
+      const float4* x4 = reinterpret_cast<const float4*>(xr);
+      const float4* v4 = reinterpret_cast<const float4*>(ia_v);
+#pragma unroll 2
+      for (int q = lane; 4 * q <= i; q += 32) {
+        const float4 xv = x4[q], vv = v4[q];
+        acc = fmaf(xv.x, vv.x, acc); acc = fmaf(xv.y, vv.y, acc);
+        acc = fmaf(xv.z, vv.z, acc); acc = fmaf(xv.w, vv.w, acc);
+      }
+    } else {
 #pragma unroll 4
-    for (int j = lane; j <= i; j += 32) acc = fmaf(xr[j], ia_v[j], acc);
+      for (int j = lane; j <= i; j += 32) acc = fmaf(xr[j], ia_v[j], acc);
+    }
     acc = warp_sum(acc);
     if (lane == 0) t[i] = (double)acc;
   }
@@ -1076,8 +1088,19 @@ __global__ void __launch_bounds__(IA_THREADS)
   for (int j = gw; j < d; j += nwarps) {                    // out_j = sum_{i >= j} X_ij t_i
     const float* xr = XC + (size_t)j * d;
     float acc = 0.f;
+    if (vec) {                                              // XC_ji = X_ij = 0 for i < j
+      const float4* x4 = reinterpret_cast<const float4*>(xr);
+      const float4* v4 = reinterpret_cast<const float4*>(ia_v);
+#pragma unroll 2
+      for (int q = (j >> 2) + lane; 4 * q < d; q += 32) {
+        const float4 xv = x4[q], vv = v4[q];
+        acc = fmaf(xv.x, vv.x, acc); acc = fmaf(xv.y, vv.y, acc);
+        acc = fmaf(xv.z, vv.z, acc); acc = fmaf(xv.w, vv.w, acc);
+      }
+    } else {
 #pragma unroll 4
-    for (int i = j + lane; i < d; i += 32) acc = fmaf(xr[i], ia_v[i], acc);
+      for (int i = j + lane; i < d; i += 32) acc = fmaf(xr[i], ia_v[i], acc);
+    }
     acc = warp_sum(acc);
     if (lane == 0) {
       const double o = (double)acc;

@@ -19,6 +19,8 @@
 // sums are combined in a fixed order, so the results are deterministic.
 // The arithmetic is exact reassociation of sum_r k_u[r] g[r] and
 // sum_u c_u k_u[r] in FP64.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tk {
@@ -396,6 +398,66 @@ __global__ void k_walk_expand(WalkArgs a, const double* base, const double* diag
   }
 }
 
+// The reduction and expansion in two wide launches.  k_walk_fold: CTA b owns
+// the segments i1 in [b C, (b + 1) C), sums each segment's piece partials in a
+// fixed order into shared memory (W_1 rows) and forms its share of the
+// expansion, part[b][r1 lsz1 + j] = sum_{its i1} A1[i1][r1] W_1[i1][j].
+// k_walk_sum: out[t] = base - diag .* y + sum_b part[b][t] in the order of b.
+__global__ void __launch_bounds__(256) k_walk_fold(WalkArgs a, int chunk, double* part) {
+  extern __shared__ double wrow[];                  // chunk x lsz1, then chunk x R1 of A1
+  const int L1 = a.lsz[1], R1 = a.R[0];
+  const int i1a = blockIdx.x * chunk;
+  const int nloc = min(chunk, a.I1 - i1a);
+  double* a1 = wrow + (size_t)chunk * L1;
+  for (int e = threadIdx.x; e < nloc * R1; e += blockDim.x) {
+    const int q = e / R1, r = e - q * R1;
+    a1[e] = a.A32[0] ? (double)__ldg(a.A32[0] + (size_t)(i1a + q) * R1 + r)
+                     : fac(a, 0, (uint32_t)(i1a + q), r);
+  }
+  for (int e = threadIdx.x; e < nloc * L1; e += blockDim.x) {
+    const int q = e / L1, j = e - q * L1;
+    const int i1 = i1a + q;
+    const int64_t p0 = a.pstart[i1], np = a.pcnt[i1];
+    const double* src = a.Wp + (size_t)p0 * L1 + j;
+    double s = 0.0;
+    int64_t k = 0;
+    for (; k + 4 <= np; k += 4) {                   // four loads in flight, summed in order
+      const double v0 = src[(size_t)k * L1], v1 = src[(size_t)(k + 1) * L1];
+      const double v2 = src[(size_t)(k + 2) * L1], v3 = src[(size_t)(k + 3) * L1];
+      s += v0; s += v1; s += v2; s += v3;
+    }
+    for (; k < np; ++k) s += src[(size_t)k * L1];
+    wrow[e] = s;
+  }
+  __syncthreads();
+  double* out = part + (size_t)blockIdx.x * a.d;
+  for (int t = threadIdx.x; t < a.d; t += blockDim.x) {
+    const int r1 = t / L1, j = t - r1 * L1;
+    double v = 0.0;
+    for (int q = 0; q < nloc; ++q) v = fma(a1[q * R1 + r1], wrow[q * L1 + j], v);
+    out[t] = v;
+  }
+}
+
+__global__ void k_walk_sum(const double* part, int nb, int d, const double* base,
+                           const double* diag, const double* y, double* out) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d; t += gridDim.x * blockDim.x) {
+    double v = 0.0;
+    int b = 0;
+    for (; b + 8 <= nb; b += 8) {                   // eight loads in flight, summed in order
+      double x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = part[(size_t)(b + q) * d + t];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v += x[q];
+    }
+    for (; b < nb; ++b) v += part[(size_t)b * d + t];
+    double o = base ? base[t] : 0.0;
+    if (diag) o -= diag[t] * y[t];
+    out[t] = o + v;
+  }
+}
+
 // ------------------------------------------------------------------ host side
 
 struct WalkGeom {
@@ -664,6 +726,21 @@ tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, const Wal
   } else {
     const size_t smem = (size_t)WK_WARPS * a.lstore * 8;
     TK_TRY(launch_by_order(h, walk_axpy_kernel(s.N), g.maxP, smem, a));
+  }
+  // segments per CTA of the fold: its partials (nb x d doubles) take the W_1 area
+  // (I1 x lsz1 doubles), so nb <= I1 / R_1
+  const int64_t nbmax = std::max<int64_t>(1, std::min<int64_t>(I1 / s.R[0], 2 * h->num_sms));
+  const int chunk = (int)((I1 + nbmax - 1) / nbmax);
+  const int nb = (int)((I1 + chunk - 1) / chunk);
+  const size_t fsm = (size_t)chunk * (a.lsz[1] + s.R[0]) * sizeof(double);
+  if (fsm <= 48 * 1024 && (size_t)nb * s.d <= (size_t)I1 * a.lsz[1]) {
+    TK_COUNT(h);
+    k_walk_fold<<<nb, 256, fsm, h->stream>>>(a, chunk, a.W1);
+    TK_LAUNCH(h);
+    TK_COUNT(h);
+    k_walk_sum<<<ceil_div(s.d, 64), 64, 0, h->stream>>>(a.W1, nb, s.d, base, diag, y, out);
+    TK_LAUNCH(h);
+    return TUCKER_OK;
   }
   TK_COUNT(h);
   k_walk_reduce<<<grid_for(h, I1 * a.lsz[1], 256), 256, 0, h->stream>>>(a);
