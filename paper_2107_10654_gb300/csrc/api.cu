@@ -796,28 +796,32 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   ev_record(h, timing, 4);
   RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
   RowSet rs64;
-  TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
   double* G = h->chol.L;
-  TK_TRY(walk_segments(h, rs, F.I[0], b.walk));
-  TK_TRY(build_gram(h, F, rs, prec, cap, b, G));
-  // the right-hand side h = K_S^T W x; when the factorisation occupies one
-  // thread-block cluster (mixed solver, small d) it runs beside it on the
-  // second stream and is joined before the solve (a grid-wide factorisation
-  // needs every SM, so there it stays in order)
+  // the FP64 factor copies, the walk tables and the right-hand side h = K_S^T W x
+  // do not depend on the Gram; when the factorisation occupies one thread-block
+  // cluster (mixed solver, small d) they run on the second stream beside the
+  // Gram and the factorisation and are joined before the solve (a grid-wide
+  // factorisation needs every SM, so there everything stays in order)
   const bool beside = h->solver == TUCKER_SOLVER_MIXED && chol32_on_cluster(h, F.d);
+  auto rhs_chain = [&]() -> tucker_status {
+    TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
+    TK_TRY(walk_segments(h, rs, F.I[0], b.walk));
+    return rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x, 1.0, nullptr,
+                     nullptr, nullptr, b.h);
+  };
   if (beside) {
     TK_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
     TK_CUDA(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
     cudaStream_t main_stream = h->stream;
     h->stream = h->aux;
-    const tucker_status st = rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x,
-                                       1.0, nullptr, nullptr, nullptr, b.h);
+    const tucker_status st = rhs_chain();
     h->stream = main_stream;
     TK_TRY(st);
     TK_CUDA(h, cudaEventRecord(h->ev_join, h->aux));
+    TK_TRY(build_gram(h, F, rs, prec, cap, b, G));
   } else {
-    TK_TRY(rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x, 1.0, nullptr,
-                     nullptr, nullptr, b.h));
+    TK_TRY(build_gram(h, F, rs, prec, cap, b, G));
+    TK_TRY(rhs_chain());
   }
   TK_TRY(launch_regdiag(h, h->chol.regdiag, F.d, lambda,
                         reg == TUCKER_REG_AUGMENTED ? b.D : nullptr));
