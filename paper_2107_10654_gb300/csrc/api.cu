@@ -32,7 +32,9 @@ tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t
                             const int* d_nu, const int64_t* d_T, const tucker_tensor* X,
                             int64_t cap, uint32_t* const* idx, double* w, double* x, double* p,
                             float* sw32, int* d_nreal, double* D, const double* p_in,
-                            double* ptab);
+                            double* ptab, bool tables_ready = false);
+tucker_status launch_prob_tables(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
+                                 double* ptab);
 tucker_status launch_cdf_from_lev(tucker_handle* h, int N, const int64_t* I,
                                   const double* const* lev, uint64_t* const* cdf);
 int gram_simt_splits(tucker_handle* h, int d, int64_t cap);
@@ -765,9 +767,23 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   const uint64_t* keys_u;
   const uint32_t* counts;
   const double* p_in = nullptr;
+  bool tables_ready = false;
   if (!fixed) {
     TK_TRY(launch_leverage(h, F, b.lev, b.cdf, b.rank, nullptr, nullptr, nullptr));
     ev_record(h, timing, 1);
+    // the gather's probability tables need only the CDFs: built on the second
+    // stream beside the sampling and the dedupe, joined before the gather
+    TK_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+    TK_CUDA(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    {
+      cudaStream_t main_stream = h->stream;
+      h->stream = h->aux;
+      const tucker_status st = launch_prob_tables(h, F, b.cdf, b.ptab);
+      h->stream = main_stream;
+      TK_TRY(st);
+    }
+    TK_CUDA(h, cudaEventRecord(h->ev_join, h->aux));
+    tables_ready = true;
     TK_TRY(sample_keys(h, F, b.cdf, m, seed, sweep, reg, X->dense ? nullptr : X, 0, b.keys_raw,
                        b.d_T, &T, ar));
     ev_record(h, timing, 2);
@@ -791,8 +807,9 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
     TK_CUDA(h, cudaStreamSynchronize(h->stream));   // host values above are stack-held
   }
   ev_record(h, timing, 3);
+  if (tables_ready) TK_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   TK_TRY(launch_gather(h, F, b.cdf, reg, keys_u, counts, b.nu, b.d_T, X, cap, b.idx, b.w, b.x,
-                       b.p, b.sw32, b.nreal, b.D, p_in, b.ptab));
+                       b.p, b.sw32, b.nreal, b.D, p_in, b.ptab, tables_ready));
   ev_record(h, timing, 4);
   RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
   RowSet rs64;

@@ -133,12 +133,36 @@ __global__ void k_gather_weights(GatherArgs a) {
   }
 }
 
+// The per-mode probability tables of the gather (they need only the CDFs, so a
+// caller may build them beside the sampling and pass tables_ready to the gather).
+tucker_status launch_prob_tables(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
+                                 double* ptab) {
+  GatherArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = F.N;
+  int64_t sumI = 0;
+  for (int n = 0; n < F.N; ++n) {
+    a.I[n] = F.I[n];
+    a.cdf[n] = cdf[n];
+    a.toff[n] = sumI;
+    sumI += F.I[n];
+  }
+  a.ftab = ptab;
+  a.rtab = ptab + sumI;
+  int tg = ceil_div(F.I[0] > 1024 ? F.I[0] : 1024, 256);
+  if (tg > h->num_sms * 4) tg = h->num_sms * 4;
+  TK_COUNT(h);
+  k_prob_tables<<<tg, 256, 0, h->stream>>>(a);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
 tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
                             int reg, const uint64_t* keys_u, const uint32_t* counts,
                             const int* d_nu, const int64_t* d_T, const tucker_tensor* X,
                             int64_t cap, uint32_t* const* idx, double* w, double* x, double* p,
                             float* sw32, int* d_nreal, double* D, const double* p_in,
-                            double* ptab) {
+                            double* ptab, bool tables_ready) {
   GatherArgs a;
   memset(&a, 0, sizeof(a));
   a.N = F.N;
@@ -168,11 +192,7 @@ tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t
     for (int n = 0; n < F.N; ++n) { a.toff[n] = sumI; sumI += F.I[n]; }
     a.ftab = ptab;
     a.rtab = ptab + sumI;
-    int tg = ceil_div(F.I[0] > 1024 ? F.I[0] : 1024, 256);
-    if (tg > h->num_sms * 4) tg = h->num_sms * 4;
-    TK_COUNT(h);
-    k_prob_tables<<<tg, 256, 0, h->stream>>>(a);
-    TK_LAUNCH(h);
+    if (!tables_ready) TK_TRY(launch_prob_tables(h, F, cdf, ptab));
   }
   int grid = ceil_div(cap, 256);
   if (grid > h->num_sms * 16) grid = h->num_sms * 16;

@@ -30,7 +30,7 @@ tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t
                             const int* d_nu, const int64_t* d_T, const tucker_tensor* X,
                             int64_t cap, uint32_t* const* idx, double* w, double* x, double* p,
                             float* sw32, int* d_nreal, double* D, const double* p_in,
-                            double* ptab);
+                            double* ptab, bool tables_ready = false);
 
 // The shared scratch.  Host code must not pass this symbol to a kernel: in
 // host code it is only a stand-in, so its device address is looked up with
