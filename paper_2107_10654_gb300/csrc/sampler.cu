@@ -39,6 +39,9 @@ struct SampleArgs {
   const uint32_t* guide;              // nullable; modes concatenated
   int64_t gofs[TUCKER_MAX_ORDER];
   int kbits[TUCKER_MAX_ORDER];
+  int items;                          // consecutive draws per thread (<= SAMPLE_ITEMS)
+  int64_t* T_out;                     // nullable: receives T_val (dense mode: T = m)
+  int64_t T_val;
 };
 
 __global__ void k_guide(SampleArgs a, uint32_t* guide) {
@@ -109,13 +112,14 @@ __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(SampleArgs a) {
   } else {
     for (int n = 0; n < a.N; ++n) C[n] = a.cdf[n];
   }
-  const int64_t base = (int64_t)blockIdx.x * SAMPLE_THREADS * SAMPLE_ITEMS +
-                       (int64_t)threadIdx.x * SAMPLE_ITEMS;
+  if (a.T_out && blockIdx.x == 0 && threadIdx.x == 0) *a.T_out = a.T_val;
+  const int64_t base = (int64_t)blockIdx.x * SAMPLE_THREADS * a.items +
+                       (int64_t)threadIdx.x * a.items;
   int nacc = 0;
 #pragma unroll
   for (int j = 0; j < SAMPLE_ITEMS; ++j) {
     int64_t e = base + j;
-    if (e >= a.count) break;
+    if (j >= a.items || e >= a.count) break;
     uint64_t key = draw_key(a, C, guided ? Gd : nullptr, (uint64_t)(a.t0 + e));
     a.keys_out[e] = key;
     if (a.slot_key) {
@@ -305,14 +309,18 @@ tucker_status sample_keys(tucker_handle* h, const FactorSet& F, const uint64_t* 
   }
   TK_CUDA(h, cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int per_block = SAMPLE_THREADS * SAMPLE_ITEMS;
+  a.items = SAMPLE_ITEMS;
   if (!observed) {
+    // one draw per thread until there are enough draws to fill every SM four times
+    a.items = m >= (int64_t)h->num_sms * SAMPLE_THREADS * SAMPLE_ITEMS ? SAMPLE_ITEMS : 1;
     a.t0 = 0;
     a.count = m;
     a.keys_out = keys_out;
+    a.T_out = d_T;                          // T = m, written by the kernel
+    a.T_val = m;
     TK_COUNT(h);
-    k_sample<<<ceil_div(m, per_block), SAMPLE_THREADS, smem, h->stream>>>(a);
+    k_sample<<<ceil_div(m, (int64_t)SAMPLE_THREADS * a.items), SAMPLE_THREADS, smem, h->stream>>>(a);
     TK_LAUNCH(h);
-    TK_CUDA(h, cudaMemcpyAsync(d_T, &m, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
     *T_host = m;
     return TUCKER_OK;
   }
