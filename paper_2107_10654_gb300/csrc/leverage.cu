@@ -24,21 +24,25 @@ struct LevArgs {
   int* status;
   double* gpart[TUCKER_MAX_ORDER];    // [nchunk][R(R+1)/2] partial Grams
   int nchunk;
+  int rows_per;                       // factor rows per partial Gram
+  double* W[TUCKER_MAX_ORDER];        // R x R outputs of k_leverage_eig
 };
 
 // Partial Gram of rows [chunk * rows_per, ...) of every mode (grid: chunk x mode).
 // Row tile staged in shared memory as FP64; thread -> (pair, row phase), then
 // a fixed-order reduction over the phases.
-constexpr int GP_ROWS = 256;
+// Rows per partial Gram: small factors are cut finer so that more CTAs share them.
+static int gram_rows_per(int64_t maxI) { return maxI <= 8192 ? 64 : 256; }
 __global__ void __launch_bounds__(256) k_gram_partial(LevArgs a) {
-  extern __shared__ double st[];                      // GP_ROWS x R, then 256 partials
+  extern __shared__ double st[];                      // rows_per x R, then 256 partials
   const int n = blockIdx.y, ch = blockIdx.x;
   const int R = a.F.R[n];
   const int64_t I = a.F.I[n];
-  const int64_t i0 = (int64_t)ch * GP_ROWS;
+  const int RP = a.rows_per;
+  const int64_t i0 = (int64_t)ch * RP;
   const int npairs = R * (R + 1) / 2;
-  double* red = st + GP_ROWS * R;
-  const int rows = (int)(i0 < I ? ((I - i0) < GP_ROWS ? (I - i0) : GP_ROWS) : 0);
+  double* red = st + RP * R;
+  const int rows = (int)(i0 < I ? ((I - i0) < RP ? (I - i0) : RP) : 0);
   for (int e = threadIdx.x; e < rows * R; e += blockDim.x)
     st[e] = load_as_double(a.F.A[n], i0 * R + e, a.F.is64);
   __syncthreads();
@@ -73,7 +77,8 @@ constexpr int LEV_PAIRS_PER_THREAD = (64 * 65 / 2 + LEV_THREADS - 1) / LEV_THREA
 // Per mode: Gram (all warps), Jacobi eigendecomposition (warp 0, warp-
 // synchronous), and W = V diag(ev^-1/2) with the columns of eigenvalues
 // <= tol zeroed, so that l_i = || a_i W ||^2 = a_i G^+ a_i^T.
-__global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a, double* const* Wout) {
+__global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a) {
+  double* const* Wout = a.W;
   extern __shared__ double sm[];
   const int n = blockIdx.x;
   const int R = a.F.R[n];
@@ -362,16 +367,17 @@ tucker_status launch_leverage(tucker_handle* h, const FactorSet& F, double* cons
     W[n] = Wbuf + (size_t)n * TUCKER_MAX_RANK * TUCKER_MAX_RANK;
     ra.I[n] = F.I[n]; ra.R[n] = F.R[n]; ra.A[n] = F.A[n]; ra.W[n] = W[n]; ra.lev[n] = lev[n];
   }
+  for (int n = 0; n < F.N; ++n) a.W[n] = W[n];             // by value: no host copy
   double** Wdev = reinterpret_cast<double**>(Wbuf + (size_t)TUCKER_MAX_ORDER * TUCKER_MAX_RANK * TUCKER_MAX_RANK);
-  TK_CUDA(h, cudaMemcpyAsync(Wdev, W, sizeof(W), cudaMemcpyHostToDevice, h->stream));
   // partial Grams behind the W matrices
   double* gp = reinterpret_cast<double*>(Wdev + TUCKER_MAX_ORDER);
-  a.nchunk = (int)((maxI + GP_ROWS - 1) / GP_ROWS);
+  a.rows_per = gram_rows_per(maxI);
+  a.nchunk = (int)((maxI + a.rows_per - 1) / a.rows_per);
   for (int n = 0; n < F.N; ++n) {
     a.gpart[n] = gp;
     gp += (size_t)a.nchunk * (F.R[n] * (F.R[n] + 1) / 2);
   }
-  const size_t gsm = (size_t)(GP_ROWS * maxR + 256) * sizeof(double);
+  const size_t gsm = (size_t)(a.rows_per * maxR + 256) * sizeof(double);
   TK_CUDA(h, cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)gsm));
   TK_COUNT(h);
@@ -382,7 +388,7 @@ tucker_status launch_leverage(tucker_handle* h, const FactorSet& F, double* cons
   TK_CUDA(h, cudaFuncSetAttribute(k_leverage_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
   TK_COUNT(h);
-  k_leverage_eig<<<F.N, LEV_THREADS, smem, h->stream>>>(a, Wdev);
+  k_leverage_eig<<<F.N, LEV_THREADS, smem, h->stream>>>(a);
   TK_LAUNCH(h);
   int gx = (int)((maxI + 255) / 256);
   if (gx > 64) gx = 64;
@@ -394,7 +400,8 @@ tucker_status launch_leverage(tucker_handle* h, const FactorSet& F, double* cons
 
 // Device bytes the leverage launcher needs behind its rank pointer.
 size_t leverage_aux_bytes(int64_t maxI) {
-  const size_t nchunk = (size_t)((maxI + GP_ROWS - 1) / GP_ROWS);
+  const int rp = gram_rows_per(maxI);
+  const size_t nchunk = (size_t)((maxI + rp - 1) / rp);
   return (2 * TUCKER_MAX_ORDER + 64) * sizeof(int) + 256 +
          (size_t)TUCKER_MAX_ORDER * TUCKER_MAX_RANK * TUCKER_MAX_RANK * sizeof(double) +
          TUCKER_MAX_ORDER * sizeof(double*) + 64 +
