@@ -230,11 +230,23 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(w, "fp64", args.reg),
+            "data": "synthetic",
+            # the same workload configuration as the GPU arm; the oracle itself computes
+            # in FP64 (explicit sampled rows, FP64 Cholesky)
+            "config": workload_config(w, ours_prec(args), args.reg, args.solver),
+            "oracle_arithmetic": "fp64",
             "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def ours_prec(args):
+    """Gram precision of the GPU arm (the same choice main() makes)."""
+    prec = args.prec
+    if prec == "auto":
+        prec = os.environ.get("TUCKER_BENCH_PREC", "bf16")
+    return prec
 
 
 def workload_config(w, prec, reg, solver="fp64"):
@@ -310,9 +322,7 @@ def main():
     torch.cuda.set_device(dev)
 
     w = synth.WORKLOADS[args.workload]
-    prec = args.prec
-    if prec == "auto":
-        prec = os.environ.get("TUCKER_BENCH_PREC", "bf16")
+    prec = ours_prec(args)
     missing = w.observed < 1.0
     if missing:
         O = synth.observed_entries(w)
