@@ -1014,22 +1014,6 @@ __global__ void __launch_bounds__(INV_THREADS) k_tri_inv_cols(const float* L, co
   }
 }
 
-// out_i = sum_j A[i][j] v_j over the lower (tri_lower) or upper part of a
-// row-major FP32 matrix, FP64 vectors; one warp per row.
-__global__ void k_gemv_tri(const float* A, int d, const double* v, double* out, int lower) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int i = warp; i < d; i += nwarps) {
-    const float* ar = A + (size_t)i * d;
-    const int j0 = lower ? 0 : i, j1 = lower ? i + 1 : d;
-    float acc = 0.f;
-    for (int j = j0 + lane; j < j1; j += 32) acc = fmaf(ar[j], (float)v[j], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) out[i] = (double)acc;
-  }
-}
-
 tucker_status chol_inverse32(tucker_handle* h, const float* L, const float* Linv, int d, float* X,
                              float* XC) {
   if (d > INV_MAX_D || !X || !XC) return fail(h, TUCKER_EINTERNAL, "explicit inverse not sized");
@@ -1043,7 +1027,7 @@ tucker_status chol_inverse32(tucker_handle* h, const float* L, const float* Linv
 int chol_inverse_fits(int d) { return d <= INV_MAX_D; }
 
 // out = X^T (X rhs) in one cooperative launch: each warp forms rows of
-// t = X rhs (the same per-row FP32 arithmetic as k_gemv_tri, rhs staged in
+// t = X rhs (FP32 products and sums, one warp per row, rhs staged in
 // shared memory as FP32), a grid barrier, then rows of X^T t from the
 // column-major copy XC.  With upd given, also upd += out and
 // stats = (sum out_i^2, sum upd_i^2): partial sums per warp and per CTA,

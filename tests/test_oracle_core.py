@@ -253,3 +253,28 @@ def test_sampled_row_products_equal_explicit_rows():
     assert np.allclose(CU.sampled_rows_apply(F, idx, v, chunk=7), K @ v, rtol=1e-13, atol=1e-13)
     assert np.allclose(CU.sampled_rows_apply_t(F, idx, c, chunk=7), K.T @ c, rtol=1e-13, atol=1e-13)
 
+
+
+def test_gram_regrouped_by_leading_index():
+    """The sampled Gram regrouped by the leading index (the structure of the
+    Kronecker rows, Sec. 4): with k_u = a_1(u) (x) b_u, b_u = a_2 (x) ... (x) a_N,
+    sum_u w_u k_u k_u^T = sum_{i_1} (a_1 a_1^T) (x) M_{i_1},
+    M_{i_1} = sum_{u: i_1(u) = i_1} w_u b_u b_u^T (row-major vec, r_1 outermost)."""
+    g = np.random.default_rng(9)
+    dims, ranks = (6, 5, 4), (3, 2, 2)
+    F = [g.standard_normal((i, r)) for i, r in zip(dims, ranks)]
+    keys = np.sort(g.choice(int(np.prod(dims)), 40, replace=False)).astype(np.uint64)
+    w = g.random(keys.size) + 0.5
+    idx = S.decode_keys(keys, dims)
+    K = CU.kron_matrix(F)[keys.astype(np.int64)]
+    G = K.T @ (K * w[:, None])
+    d1 = ranks[1] * ranks[2]
+    Gr = np.zeros_like(G)
+    for i1 in np.unique(idx[0]):
+        sel = idx[0] == i1
+        B = np.stack([np.kron(F[1][a], F[2][b]) for a, b in zip(idx[1][sel], idx[2][sel])])
+        M = B.T @ (B * w[sel][:, None])
+        a1 = F[0][i1]
+        Gr += np.kron(np.outer(a1, a1), M)
+    assert M.shape == (d1, d1)
+    assert np.allclose(Gr, G, rtol=1e-12, atol=1e-12)
