@@ -73,7 +73,10 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
  * implicit rows.  With c_k = ||correction_k|| / ||g|| (c_0 = 1) and the
  * contraction estimate rho = min(c_k / c_{k-1}, 1/2), the iteration stops once
  * the estimated remaining relative error c_k rho / (1 - rho) is below 1e-8, or
- * when the corrections stop shrinking, at most 8 iterations. */
+ * when the corrections stop shrinking, at most 8 iterations.  With a TF32 or
+ * BF16 Gram at least two corrections are always made; when the factors are
+ * FP32 the first of them evaluates its residual in FP32 (it only has to be as
+ * accurate as the Gram's rounding), every later one in FP64. */
 typedef enum {
   TUCKER_PREC_FP64 = 0,   /* FP64 CUDA-core Gram; no refinement needed */
   TUCKER_PREC_FP32 = 1,   /* FP32 CUDA-core Gram, FP64 refinement */
@@ -96,7 +99,8 @@ typedef enum {
  *                  at most 12 iterations.  It converges when kappa(M) * 2^-24 is
  *                  well below 1; lambda > 0 keeps kappa(M) <= (||G|| +
  *                  lambda)/lambda.  A matrix that FP32 cannot factor (a
- *                  pivot <= 0 after rounding) returns TUCKER_ENOTSPD. */
+ *                  pivot <= 0 after rounding, or below the smallest normal
+ *                  FP32 value) returns TUCKER_ENOTSPD. */
 typedef enum {
   TUCKER_SOLVER_FP64_CHOLESKY = 0,
   TUCKER_SOLVER_MIXED = 1
