@@ -241,6 +241,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def grouped_gram(w):
+    """Whether the library groups the tensor-core Gram by the leading index (the
+    same test as the library's: order >= 3, R_1 a power of two <= 16, d / R_1 >= 128,
+    at most 8192 (segment, tile) pairs, A^(1) within 200 KB as FP32)."""
+    R1, N = w.ranks[0], len(w.ranks)
+    if N < 3 or R1 > 16 or R1 & (R1 - 1) or w.d % R1:
+        return False
+    dp = w.d // R1
+    tiles = (dp + 255) // 256
+    I1 = w.dims[0]
+    return dp >= 128 and I1 * tiles * (tiles + 1) // 2 <= 8192 and I1 * R1 * 4 <= 200 * 1024
+
+
 def ours_prec(args):
     """Gram precision of the GPU arm (the same choice main() makes)."""
     prec = args.prec
@@ -492,12 +505,17 @@ def main():
     traffic_tab = load_traffic()
 
     def gram_roofline():
-        # n_u d (d + 1) flop for the symmetric product plus 2 n_u d for the row build
+        # n_u d (d + 1) flop for the symmetric product plus 2 n_u d for the row build;
+        # grouped by the leading index the tensor cores form n_u d' (d' + 1), d' = d / R_1
         flops = n_real * d * (d + 1) + 2 * n_real * d
+        grouped = prec in ("bf16", "tf32") and grouped_gram(w)
+        if grouped:
+            dp = d // w.ranks[0]
+            flops = n_real * dp * (dp + 1) + 2 * n_real * dp
         if prec in ("bf16", "tf32"):
             peak = pk["bf16_tflops"] * TC_RATIO[prec]
             bound, note = "tensor", f"{prec} tcgen05: {src} bf16 burst x {TC_RATIO[prec]}"
-            kernel = f"k_syrk_tc<{prec}>"
+            kernel = f"k_syrk_tc<{prec}>" + (" grouped by i_1" if grouped else "")
         elif prec == "fp32":
             peak = 152 * 128 * 2 * 2.07
             bound, note, kernel = "alu", "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz", "k_syrk_simt<float>"

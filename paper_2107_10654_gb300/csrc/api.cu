@@ -102,7 +102,11 @@ bool walk_f32_ok(const RowSet& s);
 tucker_status launch_decode_rows(tucker_handle* h, const FactorSet& F, const uint64_t* keys,
                                  int64_t n, uint32_t* const* idx, const void* vals, double* x);
 int gram_tc_supported(int prec, int d);
-size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int sumR, int64_t cap);
+size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int sumR, int64_t cap, int N, int R1,
+                         int64_t I1);
+int gram_tc_grouped_ok(int N, int d, int R1, int64_t I1);
+tucker_status launch_gram_tc_grouped(tucker_handle* h, const RowSet& s, int prec, int64_t cap,
+                                     int64_t I1, char* ws, size_t ws_bytes, double* G);
 tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_t cap, char* ws,
                              size_t ws_bytes, double* G);
 
@@ -332,7 +336,7 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
   int sumR = 0;
   for (int n = 0; n < F.N; ++n) sumR += F.R[n];
   if (prec == TUCKER_PREC_TF32 || prec == TUCKER_PREC_BF16)
-    b->gram_bytes = gram_tc_workspace(h, prec, F.d, sumR, m);
+    b->gram_bytes = gram_tc_workspace(h, prec, F.d, sumR, m, F.N, F.R[0], F.I[0]);
   else
     b->gram_bytes = gram_simt_partial_bytes(F.d, b->simt_split, prec == TUCKER_PREC_FP64);
   b->gram_ws = ar.get<char>(b->gram_bytes);
@@ -444,6 +448,9 @@ static tucker_status build_gram(tucker_handle* h, const FactorSet& F, const RowS
     return launch_gram_simt(h, rs, prec == TUCKER_PREC_FP64, b.simt_split, b.gram_ws, G);
   if (!gram_tc_supported(prec, F.d))
     return fail(h, TUCKER_ENOTSUP, "tensor-core Gram does not support d = %d", F.d);
+  // sorted sample: group the Gram by the leading index when that is the smaller job
+  if (gram_tc_grouped_ok(F.N, F.d, F.R[0], F.I[0]))
+    return launch_gram_tc_grouped(h, rs, prec, cap, F.I[0], b.gram_ws, b.gram_bytes, G);
   return launch_gram_tc(h, rs, prec, cap, b.gram_ws, b.gram_bytes, G);
 }
 

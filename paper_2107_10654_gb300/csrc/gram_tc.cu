@@ -84,6 +84,8 @@ struct TcArgs {
   const int* n_rows;
   float* partial;                      // [nsplit][ntiles][256][256]
   int* status;
+  const int* cstart;                   // nullable: first chunk of each split (grouped Gram)
+  const int* ccount;                   // chunks of each split
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -231,7 +233,6 @@ __global__ void k_tc_pack(PackArgs a) {
   }
 }
 
-// --------------------------------------------------------------- the SYRK
 __device__ __forceinline__ void tile_of(int tile, int Tt, int* ti, int* tj) {
   // upper tiles (ti <= tj), column-major packed: tile = tj (tj + 1) / 2 + ti
   int j = (int)((sqrtf(8.0f * tile + 1.0f) - 1.0f) * 0.5f);
@@ -240,6 +241,133 @@ __device__ __forceinline__ void tile_of(int tile, int Tt, int* ti, int* tj) {
   *tj = j;
   *ti = tile - j * (j + 1) / 2;
 }
+
+// ------------------------------------------ Gram grouped by the leading index
+// With the sample sorted by key, rows of one i_1 are contiguous and
+//   G = sum_u w_u k_u k_u^T = sum_{i_1} (a a^T) (x) M_{i_1},  a = A^(1)[i_1],
+//   M_{i_1} = sum_{u: i_1(u) = i_1} w_u b_u b_u^T,  b_u = a_2 (x) ... (x) a_N
+// (k_u = a (x) b_u, row-major vec with r_1 outermost).  The tensor-core kernel
+// forms every M_{i_1} as its own split (operands from modes 2..N, d / R_1
+// wide; each segment padded to whole chunks with zero rows), and a reduction
+// forms G_{(r1,j),(r1',j')} = sum_{i_1} a_{r1} a_{r1'} M_{i_1}[j][j'].  The
+// tensor-core work falls by R_1^2 for the price of the reduction's
+// (d / R_1)^2 / 2 x I_1 x R_1^2 FP32 multiply-adds.
+
+// Segment table of the sorted rows (seg_begin / seg_end zeroed beforehand).
+__global__ void k_tcg_segments(const uint32_t* idx0, const int* n_rows, int* seg_begin,
+                               int* seg_end) {
+  const int n = *n_rows;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+    const uint32_t v = idx0[u];
+    if (u == 0 || idx0[u - 1] != v) seg_begin[v] = u;
+    if (u == n - 1 || idx0[u + 1] != v) seg_end[v] = u + 1;
+  }
+}
+
+// Chunks per segment, their exclusive prefix sum and the chunk -> segment map
+// (one CTA; I_1 is bounded by the caller).
+__global__ void __launch_bounds__(1024) k_tcg_chunks(const int* seg_begin, const int* seg_end,
+                                                      int I1, int CS, int* cstart, int* ccount,
+                                                      int* cseg) {
+  __shared__ int64_t tmp[32];
+  int64_t carry = 0;
+  for (int base = 0; base < I1; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int c = i < I1 ? (seg_end[i] - seg_begin[i] + CS - 1) / CS : 0;
+    int64_t tot;
+    const int64_t ex = block_exclusive_scan(c, tmp, &tot);
+    if (i < I1) {
+      cstart[i] = (int)(carry + ex);
+      ccount[i] = c;
+      for (int k = 0; k < c; ++k) cseg[carry + ex + k] = i;
+    }
+    carry += tot;
+  }
+}
+
+// Operand table of the grouped Gram: chunk c of segment i_1 holds rows
+// seg_begin + (c - cstart) CS + s (zero past the segment), modes 2..N, sqrt(w)
+// folded into mode 2.  nch_max bounds the chunk count (the rest is not read).
+__global__ void k_tc_pack_grouped(PackArgs a, const int* seg_begin, const int* seg_end,
+                                  const int* cstart, const int* cseg, int nch_max) {
+  const int nrow_total = nch_max * a.sumR;
+  const int per_cta = blockDim.x / a.CS;
+  const int s = threadIdx.x % a.CS;
+  for (int row = blockIdx.x * per_cta + threadIdx.x / a.CS; row < nrow_total;
+       row += gridDim.x * per_cta) {
+    const int q = row / a.sumR, e = row - q * a.sumR;
+    const int i1 = cseg[q];
+    float v = 0.f;
+    if (i1 >= 0) {
+      const int64_t u = (int64_t)seg_begin[i1] + (int64_t)(q - cstart[i1]) * a.CS + s;
+      if (u < seg_end[i1]) {
+        int n = 0;
+        while (n + 1 < a.N && e >= a.off[n + 1]) ++n;
+        const int r = e - a.off[n];
+        const float f = (float)load_as_double(a.A[n], (int64_t)a.idx[n][u] * a.R[n] + r, a.is64);
+        v = n == 0 ? sqrtf((float)a.w[u]) * f : f;
+      }
+    }
+    a.pack[(int64_t)row * a.CS + pack_pos(s, a.perm)] = v;
+  }
+}
+
+// G_{(r1,j),(r1',j')} = sum_{i_1} a_{r1} a_{r1'} M_{i_1}[j][j'] for j <= j' of the
+// tiles of M (upper instances), r1 in this block's group of RB rows; written to
+// the four symmetric places (two when j = j').  FP32 sums over i_1 (the Gram's
+// operands are BF16/TF32), FP64 out.
+template <int R1, int RB>
+__global__ void __launch_bounds__(256) k_tc_reduce_grouped(const float* partial, int I1, int ntiles,
+                                                           int Tt, int dp, const void* A1, int is64,
+                                                           int d, double* G) {
+  extern __shared__ float a1s[];                   // A^(1) in FP32, staged once per CTA
+  int ti, tj;
+  tile_of(blockIdx.y, Tt, &ti, &tj);
+  const int rb0 = blockIdx.z * RB;
+  for (int e = threadIdx.x; e < I1 * R1; e += blockDim.x) a1s[e] = (float)load_as_double(A1, e, is64);
+  __syncthreads();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = ti * TC_TILE + e / TC_TILE, jp = tj * TC_TILE + e % TC_TILE;
+  const bool act = e < TC_TILE * TC_TILE && j < dp && jp < dp && j <= jp;
+  if (!act) return;                                // no barrier below
+  float acc[RB][R1];
+#pragma unroll
+  for (int r = 0; r < RB; ++r)
+#pragma unroll
+    for (int q = 0; q < R1; ++q) acc[r][q] = 0.f;
+  const size_t stride = (size_t)ntiles * (TC_TILE * TC_TILE);
+  const float* src = partial + (size_t)blockIdx.y * (TC_TILE * TC_TILE) + e;
+  for (int i1 = 0; i1 < I1; ++i1) {
+    const float m = src[(size_t)i1 * stride];
+    const float* ai = a1s + i1 * R1;
+    // (a_r1 a_q) m: the same value for (r1, q) and (q, r1), so the entries that
+    // two threads both write get identical bits
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const float ar = ai[rb0 + r];
+#pragma unroll
+      for (int q = 0; q < R1; ++q) acc[r][q] = fmaf(ar * ai[q], m, acc[r][q]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    const int r1 = rb0 + r;
+#pragma unroll
+    for (int q = 0; q < R1; ++q) {
+      const double v = (double)acc[r][q];
+      const size_t A = (size_t)r1 * dp + j, B = (size_t)q * dp + jp;
+      G[A * d + B] = v;
+      G[B * d + A] = v;
+      if (j != jp) {
+        const size_t C = (size_t)r1 * dp + jp, D = (size_t)q * dp + j;
+        G[C * d + D] = v;
+        G[D * d + C] = v;
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------- the SYRK
 
 template <int PREC>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
@@ -264,9 +392,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_syrk_tc(TcArgs a) {
   tile_of(blockIdx.x % a.ntiles, a.Tt, &ti, &tj);
   const int split = blockIdx.x / a.ntiles;
   const int nrows = *a.n_rows;
-  const int nch = (nrows + CS - 1) / CS;
-  const int cps = (nch + a.nsplit - 1) / a.nsplit;
-  const int c0 = split * cps, c1 = min(nch, c0 + cps);
+  int c0, c1;
+  if (a.cstart) {                                 // grouped Gram: one split per leading index
+    c0 = a.cstart[split];
+    c1 = c0 + a.ccount[split];
+  } else {
+    const int nch = (nrows + CS - 1) / CS;
+    const int cps = (nch + a.nsplit - 1) / a.nsplit;
+    c0 = split * cps;
+    c1 = min(nch, c0 + cps);
+  }
   const int nchunks = max(0, c1 - c0);
   const int row0 = ti * TC_TILE, col0 = tj * TC_TILE;
   const bool diag = ti == tj;                     // A rows are the B rows
@@ -590,14 +725,147 @@ static size_t tc_smem_bytes(int sumR, int CS, int tstages) {
   return ops + tab + runs + 1024;
 }
 
-size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int sumR, int64_t cap) {
+// Whether the leading-index-grouped Gram applies: order >= 3, R_1 in {1, 2, 4,
+// 8, 16}, d / R_1 >= 128, and at most 8192 (segment, tile) splits of FP32
+// partial tiles.
+int gram_tc_grouped_ok(int N, int d, int R1, int64_t I1) {
+  if (N < 3 || R1 < 1 || R1 > 16 || (R1 & (R1 - 1)) || d % R1) return 0;
+  const int dp = d / R1;
+  if (dp < 128) return 0;
+  int Tt;
+  const int nt = tiles_of(dp, &Tt);
+  return I1 >= 1 && I1 * nt <= 8192 && I1 * R1 * 4 <= 200 * 1024;   // A^(1) staged in the reduction
+}
+
+static size_t gram_tc_grouped_bytes(int prec, int d, int sumR, int R1, int64_t I1, int64_t cap) {
+  const int dp = d / R1;
+  int Tt;
+  const int nt = tiles_of(dp, &Tt);
+  const int CS = chunk_samples(prec);
+  const int64_t nchm = (cap + CS - 1) / CS + I1;
+  return (size_t)nchm * CS * (sumR - R1) * 4 + 4096 + (size_t)I1 * nt * TC_TILE * TC_TILE * 4 +
+         4096 + (size_t)(4 * I1 + nchm) * 4 + 4096;
+}
+
+size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int sumR, int64_t cap, int N, int R1,
+                         int64_t I1) {
   int Tt;
   const int ntiles = tiles_of(d, &Tt);
   const int CS = chunk_samples(prec);
   const int64_t nch = (cap + CS - 1) / CS;
   const int ns = pick_splits(ntiles, nch, h->num_sms);
   // pack (sum R_n entries per sample) + partial tiles
-  return (size_t)nch * CS * sumR * 4 + 4096 + (size_t)ns * ntiles * TC_TILE * TC_TILE * 4 + 4096;
+  size_t b = (size_t)nch * CS * sumR * 4 + 4096 + (size_t)ns * ntiles * TC_TILE * TC_TILE * 4 + 4096;
+  if (gram_tc_grouped_ok(N, d, R1, I1))
+    b = std::max(b, gram_tc_grouped_bytes(prec, d, sumR, R1, I1, cap));
+  return b;
+}
+
+template <int R1, int RB>
+static void launch_reduce_grouped(tucker_handle* h, const float* partial, int I1, int ntiles,
+                                  int Tt, int dp, const void* A1, int is64, int d, double* G) {
+  const size_t smem = (size_t)I1 * R1 * sizeof(float);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute((const void*)k_tc_reduce_grouped<R1, RB>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_tc_reduce_grouped<R1, RB><<<dim3(TC_TILE * TC_TILE / 256, ntiles, R1 / RB), 256,
+                                 (size_t)I1 * R1 * sizeof(float), h->stream>>>(
+      partial, I1, ntiles, Tt, dp, A1, is64, d, G);
+}
+
+// The Gram grouped by the leading index (sorted sample, s.idx[0] non-decreasing).
+tucker_status launch_gram_tc_grouped(tucker_handle* h, const RowSet& s, int prec, int64_t cap,
+                                     int64_t I1, char* ws, size_t ws_bytes, double* G) {
+  const int R1 = s.R[0], dp = s.d / R1;
+  int Tt;
+  const int ntiles = tiles_of(dp, &Tt);
+  const int CS = chunk_samples(prec);
+  const int64_t nchm = (cap + CS - 1) / CS + I1;
+  int sumR = 0;
+  for (int n = 0; n < s.N; ++n) sumR += s.R[n];
+  const int sumRp = sumR - R1;
+  if (gram_tc_grouped_bytes(prec, s.d, sumR, R1, I1, cap) > ws_bytes)
+    return fail(h, TUCKER_EINTERNAL, "grouped tc workspace too small");
+  if ((size_t)sumRp * CS * 4 % 16 != 0) return fail(h, TUCKER_EINTERNAL, "pack block not 16-byte sized");
+  if (nchm * sumRp >= (int64_t)1 << 31)
+    return fail(h, TUCKER_ENOTSUP, "tensor-core Gram of %lld rows too large", (long long)cap);
+  const size_t pack_bytes = (size_t)nchm * sumRp * CS * 4;
+  float* pack = reinterpret_cast<float*>(ws);
+  char* q = ws + ((pack_bytes + 255) & ~size_t(255));
+  float* partial = reinterpret_cast<float*>(q);
+  q += ((size_t)I1 * ntiles * TC_TILE * TC_TILE * 4 + 255) & ~size_t(255);
+  int* seg_begin = reinterpret_cast<int*>(q);
+  int* seg_end = seg_begin + I1;
+  int* cstart = seg_end + I1;
+  int* ccount = cstart + I1;
+  int* cseg = ccount + I1;
+  TK_CUDA(h, cudaMemsetAsync(seg_begin, 0, sizeof(int) * 2 * I1, h->stream));
+  TK_CUDA(h, cudaMemsetAsync(cseg, 0xff, sizeof(int) * nchm, h->stream));
+  int gs = (int)std::min<int64_t>((cap + 255) / 256, (int64_t)h->num_sms * 8);
+  if (gs < 1) gs = 1;
+  TK_COUNT(h);
+  k_tcg_segments<<<gs, 256, 0, h->stream>>>(s.idx[0], s.n_rows, seg_begin, seg_end);
+  TK_LAUNCH(h);
+  TK_COUNT(h);
+  k_tcg_chunks<<<1, 1024, 0, h->stream>>>(seg_begin, seg_end, (int)I1, CS, cstart, ccount, cseg);
+  TK_LAUNCH(h);
+  PackArgs p;
+  memset(&p, 0, sizeof(p));
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = p.N = s.N - 1;
+  int off = 0;
+  for (int n = 1; n < s.N; ++n) {
+    a.R[n - 1] = p.R[n - 1] = s.R[n];
+    a.off[n - 1] = p.off[n - 1] = off;
+    off += s.R[n];
+    p.A[n - 1] = s.A[n];
+    p.idx[n - 1] = s.idx[n];
+  }
+  a.sumR = p.sumR = sumRp;
+  p.is64 = s.is64;
+  p.w = s.w;
+  p.n_rows = s.n_rows;
+  p.CS = CS;
+  p.perm = prec == TUCKER_PREC_BF16;
+  p.pack = pack;
+  int pg = (int)std::min<int64_t>((nchm * sumRp * CS + 255) / 256, (int64_t)h->num_sms * 16);
+  if (pg < 1) pg = 1;
+  TK_COUNT(h);
+  k_tc_pack_grouped<<<pg, 256, 0, h->stream>>>(p, seg_begin, seg_end, cstart, cseg, (int)nchm);
+  TK_LAUNCH(h);
+  a.d = dp;
+  a.Tt = Tt;
+  a.ntiles = ntiles;
+  a.nsplit = (int)I1;
+  a.n_rows = s.n_rows;
+  a.status = h->d_status;
+  a.pack = pack;
+  a.partial = partial;
+  a.cstart = cstart;
+  a.ccount = ccount;
+  int tst = 4;
+  while (tst > 2 && tc_smem_bytes(sumRp, CS, tst) > 227 * 1024) --tst;
+  const size_t smem = tc_smem_bytes(sumRp, CS, tst);
+  if (smem > 227 * 1024) return fail(h, TUCKER_ENOTSUP, "grouped tensor-core Gram: shared memory");
+  a.tstages = tst;
+  auto kern = prec == TUCKER_PREC_BF16 ? k_syrk_tc<TUCKER_PREC_BF16> : k_syrk_tc<TUCKER_PREC_TF32>;
+  TK_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (h->timing) cudaEventRecord(h->ev[10], h->stream);
+  TK_COUNT(h);
+  kern<<<(int)(ntiles * I1), TC_THREADS, smem, h->stream>>>(a);
+  TK_LAUNCH(h);
+  if (h->timing) cudaEventRecord(h->ev[11], h->stream);
+  TK_COUNT(h);
+  switch (R1) {
+    case 1: launch_reduce_grouped<1, 1>(h, partial, (int)I1, ntiles, Tt, dp, s.A[0], s.is64, s.d, G); break;
+    case 2: launch_reduce_grouped<2, 2>(h, partial, (int)I1, ntiles, Tt, dp, s.A[0], s.is64, s.d, G); break;
+    case 4: launch_reduce_grouped<4, 4>(h, partial, (int)I1, ntiles, Tt, dp, s.A[0], s.is64, s.d, G); break;
+    case 8: launch_reduce_grouped<8, 8>(h, partial, (int)I1, ntiles, Tt, dp, s.A[0], s.is64, s.d, G); break;
+    default: launch_reduce_grouped<16, 4>(h, partial, (int)I1, ntiles, Tt, dp, s.A[0], s.is64, s.d, G); break;
+  }
+  TK_LAUNCH(h);
+  return TUCKER_OK;
 }
 
 tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_t cap, char* ws,

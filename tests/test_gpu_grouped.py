@@ -1,0 +1,40 @@
+"""GPU parity of the tensor-core Gram grouped by the leading index (used when
+d / R_1 >= 128 and the order is >= 3): sampled entries of G within the
+operand-rounding bound, h, and the FP64 residual of the refined core, against
+the oracle (explicit sampled rows), for R_1 = 4, 8, 16 and orders 3 and 4."""
+import numpy as np
+import pytest
+
+from oracle import leverage as LV, sampling as S, core_update as CU
+from tests.gpu_common import dev, host_keys, rel_err, handle  # noqa: F401
+from tests.test_gpu_fullsize import _check_gram_entries, _check_residual
+from paper_2107_10654_gb300 import tucker as T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dims,ranks,prec", [
+    ((48, 40, 40), (4, 16, 16), "bf16"),          # d = 1024, d / R_1 = 256
+    ((30, 24, 20, 22), (8, 8, 4, 4), "bf16"),     # order 4, d / R_1 = 128
+    ((64, 36, 36), (16, 8, 16), "tf32"),          # R_1 = 16, d / R_1 = 128
+])
+def test_grouped_gram_and_solve(handle, dims, ranks, prec):
+    g = np.random.default_rng(21)
+    F = [g.standard_normal((i, r)).astype(np.float32) for i, r in zip(dims, ranks)]
+    X = g.standard_normal(dims).astype(np.float32)
+    Fd, Xd = [dev(a) for a in F], dev(X)
+    m = 6000
+    levs = [LV.leverage_scores(np.asarray(a, dtype=np.float64))[0] for a in F]
+    smp = T.tucker_sample_rows(handle, dims, ranks, [dev(l) for l in levs], m, 5, 0)
+    ku = host_keys(smp.keys, smp.n_unique)
+    cnt = smp.counts[:smp.n_unique].cpu().numpy().astype(np.float64)
+    w = S.sample_weights(cnt, smp.prob[:smp.n_unique].cpu().numpy(), smp.n_draws)
+    G, h = T.tucker_sketched_gram(handle, Xd, Fd, prec, smp)
+    Gh = G.cpu().numpy()
+    assert np.array_equal(Gh, Gh.T)
+    _check_gram_entries(F, dims, ku, w, Gh, n_pairs=160, seed=3)
+    x = CU.gather_dense(X, ku, dims)
+    hr = CU.sampled_rows_apply_t(F, S.decode_keys(ku, dims), w * x)
+    assert rel_err(h.cpu().numpy(), hr) <= 1e-12
+    core = T.tucker_core_update_sketched(handle, Xd, Fd, 0.1, 0, 0, 0, "exact", prec, fixed=smp)
+    _check_residual(F, dims, ku, w, x, 0.1, core.cpu().numpy())
