@@ -76,7 +76,15 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
  * when the corrections stop shrinking, at most 8 iterations.  With a TF32 or
  * BF16 Gram at least two corrections are always made; when the factors are
  * FP32 the first of them evaluates its residual in FP32 (it only has to be as
- * accurate as the Gram's rounding), every later one in FP64. */
+ * accurate as the Gram's rounding), every later one in FP64.
+ * TF32/BF16 operands: each sampled row k_u = sqrt(w_u) a_1 (x) ... (x) a_N is
+ * formed in FP32 and rounded once.  For order >= 3 with R_1 a power of two
+ * <= 16 and d / R_1 >= 128 the Gram is grouped by the leading index instead
+ * (G = sum_{i_1} (a a^T) (x) M_{i_1}, a = A^(1)[i_1], the rows of one i_1
+ * adjacent in the key-sorted sample): the tensor cores form each M_{i_1} from
+ * the rounded rows sqrt(w_u) a_2 (x) ... (x) a_N, and an FP32 reduction
+ * applies a_{r1} a_{r1'} unrounded.  Either way G is FP32-accumulated and
+ * stored as FP64. */
 typedef enum {
   TUCKER_PREC_FP64 = 0,   /* FP64 CUDA-core Gram; no refinement needed */
   TUCKER_PREC_FP32 = 1,   /* FP32 CUDA-core Gram, FP64 refinement */
