@@ -135,7 +135,9 @@ typedef struct {
   tucker_dtype dtype;               /* element type of dense / vals (and of the factors) */
   const void* dense;                /* device, prod(I_n) elements row-major, or NULL */
   int64_t nnz;                      /* number of observed entries (COO) */
-  const uint64_t* keys;             /* device [nnz]: row-major linear indices, strictly increasing */
+  const uint64_t* keys;             /* device [nnz]: row-major linear indices, strictly increasing
+                                       (a precondition, not checked: the row walks and the
+                                       leading-index-grouped Gram rely on the order) */
   const void* vals;                 /* device [nnz]: entry values, dtype */
 } tucker_tensor;
 
@@ -146,7 +148,8 @@ typedef struct {
  * adjoint). */
 typedef struct {
   int64_t capacity;     /* length of keys / counts / prob */
-  int64_t n_unique;     /* number of distinct sampled rows, sorted ascending by key */
+  int64_t n_unique;     /* number of distinct sampled rows, sorted ascending by key (a
+                           sample passed back in must keep that order; not checked) */
   int64_t n_draws;      /* T: draws used (= m when dense; more when entries are missing) */
   uint64_t* keys;       /* row key: linear row index of K, or prod(I)+j for regulariser row j */
   uint32_t* counts;     /* multiplicity c_u of each distinct row among the accepted draws */
