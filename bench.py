@@ -241,6 +241,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank timings over the process group (the
+    slowest replica sets the job's time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def grouped_gram(w):
     """Whether the library groups the tensor-core Gram by the leading index (the
     same test as the library's: order >= 3, R_1 a power of two <= 16, d / R_1 >= 128,
@@ -495,9 +505,7 @@ def main():
     kron_rows_s = n_real / (stage["ms_gram"] * 1e-3)
 
     if world > 1:
-        t = torch.tensor([ms, ms_ex, ms_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_ex, ms_e2e = [float(v) for v in t.tolist()]
+        ms, ms_ex, ms_e2e = max_over_ranks([ms, ms_ex, ms_e2e], dev)
 
     pk, src = peaks()
     d = w.d
