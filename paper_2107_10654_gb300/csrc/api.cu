@@ -944,8 +944,11 @@ tucker_status tucker_core_update_exact(tucker_handle* h, const tucker_tensor* X,
   TK_TRY(launch_decode_rows(h, F, X->keys, nnz, b.idx, X->vals, b.x));
   TK_CUDA(h, cudaStreamSynchronize(h->stream));
   RowSet rs = make_rowset(F, b.idx, nullptr, b.nreal);
-  // unit weights: w = 1 for every observed row
-  TK_TRY(launch_regdiag(h, b.w, (int)std::min<int64_t>(nnz, 1 << 30), 1.0, nullptr));
+  // unit weights: w = 1 for every observed row (the fill kernel's 32-bit
+  // grid-stride index covers 2^30 entries per launch)
+  for (int64_t off = 0; off < nnz; off += int64_t(1) << 30)
+    TK_TRY(launch_regdiag(h, b.w + off, (int)std::min<int64_t>(nnz - off, int64_t(1) << 30), 1.0,
+                          nullptr));
   rs.w = b.w;
   RowSet rs64;
   TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
