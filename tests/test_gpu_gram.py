@@ -19,11 +19,12 @@ from paper_2107_10654_gb300 import tucker as T
 pytestmark = pytest.mark.gpu
 
 SHAPES = [
-    ((96, 80, 72), (8, 8, 8), 6000),          # d = 512: 6 tiles
+    ((96, 80, 72), (8, 8, 8), 6000),          # d = 512: 3 upper tiles
     ((40, 36, 48, 44), (4, 4, 4, 4), 5000),   # d = 256, order 4
     ((50, 60, 70), (3, 5, 7), 3000),          # d = 105: one ragged tile
     ((64, 90), (16, 20), 4000),               # order 2, d = 320, ragged
-    ((40, 44, 48), (8, 8, 16), 9000),         # d = 1024: 20 tiles, R_N = 16
+    ((40, 44, 48), (8, 8, 16), 9000),         # d = 1024, d / R_1 = 128: grouped by i_1
+    ((40, 44, 48), (16, 4, 16), 9000),        # d = 1024, d / R_1 = 64: full width, 10 tiles
 ]
 
 
