@@ -13,7 +13,9 @@ Modules (each function cites the passage of the paper it restates):
   core_update  exact (Alg. 2 core line; Lemma 4.1 proof) and sketched (Alg. 3) core updates
   als          Alg. 2 factor updates, Tucker loss, RMSE
   adjoint      gradient of the frozen-sketch solve
+  ridge_kron   lam-ridge scores of K by Lemma 4.1, d_eff(K), the overestimate constants of
+               the sample count, and an exact sampler of l^lam(K) / d_eff(K)
 
 Parity unpinned: none; every function has a pin in tests/test_oracle_*.py.
 """
-from . import philox, leverage, sampling, core_update, als, adjoint  # noqa: F401
+from . import philox, leverage, sampling, core_update, als, adjoint, ridge_kron  # noqa: F401
