@@ -50,3 +50,33 @@ def test_create_without_gpu_fails_cleanly():
     h = ctypes.c_void_p()
     st = lib.tucker_create(ctypes.byref(h), None)
     assert st in (_lib.ECUDA, _lib.ENOTSUP) and not h.value
+
+
+def test_null_handle_and_bad_arguments_fail_before_any_device_work():
+    """Every entry point that takes a handle returns EINVAL for a NULL handle, and
+    the allocation-free sampler rejects bad arguments with its message, without a
+    GPU (the checks come before any CUDA call)."""
+    from paper_2107_10654_gb300 import _lib
+    lib = _lib.load()
+    assert lib.tucker_last_error(None) == b"null handle"
+    zero = {ctypes.c_int: 0, ctypes.c_int64: 0, ctypes.c_uint64: 0, ctypes.c_uint32: 0,
+            ctypes.c_double: 0.0, ctypes.c_size_t: 0}
+    for name, (_, argtypes) in _lib.SIGNATURES.items():
+        if name in ("tucker_create", "tucker_last_error", "tucker_sample_rows_noalloc"):
+            continue
+        args = [zero.get(t) for t in argtypes]
+        assert getattr(lib, name)(*args) == _lib.EINVAL, name
+    err = ctypes.create_string_buffer(256)
+    dims = (ctypes.c_int64 * 8)(*([4] * 8))
+    ranks = (ctypes.c_int * 8)(*([2] * 8))
+    out = _lib.TuckerSamples()
+    st = lib.tucker_sample_rows_noalloc(None, 3, dims, ranks, None, 10, 0, 0, 0,
+                                        ctypes.byref(out), err, 256)
+    assert st == _lib.EINVAL and b"null" in err.value
+    lev = _lib.ptr_array([1, 1, 1])                 # never dereferenced: rejected first
+    out.keys = out.counts = out.prob = 1
+    out.capacity = 10
+    for N, m in ((0, 10), (9, 10), (3, 0), (3, 1 << 31)):
+        st = lib.tucker_sample_rows_noalloc(None, N, dims, ranks, lev, m, 0, 0, 0,
+                                            ctypes.byref(out), err, 256)
+        assert st == _lib.EINVAL and err.value, (N, m)
