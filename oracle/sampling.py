@@ -61,6 +61,12 @@ def paper_sample_count(d: int, eps: float, delta: float, beta_prime: float = 0.5
                          max(420.0 * math.log(4.0 * d / delta), 1.0 / (delta * eps))))
 
 
+def inverse_cdf(C: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """min{i : C_i > floor(u * Q / 2^64)}, Q = C[-1]: the row a 64-bit uniform
+    word u selects from fixed-point weights with inclusive prefix sums C."""
+    return np.searchsorted(C, mulhi64(u, C[-1]), side="right")
+
+
 def _mode_words(t: np.ndarray, n_modes: int, seed: int, sweep: int):
     """Uniform 64-bit words, one per mode, for draws t (list of N arrays)."""
     words = []
@@ -79,9 +85,7 @@ def draw_rows(C_list: Sequence[np.ndarray], dims: Sequence[int], t: np.ndarray,
     words = _mode_words(t, N, seed, sweep)
     key = np.zeros(t.shape, dtype=U64)
     for n in range(N):
-        C = C_list[n]
-        target = mulhi64(words[n], C[-1])
-        i = np.searchsorted(C, target, side="right").astype(U64)
+        i = inverse_cdf(C_list[n], words[n]).astype(U64)
         key = key * U64(dims[n]) + i
     if reg == REG_AUGMENTED:
         w0, w1, _, _ = philox4x64_10(t, U64(2), U64(0), U64(0), U64(seed), U64(sweep))

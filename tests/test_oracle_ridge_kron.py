@@ -10,6 +10,7 @@ beta-overestimate, or statistically (chi-square, unbiasedness over seeds)."""
 import numpy as np
 import pytest
 from scipy import stats
+from scipy.linalg import eigh
 
 from oracle import core_update as CU, leverage as LV, ridge_kron as RK, sampling as S
 
@@ -125,6 +126,12 @@ def test_missing_entry_beta_and_bound():
     l_obs = LV.ridge_leverage_scores(K[obs], lam)
     assert np.all(l_k / l_k.sum() >= beta * l_obs / l_obs.sum() - 1e-15)
     assert RK.missing_ridge_beta_bound(F, lam) <= beta + 1e-15
+    # the formula itself, with lambda_max(L_{S-bar,S-bar}) by an independent route: the
+    # generalized eigenproblem K_{S-bar}^T K_{S-bar} v = mu (K^T K + lam I) v has the same
+    # nonzero eigenvalues as K_{S-bar} (K^T K + lam I)^-1 K_{S-bar}^T
+    miss = np.setdiff1d(np.arange(K.shape[0]), obs)
+    mu = eigh(K[miss].T @ K[miss], K.T @ K + lam * np.eye(K.shape[1]), eigvals_only=True).max()
+    assert abs(1.0 / beta - (1.0 + 1.0 / (1.0 - mu))) < 1e-10 / beta
     assert RK.missing_ridge_beta(F, lam, np.arange(K.shape[0]), dims) == 1.0
 
 

@@ -41,6 +41,23 @@ def test_inverse_cdf_against_linear_scan():
     assert not np.isin(keys, [3, 4, 20]).any()
 
 
+def test_inverse_cdf_boundary_convention():
+    """At the exact bucket edges: a target of C_i - 1 selects row i, a target of
+    C_i the next row with mass (min{i : C_i > floor(u Q / 2^64)}); the words u
+    that give those targets are found with Python integers."""
+    q = np.array([3, 0, 5, 1, 7], dtype=np.uint64) * np.uint64(2 ** 29)
+    C = np.cumsum(q, dtype=np.uint64)
+    Q = int(C[-1])
+    targets = sorted({t for c in C for t in (int(c) - 1, int(c)) if 0 <= t < Q})
+    us = [-(-(t << 64) // Q) for t in targets]          # least u with floor(u Q / 2^64) = t
+    for u, t in zip(us, targets):
+        assert u < 2 ** 64 and (u * Q) >> 64 == t
+    got = S.inverse_cdf(C, np.array(us, dtype=np.uint64))
+    expect = [next(j for j in range(C.size) if int(C[j]) > t) for t in targets]
+    assert [int(v) for v in got] == expect
+    assert 1 not in expect                              # the zero-mass row is never selected
+
+
 def test_product_distribution_chi_square():
     g = np.random.default_rng(12)
     dims = (5, 3, 4)
