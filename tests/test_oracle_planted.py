@@ -132,6 +132,68 @@ def _loss_lambda_dropped(mp):
                lambda X, F, g, lam, xx=None, ktx=None: orig(X, F, g, 0.0, xx, ktx))
 
 
+def _observed_lookup_shifted(mp):
+    orig = CU.gather_observed
+
+    def bad(obs_keys, obs_vals, keys_u):
+        v = np.asarray(obs_vals, dtype=np.float64)
+        return orig(obs_keys, np.concatenate([v[1:], v[:1]]), keys_u)   # the next entry's value
+    mp.setattr(CU, "gather_observed", bad)
+
+
+def _exact_rows_lambda_dropped(mp):
+    orig = CU.exact_core_rows
+    mp.setattr(CU, "exact_core_rows",
+               lambda keys, vals, dims, F, lam, chunk=1 << 13: orig(keys, vals, dims, F, 0.0, chunk))
+
+
+def _adjoint_one_factor_scaled(mp):
+    orig = ADJ.backward
+
+    def bad(*a):
+        dA, dx = orig(*a)
+        return [2.0 * dA[0]] + list(dA[1:]), dx
+    mp.setattr(ADJ, "backward", bad)
+
+
+def _unobserved_accepted(mp):
+    orig = S.sample_keys
+
+    def bad(lev_list, dims, m, seed, sweep, reg=S.REG_EXACT, d=0, observed_keys=None,
+            max_draws=0, batch=1 << 20):
+        return orig(lev_list, dims, m, seed, sweep, reg, d, None, max_draws, batch)
+    mp.setattr(S, "sample_keys", bad)
+
+
+def _leverage_without_pinv(mp):
+    def bad(A):
+        A = np.asarray(A, dtype=np.float64)
+        return np.einsum("ir,ir->i", A, A), np.linalg.matrix_rank(A)
+    mp.setattr(LV, "leverage_scores", bad)
+
+
+def _kron_matrix_reversed(mp):
+    orig = CU.kron_matrix
+    mp.setattr(CU, "kron_matrix", lambda factors: orig(list(factors)[::-1]))
+
+
+def _augmented_reg_as_identity(mp):
+    orig = CU.regularised_matrix
+    mp.setattr(CU, "regularised_matrix",
+               lambda G, D, lam, reg: orig(G, D, lam, S.REG_EXACT))
+
+
+def _mixture_weight_dropped(mp):
+    orig = RK.ridge_row_probabilities
+
+    def bad(tables, keys_u, dims):
+        flat = dict(tables)
+        Cc = tables["Cc"]
+        flat["Cc"] = np.arange(1, Cc.size + 1, dtype=np.uint64) * np.uint64(1 << 32)
+        return orig(flat, keys_u, dims)                # every component weighted alike
+    mp.setattr(RK, "ridge_row_probabilities", bad)
+
+
 PLANTS = {
     "kron_order_reversed": (_kron_order_reversed,
                             [TC.test_sampled_row_products_equal_explicit_rows]),
@@ -161,6 +223,24 @@ PLANTS = {
                                  [TR.test_missing_entry_beta_and_bound]),
     "loss_lambda_dropped": (_loss_lambda_dropped,
                             [TC.test_ridge_loss_gram_identity_matches_residual]),
+    "observed_lookup_shifted": (_observed_lookup_shifted,
+                                [TC.test_missing_sketch_all_observed_equals_dense]),
+    "exact_rows_lambda_dropped": (_exact_rows_lambda_dropped,
+                                  [TC.test_exact_rows_all_observed_equals_dense]),
+    "adjoint_one_factor_scaled": (_adjoint_one_factor_scaled,
+                                  [lambda: TC.test_adjoint_matches_central_differences(
+                                      S.REG_EXACT)]),
+    "unobserved_accepted": (_unobserved_accepted, [TS.test_missing_entry_acceptance]),
+    "leverage_without_pinv": (_leverage_without_pinv,
+                              [lambda: TL.test_leverage_sum_is_rank_and_bounded((40, 5), 5)]),
+    "kron_matrix_reversed": (_kron_matrix_reversed,
+                             [TC.test_sampled_row_products_equal_explicit_rows]),
+    "augmented_reg_as_identity": (_augmented_reg_as_identity,
+                                  [lambda: TC.test_count_form_equals_explicit_sketch_matrix(
+                                      S.REG_AUGMENTED)]),
+    "mixture_weight_dropped": (_mixture_weight_dropped,
+                               [lambda: TR.test_ridge_sampler_probabilities_are_the_ridge_distribution(
+                                   0.4)]),
 }
 
 
