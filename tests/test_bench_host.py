@@ -1,7 +1,9 @@
 """Host-side logic of bench.py that needs no GPU: the reference arm (the
 oracle timed on the host cores) and its launch contract, the max-over-ranks
-reduction of replica timings over a two-rank gloo group, and the predicate
-that says when the Gram is grouped by the leading index."""
+reduction of replica timings over a two-rank gloo group, the predicate that
+says when the Gram is grouped by the leading index, and the x2 ladder of
+sample counts for the 1.01x loss target (its stopping rule, and the oracle's
+ladder on the small workload)."""
 import json
 import os
 import socket
@@ -134,3 +136,29 @@ def test_grouped_gram_predicate_limits():
     # A^(1) in FP32 within 200 KB of shared memory
     assert bench.grouped_gram(W((3200, 40, 40), (16, 16, 16)))
     assert not bench.grouped_gram(W((3201, 40, 40), (16, 16, 16)))
+
+
+def test_ladder_helper_doubles_m_until_the_median_meets_the_target():
+    calls = []
+
+    def ratio_of(m, s):
+        calls.append((m, s))
+        return 1.0 + 50.0 / m + 1e-4 * s          # median over s = 0..9: 1 + 50/m + 4.5e-4
+    rows, m_star = bench._ladder(ratio_of, 1000)
+    assert [r["m"] for r in rows] == [1000, 2000, 4000, 8000]
+    assert m_star == 8000 and rows[-1]["median_ratio"] <= bench.LADDER_TARGET
+    assert all(r["median_ratio"] > bench.LADDER_TARGET for r in rows[:-1])
+    assert len(calls) == 4 * bench.LADDER_SEEDS
+    rows, m_star = bench._ladder(lambda m, s: 1.5, 10)   # never met within the ladder
+    assert m_star is None and len(rows) == bench.LADDER_STEPS + 1
+
+
+def test_m_ladder_reference_small_workload():
+    r = _run(["bench.py", "--impl", "reference", "--m-ladder", "--workload", SMALL])
+    assert r.returncode == 0, r.stderr[-2000:]
+    (ln,) = _json_lines(r.stdout)
+    assert ln["mode"] == "m_ladder" and ln["impl"] == "reference" and ln["workload"] == SMALL
+    ms = [row["m"] for row in ln["ladder"]]
+    assert ms[0] == synth.WORKLOADS[SMALL].m and all(b == 2 * a for a, b in zip(ms, ms[1:]))
+    assert ln["ladder"][-1]["median_ratio"] <= 1.01 and ln["m_star"] == ms[-1]
+    assert all(row["median_ratio"] >= 1.0 for row in ln["ladder"])
