@@ -59,6 +59,13 @@ def test_reference_arm_line():
     e2e = ln["e2e"]
     assert e2e["value"] == ln["value"] and e2e["unit"] == "ms"
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    assert ln["oracle_exact"]["ms"] > 0 and ln["oracle_exact"]["sample"]
+
+
+def test_oracle_exact_timing_skips_the_observed_entry_gram():
+    w = synth.WORKLOADS["missing3_1024_r16_f32"]
+    ms, sample = bench.oracle_exact_timing(w, {"keys": None}, None)
+    assert ms is None and sample.startswith("not run")
 
 
 def test_reference_arm_other_ranks_exit_without_work():
