@@ -19,6 +19,7 @@ independent replicas (the update has no data-path collective).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -49,9 +50,11 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--prec", default="auto")
     p.add_argument("--reg", default="exact")
-    p.add_argument("--solver", default="mixed", choices=["fp64", "mixed"],
-                   help="ridge solver of the timed update (the other one is timed beside it)")
+    p.add_argument("--solver", default="kpcg", choices=["fp64", "mixed", "kpcg"],
+                   help="ridge solver of the timed update (the others are timed beside it)")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the 128^4 and 1024^3-at-10% workloads timed beside the headline")
     p.add_argument("--m-ladder", action="store_true",
                    help="the smallest m on a x2 ladder from the workload's m whose median ridge-loss "
                         "ratio over 10 seeds is <= 1.01 (with --impl reference: by the oracle on "
@@ -216,8 +219,28 @@ def oracle_step(X, F, w, reg):
     return CU.sketched_core(X, F, w.lam, w.m, w.seed_sample, 0, regc)
 
 
+def oracle_ladder(w, X, F, reg):
+    """The x2 ladder of the headline computed by the oracle on the host (the
+    library draws the same rows and its cores agree to 1e-6, so the ratios and
+    m_star are the GPU arm's too)."""
+    import numpy as np
+    from oracle import core_update as CU, sampling as S
+    regc = S.REG_EXACT if reg == "exact" else S.REG_AUGMENTED
+    X = np.asarray(X, dtype=np.float64)
+    F = [np.asarray(a, dtype=np.float64) for a in F]
+    ktx = CU.kt_x(X, F)
+    xx = float(np.sum(X * X))
+    opt = CU.ridge_loss_dense(X, F, CU.exact_core_kron_eig(X, F, w.lam, ktx), w.lam, xx, ktx)
+
+    def ratio_of(m, s):
+        g = CU.sketched_core(X, F, w.lam, m, w.seed_sample + s, 0, regc)["g"]
+        return CU.ridge_loss_dense(X, F, g, w.lam, xx, ktx) / opt
+    return _ladder(ratio_of, w.m)
+
+
 def run_reference(args):
-    """The CPU oracle as the reference arm (rank 0 only)."""
+    """The CPU oracle as the reference arm (rank 0 only), on the GPU arm's
+    workload, m and configuration."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -226,22 +249,27 @@ def run_reference(args):
     if w.observed < 1.0:
         X = synth.observed_entries(w)
         F = X["factors"]
+        x_bytes = X["keys"].nbytes + X["vals"].nbytes
     else:
         P = synth.tucker_problem(w)
         X, F = P["X"], P["factors"]
+        x_bytes = X.nbytes
     small = w.observed >= 1.0 and w.d <= 1024
+    ladder, m_star = (oracle_ladder(w, X, F, args.reg) if small else ([], None))
+    wm = dataclasses.replace(w, m=m_star or w.m)
     for _ in range(max(0, min(args.warmup, 1))):
         if small:
-            oracle_step(X, F, w, args.reg)
+            oracle_step(X, F, wm, args.reg)
     times, sample = [], ""
     for _ in range(args.steps):
         if small:
             t0 = time.perf_counter()
-            oracle_step(X, F, w, args.reg)
+            oracle_step(X, F, wm, args.reg)
             times.append((time.perf_counter() - t0) * 1e3)
-            sample = f"{args.steps} full sketched core updates of the workload (numpy FP64 oracle)"
+            sample = (f"{args.steps} full sketched core updates of the workload at m = {wm.m} "
+                      "(numpy FP64 oracle)")
         else:
-            ms_est, sample = oracle_timing(w, X, F, args.reg, budget=6.0)
+            ms_est, sample = oracle_timing(wm, X, F, args.reg, budget=6.0)
             times.append(ms_est)
     ms = statistics.mean(times)
     cores = cpu_cores()
@@ -251,11 +279,13 @@ def run_reference(args):
             "data": "synthetic",
             # the same workload configuration as the GPU arm; the oracle itself computes
             # in FP64 (explicit sampled rows, FP64 Cholesky)
-            "config": workload_config(w, ours_prec(args), args.reg, args.solver),
+            "config": workload_config(w, ours_prec(args), args.reg, args.solver, wm.m, x_bytes),
             "oracle_arithmetic": "fp64",
+            "m_ladder": {"target": LADDER_TARGET, "seeds": LADDER_SEEDS, "rows": ladder,
+                         "m_star": m_star},
             "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
                              "sample": sample},
-            "oracle_exact": dict(zip(("ms", "sample"), oracle_exact_timing(w, X, F))),
+            "oracle_exact": dict(zip(("ms", "sample"), oracle_exact_timing(wm, X, F))),
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -287,15 +317,18 @@ def ours_prec(args):
     """Gram precision of the GPU arm (the same choice main() makes)."""
     prec = args.prec
     if prec == "auto":
-        prec = os.environ.get("TUCKER_BENCH_PREC", "bf16")
+        prec = os.environ.get("TUCKER_BENCH_PREC", "tf32")
     return prec
 
 
-def workload_config(w, prec, reg, solver="fp64"):
-    return {"workload": w.name, "solver": solver, "dims": list(w.dims), "ranks": list(w.ranks), "d": w.d,
-            "m": w.m, "lambda": w.lam, "sigma": w.sigma, "x_dtype": w.dtype, "gram_prec": prec,
-            "reg": reg, "seed": w.seed_sample,
-            "l2": "flushed before every timed step (256 MiB write); X is 512 MiB"}
+def workload_config(w, prec, reg, solver, m, x_bytes):
+    """The workload a line is measured on; m is the sample count it is timed at
+    (the smallest m on the ladder whose median ridge-loss ratio meets 1.01x)."""
+    return {"workload": w.name, "solver": solver, "dims": list(w.dims), "ranks": list(w.ranks),
+            "d": w.d, "m": m, "m_workload": w.m, "lambda": w.lam, "sigma": w.sigma,
+            "x_dtype": w.dtype, "observed": w.observed, "gram_prec": prec, "reg": reg,
+            "seed": w.seed_sample,
+            "l2": f"flushed before every timed step (256 MiB write); X is {x_bytes / 2**20:.0f} MiB"}
 
 
 def run_stage_roofline(args):
@@ -435,6 +468,120 @@ def run_m_ladder(args):
     h.close()
 
 
+def gpu_inputs(w, dev, pinned=False):
+    """(X on the device, factors on the device, host copies, input bytes) of a workload."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2107_10654_gb300 import tucker as T
+    if w.observed < 1.0:
+        O = synth.observed_entries(w)
+        host_in = [torch.from_numpy(O["keys"].view(np.int64)), torch.from_numpy(O["vals"])]
+        F_h, X_h = O["factors"], O
+    else:
+        P = synth.tucker_problem(w)
+        X_h, F_h = P["X"], P["factors"]
+        host_in = [torch.from_numpy(X_h)]
+    if pinned:
+        host_in = [t.pin_memory() for t in host_in]
+    F_pin = [torch.from_numpy(a) for a in F_h]
+    if pinned:
+        F_pin = [a.pin_memory() for a in F_pin]
+    dev_in = [t.to(dev) for t in host_in]
+    F = [a.to(dev) for a in F_pin]
+    X = T.CooTensor(dev_in[0], dev_in[1], w.dims) if w.observed < 1.0 else dev_in[0]
+    in_bytes = sum(t.numel() * t.element_size() for t in host_in)
+    return X, F, {"X_h": X_h, "F_h": F_h, "host_in": host_in, "F_pin": F_pin, "dev_in": dev_in}, in_bytes
+
+
+class Timer:
+    """CUDA events on the library's stream around each step, L2 flushed before each."""
+
+    def __init__(self, stream, flush):
+        self.stream, self.flush = stream, flush
+
+    def __call__(self, fn, k):
+        import torch
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        out = []
+        for i in range(k):
+            self.flush.fill_(float(i))
+            ev[i][0].record(self.stream)
+            out.append(fn())
+            ev[i][1].record(self.stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], out
+
+
+STAGES = ("ms_leverage", "ms_sample", "ms_dedupe", "ms_gather", "ms_gram", "ms_solve")
+
+
+def measure_workload(h, w, X, F, prec, reg, steps, warmup, timer, m_override=None):
+    """The sketched core update of one workload on the GPU: the sample count the
+    1.01x ridge-loss target needs (median over LADDER_SEEDS sampling seeds on a x2
+    ladder from the workload's m), the update timed at that m (asynchronous calls,
+    no per-stage events) and at the workload's own m, the stage split, the exact
+    update (the plain method) and the loss ratios."""
+    import torch
+    from paper_2107_10654_gb300 import tucker as T
+    missing = w.observed < 1.0
+    exact_prec = prec if missing else "fp64"
+    g_ex = T.tucker_core_update_exact(h, X, F, w.lam, exact_prec)
+    loss_ex = T.tucker_ridge_loss(h, X, F, w.lam, g_ex)
+    seeds = [w.seed_sample + s for s in range(LADDER_SEEDS)]
+
+    def ratio_of(m, s):
+        g = T.tucker_core_update_sketched(h, X, F, w.lam, m, seeds[s], 0, reg, prec)
+        return T.tucker_ridge_loss(h, X, F, w.lam, g) / loss_ex
+    ladder, m_star = _ladder(ratio_of, w.m)
+    m_t = m_override or m_star or ladder[-1]["m"]
+    g = torch.empty(w.d, dtype=torch.float64, device=F[0].device)
+
+    def upd(m, stats):
+        return T.tucker_core_update_sketched(h, X, F, w.lam, m, w.seed_sample, 0, reg, prec,
+                                             core_out=g, stats=stats)
+    out = {"m": w.m, "m_star": m_star, "m_timed": m_t, "ladder": ladder}
+    for m, key in ((m_t, "at_m_star"), (w.m, "at_workload_m")):
+        if key == "at_workload_m" and m == m_t:
+            out[key] = out["at_m_star"]
+            continue
+        _, st0 = upd(m, True)
+        loss = T.tucker_ridge_loss(h, X, F, w.lam, g) / loss_ex
+        for _ in range(warmup):
+            upd(m, False)
+        torch.cuda.synchronize()
+        h.set_sync(False)
+        ms, _ = timer(lambda: upd(m, False), steps)
+        h.sync()
+        h.set_sync(True)
+        _, sts = timer(lambda: upd(m, True), steps)
+        stats = [s for _, s in sts]
+        rec = {"ms": statistics.mean(ms), "ms_min": min(ms), "loss_ratio": loss,
+               "stage_ms": {k: statistics.mean(s[k] for s in stats) for k in STAGES},
+               "ms_with_stage_events": statistics.mean(sum(s[k] for k in STAGES) for s in stats),
+               "n_unique": stats[-1]["n_unique"], "n_real": stats[-1]["n_real"],
+               "n_draws": stats[-1]["n_draws"], "refine_iters": stats[-1]["refine_iters"],
+               "inner_iters": stats[-1]["inner_iters"],
+               "kernel_ms": {"gram": statistics.mean(s["ms_gram_kernel"] for s in stats),
+                             "factor_or_convert": statistics.mean(s["ms_factor"] for s in stats),
+                             "first_cg_solve": statistics.mean(s["ms_inner"] for s in stats)},
+               "launches": int(statistics.mean(s["launches"] for s in stats)),
+               "raw_steps_ms": ms}
+        out[key] = rec
+    n_ex = steps if not missing else min(steps, 3)
+    h.set_sync(False)
+    ex_ms, _ = timer(lambda: T.tucker_core_update_exact(h, X, F, w.lam, exact_prec, core_out=g_ex),
+                     n_ex)
+    h.sync()
+    h.set_sync(True)
+    out["exact_ms"] = statistics.mean(ex_ms)
+    out["exact_prec"] = exact_prec
+    out["speedup_vs_exact"] = out["exact_ms"] / out["at_m_star"]["ms"]
+    out["speedup_vs_exact_at_workload_m"] = out["exact_ms"] / out["at_workload_m"]["ms"]
+    return out
+
+
 def main():
     args = parse()
     if args.m_ladder:
@@ -465,86 +612,22 @@ def main():
     w = synth.WORKLOADS[args.workload]
     prec = ours_prec(args)
     missing = w.observed < 1.0
-    if missing:
-        O = synth.observed_entries(w)
-        F_h = O["factors"]
-        host_in = [torch.from_numpy(O["keys"].view(np.int64)).pin_memory(),
-                   torch.from_numpy(O["vals"]).pin_memory()]
-        X_h = O
-    else:
-        P = synth.tucker_problem(w)
-        X_h, F_h = P["X"], P["factors"]
-        host_in = [torch.from_numpy(X_h).pin_memory()]
-    F_pin = [torch.from_numpy(a).pin_memory() for a in F_h]
-    dev_in = [t.to(dev) for t in host_in]
-    F = [a.to(dev) for a in F_pin]
-
-    def as_tensor(bufs):
-        return T.CooTensor(bufs[0], bufs[1], w.dims) if missing else bufs[0]
-
-    X = as_tensor(dev_in)
-    in_bytes = sum(t.numel() * t.element_size() for t in host_in)
+    X, F, hb, in_bytes = gpu_inputs(w, dev, pinned=True)
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
     h = T.Handle(solver=args.solver)
     stream = h.stream
-    # the exact update of an observed-entry tensor is the Gram of all observed
-    # rows (1e8 at 1024^3, seconds): timed once, on the tensor cores
-    exact_prec = "bf16" if missing else "fp64"
-    exact_steps = 1 if missing else args.steps
-
-    def sketched(core_out=None, stats=True):
-        return T.tucker_core_update_sketched(h, X, F, w.lam, w.m, w.seed_sample, 0, args.reg, prec,
-                                             core_out=core_out, stats=stats)
-
-    def exact(core_out=None):
-        return T.tucker_core_update_exact(h, X, F, w.lam, exact_prec, core_out=core_out)
-
-    # correctness of this configuration before timing: loss ratio vs exact
-    g_sk, st0 = sketched()
-    g_ex = exact()
-    loss_sk = T.tucker_ridge_loss(h, X, F, w.lam, g_sk)
-    loss_ex = T.tucker_ridge_loss(h, X, F, w.lam, g_ex)
-    loss_ratio = loss_sk / loss_ex
-
-    for _ in range(args.warmup):
-        sketched(core_out=g_sk)
-        if not missing:
-            exact(core_out=g_ex)
-    torch.cuda.synchronize()
-
-    def timed(fn, k):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(k)]
-        out = []
-        for i in range(k):
-            flush.fill_(float(i))
-            ev[i][0].record(stream)
-            out.append(fn())
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        return [a.elapsed_time(b) for a, b in ev], out
-
+    timer = Timer(stream, flush)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        # the headline: asynchronous calls (the host enqueues the next update while the GPU
-        # runs this one) without per-stage events; errors are collected by the sync after
-        h.set_sync(False)
-        sk_ms, _ = timed(lambda: sketched(core_out=g_sk, stats=False), args.steps)
-        h.sync()
-        h.set_sync(True)
-        # the same updates again, synchronous with per-stage events: the stage breakdown
-        st_ms, sk_out = timed(lambda: sketched(core_out=g_sk), args.steps)
-        h.set_sync(False)
-        ex_ms, _ = timed(lambda: exact(core_out=g_ex), exact_steps)
-        h.sync()
-        h.set_sync(True)
-        # end to end through the public API: host (pinned) inputs in, core out to host; two
-        # alternating device buffers, so nothing (the observed-entry hash) carries over
+        head = measure_workload(h, w, X, F, prec, args.reg, args.steps, args.warmup, timer)
+        m_t = head["m_timed"]
+        # end to end through the public API: host (pinned) inputs in, core out to host;
+        # two alternating device buffers, so nothing (the observed-entry hash) carries over
         core_host = torch.empty(w.d, dtype=torch.float64).pin_memory()
-        bufs = [[torch.empty_like(t) for t in dev_in] for _ in range(2)]
+        bufs = [[torch.empty_like(t) for t in hb["dev_in"]] for _ in range(2)]
         Fe = [torch.empty_like(a) for a in F]
         e2e_ms = []
         for i in range(args.steps):
@@ -552,82 +635,102 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             with torch.cuda.stream(stream):
-                for a, b in zip(bufs[i % 2], host_in):
+                for a, b in zip(bufs[i % 2], hb["host_in"]):
                     a.copy_(b, non_blocking=True)
-                for a, b in zip(Fe, F_pin):
+                for a, b in zip(Fe, hb["F_pin"]):
                     a.copy_(b, non_blocking=True)
-            g = T.tucker_core_update_sketched(h, as_tensor(bufs[i % 2]), Fe, w.lam, w.m,
-                                              w.seed_sample, 0, args.reg, prec)
+            Xe = T.CooTensor(bufs[i % 2][0], bufs[i % 2][1], w.dims) if missing else bufs[i % 2][0]
+            g = T.tucker_core_update_sketched(h, Xe, Fe, w.lam, m_t, w.seed_sample, 0, args.reg,
+                                              prec)
             with torch.cuda.stream(stream):
                 core_host.copy_(g, non_blocking=True)
             stream.synchronize()
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        del bufs
+        # the other ridge solvers on the same workload and m, timed the same way
+        others = {}
+        for other in ("mixed", "fp64", "kpcg"):
+            if other == args.solver:
+                continue
+            h2 = T.Handle(stream=stream, solver=other)
+            g_alt = torch.empty(w.d, dtype=torch.float64, device=dev)
+
+            def alt(stats=False):
+                return T.tucker_core_update_sketched(h2, X, F, w.lam, m_t, w.seed_sample, 0,
+                                                     args.reg, prec, core_out=g_alt, stats=stats)
+            for _ in range(args.warmup):
+                alt()
+            h2.set_sync(False)
+            k = min(args.steps, 10)
+            alt_ms, _ = timer(alt, k)
+            h2.sync()
+            h2.set_sync(True)
+            _, st = alt(True)
+            g_head = T.tucker_core_update_sketched(h, X, F, w.lam, m_t, w.seed_sample, 0, args.reg,
+                                                   prec)
+            others[other] = {"ms": statistics.mean(alt_ms), "ms_solve": st["ms_solve"],
+                             "refine_iters": st["refine_iters"],
+                             "rel_diff_vs_timed": float(torch.linalg.norm(g_alt - g_head) /
+                                                        torch.linalg.norm(g_head))}
+            h2.close()
+        # ALS sweeps (Alg. 2) and the adjoint of the frozen-sketch solve (not the headline)
+        extra = {}
+        if not missing:
+            Fa = [a.clone() for a in F]
+            ca = T.tucker_core_update_exact(h, X, F, w.lam, "fp64")
+            for kind in ("sketched", "exact"):
+                sk = kind == "sketched"
+                T.tucker_als_sweep(h, X, Fa, ca, w.lam, sk, m_t, w.seed_sample, 0, args.reg, prec)
+                ms_s, _ = timer(lambda: T.tucker_als_sweep(h, X, Fa, ca, w.lam, sk, m_t,
+                                                           w.seed_sample, 1, args.reg, prec),
+                                min(args.steps, 3))
+                extra[f"als_sweep_ms_{kind}"] = statistics.mean(ms_s)
+            lev = T.tucker_leverage_scores(h, F)[0]
+            smp = T.tucker_sample_rows(h, w.dims, w.ranks, lev, m_t, w.seed_sample, 0, args.reg)
+            gf, stf = T.tucker_core_update_sketched(h, X, F, w.lam, 0, 0, 0, args.reg, prec,
+                                                    fixed=smp, stats=True)
+            gbar = torch.ones(w.d, dtype=torch.float64, device=dev)
+            T.tucker_core_solve_adjoint(h, X, F, w.lam, args.reg, prec, smp, stf["solve_id"], gf, gbar)
+            ms_a, _ = timer(lambda: T.tucker_core_solve_adjoint(h, X, F, w.lam, args.reg, prec, smp,
+                                                                stf["solve_id"], gf, gbar),
+                            min(args.steps, 5))
+            extra["adjoint_ms"] = statistics.mean(ms_a)
+        X_h, F_h = hb["X_h"], hb["F_h"]
+        f_bytes = sum(a.numel() * a.element_size() for a in hb["F_pin"])
+        del X, F, hb
+        torch.cuda.empty_cache()
+        # the other workloads of the path, timed the same way in the same run
+        configs = {}
+        if not args.no_configs and rank == 0:
+            for name in ("dense4_128_r8_f32", "missing3_1024_r16_f32"):
+                if name == w.name:
+                    continue
+                wc = synth.WORKLOADS[name]
+                Xc, Fc, _, cbytes = gpu_inputs(wc, dev)
+                hc = T.Handle(stream=stream, solver=args.solver)
+                rec = measure_workload(hc, wc, Xc, Fc, prec, args.reg, min(args.steps, 10),
+                                       args.warmup, timer)
+                rec["config"] = workload_config(wc, prec, args.reg, args.solver, rec["m_timed"],
+                                                cbytes)
+                configs[name] = rec
+                hc.close()
+                del Xc, Fc
+                torch.cuda.empty_cache()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
 
-    # ALS sweeps (Alg. 2: factor updates, then the core update) and the adjoint of the
-    # frozen-sketch solve, timed the same way on copies of the state (not the headline)
-    extra = {}
-    if not missing:
-        Fa = [a.clone() for a in F]
-        ca = g_sk.clone()
-        for kind in ("sketched", "exact"):
-            sk = kind == "sketched"
-            T.tucker_als_sweep(h, X, Fa, ca, w.lam, sk, w.m, w.seed_sample, 0, args.reg, prec)
-            ms_s, _ = timed(lambda: T.tucker_als_sweep(h, X, Fa, ca, w.lam, sk, w.m, w.seed_sample,
-                                                       1, args.reg, prec), min(args.steps, 3))
-            extra[f"als_sweep_ms_{kind}"] = statistics.mean(ms_s)
-        smp = T.Samples.empty(w.m, dev)
-        lev = T.tucker_leverage_scores(h, F)[0]
-        smp = T.tucker_sample_rows(h, w.dims, w.ranks, lev, w.m, w.seed_sample, 0, args.reg, out=smp)
-        gf, stf = T.tucker_core_update_sketched(h, X, F, w.lam, 0, 0, 0, args.reg, prec, fixed=smp,
-                                                stats=True)
-        gbar = torch.ones(w.d, dtype=torch.float64, device=dev)
-        T.tucker_core_solve_adjoint(h, X, F, w.lam, args.reg, prec, smp, stf["solve_id"], gf, gbar)
-        ms_a, _ = timed(lambda: T.tucker_core_solve_adjoint(h, X, F, w.lam, args.reg, prec, smp,
-                                                            stf["solve_id"], gf, gbar),
-                        min(args.steps, 5))
-        extra["adjoint_ms"] = statistics.mean(ms_a)
-
-    # the other ridge solver on the same sample, timed the same way (not the headline)
-    other = "mixed" if args.solver == "fp64" else "fp64"
-    h2 = T.Handle(stream=stream, solver=other)
-    g_alt = torch.empty_like(g_sk)
-
-    def sketched_alt(stats=True):
-        return T.tucker_core_update_sketched(h2, X, F, w.lam, w.m, w.seed_sample, 0, args.reg,
-                                             prec, core_out=g_alt, stats=stats)
-    for _ in range(args.warmup):
-        sketched_alt()
-    h2.set_sync(False)
-    alt_ms, _ = timed(lambda: sketched_alt(stats=False), args.steps)
-    h2.sync()
-    h2.set_sync(True)
-    _, alt_out = timed(sketched_alt, args.steps)
-    alt_loss = T.tucker_ridge_loss(h2, X, F, w.lam, g_alt) / loss_ex
-    alt = {"solver": other, "ms": statistics.mean(alt_ms), "loss_ratio": alt_loss,
-           "ms_solve": statistics.mean(s["ms_solve"] for _, s in alt_out),
-           "refine_iters": alt_out[-1][1]["refine_iters"],
-           "rel_diff_vs_timed": float(torch.linalg.norm(g_alt - g_sk) / torch.linalg.norm(g_sk))}
-    h2.close()
-
-    ms = statistics.mean(sk_ms)
-    ms_ex = statistics.mean(ex_ms)
+    ms = head["at_m_star"]["ms"]
+    ms_ex = head["exact_ms"]
     ms_e2e = statistics.mean(e2e_ms)
-    stats = [s for _, s in sk_out]
-    stage = {k: statistics.mean(s[k] for s in stats)
-             for k in ("ms_leverage", "ms_sample", "ms_dedupe", "ms_gather", "ms_gram", "ms_solve")}
-    n_real = stats[-1]["n_real"]
-    launches = int(sum(s["launches"] for s in stats))
-    kron_rows_s = n_real / (stage["ms_gram"] * 1e-3)
-
     if world > 1:
         ms, ms_ex, ms_e2e = max_over_ranks([ms, ms_ex, ms_e2e], dev)
-
+    rec = head["at_m_star"]
+    kms = rec["kernel_ms"]
+    stage = rec["stage_ms"]
+    n_real = rec["n_real"]
     pk, src = peaks()
     d = w.d
-    kms = {k: statistics.mean(s[k] for s in stats) for k in ("ms_factor", "ms_gram_kernel")}
     traffic_tab = load_traffic()
 
     def gram_roofline():
@@ -643,45 +746,54 @@ def main():
             bound, note = "tensor", f"{prec} tcgen05: {src} bf16 burst x {TC_RATIO[prec]}"
             kernel = f"k_syrk_tc<{prec}>" + (" grouped by i_1" if grouped else "")
         elif prec == "fp32":
-            peak = 152 * 128 * 2 * 2.07
+            peak = FP32_PEAK_TFLOPS
             bound, note, kernel = "alu", "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz", "k_syrk_simt<float>"
         else:
             peak = FP64_PEAK_TFLOPS
             bound, note, kernel = "alu", "FP64 nominal 1.25 TFLOP/s", "k_syrk_simt<double>"
-        achieved = flops / (kms["ms_gram_kernel"] * 1e-3) / 1e12
+        achieved = flops / (kms["gram"] * 1e-3) / 1e12
         return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_tab.get((kernel, w.name)),
-                "kernel": kernel, "peak_source": note, "kernel_ms": kms["ms_gram_kernel"],
-                "flop_per_launch": flops}
+                "kernel": kernel, "peak_source": note, "kernel_ms": kms["gram"],
+                "flop_per_launch": flops, "launches_per_update": 1}
 
-    def factor_roofline():
-        # the one-cluster FP32 factor also forms X = L^-1: d^3 / 3 flop more
-        flops = d ** 3 / 3 * (2 if args.solver == "mixed" and d <= 512 else 1)
-        if args.solver == "fp64":
-            kernel, peak, note = "k_chol_coop<double>", FP64_PEAK_TFLOPS, "FP64 nominal 1.25 TFLOP/s"
+    def solve_roofline():
+        if args.solver == "kpcg":
+            # one CG solve: per iteration the product with M~ (2 d^2 flop) and P^-1 (4 d sum R_n)
+            solves = rec["refine_iters"] + 1
+            iters = max(1, rec["inner_iters"]) / solves
+            flops = iters * (2 * d * d + 4 * d * sum(w.ranks))
+            kernel = "k_kpcg_cluster" if d <= 576 else "k_kpcg"
+            kms_one = kms["first_cg_solve"]
+            note = ("FP32 FMA nominal of all 152 SMs (152 x 128 x 2 x 2.07 GHz); the solve runs on "
+                    + ("one 8-CTA cluster" if d <= 576 else "a cooperative grid") +
+                    " and is latency-bound (a few iterations of d-vector work per launch)")
+            launches = solves
         else:
-            # FP32 FMA nominal of the whole GPU: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
-            peak = FP32_PEAK_TFLOPS
-            if d <= 512:       # one thread-block cluster (8 or 16 SMs) holds the matrix
-                kernel, note = "k_chol32_cluster", "FP32 nominal of all 152 SMs (the kernel runs on one cluster)"
-            else:
-                kernel, note = "k_chol_coop<float>", "FP32 FMA nominal 80.5 TFLOP/s"
-        achieved = flops / (kms["ms_factor"] * 1e-3) / 1e12
+            # the method's work is the factorisation, d^3 / 3 flop
+            flops = d ** 3 / 3
+            kernel = ("k_chol_coop<double>" if args.solver == "fp64" else
+                      "k_chol32_cluster" if d <= 512 else "k_chol_coop<float>")
+            kms_one = kms["factor_or_convert"]
+            note = "FP32 FMA nominal 80.5 TFLOP/s" if args.solver == "mixed" else "FP64 nominal 1.25 TFLOP/s"
+            launches = 1
+        peak = FP64_PEAK_TFLOPS if args.solver == "fp64" else FP32_PEAK_TFLOPS
+        achieved = flops / (kms_one * 1e-3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_tab.get((kernel, w.name)),
-                "kernel": kernel, "peak_source": note, "kernel_ms": kms["ms_factor"],
-                "flop_per_launch": flops}
+                "kernel": kernel, "peak_source": note, "kernel_ms": kms_one,
+                "flop_per_launch": flops, "launches_per_update": launches}
 
-    # the dominant kernel of the timed update
-    roof = factor_roofline() if kms["ms_factor"] >= kms["ms_gram_kernel"] else gram_roofline()
-    roof_gram = gram_roofline()
-    # exact dense path: one streaming read of X by the first n-mode product
-    exact_gbs = None if missing else in_bytes / (ms_ex * 1e-3) / 1e9
+    # the dominant kernel of the timed update: the larger total time per update
+    roof_solve, roof_gram = solve_roofline(), gram_roofline()
+    t_solve = roof_solve["kernel_ms"] * roof_solve["launches_per_update"]
+    roof = roof_solve if t_solve >= roof_gram["kernel_ms"] else roof_gram
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        value, sample = oracle_timing(w, X_h, F_h, args.reg)
-        ex_ms, ex_sample = oracle_exact_timing(w, X_h, F_h)
+        wm = dataclasses.replace(w, m=m_t)
+        value, sample = oracle_timing(wm, X_h, F_h, args.reg)
+        ex_ms, ex_sample = oracle_exact_timing(wm, X_h, F_h)
         cpu = {"value": value, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
                "sample": sample, "exact_value": ex_ms, "exact_sample": ex_sample}
 
@@ -689,18 +801,28 @@ def main():
         line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
-                "config": workload_config(w, prec, args.reg, args.solver),
-                "exact_ms": ms_ex, "speedup_vs_exact": ms_ex / ms, "loss_ratio": loss_ratio,
-                "ms_with_stage_events": statistics.mean(st_ms),
-                "kron_rows_per_s": kron_rows_s * world, "n_unique": stats[-1]["n_unique"],
-                "refine_iters": stats[-1]["refine_iters"], "stage_ms": stage,
-                "exact_hbm_gbs": exact_gbs, "solver": args.solver, "other_solver": alt, **extra,
-                "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu,
+                "config": workload_config(w, prec, args.reg, args.solver, m_t, in_bytes),
+                "exact_ms": ms_ex, "speedup_vs_exact": ms_ex / ms,
+                "loss_ratio": rec["loss_ratio"],
+                "m_ladder": {"target": LADDER_TARGET, "seeds": LADDER_SEEDS, "rows": head["ladder"],
+                             "m_star": head["m_star"]},
+                "at_workload_m": {k: head["at_workload_m"][k] for k in
+                                  ("ms", "loss_ratio", "stage_ms", "refine_iters", "inner_iters")},
+                "speedup_vs_exact_at_workload_m": head["speedup_vs_exact_at_workload_m"],
+                "ms_with_stage_events": rec["ms_with_stage_events"],
+                "kron_rows_per_s": n_real / (stage["ms_gram"] * 1e-3) * world,
+                "n_unique": rec["n_unique"], "refine_iters": rec["refine_iters"],
+                "inner_iters": rec["inner_iters"], "stage_ms": stage,
+                "exact_hbm_gbs": None if missing else in_bytes / (ms_ex * 1e-3) / 1e9,
+                "solver": args.solver, "other_solvers": others, **extra,
+                "roofline": roof, "roofline_gram": roof_gram, "roofline_solve": roof_solve,
+                "configs": {k: {kk: vv for kk, vv in v.items() if kk != "ladder"} | {"ladder": v["ladder"]}
+                            for k, v in configs.items()},
+                "cpu_baseline": cpu,
                 "e2e": {"value": ms_e2e, "unit": "ms",
-                        "h2d_bytes_per_step": int(in_bytes + sum(a.numel() * a.element_size()
-                                                             for a in F)),
+                        "h2d_bytes_per_step": int(in_bytes + f_bytes),
                         "d2h_bytes_per_step": int(w.d * 8)},
-                "clocks": clk.summary(), "gpu_launches": launches}
+                "clocks": clk.summary(), "gpu_launches": rec["launches"] * args.steps}
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:

@@ -73,10 +73,12 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
  * implicit rows.  With c_k = ||correction_k|| / ||g|| (c_0 = 1) and the
  * contraction estimate rho = min(c_k / c_{k-1}, 1/2), the iteration stops once
  * the estimated remaining relative error c_k rho / (1 - rho) is below 1e-8, or
- * when the corrections stop shrinking, at most 8 iterations.  With a TF32 or
- * BF16 Gram at least two corrections are always made; when the factors are
- * FP32 the first of them evaluates its residual in FP32 (it only has to be as
- * accurate as the Gram's rounding), every later one in FP64.
+ * when the corrections stop shrinking, at most 8 iterations.  With a BF16
+ * Gram (and a TF32 one under the factor solvers) at least two corrections are
+ * always made; when the factors are FP32 the first of them evaluates its
+ * residual in FP32 (it only has to be as accurate as the Gram's rounding),
+ * every later one in FP64.  Under TUCKER_SOLVER_KRON_PCG a TF32 or FP32 Gram
+ * starts with an FP64 correction (one suffices at TF32's rounding).
  * TF32/BF16 operands: each sampled row k_u = sqrt(w_u) a_1 (x) ... (x) a_N is
  * formed in FP32 and rounded once.  For order >= 3 with R_1 a power of two
  * <= 16 and d / R_1 >= 128 the Gram is grouped by the leading index instead
@@ -108,10 +110,30 @@ typedef enum {
  *                  well below 1; lambda > 0 keeps kappa(M) <= (||G|| +
  *                  lambda)/lambda.  A matrix that FP32 cannot factor (a
  *                  pivot <= 0 after rounding, or below the smallest normal
- *                  FP32 value) returns TUCKER_ENOTSPD. */
+ *                  FP32 value) returns TUCKER_ENOTSPD.
+ *   KRON_PCG       no factorisation: the solves inside the same FP64
+ *                  refinement are conjugate gradients on the rounded Gram
+ *                  M~ = G~ + lambda R (FP32), preconditioned by
+ *                  P = (x) V_n diag(s (x) ev_n + lbar) (x) V_n^T, where
+ *                  A^(n)T A^(n) = V_n diag(ev_n) V_n^T, s = tr(G~) /
+ *                  prod_n tr(A^(n)T A^(n)) and lbar = mean(lambda R).  The
+ *                  sketched Gram estimates K^T K = (x) A^(n)T A^(n) without
+ *                  bias (Thm A.3), so P is spectrally close to M~ and CG needs
+ *                  a few iterations (each one product with M~ and 2 d sum R_n
+ *                  multiply-adds for P^-1) instead of a d^3 / 3 factorisation.
+ *                  Each solve stops at a relative residual of 1e-4 (BF16
+ *                  Gram) or 1e-5 (TF32, FP32), at most 50 iterations; the
+ *                  refinement stops by the rule above with a target of 1e-8.  If the refinement does not reach that
+ *                  target (a sketch far from K^T K, e.g. a strongly
+ *                  non-uniform observation mask), the call factors M~ as the
+ *                  MIXED solver does and solves again, so the result meets
+ *                  the same tolerances.  With an FP64 Gram (TUCKER_PREC_FP64)
+ *                  this solver behaves as FP64_CHOLESKY.  The adjoint reuses
+ *                  M~ and the V_n of the forward call. */
 typedef enum {
   TUCKER_SOLVER_FP64_CHOLESKY = 0,
-  TUCKER_SOLVER_MIXED = 1
+  TUCKER_SOLVER_MIXED = 1,
+  TUCKER_SOLVER_KRON_PCG = 2
 } tucker_solver;
 
 /* How the lambda*I term enters the sketched problem. */
@@ -169,6 +191,10 @@ typedef struct {
   int64_t launches;     /* CUDA kernels this call launched */
   double ms_factor;     /* the Cholesky factorisation kernel alone (inside ms_solve) */
   double ms_gram_kernel;/* the Kronecker SYRK kernel alone (inside ms_gram) */
+  double ms_inner;      /* TUCKER_SOLVER_KRON_PCG: the first CG solve alone (inside ms_solve) */
+  int64_t inner_iters;  /* TUCKER_SOLVER_KRON_PCG: CG iterations over all solves of the call;
+                           negative when the CG refinement missed its target and the FP32
+                           factor solved instead */
 } tucker_stats;
 
 typedef struct tucker_handle tucker_handle;
@@ -356,13 +382,17 @@ tucker_status tucker_core_solve_adjoint(tucker_handle* h, const tucker_tensor* X
  *   err_host        nullable host buffer of err_len bytes for a one-line message
  * Limits: m is bounded by the scratch size - about 2.5e5 draws for order 3;
  * larger m returns TUCKER_ECAPACITY with the bytes needed in err_host.
- * The first call on each device looks up the device address of the array
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call shares the one array, so calls whose
+ * The first successful call on each device looks up the device address of
+ * the array (cudaGetSymbolAddress, with that device current) and caches it; a
+ * lookup that failed is retried by the next call.  The call synchronises its
+ * stream, so it cannot be made while that stream is capturing a CUDA graph.
+ * Every call shares the one array, so calls whose
  * work overlaps on the GPU (two streams, two host threads) race and corrupt
  * each other: serialise them.  Each call clears what must start at zero.
  * Synchronises the stream.  Calls no cudaMalloc, cudaFree or other
- * allocating routine.  Errors: EINVAL, ECAPACITY, ERANK, ENOTSUP, ECUDA. */
+ * allocating routine.  Errors: EINVAL (also when prod(I_n) >= 4e18, where
+ * linear row keys would wrap, as for tucker_sample_rows), ECAPACITY, ERANK,
+ * ENOTSUP, ECUDA. */
 #define TUCKER_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 tucker_status tucker_sample_rows_noalloc(void* cuda_stream, int N, const int64_t* I, const int* R,

@@ -16,7 +16,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTSPD", "ERANK", "EDRAWLIM
 F32, F64 = 0, 1
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16 = 0, 1, 2, 3
 REG_EXACT, REG_AUGMENTED = 0, 1
-SOLVER_FP64_CHOLESKY, SOLVER_MIXED = 0, 1
+SOLVER_FP64_CHOLESKY, SOLVER_MIXED, SOLVER_KRON_PCG = 0, 1, 2
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtucker.so")
 
@@ -38,7 +38,8 @@ class TuckerStats(C.Structure):
                 ("ms_total", C.c_double), ("n_unique", C.c_int64), ("n_draws", C.c_int64),
                 ("n_real", C.c_int64), ("refine_iters", C.c_int), ("refine_rel", C.c_double),
                 ("solve_id", C.c_uint64), ("launches", C.c_int64), ("ms_factor", C.c_double),
-                ("ms_gram_kernel", C.c_double)]
+                ("ms_gram_kernel", C.c_double), ("ms_inner", C.c_double),
+                ("inner_iters", C.c_int64)]
 
 
 _P = C.c_void_p

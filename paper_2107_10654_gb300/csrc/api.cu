@@ -111,6 +111,13 @@ tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_
                              size_t ws_bytes, double* G);
 
 tucker_status launch_to_f64(tucker_handle* h, const FactorSet& F, double* const* out);
+tucker_status launch_gram_eig(tucker_handle* h, int N, const int* R, const double* const* gram,
+                              double* const* evecs, double* const* evals);
+int kpcg_fits(int d, int N, const int* R);
+tucker_status launch_kpcg(tucker_handle* h, const float* M, const double* regdiag, int d, int N,
+                          const int* R, const double* const* V, const double* const* ev,
+                          const double* rhs, double* out, double* upd, double* stats,
+                          double* part, float* sg, double* res, double tol, int max_iter);
 size_t leverage_aux_bytes(int64_t maxI);
 static int64_t max_dim(const FactorSet& F) { int64_t m = 1; for (int n = 0; n < F.N; ++n) if (F.I[n] > m) m = F.I[n]; return m; }
 
@@ -289,6 +296,7 @@ struct SketchBufs {
   double* ptab;                       // per-mode q/Q and Q/q tables of the gather
   WalkBuf walk;
   double* A64[TUCKER_MAX_ORDER];      // FP64 copies of FP32 factors (walk kernels)
+  double* fgram[TUCKER_MAX_ORDER];    // A^(n)T A^(n) (R_n x R_n), for the CG preconditioner
   char* gram_ws;
   size_t gram_bytes;
   int axpy_split;
@@ -302,6 +310,7 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
     b->cdf[n] = ar.get<uint64_t>(F.I[n]);
   }
   b->rank = reinterpret_cast<int*>(ar.get<char>(leverage_aux_bytes(max_dim(F))));
+  for (int n = 0; n < F.N; ++n) b->fgram[n] = ar.get<double>((size_t)F.R[n] * F.R[n]);
   b->keys_raw = fixed ? nullptr : ar.get<uint64_t>(m);
   b->d_T = ar.get<int64_t>(1);
   b->sort_bytes = fixed ? 0 : sort_dedupe_scratch(m);
@@ -344,14 +353,25 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
 
 constexpr size_t kPartDoubles = 512;            // per-CTA partial sums of one inverse application
 
+constexpr int kKresSlots = 64;                  // CG solves recorded per call, at most
+constexpr size_t kKronDoubles =                 // V_n and ev_n of every mode
+    (size_t)TUCKER_MAX_ORDER * (TUCKER_MAX_RANK * TUCKER_MAX_RANK + TUCKER_MAX_RANK);
+
+template <class T>
+static T* align16(T* p) {
+  return reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+}
+
 static tucker_status chol_reserve(tucker_handle* h, int d) {
   CholCache& c = h->chol;
   const size_t need = (size_t)d * d;
   const size_t inv = chol_inv_doubles(d);
   const size_t xinv = chol_inverse_fits(d) ? 2 * need : 0;
-  // FP64: L, LT, regdiag, tmp, Linv; FP32: L32, LT32, Linv32 (+ X32, XC32 for small d)
-  const size_t bytes = (2 * need + 2 * (size_t)d + inv + 64 + kPartDoubles) * sizeof(double) +
-                       (2 * need + inv + 64 + xinv) * sizeof(float);
+  // FP64: L, LT, regdiag, tmp, Linv, part, V_n / ev_n, CG records; FP32: L32, LT32,
+  // Linv32, the CG product exchange (+ X32, XC32 for small d)
+  const size_t bytes = (2 * need + 2 * (size_t)d + inv + 64 + kPartDoubles + kKronDoubles +
+                        2 * kKresSlots) * sizeof(double) +
+                       (2 * need + inv + 64 + xinv + 2 * (size_t)d + 64) * sizeof(float) + 64;
   if (c.cap < bytes) {
     TK_CUDA(h, cudaStreamSynchronize(h->stream));
     if (c.L) cudaFree(c.L);
@@ -370,11 +390,21 @@ static tucker_status chol_reserve(tucker_handle* h, int d) {
   c.tmp = c.regdiag + d;
   c.Linv = c.tmp + d;
   c.part = c.Linv + inv + 64;
-  c.L32 = reinterpret_cast<float*>(c.part + kPartDoubles);
+  double* kb = c.part + kPartDoubles;
+  for (int n = 0; n < TUCKER_MAX_ORDER; ++n) {
+    c.kv[n] = kb + (size_t)n * TUCKER_MAX_RANK * TUCKER_MAX_RANK;
+    c.ke[n] = kb + (size_t)TUCKER_MAX_ORDER * TUCKER_MAX_RANK * TUCKER_MAX_RANK +
+              (size_t)n * TUCKER_MAX_RANK;
+  }
+  c.kres = kb + kKronDoubles;
+  c.L32 = align16(reinterpret_cast<float*>(c.kres + 2 * kKresSlots));
   c.LT32 = c.L32 + need;
   c.Linv32 = c.LT32 + need;
-  c.X32 = xinv ? c.Linv32 + inv + 64 : nullptr;
+  c.sg = align16(c.Linv32 + inv + 64);
+  c.X32 = xinv ? align16(c.sg + 2 * (size_t)d) : nullptr;
   c.XC32 = c.X32 ? c.X32 + need : nullptr;
+  c.kpcg = 0;
+  c.kron_ready = 0;
   c.d = d;
   c.id = 0;
   return TUCKER_OK;
@@ -385,10 +415,64 @@ static tucker_status chol_reserve(tucker_handle* h, int d) {
 // when the Gram is FP64 (no refinement follows), else in FP32 on the rounded
 // factor (they only precondition the FP64 refinement).  Mixed: the FP32 copy
 // is factored and L keeps M for the FP64 residual.
-static tucker_status factorize(tucker_handle* h, double* L, int d, int prec) {
+// Whether the Kronecker-preconditioned CG solver handles this solve: chosen on
+// the handle, a rounded Gram (an FP64 Gram keeps the direct FP64 solve), and
+// the d-vectors and V_n fit in shared memory.
+static bool kpcg_wanted(tucker_handle* h, const FactorSet& F, int prec) {
+  return h->solver == TUCKER_SOLVER_KRON_PCG && prec != TUCKER_PREC_FP64 &&
+         kpcg_fits(F.d, F.N, F.R);
+}
+
+// Eigendecompositions A^(n)T A^(n) = V_n diag(ev_n) V_n^T of the factor Grams
+// (written by the leverage launcher) into the cache, for the CG preconditioner.
+static tucker_status kron_prepare(tucker_handle* h, const FactorSet& F,
+                                  const double* const* fgram) {
   CholCache& c = h->chol;
-  c.mixed = h->solver == TUCKER_SOLVER_MIXED;
+  TK_TRY(launch_gram_eig(h, F.N, F.R, fgram, c.kv, c.ke));
+  c.kN = F.N;
+  for (int n = 0; n < F.N; ++n) c.kR[n] = F.R[n];
+  c.kron_ready = 1;
+  return TUCKER_OK;
+}
+
+// Relative residual of each CG solve: below the rounding of the Gram it
+// solves with (about 3e-4 relative for BF16 operands, 3e-5 for TF32 on the
+// 512^3 workload), so that the FP64 refinement contracts at the Gram's rate.
+static double kpcg_tol(int prec) { return prec == TUCKER_PREC_BF16 ? 1e-4 : 1e-5; }
+constexpr int kKpcgMaxIter = 50;
+
+// One CG solve with the cached M~ (L32) and preconditioner: out = M~^-1 rhs
+// and/or upd += M~^-1 rhs with the norms in stats.  The first solve of a call
+// is timed (events 12, 13) when the call records stage times.
+static tucker_status kpcg_solve(tucker_handle* h, int d, const double* rhs, double* out,
+                                double* upd, double* stats) {
+  CholCache& c = h->chol;
+  double* res = c.kres_n < kKresSlots ? c.kres + 2 * c.kres_n : nullptr;
+  const bool first = c.kres_n == 0;
+  ++c.kres_n;
+  if (first) ev_record(h, h->timing, 12);
+  TK_TRY(launch_kpcg(h, c.L32, c.regdiag, d, c.kN, c.kR, c.kv, c.ke, rhs, out, upd, stats,
+                     c.part, c.sg, res, c.ktol, kKpcgMaxIter));
+  if (first) ev_record(h, h->timing, 13);
+  return TUCKER_OK;
+}
+
+static tucker_status factorize(tucker_handle* h, double* L, int d, int prec, int solver) {
+  CholCache& c = h->chol;
   c.prep64 = c.prep32 = c.inv32 = 0;
+  c.kpcg = 0;
+  if (solver == TUCKER_SOLVER_KRON_PCG && prec != TUCKER_PREC_FP64 && c.kron_ready &&
+      kpcg_fits(d, c.kN, c.kR)) {
+    // no factor: the CG solves read the FP32 copy of M (L keeps M in FP64)
+    c.mixed = 0;
+    ev_record(h, h->timing, 8);
+    TK_TRY(launch_to_f32(h, L, (size_t)d * d, c.L32));
+    ev_record(h, h->timing, 9);
+    c.kpcg = 1;
+    c.ktol = kpcg_tol(prec);
+    return TUCKER_OK;
+  }
+  c.mixed = solver == TUCKER_SOLVER_MIXED || solver == TUCKER_SOLVER_KRON_PCG;
   if (c.mixed) {
     TK_TRY(launch_to_f32(h, L, (size_t)d * d, c.L32));
     ev_record(h, h->timing, 8);
@@ -430,6 +514,7 @@ static tucker_status factorize(tucker_handle* h, double* L, int d, int prec) {
 // the rounded copy exists; FP64 otherwise.
 static tucker_status chol_solve(tucker_handle* h, int d, const double* rhs, double* g, int prec) {
   CholCache& c = h->chol;
+  if (c.kpcg) return kpcg_solve(h, d, rhs, g, nullptr, nullptr);
   if (c.mixed || (c.prep32 && prec != TUCKER_PREC_FP64)) {
     if (c.inv32) return chol_solve_inv32(h, c.X32, c.XC32, d, rhs, g, c.tmp);
     return chol_solve32(h, c.L32, c.LT32, c.Linv32, d, rhs, g, c.tmp);
@@ -462,24 +547,30 @@ static tucker_status build_gram(tucker_handle* h, const FactorSet& F, const RowS
 // stops shrinking.
 static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const RowSet& rs,
                                    int prec, SketchBufs& b, const double* rhs, double* g,
-                                   int* iters, double* rel, const RowSet* rs32 = nullptr) {
+                                   int* iters, double* rel, const RowSet* rs32 = nullptr,
+                                   bool* converged = nullptr) {
   const int d = F.d;
   TK_TRY(chol_solve(h, d, rhs, g, prec));
   *iters = 0;
   *rel = 0.0;
+  if (converged) *converged = true;
   const bool explicit_m = prec == TUCKER_PREC_FP64;
   if (explicit_m && !h->chol.mixed) return TUCKER_OK;
   // stop when the remaining relative error, estimated from the last correction
   // c_k and the contraction rho ~ c_k / c_{k-1}, is below target (c_0 = 1: the
   // first solve), or when the corrections stop shrinking (rounding level).  A
-  // tensor-core Gram (8- or 11-bit operands) always takes two corrections, so
-  // the first two are enqueued back to back and the host waits once for both.
-  // The first of them only has to be accurate to the Gram's rounding level, so
-  // with FP32 factors its residual is evaluated by the FP32 walks; every later
-  // residual, which sets the accuracy of the result, is FP64.
+  // BF16 Gram (and a TF32 one under the factor solvers) always takes two
+  // corrections, so the first two are enqueued back to back and the host waits
+  // once for both.  The first of them only has to be accurate to the Gram's
+  // rounding level, so with FP32 factors its residual is evaluated by the FP32
+  // walks; every later residual, which sets the accuracy of the result, is FP64.
   const double target = explicit_m ? 1e-13 : 1e-8;
-  const int max_iters = h->chol.mixed ? 12 : 8;
-  const int batch = (prec == TUCKER_PREC_BF16 || prec == TUCKER_PREC_TF32) ? 2 : 1;
+  const int max_iters = (h->chol.mixed || h->chol.kpcg) ? 12 : 8;
+  bool reached = false;
+  // With the CG solver on a TF32 Gram one FP64 correction reaches the target
+  // (the rounded solve is off by about 3e-5 relative; each CG solve stops at 1e-5)
+  const int batch =
+      (prec == TUCKER_PREC_BF16 || (prec == TUCKER_PREC_TF32 && !h->chol.kpcg)) ? 2 : 1;
   double prev = 1.0;
   int checked = 0;
   for (int it = 0; it < max_iters; ++it) {
@@ -495,7 +586,9 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
                        h->chol.regdiag, g, b.r));
     }
     CholCache& cc = h->chol;
-    if ((cc.mixed || (cc.prep32 && prec != TUCKER_PREC_FP64)) && cc.inv32) {
+    if (cc.kpcg) {
+      TK_TRY(kpcg_solve(h, d, b.r, nullptr, g, b.rstat + 2 * it));
+    } else if ((cc.mixed || (cc.prep32 && prec != TUCKER_PREC_FP64)) && cc.inv32) {
       TK_TRY(chol_correct_inv32(h, cc.X32, cc.XC32, d, b.r, g, b.rstat + 2 * it, cc.tmp, cc.part));
     } else {
       TK_TRY(chol_solve(h, d, b.r, b.r, prec));
@@ -511,8 +604,9 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
     for (int k = 0; k < n; ++k) {
       const double rk = hv[2 * k + 1] > 0 ? sqrt(hv[2 * k] / hv[2 * k + 1]) : 0.0;
       const double rho = fmin(rk / prev, 0.5);
-      stop = stop || rk == 0.0 || rk * rho / (1.0 - rho) < target ||
-             (checked + k > 0 && rk > 0.5 * prev);
+      const bool hit = rk == 0.0 || rk * rho / (1.0 - rho) < target || rk < 1e-10;
+      reached = reached || hit;
+      stop = stop || hit || (checked + k > 0 && rk > 0.5 * prev);
       prev = rk;
       *rel = rk;
     }
@@ -520,15 +614,31 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
     *iters = it + 1;
     if (stop) break;
   }
+  // the direct factors stop at their rounding level; the CG solver has to meet
+  // the target, else the caller factors M~ instead
+  if (converged) *converged = reached || !h->chol.kpcg;
   return TUCKER_OK;
+}
+
+// solve_refined, and when the CG solver did not reach the target (a sketch
+// far from the Kronecker Gram), the same solve with the FP32 factor of M~ (the
+// mixed solver), from the FP64 M still held in the cache.
+static tucker_status solve_checked(tucker_handle* h, const FactorSet& F, const RowSet& rs,
+                                   int prec, SketchBufs& b, const double* rhs, double* g,
+                                   int* iters, double* rel, const RowSet* rs32 = nullptr) {
+  bool conv = true;
+  TK_TRY(solve_refined(h, F, rs, prec, b, rhs, g, iters, rel, rs32, &conv));
+  if (conv) return TUCKER_OK;
+  TK_TRY(factorize(h, h->chol.L, F.d, prec, TUCKER_SOLVER_MIXED));
+  return solve_refined(h, F, rs, prec, b, rhs, g, iters, rel, rs32);
 }
 
 // Factor G + diag(regdiag) (G in the FP64 buffer L) and solve for b.h.
 static tucker_status solve_refine(tucker_handle* h, const FactorSet& F, const RowSet& rs,
                                   int prec, SketchBufs& b, int* iters, double* rel) {
   TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
-  TK_TRY(factorize(h, h->chol.L, F.d, prec));
-  return solve_refined(h, F, rs, prec, b, b.h, b.g, iters, rel);
+  TK_TRY(factorize(h, h->chol.L, F.d, prec, h->solver));
+  return solve_checked(h, F, rs, prec, b, b.h, b.g, iters, rel);
 }
 
 }  // namespace tk
@@ -606,7 +716,8 @@ tucker_status tucker_set_sync(tucker_handle* h, int synchronous) {
 
 tucker_status tucker_set_solver(tucker_handle* h, tucker_solver solver) {
   if (!h) return TUCKER_EINVAL;
-  if (solver != TUCKER_SOLVER_FP64_CHOLESKY && solver != TUCKER_SOLVER_MIXED)
+  if (solver != TUCKER_SOLVER_FP64_CHOLESKY && solver != TUCKER_SOLVER_MIXED &&
+      solver != TUCKER_SOLVER_KRON_PCG)
     return fail(h, TUCKER_EINVAL, "unknown solver %d", (int)solver);
   h->solver = solver;
   h->chol.id = 0;
@@ -775,8 +886,12 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   const uint32_t* counts;
   const double* p_in = nullptr;
   bool tables_ready = false;
+  const bool kpcg = kpcg_wanted(h, F, prec);
+  h->chol.kres_n = 0;
+  h->chol.kron_ready = 0;
   if (!fixed) {
-    TK_TRY(launch_leverage(h, F, b.lev, b.cdf, b.rank, nullptr, nullptr, nullptr));
+    TK_TRY(launch_leverage(h, F, b.lev, b.cdf, b.rank, nullptr, nullptr,
+                           kpcg ? b.fgram : nullptr));
     ev_record(h, timing, 1);
     // the gather's probability tables need only the CDFs: built on the second
     // stream beside the sampling and the dedupe, joined before the gather
@@ -785,11 +900,16 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
     {
       cudaStream_t main_stream = h->stream;
       h->stream = h->aux;
-      const tucker_status st = launch_prob_tables(h, F, b.cdf, b.ptab);
+      tucker_status st = launch_prob_tables(h, F, b.cdf, b.ptab);
+      if (st == TUCKER_OK) st = cudaEventRecord(h->ev_join, h->aux) == cudaSuccess ? TUCKER_OK
+                                                                               : TUCKER_ECUDA;
+      // the CG preconditioner's eigendecompositions of the factor Grams, behind the
+      // tables on the second stream (joined before the solve, with the right-hand side)
+      if (st == TUCKER_OK && kpcg) st = kron_prepare(h, F, b.fgram);
       h->stream = main_stream;
+      if (st == TUCKER_ECUDA && !h->err[0]) return fail(h, st, "cudaEventRecord on the second stream");
       TK_TRY(st);
     }
-    TK_CUDA(h, cudaEventRecord(h->ev_join, h->aux));
     tables_ready = true;
     TK_TRY(sample_keys(h, F, b.cdf, m, seed, sweep, reg, X->dense ? nullptr : X, 0, b.keys_raw,
                        b.d_T, &T, ar));
@@ -810,6 +930,10 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
     keys_u = fixed->keys;
     counts = fixed->counts;
     p_in = fixed->prob;
+    if (kpcg) {
+      TK_TRY(launch_leverage(h, F, b.lev, b.cdf, b.rank, nullptr, nullptr, b.fgram));
+      TK_TRY(kron_prepare(h, F, b.fgram));
+    }
     if (!X->dense) { int pr; TK_TRY(hash_ensure(h, X, &pr)); }
     TK_CUDA(h, cudaStreamSynchronize(h->stream));   // host values above are stack-held
   }
@@ -826,7 +950,7 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   // cluster (mixed solver, small d) they run on the second stream beside the
   // Gram and the factorisation and are joined before the solve (a grid-wide
   // factorisation needs every SM, so there everything stays in order)
-  const bool beside = h->solver == TUCKER_SOLVER_MIXED && chol32_on_cluster(h, F.d);
+  const bool beside = (h->solver == TUCKER_SOLVER_MIXED && chol32_on_cluster(h, F.d)) || kpcg;
   auto rhs_chain = [&]() -> tucker_status {
     TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
     TK_TRY(walk_segments(h, rs, F.I[0], b.walk));
@@ -853,9 +977,9 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   int iters = 0;
   double rel = 0.0;
   TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
-  TK_TRY(factorize(h, h->chol.L, F.d, prec));
+  TK_TRY(factorize(h, h->chol.L, F.d, prec, h->solver));
   if (beside) TK_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-  TK_TRY(solve_refined(h, F, rs64, prec, b, b.h, b.g, &iters, &rel, &rs));
+  TK_TRY(solve_checked(h, F, rs64, prec, b, b.h, b.g, &iters, &rel, &rs));
   TK_CUDA(h, cudaMemcpyAsync(core_out, b.g, sizeof(double) * F.d, cudaMemcpyDeviceToDevice,
                              h->stream));
   ev_record(h, timing, 6);
@@ -882,6 +1006,14 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
     stats->launches = h->launches - launches0;
     stats->ms_factor = ev_ms(h, 8, 9);
     stats->ms_gram_kernel = ev_ms(h, 10, 11);
+    if (h->chol.kres_n > 0) {             // CG solves ran (negative: the factor took over)
+      stats->ms_inner = ev_ms(h, 12, 13);
+      double kr[2 * kKresSlots];
+      const int nk = std::min(h->chol.kres_n, kKresSlots);
+      cudaMemcpy(kr, h->chol.kres, 2 * nk * sizeof(double), cudaMemcpyDeviceToHost);
+      for (int k = 0; k < nk; ++k) stats->inner_iters += (int64_t)kr[2 * k];
+      if (!h->chol.kpcg) stats->inner_iters = -stats->inner_iters;
+    }
     if (st != TUCKER_OK) h->chol.id = 0;
     return st;
   }
@@ -958,6 +1090,12 @@ tucker_status tucker_core_update_exact(tucker_handle* h, const tucker_tensor* X,
   TK_TRY(rows_axpy(h, F, rs64, b.walk, b.axpy_split, b.axpy_part, b.w, b.x, 1.0, nullptr, nullptr,
                    nullptr, b.h));
   TK_TRY(launch_regdiag(h, h->chol.regdiag, F.d, lambda, nullptr));
+  h->chol.kres_n = 0;
+  h->chol.kron_ready = 0;
+  if (kpcg_wanted(h, F, prec)) {
+    TK_TRY(launch_leverage(h, F, b.lev, b.cdf, b.rank, nullptr, nullptr, b.fgram));
+    TK_TRY(kron_prepare(h, F, b.fgram));
+  }
   int iters;
   double rel;
   TK_TRY(solve_refine(h, F, rs64, prec, b, &iters, &rel));
@@ -1151,17 +1289,23 @@ tucker_status tucker_core_solve_adjoint(tucker_handle* h, const tucker_tensor* X
   RowSet rs64;
   TK_TRY(rowset64(h, F, rs, b.A64, &rs64));
   TK_TRY(walk_segments(h, rs, F.I[0], b.walk));
+  h->chol.kres_n = 0;
   if (!reuse) {
+    h->chol.kron_ready = 0;
+    if (kpcg_wanted(h, F, prec)) {
+      TK_TRY(launch_leverage(h, F, b.lev, b.cdf, b.rank, nullptr, nullptr, b.fgram));
+      TK_TRY(kron_prepare(h, F, b.fgram));
+    }
     TK_TRY(build_gram(h, F, rs, prec, cap, b, h->chol.L));
     TK_TRY(launch_regdiag(h, h->chol.regdiag, F.d, lambda,
                           reg == TUCKER_REG_AUGMENTED ? b.D : nullptr));
     TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
-    TK_TRY(factorize(h, h->chol.L, F.d, prec));
+    TK_TRY(factorize(h, h->chol.L, F.d, prec, h->solver));
     h->chol.id = h->next_solve_id++;
   }
   int iters;
   double rel;
-  TK_TRY(solve_refined(h, F, rs64, prec, b, gbar, v, &iters, &rel));
+  TK_TRY(solve_checked(h, F, rs64, prec, b, gbar, v, &iters, &rel));
   TK_TRY(rows_dot(h, F, rs64, b.walk, g, v, b.z, zv));
   TK_CUDA(h, cudaMemsetAsync(dx_out, 0, sizeof(double) * cap, h->stream));
   TK_TRY(launch_adjoint_rows(h, F, b.idx, b.w, b.x, b.z, zv, g, v, b.nreal, cap, dA_out, dx_out));

@@ -47,6 +47,16 @@ struct CholCache {
   int mixed = 0;          // the cached factor is the FP32 one (L then holds M itself)
   int prep64 = 0;         // LT / Linv of the FP64 factor are ready
   int prep32 = 0;         // L32 / LT32 / Linv32 are ready (the FP32 factor, or the FP64 one rounded)
+  int kpcg = 0;           // the solves are Kronecker-preconditioned CG on L32 = M~ (no factor)
+  double* kv[TUCKER_MAX_ORDER] = {};  // KRON_PCG: eigenvectors V_n of A^(n)T A^(n) (R_n x R_n)
+  double* ke[TUCKER_MAX_ORDER] = {};  // KRON_PCG: their eigenvalues (R_n)
+  float* sg = nullptr;    // KRON_PCG: 2 d floats of product exchange
+  double* kres = nullptr; // KRON_PCG: (iterations, final relative residual) per solve
+  int kres_n = 0;         // solves recorded in kres during this call
+  double ktol = 1e-4;     // relative residual each CG solve stops at
+  int kron_ready = 0;     // kv / ke hold the eigendecompositions of the current factors
+  int kN = 0;             // order and ranks of kv / ke
+  int kR[TUCKER_MAX_ORDER] = {};
   int d = 0;
   size_t cap = 0;         // bytes allocated behind L
   uint64_t id = 0;        // solve id of the cached factor (0 = none)
@@ -67,7 +77,7 @@ struct tucker_handle {
   tk::CholCache chol;
   uint64_t next_solve_id = 1;
   int64_t launches = 0;         // kernels launched by this handle (all calls)
-  int solver = 0;               // tucker_solver: FP64 Cholesky (0) or mixed (1)
+  int solver = 0;               // tucker_solver: FP64 Cholesky (0), mixed (1), Kronecker CG (2)
   int timing = 0;               // record per-kernel events (ev[8..11]) during this call
   int chol_cluster[2] = {0, 0}; // CTAs of the one-cluster FP32 Cholesky of order chol_cluster_key
   int chol_cluster_key = -1;    // (without, with the explicit inverse; 0: does not fit)
@@ -171,6 +181,36 @@ __device__ __forceinline__ int upper_bound_u64(const uint64_t* C, int n, uint64_
     if (C[mid] > target) hi = mid; else lo = mid + 1;
   }
   return lo;
+}
+
+// ------------------------------------------ mbarrier and bulk-copy (TMA) PTX
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+               ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 template <class T>

@@ -74,6 +74,77 @@ constexpr int LEV_THREADS = 256;
 constexpr int LEV_STAGE = 4096;               // doubles of staged factor rows
 constexpr int LEV_PAIRS_PER_THREAD = (64 * 65 / 2 + LEV_THREADS - 1) / LEV_THREADS;
 
+// Cyclic Jacobi eigendecomposition of the symmetric Rp x Rp matrix G (Rp even)
+// in shared memory by one warp, with the round-robin (tournament) ordering so
+// that Rp/2 disjoint rotations run in parallel per step; at most 40 sweeps.
+// V must hold the identity on entry.  On return G is diagonal to FP64 rounding
+// (eigenvalue k in G[k][k]) and V[i][k] is component i of eigenvector k.
+// cs, sn, pp, qq: Rp/2 entries each of shared scratch.
+__device__ void jacobi_eig_warp(double* G, double* V, int Rp, double* cs, double* sn, int* pp,
+                                int* qq, int lane) {
+  const int half = Rp / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int e = lane; e < Rp * Rp; e += 32) {
+      const double v = G[e] * G[e];
+      if (e / Rp == e % Rp) dia += v; else off += v;
+    }
+    off = warp_sum(off);
+    dia = warp_sum(dia);
+    if (off <= 1e-28 * dia || Rp <= 1) break;
+    for (int step = 0; step < Rp - 1; ++step) {
+      for (int k = lane; k < half; k += 32) {
+        // circle method: slot 0 fixed, slots 1..Rp-1 rotate by `step`
+        const int s1 = Rp - 1 - k;
+        int p = k == 0 ? 0 : ((k - 1 + step) % (Rp - 1)) + 1;
+        int q = ((s1 - 1 + step) % (Rp - 1)) + 1;
+        if (p > q) { const int t = p; p = q; q = t; }
+        const double apq = G[p * Rp + q], app = G[p * Rp + p], aqq = G[q * Rp + q];
+        double c = 1.0, s = 0.0;
+        if (fabs(apq) > 1e-16 * fabs(app + aqq) && fabs(apq) > 1e-300) {
+          // tangent of the rotation angle in FP32 (an approximate annihilation
+          // is enough for Jacobi); (c, s) formed in FP64 so that the
+          // rotation is orthogonal to FP64 rounding
+          const double num = aqq - app, den = 2.0 * apq;
+          const bool in32 = fabs(den) > 1e-30 && fabs(den) < 1e30 && fabs(num) < 1e30;
+          const float theta = in32 ? (float)num / (float)den : (float)(num / den);
+          float tf;
+          if (fabsf(theta) > 1e18f) tf = 0.5f / theta;
+          else tf = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
+          const double t = (double)tf;
+          const double q2 = fma(t, t, 1.0);
+          const double y = rsqrt(q2);
+          c = y;
+          s = t * y;
+        }
+        cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
+      }
+      __syncwarp();
+      for (int e = lane; e < half * Rp; e += 32) {      // rows p, q
+        const int k = e / Rp, j = e % Rp;
+        const int p = pp[k], q = qq[k];
+        const double c = cs[k], s = sn[k];
+        const double gp = G[p * Rp + j], gq = G[q * Rp + j];
+        G[p * Rp + j] = c * gp - s * gq;
+        G[q * Rp + j] = s * gp + c * gq;
+      }
+      __syncwarp();
+      for (int e = lane; e < half * Rp; e += 32) {      // columns p, q (and V)
+        const int k = e / Rp, i = e % Rp;
+        const int p = pp[k], q = qq[k];
+        const double c = cs[k], s = sn[k];
+        const double gp = G[i * Rp + p], gq = G[i * Rp + q];
+        G[i * Rp + p] = c * gp - s * gq;
+        G[i * Rp + q] = s * gp + c * gq;
+        const double vp = V[i * Rp + p], vq = V[i * Rp + q];
+        V[i * Rp + p] = c * vp - s * vq;
+        V[i * Rp + q] = s * vp + c * vq;
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // Per mode: Gram (all warps), Jacobi eigendecomposition (warp 0, warp-
 // synchronous), and W = V diag(ev^-1/2) with the columns of eigenvalues
 // <= tol zeroed, so that l_i = || a_i W ||^2 = a_i G^+ a_i^T.
@@ -178,67 +249,7 @@ __global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a) {
     __syncwarp();
   }
   if (wid == 0) {
-    const int half = Rp / 2;
-    for (int sweep = 0; sweep < 40; ++sweep) {
-      double off = 0.0, dia = 0.0;
-      for (int e = lane; e < Rp * Rp; e += 32) {
-        const double v = G[e] * G[e];
-        if (e / Rp == e % Rp) dia += v; else off += v;
-      }
-      off = warp_sum(off);
-      dia = warp_sum(dia);
-      if (off <= 1e-28 * dia || Rp <= 1) break;
-      for (int step = 0; step < Rp - 1; ++step) {
-        for (int k = lane; k < half; k += 32) {
-          // circle method: slot 0 fixed, slots 1..Rp-1 rotate by `step`
-          const int s1 = Rp - 1 - k;
-          int p = k == 0 ? 0 : ((k - 1 + step) % (Rp - 1)) + 1;
-          int q = ((s1 - 1 + step) % (Rp - 1)) + 1;
-          if (p > q) { const int t = p; p = q; q = t; }
-          const double apq = G[p * Rp + q], app = G[p * Rp + p], aqq = G[q * Rp + q];
-          double c = 1.0, s = 0.0;
-          if (fabs(apq) > 1e-16 * fabs(app + aqq) && fabs(apq) > 1e-300) {
-            // tangent of the rotation angle in FP32 (an approximate annihilation
-            // is enough for Jacobi); (c, s) formed in FP64 so that the
-            // rotation is orthogonal to FP64 rounding
-            const double num = aqq - app, den = 2.0 * apq;
-            const bool in32 = fabs(den) > 1e-30 && fabs(den) < 1e30 && fabs(num) < 1e30;
-            const float theta = in32 ? (float)num / (float)den : (float)(num / den);
-            float tf;
-            if (fabsf(theta) > 1e18f) tf = 0.5f / theta;
-            else tf = copysignf(1.0f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.0f)));
-            const double t = (double)tf;
-            const double q2 = fma(t, t, 1.0);
-            const double y = rsqrt(q2);
-            c = y;
-            s = t * y;
-          }
-          cs[k] = c; sn[k] = s; pp[k] = p; qq[k] = q;
-        }
-        __syncwarp();
-        for (int e = lane; e < half * Rp; e += 32) {      // rows p, q
-          const int k = e / Rp, j = e % Rp;
-          const int p = pp[k], q = qq[k];
-          const double c = cs[k], s = sn[k];
-          const double gp = G[p * Rp + j], gq = G[q * Rp + j];
-          G[p * Rp + j] = c * gp - s * gq;
-          G[q * Rp + j] = s * gp + c * gq;
-        }
-        __syncwarp();
-        for (int e = lane; e < half * Rp; e += 32) {      // columns p, q (and V)
-          const int k = e / Rp, i = e % Rp;
-          const int p = pp[k], q = qq[k];
-          const double c = cs[k], s = sn[k];
-          const double gp = G[i * Rp + p], gq = G[i * Rp + q];
-          G[i * Rp + p] = c * gp - s * gq;
-          G[i * Rp + q] = s * gp + c * gq;
-          const double vp = V[i * Rp + p], vq = V[i * Rp + q];
-          V[i * Rp + p] = c * vp - s * vq;
-          V[i * Rp + q] = s * vp + c * vq;
-        }
-        __syncwarp();
-      }
-    }
+    jacobi_eig_warp(G, V, Rp, cs, sn, pp, qq, lane);
     // eigenvalues, tolerance, rank, W
     double emax = 0.0;
     for (int k = 0; k < R; ++k) emax = fmax(emax, G[k * Rp + k]);
@@ -408,4 +419,68 @@ size_t leverage_aux_bytes(int64_t maxI) {
          nchunk * TUCKER_MAX_ORDER * (TUCKER_MAX_RANK * (TUCKER_MAX_RANK + 1) / 2) * sizeof(double);
 }
 
+// Eigendecompositions of given R_n x R_n Grams (one CTA per mode, warp 0
+// works): the preconditioner of the CG ridge solver needs A^(n)T A^(n) =
+// V_n diag(ev_n) V_n^T of every factor.  gram[n] is row-major FP64 (as written
+// by the leverage launcher's gram output); evecs[n][r * R + k] = V_n[r][k],
+// evals[n][k] = ev_n[k].
+struct GramEigArgs {
+  int N;
+  int R[TUCKER_MAX_ORDER];
+  const double* gram[TUCKER_MAX_ORDER];
+  double* evecs[TUCKER_MAX_ORDER];
+  double* evals[TUCKER_MAX_ORDER];
+};
+
+__global__ void __launch_bounds__(32) k_gram_eig(GramEigArgs a) {
+  extern __shared__ double sm[];
+  const int n = blockIdx.x;
+  const int R = a.R[n];
+  const int Rp = R + (R & 1);
+  double* G = sm;
+  double* V = G + Rp * Rp;
+  double* cs = V + Rp * Rp;
+  double* sn = cs + Rp / 2;
+  int* pp = reinterpret_cast<int*>(sn + Rp / 2);
+  int* qq = pp + Rp / 2;
+  const int lane = threadIdx.x;
+  for (int e = lane; e < Rp * Rp; e += 32) {
+    const int r = e / Rp, c = e % Rp;
+    G[e] = (r < R && c < R) ? a.gram[n][r * R + c] : 0.0;
+    V[e] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  jacobi_eig_warp(G, V, Rp, cs, sn, pp, qq, lane);
+  for (int e = lane; e < R * R; e += 32) {
+    const int r = e / R, k = e % R;
+    a.evecs[n][e] = V[r * Rp + k];
+  }
+  for (int k = lane; k < R; k += 32) a.evals[n][k] = G[k * Rp + k];
+}
+
+tucker_status launch_gram_eig(tucker_handle* h, int N, const int* R, const double* const* gram,
+                              double* const* evecs, double* const* evals) {
+  GramEigArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = N;
+  int maxRp = 0;
+  for (int n = 0; n < N; ++n) {
+    a.R[n] = R[n];
+    a.gram[n] = gram[n];
+    a.evecs[n] = evecs[n];
+    a.evals[n] = evals[n];
+    const int Rp = R[n] + (R[n] & 1);
+    if (Rp > maxRp) maxRp = Rp;
+  }
+  const size_t smem = size_t(2 * maxRp * maxRp + maxRp) * sizeof(double) +
+                      size_t(maxRp + 2) * sizeof(int) + 64;
+  TK_CUDA(h, cudaFuncSetAttribute(k_gram_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  TK_COUNT(h);
+  k_gram_eig<<<N, 32, smem, h->stream>>>(a);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
 }  // namespace tk
+

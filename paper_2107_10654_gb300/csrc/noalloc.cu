@@ -34,25 +34,48 @@ tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t
 
 // The shared scratch.  Host code must not pass this symbol to a kernel: in
 // host code it is only a stand-in, so its device address is looked up with
-// cudaGetSymbolAddress once per device (see noalloc_scratch below).
+// cudaGetSymbolAddress once per device (see noalloc_device below).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TUCKER_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
-static std::once_flag g_once[kMaxDevices];
-static void* g_scratch_ptr[kMaxDevices];
-static cudaError_t g_scratch_err[kMaxDevices];
 
-// Device address of the scratch array on the current device (looked up on
-// the first call per device, with that device current).
-static cudaError_t noalloc_scratch(int device, void** out) {
-  std::call_once(g_once[device], [device] {
+// Per device: the array's device address and the two attributes the call
+// needs, cached after the first successful lookup only (a lookup that failed,
+// e.g. behind a pending error of earlier work, is tried again next call).
+struct NoallocDevice {
+  std::mutex mu;
+  bool ready = false;
+  void* scratch = nullptr;
+  int cc = 0;          // compute capability, major * 10 + minor
+  int sms = 0;
+};
+static NoallocDevice g_dev[kMaxDevices];
+
+// Look up (once per device, with that device current) the device address of
+// the scratch array, the compute capability and the SM count.
+static cudaError_t noalloc_device(int device, NoallocDevice** out) {
+  NoallocDevice& nd = g_dev[device];
+  std::lock_guard<std::mutex> lock(nd.mu);
+  if (!nd.ready) {
+    int major = 0, minor = 0, sms = 0;
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    g_scratch_ptr[device] = (e == cudaSuccess) ? p : nullptr;
-    g_scratch_err[device] = e;
-  });
-  *out = g_scratch_ptr[device];
-  return g_scratch_err[device];
+    cudaError_t e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    }
+    nd.scratch = p;
+    nd.cc = major * 10 + minor;
+    nd.sms = sms;
+    nd.ready = true;
+  }
+  *out = &nd;
+  return cudaSuccess;
 }
 
 static tucker_status noalloc_fail(char* err, size_t len, tucker_status s, const char* msg) {
@@ -85,17 +108,12 @@ extern "C" tucker_status tucker_sample_rows_noalloc(void* cuda_stream, int N, co
     cudaGetLastError();
     return noalloc_fail(err_host, err_len, TUCKER_ECUDA, "no current CUDA device");
   }
-  cudaDeviceProp prop;
-  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
-    cudaGetLastError();
-    return noalloc_fail(err_host, err_len, TUCKER_ECUDA, "cudaGetDeviceProperties failed");
-  }
-  if (prop.major * 10 + prop.minor != 103)
-    return noalloc_fail(err_host, err_len, TUCKER_ENOTSUP, "needs an sm_103 GPU");
-  void* scratch = nullptr;
-  if (noalloc_scratch(device, &scratch) != cudaSuccess || !scratch)
+  NoallocDevice* nd = nullptr;
+  if (noalloc_device(device, &nd) != cudaSuccess)
     return noalloc_fail(err_host, err_len, TUCKER_ECUDA,
-                        "cudaGetSymbolAddress of the scratch array failed");
+                        "device attributes or the scratch array's address could not be read");
+  if (nd->cc != 103) return noalloc_fail(err_host, err_len, TUCKER_ENOTSUP, "needs an sm_103 GPU");
+  void* scratch = nd->scratch;
 
   // A handle that lives on the stack and points into the static scratch:
   // no workspace growth, no pinned host buffer, no events are created.
@@ -103,7 +121,7 @@ extern "C" tucker_status tucker_sample_rows_noalloc(void* cuda_stream, int N, co
   h.err[0] = 0;
   h.stream = static_cast<cudaStream_t>(cuda_stream);
   h.device = device;
-  h.num_sms = prop.multiProcessorCount;
+  h.num_sms = nd->sms;
   int host_status = 0;
   h.h_status = &host_status;
   h.d_status = static_cast<int*>(scratch);               // first 256 bytes
@@ -115,15 +133,19 @@ extern "C" tucker_status tucker_sample_rows_noalloc(void* cuda_stream, int N, co
   F.N = N;
   int64_t d = 1;
   uint64_t total = 1;
+  double tot = 1.0;
   for (int n = 0; n < N; ++n) {
     if (I[n] < 1 || I[n] > (int64_t(1) << 31) || R[n] < 1 || R[n] > TUCKER_MAX_RANK || !lev[n])
       return noalloc_fail(err_host, err_len, TUCKER_EINVAL, "bad dims, ranks or scores");
     F.I[n] = I[n];
     F.R[n] = R[n];
     d *= R[n];
+    tot *= double(I[n]);
     total *= (uint64_t)I[n];
   }
   if (d > 8192) return noalloc_fail(err_host, err_len, TUCKER_EINVAL, "prod(R_n) exceeds 8192");
+  // linear row keys must not wrap: the same bound as tucker_sample_rows
+  if (tot >= 4.0e18) return noalloc_fail(err_host, err_len, TUCKER_EINVAL, "prod(I_n) too large");
   F.d = (int)d;
   F.total = total;
 

@@ -23,7 +23,7 @@ __all__ = ["TuckerError", "Handle", "Samples", "CooTensor", "tucker_leverage_sco
 
 PREC = {"fp64": L.PREC_FP64, "fp32": L.PREC_FP32, "tf32": L.PREC_TF32, "bf16": L.PREC_BF16}
 REG = {"exact": L.REG_EXACT, "augmented": L.REG_AUGMENTED}
-SOLVER = {"fp64": L.SOLVER_FP64_CHOLESKY, "mixed": L.SOLVER_MIXED}
+SOLVER = {"fp64": L.SOLVER_FP64_CHOLESKY, "mixed": L.SOLVER_MIXED, "kpcg": L.SOLVER_KRON_PCG}
 
 
 class TuckerError(RuntimeError):
@@ -87,8 +87,9 @@ class Handle:
         _check(self.h, L.load().tucker_set_sync(self.h, int(synchronous)))
 
     def set_solver(self, solver: str):
-        """Ridge solver of later updates: "fp64" (FP64 Cholesky) or "mixed"
-        (FP32 Cholesky preconditioning an FP64 iterative refinement)."""
+        """Ridge solver of later updates: "fp64" (FP64 Cholesky), "mixed"
+        (FP32 Cholesky preconditioning an FP64 iterative refinement) or "kpcg"
+        (Kronecker-preconditioned CG inside the same refinement)."""
         _check(self.h, L.load().tucker_set_solver(self.h, SOLVER[solver]))
 
     def close(self):

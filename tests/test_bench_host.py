@@ -60,6 +60,12 @@ def test_reference_arm_line():
     assert e2e["value"] == ln["value"] and e2e["unit"] == "ms"
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert ln["oracle_exact"]["ms"] > 0 and ln["oracle_exact"]["sample"]
+    # the line is timed at the sample count its own ladder finds for the 1.01x target
+    lad = ln["m_ladder"]
+    assert lad["rows"] and lad["rows"][0]["m"] == ln["config"]["m_workload"]
+    assert ln["config"]["m"] == (lad["m_star"] or ln["config"]["m_workload"])
+    if lad["m_star"]:
+        assert lad["rows"][-1]["median_ratio"] <= bench.LADDER_TARGET
 
 
 def test_oracle_exact_timing_skips_the_observed_entry_gram():

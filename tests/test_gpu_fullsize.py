@@ -9,7 +9,12 @@ oracle can produce at that size:
     sampled right-hand-side entries, and the FP64 residual of the returned
     core, h - (K_S^T W K_S + lambda I) g, evaluated by the oracle row by row;
   * 256^3 FP64, d = 512, m = 2e4: the adjoint against the oracle's gradient and
-    FP64 central differences on 64 random directions.
+    FP64 central differences on 64 random directions;
+  * 128^4 FP32: the exact dense update (Kronecker eigendecomposition form)
+    against the oracle's;
+  * 512^3: ten ALS sweeps (Alg. 2), exact and sketched, against the oracle's
+    sweeps (FP64 data: the comparison is of the arithmetic, not of the
+    storage precision).
 """
 import dataclasses
 
@@ -18,7 +23,7 @@ import pytest
 import torch
 
 import synth
-from oracle import leverage as LV, sampling as S, core_update as CU, adjoint as ADJ
+from oracle import leverage as LV, sampling as S, core_update as CU, adjoint as ADJ, als as ALS
 from tests.gpu_common import dev, dev_keys, host_keys, rel_err, handle  # noqa: F401
 from paper_2107_10654_gb300 import tucker as T
 
@@ -100,6 +105,36 @@ def test_bench_workload_sketched_and_exact_match_oracle(handle, dense512):
     assert 1.0 <= ratio <= 1.01
 
 
+@pytest.mark.parametrize("sketched", [False, True])
+def test_bench_workload_ten_als_sweeps(handle, dense512, sketched):
+    w, X, _ = dense512
+    X64 = X.astype(np.float64)
+    core0, F0 = synth.init_state(w)
+    Xd = dev(X64)
+    Fd = [dev(a.astype(np.float64)) for a in F0]
+    cd = dev(core0.reshape(-1).astype(np.float64))
+    c, F = core0.astype(np.float64), [a.astype(np.float64) for a in F0]
+    assert w.sweeps == 10
+    for s in range(w.sweeps):
+        loss, rmse = T.tucker_als_sweep(handle, Xd, Fd, cd, w.lam, sketched, w.m, w.seed_sample, s)
+        c, F = ALS.als_sweep(X64, c, F, w.lam, sketched, w.m, w.seed_sample, s)
+    ref_loss = ALS.tucker_loss(X64, c, F, w.lam)
+    assert abs(loss - ref_loss) <= 1e-8 * ref_loss
+    assert abs(rmse - ALS.rmse(X64, c, F)) <= 1e-8
+    # Sketched sweeps resample from the current factors through the fixed-point
+    # CDF q_i = floor(l_i 2^32): factors that agree to FP64 rounding can put a
+    # score on either side of a quantisation step, which moves that row's p by
+    # 1 / q_i (about 1.5e-8 here, l_i ~ R / I = 1/64).  The oracle alone shows it:
+    # a 1e-13 perturbation of the initial state moves its sketched core by 1e-8
+    # after one sweep and its exact core by 1e-11.  Hence 1e-6 for the state of
+    # the sketched sweeps, 1e-8 for the exact ones.
+    tol = 1e-6 if sketched else 1e-8
+    assert rel_err(cd.cpu().numpy(), c.reshape(-1)) <= tol
+    for a, b in zip(Fd, F):
+        assert rel_err(a.cpu().numpy(), b) <= tol
+    del Xd
+
+
 def test_bench_workload_sample_bit_exact(handle, dense512):
     w, X, F = dense512
     _check_sample(handle, F, w.dims, w.ranks, w.m, w.seed_sample)
@@ -127,6 +162,13 @@ def test_4way_full_size(handle, dense4, prec):
         del G
     g = T.tucker_core_update_sketched(handle, Xd, Fd, w.lam, 0, 0, 0, "exact", prec, fixed=smp)
     _check_residual(F, w.dims, ku, wts, x, w.lam, g.cpu().numpy())
+
+
+def test_4way_exact_full_size(handle, dense4):
+    w, X, F = dense4
+    g = T.tucker_core_update_exact(handle, dev(X), [dev(a) for a in F], w.lam, "fp64")
+    ref = CU.exact_core_kron_eig(X, F, w.lam)
+    assert rel_err(g.cpu().numpy(), ref) <= 1e-5           # FP32 data, FP32 first product
 
 
 # ------------------------------------------------------------------ 1024^3 at 10 %, d = 4096

@@ -62,3 +62,18 @@ def test_noalloc_allocates_nothing_and_rejects_oversize(handle):
     # the array is still usable after a rejected call
     got = T.tucker_sample_rows_noalloc(dims, ranks, lev, m, 1, 0, out=out)
     assert got.n_unique > 0
+
+
+def test_noalloc_rejects_wrapping_keys_like_sample_rows(handle):
+    # 600^7 = 2.8e19 rows: linear keys would wrap modulo 2^64, although the CDFs
+    # (7 x 600 entries) fit the fixed array; both entry points refuse before any
+    # device work
+    dims, ranks, m = (600,) * 7, (1,) * 7, 1000
+    lev = [torch.full((600,), 1.0 / 600, dtype=torch.float64, device="cuda") for _ in dims]
+    out = T.Samples.empty(m, "cuda")
+    with pytest.raises(T.TuckerError) as e1:
+        T.tucker_sample_rows(handle, dims, ranks, lev, m, 1, 0, out=out)
+    with pytest.raises(T.TuckerError) as e2:
+        T.tucker_sample_rows_noalloc(dims, ranks, lev, m, 1, 0, out=out)
+    assert e1.value.name == "EINVAL" and e2.value.name == "EINVAL"
+    assert "too large" in str(e2.value)
