@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const uint64_t* in, u
 
 // ------------------------------------------------- small samples: one cluster
 // For n <= CL_MAX keys the whole sort + dedupe runs in one launch of a cluster
-// of CL_CTAS CTAs.  The keys stay in the CTAs' shared memory between passes
+// of CL_CTAS CTAs (CL_CTAS_WIDE, where the device schedules it, up to
+// CL_MAX_WIDE keys).  The keys stay in the CTAs' shared memory between passes
 // (CTA c holds sorted positions [c CL_CHUNK, (c + 1) CL_CHUNK)): a pass reads
 // its 8192 keys (32 warps x 8 rounds x 32 lanes) from its own shared memory,
 // ranks them with the same stable match_any scheme as above, and stores each
@@ -170,12 +171,14 @@ __device__ __forceinline__ unsigned digit_peers(int dg, int dbits) {
   return dg < 0 ? inv : m;
 }
 
-constexpr int CL_CTAS = 8;
+constexpr int CL_CTAS = 8;                                  // portable cluster size
+constexpr int CL_CTAS_WIDE = 16;                            // opt-in size, where schedulable
 constexpr int CL_THREADS = 1024;
 constexpr int CL_WARPS = CL_THREADS / 32;
 constexpr int CL_ROUNDS = 8;
 constexpr int CL_CHUNK = CL_THREADS * CL_ROUNDS;            // 8192 keys per CTA
 constexpr int64_t CL_MAX = (int64_t)CL_CTAS * CL_CHUNK;     // 65536
+constexpr int64_t CL_MAX_WIDE = (int64_t)CL_CTAS_WIDE * CL_CHUNK;   // 131072
 constexpr int CL_MAX_DBITS = 10;
 
 static int cl_digit_bits(int key_bits) {
@@ -195,7 +198,8 @@ static size_t cl_smem_bytes(int dbits) {
   return (size_t)CL_CHUNK * 8 + (size_t)cl_wofs_ints(dbits) * 4 + rx * 4;
 }
 
-__global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
+template <int CTAS>
+__global__ void __launch_bounds__(CL_THREADS)
     k_sort_dedupe_cluster(const uint64_t* keys_in, int n, int key_bits, int dbits,
                           uint64_t* keys_u, uint32_t* counts_u, int* d_n_unique) {
   namespace cg = cooperative_groups;
@@ -250,11 +254,11 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
     cluster.sync();                           // every CTA's totals final; every key loaded
     int64_t all_d = 0, before = 0;
     if (threadIdx.x < RXB) {
-      int v[CL_CTAS];
+      int v[CTAS];
 #pragma unroll
-      for (int cc = 0; cc < CL_CTAS; ++cc) v[cc] = *cluster.map_shared_rank(&ctot[threadIdx.x], cc);
+      for (int cc = 0; cc < CTAS; ++cc) v[cc] = *cluster.map_shared_rank(&ctot[threadIdx.x], cc);
 #pragma unroll
-      for (int cc = 0; cc < CL_CTAS; ++cc) {
+      for (int cc = 0; cc < CTAS; ++cc) {
         all_d += v[cc];
         if (cc < c) before += v[cc];
       }
@@ -316,14 +320,14 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
   int64_t ubase = 0, utot = 0;
   int next_first = n;                                          // first head after this CTA
   {
-    int hv[CL_CTAS], fv[CL_CTAS];
+    int hv[CTAS], fv[CTAS];
 #pragma unroll
-    for (int cc = 0; cc < CL_CTAS; ++cc) {
+    for (int cc = 0; cc < CTAS; ++cc) {
       hv[cc] = *cluster.map_shared_rank(&cta_heads[0], cc);
       fv[cc] = *cluster.map_shared_rank(&cta_heads[1], cc);
     }
 #pragma unroll
-    for (int cc = CL_CTAS - 1; cc >= 0; --cc) {
+    for (int cc = CTAS - 1; cc >= 0; --cc) {
       if (cc < c) ubase += hv[cc];
       utot += hv[cc];
       if (cc > c && hv[cc] > 0) next_first = fv[cc];
@@ -398,6 +402,60 @@ size_t sort_dedupe_scratch(int64_t n) {
          size_t(n) * 8 + 4096;
 }
 
+static cudaLaunchConfig_t sort_cluster_cfg(cudaLaunchAttribute* at, int ctas, size_t smem,
+                                            cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = ctas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(CL_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Whether a 16-CTA cluster of the sort kernel with smem bytes each can be
+// scheduled (the device's answer, asked once per size).
+static bool wide_cluster_ok(size_t smem) {
+  static size_t ok = 0, bad = ~size_t(0);
+  if (smem <= ok) return true;
+  if (smem >= bad) return false;
+  const void* kern = (const void*)k_sort_dedupe_cluster<CL_CTAS_WIDE>;
+  int n = 0;
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t cfg = sort_cluster_cfg(at, CL_CTAS_WIDE, smem, nullptr);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    bad = smem;
+    return false;
+  }
+  ok = smem;
+  return true;
+}
+
+template <int CTAS>
+static tucker_status launch_sort_cluster(tucker_handle* h, const uint64_t* keys_in, int64_t n,
+                                         int key_bits, int dbits, size_t smem, uint64_t* keys_u,
+                                         uint32_t* counts_u, int* d_n_unique) {
+  const void* kern = (const void*)k_sort_dedupe_cluster<CTAS>;
+  if (CTAS > 8)
+    TK_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  TK_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t cfg = sort_cluster_cfg(at, CTAS, smem, h->stream);
+  TK_COUNT(h);
+  TK_CUDA(h, cudaLaunchKernelEx(&cfg, k_sort_dedupe_cluster<CTAS>, keys_in, (int)n, key_bits,
+                                dbits, keys_u, counts_u, d_n_unique));
+  return TUCKER_OK;
+}
+
 // Sort keys_in[0..n) (keys < 2^key_bits) and deduplicate into keys_u/counts_u;
 // *d_n_unique (device) receives the number of distinct keys.
 tucker_status sort_dedupe(tucker_handle* h, const uint64_t* keys_in, int64_t n, int key_bits,
@@ -407,17 +465,13 @@ tucker_status sort_dedupe(tucker_handle* h, const uint64_t* keys_in, int64_t n, 
     return fail(h, TUCKER_EINTERNAL, "sort scratch too small");
   const int nb = ceil_div(n, SORT_TILE);
   const int nt = ceil_div(n, RX_TILE);
-  if (n <= CL_MAX) {
-    const int dbits = cl_digit_bits(key_bits);
-    const size_t smem = cl_smem_bytes(dbits);
-    TK_CUDA(h, cudaFuncSetAttribute((const void*)k_sort_dedupe_cluster,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    TK_COUNT(h);
-    k_sort_dedupe_cluster<<<CL_CTAS, CL_THREADS, smem, h->stream>>>(
-        keys_in, (int)n, key_bits, dbits, keys_u, counts_u, d_n_unique);
-    TK_LAUNCH(h);
-    return TUCKER_OK;
-  }
+  const int dbits = cl_digit_bits(key_bits);
+  const size_t csmem = cl_smem_bytes(dbits);
+  if (n <= CL_MAX) return launch_sort_cluster<CL_CTAS>(h, keys_in, n, key_bits, dbits, csmem,
+                                                       keys_u, counts_u, d_n_unique);
+  if (n <= CL_MAX_WIDE && wide_cluster_ok(csmem))
+    return launch_sort_cluster<CL_CTAS_WIDE>(h, keys_in, n, key_bits, dbits, csmem, keys_u,
+                                             counts_u, d_n_unique);
   Arena ar(scratch);
   uint64_t* b0 = ar.get<uint64_t>(n);
   uint64_t* b1 = ar.get<uint64_t>(n);

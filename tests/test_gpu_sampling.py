@@ -61,6 +61,9 @@ def _oracle_sample(levs, dims, m, seed, sweep, reg, d, obs=None, max_draws=0):
     ((16, 12, 10, 8), (2, 2, 2, 2), 30000),     # many duplicates
     ((9, 5, 7, 6, 4), (2, 1, 3, 2, 2), 999),    # order 5: second Philox stream
     ((512, 512, 512), (8, 8, 8), 50000),        # full-size dense 3-way sample
+    ((512, 512, 512), (8, 8, 8), 100000),       # the 1.01x sample count: 16-CTA cluster sort
+    ((30, 20, 10), (3, 2, 2), 131072),          # the 16-CTA sort at its largest, 6000 rows
+    ((512, 512, 512), (8, 8, 8), 131073),       # one key past it: the multi-pass sort
     ((128, 128, 128, 128), (8, 8, 8, 8), 200000),   # full-size dense 4-way sample
 ])
 @pytest.mark.parametrize("reg", ["exact", "augmented"])
