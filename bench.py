@@ -515,6 +515,15 @@ class Timer:
 
 
 STAGES = ("ms_leverage", "ms_sample", "ms_dedupe", "ms_gather", "ms_gram", "ms_solve")
+RIDGE_LAMBDA = 1e8
+
+
+def ridge_alg1_count(d, d_eff, eps=0.1, delta=0.1):
+    """Alg. 1 line 3's s: with the exact ridge scores (d_eff given) beta' =
+    d / (d_eff + d min{1, d - d_eff}) (Eq. beta_prime); classical scores
+    (d_eff None) beta' = 1/2."""
+    bp = 0.5 if d_eff is None else d / (d_eff + d * min(1.0, d - d_eff))
+    return math.ceil(4.0 * d / bp * max(420.0 * math.log(4.0 * d / delta), 1.0 / (delta * eps)))
 
 
 def measure_workload(h, w, X, F, prec, reg, steps, warmup, timer, m_override=None):
@@ -695,6 +704,23 @@ def main():
                                                                 stf["solve_id"], gf, gbar),
                             min(args.steps, 5))
             extra["adjoint_ms"] = statistics.mean(ms_a)
+        # lambda-ridge leverage sampling of K (Lemma 4.1, lambda > 0) beside the classical
+        # product sampler on the same tensor with a strong ridge (lambda = 1e8: d_eff(K)
+        # is about half of d), each on a x2 ladder from m = w.m / 8
+        ridge_cfg = None
+        if not missing and not args.no_configs and rank == 0:
+            wr = dataclasses.replace(w, lam=RIDGE_LAMBDA, m=max(1, w.m // 8))
+            _, _, K_r, deff = T.tucker_ridge_tables(h, F, wr.lam)
+            ridge_cfg = {"lambda": wr.lam, "d_eff": deff, "d": w.d,
+                         "alg1_count_ridge": ridge_alg1_count(w.d, deff),
+                         "alg1_count_classical": ridge_alg1_count(w.d, None)}
+            for regm in ("ridge", "exact"):
+                recr = measure_workload(h, wr, X, F, prec, regm, min(args.steps, 10), args.warmup,
+                                        timer)
+                ridge_cfg[regm] = {k: recr[k] for k in ("m_star", "ladder", "exact_ms")} | {
+                    "ms_at_m_star": recr["at_m_star"]["ms"],
+                    "loss_ratio_at_m_star": recr["at_m_star"]["loss_ratio"],
+                    "stage_ms_at_m_star": recr["at_m_star"]["stage_ms"]}
         X_h, F_h = hb["X_h"], hb["F_h"]
         f_bytes = sum(a.numel() * a.element_size() for a in hb["F_pin"])
         del X, F, hb
@@ -818,6 +844,7 @@ def main():
                 "roofline": roof, "roofline_gram": roof_gram, "roofline_solve": roof_solve,
                 "configs": {k: {kk: vv for kk, vv in v.items() if kk != "ladder"} | {"ladder": v["ladder"]}
                             for k, v in configs.items()},
+                "ridge_sampling": ridge_cfg,
                 "cpu_baseline": cpu,
                 "e2e": {"value": ms_e2e, "unit": "ms",
                         "h2d_bytes_per_step": int(in_bytes + f_bytes),

@@ -145,7 +145,14 @@ typedef enum {
    * (mass l(K), normalised to d) or one of the d regulariser rows (mass 1
    * each); the sampled regulariser rows give lambda*diag(D) in place of
    * lambda*I */
-  TUCKER_REG_AUGMENTED = 1
+  TUCKER_REG_AUGMENTED = 1,
+  /* rows drawn from the lambda-ridge leverage distribution of K itself,
+   * l^lam(K) / d_eff(K) (Lemma 4.1 with lambda > 0; see tucker_ridge_tables),
+   * lambda*I added exactly; dense X only.  With m = 0 the sample count is
+   * Alg. 1 line 3's s with beta' of Eq. beta_prime for these exact scores:
+   * beta' = d / (d_eff + d min{1, d - d_eff}) (1/2 <= beta' <= 1), so fewer
+   * rows are drawn as lambda grows and d_eff(K) shrinks. */
+  TUCKER_REG_RIDGE = 2
 } tucker_reg;
 
 /* The data tensor X of the problem statement (Sec. 2): either dense or a list
@@ -360,6 +367,43 @@ tucker_status tucker_core_solve_adjoint(tucker_handle* h, const tucker_tensor* X
                                         tucker_prec prec, const tucker_samples* samples,
                                         uint64_t solve_id, const double* g, const double* gbar,
                                         double* const* dA_out, double* dx_out);
+
+/* Tables of the lambda-ridge leverage distribution of K (Lemma 4.1 with
+ * lambda > 0; Eq. d_eff_def).  With the thin SVDs A^(n) = U^(n) S^(n) V^(n)T
+ * (from the Jacobi eigendecomposition of A^(n)T A^(n), eigenpairs in
+ * decreasing order, K_n = min(I_n, R_n) of them, squared singular values at
+ * or below max(I_n, R_n) 2^-52 times the largest counted as zero):
+ *     l^lam_i(K) = sum_t c_t prod_n usq_n[t_n][i_n],
+ *     usq_n[t][i] = (u^(n)_{i t})^2,   c_t = P_t / (P_t + lambda),
+ *     P_t = prod_n s^2_{t_n}(A^(n)),   d_eff(K) = sum_t c_t.
+ *   usq_out[N]      host array of device pointers, FP64 K_n x I_n each
+ *                   (column t contiguous; 0 for a component cut to zero)
+ *   c_out           device FP64 [prod K_n], row-major over (t_1 .. t_N)
+ *   K_out_host      nullable host int[N]: K_n
+ *   d_eff_out_host  nullable: d_eff(K) (synchronises)
+ * Errors: EINVAL. */
+tucker_status tucker_ridge_tables(tucker_handle* h, int N, const int64_t* I, const int* R,
+                                  tucker_dtype dtype, const void* const* A, double lambda,
+                                  double* const* usq_out, double* c_out, int* K_out_host,
+                                  double* d_eff_out_host);
+
+/* Draw m rows of K from l^lam(K) / d_eff(K) given its tables (the mixture
+ * over components t with weights c_t of the product distributions
+ * prod_n usq_n[t_n][.]) and deduplicate them.  Fixed-point weights
+ * q = floor(clamp(x, 0, 1) 2^32) of c (one CDF, row-major over t) and of each
+ * column usq_n[t] (one CDF each); draw t takes its component from word 0 of
+ * Philox4x64-10 stream 3 (counter (t, 3, 0, 0), key (seed, sweep)) and its
+ * index in mode n from word n%4 of stream n/4, each by
+ * min{i : C_i > floor(u Q / 2^64)}.  prob[u] is the exact probability of the
+ * row under that arithmetic, sum_t (q^c_t / Q^c) prod_n (q^(n,t_n)_{i_n} /
+ * Q^(n,t_n)) in row-major order of t (FP64).  T = m.
+ *   K[N]            host: components per mode (1 <= K_n <= min(I_n, 64))
+ *   usq[N], c       device tables as written by tucker_ridge_tables
+ *   out             caller arrays of capacity >= m; n_unique/n_draws written
+ * Synchronises.  Errors: EINVAL, ERANK (every c_t is 0), ECAPACITY. */
+tucker_status tucker_sample_rows_ridge(tucker_handle* h, int N, const int64_t* I, const int* K,
+                                       const double* const* usq, const double* c, int64_t m,
+                                       uint64_t seed, uint32_t sweep, tucker_samples* out);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free sampling.  The paper has no counterpart to this entry

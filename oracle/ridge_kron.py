@@ -170,6 +170,18 @@ def missing_ridge_beta_bound(factors: Sequence[np.ndarray], lam: float) -> float
     return 1.0 / (2.0 + p / lam)
 
 
+def ridge_sample_count(factors: Sequence[np.ndarray], lam: float, eps: float,
+                       delta: float) -> int:
+    """Sample count for rows drawn from the exact lam-ridge scores of K: Alg. 1
+    line 3's s with beta' from Eq. beta_prime, taking the scores themselves as
+    the overestimate (beta = 1, ||l-hat||_1 = d_eff(K)) and d_eff(K) as the
+    lower bound d'_eff."""
+    d = int(np.prod([np.asarray(A).shape[1] for A in factors]))
+    d_eff = kron_effective_dimension(factors, lam)
+    bp = lemma_beta_prime(1.0, d, d_eff, d_eff, d_eff)
+    return S.paper_sample_count(d, eps, delta, bp)
+
+
 # ------------------------------------------- exact sampler of l^lam(K) / d_eff(K)
 
 def ridge_mixture_tables(factors: Sequence[np.ndarray], lam: float):

@@ -15,7 +15,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTSPD", "ERANK", "EDRAWLIM
                 "ECAPACITY", "ENOTSUP", "EINTERNAL"]
 F32, F64 = 0, 1
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16 = 0, 1, 2, 3
-REG_EXACT, REG_AUGMENTED = 0, 1
+REG_EXACT, REG_AUGMENTED, REG_RIDGE = 0, 1, 2
 SOLVER_FP64_CHOLESKY, SOLVER_MIXED, SOLVER_KRON_PCG = 0, 1, 2
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtucker.so")
@@ -75,6 +75,10 @@ SIGNATURES = {
                                             C.c_uint64, _P, _P, _PP, _P]),
     "tucker_sketched_gram": (C.c_int, [_P, C.POINTER(TuckerTensor), _IP, _PP, C.c_int,
                                        C.POINTER(TuckerSamples), _P, _P]),
+    "tucker_ridge_tables": (C.c_int, [_P, C.c_int, _I64P, _IP, C.c_int, _PP, C.c_double, _PP, _P,
+                                      _IP, _DP]),
+    "tucker_sample_rows_ridge": (C.c_int, [_P, C.c_int, _I64P, _IP, _PP, _P, C.c_int64, C.c_uint64,
+                                           C.c_uint32, C.POINTER(TuckerSamples)]),
     "tucker_sample_rows_noalloc": (C.c_int, [_P, C.c_int, _I64P, _IP, _PP, C.c_int64, C.c_uint64,
                                              C.c_uint32, C.c_int, C.POINTER(TuckerSamples),
                                              C.c_char_p, C.c_size_t]),

@@ -114,6 +114,17 @@ tucker_status launch_to_f64(tucker_handle* h, const FactorSet& F, double* const*
 tucker_status launch_gram_eig(tucker_handle* h, int N, const int* R, const double* const* gram,
                               double* const* evecs, double* const* evals);
 int kpcg_fits(int d, int N, const int* R);
+int ridge_components(const FactorSet& F, int* K);
+size_t ridge_tables_scratch(const FactorSet& F);
+size_t ridge_sample_scratch(const FactorSet& F, int64_t m);
+tucker_status ridge_tables(tucker_handle* h, const FactorSet& F, double lambda, char* scratch,
+                           double* const* usq, double* c, double* d_eff,
+                           double* const* V_out, double* const* ev_out);
+tucker_status ridge_draw(tucker_handle* h, const FactorSet& F, const double* const* usq,
+                         const double* c, int64_t m, uint64_t seed, uint32_t sweep,
+                         char* scratch, uint64_t* keys_raw, int64_t* d_T, RidgeState* st);
+tucker_status ridge_prob(tucker_handle* h, RidgeState* st, const uint64_t* keys_u,
+                         const int* n_unique, int64_t cap, double* prob);
 tucker_status launch_kpcg(tucker_handle* h, const float* M, const double* regdiag, int d, int N,
                           const int* R, const double* const* V, const double* const* ev,
                           const double* rhs, double* out, double* upd, double* stats,
@@ -827,9 +838,42 @@ tucker_status tucker_sample_rows(tucker_handle* h, int N, const int64_t* I, cons
   return TUCKER_OK;
 }
 
-static int64_t paper_s(int d, double eps, double delta) {
-  double s = 4.0 * d / 0.5 * fmax(420.0 * log(4.0 * d / delta), 1.0 / (delta * eps));
+// Alg. 1 line 3: s = ceil(4 d / beta' max{420 ln(4 d / delta), 1 / (delta eps)}).
+static int64_t paper_s(int d, double eps, double delta, double beta_prime = 0.5) {
+  double s = 4.0 * d / beta_prime * fmax(420.0 * log(4.0 * d / delta), 1.0 / (delta * eps));
   return (int64_t)ceil(s);
+}
+
+// beta' of Eq. beta_prime (Lemma beta_overestimate) for the exact lambda-ridge
+// scores of K as the overestimate: beta = 1, ||l-hat||_1 = d_eff, and d_eff
+// itself as the lower bound d'_eff; both terms of the minimum equal
+// d / (d_eff + d min{1, d - d_eff}).
+static double ridge_beta_prime(int d, double d_eff) {
+  const double mlt = fmin(1.0, (double)d - d_eff);
+  const double a = 1.0 * d / d_eff / (1.0 + d * mlt / d_eff);
+  const double b = 1.0 / (d_eff / d + mlt);
+  return fmin(a, b);
+}
+
+// Buffers of the lambda-ridge sampler inside the sketch arena.
+struct RidgeBufs {
+  double* usq[TUCKER_MAX_ORDER];
+  double* c;
+  double* d_eff;
+  double* p;
+  char* tab_scratch;
+  char* samp_scratch;
+};
+
+static void carve_ridge(Arena& ar, const FactorSet& F, int64_t cap, RidgeBufs* r) {
+  int K[TUCKER_MAX_ORDER];
+  const int dK = ridge_components(F, K);
+  for (int n = 0; n < F.N; ++n) r->usq[n] = ar.get<double>((size_t)K[n] * F.I[n]);
+  r->c = ar.get<double>(dK);
+  r->d_eff = ar.get<double>(1);
+  r->p = ar.get<double>(cap);
+  r->tab_scratch = ar.get<char>(ridge_tables_scratch(F));
+  r->samp_scratch = ar.get<char>(ridge_sample_scratch(F, cap));
 }
 
 tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor* X, const int* R,
@@ -845,9 +889,31 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   if (!core_out) return fail(h, TUCKER_EINVAL, "core_out NULL");
   if (!(lambda >= 0.0) || (reg == TUCKER_REG_AUGMENTED && !(lambda > 0.0)))
     return fail(h, TUCKER_EINVAL, "lambda must be >= 0 (> 0 in augmented mode)");
-  if (reg != TUCKER_REG_EXACT && reg != TUCKER_REG_AUGMENTED) return fail(h, TUCKER_EINVAL, "reg");
+  if (reg != TUCKER_REG_EXACT && reg != TUCKER_REG_AUGMENTED && reg != TUCKER_REG_RIDGE)
+    return fail(h, TUCKER_EINVAL, "reg");
   if (prec < TUCKER_PREC_FP64 || prec > TUCKER_PREC_BF16) return fail(h, TUCKER_EINVAL, "prec");
+  const bool ridge = reg == TUCKER_REG_RIDGE && !fixed;
+  if (ridge && !X->dense) return fail(h, TUCKER_EINVAL, "ridge sampling needs a dense X");
+  // a frozen sample carries its probabilities: the ridge mode then is the exact one
+  const int greg = reg == TUCKER_REG_RIDGE ? TUCKER_REG_EXACT : reg;
   int64_t cap;
+  if (ridge && m == 0) {
+    // Alg. 1 line 3 with beta' of Eq. beta_prime for the exact ridge scores: d_eff first
+    if (!(eps > 0 && eps < 1 && delta > 0 && delta < 1))
+      return fail(h, TUCKER_EINVAL, "eps, delta must be in (0,1) when m = 0");
+    Arena sz0(nullptr);
+    RidgeBufs r0;
+    carve_ridge(sz0, F, 1, &r0);
+    TK_TRY(ws_reserve(h, sz0.off));
+    Arena ar0(h->ws);
+    carve_ridge(ar0, F, 1, &r0);
+    TK_TRY(ridge_tables(h, F, lambda, r0.tab_scratch, r0.usq, r0.c, r0.d_eff, nullptr, nullptr));
+    double deff = 0.0;
+    TK_CUDA(h, cudaMemcpyAsync(&deff, r0.d_eff, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    TK_TRY(device_status(h));
+    if (!(deff > 0.0)) return fail(h, TUCKER_ERANK, "all ridge weights are zero");
+    m = paper_s(F.d, eps, delta, ridge_beta_prime(F.d, deff));
+  }
   if (fixed) {
     if (!fixed->keys || !fixed->counts || !fixed->prob || fixed->n_unique < 1 ||
         fixed->n_unique > fixed->capacity || fixed->n_draws < 1)
@@ -873,13 +939,17 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   h->timing = timing;
   SketchBufs b;
   memset(&b, 0, sizeof(b));
+  RidgeBufs rb;
+  memset(&rb, 0, sizeof(rb));
   Arena sz(nullptr);
   carve_sketch(sz, h, F, cap, prec, fixed != nullptr, &b);
+  if (ridge) carve_ridge(sz, F, cap, &rb);
   size_t extra = fixed ? 0 : sample_keys_scratch(F, !X->dense);
   TK_TRY(ws_reserve(h, sz.off + extra));
   TK_TRY(chol_reserve(h, F.d));
   Arena ar(h->ws);
   carve_sketch(ar, h, F, cap, prec, fixed != nullptr, &b);
+  if (ridge) carve_ridge(ar, F, cap, &rb);
   ev_record(h, timing, 0);
   int64_t T = 0;
   const uint64_t* keys_u;
@@ -889,7 +959,30 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   const bool kpcg = kpcg_wanted(h, F, prec);
   h->chol.kres_n = 0;
   h->chol.kron_ready = 0;
-  if (!fixed) {
+  if (ridge) {
+    // lambda-ridge leverage of K (Lemma 4.1): the factor eigenpairs (also the CG
+    // preconditioner's), the column tables and mixture weights, m draws, dedupe,
+    // and the probabilities of the distinct rows
+    TK_TRY(ridge_tables(h, F, lambda, rb.tab_scratch, rb.usq, rb.c, rb.d_eff,
+                        kpcg ? h->chol.kv : nullptr, kpcg ? h->chol.ke : nullptr));
+    if (kpcg) {
+      h->chol.kN = F.N;
+      for (int n = 0; n < F.N; ++n) h->chol.kR[n] = F.R[n];
+      h->chol.kron_ready = 1;
+    }
+    ev_record(h, timing, 1);
+    RidgeState rst;
+    TK_TRY(ridge_draw(h, F, rb.usq, rb.c, m, seed, sweep, rb.samp_scratch, b.keys_raw, b.d_T,
+                      &rst));
+    T = m;
+    ev_record(h, timing, 2);
+    TK_TRY(sort_dedupe(h, b.keys_raw, m, bits_for(F.total), b.keys_u, b.counts, b.nu,
+                       b.sort_scratch, b.sort_bytes));
+    TK_TRY(ridge_prob(h, &rst, b.keys_u, b.nu, cap, rb.p));
+    keys_u = b.keys_u;
+    counts = b.counts;
+    p_in = rb.p;
+  } else if (!fixed) {
     TK_TRY(launch_leverage(h, F, b.lev, b.cdf, b.rank, nullptr, nullptr,
                            kpcg ? b.fgram : nullptr));
     ev_record(h, timing, 1);
@@ -939,7 +1032,7 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   }
   ev_record(h, timing, 3);
   if (tables_ready) TK_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-  TK_TRY(launch_gather(h, F, b.cdf, reg, keys_u, counts, b.nu, b.d_T, X, cap, b.idx, b.w, b.x,
+  TK_TRY(launch_gather(h, F, b.cdf, greg, keys_u, counts, b.nu, b.d_T, X, cap, b.idx, b.w, b.x,
                        b.p, b.sw32, b.nreal, b.D, p_in, b.ptab, tables_ready));
   ev_record(h, timing, 4);
   RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
@@ -1282,7 +1375,8 @@ tucker_status tucker_core_solve_adjoint(tucker_handle* h, const tucker_tensor* X
   TK_CUDA(h, cudaMemcpyAsync(b.nu, &nuh, sizeof(int), cudaMemcpyHostToDevice, h->stream));
   TK_CUDA(h, cudaMemcpyAsync(b.d_T, &T, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
   if (!X->dense) { int pr; TK_TRY(hash_ensure(h, X, &pr)); }
-  TK_TRY(launch_gather(h, F, b.cdf, reg, samples->keys, samples->counts, b.nu, b.d_T, X, cap,
+  const int greg = reg == TUCKER_REG_RIDGE ? TUCKER_REG_EXACT : reg;   // p comes with the sample
+  TK_TRY(launch_gather(h, F, b.cdf, greg, samples->keys, samples->counts, b.nu, b.d_T, X, cap,
                        b.idx, b.w, b.x, b.p, b.sw32, b.nreal, b.D, samples->prob, nullptr));
   TK_CUDA(h, cudaStreamSynchronize(h->stream));
   RowSet rs = make_rowset(F, b.idx, b.w, b.nreal);
@@ -1310,6 +1404,78 @@ tucker_status tucker_core_solve_adjoint(tucker_handle* h, const tucker_tensor* X
   TK_CUDA(h, cudaMemsetAsync(dx_out, 0, sizeof(double) * cap, h->stream));
   TK_TRY(launch_adjoint_rows(h, F, b.idx, b.w, b.x, b.z, zv, g, v, b.nreal, cap, dA_out, dx_out));
   return finish(h);
+}
+
+tucker_status tucker_ridge_tables(tucker_handle* h, int N, const int64_t* I, const int* R,
+                                  tucker_dtype dtype, const void* const* A, double lambda,
+                                  double* const* usq_out, double* c_out, int* K_out_host,
+                                  double* d_eff_out_host) {
+  if (!h) return TUCKER_EINVAL;
+  if (!A || !usq_out || !c_out) return fail(h, TUCKER_EINVAL, "null factors or outputs");
+  if (!(lambda >= 0.0)) return fail(h, TUCKER_EINVAL, "lambda must be >= 0");
+  FactorSet F;
+  TK_TRY(make_factors(h, N, I, R, dtype, A, &F));
+  for (int n = 0; n < N; ++n)
+    if (!usq_out[n]) return fail(h, TUCKER_EINVAL, "usq_out[%d] is NULL", n);
+  Arena sz(nullptr);
+  double* deff = sz.get<double>(1);
+  char* scratch = sz.get<char>(ridge_tables_scratch(F));
+  TK_TRY(ws_reserve(h, sz.off));
+  Arena ar(h->ws);
+  deff = ar.get<double>(1);
+  scratch = ar.get<char>(ridge_tables_scratch(F));
+  TK_TRY(ridge_tables(h, F, lambda, scratch, usq_out, c_out, deff, nullptr, nullptr));
+  if (K_out_host) ridge_components(F, K_out_host);
+  if (d_eff_out_host) {
+    TK_CUDA(h, cudaMemcpyAsync(d_eff_out_host, deff, sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+    return device_status(h);
+  }
+  return finish(h);
+}
+
+tucker_status tucker_sample_rows_ridge(tucker_handle* h, int N, const int64_t* I, const int* K,
+                                       const double* const* usq, const double* c, int64_t m,
+                                       uint64_t seed, uint32_t sweep, tucker_samples* out) {
+  if (!h) return TUCKER_EINVAL;
+  if (!usq || !c || !out || !out->keys || !out->counts || !out->prob)
+    return fail(h, TUCKER_EINVAL, "null tables or output arrays");
+  if (m < 1 || m >= (int64_t(1) << 31)) return fail(h, TUCKER_EINVAL, "m out of range");
+  if (out->capacity < m) return fail(h, TUCKER_ECAPACITY, "capacity %lld < m %lld",
+                                     (long long)out->capacity, (long long)m);
+  FactorSet F;
+  TK_TRY(make_factors(h, N, I, K, TUCKER_F64, nullptr, &F));
+  for (int n = 0; n < N; ++n) {
+    if (!usq[n]) return fail(h, TUCKER_EINVAL, "usq[%d] is NULL", n);
+    if (K[n] > I[n]) return fail(h, TUCKER_EINVAL, "K_%d > I_%d", n, n);
+  }
+  Arena sz(nullptr);
+  auto carve = [&](Arena& ar, uint64_t** raw, int64_t** dT, char** ss, int** nu, char** rs) {
+    *raw = ar.get<uint64_t>(m);
+    *dT = ar.get<int64_t>(1);
+    *ss = ar.get<char>(sort_dedupe_scratch(m));
+    *nu = ar.get<int>(1);
+    *rs = ar.get<char>(ridge_sample_scratch(F, m));
+  };
+  uint64_t* raw;
+  int64_t* dT;
+  char *ss, *rs;
+  int* nu;
+  carve(sz, &raw, &dT, &ss, &nu, &rs);
+  TK_TRY(ws_reserve(h, sz.off));
+  Arena ar(h->ws);
+  carve(ar, &raw, &dT, &ss, &nu, &rs);
+  RidgeState st;
+  TK_TRY(ridge_draw(h, F, usq, c, m, seed, sweep, rs, raw, dT, &st));
+  TK_TRY(sort_dedupe(h, raw, m, bits_for(F.total), out->keys, out->counts, nu, ss,
+                     sort_dedupe_scratch(m)));
+  TK_TRY(ridge_prob(h, &st, out->keys, nu, m, out->prob));
+  int nuh = 0;
+  TK_CUDA(h, cudaMemcpyAsync(&nuh, nu, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  TK_TRY(device_status(h));
+  out->n_unique = nuh;
+  out->n_draws = m;
+  return TUCKER_OK;
 }
 
 }  // extern "C"

@@ -311,6 +311,33 @@ struct RowSet {                       // the deduplicated sample as device array
 
 RowSet make_rowset(const FactorSet& F, uint32_t* const* idx, const double* w, const int* n_rows);
 
+// The lambda-ridge sampler's tables and outputs (ridge.cu).
+struct RidgeSampArgs {
+  int N;
+  int64_t I[TUCKER_MAX_ORDER];
+  int K[TUCKER_MAX_ORDER];
+  int dK;
+  const double* usq[TUCKER_MAX_ORDER];     // K_n x I_n
+  const double* c;                         // dK
+  uint64_t* ccdf;                          // dK: component CDF
+  uint64_t* colcdf[TUCKER_MAX_ORDER];      // K_n x I_n: column CDFs
+  double* rc;                              // dK: q^c_t / Q^c
+  double* rrow[TUCKER_MAX_ORDER];          // I_n x K_n: q^(n,t)_i / Q^(n,t), row-major over i
+  uint64_t seed, sweep;
+  int64_t m;
+  uint64_t* keys_out;                      // m
+  int64_t* T_out;                          // nullable: receives T = m
+  const uint64_t* keys_u;                  // n_unique sorted keys
+  const int* n_unique;
+  double* prob;                            // n_unique
+  int* status;
+};
+
+struct RidgeState {
+  RidgeSampArgs a;
+};
+
+
 // leverage.cu
 tucker_status launch_leverage(tucker_handle* h, const FactorSet& F, double* const* lev,
                               uint64_t* const* cdf, int* d_rank, double* const* evecs,

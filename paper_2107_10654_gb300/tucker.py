@@ -22,7 +22,7 @@ __all__ = ["TuckerError", "Handle", "Samples", "CooTensor", "tucker_leverage_sco
            "tucker_sample_rows_noalloc", "tucker_sketched_gram", "tucker_set_solver"]
 
 PREC = {"fp64": L.PREC_FP64, "fp32": L.PREC_FP32, "tf32": L.PREC_TF32, "bf16": L.PREC_BF16}
-REG = {"exact": L.REG_EXACT, "augmented": L.REG_AUGMENTED}
+REG = {"exact": L.REG_EXACT, "augmented": L.REG_AUGMENTED, "ridge": L.REG_RIDGE}
 SOLVER = {"fp64": L.SOLVER_FP64_CHOLESKY, "mixed": L.SOLVER_MIXED, "kpcg": L.SOLVER_KRON_PCG}
 
 
@@ -278,6 +278,45 @@ def tucker_core_solve_adjoint(h: Handle, X, A: Sequence[torch.Tensor], lam: floa
         REG[reg], PREC[prec], C.byref(samples._c()), int(solve_id), g.data_ptr(), gbar.data_ptr(),
         L.ptr_array([t.data_ptr() for t in dA]), dx.data_ptr()))
     return dA, dx
+
+
+def tucker_ridge_tables(h: Handle, A: Sequence[torch.Tensor], lam: float):
+    """Tables of the lambda-ridge leverage distribution of K (Lemma 4.1):
+    (usq list of K_n x I_n FP64, c FP64 [prod K_n], K list, d_eff)."""
+    lib = L.load()
+    N = len(A)
+    I = (C.c_int64 * L.MAX_ORDER)(*[a.shape[0] for a in A])
+    K = [min(a.shape[0], a.shape[1]) for a in A]
+    dev = A[0].device
+    usq = [torch.empty((k, a.shape[0]), dtype=torch.float64, device=dev) for k, a in zip(K, A)]
+    dK = 1
+    for k in K:
+        dK *= k
+    c = torch.empty(dK, dtype=torch.float64, device=dev)
+    Kout = (C.c_int * L.MAX_ORDER)()
+    deff = C.c_double()
+    _check(h.h, lib.tucker_ridge_tables(h.h, N, I, _ranks([a.shape[1] for a in A]), _dt(A[0]),
+                                        _factors(A), float(lam),
+                                        L.ptr_array([t.data_ptr() for t in usq]), c.data_ptr(),
+                                        Kout, C.byref(deff)))
+    return usq, c, [int(Kout[n]) for n in range(N)], float(deff.value)
+
+
+def tucker_sample_rows_ridge(h: Handle, dims: Sequence[int], K: Sequence[int],
+                             usq: Sequence[torch.Tensor], c: torch.Tensor, m: int, seed: int,
+                             sweep: int = 0, out: Optional[Samples] = None) -> Samples:
+    """m rows of K drawn from l^lam(K) / d_eff(K) given its tables, deduplicated."""
+    lib = L.load()
+    N = len(dims)
+    I = (C.c_int64 * L.MAX_ORDER)(*[int(v) for v in dims])
+    out = out if out is not None else Samples.empty(m, c.device)
+    cs = out._c()
+    _check(h.h, lib.tucker_sample_rows_ridge(h.h, N, I, _ranks(K),
+                                             L.ptr_array([t.data_ptr() for t in usq]),
+                                             c.data_ptr(), int(m), int(seed), int(sweep),
+                                             C.byref(cs)))
+    out.n_unique, out.n_draws = int(cs.n_unique), int(cs.n_draws)
+    return out
 
 
 def tucker_sample_rows_noalloc(dims: Sequence[int], ranks: Sequence[int],

@@ -201,3 +201,29 @@ def test_ridge_sketched_core_loss_ratio():
     ratios = [CU.ridge_loss_dense(X, F, RK.sketched_core_ridge(X, F, lam, 800, s)["g"], lam) / opt
               for s in range(10)]
     assert 1.0 <= min(ratios) and float(np.median(ratios)) < 1 + 5 * 8 / 800
+
+
+def test_ridge_sample_count_alg1_with_exact_ridge_scores():
+    # Alg. 1 line 3 with beta' from Eq. beta_prime for the exact ridge scores of K
+    # (beta = 1, ||l-hat||_1 = d_eff, d'_eff = d_eff): d_eff from the explicit K
+    F = _factors(35, SHAPES[0])
+    K = CU.kron_matrix(F)
+    d = K.shape[1]
+    prev = None
+    for lam in (1e-2, 1.0, 10.0, 100.0):
+        de = LV.effective_dimension(K, lam)                       # explicit, Eq. d_eff_def
+        mlt = min(1.0, d - de)
+        bp = d / (de + d * mlt)                                    # both terms of Eq. beta_prime
+        s = RK.ridge_sample_count(F, lam, 0.1, 0.1)
+        assert s == S.paper_sample_count(d, 0.1, 0.1, bp)
+        assert 0.5 <= bp <= 1.0
+        # once d - d_eff >= 1, beta' = d / (d_eff + d) grows as d_eff shrinks: fewer rows
+        # (below that, min{1, d - d_eff} itself shrinks and beta' tends to 1 as d_eff -> d)
+        if d - de >= 1.0:
+            if prev is not None:
+                assert s <= prev
+            prev = s
+    # lam -> 0 with full-rank factors: d_eff -> d, beta' -> 1, half the classical count
+    s0 = RK.ridge_sample_count(F, 1e-12, 0.1, 0.1)
+    assert s0 == S.paper_sample_count(d, 0.1, 0.1, 1.0)
+    assert 2 * s0 in (S.paper_sample_count(d, 0.1, 0.1, 0.5), S.paper_sample_count(d, 0.1, 0.1, 0.5) + 1)
