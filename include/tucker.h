@@ -315,8 +315,12 @@ tucker_status tucker_core_update_exact(tucker_handle* h, const tucker_tensor* X,
  * update (sketched when `sketched`, else exact).  Dense X only.
  *   A_inout[N]      device factors (dtype of X), updated in place
  *   core_inout      device FP64 [d], updated in place
- *   loss_out_host   nullable: L = ||X - X-hat||^2 + lambda(||G||^2 + sum ||A^(n)||^2) (Sec. 2)
- *   rmse_out_host   nullable: sqrt(||X - X-hat||^2 / prod(I_n))
+ *   loss_out_host   nullable: L = ||X - X-hat||^2 + lambda(||G||^2 + sum ||A^(n)||^2) (Sec. 2),
+ *                   by the Gram identity ||X - X-hat||^2 = ||X||^2 - 2 g.K^T vec(X) +
+ *                   g.((x)_n A^(n)T A^(n)) g in FP64: K^T vec(X) from the last factor
+ *                   update's n-mode product chain, ||X||^2 in one pass (FP32 data:
+ *                   error-free squares and compensated FP32 sums, added in FP64)
+ *   rmse_out_host   nullable: sqrt(||X - X-hat||^2 / prod(I_n)), the same identity
  * Errors: EINVAL, ENOTSPD, ENOMEM, ECUDA. */
 tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const int* R,
                                void* const* A_inout, double* core_inout, double lambda,

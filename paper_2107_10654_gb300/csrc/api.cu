@@ -83,6 +83,11 @@ tucker_status residual_sq(tucker_handle* h, const FactorSet& F, const tucker_ten
                           int npartial, double* out);
 tucker_status sumsq(tucker_handle* h, const void* v, int is64, int64_t n, double* partial,
                     int npartial, double* out);
+tucker_status tensor_sumsq(tucker_handle* h, const void* X, int is64, int64_t n, double* partial,
+                           int npartial, double* out);
+tucker_status kt_x_from_last(tucker_handle* h, const FactorSet& F, const double* B, double* y);
+tucker_status kron_quad(tucker_handle* h, const FactorSet& F, double* const* gram, const double* g,
+                        const double* y, double* out);
 tucker_status factor_solve(tucker_handle* h, const FactorSet& F, int n, double* const* gram,
                            const double* core, const double* B, double lambda, void* A_out);
 tucker_status launch_adjoint_rows(tucker_handle* h, const FactorSet& F, uint32_t* const* idx,
@@ -680,6 +685,7 @@ tucker_status tucker_create(tucker_handle** out, void* cuda_stream) {
   }
   h->num_sms = prop.multiProcessorCount;
   if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->keep, kAuxDoubles * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&h->h_status, sizeof(int)) != cudaSuccess ||
       cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -705,6 +711,7 @@ tucker_status tucker_destroy(tucker_handle* h) {
   if (h->hash.slot_key) cudaFree(h->hash.slot_key);
   if (h->chol.L) cudaFree(h->chol.L);
   if (h->d_status) cudaFree(h->d_status);
+  if (h->keep) cudaFree(h->keep);
   if (h->h_status) cudaFreeHost(h->h_status);
   for (int i = 0; i < 16; ++i) cudaEventDestroy(h->ev[i]);
   if (h->aux) {
@@ -1257,7 +1264,7 @@ tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const i
     *b1 = ar.get<double>(inter);
     *B = ar.get<double>(inter);
     *part = ar.get<double>(np);
-    *res = ar.get<double>(2 + N);
+    *res = ar.get<double>(3 + N);
   };
   double *lev[TUCKER_MAX_ORDER], *gram[TUCKER_MAX_ORDER];
   uint64_t* cdf[TUCKER_MAX_ORDER];
@@ -1272,6 +1279,13 @@ tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const i
     TK_TRY(launch_leverage(h, F, lev, cdf, rk, nullptr, nullptr, gram));
     TK_TRY(ttm_chain_except(h, F, X->dense, n, b0, b1, B));
     TK_TRY(factor_solve(h, F, n, gram, core_inout, B, lambda, A_inout[n]));
+  }
+  // the loss by the Gram identity needs y = K^T vec(X) for the new factors: the last
+  // product chain B = X x_{k<N} A^(k)T, times the new A^(N); and ||X||^2 (one pass)
+  const bool want_loss = loss_out_host || rmse_out_host;
+  if (want_loss) {
+    TK_TRY(kt_x_from_last(h, F, B, h->keep));
+    TK_TRY(tensor_sumsq(h, X->dense, F.is64, (int64_t)F.total, part, np, h->keep + F.d));
   }
   TK_TRY(device_status(h));
   tucker_status st;
@@ -1288,17 +1302,22 @@ tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const i
     TK_TRY(ws_reserve(h, sz2.off));
     Arena ar2(h->ws);
     carve(ar2, lev, cdf, gram, &rk, &b0, &b1, &B, &part, &res);
-    TK_TRY(residual_sq(h, F, X, core_inout, b0, b1, part, np, res));
-    TK_TRY(sumsq(h, core_inout, 1, F.d, part, np, res + 1));
+    // L = ||X||^2 - 2 g.y + g.(x_n A^(n)T A^(n)) g + lambda (||g||^2 + sum_n ||A^(n)||^2)
+    // (the objective of Sec. 2 expanded; FP64), with the Grams of the new factors
+    TK_TRY(launch_leverage(h, F, lev, cdf, rk, nullptr, nullptr, gram));
+    TK_TRY(kron_quad(h, F, gram, core_inout, h->keep, res));
     for (int n = 0; n < N; ++n)
-      TK_TRY(sumsq(h, A_inout[n], F.is64, F.I[n] * F.R[n], part, np, res + 2 + n));
-    double hv[2 + TUCKER_MAX_ORDER];
-    TK_CUDA(h, cudaMemcpyAsync(hv, res, (2 + N) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      TK_TRY(sumsq(h, A_inout[n], F.is64, F.I[n] * F.R[n], part, np, res + 3 + n));
+    double hv[3 + TUCKER_MAX_ORDER], xx = 0.0;
+    TK_CUDA(h, cudaMemcpyAsync(hv, res, (3 + N) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    TK_CUDA(h, cudaMemcpyAsync(&xx, h->keep + F.d, sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
     TK_TRY(device_status(h));
-    double reg_sum = hv[1];
-    for (int n = 0; n < N; ++n) reg_sum += hv[2 + n];
-    if (loss_out_host) *loss_out_host = hv[0] + lambda * reg_sum;
-    if (rmse_out_host) *rmse_out_host = sqrt(hv[0] / (double)F.total);
+    const double resid = xx - 2.0 * hv[1] + hv[0];
+    double reg_sum = hv[2];
+    for (int n = 0; n < N; ++n) reg_sum += hv[3 + n];
+    if (loss_out_host) *loss_out_host = resid + lambda * reg_sum;
+    if (rmse_out_host) *rmse_out_host = sqrt(fmax(resid, 0.0) / (double)F.total);
   }
   return TUCKER_OK;
 }

@@ -73,6 +73,7 @@ struct tucker_handle {
   size_t ws_cap = 0;
   int* d_status = nullptr;      // device status word
   int* h_status = nullptr;      // pinned host copy
+  double* keep = nullptr;       // kAuxDoubles of device scratch that outlives the workspace
   tk::HashTable hash;
   tk::CholCache chol;
   uint64_t next_solve_id = 1;
@@ -88,6 +89,8 @@ struct tucker_handle {
 };
 
 namespace tk {
+
+constexpr int kAuxDoubles = 8192 + 64;   // d <= 8192 plus a few scalars
 
 // Record a host-side error message on the handle and return the status.
 tucker_status fail(tucker_handle* h, tucker_status s, const char* fmt, ...);

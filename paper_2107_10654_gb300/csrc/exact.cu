@@ -39,12 +39,61 @@ __device__ __forceinline__ T transpose_reduce(T (&v)[RP], int lane) {
   return x;
 }
 
+// Rows blocked per warp: RB rows are contracted at once so that every
+// 16-byte load of A^T from shared memory feeds RB rows (the shared-memory
+// traffic per byte of X falls by RB) and RB independent row loads are in
+// flight per lane.  Row r's accumulators see the same operations in the same
+// order as a warp working on that row alone.
+template <int RP> struct RowBlock { static constexpr int RB = RP <= 8 ? 4 : RP <= 16 ? 2 : 1; };
+
+// acc[r][j] = lane's partial of sum_i rows[r][i] At[j][i], r < nr.
+template <class T, int RP, int RB>
+__device__ __forceinline__ void rows_contract(const T* const* rows, int nr, int I, const T* At,
+                                              bool vec, int lane, T (&acc)[RB][RP]) {
+  constexpr int VEC = 16 / sizeof(T);
+#pragma unroll
+  for (int r = 0; r < RB; ++r)
+#pragma unroll
+    for (int j = 0; j < RP; ++j) acc[r][j] = T(0);
+  if (vec) {
+    for (int i0 = lane * VEC; i0 < I; i0 += 32 * VEC) {
+      T xv[RB][VEC];
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        if (r < nr) *reinterpret_cast<uint4*>(xv[r]) = __ldg(reinterpret_cast<const uint4*>(rows[r] + i0));
+#pragma unroll
+      for (int j = 0; j < RP; ++j) {
+        T av[VEC];
+        *reinterpret_cast<uint4*>(av) = *reinterpret_cast<const uint4*>(At + j * I + i0);
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) acc[r][j] = fma(xv[r][q], av[q], acc[r][j]);
+      }
+    }
+  } else {
+    for (int i = lane; i < I; i += 32) {
+      T x[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) x[r] = r < nr ? rows[r][i] : T(0);
+#pragma unroll
+      for (int j = 0; j < RP; ++j) {
+        const T a = At[j * I + i];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) acc[r][j] = fma(x[r], a, acc[r][j]);
+      }
+    }
+  }
+}
+
 // out[p][r] = sum_i X[p][i] A[i][r]   (X: P x I row-major; out FP64 P x R)
-// One warp per row; A^T in shared memory ([r][i], conflict-free); 16-byte
-// loads of X when the row length allows; R <= RP accumulators per lane.
+// One warp per RB consecutive rows; A^T in shared memory ([r][i],
+// conflict-free); 16-byte loads of X when the row length allows; R <= RP
+// accumulators per row and lane.
 template <class T, int RP>
 __global__ void __launch_bounds__(256) k_ttm_last(const T* X, int64_t P, int I, const T* A, int R,
                                                   double* out) {
+  constexpr int RB = RowBlock<RP>::RB;
   extern __shared__ unsigned char smraw[];
   T* At = reinterpret_cast<T*>(smraw);               // RP x I (zero rows beyond R)
   for (int e = threadIdx.x; e < RP * I; e += blockDim.x) {
@@ -57,48 +106,37 @@ __global__ void __launch_bounds__(256) k_ttm_last(const T* X, int64_t P, int I, 
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const bool vec = (I % VEC) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
-  for (int64_t p = warp; p < P; p += nwarps) {
-    const T* row = X + p * I;
-    T acc[RP];
+  for (int64_t p0 = warp * RB; p0 < P; p0 += nwarps * RB) {
+    const int nr = (int)(P - p0 < RB ? P - p0 : RB);
+    const T* rows[RB];
 #pragma unroll
-    for (int j = 0; j < RP; ++j) acc[j] = T(0);
-    if (vec) {
-      for (int i0 = lane * VEC; i0 < I; i0 += 32 * VEC) {
-        T xv[VEC];
-        *reinterpret_cast<uint4*>(xv) = __ldg(reinterpret_cast<const uint4*>(row + i0));
-#pragma unroll
-        for (int j = 0; j < RP; ++j) {
-          T av[VEC];
-          *reinterpret_cast<uint4*>(av) = *reinterpret_cast<const uint4*>(At + j * I + i0);
-#pragma unroll
-          for (int q = 0; q < VEC; ++q) acc[j] = fma(xv[q], av[q], acc[j]);
-        }
-      }
-    } else {
-      for (int i = lane; i < I; i += 32) {
-        const T x = row[i];
-#pragma unroll
-        for (int j = 0; j < RP; ++j) acc[j] = fma(x, At[j * I + i], acc[j]);
-      }
-    }
-    const T tot = transpose_reduce<T, RP>(acc, lane);
+    for (int r = 0; r < RB; ++r) rows[r] = X + (p0 + (r < nr ? r : 0)) * I;
+    T acc[RB][RP];
+    rows_contract<T, RP, RB>(rows, nr, I, At, vec, lane, acc);
     constexpr int G = 32 / RP;
-    if ((lane % G) == 0) {
-      const int r = lane / G;
-      if (r < R) out[p * R + r] = (double)tot;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      if (r >= nr) break;
+      const T tot = transpose_reduce<T, RP>(acc[r], lane);
+      if ((lane % G) == 0) {
+        const int c = lane / G;
+        if (c < R) out[(p0 + r) * R + c] = (double)tot;
+      }
     }
   }
 }
 
 // Fused contraction of the last two modes of one slab per CTA:
 //   out[p][a][b] = sum_{i,j} X[p][i][j] A1[i][a] A2[j][b]
-// (A1 = A^(N-1), I1 x R1; A2 = A^(N), I2 x R2).  Each warp reduces rows j of
-// the slab against A2 (as in k_ttm_last), then adds A1[i][a] * t[b] into
-// per-warp FP64 accumulators; warps are combined in a fixed order.
+// (A1 = A^(N-1), I1 x R1; A2 = A^(N), I2 x R2).  Warp w reduces rows
+// i = w, w + 8, ... of the slab against A2, RB rows at a time (rows_contract),
+// then adds A1[i][a] * t[b] into per-warp accumulators in increasing i; warps
+// are combined in a fixed order.
 template <class T, int RP>
 __global__ void __launch_bounds__(256) k_ttm_last2(const T* X, int64_t pre, int I1, int I2,
                                                    const T* A1, int R1, const T* A2, int R2,
                                                    double* out) {
+  constexpr int RB = RowBlock<RP>::RB;
   extern __shared__ unsigned char smraw[];
   T* At = reinterpret_cast<T*>(smraw);                         // RP x I2
   T* A1s = reinterpret_cast<T*>(smraw + (((size_t)RP * I2 * sizeof(T) + 15) & ~size_t(15)));
@@ -120,80 +158,29 @@ __global__ void __launch_bounds__(256) k_ttm_last2(const T* X, int64_t pre, int 
 #pragma unroll
     for (int q = 0; q < 8; ++q) y[q] = T(0);
     const T* slab = X + p * (int64_t)I1 * I2;
-    // rows of up to 4 x 16 bytes per lane: the next row of this warp is loaded
-    // while the current one is contracted (two rows in flight per warp)
-    const int nc = vec && I2 % (32 * VEC) == 0 ? I2 / (32 * VEC) : 0;
-    if (nc >= 1 && nc <= 4) {
-      uint4 xa[4], xb[4];
-      auto load = [&](uint4* buf, int ri) {
-        const T* row = slab + (int64_t)ri * I2;
+    for (int i = w; i < I1; i += 8 * RB) {
+      int nr = 0;
+      const T* rows[RB];
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (c < nc) buf[c] = __ldg(reinterpret_cast<const uint4*>(row + (c * 32 + lane) * VEC));
-      };
-      if (w < I1) load(xa, w);
-      for (int i = w; i < I1; i += 8) {
-        if (i + 8 < I1) load(xb, i + 8);
-        T acc[RP];
+      for (int r = 0; r < RB; ++r) {
+        const int ir = i + 8 * r;
+        rows[r] = slab + (int64_t)(ir < I1 ? ir : i) * I2;
+        nr += ir < I1;
+      }
+      T acc[RB][RP];
+      rows_contract<T, RP, RB>(rows, nr, I2, At, vec, lane, acc);
 #pragma unroll
-        for (int j = 0; j < RP; ++j) acc[j] = T(0);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          if (c >= nc) break;
-          T xv[VEC];
-          *reinterpret_cast<uint4*>(xv) = xa[c];
-          const int j0 = (c * 32 + lane) * VEC;
-#pragma unroll
-          for (int j = 0; j < RP; ++j) {
-            T av[VEC];
-            *reinterpret_cast<uint4*>(av) = *reinterpret_cast<const uint4*>(At + j * I2 + j0);
-#pragma unroll
-            for (int q = 0; q < VEC; ++q) acc[j] = fma(xv[q], av[q], acc[j]);
-          }
-        }
-        const T t = transpose_reduce<T, RP>(acc, lane);
+      for (int r = 0; r < RB; ++r) {
+        if (r >= nr) break;
+        const int ir = i + 8 * r;
+        const T t = transpose_reduce<T, RP>(acc[r], lane);     // t[b] at lane b*G
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int e = lane + 32 * q;
           const int b = e % R2;
           const T tb = __shfl_sync(0xffffffffu, t, (b % RP) * G);
-          if (e < RR) y[q] = fma(A1s[i * R1 + e / R2], tb, y[q]);
+          if (e < RR) y[q] = fma(A1s[ir * R1 + e / R2], tb, y[q]);
         }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) xa[c] = xb[c];
-      }
-    } else
-    for (int i = w; i < I1; i += 8) {
-      const T* row = slab + (int64_t)i * I2;
-      T acc[RP];
-#pragma unroll
-      for (int j = 0; j < RP; ++j) acc[j] = T(0);
-      if (vec) {
-        for (int j0 = lane * VEC; j0 < I2; j0 += 32 * VEC) {
-          T xv[VEC];
-          *reinterpret_cast<uint4*>(xv) = __ldg(reinterpret_cast<const uint4*>(row + j0));
-#pragma unroll
-          for (int j = 0; j < RP; ++j) {
-            T av[VEC];
-            *reinterpret_cast<uint4*>(av) = *reinterpret_cast<const uint4*>(At + j * I2 + j0);
-#pragma unroll
-            for (int q = 0; q < VEC; ++q) acc[j] = fma(xv[q], av[q], acc[j]);
-          }
-        }
-      } else {
-        for (int j0 = lane; j0 < I2; j0 += 32) {
-          const T x = row[j0];
-#pragma unroll
-          for (int j = 0; j < RP; ++j) acc[j] = fma(x, At[j * I2 + j0], acc[j]);
-        }
-      }
-      const T t = transpose_reduce<T, RP>(acc, lane);         // t[b] at lane b*G
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int e = lane + 32 * q;
-        const int b = e % R2;
-        const T tb = __shfl_sync(0xffffffffu, t, (b % RP) * G);
-        if (e < RR) y[q] = fma(A1s[i * R1 + e / R2], tb, y[q]);
       }
     }
 #pragma unroll
@@ -426,6 +413,129 @@ __global__ void k_sumsq(const void* v, int is64, int64_t n, double* partial) {
   }
 }
 
+// ||X||^2 of a dense tensor for the Gram-identity loss.  FP32 data: every
+// square is split without error, x^2 = p + e with p = fl(x x) and e = fma(x,
+// x, -p), and each thread sums its p in FP32 with Neumaier's compensation
+// (e and the compensation in a second FP32 sum); the per-thread pairs are
+// added in FP64.  The loss L = ||X||^2 - 2 g.y + g.Hg cancels most of ||X||^2
+// (by about 5e-6 relative on the 512^3 workload), so ||X||^2 must be accurate
+// well below the FP32 rounding of a single sum.  FP64 data: FP64 products.
+__global__ void __launch_bounds__(256) k_tensor_sumsq(const void* X, int is64, int vec,
+                                                      int64_t n, double* partial) {
+  __shared__ double red[8];
+  double acc;
+  if (is64) {
+    const double* x = static_cast<const double*>(X);
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+      s = fma(x[i], x[i], s);
+    acc = s;
+  } else {
+    const float* x = static_cast<const float*>(X);
+    float s = 0.f, c = 0.f;
+    auto add = [&](float v) {
+      const float p = v * v;
+      const float e = fmaf(v, v, -p);
+      const float t = s + p;
+      c += (fabsf(s) >= fabsf(p)) ? ((s - t) + p) : ((p - t) + s);
+      c += e;
+      s = t;
+    };
+    const int64_t n4 = vec ? n >> 2 : 0;                // 16-byte loads when X is aligned
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const float4 v = __ldg(x4 + i);
+      add(v.x); add(v.y); add(v.z); add(v.w);
+    }
+    for (int64_t i = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+      add(x[i]);
+    acc = (double)s + (double)c;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// y = K^T vec(X) from the last factor update's product chain B = (X x_{k<N}
+// A^(k)T) laid out (pre, I_N) with pre = prod_{k<N} R_k: y[p R_N + r] =
+// sum_i A^(N)[i][r] B[p][i] (one warp per entry, FP64).
+__global__ void k_kt_x_from_last(const double* B, int64_t pre, int64_t IN, const void* A,
+                                 int is64, int RN, double* y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (e >= pre * RN) return;
+  const int64_t p = e / RN;
+  const int r = (int)(e - p * RN);
+  double acc = 0.0;
+  for (int64_t i = lane; i < IN; i += 32) acc = fma(B[p * IN + i], load_as_double(A, i * RN + r, is64), acc);
+  acc = warp_sum(acc);
+  if (lane == 0) y[e] = acc;
+}
+
+// out = g.(x_n G_n) g (one CTA; the Kronecker product applied mode by mode in
+// shared memory), and out[1] = g.y, out[2] = g.g: the terms of the loss
+// L = ||X||^2 - 2 g.y + g.Hg + lambda (||g||^2 + sum ||A^(n)||^2).
+struct KronQuadArgs {
+  int N, d;
+  int R[TUCKER_MAX_ORDER];
+  const double* gram[TUCKER_MAX_ORDER];
+  const double* g;
+  const double* y;
+  double* out;
+};
+
+__global__ void __launch_bounds__(1024) k_kron_quad(KronQuadArgs a) {
+  extern __shared__ double kq[];
+  double* z0 = kq;
+  double* z1 = kq + a.d;
+  __shared__ double red[3][32];
+  for (int t = threadIdx.x; t < a.d; t += blockDim.x) z0[t] = a.g[t];
+  __syncthreads();
+  int pre = 1;
+  for (int k = 0; k < a.N; ++k) {
+    const int Rk = a.R[k];
+    const int post = a.d / (pre * Rk);
+    for (int t = threadIdx.x; t < a.d; t += blockDim.x) {
+      const int q = t % post, r = (t / post) % Rk, pp = t / (post * Rk);
+      double acc = 0.0;
+      for (int j = 0; j < Rk; ++j) acc = fma(a.gram[k][r * Rk + j], z0[(pp * Rk + j) * post + q], acc);
+      z1[t] = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < a.d; t += blockDim.x) z0[t] = z1[t];
+    __syncthreads();
+    pre *= Rk;
+  }
+  double q = 0.0, gy = 0.0, gg = 0.0;
+  for (int t = threadIdx.x; t < a.d; t += blockDim.x) {
+    const double gt = a.g[t];
+    q = fma(gt, z0[t], q);
+    gy = fma(gt, a.y[t], gy);
+    gg = fma(gt, gt, gg);
+  }
+  q = warp_sum(q);
+  gy = warp_sum(gy);
+  gg = warp_sum(gg);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { red[0][w] = q; red[1][w] = gy; red[2][w] = gg; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { s0 += red[0][k]; s1 += red[1][k]; s2 += red[2][k]; }
+    a.out[0] = s0;
+    a.out[1] = s1;
+    a.out[2] = s2;
+  }
+}
+
 // ------------------------------------------------------------------- host side
 
 static int grid_for(tucker_handle* h, int64_t work, int per = 256) {
@@ -449,7 +559,7 @@ static tucker_status ttm_last_t(tucker_handle* h, const T* X, int64_t P, int I, 
   int per_sm = 0;
   TK_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
   int64_t grid = (int64_t)h->num_sms * (per_sm > 0 ? per_sm : 1);
-  const int64_t need = (P + 7) / 8;
+  const int64_t need = (P + 31) / 32;                 // 8 warps x 4 rows per CTA
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   TK_COUNT(h);
@@ -682,6 +792,47 @@ tucker_status sumsq(tucker_handle* h, const void* v, int is64, int64_t n, double
   TK_LAUNCH(h);
   TK_COUNT(h);
   k_sum_partials<<<1, 1024, 0, h->stream>>>(partial, npartial, out);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+tucker_status tensor_sumsq(tucker_handle* h, const void* X, int is64, int64_t n, double* partial,
+                           int npartial, double* out) {
+  TK_COUNT(h);
+  const int vec = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  k_tensor_sumsq<<<npartial, 256, 0, h->stream>>>(X, is64, vec, n, partial);
+  TK_LAUNCH(h);
+  TK_COUNT(h);
+  k_sum_partials<<<1, 1024, 0, h->stream>>>(partial, npartial, out);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+tucker_status kt_x_from_last(tucker_handle* h, const FactorSet& F, const double* B, double* y) {
+  const int N = F.N, RN = F.R[N - 1];
+  const int64_t pre = F.d / RN, IN = F.I[N - 1];
+  const int64_t warps = pre * RN;
+  TK_COUNT(h);
+  k_kt_x_from_last<<<ceil_div(warps * 32, 256), 256, 0, h->stream>>>(B, pre, IN, F.A[N - 1],
+                                                                     F.is64, RN, y);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+tucker_status kron_quad(tucker_handle* h, const FactorSet& F, double* const* gram, const double* g,
+                        const double* y, double* out) {
+  KronQuadArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = F.N;
+  a.d = F.d;
+  for (int n = 0; n < F.N; ++n) { a.R[n] = F.R[n]; a.gram[n] = gram[n]; }
+  a.g = g;
+  a.y = y;
+  a.out = out;
+  const size_t smem = 2 * (size_t)F.d * sizeof(double);
+  TK_CUDA(h, cudaFuncSetAttribute(k_kron_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TK_COUNT(h);
+  k_kron_quad<<<1, 1024, smem, h->stream>>>(a);
   TK_LAUNCH(h);
   return TUCKER_OK;
 }
