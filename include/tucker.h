@@ -319,7 +319,11 @@ tucker_status tucker_core_update_exact(tucker_handle* h, const tucker_tensor* X,
  *                   by the Gram identity ||X - X-hat||^2 = ||X||^2 - 2 g.K^T vec(X) +
  *                   g.((x)_n A^(n)T A^(n)) g in FP64: K^T vec(X) from the last factor
  *                   update's n-mode product chain, ||X||^2 in one pass (FP32 data:
- *                   error-free squares and compensated FP32 sums, added in FP64)
+ *                   error-free squares and compensated FP32 sums, added in FP64).
+ *                   The identity cancels ||X||^2 down to the residual: its relative
+ *                   accuracy is about 1e-13 times ||X||^2 / ||X - X-hat||^2 (2e-8 for
+ *                   a 512^3 tensor with 5e-6 of its energy in the residual);
+ *                   tucker_ridge_loss sums the residual entry by entry instead
  *   rmse_out_host   nullable: sqrt(||X - X-hat||^2 / prod(I_n)), the same identity
  * Errors: EINVAL, ENOTSPD, ENOMEM, ECUDA. */
 tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const int* R,

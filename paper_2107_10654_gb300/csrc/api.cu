@@ -83,13 +83,16 @@ tucker_status residual_sq(tucker_handle* h, const FactorSet& F, const tucker_ten
                           int npartial, double* out);
 tucker_status sumsq(tucker_handle* h, const void* v, int is64, int64_t n, double* partial,
                     int npartial, double* out);
+tucker_status launch_factor_grams(tucker_handle* h, const FactorSet& F, int* d_rank,
+                                  double* const* gram);
 tucker_status tensor_sumsq(tucker_handle* h, const void* X, int is64, int64_t n, double* partial,
                            int npartial, double* out);
 tucker_status kt_x_from_last(tucker_handle* h, const FactorSet& F, const double* B, double* y);
 tucker_status kron_quad(tucker_handle* h, const FactorSet& F, double* const* gram, const double* g,
                         const double* y, double* out);
 tucker_status factor_solve(tucker_handle* h, const FactorSet& F, int n, double* const* gram,
-                           const double* core, const double* B, double lambda, void* A_out);
+                           const double* core, const double* B, double lambda, void* A_out,
+                           double* Lscratch);
 tucker_status launch_adjoint_rows(tucker_handle* h, const FactorSet& F, uint32_t* const* idx,
                                   const double* w, const double* x, const double* zg,
                                   const double* zv, const double* g, const double* v,
@@ -1252,8 +1255,10 @@ tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const i
     if (e > inter) inter = e;
   }
   const int np = h->num_sms * 8;
+  double* Ls = nullptr;                           // the R_n x R_n factor of a factor update
   auto carve = [&](Arena& ar, double** lev, uint64_t** cdf, double** gram, int** rk, double** b0,
                    double** b1, double** B, double** part, double** res) {
+    Ls = ar.get<double>(TUCKER_MAX_RANK * TUCKER_MAX_RANK);
     for (int n = 0; n < N; ++n) {
       lev[n] = ar.get<double>(F.I[n]);
       cdf[n] = ar.get<uint64_t>(F.I[n]);
@@ -1276,9 +1281,9 @@ tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const i
   Arena ar(h->ws);
   carve(ar, lev, cdf, gram, &rk, &b0, &b1, &B, &part, &res);
   for (int n = 0; n < N; ++n) {
-    TK_TRY(launch_leverage(h, F, lev, cdf, rk, nullptr, nullptr, gram));
+    TK_TRY(launch_factor_grams(h, F, rk, gram));
     TK_TRY(ttm_chain_except(h, F, X->dense, n, b0, b1, B));
-    TK_TRY(factor_solve(h, F, n, gram, core_inout, B, lambda, A_inout[n]));
+    TK_TRY(factor_solve(h, F, n, gram, core_inout, B, lambda, A_inout[n], Ls));
   }
   // the loss by the Gram identity needs y = K^T vec(X) for the new factors: the last
   // product chain B = X x_{k<N} A^(k)T, times the new A^(N); and ||X||^2 (one pass)
@@ -1304,7 +1309,7 @@ tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const i
     carve(ar2, lev, cdf, gram, &rk, &b0, &b1, &B, &part, &res);
     // L = ||X||^2 - 2 g.y + g.(x_n A^(n)T A^(n)) g + lambda (||g||^2 + sum_n ||A^(n)||^2)
     // (the objective of Sec. 2 expanded; FP64), with the Grams of the new factors
-    TK_TRY(launch_leverage(h, F, lev, cdf, rk, nullptr, nullptr, gram));
+    TK_TRY(launch_factor_grams(h, F, rk, gram));
     TK_TRY(kron_quad(h, F, gram, core_inout, h->keep, res));
     for (int n = 0; n < N; ++n)
       TK_TRY(sumsq(h, A_inout[n], F.is64, F.I[n] * F.R[n], part, np, res + 3 + n));

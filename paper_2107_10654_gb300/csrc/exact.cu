@@ -8,6 +8,8 @@
 // The first product streams X once (HBM-bound: one warp per row of the last
 // mode, lanes over the row, R_N accumulators, A^(N) in shared memory); the
 // rest act on tensors with at most prod(I)/I_N * R_N entries.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tk {
@@ -126,16 +128,18 @@ __global__ void __launch_bounds__(256) k_ttm_last(const T* X, int64_t P, int I, 
   }
 }
 
-// Fused contraction of the last two modes of one slab per CTA:
-//   out[p][a][b] = sum_{i,j} X[p][i][j] A1[i][a] A2[j][b]
-// (A1 = A^(N-1), I1 x R1; A2 = A^(N), I2 x R2).  Warp w reduces rows
-// i = w, w + 8, ... of the slab against A2, RB rows at a time (rows_contract),
-// then adds A1[i][a] * t[b] into per-warp accumulators in increasing i; warps
-// are combined in a fixed order.
+// Fused contraction of the last two modes, one (slab, row chunk) per CTA
+// iteration: part[p][c][a][b] = sum_{i in chunk c, j} X[p][i][j] A1[i][a] A2[j][b]
+// (A1 = A^(N-1), I1 x R1; A2 = A^(N), I2 x R2; the I1 rows of a slab cut into
+// nchunk chunks, so that pre * nchunk work items spread evenly over the
+// resident CTAs).  Warp w reduces rows i = i0 + w, i0 + w + 8, ... of the chunk
+// against A2, RB rows at a time (rows_contract), then adds A1[i][a] * t[b]
+// into per-warp accumulators in increasing i; warps are combined in a fixed
+// order; k_sum_chunks adds the chunks in order.
 template <class T, int RP>
 __global__ void __launch_bounds__(256) k_ttm_last2(const T* X, int64_t pre, int I1, int I2,
                                                    const T* A1, int R1, const T* A2, int R2,
-                                                   double* out) {
+                                                   int nchunk, double* out) {
   constexpr int RB = RowBlock<RP>::RB;
   extern __shared__ unsigned char smraw[];
   T* At = reinterpret_cast<T*>(smraw);                         // RP x I2
@@ -152,20 +156,32 @@ __global__ void __launch_bounds__(256) k_ttm_last2(const T* X, int64_t pre, int 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int RR = R1 * R2;
   const bool vec = (I2 % VEC) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  // output e = lane + 32 q of this lane is (a, b) = (e / R2, e % R2): fixed for the kernel
+  int ea[8], esrc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = lane + 32 * q;
+    ea[q] = e < RR ? e / R2 : -1;
+    esrc[q] = ((e % R2) % RP) * G;                    // lane holding t[b] after the reduction
+  }
   __syncthreads();
-  for (int64_t p = blockIdx.x; p < pre; p += gridDim.x) {
+  const int crows = (I1 + nchunk - 1) / nchunk;
+  for (int64_t item = blockIdx.x; item < pre * nchunk; item += gridDim.x) {
+    const int64_t p = item / nchunk;
+    const int c = (int)(item - p * nchunk);
+    const int iend = min(I1, (c + 1) * crows);
     T y[8];                                                    // outputs lane, lane+32, ...
 #pragma unroll
     for (int q = 0; q < 8; ++q) y[q] = T(0);
     const T* slab = X + p * (int64_t)I1 * I2;
-    for (int i = w; i < I1; i += 8 * RB) {
+    for (int i = c * crows + w; i < iend; i += 8 * RB) {
       int nr = 0;
       const T* rows[RB];
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
         const int ir = i + 8 * r;
-        rows[r] = slab + (int64_t)(ir < I1 ? ir : i) * I2;
-        nr += ir < I1;
+        rows[r] = slab + (int64_t)(ir < iend ? ir : i) * I2;
+        nr += ir < iend;
       }
       T acc[RB][RP];
       rows_contract<T, RP, RB>(rows, nr, I2, At, vec, lane, acc);
@@ -176,10 +192,9 @@ __global__ void __launch_bounds__(256) k_ttm_last2(const T* X, int64_t pre, int 
         const T t = transpose_reduce<T, RP>(acc[r], lane);     // t[b] at lane b*G
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const int e = lane + 32 * q;
-          const int b = e % R2;
-          const T tb = __shfl_sync(0xffffffffu, t, (b % RP) * G);
-          if (e < RR) y[q] = fma(A1s[ir * R1 + e / R2], tb, y[q]);
+          if (32 * q >= RR) break;                          // warp-uniform
+          const T tb = __shfl_sync(0xffffffffu, t, esrc[q]);
+          if (ea[q] >= 0) y[q] = fma(A1s[ir * R1 + ea[q]], tb, y[q]);
         }
       }
     }
@@ -192,13 +207,29 @@ __global__ void __launch_bounds__(256) k_ttm_last2(const T* X, int64_t pre, int 
     for (int e = threadIdx.x; e < RR; e += blockDim.x) {
       double v = 0.0;
       for (int ww = 0; ww < 8; ++ww) v += Yw[ww * RR + e];
-      out[p * RR + e] = v;
+      out[item * RR + e] = v;
     }
     __syncthreads();
   }
 }
 
+// out[p][e] = sum_c part[p][c][e] in increasing c.
+__global__ void k_sum_chunks(const double* part, int64_t pre, int nchunk, int RR, double* out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < pre * RR;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = t / RR;
+    const int e = (int)(t - p * RR);
+    double v = 0.0;
+    for (int c = 0; c < nchunk; ++c) v += part[(p * nchunk + c) * RR + e];
+    out[t] = v;
+  }
+}
+
 // out[p][r][q] = sum_i X[p][i][q] A[i][r]   (big X, middle mode; coalesced over q)
+// out[p][r][q] = sum_i X[p][i][q] A[i][r]   (big X, middle mode; coalesced over q)
+// A thread owns QB consecutive columns q (16-byte loads of X when post and the
+// base allow) and RC outputs r at a time; eight rows i are loaded before
+// their multiply-adds, which run in increasing i.
 template <class T, int RC>
 __global__ void __launch_bounds__(256) k_ttm_mid(const T* X, int64_t pre, int I, int64_t post,
                                                  const T* A, int R, double* out) {
@@ -206,23 +237,55 @@ __global__ void __launch_bounds__(256) k_ttm_mid(const T* X, int64_t pre, int I,
   T* As = reinterpret_cast<T*>(smraw);
   for (int e = threadIdx.x; e < I * R; e += blockDim.x) As[e] = A[e];
   __syncthreads();
-  const int64_t total = pre * post;
+  constexpr int QB = 16 / sizeof(T);
+  const bool vec = post % QB == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  const int qb = vec ? QB : 1;
+  const int64_t pq = post / qb;                           // column groups per slab
+  const int64_t total = pre * pq;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = t / post, q = t % post;
+    const int64_t p = t / pq, q0 = (t - p * pq) * qb;
+    const T* xp = X + p * I * post + q0;
     for (int r0 = 0; r0 < R; r0 += RC) {
-      T acc[RC];
+      T acc[RC][QB];
 #pragma unroll
-      for (int j = 0; j < RC; ++j) acc[j] = T(0);
-      for (int i = 0; i < I; ++i) {
-        const T x = X[(p * I + i) * post + q];
+      for (int j = 0; j < RC; ++j)
 #pragma unroll
-        for (int j = 0; j < RC; ++j)
-          if (r0 + j < R) acc[j] = fma(x, As[i * R + r0 + j], acc[j]);
+        for (int c = 0; c < QB; ++c) acc[j][c] = T(0);
+      for (int i0 = 0; i0 < I; i0 += 8) {
+        T xs[8][QB];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (vec) {
+            if (i0 + u < I)
+              *reinterpret_cast<uint4*>(xs[u]) =
+                  __ldg(reinterpret_cast<const uint4*>(xp + (int64_t)(i0 + u) * post));
+            else
+#pragma unroll
+              for (int c = 0; c < QB; ++c) xs[u][c] = T(0);
+          } else {
+            xs[u][0] = i0 + u < I ? __ldg(xp + (int64_t)(i0 + u) * post) : T(0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (i0 + u >= I) break;
+#pragma unroll
+          for (int j = 0; j < RC; ++j) {
+            if (r0 + j >= R) break;
+            const T a = As[(i0 + u) * R + r0 + j];
+#pragma unroll
+            for (int c = 0; c < QB; ++c)
+              if (c < qb) acc[j][c] = fma(xs[u][c], a, acc[j][c]);
+          }
+        }
       }
 #pragma unroll
       for (int j = 0; j < RC; ++j)
-        if (r0 + j < R) out[(p * R + r0 + j) * post + q] = (double)acc[j];
+        if (r0 + j < R)
+#pragma unroll
+          for (int c = 0; c < QB; ++c)
+            if (c < qb) out[(p * R + r0 + j) * post + q0 + c] = (double)acc[j][c];
     }
   }
 }
@@ -269,6 +332,38 @@ __global__ void k_ttm_small_warp(const double* in, int64_t pre, int64_t post, co
     }
     acc = warp_sum(acc);
     if (lane == 0) out[t] = acc;
+  }
+}
+
+// Contract mode with a short trailing extent (post divides 32, R <= 16): one
+// warp per leading index p, lane = (k phase, q) with q = lane % post, all R
+// outputs of the lane's q in registers; in[p][k][q] is read once, coalesced,
+// and the k phases are added by a fixed butterfly over the phase bits.
+template <int RM>
+__global__ void k_ttm_small_rows(const double* in, int64_t pre, int64_t post, const void* A,
+                                 int is64, int I, int R, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int q = lane % (int)post, kph = lane / (int)post, nph = 32 / (int)post;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = warp; p < pre; p += nwarps) {
+    double acc[RM];
+#pragma unroll
+    for (int r = 0; r < RM; ++r) acc[r] = 0.0;
+    const double* base = in + (p * I) * post + q;
+    for (int k = kph; k < I; k += nph) {
+      const double x = base[(int64_t)k * post];
+#pragma unroll
+      for (int r = 0; r < RM; ++r)
+        if (r < R) acc[r] = fma(x, load_as_double(A, (int64_t)k * R + r, is64), acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+      for (int o = (int)post; o < 32; o <<= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (kph == 0)
+#pragma unroll
+      for (int r = 0; r < RM; ++r)
+        if (r < R) out[(p * R + r) * post + q] = acc[r];
   }
 }
 
@@ -599,7 +694,14 @@ tucker_status ttm_small(tucker_handle* h, const double* in, int64_t pre, int64_t
   const int64_t total = pre * (contract ? R : I) * post;
   const int K = contract ? I : R;
   TK_COUNT(h);
-  if (K >= 64 && total < (int64_t)h->num_sms * 2048)
+  if (contract && K >= 64 && post <= 32 && 32 % post == 0 && R <= 16) {
+    const int64_t blocks = (pre * 32 + 255) / 256;
+    const int grid = (int)std::min<int64_t>(blocks, (int64_t)h->num_sms * 16);
+    if (R <= 8)
+      k_ttm_small_rows<8><<<grid, 256, 0, h->stream>>>(in, pre, post, A, is64, I, R, out);
+    else
+      k_ttm_small_rows<16><<<grid, 256, 0, h->stream>>>(in, pre, post, A, is64, I, R, out);
+  } else if (K >= 64 && total < (int64_t)h->num_sms * 2048)
     k_ttm_small_warp<<<grid_for(h, total * 32), 256, 0, h->stream>>>(in, pre, post, A, is64, I, R,
                                                                     contract, out);
   else
@@ -610,7 +712,8 @@ tucker_status ttm_small(tucker_handle* h, const double* in, int64_t pre, int64_t
 
 template <class T>
 static tucker_status ttm_last2_t(tucker_handle* h, const T* X, int64_t pre, int I1, int I2,
-                                 const T* A1, int R1, const T* A2, int R2, double* out) {
+                                 const T* A1, int R1, const T* A2, int R2, double* part,
+                                 double* out) {
   const int RP = R2 <= 4 ? 4 : R2 <= 8 ? 8 : R2 <= 16 ? 16 : 32;
   const size_t smem = (((size_t)RP * I2 * sizeof(T) + 15) & ~size_t(15)) +
                       (((size_t)I1 * R1 * sizeof(T) + 15) & ~size_t(15)) + (size_t)8 * R1 * R2 * 8;
@@ -620,10 +723,23 @@ static tucker_status ttm_last2_t(tucker_handle* h, const T* X, int64_t pre, int 
   int per_sm = 0;
   TK_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
   int64_t grid = (int64_t)h->num_sms * (per_sm > 0 ? per_sm : 1);
-  if (grid > pre) grid = pre;
+  // row chunks per slab: enough work items for about eight per CTA, each chunk
+  // at least 32 rows (four row groups of each of the eight warps)
+  int nchunk = 1;
+  while (nchunk < 16 && pre * nchunk < 8 * grid && I1 / (2 * nchunk) >= 32 &&
+         2 * nchunk * R1 <= I1)                         // partials fit in a prod(I)/I_N*R_N buffer
+    nchunk *= 2;
+  if (grid > pre * nchunk) grid = pre * nchunk;
+  const int RR = R1 * R2;
   TK_COUNT(h);
-  k<<<(int)grid, 256, smem, h->stream>>>(X, pre, I1, I2, A1, R1, A2, R2, out);
+  k<<<(int)grid, 256, smem, h->stream>>>(X, pre, I1, I2, A1, R1, A2, R2, nchunk,
+                                         nchunk > 1 ? part : out);
   TK_LAUNCH(h);
+  if (nchunk > 1) {
+    TK_COUNT(h);
+    k_sum_chunks<<<ceil_div(pre * RR, 256), 256, 0, h->stream>>>(part, pre, nchunk, RR, out);
+    TK_LAUNCH(h);
+  }
   return TUCKER_OK;
 }
 
@@ -648,12 +764,15 @@ tucker_status ttm_chain_all(tucker_handle* h, const FactorSet& F, const void* X,
     const int I1 = (int)F.I[N - 2], I2 = (int)F.I[N - 1];
     const int64_t pre = (int64_t)(F.total / (uint64_t)((int64_t)I1 * I2));
     double* cur = (N == 2) ? y : buf0;
+    // chunk partials in the other buffer (pre * 16 * R1 R2 doubles at most, within
+    // the prod(I) / I_N * R_N of a buffer because I_{N-1} >= 32 * chunks)
+    double* part = cur == buf0 ? buf1 : buf0;
     if (F.is64)
       TK_TRY(ttm_last2_t<double>(h, (const double*)X, pre, I1, I2, (const double*)F.A[N - 2],
-                                 F.R[N - 2], (const double*)F.A[N - 1], F.R[N - 1], cur));
+                                 F.R[N - 2], (const double*)F.A[N - 1], F.R[N - 1], part, cur));
     else
       TK_TRY(ttm_last2_t<float>(h, (const float*)X, pre, I1, I2, (const float*)F.A[N - 2],
-                                F.R[N - 2], (const float*)F.A[N - 1], F.R[N - 1], cur));
+                                F.R[N - 2], (const float*)F.A[N - 1], F.R[N - 1], part, cur));
     int64_t P = pre;
     int64_t post = (int64_t)F.R[N - 2] * F.R[N - 1];
     for (int n = N - 3; n >= 0; --n) {

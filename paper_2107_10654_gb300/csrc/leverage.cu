@@ -409,6 +409,60 @@ tucker_status launch_leverage(tucker_handle* h, const FactorSet& F, double* cons
   return launch_cdf_from_lev(h, F.N, F.I, lev, cdf);
 }
 
+// gram[n] = A^(n)T A^(n) (full, row-major) from the chunk partials, summed in
+// chunk order (the same order as the leverage kernels' Gram).
+__global__ void k_gram_sum(LevArgs a) {
+  const int n = blockIdx.x;
+  const int R = a.F.R[n];
+  const int npairs = R * (R + 1) / 2;
+  for (int pidx = threadIdx.x; pidx < npairs; pidx += blockDim.x) {
+    int r = 0, rem = pidx;
+    while (rem >= R - r) { rem -= R - r; ++r; }
+    const int c = r + rem;
+    double v = 0.0;
+    for (int ch = 0; ch < a.nchunk; ++ch) v += a.gpart[n][(size_t)ch * npairs + pidx];
+    a.gram[n][r * R + c] = v;
+    a.gram[n][c * R + r] = v;
+  }
+}
+
+// The factor Grams alone (the ALS factor updates and the loss need no scores):
+// two launches instead of the leverage pipeline's four.  d_rank: the scratch
+// the leverage launcher uses (leverage_aux_bytes).
+tucker_status launch_factor_grams(tucker_handle* h, const FactorSet& F, int* d_rank,
+                                  double* const* gram) {
+  LevArgs a;
+  memset(&a, 0, sizeof(a));
+  a.F = F;
+  int maxR = 0;
+  int64_t maxI = 1;
+  for (int n = 0; n < F.N; ++n) {
+    a.gram[n] = gram[n];
+    if (F.R[n] > maxR) maxR = F.R[n];
+    if (F.I[n] > maxI) maxI = F.I[n];
+  }
+  // the same carve as launch_leverage: W matrices, then the pointer table, then partials
+  double* Wbuf = reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(d_rank + 2 * TUCKER_MAX_ORDER + 64) & ~uintptr_t(255));
+  double** Wdev = reinterpret_cast<double**>(Wbuf + (size_t)TUCKER_MAX_ORDER * TUCKER_MAX_RANK * TUCKER_MAX_RANK);
+  double* gp = reinterpret_cast<double*>(Wdev + TUCKER_MAX_ORDER);
+  a.rows_per = gram_rows_per(maxI);
+  a.nchunk = (int)((maxI + a.rows_per - 1) / a.rows_per);
+  for (int n = 0; n < F.N; ++n) {
+    a.gpart[n] = gp;
+    gp += (size_t)a.nchunk * (F.R[n] * (F.R[n] + 1) / 2);
+  }
+  const size_t gsm = (size_t)(a.rows_per * maxR + 256) * sizeof(double);
+  TK_CUDA(h, cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)gsm));
+  TK_COUNT(h);
+  k_gram_partial<<<dim3(a.nchunk, F.N), 256, gsm, h->stream>>>(a);
+  TK_LAUNCH(h);
+  TK_COUNT(h);
+  k_gram_sum<<<F.N, 256, 0, h->stream>>>(a);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
 // Device bytes the leverage launcher needs behind its rank pointer.
 size_t leverage_aux_bytes(int64_t maxI) {
   const int rp = gram_rows_per(maxI);
