@@ -284,58 +284,230 @@ __global__ void k_tc_pack_grouped(PackArgs a, const int* seg_begin, const int* s
   }
 }
 
-// G_{(r1,j),(r1',j')} = sum_{i_1} a_{r1} a_{r1'} M_{i_1}[j][j'] for j <= j' of the
-// tiles of M (upper instances), r1 in this block's group of RB rows; written to
-// the four symmetric places (two when j = j').  FP32 sums over i_1 (the Gram's
-// operands are BF16/TF32), FP64 out.
-template <int R1, int RB>
-__global__ void __launch_bounds__(256) k_tc_reduce_grouped(const float* partial, int I1, int ntiles,
-                                                           int Tt, int dp, const void* A1, int is64,
-                                                           int d, double* G) {
-  extern __shared__ float a1s[];                   // A^(1) in FP32, staged once per CTA
-  int ti, tj;
-  tile_of(blockIdx.y, Tt, &ti, &tj);
-  const int rb0 = blockIdx.z * RB;
-  for (int e = threadIdx.x; e < I1 * R1; e += blockDim.x) a1s[e] = (float)load_as_double(A1, e, is64);
-  __syncthreads();
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = ti * TC_TILE + e / TC_TILE, jp = tj * TC_TILE + e % TC_TILE;
-  const bool act = e < TC_TILE * TC_TILE && j < dp && jp < dp && j <= jp;
-  if (!act) return;                                // no barrier below
-  float acc[RB][R1];
-#pragma unroll
-  for (int r = 0; r < RB; ++r)
-#pragma unroll
-    for (int q = 0; q < R1; ++q) acc[r][q] = 0.f;
-  const size_t stride = (size_t)ntiles * (TC_TILE * TC_TILE);
-  const float* src = partial + (size_t)blockIdx.y * (TC_TILE * TC_TILE) + e;
-  for (int i1 = 0; i1 < I1; ++i1) {
-    const float m = src[(size_t)i1 * stride];
-    const float* ai = a1s + i1 * R1;
-    // (a_r1 a_q) m: the same value for (r1, q) and (q, r1), so the entries that
-    // two threads both write get identical bits
-#pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      const float ar = ai[rb0 + r];
-#pragma unroll
-      for (int q = 0; q < R1; ++q) acc[r][q] = fmaf(ar * ai[q], m, acc[r][q]);
-    }
+// G_{(r1,j),(r1',j')} = sum_{i_1} a_{r1} a_{r1'} M_{i_1}[j][j'] on the tensor
+// cores: with p = (r1, r1') and n = (j, j'), G_pairs = P M, where
+// P[p][i_1] = a_{r1} a_{r1'} (R_1^2 x I_1) and M[i_1][n] are the FP32 partial
+// tiles (I_1 x (d/R_1)^2), a contraction over i_1.  Work unit: one 16 x 16
+// block (j, j') of M in the block-upper triangle (n = 16 jj + jj', the 256
+// columns of one MMA) and 128 pairs p (one TMEM accumulator; R_1 = 16 takes
+// two CTAs per block).  Per chunk of 32 values of i_1 the 256 threads stage,
+// K-major with the 128-byte swizzle, the block's M entries and the pairs' P
+// values, each split as x = hi + lo with hi = tf32(x) and lo = tf32(x - hi);
+// one thread issues Ph Mh + Ph Ml + Pl Mh (the dropped Pl Ml is 2^-22
+// relative).  P must not be rounded once: its error would repeat for every
+// sample of one i_1 instead of averaging out like the Gram's own rounding.
+// P is the same for (r1, r1') and (r1', r1).  Each entry of G is computed
+// once and stored with its mirror: (r1, j; r1', j') for j < j', and for j = j'
+// when r1 <= r1'.  The output goes through shared memory so that 16 lanes
+// store 16 consecutive doubles, both for the entry and for its mirror.
+constexpr int EX_THREADS = 256;
+constexpr int EX_KC = 32;                        // i_1 values per chunk (128 bytes of TF32)
+constexpr int EX_OP = TC_TILE * TC_ROWB;         // one 256-row operand: 32 KB
+constexpr int EX_STAGE = 3 * EX_OP;              // M hi, M lo, P hi and P lo (16 KB each)
+constexpr int EX_PS = 16 * 17 + 1;               // staged pair row: 16 rows of 17 floats, + 1
+
+struct ExpandArgs {
+  const float* partial;                          // [I1][ntiles][256][256]
+  int I1, ntiles, nb, dp, R1, d;                 // nb: 16-blocks per edge of M
+  const void* A1;
+  int is64;
+  double* G;
+  int* status;
+};
+
+__device__ __forceinline__ bool ex_wait(uint64_t* b, uint32_t parity, int* status) {
+  bool ok = false;
+  for (uint32_t i = 0; i < TC_WAIT_LIMIT && !ok; ++i) ok = mbar_try(b, parity);
+  if (!ok) set_status(status, DEV_INTERNAL);
+  return __syncthreads_and(ok) != 0;
+}
+
+__global__ void __launch_bounds__(EX_THREADS, 1) k_tcg_expand(ExpandArgs a) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  const uint32_t base_u = smem_u32(smraw);
+  unsigned char* sm = smraw + ((1024 - (base_u & 1023)) & 1023);
+  float* a1s = reinterpret_cast<float*>(sm + 2 * EX_STAGE);     // [2][EX_KC][R1]
+  __shared__ uint64_t bar_free[2], bar_done;
+  __shared__ uint32_t tmem_slot;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  int bj, bjp;
+  tile_of(blockIdx.x, a.nb, &bj, &bjp);                        // bj <= bjp
+  const int ti = bj >> 4, tj = bjp >> 4;                       // the partial tile of the block
+  const size_t tstride = (size_t)a.ntiles * (TC_TILE * TC_TILE);
+  const float* src = a.partial + (size_t)(tj * (tj + 1) / 2 + ti) * (TC_TILE * TC_TILE) +
+                     (size_t)((bj & 15) * 16) * TC_TILE + (bjp & 15) * 16;
+  const int R1 = a.R1, P2 = R1 * R1;
+  const int mb = blockIdx.y;                                   // pairs 128 mb .. 128 mb + 127
+  constexpr uint32_t ncols = 256u;
+  if (t == 0) {
+    mbar_init(&bar_free[0], 1);
+    mbar_init(&bar_free[1], 1);
+    mbar_init(&bar_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(&tmem_slot)), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  // staging map: rows n = 16 jj + 4 jq + k (k < 4), i_1 = 8 ig + i (i < 8) of the chunk
+  const int jq = t & 3, ig = (t >> 2) & 3, jj = t >> 4;
+  const float* srow = src + (size_t)jj * TC_TILE + 4 * jq;
+  const int nk = (a.I1 + EX_KC - 1) / EX_KC;
+  float4 cur[8], nxt[8];
+  float acur[2], anxt[2];
+  auto load_chunk = [&](int k, float4* v, float* av) {
 #pragma unroll
-  for (int r = 0; r < RB; ++r) {
-    const int r1 = rb0 + r;
+    for (int i = 0; i < 8; ++i) {
+      const int i1 = k * EX_KC + 8 * ig + i;
+      v[i] = i1 < a.I1 ? __ldg(reinterpret_cast<const float4*>(srow + (size_t)i1 * tstride))
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 #pragma unroll
-    for (int q = 0; q < R1; ++q) {
-      const double v = (double)acc[r][q];
-      const size_t A = (size_t)r1 * dp + j, B = (size_t)q * dp + jp;
-      G[A * d + B] = v;
-      G[B * d + A] = v;
-      if (j != jp) {
-        const size_t C = (size_t)r1 * dp + jp, D = (size_t)q * dp + j;
-        G[C * d + D] = v;
-        G[D * d + C] = v;
+    for (int q = 0; q < 2; ++q) {                              // A^(1) rows of the chunk
+      const int e = t + q * EX_THREADS, i1 = k * EX_KC + e / R1;
+      av[q] = e < EX_KC * R1 && i1 < a.I1
+                  ? (float)load_as_double(a.A1, (int64_t)i1 * R1 + e % R1, a.is64) : 0.f;
+    }
+  };
+  load_chunk(0, cur, acur);
+  bool ok = true;
+  for (int k = 0; k < nk && ok; ++k) {
+    const int s = k & 1;
+    unsigned char* hi = sm + (size_t)s * EX_STAGE;
+    unsigned char* lo = hi + EX_OP;
+    unsigned char* pp = lo + EX_OP;
+    float* as = a1s + s * EX_KC * R1;
+    if (k >= 2) ok = ex_wait(&bar_free[s], ((k - 2) >> 1) & 1, a.status);   // MMAs of chunk k - 2
+    if (!ok) break;
+    if (k + 1 < nk) load_chunk(k + 1, nxt, anxt);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (t + q * EX_THREADS < EX_KC * R1) as[t + q * EX_THREADS] = acur[q];
+    // M rows: 4 rows x 8 consecutive i_1 = two 16-byte chunks of each row, hi and lo
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int n = 16 * jj + 4 * jq + r;
+      const size_t rowoff = (size_t)(n >> 3) * 1024 + (n & 7) * TC_ROWB;
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        float v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 c = cur[4 * h2 + i];
+          v[i] = r == 0 ? c.x : r == 1 ? c.y : r == 2 ? c.z : c.w;
+        }
+        uint4 vh, vl;
+        vh.x = to_tf32(v[0]); vl.x = to_tf32(v[0] - __uint_as_float(vh.x));
+        vh.y = to_tf32(v[1]); vl.y = to_tf32(v[1] - __uint_as_float(vh.y));
+        vh.z = to_tf32(v[2]); vl.z = to_tf32(v[2] - __uint_as_float(vh.z));
+        vh.w = to_tf32(v[3]); vl.w = to_tf32(v[3] - __uint_as_float(vh.w));
+        const int chunk = (2 * ig + h2) ^ (n & 7);
+        *reinterpret_cast<uint4*>(hi + rowoff + (chunk << 4)) = vh;
+        *reinterpret_cast<uint4*>(lo + rowoff + (chunk << 4)) = vl;
       }
     }
+    __syncthreads();                                           // A^(1) rows of the chunk
+    // P rows: pair p = 128 mb + (t % 128) (zero past R1^2), 16-byte chunks 4 (t / 128) ..
+    {
+      const int pl = t & 127, p = mb * 128 + pl;
+      const size_t rowoff = (size_t)(pl >> 3) * 1024 + (pl & 7) * TC_ROWB;
+      const int r1 = p / R1, r2 = p - r1 * R1;
+#pragma unroll
+      for (int c = 4 * (t >> 7); c < 4 * (t >> 7) + 4; ++c) {
+        uint4 oh = make_uint4(0u, 0u, 0u, 0u), ol = oh;
+        if (p < P2) {
+          const float* a0 = as + (4 * c) * R1;
+          float v[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) v[i] = a0[i * R1 + r1] * a0[i * R1 + r2];
+          oh.x = to_tf32(v[0]); ol.x = to_tf32(v[0] - __uint_as_float(oh.x));
+          oh.y = to_tf32(v[1]); ol.y = to_tf32(v[1] - __uint_as_float(oh.y));
+          oh.z = to_tf32(v[2]); ol.z = to_tf32(v[2] - __uint_as_float(oh.z));
+          oh.w = to_tf32(v[3]); ol.w = to_tf32(v[3] - __uint_as_float(oh.w));
+        }
+        const size_t o = rowoff + ((c ^ (pl & 7)) << 4);
+        *reinterpret_cast<uint4*>(pp + o) = oh;
+        *reinterpret_cast<uint4*>(pp + TC_M * TC_ROWB + o) = ol;
+      }
+    }
+    fence_proxy_async();                                       // generic writes -> tensor core
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      const uint32_t id = idesc(2u);                           // TF32, M = 128, N = 256
+      const uint32_t bh = smem_u32(hi), bl = smem_u32(lo), ph = smem_u32(pp);
+      const uint32_t pl = ph + (uint32_t)(TC_M * TC_ROWB);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {                         // 8 values of i_1 per MMA
+        mma<TUCKER_PREC_TF32>(tmem, sw128_desc(ph + 32 * kk), sw128_desc(bh + 32 * kk), id,
+                              (k > 0 || kk > 0) ? 1u : 0u);
+        mma<TUCKER_PREC_TF32>(tmem, sw128_desc(ph + 32 * kk), sw128_desc(bl + 32 * kk), id, 1u);
+        mma<TUCKER_PREC_TF32>(tmem, sw128_desc(pl + 32 * kk), sw128_desc(bh + 32 * kk), id, 1u);
+      }
+      mma_commit(&bar_free[s]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) cur[i] = nxt[i];
+    acur[0] = anxt[0];
+    acur[1] = anxt[1];
+  }
+  if (t == 0) mma_commit(&bar_done);                           // tracks every MMA issued
+  const bool done = ex_wait(&bar_done, 0, a.status);
+  tc_fence_after();
+  // ---------------- epilogue through shared memory
+  float* S = reinterpret_cast<float*>(sm);                     // [128 pairs][EX_PS]
+  const bool diagb = bj == bjp;
+  if (done && ok) {
+    // TMEM -> S: warp w reads lanes 32 (w % 4).. and column half (w / 4) * 128..
+    const int quad = warp & 3, half = warp >> 2;
+    const int pl = quad * 32 + lane;
+#pragma unroll 1
+    for (int cb = 0; cb < 128; cb += 16) {
+      const int col = half * 128 + cb;                         // = 16 jj: one row of the block
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                   "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                     "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                     "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                   : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float* dst = S + (size_t)pl * EX_PS + (col >> 4) * 17;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) dst[i] = __uint_as_float(v[i]);
+    }
+    __syncthreads();
+    // S -> G: item (pair, row) with 16 lanes along the row; entry rows jj, mirror rows jj'
+    const int sub = lane >> 4, l16 = lane & 15;
+    for (int item = warp * 2 + sub; item < 128 * 16 * 2; item += (EX_THREADS / 32) * 2) {
+      const int pl2 = item >> 5, mode = (item >> 4) & 1, q = item & 15;
+      const int p = mb * 128 + pl2;
+      if (p >= P2) continue;
+      const int r1 = p / R1, r2 = p - r1 * R1;
+      // mode 0: jj = q, jj' = l16 (the entry); mode 1: jj' = q, jj = l16 (the mirror)
+      const int jjv = mode ? l16 : q, jjp = mode ? q : l16;
+      const int j = 16 * bj + jjv, jp = 16 * bjp + jjp;
+      if (j >= a.dp || jp >= a.dp) continue;
+      if (diagb && (jjv > jjp || (jjv == jjp && r1 > r2))) continue;
+      const double v = (double)S[(size_t)pl2 * EX_PS + jjv * 17 + jjp];
+      const size_t A = (size_t)r1 * a.dp + j, B = (size_t)r2 * a.dp + jp;
+      if (mode == 0) a.G[A * a.d + B] = v;
+      else a.G[B * a.d + A] = v;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+                 : "memory");
   }
 }
 
@@ -733,16 +905,29 @@ size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int sumR, int64_t ca
   return b;
 }
 
-template <int R1, int RB>
-static void launch_reduce_grouped(tucker_handle* h, const float* partial, int I1, int ntiles,
-                                  int Tt, int dp, const void* A1, int is64, int d, double* G) {
-  const size_t smem = (size_t)I1 * R1 * sizeof(float);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute((const void*)k_tc_reduce_grouped<R1, RB>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_tc_reduce_grouped<R1, RB><<<dim3(TC_TILE * TC_TILE / 256, ntiles, R1 / RB), 256,
-                                 (size_t)I1 * R1 * sizeof(float), h->stream>>>(
-      partial, I1, ntiles, Tt, dp, A1, is64, d, G);
+static size_t expand_smem_bytes() { return 2 * (size_t)EX_STAGE + 2 * EX_KC * 16 * 4 + 1024; }
+
+static tucker_status launch_expand(tucker_handle* h, const float* partial, int I1, int ntiles,
+                                   int dp, const void* A1, int is64, int R1, int d, double* G) {
+  ExpandArgs e;
+  e.partial = partial;
+  e.I1 = I1;
+  e.ntiles = ntiles;
+  e.nb = (dp + 15) / 16;
+  e.dp = dp;
+  e.R1 = R1;
+  e.d = d;
+  e.A1 = A1;
+  e.is64 = is64;
+  e.G = G;
+  e.status = h->d_status;
+  const size_t smem = expand_smem_bytes();
+  TK_CUDA(h, cudaFuncSetAttribute(k_tcg_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TK_COUNT(h);
+  k_tcg_expand<<<dim3(e.nb * (e.nb + 1) / 2, (R1 * R1 + TC_M - 1) / TC_M), EX_THREADS, smem,
+                 h->stream>>>(e);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
 }
 
 // The Gram grouped by the leading index (sorted sample, s.idx[0] non-decreasing).
@@ -828,16 +1013,7 @@ tucker_status launch_gram_tc_grouped(tucker_handle* h, const RowSet& s, int prec
   kern<<<(int)(ntiles * I1), TC_THREADS, smem, h->stream>>>(a);
   TK_LAUNCH(h);
   if (h->timing) cudaEventRecord(h->ev[11], h->stream);
-  TK_COUNT(h);
-  switch (R1) {
-    case 1: launch_reduce_grouped<1, 1>(h, partial, (int)I1, ntiles, Tt, dp, s.A[0], s.is64, s.d, G); break;
-    case 2: launch_reduce_grouped<2, 2>(h, partial, (int)I1, ntiles, Tt, dp, s.A[0], s.is64, s.d, G); break;
-    case 4: launch_reduce_grouped<4, 4>(h, partial, (int)I1, ntiles, Tt, dp, s.A[0], s.is64, s.d, G); break;
-    case 8: launch_reduce_grouped<8, 8>(h, partial, (int)I1, ntiles, Tt, dp, s.A[0], s.is64, s.d, G); break;
-    default: launch_reduce_grouped<16, 4>(h, partial, (int)I1, ntiles, Tt, dp, s.A[0], s.is64, s.d, G); break;
-  }
-  TK_LAUNCH(h);
-  return TUCKER_OK;
+  return launch_expand(h, partial, (int)I1, ntiles, dp, s.A[0], s.is64, R1, s.d, G);
 }
 
 tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_t cap, char* ws,

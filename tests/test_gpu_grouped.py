@@ -1,13 +1,16 @@
 """GPU parity of the tensor-core Gram grouped by the leading index (used when
 d / R_1 >= 128 and the order is >= 3): sampled entries of G within the
-operand-rounding bound, h, and the FP64 residual of the refined core, against
-the oracle (explicit sampled rows), for R_1 = 4, 8, 16 and orders 3 and 4."""
+operand-rounding bound (BF16 2^-7, TF32 2^-9: the expansion by a_r1 a_r1' on the
+tensor cores rounds that product to TF32 and keeps M exact as hi + lo), h, and
+the FP64 residual of the refined core, against the oracle (explicit sampled
+rows), for R_1 = 2, 4, 8, 16, orders 3 and 4, and d / R_1 not a multiple of 16
+or spanning two 256-wide tiles."""
 import numpy as np
 import pytest
 
 from oracle import leverage as LV, sampling as S, core_update as CU
 from tests.gpu_common import dev, host_keys, rel_err, handle  # noqa: F401
-from tests.test_gpu_fullsize import _check_gram_entries, _check_residual
+from tests.test_gpu_fullsize import _check_gram_entries, _check_residual, BF16_C, TF32_C
 from paper_2107_10654_gb300 import tucker as T
 
 pytestmark = pytest.mark.gpu
@@ -17,6 +20,9 @@ pytestmark = pytest.mark.gpu
     ((48, 40, 40), (4, 16, 16), "bf16"),          # d = 1024, d / R_1 = 256
     ((30, 24, 20, 22), (8, 8, 4, 4), "bf16"),     # order 4, d / R_1 = 128
     ((64, 36, 36), (16, 8, 16), "tf32"),          # R_1 = 16, d / R_1 = 128
+    ((40, 30, 25), (4, 12, 11), "tf32"),          # d / R_1 = 132: ragged 16-blocks
+    ((24, 40, 40), (2, 16, 17), "bf16"),          # d / R_1 = 272: two 256-wide tiles of M
+    ((70, 30, 30), (16, 16, 16), "tf32"),         # the 1024^3 ranks: R_1^2 = 256 pairs
 ])
 def test_grouped_gram_and_solve(handle, dims, ranks, prec):
     g = np.random.default_rng(21)
@@ -32,7 +38,8 @@ def test_grouped_gram_and_solve(handle, dims, ranks, prec):
     G, h = T.tucker_sketched_gram(handle, Xd, Fd, prec, smp)
     Gh = G.cpu().numpy()
     assert np.array_equal(Gh, Gh.T)
-    _check_gram_entries(F, dims, ku, w, Gh, n_pairs=160, seed=3)
+    _check_gram_entries(F, dims, ku, w, Gh, n_pairs=160, seed=3,
+                        c=BF16_C if prec == "bf16" else TF32_C)
     x = CU.gather_dense(X, ku, dims)
     hr = CU.sampled_rows_apply_t(F, S.decode_keys(ku, dims), w * x)
     assert rel_err(h.cpu().numpy(), hr) <= 1e-12
