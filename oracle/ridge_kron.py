@@ -17,7 +17,10 @@ Restated from the paper:
   * missing entries (Sec. 4.2, after Lemma 4.4): the ridge scores of A are a
     beta-overestimate for those of the observed rows with
     1/beta = 1 + 1/(1 - lambda_max(L_{S-bar,S-bar})), and the corollary to
-    Thm 4.3 bounds 1/(1 - lambda_max) by 1 + prod_n ||A^(n)||_2^2 / lam.
+    Thm 4.3 bounds 1/(1 - lambda_max) by 1 + prod_n ||A^(n)||_2^2 / lam;
+    lambda_max from the observed rows' Gram as a generalized eigenvalue, and
+    the sample count of the observed-entry sampler composed from beta and the
+    factor by which classical scores of K bound its ridge scores.
 
 The exact sampler is this library's design, not the paper's (the paper draws
 from the product of the classical factor scores): by Lemma 4.1,
@@ -168,6 +171,50 @@ def missing_ridge_beta_bound(factors: Sequence[np.ndarray], lam: float) -> float
     for A in factors:
         p *= float(np.linalg.norm(np.asarray(A, dtype=np.float64), 2)) ** 2
     return 1.0 / (2.0 + p / lam)
+
+
+def missing_ridge_beta_from_gram(factors: Sequence[np.ndarray], lam: float,
+                                 G_obs: np.ndarray) -> tuple[float, float]:
+    """(beta, lambda_max) of Sec. 4.2 from the Gram of the observed rows,
+    G_obs = K_S^T K_S.  The nonzero eigenvalues of
+    L_{S-bar,S-bar} = K_{S-bar} (K^T K + lam I)^-1 K_{S-bar}^T are those of the
+    pencil (K_{S-bar}^T K_{S-bar}, K^T K + lam I), and
+    K_{S-bar}^T K_{S-bar} = K^T K - G_obs, so lambda_max = 1 - nu_min with nu_min
+    the smallest eigenvalue of the pencil (G_obs + lam I, K^T K + lam I)."""
+    K = CU.kron_matrix(factors)
+    d = K.shape[1]
+    from scipy.linalg import eigh
+    nu = eigh(G_obs + lam * np.eye(d), K.T @ K + lam * np.eye(d), eigvals_only=True)
+    lmax = max(0.0, 1.0 - float(nu.min()))
+    return 1.0 / (1.0 + 1.0 / (1.0 - lmax)), lmax
+
+
+def classical_ridge_ratio_min(factors: Sequence[np.ndarray], lam: float) -> float:
+    """c_min = min_t c_t over the components with P_t > 0.  By Lemma 4.1 at lam
+    and at 0, l^lam_i(K) = sum_t c_t w_it and l_i(K) = sum_{t: P_t > 0} w_it with
+    the same w_it = prod_n (u^(n)_{i_n t_n})^2 >= 0, so every classical score of
+    K is at most l^lam_i(K) / c_min."""
+    c, _ = ridge_weights(factors, lam)
+    return float(c[c > 0].min())
+
+
+def missing_overestimate_beta(factors: Sequence[np.ndarray], lam: float,
+                              beta_miss: float) -> float:
+    """beta for the sampler of observed entries (classical product scores of K,
+    draws outside S rejected, so the distribution on S is l(K)_i / l(K)(S)) as
+    an overestimate of the ridge scores of K_S:
+    l_i / l(S) >= l^lam_i(K) / l(S) >= (l^lam(K)(S) / l(S)) beta_miss l^lam_i(K_S) / d_eff(K_S),
+    and l^lam(K)(S) / l(S) >= c_min, so beta = c_min beta_miss."""
+    return classical_ridge_ratio_min(factors, lam) * beta_miss
+
+
+def missing_sample_count(factors: Sequence[np.ndarray], lam: float, eps: float, delta: float,
+                         beta_miss: float) -> int:
+    """Alg. 1 line 3's s for the observed-entry sampler: beta' of Alg. 1 line 2
+    with d'_eff = 0 and beta = c_min beta_miss."""
+    d = int(np.prod([np.asarray(A).shape[1] for A in factors]))
+    beta = missing_overestimate_beta(factors, lam, beta_miss)
+    return S.paper_sample_count(d, eps, delta, alg1_beta_prime(beta, d, 0.0))
 
 
 def ridge_sample_count(factors: Sequence[np.ndarray], lam: float, eps: float,

@@ -227,3 +227,72 @@ def test_ridge_sample_count_alg1_with_exact_ridge_scores():
     s0 = RK.ridge_sample_count(F, 1e-12, 0.1, 0.1)
     assert s0 == S.paper_sample_count(d, 0.1, 0.1, 1.0)
     assert 2 * s0 in (S.paper_sample_count(d, 0.1, 0.1, 0.5), S.paper_sample_count(d, 0.1, 0.1, 0.5) + 1)
+
+
+@pytest.mark.parametrize("lam", [0.05, 2.0, 40.0])
+@pytest.mark.parametrize("dup", [None, (1, 0, 1)])
+def test_classical_scores_bound_ridge_scores_pointwise(lam, dup):
+    # c_min against an independent route: the nonzero eigenvalues mu of the explicit
+    # K^T K are the products P_t, so c_min = min mu / (mu + lam); every row of the
+    # explicit K then satisfies l^lam_i(K) >= c_min l_i(K), with equality on some row
+    # when one component carries it alone
+    F = _factors(41, SHAPES[0], dup)
+    K = CU.kron_matrix(F)
+    mu = np.linalg.eigvalsh(K.T @ K)
+    mu = mu[mu > 1e-9 * mu.max()]
+    cmin = RK.classical_ridge_ratio_min(F, lam)
+    assert abs(cmin - float((mu / (mu + lam)).min())) <= 1e-12
+    lr = LV.ridge_leverage_scores(K, lam)
+    lc = LV.ridge_leverage_scores(K, 0.0)
+    assert np.all(lr >= cmin * lc - 1e-13)
+    assert np.all(lr <= lc + 1e-13)
+
+
+@pytest.mark.parametrize("lam", [0.3, 3.0])
+@pytest.mark.parametrize("frac", [0.3, 0.7])
+def test_missing_overestimate_for_the_observed_entry_sampler(lam, frac):
+    # the distribution the observed-entry sampler draws from on S (classical scores of K,
+    # the rest rejected) is a (c_min beta_miss)-overestimate of the ridge scores of K_S,
+    # by brute force on the explicit K, with beta_miss exact and from the corollary
+    F = _factors(43, SHAPES[0])
+    dims = (4, 5, 3)
+    K = CU.kron_matrix(F)
+    g = np.random.default_rng(44)
+    obs = np.sort(g.choice(K.shape[0], int(frac * K.shape[0]), replace=False))
+    q = LV.ridge_leverage_scores(K, 0.0)[obs]
+    q = q / q.sum()
+    l_obs = LV.ridge_leverage_scores(K[obs], lam)
+    target = l_obs / l_obs.sum()
+    for bm in (RK.missing_ridge_beta(F, lam, obs, dims), RK.missing_ridge_beta_bound(F, lam)):
+        beta = RK.missing_overestimate_beta(F, lam, bm)
+        assert np.all(q >= beta * target - 1e-15)
+
+
+@pytest.mark.parametrize("lam", [0.1, 1.5])
+def test_missing_beta_from_the_observed_gram(lam):
+    # the pencil route equals the explicit L_{S-bar,S-bar} route; all rows observed
+    # gives lambda_max = 0 (beta = 1/2 by the formula); the bound is below it
+    F = _factors(45, SHAPES[1])
+    dims = (6, 2, 4)
+    K = CU.kron_matrix(F)
+    g = np.random.default_rng(46)
+    obs = np.sort(g.choice(K.shape[0], 30, replace=False))
+    b, lmax = RK.missing_ridge_beta_from_gram(F, lam, K[obs].T @ K[obs])
+    assert abs(b - RK.missing_ridge_beta(F, lam, obs, dims)) <= 1e-10
+    L = LV.cross_ridge_leverage_scores(K, lam)
+    miss = np.setdiff1d(np.arange(K.shape[0]), obs)
+    assert abs(lmax - np.linalg.eigvalsh(L[np.ix_(miss, miss)]).max()) <= 1e-10
+    assert RK.missing_ridge_beta_bound(F, lam) <= b + 1e-15
+    b_all, l_all = RK.missing_ridge_beta_from_gram(F, lam, K.T @ K)
+    assert l_all <= 1e-12 and abs(b_all - 0.5) <= 1e-12
+
+
+def test_missing_sample_count_reduces_to_the_classical_count():
+    # lam -> 0 with nothing missing (c_min -> 1, beta_miss = 1): beta' = 1/2, the count
+    # Alg. 1 line 3 gives for classical scores; a smaller beta_miss needs more rows
+    F = _factors(47, SHAPES[0])
+    d = 12
+    assert RK.missing_sample_count(F, 1e-14, 0.1, 0.1, 1.0) == S.paper_sample_count(d, 0.1, 0.1)
+    s1 = RK.missing_sample_count(F, 1.0, 0.1, 0.1, 0.4)
+    s2 = RK.missing_sample_count(F, 1.0, 0.1, 0.1, 0.1)
+    assert s2 > s1 > S.paper_sample_count(d, 0.1, 0.1)
