@@ -282,8 +282,10 @@ tucker_status tucker_sample_rows(tucker_handle* h, int N, const int64_t* I, cons
  *   R[N]            host ranks; d = prod(R_n) <= 8192
  *   A[N]            host array of device factor pointers
  *   lambda          >= 0 (> 0 required for TUCKER_REG_AUGMENTED)
- *   m               sample count; 0 = the paper's s of Alg. 1 line 3 with
- *                   beta' = 1/2 at (eps, delta)
+ *   m               sample count; 0 = the paper's s of Alg. 1 line 3 at
+ *                   (eps, delta): beta' = 1/2 for a dense X; for observed
+ *                   entries the beta' of tucker_missing_beta's bound mode (lambda
+ *                   > 0; EINVAL when that s is 2^31 or more)
  *   seed, sweep     Philox key (the sweep index keeps resumed runs identical)
  *   fixed           NULL, or a sample from tucker_sample_rows to reuse (frozen sketch)
  *   core_out        device FP64 [d]: vec(G) row-major
@@ -412,6 +414,62 @@ tucker_status tucker_ridge_tables(tucker_handle* h, int N, const int64_t* I, con
 tucker_status tucker_sample_rows_ridge(tucker_handle* h, int N, const int64_t* I, const int* K,
                                        const double* const* usq, const double* c, int64_t m,
                                        uint64_t seed, uint32_t sweep, tucker_samples* out);
+
+/* Overestimate factor of the observed-entry sampler (Sec. 4.2, missing data).
+ * With S the observed rows of K, S-bar the missing ones and
+ * L = K (K^T K + lambda I)^+ K^T the cross lambda-ridge scores of K, the ridge
+ * scores of K restricted to S are a beta_miss-overestimate of the ridge scores
+ * of K_S (Thm 4.3 with the lemma on sums of squared cross scores), where
+ *     1 / beta_miss = 1 + 1 / (1 - lambda_max(L_{S-bar,S-bar})).
+ * Modes:
+ *   TUCKER_BETA_BOUND  the corollary to Thm 4.3: lambda_max <= P / (P + lambda),
+ *                      P = prod_n ||A^(n)||_2^2 (the largest eigenvalue of each
+ *                      A^(n)T A^(n), FP64 Jacobi), so beta_miss >= 1 / (2 + P / lambda);
+ *   TUCKER_BETA_EXACT  lambda_max = 1 - nu_min, nu_min the smallest eigenvalue of
+ *                      the pencil (K_S^T K_S + lambda I, K^T K + lambda I).  The
+ *                      Gram of all observed rows is formed in `prec` (as the exact
+ *                      observed-entry update forms it) and whitened with the
+ *                      factor eigendecompositions, D^-1/2 Vk^T (G + lambda I) Vk D^-1/2
+ *                      (Vk = (x)_n V_n, D = (x)_n ev_n + lambda); nu_min is estimated
+ *                      by inverse iteration on an FP64 Cholesky factor (every
+ *                      estimate is at or above nu_min) and then certified from
+ *                      below: the first nu (1 - tau), tau = 1e-6, 1e-4, 1e-2, 0.1,
+ *                      0.5, for which the whitened matrix minus nu I has an FP64
+ *                      Cholesky factor.  lambda_max = 1 - that nu is an upper bound
+ *                      for the Gram as formed.  d <= 4096.  Overwrites the handle's
+ *                      cached factor (a later adjoint call factors again).
+ * A dense X has nothing missing: lambda_max = 0, beta_miss = 1.
+ * The observed-entry sampler draws from the classical scores of K and rejects
+ * unobserved rows; on S its distribution is a beta-overestimate of the ridge
+ * scores of K_S with beta = c_min beta_miss, where c_min = min_t c_t over the
+ * components with P_t > 0 (by Lemma 4.1 every classical score of K is at most
+ * l^lam_i(K) / c_min).  Alg. 1 line 2 with d'_eff = 0 gives
+ * beta' = min{beta, 1} / 2 and line 3 the count s.
+ *   X, R, A         as for tucker_core_update_sketched
+ *   lambda          > 0 (Thm 4.3)
+ *   prec            precision of the observed Gram (exact mode only)
+ *   eps, delta      in (0, 1): the accuracy and failure probability of s
+ *   out_host        filled on success
+ * Synchronises.  Errors: EINVAL, ERANK (a zero factor), ENOTSUP (exact mode
+ * with d > 4096), ENOTSPD (the whitened Gram has no Cholesky factor), ECUDA. */
+typedef enum { TUCKER_BETA_BOUND = 0, TUCKER_BETA_EXACT = 1 } tucker_beta_mode;
+
+typedef struct {
+  double lambda_max;    /* upper bound on lambda_max(L_{S-bar,S-bar}) */
+  double beta_miss;     /* 1 / (1 + 1 / (1 - lambda_max)); 1 for a dense X */
+  double c_min;         /* min_t c_t, c_t = P_t / (P_t + lambda) */
+  double beta;          /* c_min * beta_miss */
+  double beta_prime;    /* min{beta, 1} / 2 (Alg. 1 line 2, d'_eff = 0) */
+  double s;             /* Alg. 1 line 3 at (eps, delta): may exceed any sample count */
+  double nu_est;        /* exact mode: the last inverse-iteration estimate of nu_min */
+  int iters;            /* exact mode: inverse iterations */
+  int certify_tries;    /* exact mode: Cholesky factorisations of the certification */
+} tucker_missing_beta_info;
+
+tucker_status tucker_missing_beta(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                  const void* const* A, double lambda, tucker_beta_mode mode,
+                                  tucker_prec prec, double eps, double delta,
+                                  tucker_missing_beta_info* out_host);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free sampling.  The paper has no counterpart to this entry

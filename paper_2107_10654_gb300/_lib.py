@@ -42,6 +42,12 @@ class TuckerStats(C.Structure):
                 ("inner_iters", C.c_int64)]
 
 
+class TuckerMissingBetaInfo(C.Structure):
+    _fields_ = [("lambda_max", C.c_double), ("beta_miss", C.c_double), ("c_min", C.c_double),
+                ("beta", C.c_double), ("beta_prime", C.c_double), ("s", C.c_double),
+                ("nu_est", C.c_double), ("iters", C.c_int), ("certify_tries", C.c_int)]
+
+
 _P = C.c_void_p
 _PP = C.POINTER(C.c_void_p)
 _I64P = C.POINTER(C.c_int64)
@@ -79,6 +85,9 @@ SIGNATURES = {
                                       _IP, _DP]),
     "tucker_sample_rows_ridge": (C.c_int, [_P, C.c_int, _I64P, _IP, _PP, _P, C.c_int64, C.c_uint64,
                                            C.c_uint32, C.POINTER(TuckerSamples)]),
+    "tucker_missing_beta": (C.c_int, [_P, C.POINTER(TuckerTensor), _IP, _PP, C.c_double, C.c_int,
+                                      C.c_int, C.c_double, C.c_double,
+                                      C.POINTER(TuckerMissingBetaInfo)]),
     "tucker_sample_rows_noalloc": (C.c_int, [_P, C.c_int, _I64P, _IP, _PP, C.c_int64, C.c_uint64,
                                              C.c_uint32, C.c_int, C.POINTER(TuckerSamples),
                                              C.c_char_p, C.c_size_t]),

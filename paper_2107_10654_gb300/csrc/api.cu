@@ -10,11 +10,13 @@
 //     factor eigendecompositions, diagonal scaling; or the Gram of all
 //     observed rows for missing data
 //   ALS sweep (Alg. 2), ridge loss, adjoint of the frozen-sketch solve.
+#include <float.h>
 #include <math.h>
 #include <stdarg.h>
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -76,6 +78,10 @@ tucker_status ttm_chain_all(tucker_handle* h, const FactorSet& F, const void* X,
                             double* buf1, double* y);
 tucker_status ttm_chain_except(tucker_handle* h, const FactorSet& F, const void* X, int n,
                                double* buf0, double* buf1, double* out);
+tucker_status kron_whiten(tucker_handle* h, const FactorSet& F, double* const* V,
+                          double* const* ev, double lambda, const double* M, double* tmp,
+                          double* out);
+tucker_status vec_normalize(tucker_handle* h, const double* y, int d, double* x, double* norm_out);
 tucker_status kron_eig_core(tucker_handle* h, const FactorSet& F, double* const* V,
                             double* const* s, const double* y, double lambda, double* g);
 tucker_status residual_sq(tucker_handle* h, const FactorSet& F, const tucker_tensor* X,
@@ -933,7 +939,18 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
     if (m == 0) {
       if (!(eps > 0 && eps < 1 && delta > 0 && delta < 1))
         return fail(h, TUCKER_EINVAL, "eps, delta must be in (0,1) when m = 0");
-      m = paper_s(F.d, eps, delta);
+      if (X->dense) {
+        m = paper_s(F.d, eps, delta);
+      } else {
+        // observed entries: beta' from the Sec. 4.2 corollary bound and c_min
+        tucker_missing_beta_info bi;
+        TK_TRY(tucker_missing_beta(h, X, R, A, lambda, TUCKER_BETA_BOUND, prec, eps, delta, &bi));
+        if (!(bi.s < (double)(int64_t(1) << 31)))
+          return fail(h, TUCKER_EINVAL,
+                      "Alg. 1 line 3 with the missing-data bound gives s = %.3g rows (beta' = %.3g); "
+                      "pass m > 0, e.g. from tucker_missing_beta's exact mode", bi.s, bi.beta_prime);
+        m = (int64_t)bi.s;
+      }
     }
     if (m < 1 || m >= (int64_t(1) << 31)) return fail(h, TUCKER_EINVAL, "m out of range");
     cap = m;
@@ -1205,6 +1222,171 @@ tucker_status tucker_core_update_exact(tucker_handle* h, const tucker_tensor* X,
   TK_CUDA(h, cudaMemcpyAsync(core_out, b.g, sizeof(double) * F.d, cudaMemcpyDeviceToDevice,
                              h->stream));
   return finish(h);
+}
+
+// ------------------------------------------------ missing-data beta (Sec. 4.2)
+struct FactorEigs {
+  double* lev[TUCKER_MAX_ORDER];
+  uint64_t* cdf[TUCKER_MAX_ORDER];
+  double* V[TUCKER_MAX_ORDER];
+  double* ev[TUCKER_MAX_ORDER];
+  int* rk;
+};
+
+static void carve_eigs(Arena& ar, const FactorSet& F, FactorEigs* e) {
+  for (int n = 0; n < F.N; ++n) {
+    e->lev[n] = ar.get<double>(F.I[n]);
+    e->cdf[n] = ar.get<uint64_t>(F.I[n]);
+    e->V[n] = ar.get<double>(F.R[n] * F.R[n]);
+    e->ev[n] = ar.get<double>(F.R[n]);
+  }
+  e->rk = reinterpret_cast<int*>(ar.get<char>(leverage_aux_bytes(max_dim(F))));
+}
+
+// Alg. 1 line 3 as a real number (it may exceed any integer type).
+static double alg1_count(int d, double eps, double delta, double beta_prime) {
+  return ceil(4.0 * d / beta_prime * fmax(420.0 * log(4.0 * d / delta), 1.0 / (delta * eps)));
+}
+
+tucker_status tucker_missing_beta(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                  const void* const* A, double lambda, tucker_beta_mode mode,
+                                  tucker_prec prec, double eps, double delta,
+                                  tucker_missing_beta_info* out) {
+  if (!h) return TUCKER_EINVAL;
+  FactorSet F;
+  TK_TRY(check_tensor(h, X, R, A, &F));
+  if (!A || !out) return fail(h, TUCKER_EINVAL, "null factors or out");
+  if (!(lambda > 0.0)) return fail(h, TUCKER_EINVAL, "lambda must be > 0 (Thm 4.3)");
+  if (!(eps > 0 && eps < 1 && delta > 0 && delta < 1))
+    return fail(h, TUCKER_EINVAL, "eps, delta must be in (0,1)");
+  if (mode != TUCKER_BETA_BOUND && mode != TUCKER_BETA_EXACT) return fail(h, TUCKER_EINVAL, "mode");
+  if (prec < TUCKER_PREC_FP64 || prec > TUCKER_PREC_BF16) return fail(h, TUCKER_EINVAL, "prec");
+  const bool gram = mode == TUCKER_BETA_EXACT && !X->dense;
+  const int d = F.d;
+  if (gram && d > 4096) return fail(h, TUCKER_ENOTSUP, "exact missing-data beta needs d <= 4096");
+  if (gram && X->nnz >= (int64_t(1) << 31)) return fail(h, TUCKER_EINVAL, "nnz must be < 2^31");
+  memset(out, 0, sizeof(*out));
+  FactorEigs e;
+  SketchBufs b;
+  memset(&b, 0, sizeof(b));
+  double *T1 = nullptr, *C = nullptr, *vx = nullptr, *vy = nullptr, *nrm = nullptr, *dg = nullptr;
+  auto carve = [&](Arena& ar) {
+    carve_eigs(ar, F, &e);
+    if (!gram) return;
+    carve_sketch(ar, h, F, X->nnz, prec, 1, &b);
+    T1 = ar.get<double>((size_t)d * d);
+    C = ar.get<double>((size_t)d * d);
+    vx = ar.get<double>(d);
+    vy = ar.get<double>(d);
+    dg = ar.get<double>(d);
+    nrm = ar.get<double>(1);
+  };
+  Arena sz(nullptr);
+  carve(sz);
+  TK_TRY(ws_reserve(h, sz.off));
+  if (gram) TK_TRY(chol_reserve(h, d));
+  Arena ar(h->ws);
+  carve(ar);
+  // factor eigenpairs (FP64 Jacobi of A^(n)T A^(n)), eigenvalues to the host
+  TK_TRY(launch_leverage(h, F, e.lev, e.cdf, e.rk, e.V, e.ev, nullptr));
+  double evh[TUCKER_MAX_ORDER][TUCKER_MAX_RANK];
+  for (int n = 0; n < F.N; ++n)
+    TK_CUDA(h, cudaMemcpyAsync(evh[n], e.ev[n], sizeof(double) * F.R[n], cudaMemcpyDeviceToHost,
+                               h->stream));
+  TK_TRY(device_status(h));
+  // P_max = prod_n ||A^(n)||_2^2; c_min = P_min / (P_min + lambda) with P_min the
+  // product of the smallest eigenvalues above the pseudo-inverse cutoff
+  double pmax = 1.0, pmin = 1.0;
+  for (int n = 0; n < F.N; ++n) {
+    double top = 0.0;
+    for (int k = 0; k < F.R[n]; ++k) top = fmax(top, evh[n][k]);
+    const double cut = (double)std::max<int64_t>(F.I[n], F.R[n]) * DBL_EPSILON * top;
+    double lo = top;
+    for (int k = 0; k < F.R[n]; ++k)
+      if (evh[n][k] > cut) lo = fmin(lo, evh[n][k]);
+    pmax *= top;
+    pmin *= lo;
+  }
+  if (!(pmax > 0.0) || !(pmin > 0.0)) return fail(h, TUCKER_ERANK, "a factor matrix is zero");
+  out->c_min = pmin / (pmin + lambda);
+  double lmax = 0.0;
+  if (X->dense) {
+    lmax = 0.0;                                   // nothing missing: beta_miss = 1
+  } else if (mode == TUCKER_BETA_BOUND) {
+    lmax = pmax / (pmax + lambda);                // the corollary to Thm 4.3
+  } else {
+    // K_S^T K_S over all observed rows, whitened: C = D^-1/2 Vk^T (G + lambda I) Vk D^-1/2
+    h->chol.id = 0;                               // the cached factor is overwritten
+    h->chol.kron_ready = 0;
+    const int64_t nnz = X->nnz;
+    int nn = (int)nnz;
+    TK_CUDA(h, cudaMemcpyAsync(b.nreal, &nn, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    TK_TRY(launch_decode_rows(h, F, X->keys, nnz, b.idx, X->vals, b.x));
+    TK_CUDA(h, cudaStreamSynchronize(h->stream));
+    RowSet rs = make_rowset(F, b.idx, nullptr, b.nreal);
+    for (int64_t off = 0; off < nnz; off += int64_t(1) << 30)
+      TK_TRY(launch_regdiag(h, b.w + off, (int)std::min<int64_t>(nnz - off, int64_t(1) << 30), 1.0,
+                            nullptr));
+    rs.w = b.w;
+    double* G = h->chol.L;
+    TK_TRY(walk_segments(h, rs, F.I[0], b.walk));
+    TK_TRY(build_gram(h, F, rs, prec, nnz, b, G));
+    TK_TRY(kron_whiten(h, F, e.V, e.ev, lambda, G, T1, C));
+    // nu_min by inverse iteration: ||C^-1 x|| <= 1 / nu_min for unit x, so every
+    // estimate 1 / ||C^-1 x_k|| is at or above nu_min and they decrease towards it
+    TK_CUDA(h, cudaMemcpyAsync(G, C, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, h->stream));
+    TK_TRY(cholesky(h, G, d));
+    TK_TRY(device_status(h));
+    TK_TRY(chol_prepare(h, G, d, h->chol.LT, h->chol.Linv));
+    std::vector<double> x0(d);
+    for (int i = 0; i < d; ++i)                   // a fixed vector with no zero entry
+      x0[i] = 1.0 + (double)((uint32_t)(i + 1) * 2654435761u >> 22) / 1024.0;
+    TK_CUDA(h, cudaMemcpyAsync(vy, x0.data(), sizeof(double) * d, cudaMemcpyHostToDevice,
+                               h->stream));
+    TK_TRY(vec_normalize(h, vy, d, vx, nrm));
+    double nu = HUGE_VAL;
+    int it = 0;
+    while (it < 200) {
+      TK_TRY(chol_solve2(h, G, h->chol.LT, h->chol.Linv, d, vx, vy, h->chol.tmp));
+      TK_TRY(vec_normalize(h, vy, d, vx, nrm));
+      double nv = 0.0;
+      TK_CUDA(h, cudaMemcpyAsync(&nv, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      TK_TRY(device_status(h));
+      ++it;
+      if (!(nv > 0.0)) return fail(h, TUCKER_EINTERNAL, "inverse iteration lost its vector");
+      const double nn_ = 1.0 / nv;
+      const bool conv = fabs(nu - nn_) <= 1e-12 * nn_;
+      nu = nn_;
+      if (conv) break;
+    }
+    out->nu_est = nu;
+    out->iters = it;
+    // certify nu_lo <= nu_min: C - nu_lo I has an FP64 Cholesky factor
+    double nu_lo = 0.0;
+    const double taus[] = {1e-6, 1e-4, 1e-2, 1e-1, 0.5};
+    for (double tau : taus) {
+      const double lo = nu * (1.0 - tau);
+      TK_CUDA(h, cudaMemcpyAsync(G, C, sizeof(double) * d * d, cudaMemcpyDeviceToDevice,
+                                 h->stream));
+      TK_TRY(launch_regdiag(h, dg, d, -lo, nullptr));
+      TK_TRY(launch_add_diag(h, G, d, dg));
+      TK_TRY(cholesky(h, G, d));
+      ++out->certify_tries;
+      const tucker_status st = device_status(h);
+      if (st == TUCKER_OK) {
+        nu_lo = lo;
+        break;
+      }
+      if (st != TUCKER_ENOTSPD) return st;
+    }
+    lmax = fmax(0.0, 1.0 - nu_lo);
+  }
+  out->lambda_max = lmax;
+  out->beta_miss = X->dense ? 1.0 : (lmax < 1.0 ? 1.0 / (1.0 + 1.0 / (1.0 - lmax)) : 0.0);
+  out->beta = out->c_min * out->beta_miss;
+  out->beta_prime = fmin(out->beta, 1.0) / 2.0;
+  out->s = out->beta_prime > 0.0 ? alg1_count(d, eps, delta, out->beta_prime) : HUGE_VAL;
+  return TUCKER_OK;
 }
 
 tucker_status tucker_ridge_loss(tucker_handle* h, const tucker_tensor* X, const int* R,

@@ -956,4 +956,112 @@ tucker_status kron_quad(tucker_handle* h, const FactorSet& F, double* const* gra
   return TUCKER_OK;
 }
 
+// ------------------------------------------ whitening for the missing-data beta
+// Row r of a symmetric d x d matrix M: y = (V_1 (x) ... (x) V_N)^T M[r, :]^T,
+// stored as column r of `out` (so `out` = (M Vk)^T = Vk^T M).  Two passes give
+// Vk^T M Vk.  With `scale` the second pass also adds lambda on the diagonal and
+// divides by sqrt(D_c D_r), D = (x)_n ev_n + lambda: the matrix
+//     D^-1/2 Vk^T (M + lambda I) Vk D^-1/2,
+// whose eigenvalues are those of the pencil (M + lambda I, K^T K + lambda I)
+// when K^T K = Vk diag((x)_n ev_n) Vk^T (the factor eigendecompositions).
+struct RotArgs {
+  int N, d;
+  int R[TUCKER_MAX_ORDER];
+  const double* V[TUCKER_MAX_ORDER];   // R x R, V[a][k]
+  const double* ev[TUCKER_MAX_ORDER];  // R eigenvalues
+  const double* in;
+  double* out;
+  double lambda;
+  int scale;
+};
+
+__device__ __forceinline__ double kron_ev(const RotArgs& a, int t) {
+  double ev = 1.0;
+  for (int n = a.N - 1; n >= 0; --n) {
+    ev *= a.ev[n][t % a.R[n]];
+    t /= a.R[n];
+  }
+  return ev + a.lambda;
+}
+
+__global__ void __launch_bounds__(512) k_kron_rot_rows(RotArgs a) {
+  extern __shared__ double zb[];
+  double* z0 = zb;
+  double* z1 = zb + a.d;
+  const int r = blockIdx.x;
+  for (int i = threadIdx.x; i < a.d; i += blockDim.x) z0[i] = a.in[(size_t)r * a.d + i];
+  __syncthreads();
+  int pre = 1;
+  for (int n = 0; n < a.N; ++n) {               // z <- z x_n V_n^T
+    const int R = a.R[n];
+    const int post = a.d / (pre * R);
+    for (int t = threadIdx.x; t < a.d; t += blockDim.x) {
+      const int q = t % post, k = (t / post) % R, p = t / (post * R);
+      double acc = 0.0;
+      for (int j = 0; j < R; ++j) acc = fma(z0[(p * R + j) * post + q], a.V[n][j * R + k], acc);
+      z1[t] = acc;
+    }
+    __syncthreads();
+    double* tmp = z0; z0 = z1; z1 = tmp;
+    pre *= R;
+  }
+  const double dr = a.scale ? kron_ev(a, r) : 1.0;
+  for (int c = threadIdx.x; c < a.d; c += blockDim.x) {
+    double v = z0[c];
+    if (a.scale) v = (v + (c == r ? a.lambda : 0.0)) / sqrt(kron_ev(a, c) * dr);
+    a.out[(size_t)c * a.d + r] = v;
+  }
+}
+
+tucker_status kron_whiten(tucker_handle* h, const FactorSet& F, double* const* V,
+                          double* const* ev, double lambda, const double* M, double* tmp,
+                          double* out) {
+  if (F.d > 8192) return fail(h, TUCKER_ENOTSUP, "whitening of d = %d", F.d);
+  RotArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = F.N;
+  a.d = F.d;
+  for (int n = 0; n < F.N; ++n) { a.R[n] = F.R[n]; a.V[n] = V[n]; a.ev[n] = ev[n]; }
+  a.lambda = lambda;
+  const size_t smem = (size_t)2 * F.d * sizeof(double);
+  TK_CUDA(h, cudaFuncSetAttribute(k_kron_rot_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  a.in = M; a.out = tmp; a.scale = 0;
+  TK_COUNT(h);
+  k_kron_rot_rows<<<F.d, 512, smem, h->stream>>>(a);
+  TK_LAUNCH(h);
+  a.in = tmp; a.out = out; a.scale = 1;
+  TK_COUNT(h);
+  k_kron_rot_rows<<<F.d, 512, smem, h->stream>>>(a);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+// x = y / ||y||, norm_out = ||y|| (one CTA; FP64; fixed summation order).
+__global__ void __launch_bounds__(1024) k_vec_normalize(const double* y, int d, double* x,
+                                                        double* norm_out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) acc = fma(y[i], y[i], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const double nrm = sqrt(red[0]);
+  for (int i = threadIdx.x; i < d; i += blockDim.x) x[i] = nrm > 0.0 ? y[i] / nrm : 0.0;
+  if (threadIdx.x == 0) *norm_out = nrm;
+}
+
+tucker_status vec_normalize(tucker_handle* h, const double* y, int d, double* x, double* norm_out) {
+  TK_COUNT(h);
+  k_vec_normalize<<<1, 1024, 0, h->stream>>>(y, d, x, norm_out);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
 }  // namespace tk

@@ -19,7 +19,8 @@ from . import _lib as L
 __all__ = ["TuckerError", "Handle", "Samples", "CooTensor", "tucker_leverage_scores",
            "tucker_sample_rows", "tucker_core_update_sketched", "tucker_core_update_exact",
            "tucker_als_sweep", "tucker_ridge_loss", "tucker_core_solve_adjoint",
-           "tucker_sample_rows_noalloc", "tucker_sketched_gram", "tucker_set_solver"]
+           "tucker_sample_rows_noalloc", "tucker_sketched_gram", "tucker_set_solver",
+           "tucker_ridge_tables", "tucker_sample_rows_ridge", "tucker_missing_beta"]
 
 PREC = {"fp64": L.PREC_FP64, "fp32": L.PREC_FP32, "tf32": L.PREC_TF32, "bf16": L.PREC_BF16}
 REG = {"exact": L.REG_EXACT, "augmented": L.REG_AUGMENTED, "ridge": L.REG_RIDGE}
@@ -317,6 +318,22 @@ def tucker_sample_rows_ridge(h: Handle, dims: Sequence[int], K: Sequence[int],
                                              C.byref(cs)))
     out.n_unique, out.n_draws = int(cs.n_unique), int(cs.n_draws)
     return out
+
+
+BETA_MODE = {"bound": 0, "exact": 1}
+
+
+def tucker_missing_beta(h: Handle, X, A: Sequence[torch.Tensor], lam: float, mode: str = "bound",
+                        prec: str = "fp64", eps: float = 0.1, delta: float = 0.1) -> dict:
+    """Overestimate factor of the observed-entry sampler (Sec. 4.2): lambda_max of the
+    missing rows' cross ridge scores (the corollary's bound or the certified exact value),
+    beta_miss, c_min, beta = c_min beta_miss, beta' and Alg. 1 line 3's s."""
+    lib = L.load()
+    info = L.TuckerMissingBetaInfo()
+    _check(h.h, lib.tucker_missing_beta(h.h, C.byref(_tensor(X)), _ranks([a.shape[1] for a in A]),
+                                        _factors(A), float(lam), BETA_MODE[mode], PREC[prec],
+                                        float(eps), float(delta), C.byref(info)))
+    return {k: getattr(info, k) for k, _ in L.TuckerMissingBetaInfo._fields_}
 
 
 def tucker_sample_rows_noalloc(dims: Sequence[int], ranks: Sequence[int],

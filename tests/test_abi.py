@@ -39,6 +39,8 @@ def test_struct_layouts_match_c():
     assert ctypes.sizeof(_lib.TuckerTensor) == 8 + 64 + 8 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(_lib.TuckerSamples) == 6 * 8
     assert ctypes.sizeof(_lib.TuckerStats) == 7 * 8 + 3 * 8 + 8 + 8 + 8 + 8 + 2 * 8 + 2 * 8
+    # tucker_missing_beta_info: seven doubles, two ints
+    assert ctypes.sizeof(_lib.TuckerMissingBetaInfo) == 7 * 8 + 2 * 4
 
 
 def test_create_without_gpu_fails_cleanly():
