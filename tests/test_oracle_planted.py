@@ -8,6 +8,7 @@ import pytest
 from oracle import (adjoint as ADJ, als as ALS, core_update as CU, leverage as LV,
                     philox as PH, ridge_kron as RK, sampling as S)
 from tests import test_oracle_core as TC
+from tests import test_oracle_factor_sketch as TF
 from tests import test_oracle_philox_leverage as TL
 from tests import test_oracle_ridge_kron as TR
 from tests import test_oracle_sampling as TS
@@ -194,6 +195,18 @@ def _mixture_weight_dropped(mp):
     mp.setattr(RK, "ridge_row_probabilities", bad)
 
 
+def _factor_rows_modes_swapped(mp):
+    orig = ALS.factor_design_rows
+    mp.setattr(ALS, "factor_design_rows",
+               lambda core, factors, n, idx: orig(core, factors, n, list(idx)[::-1]))
+
+
+def _factor_probabilities_uniform(mp):
+    def bad(keys_u, lev_list, dims, reg=S.REG_EXACT, d=0):
+        return np.full(np.asarray(keys_u).size, 1.0 / float(np.prod([int(v) for v in dims])))
+    mp.setattr(S, "row_probabilities", bad)
+
+
 PLANTS = {
     "kron_order_reversed": (_kron_order_reversed,
                             [TC.test_sampled_row_products_equal_explicit_rows]),
@@ -238,6 +251,10 @@ PLANTS = {
     "augmented_reg_as_identity": (_augmented_reg_as_identity,
                                   [lambda: TC.test_count_form_equals_explicit_sketch_matrix(
                                       S.REG_AUGMENTED)]),
+    "factor_rows_modes_swapped": (_factor_rows_modes_swapped,
+                                  [lambda: TF.test_design_rows_are_columns_of_explicit_kn(0)]),
+    "factor_probabilities_uniform": (_factor_probabilities_uniform,
+                                     [TF.test_sketched_factor_gram_is_unbiased]),
     "mixture_weight_dropped": (_mixture_weight_dropped,
                                [lambda: TR.test_ridge_sampler_probabilities_are_the_ridge_distribution(
                                    0.4)]),
