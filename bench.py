@@ -516,6 +516,8 @@ class Timer:
 
 STAGES = ("ms_leverage", "ms_sample", "ms_dedupe", "ms_gather", "ms_gram", "ms_solve")
 RIDGE_LAMBDA = 1e8
+# fiber draws of each sketched factor update in the ALS sweeps the benchmark times
+FACTOR_M = 16384
 
 
 def ridge_alg1_count(d, d_eff, eps=0.1, delta=0.1):
@@ -687,13 +689,34 @@ def main():
         if not missing:
             Fa = [a.clone() for a in F]
             ca = T.tucker_core_update_exact(h, X, F, w.lam, "fp64")
-            for kind in ("sketched", "exact"):
-                sk = kind == "sketched"
+            # "sketched": sketched core, exact factors; "sketched_factors": both sketched
+            # (FACTOR_M fiber draws per factor update)
+            for kind in ("sketched", "exact", "sketched_factors"):
+                sk = kind != "exact"
+                T.tucker_set_factor_sketch(h, FACTOR_M if kind == "sketched_factors" else 0)
                 T.tucker_als_sweep(h, X, Fa, ca, w.lam, sk, m_t, w.seed_sample, 0, args.reg, prec)
                 ms_s, _ = timer(lambda: T.tucker_als_sweep(h, X, Fa, ca, w.lam, sk, m_t,
                                                            w.seed_sample, 1, args.reg, prec),
                                 min(args.steps, 3))
                 extra[f"als_sweep_ms_{kind}"] = statistics.mean(ms_s)
+            # ten sweeps of each from the same N(0,1) start: final loss and RMSE
+            quality = {}
+            c0, F0 = synth.init_state(w)
+            for kind in ("exact", "sketched", "sketched_factors"):
+                sk = kind != "exact"
+                T.tucker_set_factor_sketch(h, FACTOR_M if kind == "sketched_factors" else 0)
+                Fq = [torch.from_numpy(a.astype(w.np_dtype)).to(dev) for a in F0]
+                cq = torch.from_numpy(c0.reshape(-1).astype(np.float64)).to(dev)
+                try:
+                    for sw in range(10):
+                        loss, rmse = T.tucker_als_sweep(h, X, Fq, cq, w.lam, sk, m_t,
+                                                        w.seed_sample, sw, args.reg, prec)
+                    quality[kind] = {"loss": loss, "rmse": rmse}
+                except T.TuckerError as e:              # reported, not hidden
+                    quality[kind] = {"error": str(e), "sweep": sw}
+            T.tucker_set_factor_sketch(h, 0)
+            extra["als_factor_m"] = FACTOR_M
+            extra["als_ten_sweeps"] = quality
             lev = T.tucker_leverage_scores(h, F)[0]
             smp = T.tucker_sample_rows(h, w.dims, w.ranks, lev, m_t, w.seed_sample, 0, args.reg)
             gf, stf = T.tucker_core_update_sketched(h, X, F, w.lam, 0, 0, 0, args.reg, prec,

@@ -415,6 +415,39 @@ tucker_status tucker_sample_rows_ridge(tucker_handle* h, int N, const int64_t* I
                                        const double* const* usq, const double* c, int64_t m,
                                        uint64_t seed, uint32_t sweep, tucker_samples* out);
 
+/* Sketched factor update of mode n (this library's extension of Alg. 2's
+ * factor step; the paper updates the factors exactly).  The factor update is
+ * the ridge regression min ||B_n A^T - X_(n)^T||^2 + lambda ||A||^2 with the
+ * design B_n = W G_(n)^T, W = (x)_{k != n} A^(k), whose rows are indexed
+ * row-major by the multi-index over the modes k != n.  Its rows lie in the
+ * column space of W, so l_j(B_n) <= prod_{k != n} l_{j_k}(A^(k)) (Lemma 4.1 at
+ * lambda = 0): the product distribution of the other modes' leverage scores is
+ * an (R_n / prod_{k != n} R_k)-overestimate, and Alg. 1's sketch applies with
+ * B_n in place of K.  m draws use the core sampler's arithmetic over the modes
+ * k != n with Philox key (seed, sweep + (n + 1) 2^32) (apart from the core
+ * sampler's (seed, sweep)); after the dedupe, with w_u = c_u / (m p_u),
+ *     M = sum_u w_u b_u b_u^T + lambda I,   Y = sum_u w_u x_u b_u^T,   A^(n) = Y M^-1,
+ * b_u = G_(n) (x)_{k != n} A^(k)[j_k] and x_u the mode-n fiber of X at row u
+ * (I_n strided reads).  The fibers and Y are in X's element type (FP32 or
+ * FP64) summed in a fixed order; b_u, M and its inverse in FP64.
+ *   X               dense tensor (order >= 2)
+ *   A_inout[N]      device factors; A_inout[n] is overwritten
+ *   core            device FP64 [d], vec(G) row-major
+ *   n               the mode, 0 <= n < N
+ *   m               draws, 1 <= m < 2^31
+ * Errors: EINVAL, ENOTSPD, ECUDA. */
+tucker_status tucker_factor_update_sketched(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                            void* const* A_inout, const double* core, int n,
+                                            double lambda, int64_t m, uint64_t seed,
+                                            uint32_t sweep);
+
+/* m > 0: the factor updates of later tucker_als_sweep calls on h are
+ * tucker_factor_update_sketched with m draws each (key word sweep + (n+1) 2^32);
+ * 0 (the default): exact factor updates.  With sketched factor updates the
+ * sweep forms the product chain X x_{k<N} A^(k)T once more for its loss.
+ * Errors: EINVAL (h NULL, m < 0 or m >= 2^31). */
+tucker_status tucker_set_factor_sketch(tucker_handle* h, int64_t m);
+
 /* Overestimate factor of the observed-entry sampler (Sec. 4.2, missing data).
  * With S the observed rows of K, S-bar the missing ones and
  * L = K (K^T K + lambda I)^+ K^T the cross lambda-ridge scores of K, the ridge

@@ -85,6 +85,9 @@ SIGNATURES = {
                                       _IP, _DP]),
     "tucker_sample_rows_ridge": (C.c_int, [_P, C.c_int, _I64P, _IP, _PP, _P, C.c_int64, C.c_uint64,
                                            C.c_uint32, C.POINTER(TuckerSamples)]),
+    "tucker_factor_update_sketched": (C.c_int, [_P, C.POINTER(TuckerTensor), _IP, _PP, _P, C.c_int,
+                                                C.c_double, C.c_int64, C.c_uint64, C.c_uint32]),
+    "tucker_set_factor_sketch": (C.c_int, [_P, C.c_int64]),
     "tucker_missing_beta": (C.c_int, [_P, C.POINTER(TuckerTensor), _IP, _PP, C.c_double, C.c_int,
                                       C.c_int, C.c_double, C.c_double,
                                       C.POINTER(TuckerMissingBetaInfo)]),

@@ -9,6 +9,8 @@
 // FP64) and inverts it; k_factor_rows gives each warp rows of A^(n): it forms a
 // row's right-hand side with its lanes over the core entries and applies the
 // inverse.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tk {
@@ -29,6 +31,62 @@ struct FactorSolveArgs {
 
 constexpr int FS_THREADS = 256;
 constexpr int FS_ROWS = 32;                  // rows per CTA of the row kernel: four per warp
+
+// Cholesky factor of the SPD R x R matrix Lm (shared memory, in place; lane i
+// of warp 0 owns row i when R <= 32, else thread 0) and its inverse
+// L^-T L^-1 into Lout (row-major).  Called by every thread of the CTA.
+__device__ void spd_inverse(double* Lm, int Rn, double* Lout, int* status) {
+  if (Rn <= 32) {
+    if (threadIdx.x < 32) {                          // lane i owns row i
+      const int lane = threadIdx.x;
+      for (int j = 0; j < Rn; ++j) {
+        double piv = Lm[j * Rn + j];
+        if (!(piv > 0.0)) { if (lane == 0) set_status(status, DEV_NOTSPD); piv = 1.0; }
+        const double djj = sqrt(piv);
+        __syncwarp();
+        if (lane == j) Lm[j * Rn + j] = djj;
+        if (lane > j && lane < Rn) Lm[lane * Rn + j] /= djj;
+        __syncwarp();
+        if (lane > j && lane < Rn) {
+          const double lij = Lm[lane * Rn + j];
+          for (int c = j + 1; c <= lane; ++c) Lm[lane * Rn + c] -= lij * Lm[c * Rn + j];
+        }
+        __syncwarp();
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    for (int j = 0; j < Rn; ++j) {
+      double v = Lm[j * Rn + j];
+      for (int k = 0; k < j; ++k) v -= Lm[j * Rn + k] * Lm[j * Rn + k];
+      if (!(v > 0.0)) { set_status(status, DEV_NOTSPD); v = 1.0; }
+      const double djj = sqrt(v);
+      Lm[j * Rn + j] = djj;
+      for (int i = j + 1; i < Rn; ++i) {
+        double w = Lm[i * Rn + j];
+        for (int k = 0; k < j; ++k) w -= Lm[i * Rn + k] * Lm[j * Rn + k];
+        Lm[i * Rn + j] = w / djj;
+      }
+    }
+  }
+  __syncthreads();
+  // Minv = L^-T L^-1 (the inverse of the system), column j by thread j: the
+  // rows then need R_n independent dot products instead of two dependent
+  // triangular solves each
+  for (int j = threadIdx.x; j < Rn; j += blockDim.x) {
+    double z[TUCKER_MAX_RANK];
+    for (int x = 0; x < Rn; ++x) {                   // L z = e_j
+      double v = x == j ? 1.0 : 0.0;
+      for (int k = 0; k < x; ++k) v -= Lm[x * Rn + k] * z[k];
+      z[x] = v / Lm[x * Rn + x];
+    }
+    for (int x = Rn - 1; x >= 0; --x) {              // L^T w = z
+      double v = z[x];
+      for (int k = x + 1; k < Rn; ++k) v -= Lm[k * Rn + x] * z[k];
+      z[x] = v / Lm[x * Rn + x];
+    }
+    for (int x = 0; x < Rn; ++x) Lout[x * Rn + j] = z[x];
+  }
+}
 
 // The R_n x R_n system of mode n, lhs = G_(n) H G_(n)^T + lambda I with
 // H = (x)_{k != n} A^(k)T A^(k) applied to the core mode by mode, its Cholesky
@@ -78,56 +136,7 @@ __global__ void __launch_bounds__(FS_THREADS) k_factor_lhs(FactorSolveArgs a, do
     if (part == 0) Lm[e] = acc + (x == y ? a.lambda : 0.0);
   }
   __syncthreads();
-  if (Rn <= 32) {
-    if (threadIdx.x < 32) {                          // lane i owns row i
-      const int lane = threadIdx.x;
-      for (int j = 0; j < Rn; ++j) {
-        double piv = Lm[j * Rn + j];
-        if (!(piv > 0.0)) { if (lane == 0) set_status(a.status, DEV_NOTSPD); piv = 1.0; }
-        const double djj = sqrt(piv);
-        __syncwarp();
-        if (lane == j) Lm[j * Rn + j] = djj;
-        if (lane > j && lane < Rn) Lm[lane * Rn + j] /= djj;
-        __syncwarp();
-        if (lane > j && lane < Rn) {
-          const double lij = Lm[lane * Rn + j];
-          for (int c = j + 1; c <= lane; ++c) Lm[lane * Rn + c] -= lij * Lm[c * Rn + j];
-        }
-        __syncwarp();
-      }
-    }
-  } else if (threadIdx.x == 0) {
-    for (int j = 0; j < Rn; ++j) {
-      double v = Lm[j * Rn + j];
-      for (int k = 0; k < j; ++k) v -= Lm[j * Rn + k] * Lm[j * Rn + k];
-      if (!(v > 0.0)) { set_status(a.status, DEV_NOTSPD); v = 1.0; }
-      const double djj = sqrt(v);
-      Lm[j * Rn + j] = djj;
-      for (int i = j + 1; i < Rn; ++i) {
-        double w = Lm[i * Rn + j];
-        for (int k = 0; k < j; ++k) w -= Lm[i * Rn + k] * Lm[j * Rn + k];
-        Lm[i * Rn + j] = w / djj;
-      }
-    }
-  }
-  __syncthreads();
-  // Minv = L^-T L^-1 (the inverse of the system), column j by thread j: the
-  // rows then need R_n independent dot products instead of two dependent
-  // triangular solves each
-  for (int j = threadIdx.x; j < Rn; j += blockDim.x) {
-    double z[TUCKER_MAX_RANK];
-    for (int x = 0; x < Rn; ++x) {                   // L z = e_j
-      double v = x == j ? 1.0 : 0.0;
-      for (int k = 0; k < x; ++k) v -= Lm[x * Rn + k] * z[k];
-      z[x] = v / Lm[x * Rn + x];
-    }
-    for (int x = Rn - 1; x >= 0; --x) {              // L^T w = z
-      double v = z[x];
-      for (int k = x + 1; k < Rn; ++k) v -= Lm[k * Rn + x] * z[k];
-      z[x] = v / Lm[x * Rn + x];
-    }
-    for (int x = 0; x < Rn; ++x) Lout[x * Rn + j] = z[x];
-  }
+  spd_inverse(Lm, Rn, Lout, a.status);
 }
 
 // Rows of the new A^(n): warp per row, rhs_x = sum_pq B[p][i][q] core[p][x][q]
@@ -185,6 +194,289 @@ tucker_status factor_solve(tucker_handle* h, const FactorSet& F, int n, double* 
                                   (int)smem2));
   TK_COUNT(h);
   k_factor_rows<<<ceil_div(F.I[n], FS_ROWS), FS_THREADS, smem2, h->stream>>>(a, Lscratch);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+// ------------------------------------------------ sketched factor update
+// Mode n: rows u of the factor design B_n = W G_(n)^T (W = (x)_{k != n} A^(k),
+// rows indexed row-major by the multi-index over the modes k != n) drawn from
+// the product of those modes' leverage scores, deduplicated; with
+// w_u = c_u / (m p_u), p_u = prod (q / Q) in mode order (the core sampler's
+// arithmetic),
+//     M = sum_u w_u b_u b_u^T + lambda I,   Y = sum_u w_u x_u b_u^T,   A^(n) = Y M^-1,
+// b_u = G_(n) (x)_{k != n} A^(k)[j_k] and x_u the mode-n fiber of X at row u.
+// The product of leverage scores is an (R_n / prod_{k != n} R_k)-overestimate
+// of the leverage scores of B_n (its rows lie in the column space of W).
+// The fibers and the sums Y are in X's element type T (FP32 values of X are
+// exact in FP32); b_u, w_u b_u, M and its inverse are FP64.
+struct FiberArgs {
+  int N, n;                                // order; the updated mode
+  int R[TUCKER_MAX_ORDER];
+  int64_t I[TUCKER_MAX_ORDER];
+  int64_t stride[TUCKER_MAX_ORDER];        // element strides of X (row-major)
+  const void* A[TUCKER_MAX_ORDER];
+  int is64;
+  const void* X;
+  const double* core;
+  int d;
+  const uint64_t* keys;                    // distinct keys over the modes k != n
+  const uint32_t* counts;
+  const int* nu;
+  const uint64_t* cdf[TUCKER_MAX_ORDER];   // indexed by mode k (k != n)
+  int64_t m;                               // draws
+  double lambda;
+  int splits;                              // CTAs along the sample in the normal kernel
+  void* xs;                                // [cap][I_n] fibers
+  double* wb;                              // [cap][R_n]  w_u b_u (FP64)
+  double* bb;                              // [cap][R_n]  b_u (FP64)
+  double* partY;                           // [splits][I_n][R_n]
+  double* partM;                           // [splits][R_n][R_n]
+  void* A_out;                             // I_n x R_n, X's dtype
+  int* status;
+};
+
+constexpr int FB_WARPS = 8;
+
+// Warp per distinct row: decode, weight, design row b_u (lanes over the core
+// entries of each r_n, warp sums in a fixed order) and the fiber (lanes over i_n).
+template <typename T>
+__global__ void __launch_bounds__(FB_WARPS * 32) k_fiber_rows(FiberArgs a) {
+  __shared__ double arow[FB_WARPS][TUCKER_MAX_ORDER * TUCKER_MAX_RANK];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nu = *a.nu, N = a.N, n = a.n, Rn = a.R[n];
+  const int dn = a.d / Rn;                  // entries of the core per r_n
+  int postn = 1;
+  for (int k = n + 1; k < N; ++k) postn *= a.R[k];
+  double* ar = arow[wid];
+  for (int64_t u = (int64_t)blockIdx.x * FB_WARPS + wid; u < nu;
+       u += (int64_t)gridDim.x * FB_WARPS) {
+    // multi-index over the modes k != n (last fastest), probability, fiber base
+    uint64_t key = a.keys[u];
+    int64_t j[TUCKER_MAX_ORDER];
+    for (int k = N - 1; k >= 0; --k) {
+      if (k == n) { j[k] = 0; continue; }
+      j[k] = (int64_t)(key % (uint64_t)a.I[k]);
+      key /= (uint64_t)a.I[k];
+    }
+    double p = 1.0;
+    bool first = true;
+    int64_t base = 0;
+    for (int k = 0; k < N; ++k) {
+      if (k == n) continue;
+      const uint64_t* C = a.cdf[k];
+      const uint64_t Q = C[a.I[k] - 1];
+      const uint64_t q = C[j[k]] - (j[k] > 0 ? C[j[k] - 1] : 0);
+      const double f = (double)q / (double)Q;
+      p = first ? f : p * f;
+      first = false;
+      base += j[k] * a.stride[k];
+    }
+    const double w = (double)a.counts[u] / ((double)a.m * p);
+    // factor rows a_k(j_k), k != n, into shared memory (offset k * TUCKER_MAX_RANK)
+    for (int k = 0; k < N; ++k) {
+      if (k == n) continue;
+      for (int r = lane; r < a.R[k]; r += 32)
+        ar[k * TUCKER_MAX_RANK + r] = load_as_double(a.A[k], j[k] * a.R[k] + r, a.is64);
+    }
+    __syncwarp();
+    // b_u[r] = sum over the other core indices o of G[.., r, ..] prod_{k != n} a_k[r_k]
+    for (int r = 0; r < Rn; ++r) {
+      double acc = 0.0;
+      for (int o = lane; o < dn; o += 32) {
+        const int pre = o / postn, post = o - pre * postn;
+        const int e = (pre * Rn + r) * postn + post;      // core index
+        double f = a.core[e];
+        int rem = e;
+        for (int k = N - 1; k >= 0; --k) {
+          const int rk = rem % a.R[k];
+          rem /= a.R[k];
+          if (k != n) f *= ar[k * TUCKER_MAX_RANK + rk];
+        }
+        acc += f;
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        a.bb[u * Rn + r] = acc;
+        a.wb[u * Rn + r] = w * acc;
+      }
+    }
+    // the fiber x_u[i] = X[base + i stride_n]
+    T* xs = static_cast<T*>(a.xs) + u * a.I[n];
+    for (int64_t i = lane; i < a.I[n]; i += 32)
+      xs[i] = (T)load_as_double(a.X, base + i * a.stride[n], a.is64);
+    __syncwarp();
+  }
+}
+
+// Split normal equations: CTA (row block, split s) sums its share of the sample,
+// Y_s[i][r] = sum_u xs[u][i] wb[u][r] for 128 rows i, and (row block 0)
+// M_s[r][r'] = sum_u wb[u][r] b[u][r'].  Fixed order within a split; RB >= R_n
+// keeps the accumulators in registers.
+template <typename T, int RB>
+__global__ void __launch_bounds__(128) k_fiber_normal(FiberArgs a) {
+  extern __shared__ unsigned char fsm[];
+  T* wbs = reinterpret_cast<T*>(fsm);               // [64][Rn] staged rows of wb
+  const int nu = *a.nu, Rn = a.R[a.n];
+  const int64_t In = a.I[a.n];
+  const int s = blockIdx.y;
+  const int64_t chunk = (nu + a.splits - 1) / a.splits;
+  const int64_t u0 = s * chunk, u1 = min((int64_t)nu, u0 + chunk);
+  const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
+  T acc[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) acc[r] = (T)0;
+  const T* xs = static_cast<const T*>(a.xs);
+  const double* wb = a.wb;
+  for (int64_t ub = u0; ub < u1; ub += 64) {
+    const int nb = (int)min((int64_t)64, u1 - ub);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * Rn; e += 128) wbs[e] = (T)wb[ub * Rn + e];
+    __syncthreads();
+    if (i < In) {
+      for (int q = 0; q < nb; ++q) {
+        const T x = xs[(ub + q) * In + i];
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+          if (r < Rn) acc[r] = fma(x, wbs[q * Rn + r], acc[r]);
+      }
+    }
+  }
+  if (i < In) {
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+      if (r < Rn) a.partY[((int64_t)s * In + i) * Rn + r] = (double)acc[r];
+  }
+  if (blockIdx.x == 0) {
+    const double* bb = a.bb;
+    for (int e = threadIdx.x; e < Rn * Rn; e += 128) {
+      const int r = e / Rn, c = e % Rn;
+      double mv = 0.0;
+      for (int64_t u = u0; u < u1; ++u) mv = fma(wb[u * Rn + r], bb[u * Rn + c], mv);
+      a.partM[(int64_t)s * Rn * Rn + e] = mv;
+    }
+  }
+}
+
+// A^(n) = Y M^-1: every CTA sums the M partials (fixed order), adds lambda I,
+// factors and inverts it (spd_inverse), then forms its 64 rows of Y from the
+// partials and applies the inverse.
+__global__ void __launch_bounds__(256) k_fiber_finish(FiberArgs a) {
+  extern __shared__ double fin[];
+  const int Rn = a.R[a.n];
+  double* Lm = fin;                                  // Rn x Rn
+  double* Mi = Lm + Rn * Rn;                         // Rn x Rn
+  double* Ys = Mi + Rn * Rn;                         // 64 x Rn
+  const int64_t In = a.I[a.n];
+  for (int e = threadIdx.x; e < Rn * Rn; e += blockDim.x) {
+    double v = 0.0;
+    for (int s = 0; s < a.splits; ++s) v += a.partM[(int64_t)s * Rn * Rn + e];
+    const int r = e / Rn, c = e % Rn;
+    // the symmetric part, so that both triangles carry the same value
+    double vt = 0.0;
+    for (int s = 0; s < a.splits; ++s) vt += a.partM[(int64_t)s * Rn * Rn + c * Rn + r];
+    Lm[e] = 0.5 * (v + vt) + (r == c ? a.lambda : 0.0);
+  }
+  __syncthreads();
+  spd_inverse(Lm, Rn, Mi, a.status);
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * 64;
+  const int rows = (int)min((int64_t)64, In - i0);
+  for (int e = threadIdx.x; e < rows * Rn; e += blockDim.x) {
+    const int64_t i = i0 + e / Rn;
+    const int r = e % Rn;
+    double v = 0.0;
+    for (int s = 0; s < a.splits; ++s) v += a.partY[((int64_t)s * In + i) * Rn + r];
+    Ys[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rows * Rn; e += blockDim.x) {
+    const int li = e / Rn, x = e % Rn;
+    double v = 0.0;
+    for (int k = 0; k < Rn; ++k) v = fma(Mi[x * Rn + k], Ys[li * Rn + k], v);
+    const int64_t i = i0 + li;
+    if (a.is64) static_cast<double*>(a.A_out)[i * Rn + x] = v;
+    else static_cast<float*>(a.A_out)[i * Rn + x] = (float)v;
+  }
+}
+
+size_t fiber_workspace_bytes(const FactorSet& F, int n, int64_t cap, int splits) {
+  const size_t es = F.is64 ? 8 : 4;
+  const int Rn = F.R[n];
+  return (size_t)cap * F.I[n] * es + 256 + 2 * ((size_t)cap * Rn * 8 + 256) +
+         (size_t)splits * F.I[n] * Rn * 8 + 256 + (size_t)splits * Rn * Rn * 8 + 256;
+}
+
+int fiber_splits(int64_t cap) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, cap / 256)); }
+
+tucker_status launch_fiber_update(tucker_handle* h, const FactorSet& F, int n, const void* X,
+                                  const double* core, const uint64_t* keys,
+                                  const uint32_t* counts, const int* d_nu, int64_t cap,
+                                  const uint64_t* const* cdf_others, int64_t m, double lambda,
+                                  char* ws, size_t ws_bytes, void* A_out) {
+  const int splits = fiber_splits(cap);
+  if (fiber_workspace_bytes(F, n, cap, splits) > ws_bytes)
+    return fail(h, TUCKER_EINTERNAL, "fiber workspace too small");
+  const size_t es = F.is64 ? 8 : 4;
+  const int Rn = F.R[n];
+  FiberArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = F.N;
+  a.n = n;
+  int64_t st = 1;
+  for (int k = F.N - 1; k >= 0; --k) {
+    a.R[k] = F.R[k];
+    a.I[k] = F.I[k];
+    a.A[k] = F.A[k];
+    a.stride[k] = st;
+    st *= F.I[k];
+  }
+  int pos = 0;
+  for (int k = 0; k < F.N; ++k) if (k != n) a.cdf[k] = cdf_others[pos++];
+  a.is64 = F.is64;
+  a.X = X;
+  a.core = core;
+  a.d = F.d;
+  a.keys = keys;
+  a.counts = counts;
+  a.nu = d_nu;
+  a.m = m;
+  a.lambda = lambda;
+  a.splits = splits;
+  char* q = ws;
+  auto take = [&](size_t bytes) { char* r = q; q += (bytes + 255) & ~size_t(255); return r; };
+  a.xs = take((size_t)cap * F.I[n] * es);
+  a.wb = reinterpret_cast<double*>(take((size_t)cap * Rn * 8));
+  a.bb = reinterpret_cast<double*>(take((size_t)cap * Rn * 8));
+  a.partY = reinterpret_cast<double*>(take((size_t)splits * F.I[n] * Rn * 8));
+  a.partM = reinterpret_cast<double*>(take((size_t)splits * Rn * Rn * 8));
+  a.A_out = A_out;
+  a.status = h->d_status;
+  const int g1 = (int)std::min<int64_t>(ceil_div(cap, FB_WARPS), (int64_t)h->num_sms * 16);
+  TK_COUNT(h);
+  if (F.is64) k_fiber_rows<double><<<std::max(g1, 1), FB_WARPS * 32, 0, h->stream>>>(a);
+  else k_fiber_rows<float><<<std::max(g1, 1), FB_WARPS * 32, 0, h->stream>>>(a);
+  TK_LAUNCH(h);
+  const dim3 g2((unsigned)ceil_div(F.I[n], 128), (unsigned)splits);
+  const size_t sm2 = (size_t)64 * Rn * es;
+  TK_COUNT(h);
+#define TK_FIBER_NORMAL(RB)                                                        \
+  do {                                                                             \
+    if (F.is64) k_fiber_normal<double, RB><<<g2, 128, sm2, h->stream>>>(a);        \
+    else k_fiber_normal<float, RB><<<g2, 128, sm2, h->stream>>>(a);                \
+  } while (0)
+  if (Rn <= 4) TK_FIBER_NORMAL(4);
+  else if (Rn <= 8) TK_FIBER_NORMAL(8);
+  else if (Rn <= 16) TK_FIBER_NORMAL(16);
+  else if (Rn <= 32) TK_FIBER_NORMAL(32);
+  else TK_FIBER_NORMAL(64);
+#undef TK_FIBER_NORMAL
+  TK_LAUNCH(h);
+  const size_t sm3 = (size_t)(2 * Rn * Rn + 64 * Rn) * sizeof(double);
+  TK_CUDA(h, cudaFuncSetAttribute(k_fiber_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm3));
+  TK_COUNT(h);
+  k_fiber_finish<<<(unsigned)ceil_div(F.I[n], 64), 256, sm3, h->stream>>>(a);
   TK_LAUNCH(h);
   return TUCKER_OK;
 }

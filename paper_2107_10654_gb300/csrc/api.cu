@@ -26,7 +26,7 @@ namespace tk {
 tucker_status hash_ensure(tucker_handle* h, const tucker_tensor* X, int* probes_out);
 size_t sample_keys_scratch(const FactorSet& F, bool observed);
 tucker_status sample_keys(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
-                          int64_t m, uint64_t seed, uint32_t sweep, int reg,
+                          int64_t m, uint64_t seed, uint64_t sweep, int reg,
                           const tucker_tensor* observed, int64_t max_draws,
                           uint64_t* keys_out, int64_t* d_T, int64_t* T_host, Arena& ar);
 tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
@@ -78,6 +78,13 @@ tucker_status ttm_chain_all(tucker_handle* h, const FactorSet& F, const void* X,
                             double* buf1, double* y);
 tucker_status ttm_chain_except(tucker_handle* h, const FactorSet& F, const void* X, int n,
                                double* buf0, double* buf1, double* out);
+size_t fiber_workspace_bytes(const FactorSet& F, int n, int64_t cap, int splits);
+int fiber_splits(int64_t cap);
+tucker_status launch_fiber_update(tucker_handle* h, const FactorSet& F, int n, const void* X,
+                                  const double* core, const uint64_t* keys,
+                                  const uint32_t* counts, const int* d_nu, int64_t cap,
+                                  const uint64_t* const* cdf_others, int64_t m, double lambda,
+                                  char* ws, size_t ws_bytes, void* A_out);
 tucker_status kron_whiten(tucker_handle* h, const FactorSet& F, double* const* V,
                           double* const* ev, double lambda, const double* M, double* tmp,
                           double* out);
@@ -1416,6 +1423,109 @@ tucker_status tucker_ridge_loss(tucker_handle* h, const tucker_tensor* X, const 
   return TUCKER_OK;
 }
 
+// ------------------------------------------------ sketched factor update
+// Rows of the mode-n factor design B_n drawn from the product of the leverage
+// scores of A^(k), k != n (the core sampler over those modes, Philox key word
+// sweep + (n + 1) 2^32), deduplicated, and the weighted normal equations of
+// the mode-n fibers (launch_fiber_update).
+struct FsBufs {
+  double* lev[TUCKER_MAX_ORDER];
+  uint64_t* cdf[TUCKER_MAX_ORDER];
+  int* rk;
+  uint64_t* raw;
+  int64_t* d_T;
+  char* sort;
+  size_t sort_bytes;
+  uint64_t* keys_u;
+  uint32_t* counts;
+  int* nu;
+  char* fws;
+  size_t fws_bytes;
+};
+
+static FactorSet others_of(const FactorSet& F, int n) {
+  FactorSet o;
+  memset(&o, 0, sizeof(o));
+  o.is64 = F.is64;
+  o.d = F.d / F.R[n];
+  o.total = F.total / (uint64_t)F.I[n];
+  for (int k = 0; k < F.N; ++k) {
+    if (k == n) continue;
+    o.I[o.N] = F.I[k];
+    o.R[o.N] = F.R[k];
+    o.A[o.N] = F.A[k];
+    ++o.N;
+  }
+  return o;
+}
+
+static void carve_fs(Arena& ar, const FactorSet& F, int n, int64_t m, FsBufs* b) {
+  const FactorSet o = others_of(F, n);
+  for (int k = 0; k < o.N; ++k) {
+    b->lev[k] = ar.get<double>(o.I[k]);
+    b->cdf[k] = ar.get<uint64_t>(o.I[k]);
+  }
+  b->rk = reinterpret_cast<int*>(ar.get<char>(leverage_aux_bytes(max_dim(o))));
+  b->raw = ar.get<uint64_t>(m);
+  b->d_T = ar.get<int64_t>(1);
+  b->sort_bytes = sort_dedupe_scratch(m);
+  b->sort = ar.get<char>(b->sort_bytes);
+  b->keys_u = ar.get<uint64_t>(m);
+  b->counts = ar.get<uint32_t>(m);
+  b->nu = ar.get<int>(1);
+  b->fws_bytes = fiber_workspace_bytes(F, n, m, fiber_splits(m));
+  b->fws = ar.get<char>(b->fws_bytes);
+}
+
+static size_t fs_bytes(const FactorSet& F, int n, int64_t m) {
+  Arena sz(nullptr);
+  FsBufs b;
+  carve_fs(sz, F, n, m, &b);
+  return sz.off + sample_keys_scratch(others_of(F, n), false) + 4096;
+}
+
+static tucker_status factor_sketch_impl(tucker_handle* h, const FactorSet& F, const void* Xd,
+                                        void* const* A, const double* core, int n, double lambda,
+                                        int64_t m, uint64_t seed, uint32_t sweep, Arena& ar) {
+  FsBufs b;
+  carve_fs(ar, F, n, m, &b);
+  const FactorSet o = others_of(F, n);
+  TK_TRY(launch_leverage(h, o, b.lev, b.cdf, b.rk, nullptr, nullptr, nullptr));
+  int64_t T_host = 0;
+  TK_TRY(sample_keys(h, o, b.cdf, m, seed, (uint64_t)sweep + ((uint64_t)(n + 1) << 32),
+                     TUCKER_REG_EXACT, nullptr, 0, b.raw, b.d_T, &T_host, ar));
+  TK_TRY(sort_dedupe(h, b.raw, m, bits_for(o.total), b.keys_u, b.counts, b.nu, b.sort,
+                     b.sort_bytes));
+  return launch_fiber_update(h, F, n, Xd, core, b.keys_u, b.counts, b.nu, m, b.cdf, m, lambda,
+                             b.fws, b.fws_bytes, A[n]);
+}
+
+tucker_status tucker_factor_update_sketched(tucker_handle* h, const tucker_tensor* X, const int* R,
+                                            void* const* A_inout, const double* core, int n,
+                                            double lambda, int64_t m, uint64_t seed,
+                                            uint32_t sweep) {
+  if (!h) return TUCKER_EINVAL;
+  FactorSet F;
+  TK_TRY(check_tensor(h, X, R, (const void* const*)A_inout, &F));
+  if (!X->dense) return fail(h, TUCKER_EINVAL, "the sketched factor update needs a dense X");
+  if (!A_inout || !core) return fail(h, TUCKER_EINVAL, "null factors or core");
+  if (F.N < 2) return fail(h, TUCKER_EINVAL, "order must be >= 2");
+  if (n < 0 || n >= F.N) return fail(h, TUCKER_EINVAL, "mode %d out of range", n);
+  if (m < 1 || m >= (int64_t(1) << 31)) return fail(h, TUCKER_EINVAL, "m out of range");
+  if (!(lambda >= 0.0)) return fail(h, TUCKER_EINVAL, "lambda must be >= 0");
+  TK_TRY(ws_reserve(h, fs_bytes(F, n, m)));
+  Arena ar(h->ws);
+  TK_TRY(factor_sketch_impl(h, F, X->dense, A_inout, core, n, lambda, m, seed, sweep, ar));
+  return finish(h);
+}
+
+tucker_status tucker_set_factor_sketch(tucker_handle* h, int64_t m) {
+  if (!h) return TUCKER_EINVAL;
+  if (m < 0 || m >= (int64_t(1) << 31)) return fail(h, TUCKER_EINVAL, "m out of range");
+  h->factor_m = m;
+  return TUCKER_OK;
+}
+
 tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const int* R,
                                void* const* A_inout, double* core_inout, double lambda,
                                int sketched, int64_t m, uint64_t seed, uint32_t sweep,
@@ -1459,18 +1569,30 @@ tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const i
   double *b0, *b1, *B, *part, *res;
   Arena sz(nullptr);
   carve(sz, lev, cdf, gram, &rk, &b0, &b1, &B, &part, &res);
-  TK_TRY(ws_reserve(h, sz.off));
+  const int64_t mf = h->factor_m;                 // > 0: sketched factor updates
+  size_t fsb = 0;
+  if (mf > 0)
+    for (int n = 0; n < N; ++n) fsb = std::max(fsb, fs_bytes(F, n, mf));
+  TK_TRY(ws_reserve(h, sz.off + fsb + 256));
   Arena ar(h->ws);
   carve(ar, lev, cdf, gram, &rk, &b0, &b1, &B, &part, &res);
   for (int n = 0; n < N; ++n) {
+    if (mf > 0) {
+      Arena fa(h->ws + ((ar.off + 255) & ~size_t(255)));
+      TK_TRY(factor_sketch_impl(h, F, X->dense, A_inout, core_inout, n, lambda, mf, seed, sweep,
+                                fa));
+      continue;
+    }
     TK_TRY(launch_factor_grams(h, F, rk, gram));
     TK_TRY(ttm_chain_except(h, F, X->dense, n, b0, b1, B));
     TK_TRY(factor_solve(h, F, n, gram, core_inout, B, lambda, A_inout[n], Ls));
   }
   // the loss by the Gram identity needs y = K^T vec(X) for the new factors: the last
-  // product chain B = X x_{k<N} A^(k)T, times the new A^(N); and ||X||^2 (one pass)
+  // product chain B = X x_{k<N} A^(k)T (formed here when the factor updates were
+  // sketched), times the new A^(N); and ||X||^2 (one pass)
   const bool want_loss = loss_out_host || rmse_out_host;
   if (want_loss) {
+    if (mf > 0) TK_TRY(ttm_chain_except(h, F, X->dense, N - 1, b0, b1, B));
     TK_TRY(kt_x_from_last(h, F, B, h->keep));
     TK_TRY(tensor_sumsq(h, X->dense, F.is64, (int64_t)F.total, part, np, h->keep + F.d));
   }

@@ -79,6 +79,7 @@ struct tucker_handle {
   uint64_t next_solve_id = 1;
   int64_t launches = 0;         // kernels launched by this handle (all calls)
   int solver = 0;               // tucker_solver: FP64 Cholesky (0), mixed (1), Kronecker CG (2)
+  int64_t factor_m = 0;         // draws of each sketched factor update of an ALS sweep (0: exact)
   int timing = 0;               // record per-kernel events (ev[8..11]) during this call
   int chol_cluster[2] = {0, 0}; // CTAs of the one-cluster FP32 Cholesky of order chol_cluster_key
   int chol_cluster_key = -1;    // (without, with the explicit inverse; 0: does not fit)

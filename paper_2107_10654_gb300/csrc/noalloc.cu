@@ -22,7 +22,7 @@ tucker_status launch_cdf_from_lev(tucker_handle* h, int N, const int64_t* I,
                                   const double* const* lev, uint64_t* const* cdf);
 size_t sample_keys_scratch(const FactorSet& F, bool observed);
 tucker_status sample_keys(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
-                          int64_t m, uint64_t seed, uint32_t sweep, int reg,
+                          int64_t m, uint64_t seed, uint64_t sweep, int reg,
                           const tucker_tensor* observed, int64_t max_draws,
                           uint64_t* keys_out, int64_t* d_T, int64_t* T_host, Arena& ar);
 tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,

@@ -270,7 +270,7 @@ static int cdf_smem_bytes(const SampleArgs& a) {
 // until m are accepted (host loop, one sync per round).  *T_host receives T;
 // d_T (device int64) too.
 tucker_status sample_keys(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
-                          int64_t m, uint64_t seed, uint32_t sweep, int reg,
+                          int64_t m, uint64_t seed, uint64_t sweep, int reg,
                           const tucker_tensor* observed, int64_t max_draws,
                           uint64_t* keys_out, int64_t* d_T, int64_t* T_host, Arena& ar) {
   SampleArgs a;

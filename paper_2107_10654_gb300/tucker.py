@@ -20,7 +20,8 @@ __all__ = ["TuckerError", "Handle", "Samples", "CooTensor", "tucker_leverage_sco
            "tucker_sample_rows", "tucker_core_update_sketched", "tucker_core_update_exact",
            "tucker_als_sweep", "tucker_ridge_loss", "tucker_core_solve_adjoint",
            "tucker_sample_rows_noalloc", "tucker_sketched_gram", "tucker_set_solver",
-           "tucker_ridge_tables", "tucker_sample_rows_ridge", "tucker_missing_beta"]
+           "tucker_ridge_tables", "tucker_sample_rows_ridge", "tucker_missing_beta",
+           "tucker_factor_update_sketched", "tucker_set_factor_sketch"]
 
 PREC = {"fp64": L.PREC_FP64, "fp32": L.PREC_FP32, "tf32": L.PREC_TF32, "bf16": L.PREC_BF16}
 REG = {"exact": L.REG_EXACT, "augmented": L.REG_AUGMENTED, "ridge": L.REG_RIDGE}
@@ -318,6 +319,26 @@ def tucker_sample_rows_ridge(h: Handle, dims: Sequence[int], K: Sequence[int],
                                              C.byref(cs)))
     out.n_unique, out.n_draws = int(cs.n_unique), int(cs.n_draws)
     return out
+
+
+def tucker_factor_update_sketched(h: Handle, X: torch.Tensor, A: List[torch.Tensor],
+                                  core: torch.Tensor, n: int, lam: float, m: int, seed: int,
+                                  sweep: int = 0) -> torch.Tensor:
+    """Sketched factor update of mode n (leverage sample of the factor design from the other
+    modes' scores, mode-n fibers); A[n] is overwritten and returned."""
+    lib = L.load()
+    _need(core, "core")
+    _check(h.h, lib.tucker_factor_update_sketched(h.h, C.byref(_tensor(X)),
+                                                  _ranks([a.shape[1] for a in A]), _factors(A),
+                                                  core.data_ptr(), int(n), float(lam), int(m),
+                                                  int(seed), int(sweep)))
+    return A[n]
+
+
+def tucker_set_factor_sketch(h: Handle, m: int) -> None:
+    """m > 0: later ALS sweeps on h sketch their factor updates with m draws each."""
+    lib = L.load()
+    _check(h.h, lib.tucker_set_factor_sketch(h.h, int(m)))
 
 
 BETA_MODE = {"bound": 0, "exact": 1}
