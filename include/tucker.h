@@ -202,6 +202,10 @@ typedef struct {
   int64_t inner_iters;  /* TUCKER_SOLVER_KRON_PCG: CG iterations over all solves of the call;
                            negative when the CG refinement missed its target and the FP32
                            factor solved instead */
+  int gram_prec_used;   /* the Gram precision that solved: `prec`, or TUCKER_PREC_FP32 /
+                           TUCKER_PREC_FP64 when a rounded Gram or an FP32 factor met a
+                           non-positive pivot and the Gram was formed again on the CUDA
+                           cores with an FP64 factor */
 } tucker_stats;
 
 typedef struct tucker_handle tucker_handle;

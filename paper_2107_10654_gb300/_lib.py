@@ -39,7 +39,7 @@ class TuckerStats(C.Structure):
                 ("n_real", C.c_int64), ("refine_iters", C.c_int), ("refine_rel", C.c_double),
                 ("solve_id", C.c_uint64), ("launches", C.c_int64), ("ms_factor", C.c_double),
                 ("ms_gram_kernel", C.c_double), ("ms_inner", C.c_double),
-                ("inner_iters", C.c_int64)]
+                ("inner_iters", C.c_int64), ("gram_prec_used", C.c_int)]
 
 
 class TuckerMissingBetaInfo(C.Structure):

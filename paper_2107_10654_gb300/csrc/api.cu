@@ -376,10 +376,11 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
   b->simt_split = gram_simt_splits(h, F.d, m);
   int sumR = 0;
   for (int n = 0; n < F.N; ++n) sumR += F.R[n];
+  // room for the FP64 CUDA-core Gram as well: the fallback of solve_robust
+  b->gram_bytes = gram_simt_partial_bytes(F.d, b->simt_split, 1);
   if (prec == TUCKER_PREC_TF32 || prec == TUCKER_PREC_BF16)
-    b->gram_bytes = gram_tc_workspace(h, prec, F.d, sumR, m, F.N, F.R[0], F.I[0]);
-  else
-    b->gram_bytes = gram_simt_partial_bytes(F.d, b->simt_split, prec == TUCKER_PREC_FP64);
+    b->gram_bytes = std::max(b->gram_bytes,
+                             gram_tc_workspace(h, prec, F.d, sumR, m, F.N, F.R[0], F.I[0]));
   b->gram_ws = ar.get<char>(b->gram_bytes);
 }
 
@@ -603,6 +604,22 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
   // (the rounded solve is off by about 3e-5 relative; each CG solve stops at 1e-5)
   const int batch =
       (prec == TUCKER_PREC_BF16 || (prec == TUCKER_PREC_TF32 && !h->chol.kpcg)) ? 2 : 1;
+  // A single correction c_1 proves convergence only when the contraction is
+  // known to be small: along a direction that M resolves but the rounded M~
+  // does not (an eigenvalue of M far below M~'s rounding error) both the
+  // residual and the correction are scaled down by lambda_min(M) / lambda_min(M~),
+  // so c_1 is small while the error is not.  The estimate rho ~ u kappa(K^T K),
+  // u the Gram's unit roundoff and kappa from the factor eigenvalues (those of
+  // the Kronecker preconditioner), must be at most 0.1 for c_1 alone to decide
+  // (with rho ~ c_1 as before); otherwise the contraction is measured from two
+  // corrections, and corrections that stop shrinking end the solve unconverged.
+  const bool kev = h->chol.kpcg && h->chol.kron_ready;
+  if (kev)
+    for (int n = 0; n < h->chol.kN; ++n)
+      TK_CUDA(h, cudaMemcpyAsync(h->h_kev + n * TUCKER_MAX_RANK, h->chol.ke[n],
+                                 sizeof(double) * h->chol.kR[n], cudaMemcpyDeviceToHost,
+                                 h->stream));
+  bool trust_first = false;                       // decided at the first wait (copies done)
   double prev = 1.0;
   int checked = 0;
   for (int it = 0; it < max_iters; ++it) {
@@ -631,12 +648,41 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
     const int n = it + 1 - checked;
     TK_CUDA(h, cudaMemcpyAsync(hv, b.rstat + 2 * checked, 2 * n * sizeof(double),
                                cudaMemcpyDeviceToHost, h->stream));
+    TK_CUDA(h, cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                               h->stream));
     TK_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (*h->h_status) return device_status(h);     // e.g. a factor met a non-positive pivot
+    if (checked == 0 && kev) {
+      double emax = 1.0, emin = 1.0;
+      for (int q = 0; q < h->chol.kN; ++q) {
+        double top = 0.0, low = HUGE_VAL;
+        for (int k = 0; k < h->chol.kR[q]; ++k) {
+          top = fmax(top, h->h_kev[q * TUCKER_MAX_RANK + k]);
+          low = fmin(low, h->h_kev[q * TUCKER_MAX_RANK + k]);
+        }
+        emax *= top;
+        emin *= low;
+      }
+      const double u = prec == TUCKER_PREC_BF16 ? 0x1p-8 : prec == TUCKER_PREC_TF32 ? 0x1p-11
+                                                                                   : 0x1p-24;
+      const double kappa = emin > 0.0 ? emax / emin : HUGE_VAL;
+      trust_first = u * kappa <= 0.1;
+      // each CG solve stops at the relative residual ktol, so an error component
+      // whose residual share is below ktol (kappa ktol >= 1) is never corrected,
+      // whatever the corrections show: the caller solves with a factor instead
+      if (kappa * h->chol.ktol > 0.1) {
+        *iters = it + 1;
+        if (converged) *converged = false;
+        return TUCKER_OK;
+      }
+    }
     bool stop = false;
     for (int k = 0; k < n; ++k) {
       const double rk = hv[2 * k + 1] > 0 ? sqrt(hv[2 * k] / hv[2 * k + 1]) : 0.0;
+      const bool first = checked + k == 0;
       const double rho = fmin(rk / prev, 0.5);
-      const bool hit = rk == 0.0 || rk * rho / (1.0 - rho) < target || rk < 1e-10;
+      const bool hit = (!first || trust_first) &&
+                       (rk == 0.0 || rk * rho / (1.0 - rho) < target || rk < 1e-10);
       reached = reached || hit;
       stop = stop || hit || (checked + k > 0 && rk > 0.5 * prev);
       prev = rk;
@@ -646,31 +692,85 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
     *iters = it + 1;
     if (stop) break;
   }
-  // the direct factors stop at their rounding level; the CG solver has to meet
-  // the target, else the caller factors M~ instead
-  if (converged) *converged = reached || !h->chol.kpcg;
+  // every path has to meet the target: a refinement that stalls above it (an
+  // ill-conditioned matrix that the rounded Gram or the FP32 factor cannot
+  // resolve) is reported, and the caller tries a more precise step
+  if (converged) *converged = reached;
   return TUCKER_OK;
 }
 
 // solve_refined, and when the CG solver did not reach the target (a sketch
 // far from the Kronecker Gram), the same solve with the FP32 factor of M~ (the
-// mixed solver), from the FP64 M still held in the cache.
+// mixed solver), from the FP64 M still held in the cache.  A refinement that
+// still misses its target returns ENOTSPD (solve_robust then tries a more
+// precise Gram and factor).
 static tucker_status solve_checked(tucker_handle* h, const FactorSet& F, const RowSet& rs,
                                    int prec, SketchBufs& b, const double* rhs, double* g,
                                    int* iters, double* rel, const RowSet* rs32 = nullptr) {
   bool conv = true;
   TK_TRY(solve_refined(h, F, rs, prec, b, rhs, g, iters, rel, rs32, &conv));
   if (conv) return TUCKER_OK;
-  TK_TRY(factorize(h, h->chol.L, F.d, prec, TUCKER_SOLVER_MIXED));
-  return solve_refined(h, F, rs, prec, b, rhs, g, iters, rel, rs32);
+  if (h->chol.kpcg) {
+    TK_TRY(factorize(h, h->chol.L, F.d, prec, TUCKER_SOLVER_MIXED));
+    TK_TRY(solve_refined(h, F, rs, prec, b, rhs, g, iters, rel, rs32, &conv));
+    if (conv) return TUCKER_OK;
+  }
+  return fail(h, TUCKER_ENOTSPD, "the refinement stalled at %.2e above its target: the Gram or "
+              "its factor is too coarse for this matrix", *rel);
 }
 
-// Factor G + diag(regdiag) (G in the FP64 buffer L) and solve for b.h.
-static tucker_status solve_refine(tucker_handle* h, const FactorSet& F, const RowSet& rs,
-                                  int prec, SketchBufs& b, int* iters, double* rel) {
+// solve_checked, and when a rounded Gram (TF32, BF16) or an FP32 factor met a
+// non-positive pivot (an ill-conditioned Gram with a small lambda: early ALS
+// sweeps from a random start), more precise steps in turn, each with an FP64
+// Cholesky factor (and the FP64 refinement while the Gram is rounded):
+//   TF32 / BF16 Gram: the FP32 and then the FP64 CUDA-core Gram of the same rows;
+//   FP32 Gram:        its FP64 factor (FP32-factor solvers), then the FP64 Gram;
+//   FP64 Gram:        its FP64 factor (FP32-factor solvers).
+// Under the FP32-factor solvers L still holds M, so "its FP64 factor" needs no
+// new Gram.  *used: the Gram precision that solved.
+static tucker_status solve_robust(tucker_handle* h, const FactorSet& F, const RowSet& rs,
+                                  const RowSet& rs64, int prec, SketchBufs& b, int* iters,
+                                  double* rel, const RowSet* rs32, int* used) {
+  *used = prec;
+  tucker_status st = solve_checked(h, F, rs64, prec, b, b.h, b.g, iters, rel, rs32);
+  if (st != TUCKER_ENOTSPD) return st;
+  const bool fp32_factor = h->solver != TUCKER_SOLVER_FP64_CHOLESKY;
+  struct Step { int prec; bool rebuild; } steps[2];
+  int ns = 0;
+  if (prec == TUCKER_PREC_TF32 || prec == TUCKER_PREC_BF16) {
+    steps[ns++] = {TUCKER_PREC_FP32, true};
+    steps[ns++] = {TUCKER_PREC_FP64, true};
+  } else if (prec == TUCKER_PREC_FP32) {
+    if (fp32_factor) steps[ns++] = {TUCKER_PREC_FP32, false};
+    steps[ns++] = {TUCKER_PREC_FP64, true};
+  } else if (fp32_factor) {
+    steps[ns++] = {TUCKER_PREC_FP64, false};
+  }
+  for (int k = 0; k < ns; ++k) {
+    const int lp = steps[k].prec;
+    if (steps[k].rebuild) {
+      TK_TRY(launch_gram_simt(h, rs, lp == TUCKER_PREC_FP64, b.simt_split, b.gram_ws,
+                              h->chol.L));
+      TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
+    }
+    TK_TRY(factorize(h, h->chol.L, F.d, lp, TUCKER_SOLVER_FP64_CHOLESKY));
+    st = solve_checked(h, F, rs64, lp, b, b.h, b.g, iters, rel, nullptr);
+    if (st == TUCKER_OK && lp == TUCKER_PREC_FP64) st = device_status(h);  // no wait inside
+    *used = lp;
+    if (st != TUCKER_ENOTSPD) return st;
+  }
+  return st;
+}
+
+// Factor G + diag(regdiag) (G in the FP64 buffer L) and solve for b.h, with
+// the more precise steps of solve_robust when the first solve fails.
+static tucker_status solve_refine(tucker_handle* h, const FactorSet& F, const RowSet& rs_raw,
+                                  const RowSet& rs, int prec, SketchBufs& b, int* iters,
+                                  double* rel) {
   TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
   TK_TRY(factorize(h, h->chol.L, F.d, prec, h->solver));
-  return solve_checked(h, F, rs, prec, b, b.h, b.g, iters, rel);
+  int used;
+  return solve_robust(h, F, rs_raw, rs, prec, b, iters, rel, nullptr, &used);
 }
 
 }  // namespace tk
@@ -703,6 +803,8 @@ tucker_status tucker_create(tucker_handle** out, void* cuda_stream) {
   if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&h->keep, kAuxDoubles * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&h->h_status, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&h->h_kev, sizeof(double) * TUCKER_MAX_ORDER * TUCKER_MAX_RANK) !=
+          cudaSuccess ||
       cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -729,6 +831,7 @@ tucker_status tucker_destroy(tucker_handle* h) {
   if (h->d_status) cudaFree(h->d_status);
   if (h->keep) cudaFree(h->keep);
   if (h->h_status) cudaFreeHost(h->h_status);
+  if (h->h_kev) cudaFreeHost(h->h_kev);
   for (int i = 0; i < 16; ++i) cudaEventDestroy(h->ev[i]);
   if (h->aux) {
     cudaStreamSynchronize(h->aux);
@@ -1106,7 +1209,8 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
   TK_TRY(launch_add_diag(h, h->chol.L, F.d, h->chol.regdiag));
   TK_TRY(factorize(h, h->chol.L, F.d, prec, h->solver));
   if (beside) TK_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-  TK_TRY(solve_checked(h, F, rs64, prec, b, b.h, b.g, &iters, &rel, &rs));
+  int prec_used = prec;
+  TK_TRY(solve_robust(h, F, rs, rs64, prec, b, &iters, &rel, &rs, &prec_used));
   TK_CUDA(h, cudaMemcpyAsync(core_out, b.g, sizeof(double) * F.d, cudaMemcpyDeviceToDevice,
                              h->stream));
   ev_record(h, timing, 6);
@@ -1133,6 +1237,7 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
     stats->launches = h->launches - launches0;
     stats->ms_factor = ev_ms(h, 8, 9);
     stats->ms_gram_kernel = ev_ms(h, 10, 11);
+    stats->gram_prec_used = prec_used;
     if (h->chol.kres_n > 0) {             // CG solves ran (negative: the factor took over)
       stats->ms_inner = ev_ms(h, 12, 13);
       double kr[2 * kKresSlots];
@@ -1225,7 +1330,7 @@ tucker_status tucker_core_update_exact(tucker_handle* h, const tucker_tensor* X,
   }
   int iters;
   double rel;
-  TK_TRY(solve_refine(h, F, rs64, prec, b, &iters, &rel));
+  TK_TRY(solve_refine(h, F, rs, rs64, prec, b, &iters, &rel));
   TK_CUDA(h, cudaMemcpyAsync(core_out, b.g, sizeof(double) * F.d, cudaMemcpyDeviceToDevice,
                              h->stream));
   return finish(h);

@@ -73,6 +73,7 @@ struct tucker_handle {
   size_t ws_cap = 0;
   int* d_status = nullptr;      // device status word
   int* h_status = nullptr;      // pinned host copy
+  double* h_kev = nullptr;      // pinned: the factor eigenvalues the refinement's first check reads
   double* keep = nullptr;       // kAuxDoubles of device scratch that outlives the workspace
   tk::HashTable hash;
   tk::CholCache chol;

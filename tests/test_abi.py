@@ -38,7 +38,7 @@ def test_struct_layouts_match_c():
     # tucker_tensor: int, pad, int64[8], int, pad, ptr, int64, ptr, ptr
     assert ctypes.sizeof(_lib.TuckerTensor) == 8 + 64 + 8 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(_lib.TuckerSamples) == 6 * 8
-    assert ctypes.sizeof(_lib.TuckerStats) == 7 * 8 + 3 * 8 + 8 + 8 + 8 + 8 + 2 * 8 + 2 * 8
+    assert ctypes.sizeof(_lib.TuckerStats) == 7 * 8 + 3 * 8 + 8 + 8 + 8 + 8 + 2 * 8 + 2 * 8 + 8
     # tucker_missing_beta_info: seven doubles, two ints
     assert ctypes.sizeof(_lib.TuckerMissingBetaInfo) == 7 * 8 + 2 * 4
 

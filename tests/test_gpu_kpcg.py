@@ -125,3 +125,32 @@ def test_kpcg_bench_workload(kpcg):
     ref = CU.sketched_core(X, F, w.lam, w.m, w.seed_sample, 0, S.REG_EXACT)
     assert st["inner_iters"] > 0
     assert rel_err(g.cpu().numpy(), ref["g"]) <= 1e-6
+
+
+@pytest.mark.parametrize("solver", ["kpcg", "mixed", "fp64"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_rounded_gram_not_spd_falls_back_to_cuda_core_grams(solver, prec):
+    # a nearly repeated column and lambda = 0: the tensor-core Gram of rounded rows is
+    # PSD except for its FP32 accumulation (about 2^-24 ||G|| ~ 2.6e-3 here), which
+    # exceeds the smallest eigenvalue (about 2.7e-5), so the rounded matrix has no
+    # Cholesky factor, or its refinement stalls; the update rebuilds the Gram of the same
+    # rows on the CUDA cores (FP32, then FP64) with an FP64 factor and still meets the
+    # oracle (kappa ~ 1.6e9)
+    rng = np.random.default_rng(31)
+    dims, ranks, lam = (30, 25, 20), (3, 2, 2), 0.0
+    F = [rng.standard_normal((i, r)) for i, r in zip(dims, ranks)]
+    F[0][:, 2] = F[0][:, 0] + 1e-4 * rng.standard_normal(dims[0])
+    X = rng.standard_normal(dims)
+    levs = [LV.leverage_scores(a)[0] for a in F]
+    with T.Handle(solver=solver) as h:
+        smp = T.tucker_sample_rows(h, dims, ranks, [dev(l) for l in levs], 6000, 3, 0)
+        g, st = T.tucker_core_update_sketched(h, dev(X), [dev(a) for a in F], lam, 0, 0, 0,
+                                              "exact", prec, fixed=smp, stats=True)
+        torch.cuda.synchronize()
+    ref = CU.sketched_core(X, F, lam, 6000, 3, 0, S.REG_EXACT)
+    assert smp.n_unique == ref["keys"].size
+    if solver != "kpcg":
+        # a factor of the rounded matrix fails or its refinement stalls: CUDA-core Grams
+        assert st["gram_prec_used"] in (T.PREC["fp32"], T.PREC["fp64"]), st["gram_prec_used"]
+    # (CG with the FP64 correction may still reach the target on the rounded Gram)
+    assert rel_err(g.cpu().numpy(), ref["g"]) <= 1e-6
