@@ -227,6 +227,9 @@ struct FiberArgs {
   int64_t m;                               // draws
   double lambda;
   int splits;                              // CTAs along the sample in the normal kernel
+  int postn;                               // prod_{k > n} R_k
+  FastDiv div_r[TUCKER_MAX_ORDER];         // by R_k
+  FastDiv div_post;                        // by postn
   void* xs;                                // [cap][I_n] fibers
   double* wb;                              // [cap][R_n]  w_u b_u (FP64)
   double* bb;                              // [cap][R_n]  b_u (FP64)
@@ -238,16 +241,19 @@ struct FiberArgs {
 
 constexpr int FB_WARPS = 8;
 
-// Warp per distinct row: decode, weight, design row b_u (lanes over the core
-// entries of each r_n, warp sums in a fixed order) and the fiber (lanes over i_n).
-template <typename T>
+// Warp per distinct row: decode, weight, design row b_u and the fiber.  For b_u
+// the lanes walk the core index o over the modes k != n (o = (pre, post) around
+// mode n, row-major), form w_o = prod_{k != n} a_k[r_k(o)] once (multiply-high
+// divisions by R_k) and add G[pre, r, post] w_o into R_n accumulators (RB >= R_n,
+// registers); R_n warp sums in a fixed order.  The fiber: lanes over i_n, eight
+// loads in flight.
+template <typename T, int RB>
 __global__ void __launch_bounds__(FB_WARPS * 32) k_fiber_rows(FiberArgs a) {
   __shared__ double arow[FB_WARPS][TUCKER_MAX_ORDER * TUCKER_MAX_RANK];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nu = *a.nu, N = a.N, n = a.n, Rn = a.R[n];
-  const int dn = a.d / Rn;                  // entries of the core per r_n
-  int postn = 1;
-  for (int k = n + 1; k < N; ++k) postn *= a.R[k];
+  const int dn = a.d / Rn;                  // core entries per r_n
+  const int postn = a.postn;
   double* ar = arow[wid];
   for (int64_t u = (int64_t)blockIdx.x * FB_WARPS + wid; u < nu;
        u += (int64_t)gridDim.x * FB_WARPS) {
@@ -280,31 +286,50 @@ __global__ void __launch_bounds__(FB_WARPS * 32) k_fiber_rows(FiberArgs a) {
         ar[k * TUCKER_MAX_RANK + r] = load_as_double(a.A[k], j[k] * a.R[k] + r, a.is64);
     }
     __syncwarp();
-    // b_u[r] = sum over the other core indices o of G[.., r, ..] prod_{k != n} a_k[r_k]
-    for (int r = 0; r < Rn; ++r) {
-      double acc = 0.0;
-      for (int o = lane; o < dn; o += 32) {
-        const int pre = o / postn, post = o - pre * postn;
-        const int e = (pre * Rn + r) * postn + post;      // core index
-        double f = a.core[e];
-        int rem = e;
-        for (int k = N - 1; k >= 0; --k) {
-          const int rk = rem % a.R[k];
-          rem /= a.R[k];
-          if (k != n) f *= ar[k * TUCKER_MAX_RANK + rk];
-        }
-        acc += f;
+    double acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] = 0.0;
+    for (int o = lane; o < dn; o += 32) {
+      uint32_t rem = (uint32_t)o;
+      double wv = 1.0;
+      for (int k = N - 1; k >= 0; --k) {
+        if (k == n) continue;
+        const uint32_t qk = fdiv(rem, a.div_r[k]);
+        wv *= ar[k * TUCKER_MAX_RANK + (rem - qk * (uint32_t)a.R[k])];
+        rem = qk;
       }
-      acc = warp_sum(acc);
-      if (lane == 0) {
-        a.bb[u * Rn + r] = acc;
-        a.wb[u * Rn + r] = w * acc;
+      const uint32_t pre = fdiv((uint32_t)o, a.div_post);
+      const double* gp = a.core + (size_t)pre * Rn * postn + (o - pre * postn);
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        if (r < Rn) acc[r] = fma(gp[(size_t)r * postn], wv, acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      if (r < Rn) {
+        const double b = warp_sum(acc[r]);
+        if (lane == 0) {
+          a.bb[u * Rn + r] = b;
+          a.wb[u * Rn + r] = w * b;
+        }
       }
     }
-    // the fiber x_u[i] = X[base + i stride_n]
+    // the fiber x_u[i] = X[base + i stride_n], eight loads per lane in flight
     T* xs = static_cast<T*>(a.xs) + u * a.I[n];
-    for (int64_t i = lane; i < a.I[n]; i += 32)
-      xs[i] = (T)load_as_double(a.X, base + i * a.stride[n], a.is64);
+    const int64_t In = a.I[n], sn = a.stride[n];
+    for (int64_t i0 = lane; i0 < In; i0 += 32 * 8) {
+      T v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int64_t i = i0 + 32 * q;
+        v[q] = i < In ? (a.is64 ? (T)static_cast<const double*>(a.X)[base + i * sn]
+                                : (T)static_cast<const float*>(a.X)[base + i * sn])
+                      : (T)0;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (i0 + 32 * q < In) xs[i0 + 32 * q] = v[q];
+    }
     __syncwarp();
   }
 }
@@ -315,8 +340,10 @@ __global__ void __launch_bounds__(FB_WARPS * 32) k_fiber_rows(FiberArgs a) {
 // keeps the accumulators in registers.
 template <typename T, int RB>
 __global__ void __launch_bounds__(128) k_fiber_normal(FiberArgs a) {
-  extern __shared__ unsigned char fsm[];
-  T* wbs = reinterpret_cast<T*>(fsm);               // [64][Rn] staged rows of wb
+  extern __shared__ double fsm[];
+  double* wbd = fsm;                                // [64][Rn] staged rows of wb (FP64)
+  double* bbd = wbd + 64 * a.R[a.n];                // [64][Rn] staged rows of b (row block 0)
+  T* wbs = reinterpret_cast<T*>(bbd + 64 * a.R[a.n]);   // [64][Rn] wb in T
   const int nu = *a.nu, Rn = a.R[a.n];
   const int64_t In = a.I[a.n];
   const int s = blockIdx.y;
@@ -328,17 +355,37 @@ __global__ void __launch_bounds__(128) k_fiber_normal(FiberArgs a) {
   for (int r = 0; r < RB; ++r) acc[r] = (T)0;
   const T* xs = static_cast<const T*>(a.xs);
   const double* wb = a.wb;
+  const bool mblock = blockIdx.x == 0;              // this CTA also forms M_s
+  const int e0 = threadIdx.x, r0 = e0 / max(Rn, 1), c0 = e0 - r0 * Rn;
+  const bool mthread = mblock && e0 < Rn * Rn;
+  double m4[4] = {0.0, 0.0, 0.0, 0.0};             // four chains: FP64 FMA latency
   for (int64_t ub = u0; ub < u1; ub += 64) {
     const int nb = (int)min((int64_t)64, u1 - ub);
     __syncthreads();
-    for (int e = threadIdx.x; e < nb * Rn; e += 128) wbs[e] = (T)wb[ub * Rn + e];
+    for (int e = threadIdx.x; e < nb * Rn; e += 128) {
+      const double v = wb[ub * Rn + e];
+      wbs[e] = (T)v;
+      if (mblock) {
+        wbd[e] = v;
+        bbd[e] = a.bb[ub * Rn + e];
+      }
+    }
     __syncthreads();
+    if (mthread)
+      for (int q = 0; q < nb; ++q) m4[q & 3] = fma(wbd[q * Rn + r0], bbd[q * Rn + c0], m4[q & 3]);
     if (i < In) {
-      for (int q = 0; q < nb; ++q) {
-        const T x = xs[(ub + q) * In + i];
+      for (int q0 = 0; q0 < nb; q0 += 16) {        // sixteen fiber loads in flight
+        T xv[16];
 #pragma unroll
-        for (int r = 0; r < RB; ++r)
-          if (r < Rn) acc[r] = fma(x, wbs[q * Rn + r], acc[r]);
+        for (int j = 0; j < 16; ++j)
+          xv[j] = q0 + j < nb ? xs[(ub + q0 + j) * In + i] : (T)0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int q = q0 + j < nb ? q0 + j : q0;  // a zero x adds nothing
+#pragma unroll
+          for (int r = 0; r < RB; ++r)
+            if (r < Rn) acc[r] = fma(xv[j], wbs[q * Rn + r], acc[r]);
+        }
       }
     }
   }
@@ -347,46 +394,68 @@ __global__ void __launch_bounds__(128) k_fiber_normal(FiberArgs a) {
     for (int r = 0; r < RB; ++r)
       if (r < Rn) a.partY[((int64_t)s * In + i) * Rn + r] = (double)acc[r];
   }
-  if (blockIdx.x == 0) {
-    const double* bb = a.bb;
+  if (mblock)                                        // R_n^2 <= 128 here (else below)
     for (int e = threadIdx.x; e < Rn * Rn; e += 128) {
-      const int r = e / Rn, c = e % Rn;
-      double mv = 0.0;
-      for (int64_t u = u0; u < u1; ++u) mv = fma(wb[u * Rn + r], bb[u * Rn + c], mv);
-      a.partM[(int64_t)s * Rn * Rn + e] = mv;
+      if (e == e0 && mthread) {
+        a.partM[(int64_t)s * Rn * Rn + e] = (m4[0] + m4[1]) + (m4[2] + m4[3]);
+        continue;
+      }
+      const int r = e / Rn, c = e % Rn;             // R_n > 11: the rest, from global memory
+      double v = 0.0;
+      for (int64_t u = u0; u < u1; ++u) v = fma(wb[u * Rn + r], a.bb[u * Rn + c], v);
+      a.partM[(int64_t)s * Rn * Rn + e] = v;
     }
-  }
 }
 
 // A^(n) = Y M^-1: every CTA sums the M partials (fixed order), adds lambda I,
-// factors and inverts it (spd_inverse), then forms its 64 rows of Y from the
-// partials and applies the inverse.
+// factors and inverts it (spd_inverse), then forms its FIN_ROWS rows of Y from
+// the partials and applies the inverse.
+constexpr int FIN_ROWS = 16;
 __global__ void __launch_bounds__(256) k_fiber_finish(FiberArgs a) {
   extern __shared__ double fin[];
   const int Rn = a.R[a.n];
   double* Lm = fin;                                  // Rn x Rn
   double* Mi = Lm + Rn * Rn;                         // Rn x Rn
-  double* Ys = Mi + Rn * Rn;                         // 64 x Rn
+  double* Ys = Mi + Rn * Rn;                         // FIN_ROWS x Rn
   const int64_t In = a.I[a.n];
   for (int e = threadIdx.x; e < Rn * Rn; e += blockDim.x) {
-    double v = 0.0;
-    for (int s = 0; s < a.splits; ++s) v += a.partM[(int64_t)s * Rn * Rn + e];
     const int r = e / Rn, c = e % Rn;
-    // the symmetric part, so that both triangles carry the same value
-    double vt = 0.0;
-    for (int s = 0; s < a.splits; ++s) vt += a.partM[(int64_t)s * Rn * Rn + c * Rn + r];
+    // the symmetric part, so that both triangles carry the same value; sixteen
+    // loads of each in flight, added in order
+    double v = 0.0, vt = 0.0;
+    for (int s0 = 0; s0 < a.splits; s0 += 16) {
+      double t[16], tt[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const bool ok = s0 + q < a.splits;
+        t[q] = ok ? a.partM[(int64_t)(s0 + q) * Rn * Rn + e] : 0.0;
+        tt[q] = ok ? a.partM[(int64_t)(s0 + q) * Rn * Rn + c * Rn + r] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        v += t[q];
+        vt += tt[q];
+      }
+    }
     Lm[e] = 0.5 * (v + vt) + (r == c ? a.lambda : 0.0);
   }
   __syncthreads();
   spd_inverse(Lm, Rn, Mi, a.status);
   __syncthreads();
-  const int64_t i0 = (int64_t)blockIdx.x * 64;
-  const int rows = (int)min((int64_t)64, In - i0);
+  const int64_t i0 = (int64_t)blockIdx.x * FIN_ROWS;
+  const int rows = (int)min((int64_t)FIN_ROWS, In - i0);
   for (int e = threadIdx.x; e < rows * Rn; e += blockDim.x) {
     const int64_t i = i0 + e / Rn;
     const int r = e % Rn;
     double v = 0.0;
-    for (int s = 0; s < a.splits; ++s) v += a.partY[((int64_t)s * In + i) * Rn + r];
+    for (int s0 = 0; s0 < a.splits; s0 += 16) {     // sixteen loads in flight, added in order
+      double t[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        t[q] = s0 + q < a.splits ? a.partY[((int64_t)(s0 + q) * In + i) * Rn + r] : 0.0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v += t[q];
+    }
     Ys[e] = v;
   }
   __syncthreads();
@@ -443,6 +512,10 @@ tucker_status launch_fiber_update(tucker_handle* h, const FactorSet& F, int n, c
   a.m = m;
   a.lambda = lambda;
   a.splits = splits;
+  a.postn = 1;
+  for (int k = n + 1; k < F.N; ++k) a.postn *= F.R[k];
+  for (int k = 0; k < F.N; ++k) a.div_r[k] = make_fastdiv((uint32_t)F.R[k]);
+  a.div_post = make_fastdiv((uint32_t)a.postn);
   char* q = ws;
   auto take = [&](size_t bytes) { char* r = q; q += (bytes + 255) & ~size_t(255); return r; };
   a.xs = take((size_t)cap * F.I[n] * es);
@@ -454,11 +527,20 @@ tucker_status launch_fiber_update(tucker_handle* h, const FactorSet& F, int n, c
   a.status = h->d_status;
   const int g1 = (int)std::min<int64_t>(ceil_div(cap, FB_WARPS), (int64_t)h->num_sms * 16);
   TK_COUNT(h);
-  if (F.is64) k_fiber_rows<double><<<std::max(g1, 1), FB_WARPS * 32, 0, h->stream>>>(a);
-  else k_fiber_rows<float><<<std::max(g1, 1), FB_WARPS * 32, 0, h->stream>>>(a);
+#define TK_FIBER_ROWS(RB)                                                                  \
+  do {                                                                                     \
+    if (F.is64) k_fiber_rows<double, RB><<<std::max(g1, 1), FB_WARPS * 32, 0, h->stream>>>(a); \
+    else k_fiber_rows<float, RB><<<std::max(g1, 1), FB_WARPS * 32, 0, h->stream>>>(a);          \
+  } while (0)
+  if (Rn <= 4) TK_FIBER_ROWS(4);
+  else if (Rn <= 8) TK_FIBER_ROWS(8);
+  else if (Rn <= 16) TK_FIBER_ROWS(16);
+  else if (Rn <= 32) TK_FIBER_ROWS(32);
+  else TK_FIBER_ROWS(64);
+#undef TK_FIBER_ROWS
   TK_LAUNCH(h);
   const dim3 g2((unsigned)ceil_div(F.I[n], 128), (unsigned)splits);
-  const size_t sm2 = (size_t)64 * Rn * es;
+  const size_t sm2 = (size_t)64 * Rn * (16 + es);
   TK_COUNT(h);
 #define TK_FIBER_NORMAL(RB)                                                        \
   do {                                                                             \
@@ -472,11 +554,11 @@ tucker_status launch_fiber_update(tucker_handle* h, const FactorSet& F, int n, c
   else TK_FIBER_NORMAL(64);
 #undef TK_FIBER_NORMAL
   TK_LAUNCH(h);
-  const size_t sm3 = (size_t)(2 * Rn * Rn + 64 * Rn) * sizeof(double);
+  const size_t sm3 = (size_t)(2 * Rn * Rn + FIN_ROWS * Rn) * sizeof(double);
   TK_CUDA(h, cudaFuncSetAttribute(k_fiber_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm3));
   TK_COUNT(h);
-  k_fiber_finish<<<(unsigned)ceil_div(F.I[n], 64), 256, sm3, h->stream>>>(a);
+  k_fiber_finish<<<(unsigned)ceil_div(F.I[n], FIN_ROWS), 256, sm3, h->stream>>>(a);
   TK_LAUNCH(h);
   return TUCKER_OK;
 }

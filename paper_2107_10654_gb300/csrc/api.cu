@@ -458,6 +458,16 @@ static bool kpcg_wanted(tucker_handle* h, const FactorSet& F, int prec) {
 
 // Eigendecompositions A^(n)T A^(n) = V_n diag(ev_n) V_n^T of the factor Grams
 // (written by the leverage launcher) into the cache, for the CG preconditioner.
+// The eigenvalues ev_n to the pinned host buffer h_kev, on the current stream
+// (the refinement's first check of the contraction reads them).
+static tucker_status kron_ev_to_host(tucker_handle* h) {
+  const CholCache& c = h->chol;
+  for (int n = 0; n < c.kN; ++n)
+    TK_CUDA(h, cudaMemcpyAsync(h->h_kev + n * TUCKER_MAX_RANK, c.ke[n], sizeof(double) * c.kR[n],
+                               cudaMemcpyDeviceToHost, h->stream));
+  return TUCKER_OK;
+}
+
 static tucker_status kron_prepare(tucker_handle* h, const FactorSet& F,
                                   const double* const* fgram) {
   CholCache& c = h->chol;
@@ -465,7 +475,7 @@ static tucker_status kron_prepare(tucker_handle* h, const FactorSet& F,
   c.kN = F.N;
   for (int n = 0; n < F.N; ++n) c.kR[n] = F.R[n];
   c.kron_ready = 1;
-  return TUCKER_OK;
+  return kron_ev_to_host(h);
 }
 
 // Relative residual of each CG solve: below the rounding of the Gram it
@@ -613,13 +623,10 @@ static tucker_status solve_refined(tucker_handle* h, const FactorSet& F, const R
   // the Kronecker preconditioner), must be at most 0.1 for c_1 alone to decide
   // (with rho ~ c_1 as before); otherwise the contraction is measured from two
   // corrections, and corrections that stop shrinking end the solve unconverged.
+  // (h_kev was filled by kron_ev_to_host behind the eigendecompositions, on a
+  // stream the solve has joined, so the first host wait below also covers it)
   const bool kev = h->chol.kpcg && h->chol.kron_ready;
-  if (kev)
-    for (int n = 0; n < h->chol.kN; ++n)
-      TK_CUDA(h, cudaMemcpyAsync(h->h_kev + n * TUCKER_MAX_RANK, h->chol.ke[n],
-                                 sizeof(double) * h->chol.kR[n], cudaMemcpyDeviceToHost,
-                                 h->stream));
-  bool trust_first = false;                       // decided at the first wait (copies done)
+  bool trust_first = false;                       // decided at the first wait
   double prev = 1.0;
   int checked = 0;
   for (int it = 0; it < max_iters; ++it) {
@@ -1106,6 +1113,7 @@ tucker_status tucker_core_update_sketched(tucker_handle* h, const tucker_tensor*
       h->chol.kN = F.N;
       for (int n = 0; n < F.N; ++n) h->chol.kR[n] = F.R[n];
       h->chol.kron_ready = 1;
+      TK_TRY(kron_ev_to_host(h));
     }
     ev_record(h, timing, 1);
     RidgeState rst;

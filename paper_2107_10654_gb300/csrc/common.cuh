@@ -286,6 +286,27 @@ __device__ __forceinline__ double hash_value(const uint64_t* slot_key, const uin
 
 // --------------------------------------------------- cross-file launchers
 
+// Division by a small positive integer q as a multiply-high and a shift
+// (Granlund and Montgomery, PLDI 1994): for x < 2^16, x / q = (umulhi(x, mul) + x) >> shift
+// with shift = ceil(log2 q) and mul = floor(2^32 (2^shift - q) / q) + 1.
+struct FastDiv {
+  uint32_t q, mul, shift;
+};
+
+static inline FastDiv make_fastdiv(uint32_t q) {
+  FastDiv f;
+  f.q = q;
+  uint32_t sh = 0;
+  while ((1u << sh) < q) ++sh;
+  f.shift = sh;
+  f.mul = (uint32_t)((((uint64_t)1 << 32) * (((uint64_t)1 << sh) - q)) / q + 1);
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
+  return (__umulhi(x, f.mul) + x) >> f.shift;
+}
+
 struct FactorSet {
   int N;
   int64_t I[TUCKER_MAX_ORDER];
