@@ -76,8 +76,12 @@ tucker_status launch_refine_update(tucker_handle* h, double* g, const double* r,
 tucker_status launch_add_diag(tucker_handle* h, double* M, int d, const double* diag);
 tucker_status ttm_chain_all(tucker_handle* h, const FactorSet& F, const void* X, double* buf0,
                             double* buf1, double* y);
+tucker_status ttm_last(tucker_handle* h, const void* X, int is64, int64_t P, int I, const void* A,
+                       int R, double* out, double* sq_partial = nullptr, int sq_cap = 0,
+                       double* sq_out = nullptr);
 tucker_status ttm_chain_except(tucker_handle* h, const FactorSet& F, const void* X, int n,
-                               double* buf0, double* buf1, double* out);
+                               double* buf0, double* buf1, double* out,
+                               const double* ylast = nullptr);
 size_t fiber_workspace_bytes(const FactorSet& F, int n, int64_t cap, int splits);
 int fiber_splits(int64_t cap);
 tucker_status launch_fiber_update(tucker_handle* h, const FactorSet& F, int n, const void* X,
@@ -1661,9 +1665,11 @@ tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const i
   }
   const int np = h->num_sms * 8;
   double* Ls = nullptr;                           // the R_n x R_n factor of a factor update
+  double* Ylast = nullptr;                        // X x_N A^(N)T, shared by modes 1..N-1
   auto carve = [&](Arena& ar, double** lev, uint64_t** cdf, double** gram, int** rk, double** b0,
                    double** b1, double** B, double** part, double** res) {
     Ls = ar.get<double>(TUCKER_MAX_RANK * TUCKER_MAX_RANK);
+    Ylast = N >= 3 ? ar.get<double>(inter) : nullptr;
     for (int n = 0; n < N; ++n) {
       lev[n] = ar.get<double>(F.I[n]);
       cdf[n] = ar.get<uint64_t>(F.I[n]);
@@ -1689,6 +1695,8 @@ tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const i
   TK_TRY(ws_reserve(h, sz.off + fsb + 256));
   Arena ar(h->ws);
   carve(ar, lev, cdf, gram, &rk, &b0, &b1, &B, &part, &res);
+  const bool want_loss = loss_out_host || rmse_out_host;
+  bool xx_done = false;                           // ||X||^2 formed with the shared product
   for (int n = 0; n < N; ++n) {
     if (mf > 0) {
       Arena fa(h->ws + ((ar.off + 255) & ~size_t(255)));
@@ -1697,17 +1705,27 @@ tucker_status tucker_als_sweep(tucker_handle* h, const tucker_tensor* X, const i
       continue;
     }
     TK_TRY(launch_factor_grams(h, F, rk, gram));
-    TK_TRY(ttm_chain_except(h, F, X->dense, n, b0, b1, B));
+    // the chains of modes 1..N-1 start with X x_N A^(N)T, and A^(N) changes only
+    // in the last update: one pass over X serves them all (N >= 3)
+    const bool shared = Ylast && n < N - 1;
+    if (shared && n == 0) {                       // with ||X||^2 for the loss, same pass
+      int64_t P = 1;
+      for (int k = 0; k < N - 1; ++k) P *= F.I[k];
+      TK_TRY(ttm_last(h, X->dense, F.is64, P, (int)F.I[N - 1], F.A[N - 1], F.R[N - 1], Ylast,
+                      want_loss ? part : nullptr, np, h->keep + F.d));
+      xx_done = want_loss;
+    }
+    TK_TRY(ttm_chain_except(h, F, X->dense, n, b0, b1, B, shared ? Ylast : nullptr));
     TK_TRY(factor_solve(h, F, n, gram, core_inout, B, lambda, A_inout[n], Ls));
   }
   // the loss by the Gram identity needs y = K^T vec(X) for the new factors: the last
   // product chain B = X x_{k<N} A^(k)T (formed here when the factor updates were
   // sketched), times the new A^(N); and ||X||^2 (one pass)
-  const bool want_loss = loss_out_host || rmse_out_host;
   if (want_loss) {
     if (mf > 0) TK_TRY(ttm_chain_except(h, F, X->dense, N - 1, b0, b1, B));
     TK_TRY(kt_x_from_last(h, F, B, h->keep));
-    TK_TRY(tensor_sumsq(h, X->dense, F.is64, (int64_t)F.total, part, np, h->keep + F.d));
+    if (!xx_done)
+      TK_TRY(tensor_sumsq(h, X->dense, F.is64, (int64_t)F.total, part, np, h->keep + F.d));
   }
   TK_TRY(device_status(h));
   tucker_status st;

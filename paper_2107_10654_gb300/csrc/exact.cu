@@ -48,10 +48,33 @@ __device__ __forceinline__ T transpose_reduce(T (&v)[RP], int lane) {
 // order as a warp working on that row alone.
 template <int RP> struct RowBlock { static constexpr int RB = RP <= 8 ? 4 : RP <= 16 ? 2 : 1; };
 
-// acc[r][j] = lane's partial of sum_i rows[r][i] At[j][i], r < nr.
-template <class T, int RP, int RB>
+// Sum of squares of the elements read, with the arithmetic of k_tensor_sumsq:
+// FP64 FMAs for FP64 data; for FP32 data error-free products p + e = x^2
+// (e = fma(x, x, -p)) added with Neumaier's compensation.
+template <class T> struct SqAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T v) { s = fma((double)v, (double)v, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct SqAcc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float p = v * v;
+    const float e = fmaf(v, v, -p);
+    const float t = s + p;
+    c += (fabsf(s) >= fabsf(p)) ? ((s - t) + p) : ((p - t) + s);
+    c += e;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// acc[r][j] = lane's partial of sum_i rows[r][i] At[j][i], r < nr; with SQ also
+// the squares of the row elements into sq.
+template <class T, int RP, int RB, bool SQ = false>
 __device__ __forceinline__ void rows_contract(const T* const* rows, int nr, int I, const T* At,
-                                              bool vec, int lane, T (&acc)[RB][RP]) {
+                                              bool vec, int lane, T (&acc)[RB][RP],
+                                              SqAcc<T>* sq = nullptr) {
   constexpr int VEC = 16 / sizeof(T);
 #pragma unroll
   for (int r = 0; r < RB; ++r)
@@ -63,6 +86,13 @@ __device__ __forceinline__ void rows_contract(const T* const* rows, int nr, int 
 #pragma unroll
       for (int r = 0; r < RB; ++r)
         if (r < nr) *reinterpret_cast<uint4*>(xv[r]) = __ldg(reinterpret_cast<const uint4*>(rows[r] + i0));
+      if (SQ) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+          if (r < nr)
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) sq->add(xv[r][q]);
+      }
 #pragma unroll
       for (int j = 0; j < RP; ++j) {
         T av[VEC];
@@ -78,6 +108,11 @@ __device__ __forceinline__ void rows_contract(const T* const* rows, int nr, int 
       T x[RB];
 #pragma unroll
       for (int r = 0; r < RB; ++r) x[r] = r < nr ? rows[r][i] : T(0);
+      if (SQ) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+          if (r < nr) sq->add(x[r]);
+      }
 #pragma unroll
       for (int j = 0; j < RP; ++j) {
         const T a = At[j * I + i];
@@ -92,9 +127,12 @@ __device__ __forceinline__ void rows_contract(const T* const* rows, int nr, int 
 // One warp per RB consecutive rows; A^T in shared memory ([r][i],
 // conflict-free); 16-byte loads of X when the row length allows; R <= RP
 // accumulators per row and lane.
-template <class T, int RP>
+// With SQ every CTA also writes the sum of squares of the rows it read to
+// sq_partial[blockIdx.x] (rows are assigned to warps in a fixed pattern, so the
+// partials and their fixed-order sum are reproducible).
+template <class T, int RP, bool SQ>
 __global__ void __launch_bounds__(256) k_ttm_last(const T* X, int64_t P, int I, const T* A, int R,
-                                                  double* out) {
+                                                  double* out, double* sq_partial) {
   constexpr int RB = RowBlock<RP>::RB;
   extern __shared__ unsigned char smraw[];
   T* At = reinterpret_cast<T*>(smraw);               // RP x I (zero rows beyond R)
@@ -108,13 +146,14 @@ __global__ void __launch_bounds__(256) k_ttm_last(const T* X, int64_t P, int I, 
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const bool vec = (I % VEC) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  SqAcc<T> sq;
   for (int64_t p0 = warp * RB; p0 < P; p0 += nwarps * RB) {
     const int nr = (int)(P - p0 < RB ? P - p0 : RB);
     const T* rows[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) rows[r] = X + (p0 + (r < nr ? r : 0)) * I;
     T acc[RB][RP];
-    rows_contract<T, RP, RB>(rows, nr, I, At, vec, lane, acc);
+    rows_contract<T, RP, RB, SQ>(rows, nr, I, At, vec, lane, acc, &sq);
     constexpr int G = 32 / RP;
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
@@ -124,6 +163,17 @@ __global__ void __launch_bounds__(256) k_ttm_last(const T* X, int64_t P, int I, 
         const int c = lane / G;
         if (c < R) out[(p0 + r) * R + c] = (double)tot;
       }
+    }
+  }
+  if (SQ) {
+    __shared__ double red[8];
+    const double v = warp_sum(sq.value());
+    if (lane == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      sq_partial[blockIdx.x] = t;
     }
   }
 }
@@ -644,12 +694,15 @@ static int grid_for(tucker_handle* h, int64_t work, int per = 256) {
 // Contract the last mode of the dense X: out = X_(as P x I_N) A^(N)  (FP64 out)
 template <class T>
 static tucker_status ttm_last_t(tucker_handle* h, const T* X, int64_t P, int I, const T* A, int R,
-                                double* out) {
+                                double* out, double* sq_partial, int sq_cap, double* sq_out) {
   const int RP = R <= 4 ? 4 : R <= 8 ? 8 : R <= 16 ? 16 : 32;
   const size_t smem = (size_t)RP * I * sizeof(T);
   if (smem > 200 * 1024) return fail(h, TUCKER_ENOTSUP, "I_N * R_N too large for the TTM kernel");
-  auto k = RP == 4 ? k_ttm_last<T, 4> : RP == 8 ? k_ttm_last<T, 8>
-         : RP == 16 ? k_ttm_last<T, 16> : k_ttm_last<T, 32>;
+  const bool sq = sq_partial != nullptr;
+  auto k = sq ? (RP == 4 ? k_ttm_last<T, 4, true> : RP == 8 ? k_ttm_last<T, 8, true>
+                 : RP == 16 ? k_ttm_last<T, 16, true> : k_ttm_last<T, 32, true>)
+              : (RP == 4 ? k_ttm_last<T, 4, false> : RP == 8 ? k_ttm_last<T, 8, false>
+                 : RP == 16 ? k_ttm_last<T, 16, false> : k_ttm_last<T, 32, false>);
   TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   TK_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
@@ -657,17 +710,29 @@ static tucker_status ttm_last_t(tucker_handle* h, const T* X, int64_t P, int I, 
   const int64_t need = (P + 31) / 32;                 // 8 warps x 4 rows per CTA
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
+  if (sq && grid > sq_cap) return fail(h, TUCKER_EINTERNAL, "square-sum partials too few");
   TK_COUNT(h);
-  k<<<(int)grid, 256, smem, h->stream>>>(X, P, I, A, R, out);
+  k<<<(int)grid, 256, smem, h->stream>>>(X, P, I, A, R, out, sq_partial);
   TK_LAUNCH(h);
+  if (sq) {
+    TK_COUNT(h);
+    k_sum_partials<<<1, 1024, 0, h->stream>>>(sq_partial, (int)grid, sq_out);
+    TK_LAUNCH(h);
+  }
   return TUCKER_OK;
 }
 
+// sq_partial (nullable, sq_cap doubles): also ||X||^2 into *sq_out, from the
+// same pass over X.
 tucker_status ttm_last(tucker_handle* h, const void* X, int is64, int64_t P, int I, const void* A,
-                       int R, double* out) {
+                       int R, double* out, double* sq_partial = nullptr, int sq_cap = 0,
+                       double* sq_out = nullptr) {
   if (R > 32) return fail(h, TUCKER_ENOTSUP, "R_N > 32 in the TTM kernel");
-  if (is64) return ttm_last_t<double>(h, (const double*)X, P, I, (const double*)A, R, out);
-  return ttm_last_t<float>(h, (const float*)X, P, I, (const float*)A, R, out);
+  if (is64)
+    return ttm_last_t<double>(h, (const double*)X, P, I, (const double*)A, R, out, sq_partial,
+                              sq_cap, sq_out);
+  return ttm_last_t<float>(h, (const float*)X, P, I, (const float*)A, R, out, sq_partial, sq_cap,
+                           sq_out);
 }
 
 tucker_status ttm_mid(tucker_handle* h, const void* X, int is64, int64_t pre, int I, int64_t post,
@@ -801,8 +866,11 @@ tucker_status ttm_chain_all(tucker_handle* h, const FactorSet& F, const void* X,
 }
 
 // B = X x_{k != n} A^(k)T, laid out (prod_{k<n} R_k, I_n, prod_{k>n} R_k) in `out`.
+// ylast: NULL, or X x_N A^(N)T already formed (used when n != N - 1: the chains
+// of all modes but the last start with that product, which does not change
+// until the last mode's update, so an ALS sweep forms it once).
 tucker_status ttm_chain_except(tucker_handle* h, const FactorSet& F, const void* X, int n,
-                               double* buf0, double* buf1, double* out) {
+                               double* buf0, double* buf1, double* out, const double* ylast) {
   const int N = F.N;
   // shape tracked as dims[] with the current extent of each mode
   int64_t ext[TUCKER_MAX_ORDER];
@@ -817,7 +885,9 @@ tucker_status ttm_chain_except(tucker_handle* h, const FactorSet& F, const void*
   // first contraction straight from X
   int first = (n != N - 1) ? N - 1 : N - 2;
   double* dst = (--remaining == 0) ? out : bufs[which];
-  if (first == N - 1) {
+  if (ylast && first == N - 1 && remaining > 0) {
+    dst = const_cast<double*>(ylast);             // read only below: the next step writes elsewhere
+  } else if (first == N - 1) {
     TK_TRY(ttm_last(h, X, F.is64, prod(0, N - 1), (int)F.I[N - 1], F.A[N - 1], F.R[N - 1], dst));
   } else {
     TK_TRY(ttm_mid(h, X, F.is64, prod(0, first), (int)F.I[first], prod(first + 1, N), F.A[first],
