@@ -44,8 +44,8 @@ TC_RATIO = {"bf16": 1.0, "tf32": 0.5}
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
-    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--prec", default="auto")
@@ -59,6 +59,10 @@ def parse():
                    help="the smallest m on a x2 ladder from the workload's m whose median ridge-loss "
                         "ratio over 10 seeds is <= 1.01 (with --impl reference: by the oracle on "
                         "the host); prints its own JSON line, not the headline")
+    p.add_argument("--kernel-case", choices=["grouped"], default=None,
+                   help="a small case of one kernel family for ncu captures (grouped: the "
+                        "1024^3 Gram shapes, I_1 = 1024, d = 4096, m = 5e5, on a dense "
+                        "1024 x 128 x 128 tensor); prints its own JSON line, not the headline")
     p.add_argument("--stage-roofline", action="store_true",
                    help="time the sampler and the gather at 2^27 draws (their HBM/ALU rooflines); "
                         "prints its own JSON line, not the headline")
@@ -331,6 +335,31 @@ def workload_config(w, prec, reg, solver, m, x_bytes):
             "l2": f"flushed before every timed step (256 MiB write); X is {x_bytes / 2**20:.0f} MiB"}
 
 
+def run_kernel_case(args):
+    """Three sketched TF32 updates with the Gram grouped by the leading index at
+    the 1024^3-at-10% shapes (I_1 = 1024, ranks 16, d = 4096, m = 5e5) on a dense
+    1024 x 128 x 128 FP32 tensor: under 1 GB on the device, so that one launch of
+    the grouped kernels can be captured with every ncu section."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2107_10654_gb300 import tucker as T
+    g = synth.rng(4321)
+    dims, ranks, m = (1024, 128, 128), (16, 16, 16), 500000
+    F = [torch.from_numpy(g.standard_normal((i, r)).astype(np.float32)).cuda()
+         for i, r in zip(dims, ranks)]
+    X = torch.from_numpy(g.standard_normal(dims).astype(np.float32)).cuda()
+    h = T.Handle(solver=args.solver)
+    sts = [T.tucker_core_update_sketched(h, X, F, 0.1, m, 7, 0, "exact", "tf32", stats=True)[1]
+           for _ in range(3)]
+    print(json.dumps({"mode": "kernel_case", "case": args.kernel_case, "dims": dims,
+                      "ranks": ranks, "m": m,
+                      "ms": [s["ms_total"] for s in sts],
+                      "ms_gram": [s["ms_gram"] for s in sts],
+                      "ms_gram_kernel": [s["ms_gram_kernel"] for s in sts]}))
+    h.close()
+
+
 def run_stage_roofline(args):
     """Sampler and gather at 2^27 draws from the 512^3 tensor, whose per-stage
     times at the workload's m are launch-bound.  Rank-(2,2,2) factors keep the
@@ -600,6 +629,9 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.kernel_case:
+        run_kernel_case(args)
         return
     if args.stage_roofline:
         run_stage_roofline(args)
