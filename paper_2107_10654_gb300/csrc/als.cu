@@ -265,20 +265,26 @@ __global__ void __launch_bounds__(FB_WARPS * 32) k_fiber_rows(FiberArgs a) {
       j[k] = (int64_t)(key % (uint64_t)a.I[k]);
       key /= (uint64_t)a.I[k];
     }
-    double p = 1.0;
-    bool first = true;
+    // p and w by lane 0 alone (FP64 divisions are expensive on this GPU), then shared
     int64_t base = 0;
-    for (int k = 0; k < N; ++k) {
-      if (k == n) continue;
-      const uint64_t* C = a.cdf[k];
-      const uint64_t Q = C[a.I[k] - 1];
-      const uint64_t q = C[j[k]] - (j[k] > 0 ? C[j[k] - 1] : 0);
-      const double f = (double)q / (double)Q;
-      p = first ? f : p * f;
-      first = false;
-      base += j[k] * a.stride[k];
+    for (int k = 0; k < N; ++k)
+      if (k != n) base += j[k] * a.stride[k];
+    double w = 0.0;
+    if (lane == 0) {
+      double p = 1.0;
+      bool first = true;
+      for (int k = 0; k < N; ++k) {
+        if (k == n) continue;
+        const uint64_t* C = a.cdf[k];
+        const uint64_t Q = C[a.I[k] - 1];
+        const uint64_t q = C[j[k]] - (j[k] > 0 ? C[j[k] - 1] : 0);
+        const double f = (double)q / (double)Q;
+        p = first ? f : p * f;
+        first = false;
+      }
+      w = (double)a.counts[u] / ((double)a.m * p);
     }
-    const double w = (double)a.counts[u] / ((double)a.m * p);
+    w = __shfl_sync(0xffffffffu, w, 0);
     // factor rows a_k(j_k), k != n, into shared memory (offset k * TUCKER_MAX_RANK)
     for (int k = 0; k < N; ++k) {
       if (k == n) continue;

@@ -511,6 +511,278 @@ __global__ void __launch_bounds__(EX_THREADS, 1) k_tcg_expand(ExpandArgs a) {
   }
 }
 
+// ------------------------------- the grouped Gram with narrow M_{i_1} (d / R_1 <= 64)
+// Same decomposition, G = sum_{i_1} (a a^T) (x) M_{i_1}, for d' = d / R_1 <= 64,
+// where a 256-wide tile would be mostly padding.  One CTA per i_1 forms M_{i_1}
+// on the tensor cores from the segment's rows b_u = sqrt(w_u) a_2 (x) ... (x) a_N
+// (built in FP32), each split as b = b_hi + b_lo (TF32 both): with
+//   A = [B_hi^T; B_lo^T] (128 x K: rows j and 64 + j),  B = B_hi^T (64 x K)
+// one M = 128, N = 64 MMA per 8 samples gives D = [B_hi^T B_hi; B_lo^T B_hi] and
+//   M[j][j'] = D[j][j'] + D[64 + j][j'] + D[64 + j'][j]
+// (the dropped B_lo^T B_lo is 2^-22 relative), so M is as accurate as an FP32
+// Gram.  The expansion by a_{r1} a_{r1'} is a small contraction over i_1
+// (I_1 R_1^2 d'^2 / 2 multiply-adds) done on the CUDA cores in FP32.
+constexpr int NR_THREADS = 256;
+constexpr int NR_KC = 32;                        // samples per chunk (128 bytes of TF32)
+constexpr int NR_OP = TC_M * TC_ROWB;            // one 128-row operand stage: 16 KB
+constexpr int NR_COLS = 64;                      // TMEM columns (N of the MMA)
+constexpr int NR_MAXE = 9;                       // table slots per thread: 32 E <= 256 * 9
+constexpr int NR_DS = 65;                        // epilogue row stride (floats)
+
+struct NarrowArgs {
+  int nm;                                        // modes 2..N: nm = N - 1 of them
+  int R[TUCKER_MAX_ORDER];
+  int off[TUCKER_MAX_ORDER];                     // entry offset of mode n in a table row
+  int sumR;                                      // table row: sumR factor values + sqrt(w)
+  int dp;
+  const void* A[TUCKER_MAX_ORDER];
+  const uint32_t* idx[TUCKER_MAX_ORDER];
+  int is64;
+  const double* w;
+  const int* seg_begin;
+  const int* seg_end;
+  float* M;                                      // [I_1][dp][dp]
+  int* status;
+};
+
+static size_t narrow_smem_bytes(int sumR) {
+  const size_t body = 2 * (size_t)NR_OP + (size_t)NR_KC * (sumR + 1) * 4;
+  const size_t epi = (size_t)TC_M * NR_DS * 4;
+  return std::max(body, epi) + 1024;
+}
+
+__global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  const uint32_t base_u = smem_u32(smraw);
+  unsigned char* sm = smraw + ((1024 - (base_u & 1023)) & 1023);
+  const int E = a.sumR + 1, dp = a.dp;
+  float* tab = reinterpret_cast<float*>(sm + 2 * NR_OP);        // [NR_KC][E]
+  __shared__ uint64_t bar_free[2], bar_done;
+  __shared__ uint32_t tmem_slot;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int i1 = blockIdx.x;
+  const int b0 = a.seg_begin[i1], b1 = a.seg_end[i1];
+  const int nk = (b1 - b0 + NR_KC - 1) / NR_KC;
+  float* Mo = a.M + (size_t)i1 * dp * dp;
+  if (nk <= 0) {                                               // no sampled row has this i_1
+    for (int e = t; e < dp * dp; e += NR_THREADS) Mo[e] = 0.f;
+    return;
+  }
+  if (t == 0) {
+    mbar_init(&bar_free[0], 1);
+    mbar_init(&bar_free[1], 1);
+    mbar_init(&bar_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(&tmem_slot)), "r"((uint32_t)NR_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  // the two build units of this thread: operand row j (and 64 + j), 16-byte chunk q
+  int eo[2][TUCKER_MAX_ORDER - 1];
+  bool live[2];
+#pragma unroll
+  for (int h2 = 0; h2 < 2; ++h2) {
+    int j = (t + NR_THREADS * h2) & 63;
+    live[h2] = j < dp;
+#pragma unroll
+    for (int n = TUCKER_MAX_ORDER - 2; n >= 0; --n) {
+      eo[h2][n] = 0;
+      if (n < a.nm) {
+        eo[h2][n] = a.off[n] + j % a.R[n];
+        j /= a.R[n];
+      }
+    }
+  }
+  // table values of chunk k: slot v = t + 256 z holds (sample v / E, entry v % E)
+  auto load_chunk = [&](int k, float* v) {
+#pragma unroll
+    for (int z = 0; z < NR_MAXE; ++z) {
+      const int q = t + NR_THREADS * z;
+      float x = 0.f;
+      if (q < NR_KC * E) {
+        const int s = q / E, e = q - s * E;
+        const int u = b0 + k * NR_KC + s;
+        if (u < b1) {
+          if (e == a.sumR) {
+            x = sqrtf((float)a.w[u]);
+          } else {
+            int n = 0;
+            while (n + 1 < a.nm && e >= a.off[n + 1]) ++n;
+            x = (float)load_as_double(a.A[n], (int64_t)a.idx[n][u] * a.R[n] + (e - a.off[n]),
+                                      a.is64);
+          }
+        }
+      }
+      v[z] = x;
+    }
+  };
+  float cur[NR_MAXE], nxt[NR_MAXE];
+  load_chunk(0, cur);
+  const uint32_t id = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NR_COLS >> 3) << 17) |
+                      ((uint32_t)(TC_M >> 4) << 24);           // TF32, M = 128, N = 64
+  bool ok = true;
+  for (int k = 0; k < nk && ok; ++k) {
+    const int st = k & 1;
+    unsigned char* op = sm + (size_t)st * NR_OP;
+#pragma unroll
+    for (int z = 0; z < NR_MAXE; ++z)
+      if (t + NR_THREADS * z < NR_KC * E) tab[t + NR_THREADS * z] = cur[z];
+    if (k + 1 < nk) load_chunk(k + 1, nxt);
+    if (k >= 2) ok = ex_wait(&bar_free[st], ((k - 2) >> 1) & 1, a.status);  // chunk k - 2's MMAs
+    else __syncthreads();                                                   // the table
+    if (!ok) break;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int uu = t + NR_THREADS * h2, j = uu & 63, q = uu >> 6;
+      uint4 vh = make_uint4(0u, 0u, 0u, 0u), vl = vh;
+      if (live[h2]) {
+        float x[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float* row = tab + (4 * q + i) * E;
+          float p = row[a.sumR];
+#pragma unroll
+          for (int n = 0; n < TUCKER_MAX_ORDER - 1; ++n)
+            if (n < a.nm) p *= row[eo[h2][n]];
+          x[i] = p;
+        }
+        vh.x = to_tf32(x[0]); vl.x = to_tf32(x[0] - __uint_as_float(vh.x));
+        vh.y = to_tf32(x[1]); vl.y = to_tf32(x[1] - __uint_as_float(vh.y));
+        vh.z = to_tf32(x[2]); vl.z = to_tf32(x[2] - __uint_as_float(vh.z));
+        vh.w = to_tf32(x[3]); vl.w = to_tf32(x[3] - __uint_as_float(vh.w));
+      }
+      const int rl = 64 + j;                                   // j & 7 == rl & 7
+      const int c = (q ^ (j & 7)) << 4;
+      *reinterpret_cast<uint4*>(op + (size_t)(j >> 3) * 1024 + (j & 7) * TC_ROWB + c) = vh;
+      *reinterpret_cast<uint4*>(op + (size_t)(rl >> 3) * 1024 + (rl & 7) * TC_ROWB + c) = vl;
+    }
+    fence_proxy_async();                                       // generic writes -> tensor core
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      const uint32_t ob = smem_u32(op);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)                           // 8 samples per MMA
+        mma<TUCKER_PREC_TF32>(tmem, sw128_desc(ob + 32 * kk), sw128_desc(ob + 32 * kk), id,
+                              (k > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&bar_free[st]);
+    }
+#pragma unroll
+    for (int z = 0; z < NR_MAXE; ++z) cur[z] = nxt[z];
+  }
+  if (t == 0) mma_commit(&bar_done);                           // tracks every MMA issued
+  const bool done = ex_wait(&bar_done, 0, a.status);
+  tc_fence_after();
+  float* D = reinterpret_cast<float*>(sm);                     // [128][NR_DS]
+  if (done && ok) {
+    // TMEM -> D: warp w reads lanes 32 (w % 4) .. and columns 32 (w / 4) ..
+    const int quad = warp & 3, half = warp >> 2, row = quad * 32 + lane;
+#pragma unroll
+    for (int cb = 0; cb < 32; cb += 16) {
+      const int col = half * 32 + cb;
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                   "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                     "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                     "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                   : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int i = 0; i < 16; ++i) D[row * NR_DS + col + i] = __uint_as_float(v[i]);
+    }
+    __syncthreads();
+    for (int e = t; e < dp * dp; e += NR_THREADS) {
+      const int j = e / dp, jp = e - j * dp;
+      Mo[e] = D[j * NR_DS + jp] + D[(64 + j) * NR_DS + jp] + D[(64 + jp) * NR_DS + j];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 ::"r"(tmem), "r"((uint32_t)NR_COLS) : "memory");
+  }
+}
+
+// G_{(r1,j),(r2,j')} = sum_{i_1} a_{r1} a_{r2} M_{i_1}[j][j'] in FP32 on the CUDA
+// cores.  CTA: 32 entries (j <= j', the upper triangle of M in row-major order)
+// x 32 pairs (r1, r2) (pairs 32 y .. 32 y + 31); warp w sums i_1 over the w-th
+// of 16 contiguous ranges, and the 16 partials are added in a fixed order, so
+// the result does not depend on scheduling.  Writes each entry of G and its
+// mirror (for j = j' only the pairs r1 <= r2, so G is exactly symmetric).
+constexpr int XN_WARPS = 16;
+
+template <int R1>
+__global__ void __launch_bounds__(XN_WARPS * 32) k_tcg_expand_narrow(const float* M, int I1,
+                                                                     int dp, const void* A1,
+                                                                     int is64, int d, double* G) {
+  extern __shared__ float xs[];
+  float* a1 = xs;                                              // [I1][R1]
+  float* red = xs + ((I1 * R1 + 3) & ~3);                      // [16][32][32]
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  for (int i = t; i < I1 * R1; i += XN_WARPS * 32)
+    a1[i] = (float)load_as_double(A1, i, is64);
+  // entry e -> (j, j'): rows j hold dp - j entries
+  const int ne = dp * (dp + 1) / 2;
+  const int e = blockIdx.x * 32 + lane;
+  int j = 0, jp = 0;
+  if (e < ne) {
+    int start = 0;
+    while (start + (dp - j) <= e) { start += dp - j; ++j; }
+    jp = j + (e - start);
+  }
+  constexpr int NP = R1 * R1 < 32 ? R1 * R1 : 32;              // pairs of this CTA
+  constexpr int NR = NP / R1 > 0 ? NP / R1 : 1;                // values of r1 among them
+  const int r1b = blockIdx.y * 32 / R1;
+  __syncthreads();
+  float acc[NP];
+#pragma unroll
+  for (int c = 0; c < NP; ++c) acc[c] = 0.f;
+  const int ib = (int)((int64_t)I1 * warp / XN_WARPS), ie = (int)((int64_t)I1 * (warp + 1) / XN_WARPS);
+  const size_t msz = (size_t)dp * dp;
+  const float* mp = M + (size_t)j * dp + jp;
+  for (int i = ib; i < ie; ++i) {
+    const float m = e < ne ? __ldg(mp + (size_t)i * msz) : 0.f;
+    const float* ar = a1 + i * R1;
+    float tq[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) tq[r] = ar[r] * m;
+    float ap[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) ap[r] = ar[r1b + r];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) acc[c] = fmaf(ap[c / R1], tq[c % R1], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < NP; ++c) red[(warp * 32 + c) * 32 + lane] = acc[c];
+  __syncthreads();
+  for (int o = t; o < NP * 32; o += XN_WARPS * 32) {
+    const int c = o >> 5, le = o & 31;
+    const int eo = blockIdx.x * 32 + le;
+    if (eo >= ne) continue;
+    float v = 0.f;
+    for (int w = 0; w < XN_WARPS; ++w) v += red[(w * 32 + c) * 32 + le];
+    int jj = 0, start = 0;
+    while (start + (dp - jj) <= eo) { start += dp - jj; ++jj; }
+    const int jjp = jj + (eo - start);
+    const int r1 = r1b + c / R1, r2 = c % R1;
+    if (jj == jjp && r1 > r2) continue;
+    const size_t A = (size_t)r1 * dp + jj, B = (size_t)r2 * dp + jjp;
+    G[A * d + B] = (double)v;
+    G[B * d + A] = (double)v;
+  }
+}
+
 // --------------------------------------------------------------- the SYRK
 
 template <int PREC>
@@ -881,6 +1153,20 @@ int gram_tc_grouped_ok(int N, int d, int R1, int64_t I1) {
   return I1 >= 1 && I1 * nt <= 8192 && I1 * R1 * 4 <= 200 * 1024;   // A^(1) staged in the reduction
 }
 
+// Whether the narrow grouped Gram applies: order >= 3, R_1 in {2, 4, 8, 16},
+// d / R_1 <= 64, at least 2 rows per value of i_1 on average (else the full-width
+// Gram is as cheap), and A^(1) small enough to stage in shared memory.
+int gram_tc_narrow_ok(int N, int d, int R1, int64_t I1, int64_t cap) {
+  if (N < 3 || R1 < 2 || R1 > 16 || (R1 & (R1 - 1)) || d % R1) return 0;
+  const int dp = d / R1;
+  return dp <= 64 && I1 >= 1 && cap >= 2 * I1 && I1 * R1 * 4 <= 96 * 1024;
+}
+
+static size_t gram_tc_narrow_bytes(int d, int R1, int64_t I1) {
+  const int dp = d / R1;
+  return (size_t)I1 * dp * dp * 4 + 4096 + (size_t)2 * I1 * 4 + 4096;
+}
+
 static size_t gram_tc_grouped_bytes(int prec, int d, int sumR, int R1, int64_t I1, int64_t cap) {
   const int dp = d / R1;
   int Tt;
@@ -902,6 +1188,7 @@ size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int sumR, int64_t ca
   size_t b = (size_t)nch * CS * sumR * 4 + 4096 + (size_t)ns * ntiles * TC_TILE * TC_TILE * 4 + 4096;
   if (gram_tc_grouped_ok(N, d, R1, I1))
     b = std::max(b, gram_tc_grouped_bytes(prec, d, sumR, R1, I1, cap));
+  if (gram_tc_narrow_ok(N, d, R1, I1, cap)) b = std::max(b, gram_tc_narrow_bytes(d, R1, I1));
   return b;
 }
 
@@ -1014,6 +1301,74 @@ tucker_status launch_gram_tc_grouped(tucker_handle* h, const RowSet& s, int prec
   TK_LAUNCH(h);
   if (h->timing) cudaEventRecord(h->ev[11], h->stream);
   return launch_expand(h, partial, (int)I1, ntiles, dp, s.A[0], s.is64, R1, s.d, G);
+}
+
+// The narrow grouped Gram (sorted sample, s.idx[0] non-decreasing, d / R_1 <= 64).
+template <int R1>
+static tucker_status launch_expand_narrow(tucker_handle* h, const float* M, int I1, int dp,
+                                          const void* A1, int is64, int d, double* G) {
+  const int ne = dp * (dp + 1) / 2;
+  const size_t smem = (size_t)(((I1 * R1 + 3) & ~3) + XN_WARPS * 32 * 32) * 4;
+  if (smem > 227 * 1024) return fail(h, TUCKER_ENOTSUP, "narrow grouped Gram: shared memory");
+  TK_CUDA(h, cudaFuncSetAttribute(k_tcg_expand_narrow<R1>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TK_COUNT(h);
+  k_tcg_expand_narrow<R1><<<dim3((ne + 31) / 32, (R1 * R1 + 31) / 32), XN_WARPS * 32, smem,
+                            h->stream>>>(M, I1, dp, A1, is64, d, G);
+  TK_LAUNCH(h);
+  return TUCKER_OK;
+}
+
+tucker_status launch_gram_tc_narrow(tucker_handle* h, const RowSet& s, int64_t I1, char* ws,
+                                    size_t ws_bytes, double* G) {
+  const int R1 = s.R[0], dp = s.d / R1;
+  if (gram_tc_narrow_bytes(s.d, R1, I1) > ws_bytes)
+    return fail(h, TUCKER_EINTERNAL, "narrow grouped Gram workspace too small");
+  NarrowArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nm = s.N - 1;
+  int off = 0;
+  for (int n = 1; n < s.N; ++n) {
+    a.R[n - 1] = s.R[n];
+    a.off[n - 1] = off;
+    off += s.R[n];
+    a.A[n - 1] = s.A[n];
+    a.idx[n - 1] = s.idx[n];
+  }
+  a.sumR = off;
+  if (NR_KC * (a.sumR + 1) > NR_THREADS * NR_MAXE)
+    return fail(h, TUCKER_ENOTSUP, "narrow grouped Gram: sum of ranks %d too large", a.sumR);
+  a.dp = dp;
+  a.is64 = s.is64;
+  a.w = s.w;
+  float* M = reinterpret_cast<float*>(ws);
+  int* seg_begin = reinterpret_cast<int*>(ws + (((size_t)I1 * dp * dp * 4 + 255) & ~size_t(255)));
+  int* seg_end = seg_begin + I1;
+  a.seg_begin = seg_begin;
+  a.seg_end = seg_end;
+  a.M = M;
+  a.status = h->d_status;
+  TK_CUDA(h, cudaMemsetAsync(seg_begin, 0, sizeof(int) * 2 * I1, h->stream));
+  int gs = (int)std::min<int64_t>(((int64_t)I1 * 64 + 255) / 256, (int64_t)h->num_sms * 8);
+  if (gs < 1) gs = 1;
+  TK_COUNT(h);
+  k_tcg_segments<<<gs, 256, 0, h->stream>>>(s.idx[0], s.n_rows, seg_begin, seg_end);
+  TK_LAUNCH(h);
+  const size_t smem = narrow_smem_bytes(a.sumR);
+  TK_CUDA(h, cudaFuncSetAttribute(k_tcg_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  if (h->timing) cudaEventRecord(h->ev[10], h->stream);
+  TK_COUNT(h);
+  k_tcg_narrow<<<(int)I1, NR_THREADS, smem, h->stream>>>(a);
+  TK_LAUNCH(h);
+  if (h->timing) cudaEventRecord(h->ev[11], h->stream);
+  switch (R1) {
+    case 2: return launch_expand_narrow<2>(h, M, (int)I1, dp, s.A[0], s.is64, s.d, G);
+    case 4: return launch_expand_narrow<4>(h, M, (int)I1, dp, s.A[0], s.is64, s.d, G);
+    case 8: return launch_expand_narrow<8>(h, M, (int)I1, dp, s.A[0], s.is64, s.d, G);
+    case 16: return launch_expand_narrow<16>(h, M, (int)I1, dp, s.A[0], s.is64, s.d, G);
+    default: return fail(h, TUCKER_EINTERNAL, "narrow grouped Gram: R_1 = %d", R1);
+  }
 }
 
 tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_t cap, char* ws,

@@ -486,30 +486,92 @@ struct GramEigArgs {
   double* evals[TUCKER_MAX_ORDER];
 };
 
+// FP32 cyclic Jacobi by one warp (the same tournament ordering as
+// jacobi_eig_warp): the preconditioner is applied in FP32, so its V_n and ev_n
+// need FP32 accuracy only, and on this GPU a dependent FP64 operation costs
+// tens of cycles (the FP64 eigendecomposition of three 8 x 8 Grams took about
+// 70 us, the FP32 one a few).  Stops when the off-diagonal mass is below
+// (2^-24)^2 of the diagonal's, at most 40 sweeps.
+__device__ void jacobi_eig_warp_f32(float* G, float* V, int Rp, float* cs, float* sn, int* pp,
+                                    int* qq, int lane) {
+  const int half = Rp / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    float off = 0.f, dia = 0.f;
+    for (int e = lane; e < Rp * Rp; e += 32) {
+      const float v = G[e] * G[e];
+      if (e / Rp == e % Rp) dia += v; else off += v;
+    }
+    off = warp_sum(off);
+    dia = warp_sum(dia);
+    if (!(off > 3.6e-15f * dia) || Rp <= 1) break;
+    for (int step = 0; step < Rp - 1; ++step) {
+      for (int k = lane; k < half; k += 32) {
+        const int s1 = Rp - 1 - k;
+        int p = k == 0 ? 0 : ((k - 1 + step) % (Rp - 1)) + 1;
+        int q = ((s1 - 1 + step) % (Rp - 1)) + 1;
+        if (p > q) { const int t = p; p = q; q = t; }
+        const float apq = G[p * Rp + q], app = G[p * Rp + p], aqq = G[q * Rp + q];
+        float c = 1.f, sv = 0.f;
+        if (fabsf(apq) > 1e-8f * fabsf(app + aqq) && fabsf(apq) > 1e-30f) {
+          const float theta = (aqq - app) / (2.f * apq);
+          const float t = fabsf(theta) > 1e18f
+                              ? 0.5f / theta
+                              : copysignf(1.f, theta) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+          c = rsqrtf(fmaf(t, t, 1.f));
+          sv = t * c;
+        }
+        cs[k] = c; sn[k] = sv; pp[k] = p; qq[k] = q;
+      }
+      __syncwarp();
+      for (int e = lane; e < half * Rp; e += 32) {      // rows p, q
+        const int k = e / Rp, j = e % Rp;
+        const int p = pp[k], q = qq[k];
+        const float c = cs[k], sv = sn[k];
+        const float gp = G[p * Rp + j], gq = G[q * Rp + j];
+        G[p * Rp + j] = c * gp - sv * gq;
+        G[q * Rp + j] = sv * gp + c * gq;
+      }
+      __syncwarp();
+      for (int e = lane; e < half * Rp; e += 32) {      // columns p, q (and V)
+        const int k = e / Rp, i = e % Rp;
+        const int p = pp[k], q = qq[k];
+        const float c = cs[k], sv = sn[k];
+        const float gp = G[i * Rp + p], gq = G[i * Rp + q];
+        G[i * Rp + p] = c * gp - sv * gq;
+        G[i * Rp + q] = sv * gp + c * gq;
+        const float vp = V[i * Rp + p], vq = V[i * Rp + q];
+        V[i * Rp + p] = c * vp - sv * vq;
+        V[i * Rp + q] = sv * vp + c * vq;
+      }
+      __syncwarp();
+    }
+  }
+}
+
 __global__ void __launch_bounds__(32) k_gram_eig(GramEigArgs a) {
-  extern __shared__ double sm[];
+  extern __shared__ float smf[];
   const int n = blockIdx.x;
   const int R = a.R[n];
   const int Rp = R + (R & 1);
-  double* G = sm;
-  double* V = G + Rp * Rp;
-  double* cs = V + Rp * Rp;
-  double* sn = cs + Rp / 2;
+  float* G = smf;
+  float* V = G + Rp * Rp;
+  float* cs = V + Rp * Rp;
+  float* sn = cs + Rp / 2;
   int* pp = reinterpret_cast<int*>(sn + Rp / 2);
   int* qq = pp + Rp / 2;
   const int lane = threadIdx.x;
   for (int e = lane; e < Rp * Rp; e += 32) {
     const int r = e / Rp, c = e % Rp;
-    G[e] = (r < R && c < R) ? a.gram[n][r * R + c] : 0.0;
-    V[e] = (r == c) ? 1.0 : 0.0;
+    G[e] = (r < R && c < R) ? (float)a.gram[n][r * R + c] : 0.f;
+    V[e] = (r == c) ? 1.f : 0.f;
   }
   __syncwarp();
-  jacobi_eig_warp(G, V, Rp, cs, sn, pp, qq, lane);
+  jacobi_eig_warp_f32(G, V, Rp, cs, sn, pp, qq, lane);
   for (int e = lane; e < R * R; e += 32) {
     const int r = e / R, k = e % R;
-    a.evecs[n][e] = V[r * Rp + k];
+    a.evecs[n][e] = (double)V[r * Rp + k];
   }
-  for (int k = lane; k < R; k += 32) a.evals[n][k] = G[k * Rp + k];
+  for (int k = lane; k < R; k += 32) a.evals[n][k] = (double)G[k * Rp + k];
 }
 
 tucker_status launch_gram_eig(tucker_handle* h, int N, const int* R, const double* const* gram,
@@ -526,7 +588,7 @@ tucker_status launch_gram_eig(tucker_handle* h, int N, const int* R, const doubl
     const int Rp = R[n] + (R[n] & 1);
     if (Rp > maxRp) maxRp = Rp;
   }
-  const size_t smem = size_t(2 * maxRp * maxRp + maxRp) * sizeof(double) +
+  const size_t smem = size_t(2 * maxRp * maxRp + maxRp) * sizeof(float) +
                       size_t(maxRp + 2) * sizeof(int) + 64;
   TK_CUDA(h, cudaFuncSetAttribute(k_gram_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));

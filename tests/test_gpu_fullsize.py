@@ -63,13 +63,13 @@ def _check_gram_entries(F, dims, ku, w, G, n_pairs=96, seed=0, c=BF16_C):
     g = np.random.default_rng(seed)
     pairs = list(zip(g.integers(0, d, n_pairs), g.integers(0, d, n_pairs)))
     pairs += [(r, r) for r in g.integers(0, d, 16)]
-    for r, c in pairs:
-        rr, cc = np.unravel_index(r, R), np.unravel_index(c, R)
+    for ri, ci in pairs:
+        rr, cc = np.unravel_index(ri, R), np.unravel_index(ci, R)
         kr = np.prod([rows[n][:, rr[n]] for n in range(len(R))], axis=0)
         kc = np.prod([rows[n][:, cc[n]] for n in range(len(R))], axis=0)
         ref = float(np.sum(w * kr * kc))
         bound = c * float(np.sum(w * np.abs(kr) * np.abs(kc)))
-        assert abs(G[r, c] - ref) <= bound + 1e-12 * abs(ref), (r, c, G[r, c], ref, bound)
+        assert abs(G[ri, ci] - ref) <= bound + 1e-12 * abs(ref), (ri, ci, G[ri, ci], ref, bound)
 
 
 def _check_residual(F, dims, ku, w, x, lam, g, tol=1e-7):
