@@ -81,11 +81,23 @@ __device__ __forceinline__ void rows_contract(const T* const* rows, int nr, int 
 #pragma unroll
     for (int j = 0; j < RP; ++j) acc[r][j] = T(0);
   if (vec) {
-    for (int i0 = lane * VEC; i0 < I; i0 += 32 * VEC) {
-      T xv[RB][VEC];
+    // the loads of the next 16-byte column group are issued before the
+    // multiply-adds of the current one (2 RB loads in flight per lane)
+    T xv[RB][VEC], xn[RB][VEC];
+    if (lane * VEC < I) {
 #pragma unroll
       for (int r = 0; r < RB; ++r)
-        if (r < nr) *reinterpret_cast<uint4*>(xv[r]) = __ldg(reinterpret_cast<const uint4*>(rows[r] + i0));
+        if (r < nr)
+          *reinterpret_cast<uint4*>(xv[r]) = __ldg(reinterpret_cast<const uint4*>(rows[r] + lane * VEC));
+    }
+    for (int i0 = lane * VEC; i0 < I; i0 += 32 * VEC) {
+      if (i0 + 32 * VEC < I) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+          if (r < nr)
+            *reinterpret_cast<uint4*>(xn[r]) =
+                __ldg(reinterpret_cast<const uint4*>(rows[r] + i0 + 32 * VEC));
+      }
       if (SQ) {
 #pragma unroll
         for (int r = 0; r < RB; ++r)
@@ -102,6 +114,10 @@ __device__ __forceinline__ void rows_contract(const T* const* rows, int nr, int 
 #pragma unroll
           for (int q = 0; q < VEC; ++q) acc[r][j] = fma(xv[r][q], av[q], acc[r][j]);
       }
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) xv[r][q] = xn[r][q];
     }
   } else {
     for (int i = lane; i < I; i += 32) {

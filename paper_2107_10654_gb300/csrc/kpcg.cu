@@ -180,6 +180,78 @@ __device__ void kron_precond(int d, int N, const KpcgShared& sh, const float* Vs
   }
 }
 
+// kron_precond when every R_n equals R = 2^LR and d = R^NT: the digit of mode n
+// in e is (e >> LR (NT - 1 - n)) & (R - 1), so each pass is shifts, masks and R
+// multiply-adds with compile-time strides (no divisions, no per-mode dispatch);
+// same arithmetic, in the same order, as kron_precond.
+template <int NT, int LR>
+__device__ void kron_precond_pow2(int d, const float* Vs, const float* dg, const float* r,
+                                  float* t0, float* t1, float* z) {
+  constexpr int R = 1 << LR, RR = R * R;
+  const float* cur = r;
+  float* bufs[2] = {t0, t1};
+  int nb = 0;
+#pragma unroll
+  for (int n = 0; n < NT; ++n) {                       // t = (x V_n)^T r, then the scale
+    const int sh = LR * (NT - 1 - n);
+    float* dst = bufs[nb];
+    const float* Vn = Vs + n * RR;
+    for (int e = threadIdx.x; e < d; e += KP_THREADS) {
+      const int k = (e >> sh) & (R - 1);
+      const float* src = cur + (e - (k << sh));
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < R; ++q) acc = fmaf(Vn[q * R + k], src[q << sh], acc);
+      dst[e] = n == NT - 1 ? acc * dg[e] : acc;
+    }
+    __syncthreads();
+    cur = dst;
+    nb ^= 1;
+  }
+#pragma unroll
+  for (int n = NT - 1; n >= 0; --n) {                  // z = (x V_n) t
+    const int sh = LR * (NT - 1 - n);
+    float* dst = n == 0 ? z : bufs[nb];
+    const float* Vn = Vs + n * RR;
+    for (int e = threadIdx.x; e < d; e += KP_THREADS) {
+      const int k = (e >> sh) & (R - 1);
+      const float* src = cur + (e - (k << sh));
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < R; ++q) acc = fmaf(Vn[k * R + q], src[q << sh], acc);
+      dst[e] = acc;
+    }
+    __syncthreads();
+    cur = dst;
+    nb ^= 1;
+  }
+}
+
+// Which kron_precond_pow2 instance applies (0: none): equal ranks R = 2^LR,
+// d = R^N, for (N, R) in {2, 3, 4} x {4, 8, 16} with d <= KP_BMAX * KP_THREADS.
+__device__ __forceinline__ int precond_kind(int N, const int* R, int d) {
+  for (int n = 1; n < N; ++n)
+    if (R[n] != R[0]) return 0;
+  const int lr = R[0] == 4 ? 2 : R[0] == 8 ? 3 : R[0] == 16 ? 4 : 0;
+  if (lr == 0 || N < 2 || N > 4 || d != 1 << (lr * N) || d > KP_BMAX * KP_THREADS) return 0;
+  return N * 8 + lr;
+}
+
+__device__ __forceinline__ void precond_any(int kind, int d, int N, const KpcgShared& sh,
+                                            const float* Vs, const float* dg, const float* r,
+                                            float* t0, float* t1, float* z) {
+  switch (kind) {
+    case 2 * 8 + 3: kron_precond_pow2<2, 3>(d, Vs, dg, r, t0, t1, z); break;
+    case 2 * 8 + 4: kron_precond_pow2<2, 4>(d, Vs, dg, r, t0, t1, z); break;
+    case 3 * 8 + 2: kron_precond_pow2<3, 2>(d, Vs, dg, r, t0, t1, z); break;
+    case 3 * 8 + 3: kron_precond_pow2<3, 3>(d, Vs, dg, r, t0, t1, z); break;
+    case 3 * 8 + 4: kron_precond_pow2<3, 4>(d, Vs, dg, r, t0, t1, z); break;
+    case 4 * 8 + 2: kron_precond_pow2<4, 2>(d, Vs, dg, r, t0, t1, z); break;
+    case 4 * 8 + 3: kron_precond_pow2<4, 3>(d, Vs, dg, r, t0, t1, z); break;
+    default: kron_precond(d, N, sh, Vs, dg, r, t0, t1, z); break;
+  }
+}
+
 // Shared-memory vectors of one CTA (d-vectors padded to dp, 16-byte slots).
 struct KpcgVecs {
   float *r, *z, *p, *q, *x, *dg, *t0, *t1, *Vs;
@@ -212,15 +284,30 @@ __device__ float kpcg_setup(const KpcgArgs& a, KpcgShared& sh, const KpcgVecs& v
     sh.div_r[tid] = a.div_r[tid];
   }
   {                                                    // V_n, ev_n into shared memory
+    // one pass over all modes' entries, so that every load is in flight at once
     int off = 0, eoff = 0;
+    int vo[TUCKER_MAX_ORDER + 1], eo[TUCKER_MAX_ORDER + 1];
     for (int n = 0; n < a.N; ++n) {
-      const int R = a.R[n], RR = R * R;
-      for (int e = tid; e < RR; e += KP_THREADS) v.Vs[off + e] = (float)a.V[n][e];
-      for (int e = tid; e < R; e += KP_THREADS) sh.ev[eoff + e] = fmaxf((float)a.ev[n][e], 0.f);
-      sh.evoff[n] = eoff;
-      off += RR;
-      eoff += R;
+      vo[n] = off;
+      eo[n] = eoff;
+      off += a.R[n] * a.R[n];
+      eoff += a.R[n];
     }
+    vo[a.N] = off;
+    eo[a.N] = eoff;
+    for (int e = tid; e < off + eoff; e += KP_THREADS) {
+      if (e < off) {
+        int n = 0;
+        while (e >= vo[n + 1]) ++n;
+        v.Vs[e] = (float)a.V[n][e - vo[n]];
+      } else {
+        const int f = e - off;
+        int n = 0;
+        while (f >= eo[n + 1]) ++n;
+        sh.ev[f] = fmaxf((float)a.ev[n][f - eo[n]], 0.f);
+      }
+    }
+    if (tid < a.N) sh.evoff[tid] = eo[tid];
   }
   // one wave of global loads: the diagonal of M, lambda R and b (b stays in
   // registers: at most KP_BMAX entries per thread)
@@ -396,9 +483,11 @@ __device__ __forceinline__ float4 rows_dot4(const float* m0, size_t ld, int nr, 
 }
 
 // Outputs of this CTA's rows: out = x and/or upd += x; returns the partial
-// (||x||^2, ||upd||^2) of those rows in FP64 (warp sums, then warp 0 in order).
+// (||x||^2, ||upd||^2) of those rows in FP64 (warp sums, then a fixed-order
+// shuffle tree over the warps; valid in thread 0).  upd0: upd[lo + tid], loaded
+// by the caller before the iterations (its latency off this tail).
 __device__ double2 kpcg_write(const KpcgArgs& a, const KpcgShared& sh, const KpcgVecs& v, int lo,
-                              int hi) {
+                             int hi, double upd0) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   double so = 0.0, su = 0.0;
   const double sc = sh.bscale;                         // undo the scaling of b
@@ -406,7 +495,7 @@ __device__ double2 kpcg_write(const KpcgArgs& a, const KpcgShared& sh, const Kpc
     const double xi = (double)v.x[i] * sc;
     if (a.out) a.out[i] = xi;
     if (a.upd) {
-      const double gn = a.upd[i] + xi;
+      const double gn = (i == lo + tid ? upd0 : a.upd[i]) + xi;
       a.upd[i] = gn;
       so = fma(xi, xi, so);
       su = fma(gn, gn, su);
@@ -418,8 +507,12 @@ __device__ double2 kpcg_write(const KpcgArgs& a, const KpcgShared& sh, const Kpc
   if (lane == 0) { wpart[0][w] = so; wpart[1][w] = su; }
   __syncthreads();
   double2 t = make_double2(0.0, 0.0);
-  if (tid == 0)
-    for (int k = 0; k < KP_WARPS; ++k) { t.x += wpart[0][k]; t.y += wpart[1][k]; }
+  if (w == 0) {
+    double x = lane < KP_WARPS ? wpart[0][lane] : 0.0, y = lane < KP_WARPS ? wpart[1][lane] : 0.0;
+    x = warp_sum(x);
+    y = warp_sum(y);
+    t = make_double2(x, y);
+  }
   return t;
 }
 
@@ -439,13 +532,15 @@ __global__ void __launch_bounds__(KP_THREADS, 1) k_kpcg(KpcgArgs a) {
   const int C = gridDim.x;
   const int rows = (d + C - 1) / C;
   const int lo = min(d, (int)blockIdx.x * rows), hi = min(d, lo + rows);
+  const double upd0 = (a.upd && lo + tid < hi) ? a.upd[lo + tid] : 0.0;
   const float bnorm2 = kpcg_setup(a, sh, v);
+  const int pkind = precond_kind(a.N, a.R, d);
   const float stop2 = (float)(a.tol * a.tol) * bnorm2;
   float rr = bnorm2, gamma_old = 1.f, alpha_old = 1.f;
   int it = 0;
   const bool vec = (d & 3) == 0;
   for (; it < a.max_iter && rr > stop2; ++it) {
-    kron_precond(d, a.N, sh, v.Vs, v.dg, v.r, v.t0, v.t1, v.z);   // ends with a barrier
+    precond_any(pkind, d, a.N, sh, v.Vs, v.dg, v.r, v.t0, v.t1, v.z);   // ends with a barrier
     float* sgk = a.sg + (size_t)(it & 1) * d;
     for (int i = lo + 4 * w; i < hi; i += 4 * KP_WARPS) {
       const int nr = min(4, hi - i);
@@ -462,7 +557,7 @@ __global__ void __launch_bounds__(KP_THREADS, 1) k_kpcg(KpcgArgs a) {
   // every CTA read rhs before the first barrier, and a barrier follows here in
   // any case (rhs may alias out)
   grid.sync();
-  const double2 t = kpcg_write(a, sh, v, lo, hi);
+  const double2 t = kpcg_write(a, sh, v, lo, hi, upd0);
   if (a.res && blockIdx.x == 0 && tid == 0) {
     a.res[0] = (double)it;
     a.res[1] = bnorm2 > 0.f ? sqrt((double)rr / (double)bnorm2) : 0.0;
@@ -527,6 +622,7 @@ __global__ void __launch_bounds__(KP_THREADS, 1) k_kpcg_cluster(KpcgArgs a) {
       for (int c = lane; c < d; c += 32) dst[c] = __ldg(src + c);
     }
   }
+  const double upd0 = (a.upd && lo + tid < hi) ? a.upd[lo + tid] : 0.0;
   const float bnorm2 = kpcg_setup(a, sh, v);           // ends with a barrier
   if (tma) {                                           // bounded wait for the rows
     bool ok = false;
@@ -534,11 +630,12 @@ __global__ void __launch_bounds__(KP_THREADS, 1) k_kpcg_cluster(KpcgArgs a) {
     if (!ok) set_status(a.status, DEV_INTERNAL);       // reported by the host; no barrier skipped
   }
   cl.sync();                                          // every CTA running before remote stores
+  const int pkind = precond_kind(a.N, a.R, d);
   const float stop2 = (float)(a.tol * a.tol) * bnorm2;
   float rr = bnorm2, gamma_old = 1.f, alpha_old = 1.f;
   int it = 0;
   for (; it < a.max_iter && rr > stop2; ++it) {
-    kron_precond(d, a.N, sh, v.Vs, v.dg, v.r, v.t0, v.t1, v.z);   // ends with a barrier
+    precond_any(pkind, d, a.N, sh, v.Vs, v.dg, v.r, v.t0, v.t1, v.z);   // ends with a barrier
     float* sk = s2 + (size_t)(it & 1) * dp;
     for (int i = lo + 4 * w; i < hi; i += 4 * KP_WARPS) {
       const int nr = min(4, hi - i);
@@ -554,7 +651,7 @@ __global__ void __launch_bounds__(KP_THREADS, 1) k_kpcg_cluster(KpcgArgs a) {
     rr = r2;
   }
   cl.sync();                                          // rhs read everywhere (it may alias out)
-  const double2 t = kpcg_write(a, sh, v, lo, hi);
+  const double2 t = kpcg_write(a, sh, v, lo, hi, upd0);
   if (a.res && me == 0 && tid == 0) {
     a.res[0] = (double)it;
     a.res[1] = bnorm2 > 0.f ? sqrt((double)rr / (double)bnorm2) : 0.0;
