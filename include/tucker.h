@@ -81,12 +81,16 @@ typedef enum { TUCKER_F32 = 0, TUCKER_F64 = 1 } tucker_dtype;
  * starts with an FP64 correction (one suffices at TF32's rounding).
  * TF32/BF16 operands: each sampled row k_u = sqrt(w_u) a_1 (x) ... (x) a_N is
  * formed in FP32 and rounded once.  For order >= 3 with R_1 a power of two
- * <= 16 and d / R_1 >= 128 the Gram is grouped by the leading index instead
- * (G = sum_{i_1} (a a^T) (x) M_{i_1}, a = A^(1)[i_1], the rows of one i_1
- * adjacent in the key-sorted sample): the tensor cores form each M_{i_1} from
- * the rounded rows sqrt(w_u) a_2 (x) ... (x) a_N, and an FP32 reduction
- * applies a_{r1} a_{r1'} unrounded.  Either way G is FP32-accumulated and
- * stored as FP64. */
+ * <= 16 the Gram is grouped by the leading index instead when d / R_1 >= 128
+ * or (d / R_1 <= 64, at least two sampled rows per value of i_1) (G = sum_{i_1}
+ * (a a^T) (x) M_{i_1}, a = A^(1)[i_1], the rows of one i_1 adjacent in the
+ * key-sorted sample).  Wide M_{i_1}: the tensor cores form each from the
+ * rounded rows sqrt(w_u) a_2 (x) ... (x) a_N, and the expansion by a_{r1} a_{r1'}
+ * runs on the tensor cores with both operands split into TF32 hi + lo parts.
+ * Narrow M_{i_1} (d / R_1 <= 64): the tensor cores form each from rows split
+ * into TF32 hi + lo parts (an FP32-level Gram, for either tensor-core
+ * precision), and the expansion runs in FP32 on the CUDA cores.  Either way G
+ * is FP32-accumulated and stored as FP64. */
 typedef enum {
   TUCKER_PREC_FP64 = 0,   /* FP64 CUDA-core Gram; no refinement needed */
   TUCKER_PREC_FP32 = 1,   /* FP32 CUDA-core Gram, FP64 refinement */

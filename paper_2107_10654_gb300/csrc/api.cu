@@ -131,8 +131,8 @@ size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int sumR, int64_t ca
                          int64_t I1);
 int gram_tc_grouped_ok(int N, int d, int R1, int64_t I1);
 int gram_tc_narrow_ok(int N, int d, int R1, int64_t I1, int64_t cap);
-tucker_status launch_gram_tc_narrow(tucker_handle* h, const RowSet& s, int64_t I1, char* ws,
-                                    size_t ws_bytes, double* G);
+tucker_status launch_gram_tc_narrow(tucker_handle* h, const RowSet& s, int64_t I1, int64_t cap,
+                                    char* ws, size_t ws_bytes, double* G);
 tucker_status launch_gram_tc_grouped(tucker_handle* h, const RowSet& s, int prec, int64_t cap,
                                      int64_t I1, char* ws, size_t ws_bytes, double* G);
 tucker_status launch_gram_tc(tucker_handle* h, const RowSet& s, int prec, int64_t cap, char* ws,
@@ -585,7 +585,7 @@ static tucker_status build_gram(tucker_handle* h, const FactorSet& F, const RowS
     return fail(h, TUCKER_ENOTSUP, "tensor-core Gram does not support d = %d", F.d);
   // sorted sample: group the Gram by the leading index when that is the smaller job
   if (gram_tc_narrow_ok(F.N, F.d, F.R[0], F.I[0], cap))
-    return launch_gram_tc_narrow(h, rs, F.I[0], b.gram_ws, b.gram_bytes, G);
+    return launch_gram_tc_narrow(h, rs, F.I[0], cap, b.gram_ws, b.gram_bytes, G);
   if (gram_tc_grouped_ok(F.N, F.d, F.R[0], F.I[0]))
     return launch_gram_tc_grouped(h, rs, prec, cap, F.I[0], b.gram_ws, b.gram_bytes, G);
   return launch_gram_tc(h, rs, prec, cap, b.gram_ws, b.gram_bytes, G);

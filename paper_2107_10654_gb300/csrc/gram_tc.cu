@@ -513,21 +513,28 @@ __global__ void __launch_bounds__(EX_THREADS, 1) k_tcg_expand(ExpandArgs a) {
 
 // ------------------------------- the grouped Gram with narrow M_{i_1} (d / R_1 <= 64)
 // Same decomposition, G = sum_{i_1} (a a^T) (x) M_{i_1}, for d' = d / R_1 <= 64,
-// where a 256-wide tile would be mostly padding.  One CTA per i_1 forms M_{i_1}
-// on the tensor cores from the segment's rows b_u = sqrt(w_u) a_2 (x) ... (x) a_N
-// (built in FP32), each split as b = b_hi + b_lo (TF32 both): with
+// where a 256-wide tile would be mostly padding.  The rows of each i_1 segment
+// are cut into pieces of at most 256 rows, and one CTA per piece forms the
+// piece's share of M_{i_1} on the tensor cores from its rows
+// b_u = sqrt(w_u) a_2 (x) ... (x) a_N (built in FP32), each split as
+// b = b_hi + b_lo (TF32 both): with
 //   A = [B_hi^T; B_lo^T] (128 x K: rows j and 64 + j),  B = B_hi^T (64 x K)
 // one M = 128, N = 64 MMA per 8 samples gives D = [B_hi^T B_hi; B_lo^T B_hi] and
 //   M[j][j'] = D[j][j'] + D[64 + j][j'] + D[64 + j'][j]
-// (the dropped B_lo^T B_lo is 2^-22 relative), so M is as accurate as an FP32
-// Gram.  The expansion by a_{r1} a_{r1'} is a small contraction over i_1
-// (I_1 R_1^2 d'^2 / 2 multiply-adds) done on the CUDA cores in FP32.
+// (the dropped B_lo^T B_lo is 2^-22 relative), as accurate as an FP32 Gram.
+// The piece's factor rows and weights are loaded into shared memory at once
+// (every load of the piece in flight together), so a piece costs about one
+// memory latency plus its MMAs, and no CTA waits on a long segment.  The
+// expansion by a_{r1} a_{r1'} is a small contraction over the pieces
+// (I_1 R_1^2 d'^2 / 2 multiply-adds and then some), done on the CUDA cores in FP32.
 constexpr int NR_THREADS = 256;
+constexpr int NR_WARPS = NR_THREADS / 32;
 constexpr int NR_KC = 32;                        // samples per chunk (128 bytes of TF32)
+constexpr int NR_PR = 256;                       // rows of one piece (8 chunks)
 constexpr int NR_OP = TC_M * TC_ROWB;            // one 128-row operand stage: 16 KB
 constexpr int NR_COLS = 64;                      // TMEM columns (N of the MMA)
-constexpr int NR_MAXE = 9;                       // table slots per thread: 32 E <= 256 * 9
 constexpr int NR_DS = 65;                        // epilogue row stride (floats)
+constexpr int NR_MAXE = 96;                      // table row: sum R_n (n >= 2) + 1 <= 3 x 32
 
 struct NarrowArgs {
   int nm;                                        // modes 2..N: nm = N - 1 of them
@@ -539,16 +546,40 @@ struct NarrowArgs {
   const uint32_t* idx[TUCKER_MAX_ORDER];
   int is64;
   const double* w;
-  const int* seg_begin;
-  const int* seg_end;
-  float* M;                                      // [I_1][dp][dp]
+  const int* prow0;                              // [pieces] first row of each piece
+  const int* prow1;                              // [pieces] end row
+  const int* npieces;                            // [1]
+  float* Mp;                                     // [pieces][dp][dp]
   int* status;
 };
 
-static size_t narrow_smem_bytes(int sumR) {
-  const size_t body = 2 * (size_t)NR_OP + (size_t)NR_KC * (sumR + 1) * 4;
+static size_t narrow_smem_bytes(int sumR, int nm) {
+  const size_t body = 2 * (size_t)NR_OP + (size_t)NR_PR * (sumR + 1) * 4 + (size_t)nm * NR_PR * 4;
   const size_t epi = (size_t)TC_M * NR_DS * 4;
   return std::max(body, epi) + 1024;
+}
+
+// Pieces of at most NR_PR rows of every i_1 segment, in order of i_1 (one CTA).
+__global__ void __launch_bounds__(1024) k_tcg_pieces(const int* seg_begin, const int* seg_end,
+                                                      int I1, int* prow0, int* prow1, int* pseg,
+                                                      int* npieces) {
+  __shared__ int64_t tmp[32];
+  int64_t carry = 0;
+  for (int base = 0; base < I1; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int b0 = i < I1 ? seg_begin[i] : 0, b1 = i < I1 ? seg_end[i] : 0;
+    const int c = (b1 - b0 + NR_PR - 1) / NR_PR;
+    int64_t tot;
+    const int64_t ex = block_exclusive_scan(c, tmp, &tot);
+    for (int k = 0; k < c; ++k) {
+      const int64_t q = carry + ex + k;
+      prow0[q] = b0 + k * NR_PR;
+      prow1[q] = min(b1, b0 + (k + 1) * NR_PR);
+      pseg[q] = i;
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *npieces = (int)carry;
 }
 
 __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
@@ -556,18 +587,15 @@ __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
   const uint32_t base_u = smem_u32(smraw);
   unsigned char* sm = smraw + ((1024 - (base_u & 1023)) & 1023);
   const int E = a.sumR + 1, dp = a.dp;
-  float* tab = reinterpret_cast<float*>(sm + 2 * NR_OP);        // [NR_KC][E]
+  float* tab = reinterpret_cast<float*>(sm + 2 * NR_OP);        // [NR_PR][E]
   __shared__ uint64_t bar_free[2], bar_done;
   __shared__ uint32_t tmem_slot;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int i1 = blockIdx.x;
-  const int b0 = a.seg_begin[i1], b1 = a.seg_end[i1];
-  const int nk = (b1 - b0 + NR_KC - 1) / NR_KC;
-  float* Mo = a.M + (size_t)i1 * dp * dp;
-  if (nk <= 0) {                                               // no sampled row has this i_1
-    for (int e = t; e < dp * dp; e += NR_THREADS) Mo[e] = 0.f;
-    return;
-  }
+  const int p = blockIdx.x;
+  if (p >= *a.npieces) return;                                 // the grid is an upper bound
+  const int b0 = a.prow0[p], b1 = a.prow1[p];
+  const int nk = (b1 - b0 + NR_KC - 1) / NR_KC;                // 1 .. NR_PR / NR_KC
+  float* Mo = a.Mp + (size_t)p * dp * dp;
   if (t == 0) {
     mbar_init(&bar_free[0], 1);
     mbar_init(&bar_free[1], 1);
@@ -579,8 +607,46 @@ __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
                  ::"r"(smem_u32(&tmem_slot)), "r"((uint32_t)NR_COLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // the table of the piece: row s (sample b0 + s) holds the factor entries of
+  // modes 2..N and sqrt(w).  Two rounds of loads: the rows' indices into shared
+  // memory (one per thread and mode), then every entry at once (lane = entry,
+  // warp = rows w + 8 i, all 32 rows of a warp in flight together).
+  {
+    uint32_t* sidx = reinterpret_cast<uint32_t*>(sm + 2 * NR_OP + (size_t)NR_PR * E * 4);
+    const int nrow = nk * NR_KC;
+    for (int q = t; q < a.nm * NR_PR; q += NR_THREADS) {
+      const int n = q / NR_PR, s = q - n * NR_PR;
+      const int u = b0 + s;
+      sidx[q] = (s < nrow && u < b1) ? __ldg(a.idx[n] + u) : 0u;
+    }
+    __syncthreads();
+    for (int z = 0; z * 32 < E; ++z) {
+      const int e = lane + 32 * z;
+      const bool on = e < E, isw = e == a.sumR;
+      int n = 0;
+      while (n + 1 < a.nm && e >= a.off[n + 1]) ++n;
+      const void* ap = a.A[n];
+      const int rn = a.R[n], rr = e - a.off[n];
+      const uint32_t* si = sidx + n * NR_PR;
+      float xv[NR_PR / NR_WARPS];
+#pragma unroll
+      for (int i = 0; i < NR_PR / NR_WARPS; ++i) {
+        const int s = warp + NR_WARPS * i, u = b0 + s;
+        float x = 0.f;
+        if (on && s < nrow && u < b1)
+          x = isw ? sqrtf((float)__ldg(a.w + u))
+                  : (float)load_as_double(ap, (int64_t)si[s] * rn + rr, a.is64);
+        xv[i] = x;
+      }
+#pragma unroll
+      for (int i = 0; i < NR_PR / NR_WARPS; ++i) {
+        const int s = warp + NR_WARPS * i;
+        if (on && s < nrow) tab[s * E + e] = xv[i];
+      }
+    }
+  }
   tc_fence_before();
-  __syncthreads();
+  __syncthreads();                                             // the table, TMEM address
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
@@ -600,43 +666,13 @@ __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
       }
     }
   }
-  // table values of chunk k: slot v = t + 256 z holds (sample v / E, entry v % E)
-  auto load_chunk = [&](int k, float* v) {
-#pragma unroll
-    for (int z = 0; z < NR_MAXE; ++z) {
-      const int q = t + NR_THREADS * z;
-      float x = 0.f;
-      if (q < NR_KC * E) {
-        const int s = q / E, e = q - s * E;
-        const int u = b0 + k * NR_KC + s;
-        if (u < b1) {
-          if (e == a.sumR) {
-            x = sqrtf((float)a.w[u]);
-          } else {
-            int n = 0;
-            while (n + 1 < a.nm && e >= a.off[n + 1]) ++n;
-            x = (float)load_as_double(a.A[n], (int64_t)a.idx[n][u] * a.R[n] + (e - a.off[n]),
-                                      a.is64);
-          }
-        }
-      }
-      v[z] = x;
-    }
-  };
-  float cur[NR_MAXE], nxt[NR_MAXE];
-  load_chunk(0, cur);
   const uint32_t id = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NR_COLS >> 3) << 17) |
                       ((uint32_t)(TC_M >> 4) << 24);           // TF32, M = 128, N = 64
   bool ok = true;
   for (int k = 0; k < nk && ok; ++k) {
     const int st = k & 1;
     unsigned char* op = sm + (size_t)st * NR_OP;
-#pragma unroll
-    for (int z = 0; z < NR_MAXE; ++z)
-      if (t + NR_THREADS * z < NR_KC * E) tab[t + NR_THREADS * z] = cur[z];
-    if (k + 1 < nk) load_chunk(k + 1, nxt);
     if (k >= 2) ok = ex_wait(&bar_free[st], ((k - 2) >> 1) & 1, a.status);  // chunk k - 2's MMAs
-    else __syncthreads();                                                   // the table
     if (!ok) break;
 #pragma unroll
     for (int h2 = 0; h2 < 2; ++h2) {
@@ -646,12 +682,12 @@ __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
         float x[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const float* row = tab + (4 * q + i) * E;
-          float p = row[a.sumR];
+          const float* row = tab + (k * NR_KC + 4 * q + i) * E;
+          float pr = row[a.sumR];
 #pragma unroll
           for (int n = 0; n < TUCKER_MAX_ORDER - 1; ++n)
-            if (n < a.nm) p *= row[eo[h2][n]];
-          x[i] = p;
+            if (n < a.nm) pr *= row[eo[h2][n]];
+          x[i] = pr;
         }
         vh.x = to_tf32(x[0]); vl.x = to_tf32(x[0] - __uint_as_float(vh.x));
         vh.y = to_tf32(x[1]); vl.y = to_tf32(x[1] - __uint_as_float(vh.y));
@@ -674,8 +710,6 @@ __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
                               (k > 0 || kk > 0) ? 1u : 0u);
       mma_commit(&bar_free[st]);
     }
-#pragma unroll
-    for (int z = 0; z < NR_MAXE; ++z) cur[z] = nxt[z];
   }
   if (t == 0) mma_commit(&bar_done);                           // tracks every MMA issued
   const bool done = ex_wait(&bar_done, 0, a.status);
@@ -714,16 +748,19 @@ __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
   }
 }
 
-// G_{(r1,j),(r2,j')} = sum_{i_1} a_{r1} a_{r2} M_{i_1}[j][j'] in FP32 on the CUDA
-// cores.  CTA: 32 entries (j <= j', the upper triangle of M in row-major order)
-// x 32 pairs (r1, r2) (pairs 32 y .. 32 y + 31); warp w sums i_1 over the w-th
-// of 16 contiguous ranges, and the 16 partials are added in a fixed order, so
+// G_{(r1,j),(r2,j')} = sum_{pieces} a_{r1} a_{r2} M_piece[j][j'] (a = A^(1) row of
+// the piece's i_1) in FP32 on the CUDA cores.  CTA: 32 entries (j <= j', the
+// upper triangle of M in row-major order) x 32 pairs (r1, r2) (pairs 32 y ..
+// 32 y + 31); warp w sums the w-th of 16 contiguous ranges of pieces, eight
+// pieces' loads in flight, and the 16 partials are added in a fixed order, so
 // the result does not depend on scheduling.  Writes each entry of G and its
 // mirror (for j = j' only the pairs r1 <= r2, so G is exactly symmetric).
 constexpr int XN_WARPS = 16;
 
 template <int R1>
-__global__ void __launch_bounds__(XN_WARPS * 32) k_tcg_expand_narrow(const float* M, int I1,
+__global__ void __launch_bounds__(XN_WARPS * 32) k_tcg_expand_narrow(const float* Mp,
+                                                                     const int* pseg,
+                                                                     const int* npieces, int I1,
                                                                      int dp, const void* A1,
                                                                      int is64, int d, double* G) {
   extern __shared__ float xs[];
@@ -744,24 +781,36 @@ __global__ void __launch_bounds__(XN_WARPS * 32) k_tcg_expand_narrow(const float
   constexpr int NP = R1 * R1 < 32 ? R1 * R1 : 32;              // pairs of this CTA
   constexpr int NR = NP / R1 > 0 ? NP / R1 : 1;                // values of r1 among them
   const int r1b = blockIdx.y * 32 / R1;
+  const int P = *npieces;
   __syncthreads();
   float acc[NP];
 #pragma unroll
   for (int c = 0; c < NP; ++c) acc[c] = 0.f;
-  const int ib = (int)((int64_t)I1 * warp / XN_WARPS), ie = (int)((int64_t)I1 * (warp + 1) / XN_WARPS);
+  const int pb = (int)((int64_t)P * warp / XN_WARPS), pe = (int)((int64_t)P * (warp + 1) / XN_WARPS);
   const size_t msz = (size_t)dp * dp;
-  const float* mp = M + (size_t)j * dp + jp;
-  for (int i = ib; i < ie; ++i) {
-    const float m = e < ne ? __ldg(mp + (size_t)i * msz) : 0.f;
-    const float* ar = a1 + i * R1;
-    float tq[R1];
+  const float* mp = Mp + (size_t)j * dp + jp;
+  for (int p0 = pb; p0 < pe; p0 += 8) {
+    float m[8];
+    int seg[8];
 #pragma unroll
-    for (int r = 0; r < R1; ++r) tq[r] = ar[r] * m;
-    float ap[NR];
+    for (int q = 0; q < 8; ++q) {
+      const int pq = p0 + q;
+      seg[q] = pq < pe ? __ldg(pseg + pq) : 0;
+      m[q] = (pq < pe && e < ne) ? __ldg(mp + (size_t)pq * msz) : 0.f;
+    }
 #pragma unroll
-    for (int r = 0; r < NR; ++r) ap[r] = ar[r1b + r];
+    for (int q = 0; q < 8; ++q) {
+      if (p0 + q >= pe) break;
+      const float* ar = a1 + seg[q] * R1;
+      float tq[R1];
 #pragma unroll
-    for (int c = 0; c < NP; ++c) acc[c] = fmaf(ap[c / R1], tq[c % R1], acc[c]);
+      for (int r = 0; r < R1; ++r) tq[r] = ar[r] * m[q];
+      float ap[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) ap[r] = ar[r1b + r];
+#pragma unroll
+      for (int c = 0; c < NP; ++c) acc[c] = fmaf(ap[c / R1], tq[c % R1], acc[c]);
+    }
   }
 #pragma unroll
   for (int c = 0; c < NP; ++c) red[(warp * 32 + c) * 32 + lane] = acc[c];
@@ -1162,9 +1211,12 @@ int gram_tc_narrow_ok(int N, int d, int R1, int64_t I1, int64_t cap) {
   return dp <= 64 && I1 >= 1 && cap >= 2 * I1 && I1 * R1 * 4 <= 96 * 1024;
 }
 
-static size_t gram_tc_narrow_bytes(int d, int R1, int64_t I1) {
+static int64_t narrow_max_pieces(int64_t I1, int64_t cap) { return I1 + (cap + NR_PR - 1) / NR_PR; }
+
+static size_t gram_tc_narrow_bytes(int d, int R1, int64_t I1, int64_t cap) {
   const int dp = d / R1;
-  return (size_t)I1 * dp * dp * 4 + 4096 + (size_t)2 * I1 * 4 + 4096;
+  const int64_t P = narrow_max_pieces(I1, cap);
+  return (size_t)P * dp * dp * 4 + 4096 + (size_t)(2 * I1 + 3 * P + 1) * 4 + 4096;
 }
 
 static size_t gram_tc_grouped_bytes(int prec, int d, int sumR, int R1, int64_t I1, int64_t cap) {
@@ -1188,7 +1240,7 @@ size_t gram_tc_workspace(tucker_handle* h, int prec, int d, int sumR, int64_t ca
   size_t b = (size_t)nch * CS * sumR * 4 + 4096 + (size_t)ns * ntiles * TC_TILE * TC_TILE * 4 + 4096;
   if (gram_tc_grouped_ok(N, d, R1, I1))
     b = std::max(b, gram_tc_grouped_bytes(prec, d, sumR, R1, I1, cap));
-  if (gram_tc_narrow_ok(N, d, R1, I1, cap)) b = std::max(b, gram_tc_narrow_bytes(d, R1, I1));
+  if (gram_tc_narrow_ok(N, d, R1, I1, cap)) b = std::max(b, gram_tc_narrow_bytes(d, R1, I1, cap));
   return b;
 }
 
@@ -1305,8 +1357,9 @@ tucker_status launch_gram_tc_grouped(tucker_handle* h, const RowSet& s, int prec
 
 // The narrow grouped Gram (sorted sample, s.idx[0] non-decreasing, d / R_1 <= 64).
 template <int R1>
-static tucker_status launch_expand_narrow(tucker_handle* h, const float* M, int I1, int dp,
-                                          const void* A1, int is64, int d, double* G) {
+static tucker_status launch_expand_narrow(tucker_handle* h, const float* Mp, const int* pseg,
+                                          const int* npieces, int I1, int dp, const void* A1,
+                                          int is64, int d, double* G) {
   const int ne = dp * (dp + 1) / 2;
   const size_t smem = (size_t)(((I1 * R1 + 3) & ~3) + XN_WARPS * 32 * 32) * 4;
   if (smem > 227 * 1024) return fail(h, TUCKER_ENOTSUP, "narrow grouped Gram: shared memory");
@@ -1314,16 +1367,18 @@ static tucker_status launch_expand_narrow(tucker_handle* h, const float* M, int 
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   TK_COUNT(h);
   k_tcg_expand_narrow<R1><<<dim3((ne + 31) / 32, (R1 * R1 + 31) / 32), XN_WARPS * 32, smem,
-                            h->stream>>>(M, I1, dp, A1, is64, d, G);
+                            h->stream>>>(Mp, pseg, npieces, I1, dp, A1, is64, d, G);
   TK_LAUNCH(h);
   return TUCKER_OK;
 }
 
-tucker_status launch_gram_tc_narrow(tucker_handle* h, const RowSet& s, int64_t I1, char* ws,
-                                    size_t ws_bytes, double* G) {
+tucker_status launch_gram_tc_narrow(tucker_handle* h, const RowSet& s, int64_t I1, int64_t cap,
+                                    char* ws, size_t ws_bytes, double* G) {
   const int R1 = s.R[0], dp = s.d / R1;
-  if (gram_tc_narrow_bytes(s.d, R1, I1) > ws_bytes)
+  if (gram_tc_narrow_bytes(s.d, R1, I1, cap) > ws_bytes)
     return fail(h, TUCKER_EINTERNAL, "narrow grouped Gram workspace too small");
+  const int64_t P = narrow_max_pieces(I1, cap);
+  if (P >= (int64_t)1 << 31) return fail(h, TUCKER_ENOTSUP, "narrow grouped Gram: %lld rows", (long long)cap);
   NarrowArgs a;
   memset(&a, 0, sizeof(a));
   a.nm = s.N - 1;
@@ -1336,37 +1391,45 @@ tucker_status launch_gram_tc_narrow(tucker_handle* h, const RowSet& s, int64_t I
     a.idx[n - 1] = s.idx[n];
   }
   a.sumR = off;
-  if (NR_KC * (a.sumR + 1) > NR_THREADS * NR_MAXE)
+  if (a.sumR + 1 > NR_MAXE)
     return fail(h, TUCKER_ENOTSUP, "narrow grouped Gram: sum of ranks %d too large", a.sumR);
   a.dp = dp;
   a.is64 = s.is64;
   a.w = s.w;
-  float* M = reinterpret_cast<float*>(ws);
-  int* seg_begin = reinterpret_cast<int*>(ws + (((size_t)I1 * dp * dp * 4 + 255) & ~size_t(255)));
+  float* Mp = reinterpret_cast<float*>(ws);
+  int* seg_begin = reinterpret_cast<int*>(ws + (((size_t)P * dp * dp * 4 + 255) & ~size_t(255)));
   int* seg_end = seg_begin + I1;
-  a.seg_begin = seg_begin;
-  a.seg_end = seg_end;
-  a.M = M;
+  int* prow0 = seg_end + I1;
+  int* prow1 = prow0 + P;
+  int* pseg = prow1 + P;
+  int* npieces = pseg + P;
+  a.prow0 = prow0;
+  a.prow1 = prow1;
+  a.npieces = npieces;
+  a.Mp = Mp;
   a.status = h->d_status;
   TK_CUDA(h, cudaMemsetAsync(seg_begin, 0, sizeof(int) * 2 * I1, h->stream));
-  int gs = (int)std::min<int64_t>(((int64_t)I1 * 64 + 255) / 256, (int64_t)h->num_sms * 8);
+  int gs = (int)std::min<int64_t>((cap + 255) / 256, (int64_t)h->num_sms * 8);
   if (gs < 1) gs = 1;
   TK_COUNT(h);
   k_tcg_segments<<<gs, 256, 0, h->stream>>>(s.idx[0], s.n_rows, seg_begin, seg_end);
   TK_LAUNCH(h);
-  const size_t smem = narrow_smem_bytes(a.sumR);
+  TK_COUNT(h);
+  k_tcg_pieces<<<1, 1024, 0, h->stream>>>(seg_begin, seg_end, (int)I1, prow0, prow1, pseg, npieces);
+  TK_LAUNCH(h);
+  const size_t smem = narrow_smem_bytes(a.sumR, a.nm);
   TK_CUDA(h, cudaFuncSetAttribute(k_tcg_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
   if (h->timing) cudaEventRecord(h->ev[10], h->stream);
   TK_COUNT(h);
-  k_tcg_narrow<<<(int)I1, NR_THREADS, smem, h->stream>>>(a);
+  k_tcg_narrow<<<(int)P, NR_THREADS, smem, h->stream>>>(a);
   TK_LAUNCH(h);
   if (h->timing) cudaEventRecord(h->ev[11], h->stream);
   switch (R1) {
-    case 2: return launch_expand_narrow<2>(h, M, (int)I1, dp, s.A[0], s.is64, s.d, G);
-    case 4: return launch_expand_narrow<4>(h, M, (int)I1, dp, s.A[0], s.is64, s.d, G);
-    case 8: return launch_expand_narrow<8>(h, M, (int)I1, dp, s.A[0], s.is64, s.d, G);
-    case 16: return launch_expand_narrow<16>(h, M, (int)I1, dp, s.A[0], s.is64, s.d, G);
+    case 2: return launch_expand_narrow<2>(h, Mp, pseg, npieces, (int)I1, dp, s.A[0], s.is64, s.d, G);
+    case 4: return launch_expand_narrow<4>(h, Mp, pseg, npieces, (int)I1, dp, s.A[0], s.is64, s.d, G);
+    case 8: return launch_expand_narrow<8>(h, Mp, pseg, npieces, (int)I1, dp, s.A[0], s.is64, s.d, G);
+    case 16: return launch_expand_narrow<16>(h, Mp, pseg, npieces, (int)I1, dp, s.A[0], s.is64, s.d, G);
     default: return fail(h, TUCKER_EINTERNAL, "narrow grouped Gram: R_1 = %d", R1);
   }
 }

@@ -9,6 +9,8 @@
 //   3. l_i = sum_{k: ev_k > tol} (a_i . v_k)^2 / ev_k, tol = max(I,R) 2^-52 ev_max
 //      (the pseudo-inverse of the Gram, eigenvalues below tol taken as zero);
 //   4. q_i = floor(clamp(l_i,0,1) 2^32) and C = inclusive prefix sum (uint64).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tk {
@@ -71,8 +73,6 @@ __global__ void __launch_bounds__(256) k_gram_partial(LevArgs a) {
 }
 
 constexpr int LEV_THREADS = 256;
-constexpr int LEV_STAGE = 4096;               // doubles of staged factor rows
-constexpr int LEV_PAIRS_PER_THREAD = (64 * 65 / 2 + LEV_THREADS - 1) / LEV_THREADS;
 
 // Cyclic Jacobi eigendecomposition of the symmetric Rp x Rp matrix G (Rp even)
 // in shared memory by one warp, with the round-robin (tournament) ordering so
@@ -148,15 +148,15 @@ __device__ void jacobi_eig_warp(double* G, double* V, int Rp, double* cs, double
 // Per mode: Gram (all warps), Jacobi eigendecomposition (warp 0, warp-
 // synchronous), and W = V diag(ev^-1/2) with the columns of eigenvalues
 // <= tol zeroed, so that l_i = || a_i W ||^2 = a_i G^+ a_i^T.
-__global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a) {
+// The body of k_leverage_eig for mode n, given the chunk partial Grams
+// gparts[ch * npairs + pidx] (global or shared memory); sm: the eigensolver's
+// scratch (2 Rp^2 + Rp doubles and Rp + 2 ints).  Every thread of the CTA calls
+// it; warp 0 does the factorisation.  W goes to a.W[n] (global).
+__device__ void lev_factor_W(const LevArgs& a, int n, const double* gparts, double* sm) {
   double* const* Wout = a.W;
-  extern __shared__ double sm[];
-  const int n = blockIdx.x;
   const int R = a.F.R[n];
   const int Rp = R + (R & 1);                 // even size for the tournament
   const int64_t I = a.F.I[n];
-  const void* A = a.F.A[n];
-  const int is64 = a.F.is64;
   double* G = sm;                             // Rp x Rp
   double* V = G + Rp * Rp;                    // Rp x Rp
   double* cs = V + Rp * Rp;                   // Rp/2 cos
@@ -171,14 +171,14 @@ __global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a) {
   }
   __syncthreads();
   // Gram = sum of the per-chunk partial Grams (fixed order)
-  (void)A; (void)is64; (void)nw; (void)wid;
+  (void)nw; (void)wid;
   const int npairs = R * (R + 1) / 2;
   for (int pidx = tid; pidx < npairs; pidx += blockDim.x) {
     int r = 0, rem = pidx;
     while (rem >= R - r) { rem -= R - r; ++r; }
     const int c = r + rem;
     double v = 0.0;
-    for (int ch = 0; ch < a.nchunk; ++ch) v += a.gpart[n][(size_t)ch * npairs + pidx];
+    for (int ch = 0; ch < a.nchunk; ++ch) v += gparts[(size_t)ch * npairs + pidx];
     G[r * Rp + c] = v;
     G[c * Rp + r] = v;
   }
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a) {
       while (rem >= R - r) { rem -= R - r; ++r; }
       const int c = r + rem;
       double v = 0.0;
-      for (int ch = 0; ch < a.nchunk; ++ch) v += a.gpart[n][(size_t)ch * npairs + pidx];
+      for (int ch = 0; ch < a.nchunk; ++ch) v += gparts[(size_t)ch * npairs + pidx];
       G[r * Rp + c] = v;
       G[c * Rp + r] = v;
     }
@@ -266,6 +266,103 @@ __global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a) {
     if (a.evals[n])
       for (int k = lane; k < R; k += 32) a.evals[n][k] = G[k * Rp + k];
   }
+}
+
+
+__global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a) {
+  extern __shared__ double sm[];
+  lev_factor_W(a, blockIdx.x, a.gpart[blockIdx.x], sm);
+}
+
+// The whole leverage pipeline of one mode in one CTA for a small factor
+// (I_n R_n <= LS_MAX_ENTRIES): the same arithmetic as k_gram_partial ->
+// k_leverage_eig -> k_leverage_rows -> k_cdf_from_lev (chunk partial Grams with
+// the same row cut and phase sums, added in chunk order; the same W; the same
+// row quadratic forms and integer prefix sums), so the scores and CDFs are
+// bit-identical to the four-launch path, without its launches and its round
+// trips through global memory.  Two groups of 256 threads take two chunks at a
+// time.
+constexpr int LS_THREADS = 512;
+constexpr int LS_MAX_ENTRIES = 8192;           // I_n R_n: 64 KB of FP64 factor rows
+
+static size_t ls_smem_doubles(int64_t I, int R, int64_t nchunk) {
+  const int Rp = R + (R & 1);
+  return (size_t)((I * R + 1) & ~int64_t(1)) + (size_t)nchunk * (R * (R + 1) / 2) + 512 +
+         (size_t)R * R + (size_t)(2 * Rp * Rp + Rp) + (size_t)(Rp + 2 + 1) / 2 + 8;
+}
+
+__global__ void __launch_bounds__(LS_THREADS) k_leverage_small(LevArgs a) {
+  extern __shared__ double lsm[];
+  const int n = blockIdx.x;
+  const int R = a.F.R[n];
+  const int64_t I = a.F.I[n];
+  const int RP = a.rows_per;
+  const int nchunk = a.nchunk;                                 // of the largest mode, as there
+  const int npairs = R * (R + 1) / 2;
+  double* Ast = lsm;                                           // I x R
+  double* parts = Ast + ((I * R + 1) & ~int64_t(1));           // [nchunk][npairs]
+  double* red = parts + (size_t)nchunk * npairs;               // [2][256]
+  double* Ws = red + 512;                                      // R x R
+  double* esm = Ws + R * R;                                    // eigensolver scratch
+  const int tid = threadIdx.x, grp = tid >> 8, gt = tid & 255;
+  for (int64_t e = tid; e < I * R; e += LS_THREADS) Ast[e] = load_as_double(a.F.A[n], e, a.F.is64);
+  __syncthreads();
+  const int phases = npairs >= 256 ? 1 : 256 / npairs;
+  for (int c0 = 0; c0 < nchunk; c0 += 2) {
+    const int ch = c0 + grp;
+    const int64_t i0 = (int64_t)ch * RP;
+    const int rows = (int)(ch < nchunk && i0 < I ? ((I - i0) < RP ? (I - i0) : RP) : 0);
+    const double* st = Ast + i0 * R;
+    double* rd = red + grp * 256;
+    for (int base = 0; base < npairs; base += 256 / phases) {
+      const int pidx = base + gt / phases, ph = gt % phases;
+      double v = 0.0;
+      if (pidx < npairs && gt / phases < 256 / phases) {
+        int r = 0, rem = pidx;
+        while (rem >= R - r) { rem -= R - r; ++r; }
+        const int c = r + rem;
+        for (int i = ph; i < rows; i += phases) v = fma(st[i * R + r], st[i * R + c], v);
+      }
+      rd[gt] = v;
+      __syncthreads();
+      if (gt < 256 / phases && ch < nchunk) {
+        const int pi = base + gt;
+        if (pi < npairs) {
+          double sum = 0.0;
+          for (int q = 0; q < phases; ++q) sum += rd[gt * phases + q];
+          parts[(size_t)ch * npairs + pi] = sum;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  lev_factor_W(a, n, parts, esm);                              // W into a.W[n]
+  __syncthreads();
+  for (int e = tid; e < R * R; e += LS_THREADS) Ws[e] = a.W[n][e];
+  __syncthreads();
+  __shared__ int64_t scan_tmp[32];
+  uint64_t carry = 0;
+  for (int64_t base = 0; base < I; base += LS_THREADS) {
+    const int64_t i = base + tid;
+    uint64_t q = 0;
+    if (i < I) {
+      const double* row = Ast + i * R;
+      double l = 0.0;
+      for (int k = 0; k < R; ++k) {
+        double p = 0.0;
+        for (int r = 0; r < R; ++r) p = fma(row[r], Ws[r * R + k], p);
+        l = fma(p, p, l);
+      }
+      a.lev[n][i] = l;
+      const double v = fmin(fmax(l, 0.0), 1.0) * 4294967296.0;
+      q = (uint64_t)__double2ull_rz(v);
+    }
+    int64_t tot;
+    const int64_t ex = block_exclusive_scan((int64_t)q, scan_tmp, &tot);
+    if (i < I) a.cdf[n][i] = carry + (uint64_t)ex + q;
+    carry += (uint64_t)tot;
+  }
+  if (tid == 0 && carry == 0) set_status(a.status, DEV_RANK);
 }
 
 // l_i = || a_i W ||^2 for every row of every mode (grid y = mode).
@@ -387,6 +484,24 @@ tucker_status launch_leverage(tucker_handle* h, const FactorSet& F, double* cons
   for (int n = 0; n < F.N; ++n) {
     a.gpart[n] = gp;
     gp += (size_t)a.nchunk * (F.R[n] * (F.R[n] + 1) / 2);
+  }
+  // small factors: the whole pipeline of each mode in one CTA (identical results)
+  {
+    bool small = maxR <= 32;
+    size_t lsm = 0;
+    for (int n = 0; n < F.N && small; ++n) {
+      small = F.I[n] * F.R[n] <= LS_MAX_ENTRIES;
+      lsm = std::max(lsm, ls_smem_doubles(F.I[n], F.R[n], a.nchunk) * sizeof(double));
+    }
+    if (small && lsm <= 200 * 1024) {
+      for (int n = 0; n < F.N; ++n) a.W[n] = W[n];
+      TK_CUDA(h, cudaFuncSetAttribute(k_leverage_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)lsm));
+      TK_COUNT(h);
+      k_leverage_small<<<F.N, LS_THREADS, lsm, h->stream>>>(a);
+      TK_LAUNCH(h);
+      return TUCKER_OK;
+    }
   }
   const size_t gsm = (size_t)(a.rows_per * maxR + 256) * sizeof(double);
   TK_CUDA(h, cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
