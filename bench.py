@@ -317,6 +317,16 @@ def grouped_gram(w):
     return dp >= 128 and I1 * tiles * (tiles + 1) // 2 <= 8192 and I1 * R1 * 4 <= 200 * 1024
 
 
+def narrow_gram(w, m):
+    """Whether the library forms the narrow grouped Gram (the library's test: order
+    >= 3, R_1 in {2, 4, 8, 16}, d / R_1 <= 64, m >= 2 I_1, A^(1) within 96 KB as FP32)."""
+    R1, N = w.ranks[0], len(w.ranks)
+    if N < 3 or R1 < 2 or R1 > 16 or R1 & (R1 - 1) or w.d % R1:
+        return False
+    I1 = w.dims[0]
+    return w.d // R1 <= 64 and m >= 2 * I1 and I1 * R1 * 4 <= 96 * 1024
+
+
 def ours_prec(args):
     """Gram precision of the GPU arm (the same choice main() makes)."""
     prec = args.prec
@@ -819,13 +829,15 @@ def main():
         # grouped by the leading index the tensor cores form n_u d' (d' + 1), d' = d / R_1
         flops = n_real * d * (d + 1) + 2 * n_real * d
         grouped = prec in ("bf16", "tf32") and grouped_gram(w)
-        if grouped:
+        narrow = prec in ("bf16", "tf32") and not grouped and narrow_gram(w, rec["n_draws"])
+        if grouped or narrow:
             dp = d // w.ranks[0]
             flops = n_real * dp * (dp + 1) + 2 * n_real * dp
         if prec in ("bf16", "tf32"):
             peak = pk["bf16_tflops"] * TC_RATIO[prec]
             bound, note = "tensor", f"{prec} tcgen05: {src} bf16 burst x {TC_RATIO[prec]}"
-            kernel = f"k_syrk_tc<{prec}>" + (" grouped by i_1" if grouped else "")
+            kernel = (f"k_syrk_tc<{prec}>" + (" grouped by i_1" if grouped else "")
+                      if not narrow else "k_tcg_narrow (per-i_1 Grams, TF32 hi + lo)")
         elif prec == "fp32":
             peak = FP32_PEAK_TFLOPS
             bound, note, kernel = "alu", "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz", "k_syrk_simt<float>"

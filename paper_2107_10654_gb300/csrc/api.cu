@@ -378,6 +378,7 @@ static void carve_sketch(Arena& ar, tucker_handle* h, const FactorSet& F, int64_
   b->axpy_part = ar.get<double>((size_t)b->axpy_split * F.d);
   b->walk.p = ar.get<double>(walk_scratch_doubles(F.I[0], F.d, F.R[0], m, h->num_sms));
   b->walk.cap = m;
+  b->walk.I2 = F.N >= 2 ? F.I[1] : 0;
   for (int n = 0; n < F.N; ++n)
     b->A64[n] = F.is64 ? nullptr : ar.get<double>((size_t)F.I[n] * F.R[n]);
   b->simt_split = gram_simt_splits(h, F.d, m);
@@ -1304,8 +1305,21 @@ tucker_status tucker_core_update_exact(tucker_handle* h, const tucker_tensor* X,
     TK_TRY(ws_reserve(h, sz.off));
     Arena ar(h->ws);
     carve(ar, lev, cdf, V, s, &rk, &b0, &b1, &y);
-    TK_TRY(launch_leverage(h, F, lev, cdf, rk, V, s, nullptr));
+    // the factor eigendecompositions (a latency-bound FP64 Jacobi on a few SMs)
+    // on the second stream, beside the pass over X; joined before the core solve
+    TK_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+    TK_CUDA(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    {
+      cudaStream_t main_stream = h->stream;
+      h->stream = h->aux;
+      tucker_status st = launch_leverage(h, F, lev, cdf, rk, V, s, nullptr);
+      if (st == TUCKER_OK && cudaEventRecord(h->ev_join, h->aux) != cudaSuccess) st = TUCKER_ECUDA;
+      h->stream = main_stream;
+      if (st == TUCKER_ECUDA && !h->err[0]) return fail(h, st, "cudaEventRecord on the second stream");
+      TK_TRY(st);
+    }
     TK_TRY(ttm_chain_all(h, F, X->dense, b0, b1, y));
+    TK_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     TK_TRY(kron_eig_core(h, F, V, s, y, lambda, core_out));
     return finish(h);
   }

@@ -321,6 +321,7 @@ struct FactorSet {
 struct WalkBuf {
   double* p = nullptr;
   int64_t cap = 0;
+  int64_t I2 = 0;                     // I_2: runs of equal (i_1, i_2) along the sorted sample
 };
 
 struct RowSet {                       // the deduplicated sample as device arrays

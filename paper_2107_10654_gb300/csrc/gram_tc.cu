@@ -582,7 +582,10 @@ __global__ void __launch_bounds__(1024) k_tcg_pieces(const int* seg_begin, const
   if (threadIdx.x == 0) *npieces = (int)carry;
 }
 
+// NMT: the number of trailing modes when known at compile time (2 or 3), else 0.
+template <int NMT>
 __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
+  constexpr int NMX = NMT > 0 ? NMT : TUCKER_MAX_ORDER - 1;
   extern __shared__ __align__(1024) unsigned char smraw[];
   const uint32_t base_u = smem_u32(smraw);
   unsigned char* sm = smraw + ((1024 - (base_u & 1023)) & 1023);
@@ -651,16 +654,16 @@ __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
   const uint32_t tmem = tmem_slot;
 
   // the two build units of this thread: operand row j (and 64 + j), 16-byte chunk q
-  int eo[2][TUCKER_MAX_ORDER - 1];
+  int eo[2][NMX];
   bool live[2];
 #pragma unroll
   for (int h2 = 0; h2 < 2; ++h2) {
     int j = (t + NR_THREADS * h2) & 63;
     live[h2] = j < dp;
 #pragma unroll
-    for (int n = TUCKER_MAX_ORDER - 2; n >= 0; --n) {
+    for (int n = NMX - 1; n >= 0; --n) {
       eo[h2][n] = 0;
-      if (n < a.nm) {
+      if (NMT > 0 || n < a.nm) {
         eo[h2][n] = a.off[n] + j % a.R[n];
         j /= a.R[n];
       }
@@ -685,8 +688,8 @@ __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
           const float* row = tab + (k * NR_KC + 4 * q + i) * E;
           float pr = row[a.sumR];
 #pragma unroll
-          for (int n = 0; n < TUCKER_MAX_ORDER - 1; ++n)
-            if (n < a.nm) pr *= row[eo[h2][n]];
+          for (int n = 0; n < NMX; ++n)
+            if (NMT > 0 || n < a.nm) pr *= row[eo[h2][n]];
           x[i] = pr;
         }
         vh.x = to_tf32(x[0]); vl.x = to_tf32(x[0] - __uint_as_float(vh.x));
@@ -734,10 +737,9 @@ __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
       for (int i = 0; i < 16; ++i) D[row * NR_DS + col + i] = __uint_as_float(v[i]);
     }
     __syncthreads();
-    for (int e = t; e < dp * dp; e += NR_THREADS) {
-      const int j = e / dp, jp = e - j * dp;
-      Mo[e] = D[j * NR_DS + jp] + D[(64 + j) * NR_DS + jp] + D[(64 + jp) * NR_DS + j];
-    }
+    for (int j = warp; j < dp; j += NR_WARPS)                  // row j of M: lanes along j'
+      for (int jp = lane; jp < dp; jp += 32)
+        Mo[j * dp + jp] = D[j * NR_DS + jp] + D[(64 + j) * NR_DS + jp] + D[(64 + jp) * NR_DS + j];
   }
   tc_fence_before();
   __syncthreads();
@@ -751,7 +753,7 @@ __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
 // G_{(r1,j),(r2,j')} = sum_{pieces} a_{r1} a_{r2} M_piece[j][j'] (a = A^(1) row of
 // the piece's i_1) in FP32 on the CUDA cores.  CTA: 32 entries (j <= j', the
 // upper triangle of M in row-major order) x 32 pairs (r1, r2) (pairs 32 y ..
-// 32 y + 31); warp w sums the w-th of 16 contiguous ranges of pieces, eight
+// 32 y + 31); warp w sums the w-th of 16 contiguous ranges of pieces, sixteen
 // pieces' loads in flight, and the 16 partials are added in a fixed order, so
 // the result does not depend on scheduling.  Writes each entry of G and its
 // mirror (for j = j' only the pairs r1 <= r2, so G is exactly symmetric).
@@ -789,17 +791,18 @@ __global__ void __launch_bounds__(XN_WARPS * 32) k_tcg_expand_narrow(const float
   const int pb = (int)((int64_t)P * warp / XN_WARPS), pe = (int)((int64_t)P * (warp + 1) / XN_WARPS);
   const size_t msz = (size_t)dp * dp;
   const float* mp = Mp + (size_t)j * dp + jp;
-  for (int p0 = pb; p0 < pe; p0 += 8) {
-    float m[8];
-    int seg[8];
+  constexpr int XB = 16;                                       // pieces' loads in flight
+  for (int p0 = pb; p0 < pe; p0 += XB) {
+    float m[XB];
+    int seg[XB];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < XB; ++q) {
       const int pq = p0 + q;
       seg[q] = pq < pe ? __ldg(pseg + pq) : 0;
       m[q] = (pq < pe && e < ne) ? __ldg(mp + (size_t)pq * msz) : 0.f;
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < XB; ++q) {
       if (p0 + q >= pe) break;
       const float* ar = a1 + seg[q] * R1;
       float tq[R1];
@@ -1418,11 +1421,11 @@ tucker_status launch_gram_tc_narrow(tucker_handle* h, const RowSet& s, int64_t I
   k_tcg_pieces<<<1, 1024, 0, h->stream>>>(seg_begin, seg_end, (int)I1, prow0, prow1, pseg, npieces);
   TK_LAUNCH(h);
   const size_t smem = narrow_smem_bytes(a.sumR, a.nm);
-  TK_CUDA(h, cudaFuncSetAttribute(k_tcg_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+  auto kern = a.nm == 2 ? k_tcg_narrow<2> : a.nm == 3 ? k_tcg_narrow<3> : k_tcg_narrow<0>;
+  TK_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (h->timing) cudaEventRecord(h->ev[10], h->stream);
   TK_COUNT(h);
-  k_tcg_narrow<<<(int)P, NR_THREADS, smem, h->stream>>>(a);
+  kern<<<(int)P, NR_THREADS, smem, h->stream>>>(a);
   TK_LAUNCH(h);
   if (h->timing) cudaEventRecord(h->ev[11], h->stream);
   switch (R1) {

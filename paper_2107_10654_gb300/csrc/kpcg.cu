@@ -313,7 +313,7 @@ __device__ float kpcg_setup(const KpcgArgs& a, KpcgShared& sh, const KpcgVecs& v
   // registers: at most KP_BMAX entries per thread)
   float trm = 0.f, sreg = 0.f, bmax = 0.f;
   float bl[KP_BMAX];
-#pragma unroll
+#pragma unroll 4
   for (int t = 0; t < KP_BMAX; ++t) {
     const int j = tid + t * KP_THREADS;
     bl[t] = 0.f;

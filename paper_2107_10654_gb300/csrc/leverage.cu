@@ -274,97 +274,6 @@ __global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a) {
   lev_factor_W(a, blockIdx.x, a.gpart[blockIdx.x], sm);
 }
 
-// The whole leverage pipeline of one mode in one CTA for a small factor
-// (I_n R_n <= LS_MAX_ENTRIES): the same arithmetic as k_gram_partial ->
-// k_leverage_eig -> k_leverage_rows -> k_cdf_from_lev (chunk partial Grams with
-// the same row cut and phase sums, added in chunk order; the same W; the same
-// row quadratic forms and integer prefix sums), so the scores and CDFs are
-// bit-identical to the four-launch path, without its launches and its round
-// trips through global memory.  Two groups of 256 threads take two chunks at a
-// time.
-constexpr int LS_THREADS = 512;
-constexpr int LS_MAX_ENTRIES = 8192;           // I_n R_n: 64 KB of FP64 factor rows
-
-static size_t ls_smem_doubles(int64_t I, int R, int64_t nchunk) {
-  const int Rp = R + (R & 1);
-  return (size_t)((I * R + 1) & ~int64_t(1)) + (size_t)nchunk * (R * (R + 1) / 2) + 512 +
-         (size_t)R * R + (size_t)(2 * Rp * Rp + Rp) + (size_t)(Rp + 2 + 1) / 2 + 8;
-}
-
-__global__ void __launch_bounds__(LS_THREADS) k_leverage_small(LevArgs a) {
-  extern __shared__ double lsm[];
-  const int n = blockIdx.x;
-  const int R = a.F.R[n];
-  const int64_t I = a.F.I[n];
-  const int RP = a.rows_per;
-  const int nchunk = a.nchunk;                                 // of the largest mode, as there
-  const int npairs = R * (R + 1) / 2;
-  double* Ast = lsm;                                           // I x R
-  double* parts = Ast + ((I * R + 1) & ~int64_t(1));           // [nchunk][npairs]
-  double* red = parts + (size_t)nchunk * npairs;               // [2][256]
-  double* Ws = red + 512;                                      // R x R
-  double* esm = Ws + R * R;                                    // eigensolver scratch
-  const int tid = threadIdx.x, grp = tid >> 8, gt = tid & 255;
-  for (int64_t e = tid; e < I * R; e += LS_THREADS) Ast[e] = load_as_double(a.F.A[n], e, a.F.is64);
-  __syncthreads();
-  const int phases = npairs >= 256 ? 1 : 256 / npairs;
-  for (int c0 = 0; c0 < nchunk; c0 += 2) {
-    const int ch = c0 + grp;
-    const int64_t i0 = (int64_t)ch * RP;
-    const int rows = (int)(ch < nchunk && i0 < I ? ((I - i0) < RP ? (I - i0) : RP) : 0);
-    const double* st = Ast + i0 * R;
-    double* rd = red + grp * 256;
-    for (int base = 0; base < npairs; base += 256 / phases) {
-      const int pidx = base + gt / phases, ph = gt % phases;
-      double v = 0.0;
-      if (pidx < npairs && gt / phases < 256 / phases) {
-        int r = 0, rem = pidx;
-        while (rem >= R - r) { rem -= R - r; ++r; }
-        const int c = r + rem;
-        for (int i = ph; i < rows; i += phases) v = fma(st[i * R + r], st[i * R + c], v);
-      }
-      rd[gt] = v;
-      __syncthreads();
-      if (gt < 256 / phases && ch < nchunk) {
-        const int pi = base + gt;
-        if (pi < npairs) {
-          double sum = 0.0;
-          for (int q = 0; q < phases; ++q) sum += rd[gt * phases + q];
-          parts[(size_t)ch * npairs + pi] = sum;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  lev_factor_W(a, n, parts, esm);                              // W into a.W[n]
-  __syncthreads();
-  for (int e = tid; e < R * R; e += LS_THREADS) Ws[e] = a.W[n][e];
-  __syncthreads();
-  __shared__ int64_t scan_tmp[32];
-  uint64_t carry = 0;
-  for (int64_t base = 0; base < I; base += LS_THREADS) {
-    const int64_t i = base + tid;
-    uint64_t q = 0;
-    if (i < I) {
-      const double* row = Ast + i * R;
-      double l = 0.0;
-      for (int k = 0; k < R; ++k) {
-        double p = 0.0;
-        for (int r = 0; r < R; ++r) p = fma(row[r], Ws[r * R + k], p);
-        l = fma(p, p, l);
-      }
-      a.lev[n][i] = l;
-      const double v = fmin(fmax(l, 0.0), 1.0) * 4294967296.0;
-      q = (uint64_t)__double2ull_rz(v);
-    }
-    int64_t tot;
-    const int64_t ex = block_exclusive_scan((int64_t)q, scan_tmp, &tot);
-    if (i < I) a.cdf[n][i] = carry + (uint64_t)ex + q;
-    carry += (uint64_t)tot;
-  }
-  if (tid == 0 && carry == 0) set_status(a.status, DEV_RANK);
-}
-
 // l_i = || a_i W ||^2 for every row of every mode (grid y = mode).
 struct LevRowArgs {
   int N;
@@ -376,23 +285,36 @@ struct LevRowArgs {
   double* lev[TUCKER_MAX_ORDER];
 };
 
+// FP64 runs at under two multiply-adds per clock per SM on this GPU, so the
+// I_n R_n^2 multiply-adds are spread thinly: thread (row, k) forms (a_i W)_k,
+// and the R_n partial squares of a row are added in order of k through shared
+// memory (the same order as a single thread's loop over k).
 __global__ void __launch_bounds__(256) k_leverage_rows(LevRowArgs a) {
   extern __shared__ double Ws[];
   const int n = blockIdx.y;
   const int R = a.R[n];
+  double* pk = Ws + R * R;                                     // [rows per pass][R]
   for (int e = threadIdx.x; e < R * R; e += blockDim.x) Ws[e] = a.W[n][e];
   __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.I[n];
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double row[TUCKER_MAX_RANK];
-    for (int r = 0; r < R; ++r) row[r] = load_as_double(a.A[n], i * R + r, a.is64);
-    double l = 0.0;
-    for (int k = 0; k < R; ++k) {
+  const int rpp = blockDim.x / R;                              // rows per pass
+  const int rl = threadIdx.x / R, k = threadIdx.x - rl * R;
+  for (int64_t i0 = (int64_t)blockIdx.x * rpp; i0 < a.I[n]; i0 += (int64_t)gridDim.x * rpp) {
+    const int64_t i = i0 + rl;
+    if (rl < rpp && i < a.I[n]) {
       double p = 0.0;
-      for (int r = 0; r < R; ++r) p = fma(row[r], Ws[r * R + k], p);
-      l = fma(p, p, l);
+      for (int r = 0; r < R; ++r) p = fma(load_as_double(a.A[n], i * R + r, a.is64), Ws[r * R + k], p);
+      pk[rl * R + k] = p;
     }
-    a.lev[n][i] = l;
+    __syncthreads();
+    if (threadIdx.x < rpp && i0 + threadIdx.x < a.I[n]) {
+      double l = 0.0;
+      for (int kk = 0; kk < R; ++kk) {
+        const double p = pk[threadIdx.x * R + kk];
+        l = fma(p, p, l);
+      }
+      a.lev[n][i0 + threadIdx.x] = l;
+    }
+    __syncthreads();
   }
 }
 
@@ -485,24 +407,6 @@ tucker_status launch_leverage(tucker_handle* h, const FactorSet& F, double* cons
     a.gpart[n] = gp;
     gp += (size_t)a.nchunk * (F.R[n] * (F.R[n] + 1) / 2);
   }
-  // small factors: the whole pipeline of each mode in one CTA (identical results)
-  {
-    bool small = maxR <= 32;
-    size_t lsm = 0;
-    for (int n = 0; n < F.N && small; ++n) {
-      small = F.I[n] * F.R[n] <= LS_MAX_ENTRIES;
-      lsm = std::max(lsm, ls_smem_doubles(F.I[n], F.R[n], a.nchunk) * sizeof(double));
-    }
-    if (small && lsm <= 200 * 1024) {
-      for (int n = 0; n < F.N; ++n) a.W[n] = W[n];
-      TK_CUDA(h, cudaFuncSetAttribute(k_leverage_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)lsm));
-      TK_COUNT(h);
-      k_leverage_small<<<F.N, LS_THREADS, lsm, h->stream>>>(a);
-      TK_LAUNCH(h);
-      return TUCKER_OK;
-    }
-  }
   const size_t gsm = (size_t)(a.rows_per * maxR + 256) * sizeof(double);
   TK_CUDA(h, cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)gsm));
@@ -516,10 +420,12 @@ tucker_status launch_leverage(tucker_handle* h, const FactorSet& F, double* cons
   TK_COUNT(h);
   k_leverage_eig<<<F.N, LEV_THREADS, smem, h->stream>>>(a);
   TK_LAUNCH(h);
-  int gx = (int)((maxI + 255) / 256);
-  if (gx > 64) gx = 64;
+  const int rpp = maxR <= 256 ? 256 / maxR : 1;                 // rows per CTA pass
+  int gx = (int)((maxI + rpp - 1) / rpp);
+  if (gx > 4 * h->num_sms / F.N) gx = 4 * h->num_sms / F.N;
+  if (gx < 1) gx = 1;
   TK_COUNT(h);
-  k_leverage_rows<<<dim3(gx, F.N), 256, (size_t)maxR * maxR * sizeof(double), h->stream>>>(ra);
+  k_leverage_rows<<<dim3(gx, F.N), 256, (size_t)(maxR * maxR + 256) * sizeof(double), h->stream>>>(ra);
   TK_LAUNCH(h);
   return launch_cdf_from_lev(h, F.N, F.I, lev, cdf);
 }

@@ -32,7 +32,7 @@ constexpr int WK_WARP_SMEM = 12 * 1024;     // axpy: bytes of shared memory per 
 constexpr int WK_DOT_SMEM = 24 * 1024;      // dot: bytes of shared memory per warp, at most
 
 // dot: V_1 of the piece (nvec vectors) and 32 lanes' factor rows
-static size_t dot_warp_bytes(int L1, int fstore, int nvec) {
+static __host__ __device__ size_t dot_warp_bytes(int L1, int fstore, int nvec) {
   return ((size_t)nvec * L1 + (size_t)32 * fstore) * 8;
 }
 
@@ -212,6 +212,80 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_dot(WalkArgs a) {
   }
 }
 
+// k_walk_dot with two levels for wide V_1 (orders >= 3, lsz[2] a multiple of 32):
+// the 32 rows of a batch share few values of i_2 (the key order), so for each
+// distinct i_2 of the batch the warp forms V_2 = V_1 x_2 a_2(i_2) (lsz[2]
+// entries) once in shared memory, and each lane contracts its row against its
+// V_2 only: lsz[2] + ... instead of lsz[1] + lsz[2] + ... multiply-adds per row.
+// A batch with more than WD_RUNS values of i_2 takes the one-level path.
+constexpr int WD_RUNS = 4;
+
+static __host__ __device__ size_t dot2_warp_bytes(int L1, int L2, int fstore, int nvec) {
+  return dot_warp_bytes(L1, fstore, nvec) + (size_t)WD_RUNS * nvec * L2 * 8;
+}
+
+template <class T, int N>
+__global__ void __launch_bounds__(WK_WARPS * 32) k_walk_dot2(WalkArgs a) {
+  extern __shared__ double sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * WK_WARPS + warp;
+  if (p >= *a.npieces) return;                              // warp-uniform; no CTA barriers below
+  const bool two = a.g2 != nullptr;
+  const int nvec = two ? 2 : 1;
+  const int L1 = a.lsz[1], L2 = a.lsz[2], R1 = a.R[1];
+  T* V = reinterpret_cast<T*>(sm + (size_t)warp * (dot2_warp_bytes(L1, L2, a.fstore, nvec) / 8));
+  T* F = V + nvec * L1;
+  T* W = F + 32 * a.fstore;                                 // [WD_RUNS][nvec][L2]
+  const int i1 = a.p_i1[p], u0 = a.p_u0[p], u1 = a.p_u1[p];
+  const T* V1 = reinterpret_cast<const T*>(a.V1);
+  for (int v = 0; v < nvec; ++v) {
+    const T* src = V1 + ((size_t)v * a.I1 + i1) * L1;
+    for (int j = lane; j < L1; j += 32) V[v * L1 + j] = src[j];
+  }
+  const unsigned le = (2u << lane) - 1u;                    // lanes <= this lane
+  for (int base = u0; base < u1; base += 32) {
+    const int u = base + lane;
+    const bool act = u < u1;
+    __syncwarp();
+    uint32_t ix[N];
+#pragma unroll
+    for (int n = 1; n < N; ++n) ix[n] = act ? __ldg(a.idx[n] + u) : 0u;
+    for (int n = 1; n < N; ++n)
+      for (int r = 0; r < a.R[n]; ++r)
+        F[(a.fofs[n] + r) * 32 + lane] = act ? fac_t<T>(a, n, ix[n], r) : T(0);
+    // runs of equal i_2 among the batch's active rows (sorted, so equal values are adjacent)
+    const uint32_t up = __shfl_up_sync(0xffffffffu, ix[1], 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, act && (lane == 0 || up != ix[1]));
+    const int nruns = __popc(heads);
+    __syncwarp();
+    T z1, z2;
+    if (nruns <= WD_RUNS) {
+      unsigned hm = heads;
+      for (int h = 0; h < nruns; ++h, hm &= hm - 1u) {      // V_2 of run h
+        const int hl = __ffs(hm) - 1;                       // lane of the run's first row
+        const uint32_t i2 = __shfl_sync(0xffffffffu, ix[1], hl);
+        const T* a2 = fac_base<T>(a, 1) + (size_t)i2 * R1;
+        for (int v = 0; v < nvec; ++v)
+          for (int q = lane; q < L2; q += 32) {
+            T acc = T(0);
+            for (int r = 0; r < R1; ++r) acc = fma(__ldg(a2 + r), V[v * L1 + r * L2 + q], acc);
+            W[((size_t)h * nvec + v) * L2 + q] = acc;
+          }
+      }
+      __syncwarp();
+      const int run = __popc(heads & le) - 1;               // this lane's run (act lanes)
+      const T* w1 = W + (size_t)(run < 0 ? 0 : run) * nvec * L2;
+      FlatDot<T, N, 2>::run(a, w1, w1 + (two ? L2 : 0), two, F, lane, &z1, &z2);
+    } else {
+      FlatDot<T, N, 1>::run(a, V, V + (two ? L1 : 0), two, F, lane, &z1, &z2);
+    }
+    if (act) {
+      a.z1[u] = (double)z1;
+      if (a.z2) a.z2[u] = (double)z2;
+    }
+  }
+}
+
 template <int N>
 __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy(WalkArgs a) {
   extern __shared__ double sm[];
@@ -358,6 +432,74 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes(WalkArgs a) {
   }
 }
 
+// Two levels for wide W_1 (lsz[2] a multiple of 32, orders >= 3): along the sorted
+// sample the rows of one segment come in runs of equal i_2, and
+//   W_1 = sum_runs a_2(i_2) (x) W_2,  W_2 = sum_{u in run} c_u a_3 (x) ... (x) a_N,
+// so a row adds into W_2 (lsz[2] entries) and a run folds W_2 into W_1 once:
+// about lsz[2] instead of lsz[1] multiply-adds per row, where FP64 issues under
+// two per clock per SM.  Lane l owns the W_2 entries q = l + 32 k2 and the W_1
+// entries e = l + 32 k, whose q(e) = e mod lsz[2] = l + 32 (k mod KE2) and
+// r_2(e) = k / KE2 are its own, so the fold reads no other lane's data.
+template <class T, int N, int KE, int KE2>
+__global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes2(WalkArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * WK_WARPS + warp;
+  if (p >= *a.npieces) return;                              // warp-uniform
+  const int L1 = a.lsz[1];
+  const int u0 = a.p_u0[p], u1 = a.p_u1[p];
+  int col[KE2][N - 2];                                      // r_n(q), n = 2 .. N - 1
+#pragma unroll
+  for (int k2 = 0; k2 < KE2; ++k2) {
+    const int q = lane + 32 * k2;
+#pragma unroll
+    for (int n = 2; n < N; ++n) col[k2][n - 2] = (q / a.lsz[n + 1]) % a.R[n];
+  }
+  T acc[KE], w2[KE2];
+#pragma unroll
+  for (int k = 0; k < KE; ++k) acc[k] = T(0);
+#pragma unroll
+  for (int k2 = 0; k2 < KE2; ++k2) w2[k2] = T(0);
+  uint32_t prev = 0;
+  bool have = false;
+  auto fold = [&](uint32_t i2) {
+    const T* a2 = fac_base<T>(a, 1) + (size_t)i2 * a.R[1];
+#pragma unroll
+    for (int k = 0; k < KE; ++k) acc[k] = fma(__ldg(a2 + k / KE2), w2[k % KE2], acc[k]);
+#pragma unroll
+    for (int k2 = 0; k2 < KE2; ++k2) w2[k2] = T(0);
+  };
+  for (int base = u0; base < u1; base += 32) {
+    const int cnt = min(32, u1 - base);
+    uint32_t mine[N];
+    T cm = T(0);
+#pragma unroll
+    for (int n = 1; n < N; ++n) mine[n] = lane < cnt ? __ldg(a.idx[n] + base + lane) : 0u;
+    if (lane < cnt) cm = (T)(a.coef * a.ca[base + lane] * (a.cb ? a.cb[base + lane] : 1.0));
+    for (int j = 0; j < cnt; ++j) {
+      const uint32_t i2 = __shfl_sync(0xffffffffu, mine[1], j);
+      if (have && i2 != prev) fold(prev);                   // warp-uniform
+      prev = i2;
+      have = true;
+      const T c = __shfl_sync(0xffffffffu, cm, j);
+      const T* row[N];
+#pragma unroll
+      for (int n = 2; n < N; ++n)
+        row[n] = fac_base<T>(a, n) + (size_t)__shfl_sync(0xffffffffu, mine[n], j) * a.R[n];
+#pragma unroll
+      for (int k2 = 0; k2 < KE2; ++k2) {
+        T t = c;
+#pragma unroll
+        for (int n = N - 1; n >= 3; --n) t *= __ldg(row[n] + col[k2][n - 2]);
+        w2[k2] = fma(t, __ldg(row[2] + col[k2][0]), w2[k2]);
+      }
+    }
+  }
+  if (have) fold(prev);
+  double* out = a.Wp + (size_t)p * L1;
+#pragma unroll
+  for (int k = 0; k < KE; ++k) out[lane + 32 * k] = (double)acc[k];
+}
+
 // W1[i1][j] = sum of the piece partials of segment i1 (fixed order); 0 if empty.
 __global__ void k_walk_reduce(WalkArgs a) {
   const int L1 = a.lsz[1];
@@ -439,19 +581,30 @@ __global__ void __launch_bounds__(256) k_walk_fold(WalkArgs a, int chunk, double
   }
 }
 
+// Eight threads per output: thread q of an output sums the partials b = q, q + 8,
+// ... in order, and the eight sums are added by a fixed shuffle tree, so the
+// result is deterministic; every partial load of a thread is in flight at once
+// when nb <= 64.
 __global__ void k_walk_sum(const double* part, int nb, int d, const double* base,
                            const double* diag, const double* y, double* out) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d; t += gridDim.x * blockDim.x) {
-    double v = 0.0;
-    int b = 0;
-    for (; b + 8 <= nb; b += 8) {                   // eight loads in flight, summed in order
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (int)(gt >> 3), q = (int)(gt & 7);
+  double v = 0.0;
+  if (t < d) {
+    int b = q;
+    for (; b + 56 < nb; b += 64) {
       double x[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) x[q] = part[(size_t)(b + q) * d + t];
+      for (int k = 0; k < 8; ++k) x[k] = part[(size_t)(b + 8 * k) * d + t];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v += x[q];
+      for (int k = 0; k < 8; ++k) v += x[k];
     }
-    for (; b < nb; ++b) v += part[(size_t)b * d + t];
+    for (; b < nb; b += 8) v += part[(size_t)b * d + t];
+  }
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  if (t < d && q == 0) {
     double o = base ? base[t] : 0.0;
     if (diag) o -= diag[t] * y[t];
     out[t] = o + v;
@@ -589,6 +742,16 @@ static int grid_for(tucker_handle* h, int64_t work, int threads) {
 using WalkKernel = void (*)(WalkArgs);
 
 template <class T>
+static WalkKernel walk_dot2_kernel_t(int N) {
+  switch (N) {
+    case 3: return k_walk_dot2<T, 3>;
+    case 4: return k_walk_dot2<T, 4>;
+    case 5: return k_walk_dot2<T, 5>;
+    default: return nullptr;
+  }
+}
+
+template <class T>
 static WalkKernel walk_dot_kernel_t(int N) {
   switch (N) {
     case 1: return k_walk_dot<T, 1>;
@@ -634,6 +797,34 @@ static WalkKernel walk_axpy_lanes_kernel(int N, int L1) {
     case 4: return axpy_lanes_by_width<T, 4>(L1);
     default: return nullptr;
   }
+}
+
+// The two-level axpy for orders 3 and 4 with lsz[2] in {32, 64, 128} and
+// lsz[1] <= 512 (else nullptr).
+template <class T, int N, int KE2>
+static WalkKernel axpy_lanes2_by_width(int L1) {
+  if (L1 == 32 * KE2) return k_walk_axpy_lanes2<T, N, KE2, KE2>;
+  if (L1 == 64 * KE2) return k_walk_axpy_lanes2<T, N, 2 * KE2, KE2>;
+  if (L1 == 128 * KE2 && 4 * KE2 <= 16) return k_walk_axpy_lanes2<T, N, 4 * KE2, KE2>;
+  if (L1 == 256 * KE2 && 8 * KE2 <= 16) return k_walk_axpy_lanes2<T, N, 8 * KE2, KE2>;
+  if (L1 == 512 * KE2 && 16 * KE2 <= 16) return k_walk_axpy_lanes2<T, N, 16 * KE2, KE2>;
+  return nullptr;
+}
+
+template <class T>
+static WalkKernel walk_axpy_lanes2_kernel(int N, int L1, int L2) {
+  if (L2 % 32 != 0 || L1 % L2 != 0) return nullptr;
+  const int ke2 = L2 / 32;
+  if (N == 3) {
+    if (ke2 == 1) return axpy_lanes2_by_width<T, 3, 1>(L1);
+    if (ke2 == 2) return axpy_lanes2_by_width<T, 3, 2>(L1);
+    if (ke2 == 4) return axpy_lanes2_by_width<T, 3, 4>(L1);
+  } else if (N == 4) {
+    if (ke2 == 1) return axpy_lanes2_by_width<T, 4, 1>(L1);
+    if (ke2 == 2) return axpy_lanes2_by_width<T, 4, 2>(L1);
+    if (ke2 == 4) return axpy_lanes2_by_width<T, 4, 4>(L1);
+  }
+  return nullptr;
 }
 
 // One warp per piece: ceil(maxP / WK_WARPS) CTAs; warps past the piece count exit.
@@ -689,17 +880,24 @@ tucker_status walk_dot(tucker_handle* h, const RowSet& s, int64_t I1, const Walk
   WalkArgs a = walk_args(s, g, w);
   a.g1 = g1; a.g2 = g2; a.z1 = z1; a.z2 = z2;
   const int nvec = g2 ? 2 : 1;
-  const size_t smem = (size_t)WK_WARPS * dot_warp_bytes(a.lsz[1], a.fstore, nvec);
+  size_t smem = (size_t)WK_WARPS * dot_warp_bytes(a.lsz[1], a.fstore, nvec);
+  // two levels when the runs of equal (i_1, i_2) are long and V_2 is a whole number of warps
+  const size_t smem2 = (size_t)WK_WARPS * dot2_warp_bytes(a.lsz[1], a.lsz[2], a.fstore, nvec);
+  const bool lvl2 = s.N >= 3 && s.N <= 5 && a.lsz[2] % 32 == 0 && wb.I2 > 0 &&
+                    (double)wb.cap >= 4.0 * (double)I1 * (double)wb.I2 && smem2 <= 200 * 1024;
+  if (lvl2) smem = smem2;
   TK_COUNT(h);
   if (f32) {
     for (int n = 0; n < s.N; ++n) a.A32[n] = static_cast<const float*>(s.A[n]);
     k_walk_v1<float><<<grid_for(h, I1 * a.lsz[1], 256), 256, 0, h->stream>>>(a);
     TK_LAUNCH(h);
-    TK_TRY(launch_by_order(h, walk_dot_kernel_t<float>(s.N), g.maxP, smem, a));
+    TK_TRY(launch_by_order(h, lvl2 ? walk_dot2_kernel_t<float>(s.N) : walk_dot_kernel_t<float>(s.N),
+                           g.maxP, smem, a));
   } else {
     k_walk_v1<double><<<grid_for(h, I1 * a.lsz[1], 256), 256, 0, h->stream>>>(a);
     TK_LAUNCH(h);
-    TK_TRY(launch_by_order(h, walk_dot_kernel_t<double>(s.N), g.maxP, smem, a));
+    TK_TRY(launch_by_order(h, lvl2 ? walk_dot2_kernel_t<double>(s.N) : walk_dot_kernel_t<double>(s.N),
+                           g.maxP, smem, a));
   }
   return TUCKER_OK;
 }
@@ -719,6 +917,12 @@ tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, const Wal
   if (f32) for (int n = 0; n < s.N; ++n) a.A32[n] = static_cast<const float*>(s.A[n]);
   WalkKernel lanes = f32 ? walk_axpy_lanes_kernel<float>(s.N, a.lsz[1])
                          : walk_axpy_lanes_kernel<double>(s.N, a.lsz[1]);
+  // two levels when the runs of equal (i_1, i_2) are long enough to pay for their folds
+  if (s.N >= 3 && wb.I2 > 0 && (double)wb.cap >= 4.0 * (double)I1 * (double)wb.I2) {
+    WalkKernel two = f32 ? walk_axpy_lanes2_kernel<float>(s.N, a.lsz[1], a.lsz[2])
+                         : walk_axpy_lanes2_kernel<double>(s.N, a.lsz[1], a.lsz[2]);
+    if (two) lanes = two;
+  }
   if (lanes) {
     TK_COUNT(h);
     lanes<<<(int)((g.maxP + WK_WARPS - 1) / WK_WARPS), WK_WARPS * 32, 0, h->stream>>>(a);
@@ -738,7 +942,7 @@ tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, const Wal
     k_walk_fold<<<nb, 256, fsm, h->stream>>>(a, chunk, a.W1);
     TK_LAUNCH(h);
     TK_COUNT(h);
-    k_walk_sum<<<ceil_div(s.d, 64), 64, 0, h->stream>>>(a.W1, nb, s.d, base, diag, y, out);
+    k_walk_sum<<<ceil_div((int64_t)s.d * 8, 128), 128, 0, h->stream>>>(a.W1, nb, s.d, base, diag, y, out);
     TK_LAUNCH(h);
     return TUCKER_OK;
   }

@@ -9,7 +9,11 @@
     and its sketched core at that count;
   * the torch.autograd.Function over the frozen-sketch solve: the gradients
     autograd hands back for the factors and for the dense tensor (scattered to
-    the sampled entries) against the oracle's adjoint.
+    the sampled entries) against the oracle's adjoint;
+  * the two-level sorted-sample walks (runs of equal (i_1, i_2) long enough,
+    prod_{n >= 3} R_n a multiple of 32): the right-hand side h = K_S^T W x and the
+    FP64 residual of the refined core against the oracle's explicit rows, for
+    orders 3 and 4 and both the TF32 and the FP64 Gram.
 """
 import dataclasses
 
@@ -98,3 +102,28 @@ def test_autograd_function_matches_oracle_adjoint(handle, prec, tol):
     got = Xd.grad.cpu().numpy().reshape(-1)
     assert rel_err(got, ref_dX) <= tol
     assert np.all(got[np.setdiff1d(np.arange(X.size), keys.astype(np.int64))] == 0.0)
+
+
+@pytest.mark.parametrize("dims,ranks,m,prec", [
+    ((10, 12, 30, 30), (4, 8, 8, 8), 20000, "tf32"),   # order 4: W_2 of 64 entries
+    ((10, 12, 30, 30), (4, 8, 8, 8), 20000, "fp64"),
+    ((20, 30, 200), (2, 4, 32), 8000, "tf32"),         # order 3: W_2 of 32 entries
+])
+def test_two_level_walks(handle, dims, ranks, m, prec):
+    from tests.test_gpu_fullsize import _check_residual
+    g = np.random.default_rng(41)
+    F = [g.standard_normal((i, r)).astype(np.float32) for i, r in zip(dims, ranks)]
+    X = g.standard_normal(dims).astype(np.float32)
+    Fd, Xd = [dev(a) for a in F], dev(X)
+    assert m >= 4 * dims[0] * dims[1]                   # the library's test for two levels
+    levs = [LV.leverage_scores(np.asarray(a, dtype=np.float64))[0] for a in F]
+    smp = T.tucker_sample_rows(handle, dims, ranks, [dev(l) for l in levs], m, 13, 0)
+    ku = host_keys(smp.keys, smp.n_unique)
+    cnt = smp.counts[:smp.n_unique].cpu().numpy().astype(np.float64)
+    w = S.sample_weights(cnt, smp.prob[:smp.n_unique].cpu().numpy(), smp.n_draws)
+    _, h = T.tucker_sketched_gram(handle, Xd, Fd, prec, smp)
+    x = CU.gather_dense(X, ku, dims)
+    hr = CU.sampled_rows_apply_t(F, S.decode_keys(ku, dims), w * x)
+    assert rel_err(h.cpu().numpy(), hr) <= 1e-12
+    core = T.tucker_core_update_sketched(handle, Xd, Fd, 0.1, 0, 0, 0, "exact", prec, fixed=smp)
+    _check_residual(F, dims, ku, w, x, 0.1, core.cpu().numpy())
