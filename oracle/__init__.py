@@ -15,7 +15,9 @@ Modules (each function cites the passage of the paper it restates):
   adjoint      gradient of the frozen-sketch solve
   ridge_kron   lam-ridge scores of K by Lemma 4.1, d_eff(K), the overestimate constants of
                the sample count, and an exact sampler of l^lam(K) / d_eff(K)
+  cp           regularised CP-ALS: exact and sketched factor updates on the Khatri-Rao
+               design (Sec. 4's Khatri-Rao remark, Sec. 6's L2 extension)
 
 Parity unpinned: none; every function has a pin in tests/test_oracle_*.py.
 """
-from . import philox, leverage, sampling, core_update, als, adjoint, ridge_kron  # noqa: F401
+from . import philox, leverage, sampling, core_update, als, adjoint, ridge_kron, cp  # noqa: F401
