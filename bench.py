@@ -59,10 +59,11 @@ def parse():
                    help="the smallest m on a x2 ladder from the workload's m whose median ridge-loss "
                         "ratio over 10 seeds is <= 1.01 (with --impl reference: by the oracle on "
                         "the host); prints its own JSON line, not the headline")
-    p.add_argument("--kernel-case", choices=["grouped"], default=None,
+    p.add_argument("--kernel-case", choices=["grouped", "walk2"], default=None,
                    help="a small case of one kernel family for ncu captures (grouped: the "
                         "1024^3 Gram shapes, I_1 = 1024, d = 4096, m = 5e5, on a dense "
-                        "1024 x 128 x 128 tensor); prints its own JSON line, not the headline")
+                        "1024 x 128 x 128 tensor; walk2: the 128^4 two-level walks at "
+                        "m = 8e5); prints its own JSON line, not the headline")
     p.add_argument("--stage-roofline", action="store_true",
                    help="time the sampler and the gather at 2^27 draws (their HBM/ALU rooflines); "
                         "prints its own JSON line, not the headline")
@@ -346,16 +347,22 @@ def workload_config(w, prec, reg, solver, m, x_bytes):
 
 
 def run_kernel_case(args):
-    """Three sketched TF32 updates with the Gram grouped by the leading index at
-    the 1024^3-at-10% shapes (I_1 = 1024, ranks 16, d = 4096, m = 5e5) on a dense
-    1024 x 128 x 128 FP32 tensor: under 1 GB on the device, so that one launch of
-    the grouped kernels can be captured with every ncu section."""
+    """Three sketched TF32 updates of a small case of one kernel family, so that one
+    launch can be captured with every ncu section:
+      grouped: the Gram grouped by the leading index at the 1024^3-at-10% shapes
+        (I_1 = 1024, ranks 16, d = 4096, m = 5e5) on a dense 1024 x 128 x 128 FP32
+        tensor (under 1 GB on the device);
+      walk2: the two-level walks of the 128^4 workload's FP64 residual and right-hand
+        side (ranks 8^4, m = 8e5) on a dense 128^4 FP32 tensor (1 GiB)."""
     import numpy as np
     import torch
     import synth
     from paper_2107_10654_gb300 import tucker as T
     g = synth.rng(4321)
-    dims, ranks, m = (1024, 128, 128), (16, 16, 16), 500000
+    if args.kernel_case == "walk2":
+        dims, ranks, m = (128, 128, 128, 128), (8, 8, 8, 8), 800000
+    else:
+        dims, ranks, m = (1024, 128, 128), (16, 16, 16), 500000
     F = [torch.from_numpy(g.standard_normal((i, r)).astype(np.float32)).cuda()
          for i, r in zip(dims, ranks)]
     X = torch.from_numpy(g.standard_normal(dims).astype(np.float32)).cuda()
@@ -759,6 +766,14 @@ def main():
             T.tucker_set_factor_sketch(h, 0)
             extra["als_factor_m"] = FACTOR_M
             extra["als_ten_sweeps"] = quality
+            # the CP-ALS variant: one sweep of sketched CP factor updates of rank R_1
+            # (FACTOR_M draws per mode) from the workload's factors
+            Fc = [a.clone() for a in F]
+            T.tucker_cp_als_sweep(h, X, Fc, w.lam, FACTOR_M, w.seed_sample, 0)
+            ms_cp, _ = timer(lambda: T.tucker_cp_als_sweep(h, X, Fc, w.lam, FACTOR_M,
+                                                           w.seed_sample, 1), min(args.steps, 5))
+            extra["cp_als_sweep_ms"] = statistics.mean(ms_cp)
+            extra["cp_rank"] = int(F[0].shape[1])
             lev = T.tucker_leverage_scores(h, F)[0]
             smp = T.tucker_sample_rows(h, w.dims, w.ranks, lev, m_t, w.seed_sample, 0, args.reg)
             gf, stf = T.tucker_core_update_sketched(h, X, F, w.lam, 0, 0, 0, args.reg, prec,

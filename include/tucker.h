@@ -449,6 +449,37 @@ tucker_status tucker_factor_update_sketched(tucker_handle* h, const tucker_tenso
                                             double lambda, int64_t m, uint64_t seed,
                                             uint32_t sweep);
 
+/* Sketched factor update of regularised CP-ALS: the extension to L2-regularised
+ * CP decompositions that Sec. 6 notes, with the Khatri-Rao design overestimated
+ * by Kronecker leverage scores as the remark in Sec. 4 recalls.  The rank-R CP
+ * model is X_hat = sum_r a_1[:, r] o ... o a_N[:, r]; the mode-n update is the
+ * ridge regression min ||Z_n A^T - X_(n)^T||^2 + lambda ||A||^2 with the design
+ * Z_n whose row for the multi-index over the modes k != n (row-major, last
+ * fastest) is the Hadamard product of A^(k)[j_k, :].  Z_n's columns are columns
+ * of (x)_{k != n} A^(k), so l_j(Z_n) <= prod_{k != n} l_{j_k}(A^(k)) and the
+ * product distribution of the other modes' leverage scores is an
+ * (R / prod_{k != n} rank A^(k))-overestimate.  The draws, dedupe, weights and
+ * normal equations are those of tucker_factor_update_sketched with z_u (the
+ * Hadamard row, FP64, modes in increasing order) in place of b_u:
+ *     M = sum_u w_u z_u z_u^T + lambda I,   Y = sum_u w_u x_u z_u^T,   A^(n) = Y M^-1.
+ *   X               dense tensor (order >= 2), FP32 or FP64
+ *   R               CP rank, 1 <= R <= TUCKER_MAX_RANK
+ *   A_inout[N]      device factors I_n x R (X's dtype); A_inout[n] is overwritten
+ *   n, m, seed, sweep, lambda: as for tucker_factor_update_sketched (Philox key
+ *                   word sweep + (n + 1) 2^32)
+ * Errors: EINVAL, ENOTSPD, ECUDA. */
+tucker_status tucker_cp_factor_update_sketched(tucker_handle* h, const tucker_tensor* X, int R,
+                                               void* const* A_inout, int n, double lambda,
+                                               int64_t m, uint64_t seed, uint32_t sweep);
+
+/* One sweep of regularised CP-ALS: tucker_cp_factor_update_sketched for the
+ * modes n = 0 .. N-1 in turn, m draws each, every update using the factors the
+ * earlier ones wrote.  Returns no loss (the library does not form the CP model).
+ * Errors: as tucker_cp_factor_update_sketched. */
+tucker_status tucker_cp_als_sweep(tucker_handle* h, const tucker_tensor* X, int R,
+                                  void* const* A_inout, double lambda, int64_t m, uint64_t seed,
+                                  uint32_t sweep);
+
 /* m > 0: the factor updates of later tucker_als_sweep calls on h are
  * tucker_factor_update_sketched with m draws each (key word sweep + (n+1) 2^32);
  * 0 (the default): exact factor updates.  With sketched factor updates the

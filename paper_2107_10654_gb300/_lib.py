@@ -88,6 +88,11 @@ SIGNATURES = {
     "tucker_factor_update_sketched": (C.c_int, [_P, C.POINTER(TuckerTensor), _IP, _PP, _P, C.c_int,
                                                 C.c_double, C.c_int64, C.c_uint64, C.c_uint32]),
     "tucker_set_factor_sketch": (C.c_int, [_P, C.c_int64]),
+    "tucker_cp_factor_update_sketched": (C.c_int, [_P, C.POINTER(TuckerTensor), C.c_int, _PP,
+                                                   C.c_int, C.c_double, C.c_int64, C.c_uint64,
+                                                   C.c_uint32]),
+    "tucker_cp_als_sweep": (C.c_int, [_P, C.POINTER(TuckerTensor), C.c_int, _PP, C.c_double,
+                                      C.c_int64, C.c_uint64, C.c_uint32]),
     "tucker_missing_beta": (C.c_int, [_P, C.POINTER(TuckerTensor), _IP, _PP, C.c_double, C.c_int,
                                       C.c_int, C.c_double, C.c_double,
                                       C.POINTER(TuckerMissingBetaInfo)]),

@@ -237,6 +237,7 @@ struct FiberArgs {
   double* partM;                           // [splits][R_n][R_n]
   void* A_out;                             // I_n x R_n, X's dtype
   int* status;
+  int cp;                                  // 1: CP design rows (Hadamard of the factor rows)
 };
 
 constexpr int FB_WARPS = 8;
@@ -292,6 +293,21 @@ __global__ void __launch_bounds__(FB_WARPS * 32) k_fiber_rows(FiberArgs a) {
         ar[k * TUCKER_MAX_RANK + r] = load_as_double(a.A[k], j[k] * a.R[k] + r, a.is64);
     }
     __syncwarp();
+    if (a.cp) {
+      // CP: z_u[r] = prod_{k != n} a_k(j_k)[r], the Khatri-Rao row (modes in order)
+      for (int r = lane; r < Rn; r += 32) {
+        double b = 1.0;
+        bool first = true;
+        for (int k = 0; k < N; ++k) {
+          if (k == n) continue;
+          const double v = ar[k * TUCKER_MAX_RANK + r];
+          b = first ? v : b * v;
+          first = false;
+        }
+        a.bb[u * Rn + r] = b;
+        a.wb[u * Rn + r] = w * b;
+      }
+    } else {
     double acc[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) acc[r] = 0.0;
@@ -319,6 +335,7 @@ __global__ void __launch_bounds__(FB_WARPS * 32) k_fiber_rows(FiberArgs a) {
           a.wb[u * Rn + r] = w * b;
         }
       }
+    }
     }
     // the fiber x_u[i] = X[base + i stride_n], eight loads per lane in flight
     T* xs = static_cast<T*>(a.xs) + u * a.I[n];
@@ -488,7 +505,7 @@ tucker_status launch_fiber_update(tucker_handle* h, const FactorSet& F, int n, c
                                   const double* core, const uint64_t* keys,
                                   const uint32_t* counts, const int* d_nu, int64_t cap,
                                   const uint64_t* const* cdf_others, int64_t m, double lambda,
-                                  char* ws, size_t ws_bytes, void* A_out) {
+                                  char* ws, size_t ws_bytes, void* A_out, int cp) {
   const int splits = fiber_splits(cap);
   if (fiber_workspace_bytes(F, n, cap, splits) > ws_bytes)
     return fail(h, TUCKER_EINTERNAL, "fiber workspace too small");
@@ -518,8 +535,9 @@ tucker_status launch_fiber_update(tucker_handle* h, const FactorSet& F, int n, c
   a.m = m;
   a.lambda = lambda;
   a.splits = splits;
-  a.postn = 1;
-  for (int k = n + 1; k < F.N; ++k) a.postn *= F.R[k];
+  a.postn = 1;                              // the Tucker core's trailing size (unused for CP)
+  if (!cp)
+    for (int k = n + 1; k < F.N; ++k) a.postn *= F.R[k];
   for (int k = 0; k < F.N; ++k) a.div_r[k] = make_fastdiv((uint32_t)F.R[k]);
   a.div_post = make_fastdiv((uint32_t)a.postn);
   char* q = ws;
@@ -531,6 +549,7 @@ tucker_status launch_fiber_update(tucker_handle* h, const FactorSet& F, int n, c
   a.partM = reinterpret_cast<double*>(take((size_t)splits * Rn * Rn * 8));
   a.A_out = A_out;
   a.status = h->d_status;
+  a.cp = cp;
   const int g1 = (int)std::min<int64_t>(ceil_div(cap, FB_WARPS), (int64_t)h->num_sms * 16);
   TK_COUNT(h);
 #define TK_FIBER_ROWS(RB)                                                                  \
@@ -548,10 +567,20 @@ tucker_status launch_fiber_update(tucker_handle* h, const FactorSet& F, int n, c
   const dim3 g2((unsigned)ceil_div(F.I[n], 128), (unsigned)splits);
   const size_t sm2 = (size_t)64 * Rn * (16 + es);
   TK_COUNT(h);
+  // (over 48 KB of dynamic shared memory for R_n > 32: the limit is raised per instance)
 #define TK_FIBER_NORMAL(RB)                                                        \
   do {                                                                             \
-    if (F.is64) k_fiber_normal<double, RB><<<g2, 128, sm2, h->stream>>>(a);        \
-    else k_fiber_normal<float, RB><<<g2, 128, sm2, h->stream>>>(a);                \
+    if (F.is64) {                                                                  \
+      TK_CUDA(h, cudaFuncSetAttribute(k_fiber_normal<double, RB>,                  \
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      (int)sm2));                                  \
+      k_fiber_normal<double, RB><<<g2, 128, sm2, h->stream>>>(a);                  \
+    } else {                                                                       \
+      TK_CUDA(h, cudaFuncSetAttribute(k_fiber_normal<float, RB>,                   \
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      (int)sm2));                                  \
+      k_fiber_normal<float, RB><<<g2, 128, sm2, h->stream>>>(a);                   \
+    }                                                                              \
   } while (0)
   if (Rn <= 4) TK_FIBER_NORMAL(4);
   else if (Rn <= 8) TK_FIBER_NORMAL(8);

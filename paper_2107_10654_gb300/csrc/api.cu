@@ -88,7 +88,7 @@ tucker_status launch_fiber_update(tucker_handle* h, const FactorSet& F, int n, c
                                   const double* core, const uint64_t* keys,
                                   const uint32_t* counts, const int* d_nu, int64_t cap,
                                   const uint64_t* const* cdf_others, int64_t m, double lambda,
-                                  char* ws, size_t ws_bytes, void* A_out);
+                                  char* ws, size_t ws_bytes, void* A_out, int cp);
 tucker_status kron_whiten(tucker_handle* h, const FactorSet& F, double* const* V,
                           double* const* ev, double lambda, const double* M, double* tmp,
                           double* out);
@@ -1633,7 +1633,7 @@ static tucker_status factor_sketch_impl(tucker_handle* h, const FactorSet& F, co
   TK_TRY(sort_dedupe(h, b.raw, m, bits_for(o.total), b.keys_u, b.counts, b.nu, b.sort,
                      b.sort_bytes));
   return launch_fiber_update(h, F, n, Xd, core, b.keys_u, b.counts, b.nu, m, b.cdf, m, lambda,
-                             b.fws, b.fws_bytes, A[n]);
+                             b.fws, b.fws_bytes, A[n], core == nullptr);
 }
 
 tucker_status tucker_factor_update_sketched(tucker_handle* h, const tucker_tensor* X, const int* R,
@@ -1652,6 +1652,72 @@ tucker_status tucker_factor_update_sketched(tucker_handle* h, const tucker_tenso
   TK_TRY(ws_reserve(h, fs_bytes(F, n, m)));
   Arena ar(h->ws);
   TK_TRY(factor_sketch_impl(h, F, X->dense, A_inout, core, n, lambda, m, seed, sweep, ar));
+  return finish(h);
+}
+
+// ----------------------------------------------- CP-ALS (Sec. 6's extension)
+// The factor set of a rank-R CP model: every R_n = R.  d is not a Kronecker
+// dimension here (the CP design has R columns), so prod R_n is not bounded.
+static tucker_status cp_factors(tucker_handle* h, const tucker_tensor* X, int R,
+                                void* const* A, FactorSet* F) {
+  if (!X) return fail(h, TUCKER_EINVAL, "X is NULL");
+  if (!X->dense) return fail(h, TUCKER_EINVAL, "the CP update needs a dense X");
+  const int N = X->order;
+  if (N < 2 || N > TUCKER_MAX_ORDER) return fail(h, TUCKER_EINVAL, "order %d out of range", N);
+  if (R < 1 || R > TUCKER_MAX_RANK) return fail(h, TUCKER_EINVAL, "CP rank %d out of range", R);
+  if (X->dtype != TUCKER_F32 && X->dtype != TUCKER_F64) return fail(h, TUCKER_EINVAL, "bad dtype");
+  if (!A) return fail(h, TUCKER_EINVAL, "null factors");
+  memset(F, 0, sizeof(*F));
+  F->N = N;
+  F->is64 = X->dtype == TUCKER_F64;
+  double tot = 1.0;
+  uint64_t total = 1;
+  for (int n = 0; n < N; ++n) {
+    if (X->dims[n] < 1 || X->dims[n] > (int64_t(1) << 31))
+      return fail(h, TUCKER_EINVAL, "I_%d out of range", n);
+    if (!A[n]) return fail(h, TUCKER_EINVAL, "factor %d is NULL", n);
+    F->I[n] = X->dims[n];
+    F->R[n] = R;
+    F->A[n] = A[n];
+    tot *= double(X->dims[n]);
+    total *= (uint64_t)X->dims[n];
+  }
+  if (tot >= 4.0e18) return fail(h, TUCKER_EINVAL, "prod(I_n) too large");
+  F->d = R;
+  F->total = total;
+  return TUCKER_OK;
+}
+
+tucker_status tucker_cp_factor_update_sketched(tucker_handle* h, const tucker_tensor* X, int R,
+                                               void* const* A_inout, int n, double lambda,
+                                               int64_t m, uint64_t seed, uint32_t sweep) {
+  if (!h) return TUCKER_EINVAL;
+  FactorSet F;
+  TK_TRY(cp_factors(h, X, R, A_inout, &F));
+  if (n < 0 || n >= F.N) return fail(h, TUCKER_EINVAL, "mode %d out of range", n);
+  if (m < 1 || m >= (int64_t(1) << 31)) return fail(h, TUCKER_EINVAL, "m out of range");
+  if (!(lambda >= 0.0)) return fail(h, TUCKER_EINVAL, "lambda must be >= 0");
+  TK_TRY(ws_reserve(h, fs_bytes(F, n, m)));
+  Arena ar(h->ws);
+  TK_TRY(factor_sketch_impl(h, F, X->dense, A_inout, nullptr, n, lambda, m, seed, sweep, ar));
+  return finish(h);
+}
+
+tucker_status tucker_cp_als_sweep(tucker_handle* h, const tucker_tensor* X, int R,
+                                  void* const* A_inout, double lambda, int64_t m, uint64_t seed,
+                                  uint32_t sweep) {
+  if (!h) return TUCKER_EINVAL;
+  FactorSet F;
+  TK_TRY(cp_factors(h, X, R, A_inout, &F));
+  if (m < 1 || m >= (int64_t(1) << 31)) return fail(h, TUCKER_EINVAL, "m out of range");
+  if (!(lambda >= 0.0)) return fail(h, TUCKER_EINVAL, "lambda must be >= 0");
+  size_t need = 0;
+  for (int n = 0; n < F.N; ++n) need = std::max(need, fs_bytes(F, n, m));
+  TK_TRY(ws_reserve(h, need));
+  for (int n = 0; n < F.N; ++n) {
+    Arena ar(h->ws);
+    TK_TRY(factor_sketch_impl(h, F, X->dense, A_inout, nullptr, n, lambda, m, seed, sweep, ar));
+  }
   return finish(h);
 }
 

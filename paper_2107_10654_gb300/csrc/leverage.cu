@@ -512,7 +512,9 @@ struct GramEigArgs {
 // need FP32 accuracy only, and on this GPU a dependent FP64 operation costs
 // tens of cycles (the FP64 eigendecomposition of three 8 x 8 Grams took about
 // 70 us, the FP32 one a few).  Stops when the off-diagonal mass is below
-// (2^-24)^2 of the diagonal's, at most 40 sweeps.
+// 1e-12 of the diagonal's (off-diagonal entries about 1e-6 of the diagonal, the
+// level FP32 rotations reach; a tighter test never passes and runs every
+// sweep), at most 40 sweeps.
 __device__ void jacobi_eig_warp_f32(float* G, float* V, int Rp, float* cs, float* sn, int* pp,
                                     int* qq, int lane) {
   const int half = Rp / 2;
@@ -524,7 +526,7 @@ __device__ void jacobi_eig_warp_f32(float* G, float* V, int Rp, float* cs, float
     }
     off = warp_sum(off);
     dia = warp_sum(dia);
-    if (!(off > 3.6e-15f * dia) || Rp <= 1) break;
+    if (!(off > 1e-12f * dia) || Rp <= 1) break;
     for (int step = 0; step < Rp - 1; ++step) {
       for (int k = lane; k < half; k += 32) {
         const int s1 = Rp - 1 - k;

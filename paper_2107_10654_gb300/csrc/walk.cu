@@ -459,6 +459,7 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes2(WalkArgs a) 
   for (int k = 0; k < KE; ++k) acc[k] = T(0);
 #pragma unroll
   for (int k2 = 0; k2 < KE2; ++k2) w2[k2] = T(0);
+  const bool shared_last = N >= 4 && 32 % a.R[N - 1] == 0;
   uint32_t prev = 0;
   bool have = false;
   auto fold = [&](uint32_t i2) {
@@ -485,11 +486,16 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes2(WalkArgs a) 
 #pragma unroll
       for (int n = 2; n < N; ++n)
         row[n] = fac_base<T>(a, n) + (size_t)__shfl_sync(0xffffffffu, mine[n], j) * a.R[n];
+      // the last mode's column of entry l + 32 k2 is the same for every k2 when
+      // R_N divides 32: c_u a_N[r_N] is then formed once per row
+      T cl = c;
+      if (N >= 4 && shared_last) cl = c * __ldg(row[N - 1] + col[0][N - 3]);
 #pragma unroll
       for (int k2 = 0; k2 < KE2; ++k2) {
-        T t = c;
+        T t = cl;
 #pragma unroll
-        for (int n = N - 1; n >= 3; --n) t *= __ldg(row[n] + col[k2][n - 2]);
+        for (int n = N - 1; n >= 3; --n)
+          if (!(n == N - 1 && shared_last)) t *= __ldg(row[n] + col[k2][n - 2]);
         w2[k2] = fma(t, __ldg(row[2] + col[k2][0]), w2[k2]);
       }
     }

@@ -335,6 +335,27 @@ def tucker_factor_update_sketched(h: Handle, X: torch.Tensor, A: List[torch.Tens
     return A[n]
 
 
+def tucker_cp_factor_update_sketched(h: Handle, X: torch.Tensor, A: List[torch.Tensor], n: int,
+                                     lam: float, m: int, seed: int, sweep: int = 0) -> torch.Tensor:
+    """Sketched CP factor update of mode n (Khatri-Rao design rows sampled by the other
+    modes' leverage scores, mode-n fibers); A[n] is overwritten and returned."""
+    lib = L.load()
+    _check(h.h, lib.tucker_cp_factor_update_sketched(h.h, C.byref(_tensor(X)), int(A[0].shape[1]),
+                                                     _factors(A), int(n), float(lam), int(m),
+                                                     int(seed), int(sweep)))
+    return A[n]
+
+
+def tucker_cp_als_sweep(h: Handle, X: torch.Tensor, A: List[torch.Tensor], lam: float, m: int,
+                        seed: int, sweep: int = 0) -> List[torch.Tensor]:
+    """One regularised CP-ALS sweep of sketched factor updates; the factors A are updated
+    in place and returned."""
+    lib = L.load()
+    _check(h.h, lib.tucker_cp_als_sweep(h.h, C.byref(_tensor(X)), int(A[0].shape[1]), _factors(A),
+                                        float(lam), int(m), int(seed), int(sweep)))
+    return A
+
+
 def tucker_set_factor_sketch(h: Handle, m: int) -> None:
     """m > 0: later ALS sweeps on h sketch their factor updates with m draws each."""
     lib = L.load()
