@@ -279,6 +279,76 @@ __global__ void __launch_bounds__(256) k_ttm_last2(const T* X, int64_t pre, int 
   }
 }
 
+// The same contraction with warp-sized work items: each warp of the grid takes
+// items (slab p, row chunk c) in turn, reduces the chunk's rows against A2 RB at
+// a time in increasing i and adds A1[i][a] * t[b] into its accumulators, then
+// writes the item's R1 R2 partial sums (k_sum_chunks adds a slab's chunks in
+// order).  No CTA barrier separates the items, so a warp never waits for the
+// others between chunks.
+template <class T, int RP>
+__global__ void __launch_bounds__(256) k_ttm_last2w(const T* X, int64_t pre, int I1, int I2,
+                                                    const T* A1, int R1, const T* A2, int R2,
+                                                    int nchunk, double* out) {
+  constexpr int RB = RowBlock<RP>::RB;
+  extern __shared__ unsigned char smraw[];
+  T* At = reinterpret_cast<T*>(smraw);                         // RP x I2
+  T* A1s = reinterpret_cast<T*>(smraw + (((size_t)RP * I2 * sizeof(T) + 15) & ~size_t(15)));
+  for (int e = threadIdx.x; e < RP * I2; e += blockDim.x) {
+    const int r = e / I2, j = e % I2;
+    At[e] = r < R2 ? A2[(int64_t)j * R2 + r] : T(0);
+  }
+  for (int e = threadIdx.x; e < I1 * R1; e += blockDim.x) A1s[e] = A1[e];
+  constexpr int VEC = 16 / sizeof(T);
+  constexpr int G = 32 / RP;
+  const int lane = threadIdx.x & 31;
+  const int RR = R1 * R2;
+  const bool vec = (I2 % VEC) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  int ea[8], esrc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = lane + 32 * q;
+    ea[q] = e < RR ? e / R2 : -1;
+    esrc[q] = ((e % R2) % RP) * G;
+  }
+  __syncthreads();
+  const int crows = (I1 + nchunk - 1) / nchunk;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t item = gw; item < pre * nchunk; item += nw) {
+    const int64_t p = item / nchunk;
+    const int c = (int)(item - p * nchunk);
+    const int i0 = c * crows, iend = min(I1, i0 + crows);
+    T y[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) y[q] = T(0);
+    const T* slab = X + p * (int64_t)I1 * I2;
+    for (int i = i0; i < iend; i += RB) {
+      const int nr = min(RB, iend - i);
+      const T* rows[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) rows[r] = slab + (int64_t)(i + (r < nr ? r : 0)) * I2;
+      T acc[RB][RP];
+      rows_contract<T, RP, RB>(rows, nr, I2, At, vec, lane, acc);
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        if (r >= nr) break;
+        const T t = transpose_reduce<T, RP>(acc[r], lane);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (32 * q >= RR) break;
+          const T tb = __shfl_sync(0xffffffffu, t, esrc[q]);
+          if (ea[q] >= 0) y[q] = fma(A1s[(i + r) * R1 + ea[q]], tb, y[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = lane + 32 * q;
+      if (e < RR) out[item * RR + e] = (double)y[q];
+    }
+  }
+}
+
 // out[p][e] = sum_c part[p][c][e] in increasing c.
 __global__ void k_sum_chunks(const double* part, int64_t pre, int nchunk, int RR, double* out) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < pre * RR;
@@ -798,19 +868,20 @@ static tucker_status ttm_last2_t(tucker_handle* h, const T* X, int64_t pre, int 
   const int RP = R2 <= 4 ? 4 : R2 <= 8 ? 8 : R2 <= 16 ? 16 : 32;
   const size_t smem = (((size_t)RP * I2 * sizeof(T) + 15) & ~size_t(15)) +
                       (((size_t)I1 * R1 * sizeof(T) + 15) & ~size_t(15)) + (size_t)8 * R1 * R2 * 8;
-  auto k = RP == 4 ? k_ttm_last2<T, 4> : RP == 8 ? k_ttm_last2<T, 8>
-         : RP == 16 ? k_ttm_last2<T, 16> : k_ttm_last2<T, 32>;
+  auto k = RP == 4 ? k_ttm_last2w<T, 4> : RP == 8 ? k_ttm_last2w<T, 8>
+         : RP == 16 ? k_ttm_last2w<T, 16> : k_ttm_last2w<T, 32>;
   TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   TK_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
   int64_t grid = (int64_t)h->num_sms * (per_sm > 0 ? per_sm : 1);
-  // row chunks per slab: enough work items for about eight per CTA, each chunk
-  // at least 32 rows (four row groups of each of the eight warps)
+  // row chunks per slab: about four items per warp of the grid, each chunk at
+  // least 4 RB rows, the partials within the prod(I)/I_N * R_N buffer
+  const int RB = RP <= 8 ? 4 : RP <= 16 ? 2 : 1;
   int nchunk = 1;
-  while (nchunk < 16 && pre * nchunk < 8 * grid && I1 / (2 * nchunk) >= 32 &&
-         2 * nchunk * R1 <= I1)                         // partials fit in a prod(I)/I_N*R_N buffer
+  while (pre * nchunk < 4 * grid * 8 && I1 / (2 * nchunk) >= 4 * RB && 2 * nchunk * R1 <= I1)
     nchunk *= 2;
-  if (grid > pre * nchunk) grid = pre * nchunk;
+  const int64_t items = pre * nchunk;
+  if (grid * 8 > items) grid = (items + 7) / 8;
   const int RR = R1 * R2;
   TK_COUNT(h);
   k<<<(int)grid, 256, smem, h->stream>>>(X, pre, I1, I2, A1, R1, A2, R2, nchunk,

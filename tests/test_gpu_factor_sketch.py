@@ -34,6 +34,7 @@ CASES = [
     ((40, 35), (5, 3), 500),                        # order 2: one other mode
     ((9, 8, 7, 6), (2, 3, 2, 2), 2500),             # order 4
     ((33, 130, 17), (4, 8, 3), 8000),               # I_n > 128: several row blocks
+    ((50, 44, 46), (40, 8, 8), 6000),               # R_n > 32: over 48 KB of normal-equation tiles
 ]
 
 
