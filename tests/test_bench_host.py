@@ -151,6 +151,33 @@ def test_grouped_gram_predicate_limits():
     assert not bench.grouped_gram(W((3201, 40, 40), (16, 16, 16)))
 
 
+@pytest.mark.parametrize("name,m,expect", [
+    ("dense3_512_r8_f32", 100000, True),            # d / R_1 = 64: the narrow grouped Gram
+    ("dense3_512_r8_f32", 1000, False),             # fewer than 2 I_1 rows
+    ("dense4_128_r8_f32", 800000, False),           # d / R_1 = 512: the wide grouped Gram
+    ("dense3_64_r4_f64", 2000, True),               # d / R_1 = 16
+])
+def test_narrow_gram_predicate(name, m, expect):
+    assert bench.narrow_gram(synth.WORKLOADS[name], m) is expect
+
+
+def test_narrow_gram_predicate_limits():
+    class W:
+        def __init__(self, dims, ranks):
+            self.dims, self.ranks = dims, ranks
+            self.d = 1
+            for r in ranks:
+                self.d *= r
+    assert not bench.narrow_gram(W((40, 40), (8, 8)), 10 ** 5)              # order 2
+    assert not bench.narrow_gram(W((40, 40, 40), (3, 4, 4)), 10 ** 5)       # R_1 not a power of two
+    assert not bench.narrow_gram(W((40, 40, 40), (1, 8, 8)), 10 ** 5)       # R_1 = 1
+    assert bench.narrow_gram(W((40, 40, 40), (16, 8, 8)), 10 ** 5)          # d / R_1 = 64
+    assert not bench.narrow_gram(W((40, 40, 40), (2, 8, 16)), 10 ** 5)      # d / R_1 = 128
+    assert bench.narrow_gram(W((3072, 40, 40), (8, 8, 8)), 6144)             # m = 2 I_1
+    assert not bench.narrow_gram(W((3072, 40, 40), (8, 8, 8)), 6143)
+    assert not bench.narrow_gram(W((3073, 40, 40), (8, 8, 8)), 10 ** 6)     # A^(1) over 96 KB
+
+
 def test_ladder_helper_doubles_m_until_the_median_meets_the_target():
     calls = []
 
