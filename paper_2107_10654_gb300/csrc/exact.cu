@@ -194,92 +194,11 @@ __global__ void __launch_bounds__(256) k_ttm_last(const T* X, int64_t P, int I, 
   }
 }
 
-// Fused contraction of the last two modes, one (slab, row chunk) per CTA
-// iteration: part[p][c][a][b] = sum_{i in chunk c, j} X[p][i][j] A1[i][a] A2[j][b]
+// Fused contraction of the last two modes:
+// part[p][c][a][b] = sum_{i in chunk c, j} X[p][i][j] A1[i][a] A2[j][b]
 // (A1 = A^(N-1), I1 x R1; A2 = A^(N), I2 x R2; the I1 rows of a slab cut into
-// nchunk chunks, so that pre * nchunk work items spread evenly over the
-// resident CTAs).  Warp w reduces rows i = i0 + w, i0 + w + 8, ... of the chunk
-// against A2, RB rows at a time (rows_contract), then adds A1[i][a] * t[b]
-// into per-warp accumulators in increasing i; warps are combined in a fixed
-// order; k_sum_chunks adds the chunks in order.
-template <class T, int RP>
-__global__ void __launch_bounds__(256) k_ttm_last2(const T* X, int64_t pre, int I1, int I2,
-                                                   const T* A1, int R1, const T* A2, int R2,
-                                                   int nchunk, double* out) {
-  constexpr int RB = RowBlock<RP>::RB;
-  extern __shared__ unsigned char smraw[];
-  T* At = reinterpret_cast<T*>(smraw);                         // RP x I2
-  T* A1s = reinterpret_cast<T*>(smraw + (((size_t)RP * I2 * sizeof(T) + 15) & ~size_t(15)));
-  double* Yw = reinterpret_cast<double*>(smraw + (((size_t)RP * I2 * sizeof(T) + 15) & ~size_t(15)) +
-                                         (((size_t)I1 * R1 * sizeof(T) + 15) & ~size_t(15)));
-  for (int e = threadIdx.x; e < RP * I2; e += blockDim.x) {
-    const int r = e / I2, j = e % I2;
-    At[e] = r < R2 ? A2[(int64_t)j * R2 + r] : T(0);
-  }
-  for (int e = threadIdx.x; e < I1 * R1; e += blockDim.x) A1s[e] = A1[e];
-  constexpr int VEC = 16 / sizeof(T);
-  constexpr int G = 32 / RP;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int RR = R1 * R2;
-  const bool vec = (I2 % VEC) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
-  // output e = lane + 32 q of this lane is (a, b) = (e / R2, e % R2): fixed for the kernel
-  int ea[8], esrc[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int e = lane + 32 * q;
-    ea[q] = e < RR ? e / R2 : -1;
-    esrc[q] = ((e % R2) % RP) * G;                    // lane holding t[b] after the reduction
-  }
-  __syncthreads();
-  const int crows = (I1 + nchunk - 1) / nchunk;
-  for (int64_t item = blockIdx.x; item < pre * nchunk; item += gridDim.x) {
-    const int64_t p = item / nchunk;
-    const int c = (int)(item - p * nchunk);
-    const int iend = min(I1, (c + 1) * crows);
-    T y[8];                                                    // outputs lane, lane+32, ...
-#pragma unroll
-    for (int q = 0; q < 8; ++q) y[q] = T(0);
-    const T* slab = X + p * (int64_t)I1 * I2;
-    for (int i = c * crows + w; i < iend; i += 8 * RB) {
-      int nr = 0;
-      const T* rows[RB];
-#pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        const int ir = i + 8 * r;
-        rows[r] = slab + (int64_t)(ir < iend ? ir : i) * I2;
-        nr += ir < iend;
-      }
-      T acc[RB][RP];
-      rows_contract<T, RP, RB>(rows, nr, I2, At, vec, lane, acc);
-#pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        if (r >= nr) break;
-        const int ir = i + 8 * r;
-        const T t = transpose_reduce<T, RP>(acc[r], lane);     // t[b] at lane b*G
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (32 * q >= RR) break;                          // warp-uniform
-          const T tb = __shfl_sync(0xffffffffu, t, esrc[q]);
-          if (ea[q] >= 0) y[q] = fma(A1s[ir * R1 + ea[q]], tb, y[q]);
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = lane + 32 * q;
-      if (e < RR) Yw[w * RR + e] = (double)y[q];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-      double v = 0.0;
-      for (int ww = 0; ww < 8; ++ww) v += Yw[ww * RR + e];
-      out[item * RR + e] = v;
-    }
-    __syncthreads();
-  }
-}
-
-// The same contraction with warp-sized work items: each warp of the grid takes
+// nchunk chunks).
+// It runs in warp-sized work items: each warp of the grid takes
 // items (slab p, row chunk c) in turn, reduces the chunk's rows against A2 RB at
 // a time in increasing i and adds A1[i][a] * t[b] into its accumulators, then
 // writes the item's R1 R2 partial sums (k_sum_chunks adds a slab's chunks in
@@ -867,7 +786,7 @@ static tucker_status ttm_last2_t(tucker_handle* h, const T* X, int64_t pre, int 
                                  double* out) {
   const int RP = R2 <= 4 ? 4 : R2 <= 8 ? 8 : R2 <= 16 ? 16 : 32;
   const size_t smem = (((size_t)RP * I2 * sizeof(T) + 15) & ~size_t(15)) +
-                      (((size_t)I1 * R1 * sizeof(T) + 15) & ~size_t(15)) + (size_t)8 * R1 * R2 * 8;
+                      (((size_t)I1 * R1 * sizeof(T) + 15) & ~size_t(15));
   auto k = RP == 4 ? k_ttm_last2w<T, 4> : RP == 8 ? k_ttm_last2w<T, 8>
          : RP == 16 ? k_ttm_last2w<T, 16> : k_ttm_last2w<T, 32>;
   TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
