@@ -156,7 +156,8 @@ tucker_status ridge_prob(tucker_handle* h, RidgeState* st, const uint64_t* keys_
 tucker_status launch_kpcg(tucker_handle* h, const float* M, const double* regdiag, int d, int N,
                           const int* R, const double* const* V, const double* const* ev,
                           const double* rhs, double* out, double* upd, double* stats,
-                          double* part, float* sg, double* res, double tol, int max_iter);
+                          double* part, float* sg, double* res, double tol, int max_iter,
+                          bool dep);
 size_t leverage_aux_bytes(int64_t maxI);
 static int64_t max_dim(const FactorSet& F) { int64_t m = 1; for (int n = 0; n < F.N; ++n) if (F.I[n] > m) m = F.I[n]; return m; }
 
@@ -502,8 +503,11 @@ static tucker_status kpcg_solve(tucker_handle* h, int d, const double* rhs, doub
   const bool first = c.kres_n == 0;
   ++c.kres_n;
   if (first) ev_record(h, h->timing, 12);
+  // a correction's solve follows the residual's kernels on this stream: launched
+  // with programmatic dependence on them (the first follows the join of the
+  // second stream, and is launched in full order)
   TK_TRY(launch_kpcg(h, c.L32, c.regdiag, d, c.kN, c.kR, c.kv, c.ke, rhs, out, upd, stats,
-                     c.part, c.sg, res, c.ktol, kKpcgMaxIter));
+                     c.part, c.sg, res, c.ktol, kKpcgMaxIter, !first));
   if (first) ev_record(h, h->timing, 13);
   return TUCKER_OK;
 }

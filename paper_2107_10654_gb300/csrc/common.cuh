@@ -117,6 +117,34 @@ tucker_status fail(tucker_handle* h, tucker_status s, const char* fmt, ...);
 // Count one kernel launch on the handle (reported through tucker_stats).
 #define TK_COUNT(h) (++(h)->launches)
 
+// Launch on h->stream with programmatic dependent launch allowed: the grid may
+// be scheduled while the previous kernel on the stream drains, which hides the
+// launch latency between short dependent kernels.  Every kernel launched this
+// way calls pdl_wait() first, before any access to global memory, so it sees
+// all of the previous kernel's writes and overwrites nothing that kernel reads.
+// Used only where the previous operation on the stream is a kernel of the same
+// stream (not behind an event wait on another stream).
+template <class... KArgs, class... Args>
+inline cudaError_t launch_dep(tucker_handle* h, void (*k)(KArgs...), dim3 grid, dim3 block,
+                              size_t smem, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = h->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  ++h->launches;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+// Wait for the previous kernel on the stream (and its memory writes); a no-op
+// when the kernel was not launched with programmatic dependent launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 #define TK_TRY(expr)                                                                  \
   do {                                                                                \
     tucker_status s_ = (expr);                                                        \

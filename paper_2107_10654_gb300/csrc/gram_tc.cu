@@ -563,6 +563,7 @@ static size_t narrow_smem_bytes(int sumR, int nm) {
 __global__ void __launch_bounds__(1024) k_tcg_pieces(const int* seg_begin, const int* seg_end,
                                                       int I1, int* prow0, int* prow1, int* pseg,
                                                       int* npieces) {
+  pdl_wait();
   __shared__ int64_t tmp[32];
   int64_t carry = 0;
   for (int base = 0; base < I1; base += blockDim.x) {
@@ -585,6 +586,7 @@ __global__ void __launch_bounds__(1024) k_tcg_pieces(const int* seg_begin, const
 // NMT: the number of trailing modes when known at compile time (2 or 3), else 0.
 template <int NMT>
 __global__ void __launch_bounds__(NR_THREADS, 4) k_tcg_narrow(NarrowArgs a) {
+  pdl_wait();
   constexpr int NMX = NMT > 0 ? NMT : TUCKER_MAX_ORDER - 1;
   extern __shared__ __align__(1024) unsigned char smraw[];
   const uint32_t base_u = smem_u32(smraw);
@@ -765,6 +767,7 @@ __global__ void __launch_bounds__(XN_WARPS * 32) k_tcg_expand_narrow(const float
                                                                      const int* npieces, int I1,
                                                                      int dp, const void* A1,
                                                                      int is64, int d, double* G) {
+  pdl_wait();
   extern __shared__ float xs[];
   float* a1 = xs;                                              // [I1][R1]
   float* red = xs + ((I1 * R1 + 3) & ~3);                      // [16][32][32]
@@ -1368,10 +1371,8 @@ static tucker_status launch_expand_narrow(tucker_handle* h, const float* Mp, con
   if (smem > 227 * 1024) return fail(h, TUCKER_ENOTSUP, "narrow grouped Gram: shared memory");
   TK_CUDA(h, cudaFuncSetAttribute(k_tcg_expand_narrow<R1>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  TK_COUNT(h);
-  k_tcg_expand_narrow<R1><<<dim3((ne + 31) / 32, (R1 * R1 + 31) / 32), XN_WARPS * 32, smem,
-                            h->stream>>>(Mp, pseg, npieces, I1, dp, A1, is64, d, G);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_tcg_expand_narrow<R1>, dim3((ne + 31) / 32, (R1 * R1 + 31) / 32),
+                        XN_WARPS * 32, smem, Mp, pseg, npieces, I1, dp, A1, is64, d, G));
   return TUCKER_OK;
 }
 
@@ -1417,16 +1418,13 @@ tucker_status launch_gram_tc_narrow(tucker_handle* h, const RowSet& s, int64_t I
   TK_COUNT(h);
   k_tcg_segments<<<gs, 256, 0, h->stream>>>(s.idx[0], s.n_rows, seg_begin, seg_end);
   TK_LAUNCH(h);
-  TK_COUNT(h);
-  k_tcg_pieces<<<1, 1024, 0, h->stream>>>(seg_begin, seg_end, (int)I1, prow0, prow1, pseg, npieces);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_tcg_pieces, 1, 1024, 0, seg_begin, seg_end, (int)I1, prow0, prow1,
+                        pseg, npieces));
   const size_t smem = narrow_smem_bytes(a.sumR, a.nm);
   auto kern = a.nm == 2 ? k_tcg_narrow<2> : a.nm == 3 ? k_tcg_narrow<3> : k_tcg_narrow<0>;
   TK_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (h->timing) cudaEventRecord(h->ev[10], h->stream);
-  TK_COUNT(h);
-  kern<<<(int)P, NR_THREADS, smem, h->stream>>>(a);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, kern, (int)P, NR_THREADS, smem, a));
   if (h->timing) cudaEventRecord(h->ev[11], h->stream);
   switch (R1) {
     case 2: return launch_expand_narrow<2>(h, Mp, pseg, npieces, (int)I1, dp, s.A[0], s.is64, s.d, G);

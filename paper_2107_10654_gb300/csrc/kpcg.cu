@@ -585,6 +585,7 @@ __global__ void __launch_bounds__(KP_THREADS, 1) k_kpcg(KpcgArgs a) {
 constexpr int KPCL_CTAS = 8;
 
 __global__ void __launch_bounds__(KP_THREADS, 1) k_kpcg_cluster(KpcgArgs a) {
+  pdl_wait();
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) float kp_sm[];
   __shared__ KpcgShared sh;
@@ -750,7 +751,8 @@ static bool kpcg_cluster_ok(int d, int N, const int* R) {
 tucker_status launch_kpcg(tucker_handle* h, const float* M, const double* regdiag, int d, int N,
                           const int* R, const double* const* V, const double* const* ev,
                           const double* rhs, double* out, double* upd, double* stats,
-                          double* part, float* sg, double* res, double tol, int max_iter) {
+                          double* part, float* sg, double* res, double tol, int max_iter,
+                          bool dep) {
   KpcgArgs a;
   memset(&a, 0, sizeof(a));
   a.M = M; a.regdiag = regdiag; a.d = d; a.N = N;
@@ -771,8 +773,13 @@ tucker_status launch_kpcg(tucker_handle* h, const float* M, const double* regdia
     const size_t smem = kpcg_cluster_smem_bytes(d, N, R);
     TK_CUDA(h, cudaFuncSetAttribute(k_kpcg_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     cudaLaunchConfig_t cfg = cluster_cfg(at, smem, h->stream);
+    if (dep) {            // programmatic dependent launch (the kernel waits first)
+      at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[1].val.programmaticStreamSerializationAllowed = 1;
+      cfg.numAttrs = 2;
+    }
     TK_COUNT(h);
     TK_CUDA(h, cudaLaunchKernelEx(&cfg, k_kpcg_cluster, a));
     return TUCKER_OK;

@@ -270,6 +270,7 @@ __device__ void lev_factor_W(const LevArgs& a, int n, const double* gparts, doub
 
 
 __global__ void __launch_bounds__(LEV_THREADS) k_leverage_eig(LevArgs a) {
+  pdl_wait();
   extern __shared__ double sm[];
   lev_factor_W(a, blockIdx.x, a.gpart[blockIdx.x], sm);
 }
@@ -290,6 +291,7 @@ struct LevRowArgs {
 // and the R_n partial squares of a row are added in order of k through shared
 // memory (the same order as a single thread's loop over k).
 __global__ void __launch_bounds__(256) k_leverage_rows(LevRowArgs a) {
+  pdl_wait();
   extern __shared__ double Ws[];
   const int n = blockIdx.y;
   const int R = a.R[n];
@@ -332,6 +334,7 @@ struct CdfArgs {
 };
 
 __global__ void __launch_bounds__(LEV_THREADS) k_cdf_from_lev(CdfArgs a) {
+  pdl_wait();
   __shared__ int64_t scan_tmp[32];
   const int n = blockIdx.x;
   const int64_t I = a.I[n];
@@ -358,9 +361,7 @@ tucker_status launch_cdf_from_lev(tucker_handle* h, int N, const int64_t* I,
   a.N = N;
   for (int n = 0; n < N; ++n) { a.I[n] = I[n]; a.lev[n] = lev[n]; a.cdf[n] = cdf[n]; }
   a.status = h->d_status;
-  TK_COUNT(h);
-  k_cdf_from_lev<<<N, LEV_THREADS, 0, h->stream>>>(a);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_cdf_from_lev, N, LEV_THREADS, 0, a));
   return TUCKER_OK;
 }
 
@@ -417,16 +418,13 @@ tucker_status launch_leverage(tucker_handle* h, const FactorSet& F, double* cons
                       size_t(maxRp + 2) * sizeof(int) + 64;
   TK_CUDA(h, cudaFuncSetAttribute(k_leverage_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-  TK_COUNT(h);
-  k_leverage_eig<<<F.N, LEV_THREADS, smem, h->stream>>>(a);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_leverage_eig, F.N, LEV_THREADS, smem, a));
   const int rpp = maxR <= 256 ? 256 / maxR : 1;                 // rows per CTA pass
   int gx = (int)((maxI + rpp - 1) / rpp);
   if (gx > 4 * h->num_sms / F.N) gx = 4 * h->num_sms / F.N;
   if (gx < 1) gx = 1;
-  TK_COUNT(h);
-  k_leverage_rows<<<dim3(gx, F.N), 256, (size_t)(maxR * maxR + 256) * sizeof(double), h->stream>>>(ra);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_leverage_rows, dim3(gx, F.N), 256,
+                        (size_t)(maxR * maxR + 256) * sizeof(double), ra));
   return launch_cdf_from_lev(h, F.N, F.I, lev, cdf);
 }
 

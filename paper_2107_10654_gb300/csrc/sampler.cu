@@ -88,6 +88,7 @@ __device__ __forceinline__ uint64_t draw_key(const SampleArgs& a, const uint64_t
 }
 
 __global__ void __launch_bounds__(SAMPLE_THREADS) k_sample(SampleArgs a) {
+  pdl_wait();
   extern __shared__ uint64_t scdf[];
   __shared__ int64_t scan_tmp[32];
   const uint64_t* C[TUCKER_MAX_ORDER];
@@ -318,9 +319,8 @@ tucker_status sample_keys(tucker_handle* h, const FactorSet& F, const uint64_t* 
     a.keys_out = keys_out;
     a.T_out = d_T;                          // T = m, written by the kernel
     a.T_val = m;
-    TK_COUNT(h);
-    k_sample<<<ceil_div(m, (int64_t)SAMPLE_THREADS * a.items), SAMPLE_THREADS, smem, h->stream>>>(a);
-    TK_LAUNCH(h);
+    TK_CUDA(h, launch_dep(h, k_sample, ceil_div(m, (int64_t)SAMPLE_THREADS * a.items),
+                          SAMPLE_THREADS, smem, a));
     *T_host = m;
     return TUCKER_OK;
   }

@@ -32,17 +32,20 @@ constexpr int CHOL_THREADS = 128;   // one warp per SM sub-partition: enough for
 constexpr int CHOL_CL_MAX_D = 1024; // largest order factored by one cluster (if it fits)
 
 __global__ void k_add_diag(double* M, int d, const double* diag) {
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x)
     M[(size_t)i * d + i] += diag[i];
 }
 
 // regdiag[j] = lambda (exact) or lambda * D[j] (augmented)
 __global__ void k_regdiag(double* out, int d, double lambda, const double* D) {
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d; i += gridDim.x * blockDim.x)
     out[i] = D ? lambda * D[i] : lambda;
 }
 
 __global__ void k_to_f32(const double* in, size_t n, float* out) {
+  pdl_wait();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
 }
@@ -1148,9 +1151,7 @@ tucker_status chol_correct_inv32(tucker_handle* h, const float* X, const float* 
 tucker_status launch_to_f32(tucker_handle* h, const double* in, size_t n, float* out) {
   int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)h->num_sms * 16);
   if (grid < 1) grid = 1;
-  TK_COUNT(h);
-  k_to_f32<<<grid, 256, 0, h->stream>>>(in, n, out);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_to_f32, grid, 256, 0, in, n, out));
   return TUCKER_OK;
 }
 
@@ -1210,16 +1211,12 @@ tucker_status launch_refine_update(tucker_handle* h, double* g, const double* r,
 }
 
 tucker_status launch_regdiag(tucker_handle* h, double* out, int d, double lambda, const double* D) {
-  TK_COUNT(h);
-  k_regdiag<<<ceil_div(d, 256), 256, 0, h->stream>>>(out, d, lambda, D);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_regdiag, ceil_div(d, 256), 256, 0, out, d, lambda, D));
   return TUCKER_OK;
 }
 
 tucker_status launch_add_diag(tucker_handle* h, double* M, int d, const double* diag) {
-  TK_COUNT(h);
-  k_add_diag<<<ceil_div(d, 256), 256, 0, h->stream>>>(M, d, diag);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_add_diag, ceil_div(d, 256), 256, 0, M, d, diag));
   return TUCKER_OK;
 }
 

@@ -22,6 +22,7 @@ constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 // ---------------------------------------------------------- int64 scan (1 CTA)
 __global__ void __launch_bounds__(1024) k_scan_i64(const int64_t* in, int64_t* out, int64_t n,
                                                    int64_t* total) {
+  pdl_wait();
   __shared__ int64_t tmp[32];
   int64_t carry = 0;
   for (int64_t base = 0; base < n; base += 4 * (int64_t)blockDim.x) {
@@ -44,8 +45,8 @@ __global__ void __launch_bounds__(1024) k_scan_i64(const int64_t* in, int64_t* o
 
 void launch_scan_i64(tucker_handle* h, const int64_t* in, int64_t* out_excl, int64_t n,
                      int64_t* total) {
-  TK_COUNT(h);
-  k_scan_i64<<<1, 1024, 0, h->stream>>>(in, out_excl, n, total);
+  // a launch error stays in cudaGetLastError for the caller's check
+  (void)launch_dep(h, k_scan_i64, 1, 1024, 0, in, out_excl, n, total);
 }
 
 // ------------------------------------------------------------------ radix sort
@@ -202,6 +203,7 @@ template <int CTAS>
 __global__ void __launch_bounds__(CL_THREADS)
     k_sort_dedupe_cluster(const uint64_t* keys_in, int n, int key_bits, int dbits,
                           uint64_t* keys_u, uint32_t* counts_u, int* d_n_unique) {
+  pdl_wait();
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char csm[];
@@ -448,8 +450,12 @@ static tucker_status launch_sort_cluster(tucker_handle* h, const uint64_t* keys_
   if (CTAS > 8)
     TK_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   TK_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   cudaLaunchConfig_t cfg = sort_cluster_cfg(at, CTAS, smem, h->stream);
+  // programmatic dependent launch behind the sampler (the kernel waits first)
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.numAttrs = 2;
   TK_COUNT(h);
   TK_CUDA(h, cudaLaunchKernelEx(&cfg, k_sort_dedupe_cluster<CTAS>, keys_in, (int)n, key_bits,
                                 dbits, keys_u, counts_u, d_n_unique));

@@ -100,6 +100,7 @@ __global__ void k_segments(const uint32_t* idx0, const int* n_rows, int* seg_beg
 
 __global__ void k_piece_count(const int* seg_begin, const int* seg_end, int I1, int CH,
                               int64_t* pcnt) {
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I1; i += gridDim.x * blockDim.x) {
     const int len = seg_end[i] - seg_begin[i];
     pcnt[i] = len > 0 ? (len + CH - 1) / CH : 0;
@@ -109,6 +110,7 @@ __global__ void k_piece_count(const int* seg_begin, const int* seg_end, int I1, 
 __global__ void k_piece_fill(const int* seg_begin, const int* seg_end, int I1, int CH,
                              const int64_t* pcnt, const int64_t* pstart, int* p_i1, int* p_u0,
                              int* p_u1) {
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I1; i += gridDim.x * blockDim.x) {
     const int b = seg_begin[i], e = seg_end[i];
     for (int64_t q = 0; q < pcnt[i]; ++q) {
@@ -125,6 +127,7 @@ __global__ void k_piece_fill(const int* seg_begin, const int* seg_end, int I1, i
 // stored in the walk's arithmetic type T.
 template <class T>
 __global__ void k_walk_v1(WalkArgs a) {
+  pdl_wait();
   const int L1 = a.lsz[1];
   const int nvec = a.g2 ? 2 : 1;
   T* V1 = reinterpret_cast<T*>(a.V1);
@@ -178,6 +181,7 @@ struct FlatDot<T, N, N> {
 // stages its own factor rows of modes 2..N, and contracts them against V_1.
 template <class T, int N>
 __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_dot(WalkArgs a) {
+  pdl_wait();
   extern __shared__ double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t p = (int64_t)blockIdx.x * WK_WARPS + warp;
@@ -226,6 +230,7 @@ static __host__ __device__ size_t dot2_warp_bytes(int L1, int L2, int fstore, in
 
 template <class T, int N>
 __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_dot2(WalkArgs a) {
+  pdl_wait();
   extern __shared__ double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t p = (int64_t)blockIdx.x * WK_WARPS + warp;
@@ -288,6 +293,7 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_dot2(WalkArgs a) {
 
 template <int N>
 __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy(WalkArgs a) {
+  pdl_wait();
   extern __shared__ double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t p = (int64_t)blockIdx.x * WK_WARPS + warp;
@@ -364,6 +370,7 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy(WalkArgs a) {
 // rows overlap (the level fold above waits on each row's loads in turn).
 template <class T, int N, int KE>
 __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes(WalkArgs a) {
+  pdl_wait();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t p = (int64_t)blockIdx.x * WK_WARPS + warp;
   if (p >= *a.npieces) return;                              // warp-uniform
@@ -442,6 +449,7 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes(WalkArgs a) {
 // r_2(e) = k / KE2 are its own, so the fold reads no other lane's data.
 template <class T, int N, int KE, int KE2>
 __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes2(WalkArgs a) {
+  pdl_wait();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t p = (int64_t)blockIdx.x * WK_WARPS + warp;
   if (p >= *a.npieces) return;                              // warp-uniform
@@ -508,6 +516,7 @@ __global__ void __launch_bounds__(WK_WARPS * 32) k_walk_axpy_lanes2(WalkArgs a) 
 
 // W1[i1][j] = sum of the piece partials of segment i1 (fixed order); 0 if empty.
 __global__ void k_walk_reduce(WalkArgs a) {
+  pdl_wait();
   const int L1 = a.lsz[1];
   const int64_t total = (int64_t)a.I1 * L1;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -525,6 +534,7 @@ __global__ void k_walk_reduce(WalkArgs a) {
 // lane partial sums combined by a fixed butterfly: deterministic.
 __global__ void k_walk_expand(WalkArgs a, const double* base, const double* diag, const double* y,
                               double* out) {
+  pdl_wait();
   const int lsz1 = a.lsz[1];
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -552,6 +562,7 @@ __global__ void k_walk_expand(WalkArgs a, const double* base, const double* diag
 // expansion, part[b][r1 lsz1 + j] = sum_{its i1} A1[i1][r1] W_1[i1][j].
 // k_walk_sum: out[t] = base - diag .* y + sum_b part[b][t] in the order of b.
 __global__ void __launch_bounds__(256) k_walk_fold(WalkArgs a, int chunk, double* part) {
+  pdl_wait();
   extern __shared__ double wrow[];                  // chunk x lsz1, then chunk x R1 of A1
   const int L1 = a.lsz[1], R1 = a.R[0];
   const int i1a = blockIdx.x * chunk;
@@ -593,6 +604,7 @@ __global__ void __launch_bounds__(256) k_walk_fold(WalkArgs a, int chunk, double
 // when nb <= 64.
 __global__ void k_walk_sum(const double* part, int nb, int d, const double* base,
                            const double* diag, const double* y, double* out) {
+  pdl_wait();
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int t = (int)(gt >> 3), q = (int)(gt & 7);
   double v = 0.0;
@@ -838,9 +850,7 @@ static tucker_status launch_by_order(tucker_handle* h, WalkKernel k, int64_t max
                                      const WalkArgs& a) {
   TK_CUDA(h, cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-  TK_COUNT(h);
-  k<<<(int)((maxP + WK_WARPS - 1) / WK_WARPS), WK_WARPS * 32, smem, h->stream>>>(a);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k, (int)((maxP + WK_WARPS - 1) / WK_WARPS), WK_WARPS * 32, smem, a));
   return TUCKER_OK;
 }
 
@@ -855,17 +865,12 @@ tucker_status walk_segments(tucker_handle* h, const RowSet& s, int64_t I1, const
   k_segments<<<grid_for(h, wb.cap, 256), 256, 0, h->stream>>>(s.idx[0], s.n_rows, w.seg_begin,
                                                               w.seg_end);
   TK_LAUNCH(h);
-  TK_COUNT(h);
-  k_piece_count<<<grid_for(h, I1, 256), 256, 0, h->stream>>>(w.seg_begin, w.seg_end, (int)I1,
-                                                             g.CH, w.pcnt);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_piece_count, grid_for(h, I1, 256), 256, 0, w.seg_begin, w.seg_end,
+                        (int)I1, g.CH, w.pcnt));
   launch_scan_i64(h, w.pcnt, w.pstart, I1, w.npieces);
   TK_LAUNCH(h);
-  TK_COUNT(h);
-  k_piece_fill<<<grid_for(h, I1, 128), 128, 0, h->stream>>>(w.seg_begin, w.seg_end, (int)I1, g.CH,
-                                                            w.pcnt, w.pstart, w.p_i1, w.p_u0,
-                                                            w.p_u1);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_piece_fill, grid_for(h, I1, 128), 128, 0, w.seg_begin, w.seg_end,
+                        (int)I1, g.CH, w.pcnt, w.pstart, w.p_i1, w.p_u0, w.p_u1));
   return TUCKER_OK;
 }
 
@@ -892,16 +897,13 @@ tucker_status walk_dot(tucker_handle* h, const RowSet& s, int64_t I1, const Walk
   const bool lvl2 = s.N >= 3 && s.N <= 5 && a.lsz[2] % 32 == 0 && wb.I2 > 0 &&
                     (double)wb.cap >= 4.0 * (double)I1 * (double)wb.I2 && smem2 <= 200 * 1024;
   if (lvl2) smem = smem2;
-  TK_COUNT(h);
   if (f32) {
     for (int n = 0; n < s.N; ++n) a.A32[n] = static_cast<const float*>(s.A[n]);
-    k_walk_v1<float><<<grid_for(h, I1 * a.lsz[1], 256), 256, 0, h->stream>>>(a);
-    TK_LAUNCH(h);
+    TK_CUDA(h, launch_dep(h, k_walk_v1<float>, grid_for(h, I1 * a.lsz[1], 256), 256, 0, a));
     TK_TRY(launch_by_order(h, lvl2 ? walk_dot2_kernel_t<float>(s.N) : walk_dot_kernel_t<float>(s.N),
                            g.maxP, smem, a));
   } else {
-    k_walk_v1<double><<<grid_for(h, I1 * a.lsz[1], 256), 256, 0, h->stream>>>(a);
-    TK_LAUNCH(h);
+    TK_CUDA(h, launch_dep(h, k_walk_v1<double>, grid_for(h, I1 * a.lsz[1], 256), 256, 0, a));
     TK_TRY(launch_by_order(h, lvl2 ? walk_dot2_kernel_t<double>(s.N) : walk_dot_kernel_t<double>(s.N),
                            g.maxP, smem, a));
   }
@@ -930,9 +932,7 @@ tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, const Wal
     if (two) lanes = two;
   }
   if (lanes) {
-    TK_COUNT(h);
-    lanes<<<(int)((g.maxP + WK_WARPS - 1) / WK_WARPS), WK_WARPS * 32, 0, h->stream>>>(a);
-    TK_LAUNCH(h);
+    TK_CUDA(h, launch_dep(h, lanes, (int)((g.maxP + WK_WARPS - 1) / WK_WARPS), WK_WARPS * 32, 0, a));
   } else {
     const size_t smem = (size_t)WK_WARPS * a.lstore * 8;
     TK_TRY(launch_by_order(h, walk_axpy_kernel(s.N), g.maxP, smem, a));
@@ -944,20 +944,13 @@ tucker_status walk_axpy(tucker_handle* h, const RowSet& s, int64_t I1, const Wal
   const int nb = (int)((I1 + chunk - 1) / chunk);
   const size_t fsm = (size_t)chunk * (a.lsz[1] + s.R[0]) * sizeof(double);
   if (fsm <= 48 * 1024 && (size_t)nb * s.d <= (size_t)I1 * a.lsz[1]) {
-    TK_COUNT(h);
-    k_walk_fold<<<nb, 256, fsm, h->stream>>>(a, chunk, a.W1);
-    TK_LAUNCH(h);
-    TK_COUNT(h);
-    k_walk_sum<<<ceil_div((int64_t)s.d * 8, 128), 128, 0, h->stream>>>(a.W1, nb, s.d, base, diag, y, out);
-    TK_LAUNCH(h);
+    TK_CUDA(h, launch_dep(h, k_walk_fold, nb, 256, fsm, a, chunk, a.W1));
+    TK_CUDA(h, launch_dep(h, k_walk_sum, ceil_div((int64_t)s.d * 8, 128), 128, 0, a.W1, nb, s.d, base,
+                          diag, y, out));
     return TUCKER_OK;
   }
-  TK_COUNT(h);
-  k_walk_reduce<<<grid_for(h, I1 * a.lsz[1], 256), 256, 0, h->stream>>>(a);
-  TK_LAUNCH(h);
-  TK_COUNT(h);
-  k_walk_expand<<<ceil_div(s.d, 8), 256, 0, h->stream>>>(a, base, diag, y, out);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_walk_reduce, grid_for(h, I1 * a.lsz[1], 256), 256, 0, a));
+  TK_CUDA(h, launch_dep(h, k_walk_expand, ceil_div(s.d, 8), 256, 0, a, base, diag, y, out));
   return TUCKER_OK;
 }
 
