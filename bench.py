@@ -59,11 +59,13 @@ def parse():
                    help="the smallest m on a x2 ladder from the workload's m whose median ridge-loss "
                         "ratio over 10 seeds is <= 1.01 (with --impl reference: by the oracle on "
                         "the host); prints its own JSON line, not the headline")
-    p.add_argument("--kernel-case", choices=["grouped", "walk2"], default=None,
+    p.add_argument("--kernel-case", choices=["grouped", "walk2", "headline"], default=None,
                    help="a small case of one kernel family for ncu captures (grouped: the "
                         "1024^3 Gram shapes, I_1 = 1024, d = 4096, m = 5e5, on a dense "
                         "1024 x 128 x 128 tensor; walk2: the 128^4 two-level walks at "
-                        "m = 8e5); prints its own JSON line, not the headline")
+                        "m = 8e5; headline: three sketched updates of the 512^3 workload at "
+                        "m = 1e5 and three exact ones, nothing else); prints its own JSON "
+                        "line, not the headline")
     p.add_argument("--stage-roofline", action="store_true",
                    help="time the sampler and the gather at 2^27 draws (their HBM/ALU rooflines); "
                         "prints its own JSON line, not the headline")
@@ -358,6 +360,25 @@ def run_kernel_case(args):
     import torch
     import synth
     from paper_2107_10654_gb300 import tucker as T
+    if args.kernel_case == "headline":
+        # the timed workload's kernels alone: its sample count at the 1.01 ladder (m* = 1e5)
+        w = synth.WORKLOADS[WORKLOAD]
+        P = synth.tucker_problem(w)
+        X = torch.from_numpy(P["X"]).cuda()
+        F = [torch.from_numpy(a).cuda() for a in P["factors"]]
+        h = T.Handle(solver=args.solver)
+        ms, ex = [], []
+        for _ in range(3):
+            st = T.tucker_core_update_sketched(h, X, F, w.lam, 100000, w.seed_sample, 0, "exact",
+                                               "tf32", stats=True)[1]
+            ms.append(st["ms_total"])
+        for _ in range(3):
+            T.tucker_core_update_exact(h, X, F, w.lam, "fp64")
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "kernel_case", "case": "headline", "workload": w.name,
+                          "m": 100000, "ms": ms}))
+        h.close()
+        return
     g = synth.rng(4321)
     if args.kernel_case == "walk2":
         dims, ranks, m = (128, 128, 128, 128), (8, 8, 8, 8), 800000

@@ -149,6 +149,7 @@ __device__ __forceinline__ void rows_contract(const T* const* rows, int nr, int 
 template <class T, int RP, bool SQ>
 __global__ void __launch_bounds__(256) k_ttm_last(const T* X, int64_t P, int I, const T* A, int R,
                                                   double* out, double* sq_partial) {
+  pdl_wait();
   constexpr int RB = RowBlock<RP>::RB;
   extern __shared__ unsigned char smraw[];
   T* At = reinterpret_cast<T*>(smraw);               // RP x I (zero rows beyond R)
@@ -208,6 +209,7 @@ template <class T, int RP>
 __global__ void __launch_bounds__(256) k_ttm_last2w(const T* X, int64_t pre, int I1, int I2,
                                                     const T* A1, int R1, const T* A2, int R2,
                                                     int nchunk, double* out) {
+  pdl_wait();
   constexpr int RB = RowBlock<RP>::RB;
   extern __shared__ unsigned char smraw[];
   T* At = reinterpret_cast<T*>(smraw);                         // RP x I2
@@ -270,6 +272,7 @@ __global__ void __launch_bounds__(256) k_ttm_last2w(const T* X, int64_t pre, int
 
 // out[p][e] = sum_c part[p][c][e] in increasing c.
 __global__ void k_sum_chunks(const double* part, int64_t pre, int nchunk, int RR, double* out) {
+  pdl_wait();
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < pre * RR;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = t / RR;
@@ -288,6 +291,7 @@ __global__ void k_sum_chunks(const double* part, int64_t pre, int nchunk, int RR
 template <class T, int RC>
 __global__ void __launch_bounds__(256) k_ttm_mid(const T* X, int64_t pre, int I, int64_t post,
                                                  const T* A, int R, double* out) {
+  pdl_wait();
   extern __shared__ unsigned char smraw[];
   T* As = reinterpret_cast<T*>(smraw);
   for (int e = threadIdx.x; e < I * R; e += blockDim.x) As[e] = A[e];
@@ -349,6 +353,7 @@ __global__ void __launch_bounds__(256) k_ttm_mid(const T* X, int64_t pre, int I,
 // expand:   out[p][i][q] = sum_{r<R} in[p][r][q] A[i][r]   (out middle dim I)
 __global__ void k_ttm_small(const double* in, int64_t pre, int64_t post, const void* A, int is64,
                             int I, int R, int contract, double* out) {
+  pdl_wait();
   const int K = contract ? I : R, M = contract ? R : I;
   const int64_t total = pre * M * post;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -370,6 +375,7 @@ __global__ void k_ttm_small(const double* in, int64_t pre, int64_t post, const v
 // for long contractions; fixed butterfly order.
 __global__ void k_ttm_small_warp(const double* in, int64_t pre, int64_t post, const void* A,
                                  int is64, int I, int R, int contract, double* out) {
+  pdl_wait();
   const int K = contract ? I : R, M = contract ? R : I;
   const int64_t total = pre * M * post;
   const int lane = threadIdx.x & 31;
@@ -397,6 +403,7 @@ __global__ void k_ttm_small_warp(const double* in, int64_t pre, int64_t post, co
 template <int RM>
 __global__ void k_ttm_small_rows(const double* in, int64_t pre, int64_t post, const void* A,
                                  int is64, int I, int R, double* out) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int q = lane % (int)post, kph = lane / (int)post, nph = 32 / (int)post;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -477,6 +484,7 @@ __global__ void __launch_bounds__(1024) k_kron_eig_core(EigArgs a) {
 __global__ void __launch_bounds__(256) k_residual_dense(const void* X, int is64, int64_t P, int I,
                                                         const double* T, const void* A, int R,
                                                         double* partial) {
+  pdl_wait();
   extern __shared__ double As[];             // I x R
   __shared__ double red[8];
   for (int e = threadIdx.x; e < I * R; e += blockDim.x) As[e] = load_as_double(A, e, is64);
@@ -508,6 +516,7 @@ __global__ void __launch_bounds__(256) k_residual_coo(const uint64_t* keys, cons
                                                       int is64, int64_t nnz, int I,
                                                       const double* T, const void* A, int R,
                                                       double* partial) {
+  pdl_wait();
   __shared__ double red[8];
   double acc = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
@@ -531,6 +540,7 @@ __global__ void __launch_bounds__(256) k_residual_coo(const uint64_t* keys, cons
 }
 
 __global__ void k_sum_partials(const double* partial, int n, double* out) {
+  pdl_wait();
   __shared__ double red[32];
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
@@ -546,6 +556,7 @@ __global__ void k_sum_partials(const double* partial, int n, double* out) {
 
 // sum of squares of a device FP64/FP32 array (block partials + final sum)
 __global__ void k_sumsq(const void* v, int is64, int64_t n, double* partial) {
+  pdl_wait();
   __shared__ double red[32];
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -572,6 +583,7 @@ __global__ void k_sumsq(const void* v, int is64, int64_t n, double* partial) {
 // well below the FP32 rounding of a single sum.  FP64 data: FP64 products.
 __global__ void __launch_bounds__(256) k_tensor_sumsq(const void* X, int is64, int vec,
                                                       int64_t n, double* partial) {
+  pdl_wait();
   __shared__ double red[8];
   double acc;
   if (is64) {
@@ -619,6 +631,7 @@ __global__ void __launch_bounds__(256) k_tensor_sumsq(const void* X, int is64, i
 // sum_i A^(N)[i][r] B[p][i] (one warp per entry, FP64).
 __global__ void k_kt_x_from_last(const double* B, int64_t pre, int64_t IN, const void* A,
                                  int is64, int RN, double* y) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (e >= pre * RN) return;
@@ -716,14 +729,8 @@ static tucker_status ttm_last_t(tucker_handle* h, const T* X, int64_t P, int I, 
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   if (sq && grid > sq_cap) return fail(h, TUCKER_EINTERNAL, "square-sum partials too few");
-  TK_COUNT(h);
-  k<<<(int)grid, 256, smem, h->stream>>>(X, P, I, A, R, out, sq_partial);
-  TK_LAUNCH(h);
-  if (sq) {
-    TK_COUNT(h);
-    k_sum_partials<<<1, 1024, 0, h->stream>>>(sq_partial, (int)grid, sq_out);
-    TK_LAUNCH(h);
-  }
+  TK_CUDA(h, launch_dep(h, k, (int)grid, 256, smem, X, P, I, A, R, out, sq_partial));
+  if (sq) TK_CUDA(h, launch_dep(h, k_sum_partials, 1, 1024, 0, sq_partial, (int)grid, sq_out));
   return TUCKER_OK;
 }
 
@@ -747,15 +754,14 @@ tucker_status ttm_mid(tucker_handle* h, const void* X, int is64, int64_t pre, in
   if (is64) {
     auto k = R <= 8 ? k_ttm_mid<double, 8> : k_ttm_mid<double, 16>;
     TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    TK_COUNT(h);
-    k<<<grid, 256, smem, h->stream>>>((const double*)X, pre, I, post, (const double*)A, R, out);
+    TK_CUDA(h, launch_dep(h, k, grid, 256, smem, (const double*)X, pre, I, post, (const double*)A,
+                          R, out));
   } else {
     auto k = R <= 8 ? k_ttm_mid<float, 8> : k_ttm_mid<float, 16>;
     TK_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    TK_COUNT(h);
-    k<<<grid, 256, smem, h->stream>>>((const float*)X, pre, I, post, (const float*)A, R, out);
+    TK_CUDA(h, launch_dep(h, k, grid, 256, smem, (const float*)X, pre, I, post, (const float*)A, R,
+                          out));
   }
-  TK_LAUNCH(h);
   return TUCKER_OK;
 }
 
@@ -763,20 +769,18 @@ tucker_status ttm_small(tucker_handle* h, const double* in, int64_t pre, int64_t
                         const void* A, int is64, int I, int R, int contract, double* out) {
   const int64_t total = pre * (contract ? R : I) * post;
   const int K = contract ? I : R;
-  TK_COUNT(h);
   if (contract && K >= 64 && post <= 32 && 32 % post == 0 && R <= 16) {
     const int64_t blocks = (pre * 32 + 255) / 256;
     const int grid = (int)std::min<int64_t>(blocks, (int64_t)h->num_sms * 16);
-    if (R <= 8)
-      k_ttm_small_rows<8><<<grid, 256, 0, h->stream>>>(in, pre, post, A, is64, I, R, out);
-    else
-      k_ttm_small_rows<16><<<grid, 256, 0, h->stream>>>(in, pre, post, A, is64, I, R, out);
-  } else if (K >= 64 && total < (int64_t)h->num_sms * 2048)
-    k_ttm_small_warp<<<grid_for(h, total * 32), 256, 0, h->stream>>>(in, pre, post, A, is64, I, R,
-                                                                    contract, out);
-  else
-    k_ttm_small<<<grid_for(h, total), 256, 0, h->stream>>>(in, pre, post, A, is64, I, R, contract, out);
-  TK_LAUNCH(h);
+    TK_CUDA(h, launch_dep(h, R <= 8 ? k_ttm_small_rows<8> : k_ttm_small_rows<16>, grid, 256, 0, in,
+                          pre, post, A, is64, I, R, out));
+  } else if (K >= 64 && total < (int64_t)h->num_sms * 2048) {
+    TK_CUDA(h, launch_dep(h, k_ttm_small_warp, grid_for(h, total * 32), 256, 0, in, pre, post, A,
+                          is64, I, R, contract, out));
+  } else {
+    TK_CUDA(h, launch_dep(h, k_ttm_small, grid_for(h, total), 256, 0, in, pre, post, A, is64, I, R,
+                          contract, out));
+  }
   return TUCKER_OK;
 }
 
@@ -802,15 +806,11 @@ static tucker_status ttm_last2_t(tucker_handle* h, const T* X, int64_t pre, int 
   const int64_t items = pre * nchunk;
   if (grid * 8 > items) grid = (items + 7) / 8;
   const int RR = R1 * R2;
-  TK_COUNT(h);
-  k<<<(int)grid, 256, smem, h->stream>>>(X, pre, I1, I2, A1, R1, A2, R2, nchunk,
-                                         nchunk > 1 ? part : out);
-  TK_LAUNCH(h);
-  if (nchunk > 1) {
-    TK_COUNT(h);
-    k_sum_chunks<<<ceil_div(pre * RR, 256), 256, 0, h->stream>>>(part, pre, nchunk, RR, out);
-    TK_LAUNCH(h);
-  }
+  TK_CUDA(h, launch_dep(h, k, (int)grid, 256, smem, X, pre, I1, I2, A1, R1, A2, R2, nchunk,
+                        nchunk > 1 ? part : out));
+  if (nchunk > 1)
+    TK_CUDA(h, launch_dep(h, k_sum_chunks, ceil_div(pre * RR, 256), 256, 0, part, pre, nchunk, RR,
+                          out));
   return TUCKER_OK;
 }
 
@@ -965,41 +965,28 @@ tucker_status residual_sq(tucker_handle* h, const FactorSet& F, const tucker_ten
     const size_t smem = (size_t)I * R * 8;
     TK_CUDA(h, cudaFuncSetAttribute(k_residual_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
-    TK_COUNT(h);
-    k_residual_dense<<<grid, 256, smem, h->stream>>>(X->dense, F.is64, P, I, T, F.A[N - 1], R,
-                                                    partial);
+    TK_CUDA(h, launch_dep(h, k_residual_dense, grid, 256, smem, X->dense, F.is64, P, I,
+                          (const double*)T, F.A[N - 1], R, partial));
   } else {
-    TK_COUNT(h);
-    k_residual_coo<<<grid, 256, 0, h->stream>>>(X->keys, X->vals, F.is64, X->nnz, I, T,
-                                               F.A[N - 1], R, partial);
+    TK_CUDA(h, launch_dep(h, k_residual_coo, grid, 256, 0, X->keys, X->vals, F.is64, X->nnz, I,
+                          (const double*)T, F.A[N - 1], R, partial));
   }
-  TK_LAUNCH(h);
-  TK_COUNT(h);
-  k_sum_partials<<<1, 1024, 0, h->stream>>>(partial, grid, out);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_sum_partials, 1, 1024, 0, (const double*)partial, grid, out));
   return TUCKER_OK;
 }
 
 tucker_status sumsq(tucker_handle* h, const void* v, int is64, int64_t n, double* partial,
                     int npartial, double* out) {
-  TK_COUNT(h);
-  k_sumsq<<<npartial, 256, 0, h->stream>>>(v, is64, n, partial);
-  TK_LAUNCH(h);
-  TK_COUNT(h);
-  k_sum_partials<<<1, 1024, 0, h->stream>>>(partial, npartial, out);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_sumsq, npartial, 256, 0, v, is64, n, partial));
+  TK_CUDA(h, launch_dep(h, k_sum_partials, 1, 1024, 0, (const double*)partial, npartial, out));
   return TUCKER_OK;
 }
 
 tucker_status tensor_sumsq(tucker_handle* h, const void* X, int is64, int64_t n, double* partial,
                            int npartial, double* out) {
-  TK_COUNT(h);
   const int vec = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
-  k_tensor_sumsq<<<npartial, 256, 0, h->stream>>>(X, is64, vec, n, partial);
-  TK_LAUNCH(h);
-  TK_COUNT(h);
-  k_sum_partials<<<1, 1024, 0, h->stream>>>(partial, npartial, out);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_tensor_sumsq, npartial, 256, 0, X, is64, vec, n, partial));
+  TK_CUDA(h, launch_dep(h, k_sum_partials, 1, 1024, 0, (const double*)partial, npartial, out));
   return TUCKER_OK;
 }
 
@@ -1007,10 +994,8 @@ tucker_status kt_x_from_last(tucker_handle* h, const FactorSet& F, const double*
   const int N = F.N, RN = F.R[N - 1];
   const int64_t pre = F.d / RN, IN = F.I[N - 1];
   const int64_t warps = pre * RN;
-  TK_COUNT(h);
-  k_kt_x_from_last<<<ceil_div(warps * 32, 256), 256, 0, h->stream>>>(B, pre, IN, F.A[N - 1],
-                                                                     F.is64, RN, y);
-  TK_LAUNCH(h);
+  TK_CUDA(h, launch_dep(h, k_kt_x_from_last, ceil_div(warps * 32, 256), 256, 0, B, pre, IN,
+                        F.A[N - 1], F.is64, RN, y));
   return TUCKER_OK;
 }
 
