@@ -34,7 +34,7 @@ def _first_statement(src, kernel):
     out = []
     for m in re.finditer(r"__global__[^;{]*?\b" + re.escape(kernel) + r"\s*\(", src):
         body = src.index("{", m.end())
-        # skip the parameter list's closing parenthesis to the body's brace
+        # the body opens at the first brace after the parameter list
         stmt = src[body + 1:].lstrip().split("\n", 1)[0].strip()
         out.append(stmt)
     return out
