@@ -38,7 +38,8 @@ tucker_status launch_gather(tucker_handle* h, const FactorSet& F, const uint64_t
 tucker_status launch_prob_tables(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
                                  double* ptab);
 tucker_status launch_cdf_from_lev(tucker_handle* h, int N, const int64_t* I,
-                                  const double* const* lev, uint64_t* const* cdf);
+                                  const double* const* lev, uint64_t* const* cdf,
+                                  bool dep = false);
 int gram_simt_splits(tucker_handle* h, int d, int64_t cap);
 size_t gram_simt_partial_bytes(int d, int nsplit, int is64);
 tucker_status launch_gram_simt(tucker_handle* h, const RowSet& s, int use64, int nsplit,

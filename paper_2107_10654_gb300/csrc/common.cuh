@@ -122,8 +122,10 @@ tucker_status fail(tucker_handle* h, tucker_status s, const char* fmt, ...);
 // launch latency between short dependent kernels.  Every kernel launched this
 // way calls pdl_wait() first, before any access to global memory, so it sees
 // all of the previous kernel's writes and overwrites nothing that kernel reads.
-// Used only where the previous operation on the stream is a kernel of the same
-// stream (not behind an event wait on another stream).
+// Used where the previous operation on the stream is one of this library's
+// kernels (an event record may sit in between), or where the host has just
+// synchronised the stream; never right behind an event wait on another stream
+// or behind a memset or copy whose data the kernel reads.
 template <class... KArgs, class... Args>
 inline cudaError_t launch_dep(tucker_handle* h, void (*k)(KArgs...), dim3 grid, dim3 block,
                               size_t smem, Args... args) {

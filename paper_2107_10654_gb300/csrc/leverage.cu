@@ -321,7 +321,8 @@ __global__ void __launch_bounds__(256) k_leverage_rows(LevRowArgs a) {
 }
 
 tucker_status launch_cdf_from_lev(tucker_handle* h, int N, const int64_t* I,
-                                  const double* const* lev, uint64_t* const* cdf);
+                                  const double* const* lev, uint64_t* const* cdf,
+                                  bool dep = false);
 
 // q_i = floor(clamp(l_i,0,1) 2^32) and inclusive prefix sums from given scores
 // (the sampler's integer CDF), one CTA per mode.
@@ -354,14 +355,23 @@ __global__ void __launch_bounds__(LEV_THREADS) k_cdf_from_lev(CdfArgs a) {
   if (threadIdx.x == 0 && carry == 0) set_status(a.status, DEV_RANK);
 }
 
+// dep: the previous operation on the stream is this library's leverage kernel, so
+// the launch may depend on it programmatically (otherwise it is launched in full
+// order: the scores come from the caller, behind a memset of the status word)
 tucker_status launch_cdf_from_lev(tucker_handle* h, int N, const int64_t* I,
-                                  const double* const* lev, uint64_t* const* cdf) {
+                                  const double* const* lev, uint64_t* const* cdf, bool dep) {
   CdfArgs a;
   memset(&a, 0, sizeof(a));
   a.N = N;
   for (int n = 0; n < N; ++n) { a.I[n] = I[n]; a.lev[n] = lev[n]; a.cdf[n] = cdf[n]; }
   a.status = h->d_status;
-  TK_CUDA(h, launch_dep(h, k_cdf_from_lev, N, LEV_THREADS, 0, a));
+  if (dep) {
+    TK_CUDA(h, launch_dep(h, k_cdf_from_lev, N, LEV_THREADS, 0, a));
+  } else {
+    TK_COUNT(h);
+    k_cdf_from_lev<<<N, LEV_THREADS, 0, h->stream>>>(a);
+    TK_LAUNCH(h);
+  }
   return TUCKER_OK;
 }
 
@@ -425,7 +435,7 @@ tucker_status launch_leverage(tucker_handle* h, const FactorSet& F, double* cons
   if (gx < 1) gx = 1;
   TK_CUDA(h, launch_dep(h, k_leverage_rows, dim3(gx, F.N), 256,
                         (size_t)(maxR * maxR + 256) * sizeof(double), ra));
-  return launch_cdf_from_lev(h, F.N, F.I, lev, cdf);
+  return launch_cdf_from_lev(h, F.N, F.I, lev, cdf, true);
 }
 
 // gram[n] = A^(n)T A^(n) (full, row-major) from the chunk partials, summed in

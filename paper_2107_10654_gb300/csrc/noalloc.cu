@@ -19,7 +19,8 @@
 namespace tk {
 
 tucker_status launch_cdf_from_lev(tucker_handle* h, int N, const int64_t* I,
-                                  const double* const* lev, uint64_t* const* cdf);
+                                  const double* const* lev, uint64_t* const* cdf,
+                                  bool dep = false);
 size_t sample_keys_scratch(const FactorSet& F, bool observed);
 tucker_status sample_keys(tucker_handle* h, const FactorSet& F, const uint64_t* const* cdf,
                           int64_t m, uint64_t seed, uint64_t sweep, int reg,
