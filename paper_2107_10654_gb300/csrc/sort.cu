@@ -153,8 +153,10 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const uint64_t* in, u
 // CL_MAX_WIDE keys).  The keys stay in the CTAs' shared memory between passes
 // (CTA c holds sorted positions [c CL_CHUNK, (c + 1) CL_CHUNK)): a pass reads
 // its 8192 keys (32 warps x 8 rounds x 32 lanes) from its own shared memory,
-// ranks them with the same stable match_any scheme as above, and stores each
-// key straight into the shared memory of the CTA that owns its new position.
+// ranks them stably as above (per-warp digit counts, rank within a round from
+// the lanes holding the same digit), finding those lanes with one ballot per
+// digit bit instead of match_any, and stores each key straight into the shared
+// memory of the CTA that owns its new position.
 // Digits are up to 10 bits (as many passes as the key range needs, all of
 // equal width), per-CTA digit totals are exchanged through distributed shared
 // memory, and cluster barriers separate the passes.
